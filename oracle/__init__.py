@@ -1,0 +1,245 @@
+"""FP64 CPU oracle of the line radiative-transfer march -- TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of `bench.py` may import
+this package. It wraps `rt_oracle.c` (plain C, double precision, OpenMP over pixel rows)
+with ctypes and shares no code with the CUDA library.
+
+Problems are passed as any object with the attributes of the C struct `orc_problem`
+(grid, node fields, geometry, view and line constants); arrays are converted to float64.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rt_oracle.c")
+_HDR = os.path.join(_HERE, "rt_oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, IEEE semantics, OpenMP)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                               "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("nr", C.c_int), ("nz", C.c_int), ("r_log", C.c_int),
+        ("r_in_au", C.c_double), ("r_out_au", C.c_double), ("zr_max", C.c_double),
+        ("T", C.POINTER(C.c_double)), ("n_h2", C.POINTER(C.c_double)),
+        ("vturb", C.POINTER(C.c_double)), ("h_lo", C.POINTER(C.c_double)),
+        ("h_hi", C.POINTER(C.c_double)),
+        ("x_co", C.c_double), ("edge_w", C.c_double), ("vturb_mach", C.c_int),
+        ("incl_deg", C.c_double), ("pa_deg", C.c_double), ("dist_pc", C.c_double),
+        ("mstar_msun", C.c_double), ("vsys_kms", C.c_double),
+        ("nx", C.c_int), ("ny", C.c_int), ("half_fov_au", C.c_double), ("nch", C.c_int),
+        ("v_kms", C.POINTER(C.c_double)), ("n_samples", C.c_int), ("I0", C.c_double),
+        ("units", C.c_int),
+        ("nu0_hz", C.c_double), ("A_ul", C.c_double), ("B_rot_hz", C.c_double),
+        ("m_co_amu", C.c_double), ("m_mol_amu", C.c_double), ("J_u", C.c_int),
+    ]
+
+
+class _MLP(C.Structure):
+    _fields_ = [
+        ("n_freq", C.c_int), ("B", C.POINTER(C.c_double)), ("n_layers", C.c_int),
+        ("dims", C.POINTER(C.c_int)), ("W", C.POINTER(C.POINTER(C.c_double))),
+        ("b", C.POINTER(C.POINTER(C.c_double))), ("h_scale", C.c_double),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            dp = C.POINTER(C.c_double)
+            pp = C.POINTER(_Problem)
+            lib.orc_render.argtypes = [pp, dp, C.c_int]
+            lib.orc_render_pixels.argtypes = [pp, C.POINTER(C.c_longlong), C.c_int, dp, C.c_int]
+            lib.orc_ray.argtypes = [pp, C.c_int, C.c_int, dp, dp, dp, dp]
+            lib.orc_point.argtypes = [pp, C.c_double, C.c_double, C.c_double, C.c_double, dp]
+            lib.orc_partition.argtypes = [C.c_double, C.c_double]
+            lib.orc_partition.restype = C.c_double
+            lib.orc_render_adjoint.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
+            lib.orc_mlp_eval.argtypes = [C.POINTER(_MLP), dp, C.c_int, dp]
+            lib.orc_render_mlp.argtypes = [pp, C.POINTER(_MLP), C.POINTER(C.c_longlong),
+                                           C.c_int, dp, C.c_int]
+            _lib = lib
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class _Packed:
+    """Keeps the float64 copies alive while the struct is in use."""
+
+    def __init__(self, p):
+        self.keep = []
+
+        def arr(x):
+            a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+            self.keep.append(a)
+            return _dptr(a)
+
+        s = _Problem()
+        s.nr, s.nz, s.r_log = int(p.nr), int(p.nz), int(p.r_log)
+        s.r_in_au, s.r_out_au, s.zr_max = float(p.r_in_au), float(p.r_out_au), float(p.zr_max)
+        s.T, s.n_h2, s.vturb = arr(p.T), arr(p.n_h2), arr(p.vturb)
+        s.h_lo, s.h_hi = arr(p.h_lo), arr(p.h_hi)
+        s.x_co, s.edge_w, s.vturb_mach = float(p.x_co), float(p.edge_w), int(p.vturb_mach)
+        s.incl_deg, s.pa_deg, s.dist_pc = float(p.incl_deg), float(p.pa_deg), float(p.dist_pc)
+        s.mstar_msun, s.vsys_kms = float(p.mstar_msun), float(p.vsys_kms)
+        s.nx, s.ny, s.half_fov_au = int(p.nx), int(p.ny), float(p.half_fov_au)
+        v = np.asarray(p.v_kms, dtype=np.float64)
+        s.nch, s.v_kms = int(v.size), arr(v)
+        s.n_samples, s.I0, s.units = int(p.n_samples), float(p.I0), int(p.units)
+        s.nu0_hz, s.A_ul, s.B_rot_hz = float(p.nu0_hz), float(p.A_ul), float(p.B_rot_hz)
+        s.m_co_amu, s.m_mol_amu, s.J_u = float(p.m_co_amu), float(p.m_mol_amu), int(p.J_u)
+        self.s = s
+        self.nch = s.nch
+
+
+class _PackedMLP:
+    def __init__(self, w):
+        self.keep = []
+        B = np.ascontiguousarray(np.asarray(w.B, dtype=np.float64))
+        Ws = [np.ascontiguousarray(np.asarray(x, dtype=np.float64)) for x in w.W]
+        bs = [np.ascontiguousarray(np.asarray(x, dtype=np.float64)) for x in w.b]
+        dims = np.array([Ws[0].shape[1]] + [x.shape[0] for x in Ws], dtype=np.int32)
+        Wp = (C.POINTER(C.c_double) * len(Ws))(*[_dptr(x) for x in Ws])
+        bp = (C.POINTER(C.c_double) * len(bs))(*[_dptr(x) for x in bs])
+        self.keep += [B, Ws, bs, dims, Wp, bp]
+        m = _MLP()
+        m.n_freq = int(B.shape[0])
+        m.B = _dptr(B)
+        m.n_layers = len(Ws)
+        m.dims = dims.ctypes.data_as(C.POINTER(C.c_int))
+        m.W = Wp
+        m.b = bp
+        m.h_scale = float(getattr(w, "h_scale", 0.02))
+        self.m = m
+        self.n_out = int(dims[-1])
+
+
+def _threads(nthreads):
+    return int(nthreads) if nthreads else 0
+
+
+def render(p, nthreads: int = 0) -> np.ndarray:
+    """Cube [nch][ny][nx] in float64."""
+    lib = _load()
+    pk = _Packed(p)
+    cube = np.zeros((pk.nch, int(p.ny), int(p.nx)), dtype=np.float64)
+    rc = lib.orc_render(C.byref(pk.s), _dptr(cube), _threads(nthreads))
+    if rc:
+        raise ValueError("oracle: invalid problem")
+    return cube
+
+
+def render_pixels(p, pix, nthreads: int = 0) -> np.ndarray:
+    """Spectra [npix][nch] of flat pixel indices pix = iy*nx + ix."""
+    lib = _load()
+    pk = _Packed(p)
+    pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int64))
+    out = np.zeros((pix.size, pk.nch), dtype=np.float64)
+    rc = lib.orc_render_pixels(C.byref(pk.s), pix.ctypes.data_as(C.POINTER(C.c_longlong)),
+                               int(pix.size), _dptr(out), _threads(nthreads))
+    if rc:
+        raise ValueError("oracle: invalid problem")
+    return out
+
+
+def ray(p, ix: int, iy: int):
+    """(hit, s_in, s_out, P0[3], omega[3]) of one pixel's ray (au)."""
+    lib = _load()
+    pk = _Packed(p)
+    s0, s1 = C.c_double(), C.c_double()
+    P0 = np.zeros(3)
+    om = np.zeros(3)
+    hit = lib.orc_ray(C.byref(pk.s), int(ix), int(iy), C.byref(s0), C.byref(s1), _dptr(P0),
+                      _dptr(om))
+    return bool(hit), s0.value, s1.value, P0, om
+
+
+POINT_KEYS = ("j", "beta", "T", "n_h2", "X_co", "v_los_kms", "alpha_kms", "n_u", "n_l",
+              "phi", "S", "vturb")
+
+
+def point(p, x: float, y: float, z: float, v_kms: float) -> dict:
+    """Local quantities at a disk-frame point (au) for one channel velocity."""
+    lib = _load()
+    pk = _Packed(p)
+    out = np.zeros(12)
+    gas = lib.orc_point(C.byref(pk.s), float(x), float(y), float(z), float(v_kms), _dptr(out))
+    d = dict(zip(POINT_KEYS, out.tolist()))
+    d["gas"] = bool(gas)
+    return d
+
+
+def partition(T: float, B_rot_hz: float) -> float:
+    return float(_load().orc_partition(float(T), float(B_rot_hz)))
+
+
+def render_adjoint(p, dL_dcube: np.ndarray, nthreads: int = 0):
+    """(cube, grads) with grads = dict(T, n_h2, vturb [nz][nr], h_lo, h_hi [nr])."""
+    lib = _load()
+    pk = _Packed(p)
+    g = np.ascontiguousarray(np.asarray(dL_dcube, dtype=np.float64))
+    cube = np.zeros((pk.nch, int(p.ny), int(p.nx)), dtype=np.float64)
+    shp = (int(p.nz), int(p.nr))
+    dT, dn, dvt = np.zeros(shp), np.zeros(shp), np.zeros(shp)
+    dlo, dhi = np.zeros(int(p.nr)), np.zeros(int(p.nr))
+    rc = lib.orc_render_adjoint(C.byref(pk.s), _dptr(g), _dptr(cube), _dptr(dT), _dptr(dn),
+                                _dptr(dvt), _dptr(dlo), _dptr(dhi), _threads(nthreads))
+    if rc:
+        raise ValueError("oracle: invalid problem")
+    return cube, dict(T=dT, n_h2=dn, vturb=dvt, h_lo=dlo, h_hi=dhi)
+
+
+def mlp_eval(w, x: np.ndarray) -> np.ndarray:
+    """Network outputs [npts][n_out] at inputs x [npts][2] = (rhat, zhat)."""
+    lib = _load()
+    pm = _PackedMLP(w)
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 2))
+    out = np.zeros((x.shape[0], pm.n_out))
+    rc = lib.orc_mlp_eval(C.byref(pm.m), _dptr(x), int(x.shape[0]), _dptr(out))
+    if rc:
+        raise ValueError("oracle: invalid network")
+    return out
+
+
+def render_mlp(p, w, pix=None, nthreads: int = 0) -> np.ndarray:
+    """Neural-field render: full cube [nch][ny][nx] (pix None) or spectra [npix][nch]."""
+    lib = _load()
+    pk = _Packed(p)
+    pm = _PackedMLP(w)
+    if pix is None:
+        out = np.zeros((pk.nch, int(p.ny), int(p.nx)))
+        rc = lib.orc_render_mlp(C.byref(pk.s), C.byref(pm.m), None, 0, _dptr(out),
+                                _threads(nthreads))
+    else:
+        pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int64))
+        out = np.zeros((pix.size, pk.nch))
+        rc = lib.orc_render_mlp(C.byref(pk.s), C.byref(pm.m),
+                                pix.ctypes.data_as(C.POINTER(C.c_longlong)), int(pix.size),
+                                _dptr(out), _threads(nthreads))
+    if rc:
+        raise ValueError("oracle: invalid problem or network")
+    return out

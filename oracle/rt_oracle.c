@@ -1,0 +1,676 @@
+/*
+ * FP64 CPU oracle for the line radiative-transfer march -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow and deliberately unoptimised: every step is written in the order and notation
+ * of arXiv 2509.03623, Methods, "Line Radiative Transfer with RadJAX":
+ *   I_nu = int j_nu(s') exp(-tau_nu(s,s')) ds'          (Eq. rt-int)
+ *   tau_nu(s,s') = int_{s'}^{s} beta_nu ds''             (Eq. optical_depth)
+ *   j_nu    = h nu0/(4 pi) n_u A_ul phi                  (emissivity equation)
+ *   beta_nu = h nu0/(4 pi) (n_l B_lu - n_u B_ul) phi     (extinction equation)
+ *   phi(nu) = c/(nu0 alpha sqrt(pi)) exp(-(c[nu - nu0(1-dnu)]/(nu0 alpha))^2),
+ *             dnu = omega.v/c                            (line-profile equation)
+ *   alpha   = sqrt(2kT/m_CO + v_turb^2 c_s^2), c_s^2 = 2kT/m_mol (line-width equations)
+ *   v_phi^2/r = G M r/(r^2+z^2)^{3/2}                    (Keplerian term of
+ *                                                          Eq. gas_velocity_pressure)
+ * with LTE (Boltzmann) populations of a rigid rotor. Where the paper is silent the readings
+ * are stated at the point of use (sampling rule, grid interpolation, CO-layer edges, sign and
+ * frame conventions); the design notes list them all.
+ *
+ * Only tests, the smoke check and the CPU-baseline leg of the benchmark may load this file.
+ * It shares nothing with the CUDA library.
+ */
+#include "rt_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* CGS constants: CODATA 2018 exact SI-defining values, IAU 2012/2015 nominal values. */
+static const double H_PLANCK = 6.62607015e-27;  /* erg s */
+static const double K_BOLTZ = 1.380649e-16;     /* erg K^-1 */
+static const double C_LIGHT = 2.99792458e10;    /* cm s^-1 */
+static const double AMU_G = 1.66053906660e-24;  /* g */
+static const double GM_SUN = 1.3271244e26;      /* cm^3 s^-2, IAU 2015 nominal */
+static const double AU_CM = 1.495978707e13;     /* cm, IAU 2012 */
+/* 1 au at 1 pc subtends 1 arcsec (definition of the parsec). */
+static const double ARCSEC_RAD = M_PI / 648000.0;
+
+/* ---------------------------------------------------------------------------------------- */
+/* Molecular data: LTE rigid rotor (the paper precomputes Boltzmann populations from       */
+/* tabulated levels; the table is replaced by E_J = h B J(J+1), g_J = 2J+1).                */
+/* ---------------------------------------------------------------------------------------- */
+
+static double rot_B(const orc_problem *p) {
+  return p->B_rot_hz > 0 ? p->B_rot_hz : p->nu0_hz / (2.0 * p->J_u);
+}
+
+double orc_partition(double T, double B_rot_hz) {
+  /* Z(T) = sum_J (2J+1) exp(-h B J(J+1)/kT), summed until the term is below 1e-17 Z. */
+  double Z = 0.0;
+  for (int J = 0; J < 100000; J++) {
+    double term = (2.0 * J + 1.0) * exp(-H_PLANCK * B_rot_hz * J * (J + 1.0) / (K_BOLTZ * T));
+    Z += term;
+    if (J > 2 && term < 1e-17 * Z) break;
+  }
+  return Z;
+}
+
+/* Mean level energy <E> = sum g E exp(-E/kT) / Z (for dZ/dT = Z <E>/(k T^2)). */
+static double mean_energy(double T, double B) {
+  double Z = 0.0, EZ = 0.0;
+  for (int J = 0; J < 100000; J++) {
+    double E = H_PLANCK * B * J * (J + 1.0);
+    double term = (2.0 * J + 1.0) * exp(-E / (K_BOLTZ * T));
+    Z += term;
+    EZ += E * term;
+    if (J > 2 && term < 1e-17 * Z) break;
+  }
+  return EZ / Z;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Geometry                                                                                */
+/* ---------------------------------------------------------------------------------------- */
+
+static double half_fov(const orc_problem *p) {
+  return p->half_fov_au > 0 ? p->half_fov_au : 1.1 * p->r_out_au;
+}
+
+/* Ray through pixel (ix, iy). Disk frame: +z along the disk angular momentum. Observer
+   direction n_obs = (0, -sin i, cos i); sky basis e_x = (1,0,0), e_y = (0, cos i, sin i)
+   (e_x x e_y = n_obs). Pixel centres (i + 1/2 - n/2) * 2 half_fov / n au; the position
+   angle rotates image coordinates into the sky basis. The ray direction omega = -n_obs
+   points away from the observer (backward ray tracing), so s increases front to back. */
+static void ray_setup(const orc_problem *p, int ix, int iy, double P0[3], double om[3]) {
+  double hf = half_fov(p);
+  double X = (ix + 0.5 - 0.5 * p->nx) * (2.0 * hf / p->nx);
+  double Y = (iy + 0.5 - 0.5 * p->ny) * (2.0 * hf / p->ny);
+  double pa = p->pa_deg * M_PI / 180.0, inc = p->incl_deg * M_PI / 180.0;
+  double xs = X * cos(pa) + Y * sin(pa);
+  double ys = -X * sin(pa) + Y * cos(pa);
+  double ex[3] = {1.0, 0.0, 0.0};
+  double ey[3] = {0.0, cos(inc), sin(inc)};
+  double nobs[3] = {0.0, -sin(inc), cos(inc)};
+  for (int a = 0; a < 3; a++) {
+    P0[a] = xs * ex[a] + ys * ey[a];
+    om[a] = -nobs[a];
+  }
+}
+
+/* Chord of the ray through the bounding cylinder r <= r_out, |z| <= zr_max r_out
+   (sampling rule: the paper does not state one). */
+static int chord(const orc_problem *p, const double P0[3], const double om[3], double *s0,
+                 double *s1) {
+  double R = p->r_out_au, H = p->zr_max * p->r_out_au;
+  double lo = -INFINITY, hi = INFINITY;
+  if (om[2] != 0.0) {
+    double t1 = (-H - P0[2]) / om[2], t2 = (H - P0[2]) / om[2];
+    lo = fmax(lo, fmin(t1, t2));
+    hi = fmin(hi, fmax(t1, t2));
+  } else if (fabs(P0[2]) > H) {
+    return 0;
+  }
+  double a = om[0] * om[0] + om[1] * om[1];
+  double b = 2.0 * (P0[0] * om[0] + P0[1] * om[1]);
+  double c = P0[0] * P0[0] + P0[1] * P0[1] - R * R;
+  if (a > 0.0) {
+    double disc = b * b - 4.0 * a * c;
+    if (disc < 0.0) return 0;
+    double sq = sqrt(disc);
+    lo = fmax(lo, (-b - sq) / (2.0 * a));
+    hi = fmin(hi, (-b + sq) / (2.0 * a));
+  } else if (c > 0.0) {
+    return 0;
+  }
+  if (!(hi > lo)) return 0;
+  *s0 = lo;
+  *s1 = hi;
+  return 1;
+}
+
+int orc_ray(const orc_problem *p, int ix, int iy, double *s_in, double *s_out, double *P0,
+            double *omega) {
+  double P[3], om[3];
+  ray_setup(p, ix, iy, P, om);
+  for (int a = 0; a < 3; a++) {
+    P0[a] = P[a];
+    omega[a] = om[a];
+  }
+  return chord(p, P, om, s_in, s_out);
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Local state at a point                                                                  */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct {
+  int gas;
+  /* interpolation: r-cell i0 with weight fr, (z/r)-cell j0 with weight fz */
+  int i0, j0;
+  double fr, fz;
+  double zr;                  /* |z|/r */
+  double T, n, vt, hlo, hhi;  /* interpolated primitives */
+  double sa, sb, X;           /* CO-layer edge factors and abundance */
+  double vlos;                /* cm/s, positive receding */
+  double alpha;               /* cm/s */
+  double Z, fu, fl;           /* partition function, n_u/n_CO, n_l/n_CO */
+  double nco, nu_, nl_;       /* n_CO, n_u, n_l */
+  double D;                   /* n_l B_lu - n_u B_ul */
+  double S;                   /* j/beta */
+} pt;
+
+static double bilerp(const double *F, int nr, int i0, int j0, double fr, double fz) {
+  return (1.0 - fr) * (1.0 - fz) * F[j0 * nr + i0] + fr * (1.0 - fz) * F[j0 * nr + i0 + 1] +
+         (1.0 - fr) * fz * F[(j0 + 1) * nr + i0] + fr * fz * F[(j0 + 1) * nr + i0 + 1];
+}
+
+static double logistic(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+#define ORC_MLP_MAXW 1024
+
+static void mlp_forward(const orc_mlp *m, const double xin[2], double *out);
+
+/* Evaluate the local state at disk-frame point P (au). */
+static void eval_point(const orc_problem *p, const orc_mlp *m, const double P[3],
+                       const double om[3], pt *st) {
+  memset(st, 0, sizeof(*st));
+  double x = P[0], y = P[1], z = P[2];
+  double r = sqrt(x * x + y * y);
+  double zr = r > 0 ? fabs(z) / r : INFINITY;
+  st->zr = zr;
+  /* Outside the grid (reading): r < r_in or z/r > zr_max carries no gas. */
+  if (!(r >= p->r_in_au) || !(zr <= p->zr_max)) return;
+  /* Fractional node coordinates: log-spaced (or linear) in r, linear in z/r; clamped to
+     the last cell. */
+  double u;
+  if (p->r_log)
+    u = (log(r) - log(p->r_in_au)) / (log(p->r_out_au) - log(p->r_in_au)) * (p->nr - 1);
+  else
+    u = (r - p->r_in_au) / (p->r_out_au - p->r_in_au) * (p->nr - 1);
+  if (u > p->nr - 1) u = p->nr - 1;
+  if (u < 0) u = 0;
+  int i0 = (int)floor(u);
+  if (i0 > p->nr - 2) i0 = p->nr - 2;
+  double w = zr / p->zr_max * (p->nz - 1);
+  if (w > p->nz - 1) w = p->nz - 1;
+  int j0 = (int)floor(w);
+  if (j0 > p->nz - 2) j0 = p->nz - 2;
+  st->i0 = i0;
+  st->j0 = j0;
+  st->fr = u - i0;
+  st->fz = w - j0;
+  /* Bilinear interpolation of the primitive fields (mirror symmetry: |z|). */
+  st->T = bilerp(p->T, p->nr, i0, j0, st->fr, st->fz);
+  st->n = bilerp(p->n_h2, p->nr, i0, j0, st->fr, st->fz);
+  st->vt = bilerp(p->vturb, p->nr, i0, j0, st->fr, st->fz);
+  st->hlo = (1.0 - st->fr) * p->h_lo[i0] + st->fr * p->h_lo[i0 + 1];
+  st->hhi = (1.0 - st->fr) * p->h_hi[i0] + st->fr * p->h_hi[i0 + 1];
+  if (m) {
+    /* Neural field: outputs modulate the grid fields (log T, log n residuals and surface
+       offsets). Inputs are the normalised grid coordinates. */
+    double xin[2] = {u / (p->nr - 1), zr / p->zr_max};
+    double o[8];
+    mlp_forward(m, xin, o);
+    st->T *= exp(o[0]);
+    st->n *= exp(o[1]);
+    st->hlo += m->h_scale * o[2];
+    st->hhi += m->h_scale * o[3];
+  }
+  /* CO layer between the two surfaces (stand-in for the freeze-out / photodissociation
+     gates of Eq. co_layer): logistic edges of width edge_w in z/r, or hard steps. */
+  if (p->edge_w > 0) {
+    st->sa = logistic((zr - st->hlo) / p->edge_w);
+    st->sb = logistic((st->hhi - zr) / p->edge_w);
+  } else {
+    st->sa = zr >= st->hlo ? 1.0 : 0.0;
+    st->sb = zr <= st->hhi ? 1.0 : 0.0;
+  }
+  st->X = p->x_co * st->sa * st->sb;
+  /* Keplerian rotation (first term of Eq. gas_velocity_pressure), counter-clockwise about
+     +z: v = v_phi (-y/r, x/r, 0). Line-of-sight velocity omega.v plus systemic velocity. */
+  double rc = r * AU_CM, zc = z * AU_CM;
+  double vphi = sqrt(GM_SUN * p->mstar_msun * rc * rc / pow(rc * rc + zc * zc, 1.5));
+  double v[3] = {-vphi * y / r, vphi * x / r, 0.0};
+  st->vlos = om[0] * v[0] + om[1] * v[1] + om[2] * v[2] + p->vsys_kms * 1e5;
+  /* Line width: thermal + turbulent. Absolute mode (v_turb in km/s) or the paper's Mach
+     form with c_s^2 = 2kT/m_mol as printed. */
+  double mco = p->m_co_amu * AMU_G, mmol = p->m_mol_amu * AMU_G;
+  double th = 2.0 * K_BOLTZ * st->T / mco;
+  if (p->vturb_mach)
+    st->alpha = sqrt(th + st->vt * st->vt * (2.0 * K_BOLTZ * st->T / mmol));
+  else
+    st->alpha = sqrt(th + (st->vt * 1e5) * (st->vt * 1e5));
+  /* LTE Boltzmann populations. */
+  double B = rot_B(p);
+  int Ju = p->J_u, Jl = p->J_u - 1;
+  double Eu = H_PLANCK * B * Ju * (Ju + 1.0), El = H_PLANCK * B * Jl * (Jl + 1.0);
+  st->Z = orc_partition(st->T, B);
+  st->fu = (2.0 * Ju + 1.0) * exp(-Eu / (K_BOLTZ * st->T)) / st->Z;
+  st->fl = (2.0 * Jl + 1.0) * exp(-El / (K_BOLTZ * st->T)) / st->Z;
+  st->nco = st->X * st->n;
+  st->nu_ = st->nco * st->fu;
+  st->nl_ = st->nco * st->fl;
+  /* Einstein coefficients: B_ul = A_ul c^2/(2 h nu0^3), B_lu = (g_u/g_l) B_ul. */
+  double Bul = p->A_ul * C_LIGHT * C_LIGHT / (2.0 * H_PLANCK * pow(p->nu0_hz, 3));
+  double Blu = (2.0 * Ju + 1.0) / (2.0 * Jl + 1.0) * Bul;
+  st->D = st->nl_ * Blu - st->nu_ * Bul;
+  /* Source function S = j/beta; the profile cancels, so it is formed from the
+     populations (the pins check it equals the Planck function B_nu0(T)). */
+  double Du = st->fl * Blu - st->fu * Bul;
+  st->S = p->A_ul * st->fu / Du;
+  st->gas = st->nco > 0.0 ? 1 : 0;
+}
+
+/* Profile phi(nu_c) [Hz^-1] for channel velocity v_c [km/s] (radio convention
+   nu_c = nu0 (1 - v_c/c)); also returns the profile argument xarg. */
+static double profile(const orc_problem *p, const pt *st, double v_kms, double *xarg) {
+  double nu0 = p->nu0_hz;
+  double nu = nu0 * (1.0 - v_kms * 1e5 / C_LIGHT);
+  double dnu = st->vlos / C_LIGHT;
+  double xx = C_LIGHT * (nu - nu0 * (1.0 - dnu)) / (nu0 * st->alpha);
+  if (xarg) *xarg = xx;
+  return C_LIGHT / (nu0 * st->alpha * sqrt(M_PI)) * exp(-xx * xx);
+}
+
+int orc_point(const orc_problem *p, double x, double y, double z, double v_kms, double *out) {
+  double P[3] = {x, y, z}, P0[3], om[3];
+  ray_setup(p, 0, 0, P0, om);
+  pt st;
+  eval_point(p, NULL, P, om, &st);
+  for (int a = 0; a < 12; a++) out[a] = 0.0;
+  out[2] = st.T;
+  out[3] = st.n;
+  out[4] = st.X;
+  out[5] = st.vlos * 1e-5;
+  out[6] = st.alpha * 1e-5;
+  out[11] = st.vt;
+  if (!st.gas) return 0;
+  double phi = profile(p, &st, v_kms, NULL);
+  double hnu = H_PLANCK * p->nu0_hz / (4.0 * M_PI);
+  out[0] = hnu * st.nu_ * p->A_ul * phi;
+  out[1] = hnu * st.D * phi;
+  out[7] = st.nu_;
+  out[8] = st.nl_;
+  out[9] = phi;
+  out[10] = st.S;
+  return 1;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* The march (Eq. rt-int with Eq. optical_depth), one ray                                  */
+/* ---------------------------------------------------------------------------------------- */
+
+static double unit_conv(const orc_problem *p) {
+  if (p->units != 1) return 1.0;
+  double hf = half_fov(p);
+  double ax = (2.0 * hf / p->nx) / p->dist_pc * ARCSEC_RAD;
+  double ay = (2.0 * hf / p->ny) / p->dist_pc * ARCSEC_RAD;
+  return ax * ay * 1e23; /* erg s^-1 cm^-2 Hz^-1 sr^-1 -> Jy per pixel */
+}
+
+/* Front-to-back march of one pixel. The chord is split into n_samples equal segments with
+   the source and extinction taken at each midpoint (piecewise-constant step): over segment
+   k the intensity gains Tr_k S_k (1 - exp(-dtau_k)) and Tr_{k+1} = Tr_k exp(-dtau_k). The
+   background I0 is attenuated by the whole chord. */
+static void march_pixel(const orc_problem *p, const orc_mlp *m, int ix, int iy, double *I) {
+  double P0[3], om[3], s0, s1;
+  ray_setup(p, ix, iy, P0, om);
+  double conv = unit_conv(p);
+  if (!chord(p, P0, om, &s0, &s1)) {
+    for (int c = 0; c < p->nch; c++) I[c] = p->I0;
+    return;
+  }
+  double ds = (s1 - s0) / p->n_samples;
+  double ds_cm = ds * AU_CM;
+  double hnu = H_PLANCK * p->nu0_hz / (4.0 * M_PI);
+  double *Tr = (double *)malloc(sizeof(double) * p->nch);
+  double *Ic = (double *)malloc(sizeof(double) * p->nch);
+  for (int c = 0; c < p->nch; c++) {
+    Tr[c] = 1.0;
+    Ic[c] = 0.0;
+  }
+  for (int k = 0; k < p->n_samples; k++) {
+    double s = s0 + (k + 0.5) * ds;
+    double P[3] = {P0[0] + s * om[0], P0[1] + s * om[1], P0[2] + s * om[2]};
+    pt st;
+    eval_point(p, m, P, om, &st);
+    if (!st.gas) continue;
+    for (int c = 0; c < p->nch; c++) {
+      double phi = profile(p, &st, p->v_kms[c], NULL);
+      double beta = hnu * st.D * phi;
+      double dtau = beta * ds_cm;
+      if (!(dtau > 0.0)) continue;
+      Ic[c] += Tr[c] * st.S * (-expm1(-dtau));
+      Tr[c] *= exp(-dtau);
+    }
+  }
+  for (int c = 0; c < p->nch; c++) I[c] = Ic[c] * conv + p->I0 * Tr[c];
+  free(Tr);
+  free(Ic);
+}
+
+static int check(const orc_problem *p) {
+  if (!p || p->nr < 2 || p->nz < 2 || p->nx < 1 || p->ny < 1 || p->nch < 0 ||
+      p->n_samples < 1)
+    return -1;
+  if (!(p->r_in_au > 0) || !(p->r_out_au > p->r_in_au) || !(p->zr_max > 0)) return -1;
+  if (!p->T || !p->n_h2 || !p->vturb || !p->h_lo || !p->h_hi || (p->nch > 0 && !p->v_kms))
+    return -1;
+  if (p->J_u < 1 || !(p->nu0_hz > 0) || !(p->dist_pc > 0)) return -1;
+  return 0;
+}
+
+int orc_render(const orc_problem *p, double *cube, int nthreads) {
+  if (check(p)) return -1;
+  long long npix = (long long)p->nx * p->ny;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int iy = 0; iy < p->ny; iy++) {
+    double *I = (double *)malloc(sizeof(double) * (p->nch > 0 ? p->nch : 1));
+    for (int ix = 0; ix < p->nx; ix++) {
+      march_pixel(p, NULL, ix, iy, I);
+      for (int c = 0; c < p->nch; c++) cube[c * npix + (long long)iy * p->nx + ix] = I[c];
+    }
+    free(I);
+  }
+  (void)nthreads;
+  return 0;
+}
+
+int orc_render_pixels(const orc_problem *p, const long long *pix, int npix, double *out,
+                      int nthreads) {
+  if (check(p)) return -1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int i = 0; i < npix; i++) {
+    int ix = (int)(pix[i] % p->nx), iy = (int)(pix[i] / p->nx);
+    march_pixel(p, NULL, ix, iy, out + (long long)i * p->nch);
+  }
+  (void)nthreads;
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Reverse mode of the march (hand-derived, no checkpoints: every per-sample state is kept) */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct {
+  double *gT, *gn, *gvt, *ghlo, *ghhi;
+} grads;
+
+static void adjoint_pixel(const orc_problem *p, int ix, int iy, const double *gout,
+                          double *I, grads *g) {
+  double P0[3], om[3], s0, s1;
+  ray_setup(p, ix, iy, P0, om);
+  double conv = unit_conv(p);
+  int N = p->n_samples, C = p->nch;
+  if (!chord(p, P0, om, &s0, &s1)) {
+    for (int c = 0; c < C; c++) I[c] = p->I0;
+    return;
+  }
+  double ds = (s1 - s0) / N, ds_cm = ds * AU_CM;
+  double hnu = H_PLANCK * p->nu0_hz / (4.0 * M_PI);
+  pt *st = (pt *)malloc(sizeof(pt) * N);
+  double *phi = (double *)malloc(sizeof(double) * N * C);
+  double *xarg = (double *)malloc(sizeof(double) * N * C);
+  double *dtau = (double *)malloc(sizeof(double) * N * C);
+  double *Tr = (double *)malloc(sizeof(double) * (N + 1) * C); /* Tr[k][c] before sample k */
+  double *Ic = (double *)calloc(C, sizeof(double));
+  for (int c = 0; c < C; c++) Tr[c] = 1.0;
+  /* forward, keeping every state */
+  for (int k = 0; k < N; k++) {
+    double s = s0 + (k + 0.5) * ds;
+    double P[3] = {P0[0] + s * om[0], P0[1] + s * om[1], P0[2] + s * om[2]};
+    eval_point(p, NULL, P, om, &st[k]);
+    for (int c = 0; c < C; c++) {
+      double tr = Tr[k * C + c];
+      phi[k * C + c] = 0.0;
+      dtau[k * C + c] = 0.0;
+      if (st[k].gas) {
+        phi[k * C + c] = profile(p, &st[k], p->v_kms[c], &xarg[k * C + c]);
+        dtau[k * C + c] = hnu * st[k].D * phi[k * C + c] * ds_cm;
+      }
+      double dt = dtau[k * C + c];
+      if (dt > 0.0) {
+        Ic[c] += tr * st[k].S * (-expm1(-dt));
+        Tr[(k + 1) * C + c] = tr * exp(-dt);
+      } else {
+        Tr[(k + 1) * C + c] = tr;
+      }
+    }
+  }
+  for (int c = 0; c < C; c++) I[c] = Ic[c] * conv + p->I0 * Tr[N * C + c];
+
+  /* reverse */
+  double B = rot_B(p);
+  int Ju = p->J_u, Jl = p->J_u - 1;
+  double Eu = H_PLANCK * B * Ju * (Ju + 1.0), El = H_PLANCK * B * Jl * (Jl + 1.0);
+  double Bul = p->A_ul * C_LIGHT * C_LIGHT / (2.0 * H_PLANCK * pow(p->nu0_hz, 3));
+  double Blu = (2.0 * Ju + 1.0) / (2.0 * Jl + 1.0) * Bul;
+  double mco = p->m_co_amu * AMU_G, mmol = p->m_mol_amu * AMU_G;
+  double *gI = (double *)malloc(sizeof(double) * C);
+  double *gTr = (double *)malloc(sizeof(double) * C);
+  for (int c = 0; c < C; c++) {
+    gI[c] = gout[c] * conv;   /* dL/d(sum in cgs) */
+    gTr[c] = gout[c] * p->I0; /* dL/dTr_N through the background term */
+  }
+  for (int k = N - 1; k >= 0; k--) {
+    const pt *q = &st[k];
+    double gS = 0.0, gD = 0.0, galpha = 0.0;
+    for (int c = 0; c < C; c++) {
+      double tr = Tr[k * C + c], dt = dtau[k * C + c];
+      if (!(dt > 0.0)) continue; /* this step was the identity */
+      double e = exp(-dt), em = -expm1(-dt);
+      /* step: I += tr S em ; Tr' = tr e */
+      double g_dtau = gI[c] * tr * q->S * e - gTr[c] * tr * e;
+      gS += gI[c] * tr * em;
+      gTr[c] = gI[c] * q->S * em + gTr[c] * e;
+      /* dtau = (h nu0/4pi) D phi ds */
+      double g_beta = g_dtau * ds_cm;
+      gD += g_beta * hnu * phi[k * C + c];
+      double g_phi = g_beta * hnu * q->D;
+      /* phi = c/(nu0 alpha sqrt(pi)) exp(-x^2), x = Q/alpha: dphi/dalpha = phi (2x^2-1)/alpha */
+      double xx = xarg[k * C + c];
+      galpha += g_phi * phi[k * C + c] * (2.0 * xx * xx - 1.0) / q->alpha;
+    }
+    if (!q->gas) continue;
+    /* S = A_ul n_u / D (both populations scale with n_CO, which cancels) */
+    double gnu = gS * p->A_ul / q->D - gD * Bul;
+    double gnl = gD * Blu;
+    double gD_from_S = -gS * p->A_ul * q->nu_ / (q->D * q->D);
+    gnu += -gD_from_S * Bul;
+    gnl += gD_from_S * Blu;
+    /* n_u = n_CO f_u(T), n_l = n_CO f_l(T), f_J = g_J exp(-E_J/kT)/Z */
+    double kT2 = K_BOLTZ * q->T * q->T;
+    double Em = mean_energy(q->T, B);
+    double dfu = q->fu * (Eu - Em) / kT2, dfl = q->fl * (El - Em) / kT2;
+    double gnco = gnu * q->fu + gnl * q->fl;
+    double gT = q->nco * (gnu * dfu + gnl * dfl);
+    /* alpha */
+    double dadT, dadvt;
+    if (p->vturb_mach) {
+      dadT = (K_BOLTZ / mco + q->vt * q->vt * K_BOLTZ / mmol) / q->alpha;
+      dadvt = q->vt * 2.0 * K_BOLTZ * q->T / mmol / q->alpha;
+    } else {
+      dadT = (K_BOLTZ / mco) / q->alpha;
+      dadvt = 1e5 * (q->vt * 1e5) / q->alpha;
+    }
+    gT += galpha * dadT;
+    double gvt = galpha * dadvt;
+    /* n_CO = X n */
+    double gX = gnco * q->n, gn = gnco * q->X;
+    double ghlo = 0.0, ghhi = 0.0;
+    if (p->edge_w > 0) {
+      ghlo = gX * p->x_co * q->sb * q->sa * (1.0 - q->sa) * (-1.0 / p->edge_w);
+      ghhi = gX * p->x_co * q->sa * q->sb * (1.0 - q->sb) * (1.0 / p->edge_w);
+    }
+    /* bilinear scatter to the nodes */
+    int nr = p->nr, i0 = q->i0, j0 = q->j0;
+    double fr = q->fr, fz = q->fz;
+    int idx[4] = {j0 * nr + i0, j0 * nr + i0 + 1, (j0 + 1) * nr + i0, (j0 + 1) * nr + i0 + 1};
+    double wt[4] = {(1 - fr) * (1 - fz), fr * (1 - fz), (1 - fr) * fz, fr * fz};
+    for (int a = 0; a < 4; a++) {
+      g->gT[idx[a]] += gT * wt[a];
+      g->gn[idx[a]] += gn * wt[a];
+      g->gvt[idx[a]] += gvt * wt[a];
+    }
+    g->ghlo[i0] += ghlo * (1 - fr);
+    g->ghlo[i0 + 1] += ghlo * fr;
+    g->ghhi[i0] += ghhi * (1 - fr);
+    g->ghhi[i0 + 1] += ghhi * fr;
+  }
+  free(gI);
+  free(gTr);
+  free(st);
+  free(phi);
+  free(xarg);
+  free(dtau);
+  free(Tr);
+  free(Ic);
+}
+
+int orc_render_adjoint(const orc_problem *p, const double *dL_dcube, double *cube,
+                       double *dT, double *dn, double *dvt, double *dh_lo, double *dh_hi,
+                       int nthreads) {
+  if (check(p) || !dL_dcube) return -1;
+  int G = p->nr * p->nz;
+  long long npix = (long long)p->nx * p->ny;
+  memset(dT, 0, sizeof(double) * G);
+  memset(dn, 0, sizeof(double) * G);
+  memset(dvt, 0, sizeof(double) * G);
+  memset(dh_lo, 0, sizeof(double) * p->nr);
+  memset(dh_hi, 0, sizeof(double) * p->nr);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+  {
+    grads g;
+    g.gT = (double *)calloc(G, sizeof(double));
+    g.gn = (double *)calloc(G, sizeof(double));
+    g.gvt = (double *)calloc(G, sizeof(double));
+    g.ghlo = (double *)calloc(p->nr, sizeof(double));
+    g.ghhi = (double *)calloc(p->nr, sizeof(double));
+    double *gout = (double *)malloc(sizeof(double) * (p->nch > 0 ? p->nch : 1));
+    double *I = (double *)malloc(sizeof(double) * (p->nch > 0 ? p->nch : 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+    for (int iy = 0; iy < p->ny; iy++) {
+      for (int ix = 0; ix < p->nx; ix++) {
+        long long pix = (long long)iy * p->nx + ix;
+        for (int c = 0; c < p->nch; c++) gout[c] = dL_dcube[c * npix + pix];
+        adjoint_pixel(p, ix, iy, gout, I, &g);
+        if (cube)
+          for (int c = 0; c < p->nch; c++) cube[c * npix + pix] = I[c];
+      }
+    }
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+    {
+      for (int a = 0; a < G; a++) {
+        dT[a] += g.gT[a];
+        dn[a] += g.gn[a];
+        dvt[a] += g.gvt[a];
+      }
+      for (int a = 0; a < p->nr; a++) {
+        dh_lo[a] += g.ghlo[a];
+        dh_hi[a] += g.ghhi[a];
+      }
+    }
+    free(g.gT);
+    free(g.gn);
+    free(g.gvt);
+    free(g.ghlo);
+    free(g.ghhi);
+    free(gout);
+    free(I);
+  }
+  (void)nthreads;
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Neural field (the symmetric MLP T(r,|z|) = MLP_w(gamma(r,|z|)) of the neural-temperature */
+/* section, with Fourier-feature encoding gamma and SiLU hidden activations)               */
+/* ---------------------------------------------------------------------------------------- */
+
+static void mlp_forward(const orc_mlp *m, const double xin[2], double *out) {
+  double buf1[ORC_MLP_MAXW], buf2[ORC_MLP_MAXW];
+  double *h = buf1, *h2 = buf2;
+  /* gamma(x): [sin(2 pi B x), cos(2 pi B x)] */
+  for (int f = 0; f < m->n_freq; f++) {
+    double a = 2.0 * M_PI * (m->B[2 * f] * xin[0] + m->B[2 * f + 1] * xin[1]);
+    h[f] = sin(a);
+    h[m->n_freq + f] = cos(a);
+  }
+  for (int l = 0; l < m->n_layers; l++) {
+    int din = m->dims[l], dout = m->dims[l + 1];
+    for (int o = 0; o < dout; o++) {
+      double acc = m->b[l][o];
+      for (int i = 0; i < din; i++) acc += m->W[l][(long long)o * din + i] * h[i];
+      /* SiLU on hidden layers, identity on the output layer */
+      h2[o] = (l < m->n_layers - 1) ? acc / (1.0 + exp(-acc)) : acc;
+    }
+    double *t = h;
+    h = h2;
+    h2 = t;
+  }
+  for (int o = 0; o < m->dims[m->n_layers]; o++) out[o] = h[o];
+}
+
+static int mlp_check(const orc_mlp *m) {
+  if (!m || m->n_layers < 1 || m->dims[0] != 2 * m->n_freq) return -1;
+  for (int l = 0; l <= m->n_layers; l++)
+    if (m->dims[l] < 1 || m->dims[l] > ORC_MLP_MAXW) return -1;
+  return 0;
+}
+
+int orc_mlp_eval(const orc_mlp *m, const double *x, int npts, double *out) {
+  if (mlp_check(m)) return -1;
+  int no = m->dims[m->n_layers];
+  for (int i = 0; i < npts; i++) {
+    double o[64];
+    if (no > 64) return -1;
+    mlp_forward(m, x + 2 * i, o);
+    for (int a = 0; a < no; a++) out[(long long)i * no + a] = o[a];
+  }
+  return 0;
+}
+
+int orc_render_mlp(const orc_problem *p, const orc_mlp *m, const long long *pix, int npix,
+                   double *out, int nthreads) {
+  if (check(p) || mlp_check(m) || m->dims[m->n_layers] < 4) return -1;
+  long long np = pix ? npix : (long long)p->nx * p->ny;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (long long i = 0; i < np; i++) {
+    long long q = pix ? pix[i] : i;
+    int ix = (int)(q % p->nx), iy = (int)(q / p->nx);
+    double *I = (double *)malloc(sizeof(double) * (p->nch > 0 ? p->nch : 1));
+    march_pixel(p, m, ix, iy, I);
+    for (int c = 0; c < p->nch; c++) {
+      if (pix)
+        out[i * p->nch + c] = I[c];
+      else
+        out[(long long)c * p->nx * p->ny + q] = I[c];
+    }
+    free(I);
+  }
+  (void)nthreads;
+  return 0;
+}

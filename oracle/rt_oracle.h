@@ -1,0 +1,105 @@
+/*
+ * FP64 CPU oracle for the line radiative-transfer march (TEST INFRASTRUCTURE ONLY).
+ *
+ * This library is the slow, plain, double-precision statement of what the GPU path
+ * computes. Only the tests, the smoke check and the CPU-baseline leg of the benchmark may
+ * load it; the product path never links, loads or calls it, and it shares no code, header,
+ * table or constant with the CUDA library.
+ *
+ * Physics followed (arXiv 2509.03623, Methods):
+ *   - integral form of the transfer equation, Eq. rt-int, with the optical depth of
+ *     Eq. optical_depth, traced backward from each image pixel;
+ *   - emissivity j_nu and extinction beta_nu from the level populations and Einstein
+ *     coefficients (the two equations following Eq. optical_depth);
+ *   - LTE (Boltzmann) level populations;
+ *   - the Doppler-shifted Gaussian line profile phi(nu) with delta_nu = omega.v / c;
+ *   - the line width alpha(x) (thermal + turbulent) and sound speed c_s;
+ *   - the Keplerian term of Eq. gas_velocity_pressure.
+ * Readings where the paper is silent are listed in the design notes and repeated at the
+ * point of use below.
+ */
+#ifndef RT_ORACLE_H
+#define RT_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  /* (r, z/r) node grid: r log-spaced (r_log=1) or linear (r_log=0) in [r_in, r_out] au,
+     z/r linear in [0, zr_max]. */
+  int nr, nz, r_log;
+  double r_in_au, r_out_au, zr_max;
+  /* node fields, [nz][nr] row-major: T [K], n_H2 [cm^-3], v_turb [km/s, or Mach number
+     when vturb_mach=1]; surfaces h_lo, h_hi [nr] in z/r units. */
+  const double *T, *n_h2, *vturb, *h_lo, *h_hi;
+  double x_co, edge_w;
+  int vturb_mach;
+  /* geometry */
+  double incl_deg, pa_deg, dist_pc, mstar_msun, vsys_kms;
+  /* image and spectral sampling */
+  int nx, ny;
+  double half_fov_au;
+  int nch;
+  const double *v_kms;
+  int n_samples;
+  double I0;
+  int units; /* 0: erg s^-1 cm^-2 Hz^-1 sr^-1, 1: Jy per pixel */
+  /* line (rigid rotor, J_u -> J_u-1) */
+  double nu0_hz, A_ul, B_rot_hz, m_co_amu, m_mol_amu;
+  int J_u;
+} orc_problem;
+
+/* Full cube [nch][ny][nx]. Returns 0, or -1 on invalid arguments. */
+int orc_render(const orc_problem *p, double *cube, int nthreads);
+
+/* Spectra of selected pixels: pix[i] = iy*nx + ix; out [npix][nch]. */
+int orc_render_pixels(const orc_problem *p, const long long *pix, int npix, double *out,
+                      int nthreads);
+
+/* Ray chord through the bounding cylinder: returns 1 and fills s_in, s_out (au along the
+   ray, origin on the sky plane through the star) and the ray origin/direction, or 0 on a
+   miss. */
+int orc_ray(const orc_problem *p, int ix, int iy, double *s_in, double *s_out, double *P0,
+            double *omega);
+
+/* Local quantities at a disk-frame point (au) for channel velocity v_kms:
+   out[0]=j_nu, out[1]=beta_nu (cgs), out[2]=T, out[3]=n_H2, out[4]=X_CO, out[5]=v_los [km/s],
+   out[6]=alpha [km/s], out[7]=n_u, out[8]=n_l, out[9]=phi [Hz^-1], out[10]=S=j/beta,
+   out[11]=v_turb (input units). Returns 1 if gas is present, 0 otherwise. */
+int orc_point(const orc_problem *p, double x, double y, double z, double v_kms, double *out);
+
+/* Rigid-rotor partition function Z(T) = sum_J (2J+1) exp(-h B J(J+1) / kT). */
+double orc_partition(double T, double B_rot_hz);
+
+/* Reverse-mode gradient of a scalar loss L given dL/dcube [nch][ny][nx] (cube units).
+   Writes the cube and dL/d(node fields) [nz][nr] and dL/d(surfaces) [nr]; every gradient
+   array is overwritten. */
+int orc_render_adjoint(const orc_problem *p, const double *dL_dcube, double *cube,
+                       double *dT, double *dn, double *dvt, double *dh_lo, double *dh_hi,
+                       int nthreads);
+
+/* Neural field (fully connected, SiLU hidden activations, Fourier-feature input). */
+typedef struct {
+  int n_freq;              /* number of Fourier directions; features = 2*n_freq */
+  const double *B;         /* [n_freq][2] frequencies applied to (rhat, zhat) */
+  int n_layers;            /* number of Linear layers (hidden layers + output layer) */
+  const int *dims;         /* [n_layers+1]: dims[0] = 2*n_freq, ..., dims[n_layers] = outputs */
+  const double *const *W;  /* W[l]: [dims[l+1]][dims[l]] row-major */
+  const double *const *b;  /* b[l]: [dims[l+1]] */
+  double h_scale;          /* surface offset scale applied to outputs 2 and 3 */
+} orc_mlp;
+
+/* Network outputs for npts inputs x[i] = (rhat, zhat): out [npts][dims[n_layers]]. */
+int orc_mlp_eval(const orc_mlp *m, const double *x, int npts, double *out);
+
+/* Cube rendered with the neural field: at every sample the grid values are modulated by the
+   network outputs o: T <- T exp(o0), n <- n exp(o1), h_lo <- h_lo + h_scale o2,
+   h_hi <- h_hi + h_scale o3. pix/npix select pixels as in orc_render_pixels (pix=NULL: all,
+   out is then the full cube [nch][ny][nx]). */
+int orc_render_mlp(const orc_problem *p, const orc_mlp *m, const long long *pix, int npix,
+                   double *out, int nthreads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,307 @@
+"""Seeded synthetic disk problems (input generation only).
+
+This module builds the inputs of the line radiative-transfer march: node grids of the
+axisymmetric (r, z/r) fields, the CO-layer surfaces, the viewing geometry, channel
+velocities and the line constants, plus neural-field weights and serving request mixes.
+It holds none of the march's arithmetic (no ray tracing, line profile, populations or
+transfer): both the CUDA path and the FP64 oracle read the plain arrays produced here.
+
+Disk family (arXiv 2509.03623, Methods, "Parametric Disk Modeling"; sizes and laws as
+fixed by the workload definitions):
+  * temperature  T(r,z) = T_mid(r) + (T_atm(r) - T_mid(r)) sin^2(pi z / 2 z_q) below z_q,
+    T_atm above, with T_mid = T_mid0 (r/100 au)^-0.5, T_atm = T_atm0 (r/100 au)^-0.5 and
+    z_q = z_q0 (r / r_scale)^1.3 (z_q0 = 70 au, r_scale = 150 au from Table 2); this is the
+    paper's cos^{2 delta} blend with delta = 1;
+  * density      Gaussian scale height: rho = Sigma / (sqrt(2 pi) H) exp(-z^2 / 2H^2),
+    H = c_s / Omega, c_s^2 = k T_mid / m_mol, Omega^2 = G M / r^3,
+    Sigma = Sigma0 (r/100 au)^-1 exp(-r/300 au), Sigma0 set by M_gas = 0.09 M_sun (Table 2)
+    over 10-600 au; n_H2 = rho / m_mol;
+  * CO layer     between surfaces z = c_lo r (r/100)^p and z = c_hi r (r/100)^p
+    (c_lo = 0.1, c_hi = 0.35, p = 0.25), stored as z/r heights per radial node;
+  * turbulence   v_turb = 0.05 km/s (absolute).
+Random jitter, log-normal perturbations and rings/gaps follow the workload definitions.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+# CGS constants used by the generator (CODATA 2018, IAU 2015 nominal).
+K_BOLTZ = 1.380649e-16
+H_PLANCK = 6.62607015e-27
+C_LIGHT = 2.99792458e10
+AMU_G = 1.66053906660e-24
+GM_SUN = 1.3271244e26
+M_SUN_G = 1.98840987e33  # GM_SUN / G with G = 6.67430e-8
+AU_CM = 1.495978707e13
+M_H_AMU = 1.007825
+DEBYE = 1e-18
+
+CO21_NU0 = 230.538e9
+CO_MASS_AMU = 28.0101
+MEAN_MOL_AMU = 2.37 * M_H_AMU
+
+
+def dipole_A(nu0_hz: float, mu_debye: float, J_u: int) -> float:
+    """Einstein A of a rigid-rotor J_u -> J_u-1 transition from its dipole moment
+    (A = 64 pi^4 nu^3 mu^2 / (3 h c^3) * J_u / (2 J_u + 1)); stands in for the missing
+    molecular table."""
+    mu = mu_debye * DEBYE
+    return (64.0 * math.pi ** 4 * nu0_hz ** 3 * mu ** 2 / (3.0 * H_PLANCK * C_LIGHT ** 3)
+            * J_u / (2.0 * J_u + 1.0))
+
+
+@dataclasses.dataclass
+class Problem:
+    """One render problem: plain arrays and scalars in the units of the C interface."""
+    # grid
+    nr: int
+    nz: int
+    r_in_au: float
+    r_out_au: float
+    zr_max: float
+    r_log: int
+    # node fields [nz][nr] float64 and surfaces [nr]
+    T: np.ndarray
+    n_h2: np.ndarray
+    vturb: np.ndarray
+    h_lo: np.ndarray
+    h_hi: np.ndarray
+    x_co: float = 1e-4
+    edge_w: float = 0.01
+    vturb_mach: int = 0
+    # geometry
+    incl_deg: float = 45.0
+    pa_deg: float = 0.0
+    dist_pc: float = 100.0
+    mstar_msun: float = 2.0
+    vsys_kms: float = 0.0
+    # view
+    nx: int = 64
+    ny: int = 64
+    half_fov_au: float = 0.0
+    v_kms: np.ndarray = dataclasses.field(default_factory=lambda: np.linspace(-4, 4, 16))
+    n_samples: int = 128
+    I0: float = 0.0
+    units: int = 0
+    # line
+    nu0_hz: float = CO21_NU0
+    A_ul: float = dataclasses.field(default_factory=lambda: dipole_A(CO21_NU0, 0.112, 2))
+    B_rot_hz: float = 0.0
+    m_co_amu: float = CO_MASS_AMU
+    m_mol_amu: float = MEAN_MOL_AMU
+    J_u: int = 2
+    # provenance
+    name: str = ""
+    seed: int = 0
+    # surface power-law parameters (c_lo, p_lo, c_hi, p_hi) and ring modulation per node
+    surf: tuple = (0.1, 0.25, 0.35, 0.25)
+    ring_mod: Optional[np.ndarray] = None
+
+    @property
+    def nch(self) -> int:
+        return int(len(self.v_kms))
+
+    @property
+    def npix(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def evals(self) -> int:
+        """Nominal sample-channel evaluations of one render: N_pix N_ch N_s."""
+        return self.nx * self.ny * self.nch * self.n_samples
+
+    def r_nodes(self) -> np.ndarray:
+        if self.r_log:
+            return self.r_in_au * (self.r_out_au / self.r_in_au) ** (
+                np.arange(self.nr) / (self.nr - 1))
+        return np.linspace(self.r_in_au, self.r_out_au, self.nr)
+
+    def zr_nodes(self) -> np.ndarray:
+        return np.linspace(0.0, self.zr_max, self.nz)
+
+    def replace(self, **kw) -> "Problem":
+        return dataclasses.replace(self, **kw)
+
+
+def _sigma0_from_mass(m_gas_msun: float, r_in: float, r_out: float) -> float:
+    """Sigma0 [g cm^-2] of Sigma = Sigma0 (r/100 au)^-1 exp(-r/300 au) holding M_gas
+    between r_in and r_out (closed-form integral of 2 pi r Sigma dr)."""
+    integral = (2.0 * math.pi * 100.0 * 300.0 * AU_CM ** 2
+                * (math.exp(-r_in / 300.0) - math.exp(-r_out / 300.0)))
+    return m_gas_msun * M_SUN_G / integral
+
+
+def parametric_fields(r_au: np.ndarray, zr: np.ndarray, *, T_mid0: float, T_atm0: float,
+                      sigma0: float, mstar: float, z_q0: float = 70.0,
+                      r_scale: float = 150.0, vturb_kms: float = 0.05):
+    """Node values [nz][nr] of T [K], n_H2 [cm^-3], v_turb [km/s]."""
+    R, ZR = np.meshgrid(r_au, zr)  # [nz][nr]
+    Z = ZR * R
+    T_mid = T_mid0 * (R / 100.0) ** -0.5
+    T_atm = T_atm0 * (R / 100.0) ** -0.5
+    z_q = z_q0 * (R / r_scale) ** 1.3
+    blend = np.where(Z < z_q, np.sin(math.pi * Z / (2.0 * z_q)) ** 2, 1.0)
+    T = T_mid + (T_atm - T_mid) * blend
+    m_mol = MEAN_MOL_AMU * AMU_G
+    cs = np.sqrt(K_BOLTZ * T_mid / m_mol)
+    omega = np.sqrt(GM_SUN * mstar / (R * AU_CM) ** 3)
+    H = cs / omega  # cm
+    sigma = sigma0 * (R / 100.0) ** -1 * np.exp(-R / 300.0)
+    rho = sigma / (math.sqrt(2.0 * math.pi) * H) * np.exp(-(Z * AU_CM) ** 2 / (2.0 * H ** 2))
+    n = rho / m_mol
+    vt = np.full_like(T, vturb_kms)
+    return T, n, vt
+
+
+def surfaces(r_au: np.ndarray, c_lo: float, p_lo: float, c_hi: float, p_hi: float,
+             ring_mod: Optional[np.ndarray] = None):
+    """CO-layer heights in z/r: h_s(r) = c_s (r/100 au)^p_s (x ring modulation)."""
+    h_lo = c_lo * (r_au / 100.0) ** p_lo
+    h_hi = c_hi * (r_au / 100.0) ** p_hi
+    if ring_mod is not None:
+        h_lo = h_lo * ring_mod
+        h_hi = h_hi * ring_mod
+    return h_lo, h_hi
+
+
+def disk(seed: int = 0, *, nr: int = 64, nz: int = 32, r_in: float = 10.0,
+         r_out: float = 600.0, zr_max: float = 0.5, nx: int = 64, ny: int = 64,
+         nch: int = 16, vmax: float = 4.0, n_samples: int = 128, incl: float = 45.0,
+         pa: float = 0.0, dist: float = 100.0, mstar: float = 2.0, jitter: float = 0.1,
+         lognormal: float = 0.0, rings: int = 0, edge_w: float = 0.01,
+         name: str = "") -> Problem:
+    """The parametric disk family with seeded jitter (PCG64). Each of T_mid0, T_atm0,
+    Sigma0, M_star and the two surface coefficients is scaled by U(1-jitter, 1+jitter);
+    `lognormal` multiplies T and n_H2 node values by exp(sigma N(0,1)); `rings` adds Gaussian
+    rings/gaps a_k exp(-(r-r_k)^2/2w_k^2) (w_k ~ U(10,30) au, r_k ~ U(50,550) au,
+    |a_k| ~ U(0.1,0.3) with alternating sign) to the CO-layer heights."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    j = rng.uniform(1.0 - jitter, 1.0 + jitter, size=6) if jitter > 0 else np.ones(6)
+    T_mid0, T_atm0 = 20.0 * j[0], 60.0 * j[1]
+    sigma0 = _sigma0_from_mass(0.09, r_in, r_out) * j[2]
+    mstar_j = mstar * j[3]
+    c_lo, c_hi = 0.1 * j[4], 0.35 * j[5]
+    grid_r = r_in * (r_out / r_in) ** (np.arange(nr) / (nr - 1))
+    grid_zr = np.linspace(0.0, zr_max, nz)
+    T, n, vt = parametric_fields(grid_r, grid_zr, T_mid0=T_mid0, T_atm0=T_atm0,
+                                 sigma0=sigma0, mstar=mstar_j)
+    if lognormal > 0:
+        T = T * np.exp(lognormal * rng.standard_normal(T.shape))
+        n = n * np.exp(lognormal * rng.standard_normal(n.shape))
+    ring_mod = None
+    if rings > 0:
+        ring_mod = np.ones(nr)
+        for k in range(rings):
+            w = rng.uniform(10.0, 30.0)
+            rk = rng.uniform(50.0, 550.0)
+            a = rng.uniform(0.1, 0.3) * (1.0 if k % 2 == 0 else -1.0)
+            ring_mod = ring_mod + a * np.exp(-(grid_r - rk) ** 2 / (2.0 * w * w))
+    h_lo, h_hi = surfaces(grid_r, c_lo, 0.25, c_hi, 0.25, ring_mod)
+    return Problem(nr=nr, nz=nz, r_in_au=r_in, r_out_au=r_out, zr_max=zr_max, r_log=1,
+                   T=T, n_h2=n, vturb=vt, h_lo=h_lo, h_hi=h_hi, edge_w=edge_w,
+                   incl_deg=incl, pa_deg=pa, dist_pc=dist, mstar_msun=mstar_j,
+                   nx=nx, ny=ny, v_kms=np.linspace(-vmax, vmax, nch), n_samples=n_samples,
+                   name=name, seed=seed, surf=(c_lo, 0.25, c_hi, 0.25), ring_mod=ring_mod)
+
+
+# --------------------------------------------------------------------------------------
+# The workloads (small parity case, observation scale, neural field, serving mix)
+# --------------------------------------------------------------------------------------
+
+def config_small(seed: int = 0) -> Problem:
+    """64x32 grid, 64x64 px, 16 channels over +-4 km/s, 128 samples, i=45, PA=0, 100 pc."""
+    return disk(seed, name="disk64x32_px64_ch16_ns128")
+
+
+def config_observation(seed: int = 0) -> Problem:
+    """512x256 grid, 256x256 px, 64 channels over +-6 km/s, 512 samples, i=47, PA=133,
+    log-normal (sigma=0.1) T and n_H2, three rings/gaps in the CO-layer height."""
+    return disk(seed, nr=512, nz=256, nx=256, ny=256, nch=64, vmax=6.0, n_samples=512,
+                incl=47.0, pa=133.0, lognormal=0.1, rings=3,
+                name="disk512x256_px256_ch64_ns512")
+
+
+def config_neural(seed: int = 0) -> Problem:
+    """Neural-field render shape: 512x512 px, 128 channels over +-6 km/s, 256 samples."""
+    return disk(seed, nx=512, ny=512, nch=128, vmax=6.0, n_samples=256,
+                name="mlp_px512_ch128_ns256")
+
+
+def noisy_target(cube: np.ndarray, seed: int, frac: float = 0.05) -> np.ndarray:
+    """Target cube = cube + N(0, (frac * peak)^2) noise (seeded)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return cube + frac * float(np.max(np.abs(cube))) * rng.standard_normal(cube.shape)
+
+
+# --------------------------------------------------------------------------------------
+# Neural field weights
+# --------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class MLPWeights:
+    """Fourier-feature MLP: features [sin(2 pi B x), cos(2 pi B x)] of x = (rhat, zhat),
+    Linear layers with SiLU on hidden layers. W[l] is [out][in] float32 (master copy)."""
+    B: np.ndarray            # [n_freq][2]
+    W: List[np.ndarray]
+    b: List[np.ndarray]
+    h_scale: float = 0.02
+
+    @property
+    def dims(self) -> List[int]:
+        return [self.W[0].shape[1]] + [w.shape[0] for w in self.W]
+
+
+def mlp_weights(seed: int = 0, n_freq: int = 32, width: int = 128, hidden: int = 4,
+                n_out: int = 4, sigma_b: float = 4.0, out_gain: float = 1.0) -> MLPWeights:
+    """Xavier-uniform weights (bound sqrt(6/(fan_in+fan_out))), zero biases, Gaussian
+    Fourier directions B ~ N(0, sigma_b^2); all float32 from a PCG64 seed."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    B = (sigma_b * rng.standard_normal((n_freq, 2))).astype(np.float32)
+    dims = [2 * n_freq] + [width] * hidden + [n_out]
+    W, b = [], []
+    for l in range(len(dims) - 1):
+        fi, fo = dims[l], dims[l + 1]
+        bound = math.sqrt(6.0 / (fi + fo))
+        w = rng.uniform(-bound, bound, size=(fo, fi))
+        if l == len(dims) - 2:
+            w = w * out_gain
+        W.append(w.astype(np.float32))
+        b.append(np.zeros(fo, dtype=np.float32))
+    return MLPWeights(B=B, W=W, b=b)
+
+
+# --------------------------------------------------------------------------------------
+# Serving request mix
+# --------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Request:
+    t_arrival_s: float
+    problem: Problem
+    adjoint: bool
+
+
+def request_mix(n: int = 256, seed: int = 0, rate_hz: float = 200.0,
+                pixels=(128, 256, 512), channels=(32, 64, 128), samples=(128, 256, 1024),
+                adjoint_frac: float = 0.3) -> List[Request]:
+    """Poisson arrivals (exponential gaps, mean 1/rate) of seeded small-family disks with
+    uniformly drawn image size, channel count and samples per ray; a fraction are
+    gradient requests."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate_hz)
+        px = int(rng.choice(pixels))
+        ch = int(rng.choice(channels))
+        ns = int(rng.choice(samples))
+        adj = bool(rng.uniform() < adjoint_frac)
+        prob = disk(seed * 100003 + i, nx=px, ny=px, nch=ch, n_samples=ns,
+                    name=f"req{i}_px{px}_ch{ch}_ns{ns}")
+        out.append(Request(t, prob, adj))
+    return out
