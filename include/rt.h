@@ -1,0 +1,141 @@
+/*
+ * rt.h -- C interface of the B300 line radiative-transfer library (librt_b300.so).
+ *
+ * The library renders spectral-line cubes of axisymmetric protoplanetary disks by backward
+ * ray tracing, following arXiv 2509.03623, Methods, "Line Radiative Transfer with RadJAX":
+ * the integral transfer equation (Eq. rt-int) with the optical depth of Eq. optical_depth,
+ * emissivity j_nu = h nu0/(4 pi) n_u A_ul phi and extinction
+ * beta_nu = h nu0/(4 pi)(n_l B_lu - n_u B_ul) phi, LTE (Boltzmann) level populations, the
+ * Doppler-shifted Gaussian profile phi(nu) with delta_nu = omega.v/c, the line width
+ * alpha = sqrt(2kT/m_CO + v_turb^2 c_s^2), and Keplerian rotation (first term of
+ * Eq. gas_velocity_pressure).
+ *
+ * Conventions (the paper leaves them open; fixed here):
+ *   - Disk frame: +z along the angular momentum; rotation counter-clockwise about +z.
+ *     Observer direction (0, -sin i, cos i); sky basis e_x = (1,0,0), e_y = (0, cos i, sin i).
+ *     Image pixel (ix, iy) has centre X = (ix + 1/2 - nx/2) 2 half_fov/nx au (Y likewise);
+ *     (x_s, y_s) = (X cos PA + Y sin PA, -X sin PA + Y cos PA). Orthographic rays.
+ *   - The ray's chord through the cylinder r <= r_out, |z| <= zr_max r_out is cut into
+ *     n_samples equal segments sampled at their midpoints; segment k adds
+ *     Tr_k S_k (1 - exp(-dtau_k)) and multiplies the transmittance by exp(-dtau_k).
+ *     Rays that miss the cylinder return I0.
+ *   - Node grids: r log-spaced (r_log = 1) or linear in [r_in, r_out]; z/r linear in
+ *     [0, zr_max]; bilinear interpolation in (grid r coordinate, z/r) of T, n_H2, v_turb;
+ *     no gas at r < r_in or |z|/r > zr_max. Surfaces h_lo, h_hi (z/r units) are
+ *     interpolated in r.
+ *   - CO abundance x_co between the surfaces with logistic edges of width edge_w in z/r
+ *     (edge_w = 0: hard steps).
+ *   - Channel velocities use the radio convention; line-of-sight velocity positive receding.
+ *   - Molecule: rigid rotor J_u -> J_u - 1, E_J = h B J(J+1), g_J = 2J+1, B = B_rot_hz or
+ *     nu0/(2 J_u) when B_rot_hz <= 0.
+ *   - Output cube [nch][ny][nx] (x fastest), float32, in erg s^-1 cm^-2 Hz^-1 sr^-1
+ *     (units = 0) or Jy per pixel (units = 1). I0 is in output units.
+ *
+ * Memory and ownership: every buffer is owned by the caller and is never freed by the
+ * library. Field, surface, cube and gradient pointers are DEVICE pointers on the current
+ * device; v_kms is a HOST pointer read during the call. Calls are asynchronous on the given
+ * CUDA stream (NULL = the legacy default stream) and return once the work is enqueued.
+ *
+ * Errors: functions return RT_OK (0) or a negative RT_E* code; rt_last_error() returns a
+ * thread-local message for the last failure on the calling thread. Invalid arguments are
+ * detected on the host before anything is enqueued.
+ */
+#ifndef RT_B300_H
+#define RT_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT_OK 0
+#define RT_EINVAL (-1)     /* invalid argument (sizes, pointers, non-finite values) */
+#define RT_ENOMEM (-2)     /* device or host allocation failed */
+#define RT_EBUSY (-3)      /* serving: no admission slot or memory budget now */
+#define RT_ETIMEDOUT (-4)  /* a bounded wait ran out */
+#define RT_ECUDA (-5)      /* a CUDA runtime call failed */
+#define RT_ENOTFOUND (-6)  /* serving: unknown ticket */
+
+#define RT_MAX_CH 256      /* channels per render */
+
+/* (r, z/r) node grid. */
+typedef struct {
+  int nr, nz;       /* nodes in r and in z/r, each >= 2 */
+  int r_log;        /* 1: r nodes log-spaced, 0: linear */
+  double r_in_au, r_out_au;
+  double zr_max;    /* z/r of the last node row */
+} rt_grid;
+
+/* Node fields, DEVICE float32, [nz][nr] row-major (z/r row, r fastest); surfaces [nr]. */
+typedef struct {
+  const float *T_K;       /* gas temperature [K], > 0 */
+  const float *n_h2_cm3;  /* H2 number density [cm^-3] */
+  const float *vturb;     /* turbulent velocity [km/s] (Mach number if vturb_mach) */
+  const float *h_lo;      /* lower CO surface, z/r */
+  const float *h_hi;      /* upper CO surface, z/r */
+  double x_co;            /* CO abundance between the surfaces */
+  double edge_w;          /* logistic edge width in z/r (0: hard steps) */
+  int vturb_mach;         /* 0: alpha^2 = 2kT/m_CO + v_turb^2; 1: + v_turb^2 2kT/m_mol */
+} rt_fields;
+
+/* Viewing geometry and kinematics. */
+typedef struct {
+  double incl_deg, pa_deg;
+  double dist_pc;       /* used for Jy per pixel */
+  double mstar_msun;    /* Keplerian rotation */
+  double vsys_kms;      /* systemic velocity added to omega.v */
+} rt_geom;
+
+/* Image and spectral sampling. */
+typedef struct {
+  int nx, ny;           /* pixels (0 allowed: nothing to do) */
+  double half_fov_au;   /* <= 0: 1.1 r_out */
+  int nch;              /* 0..RT_MAX_CH */
+  const float *v_kms;   /* HOST [nch] channel velocities */
+  int n_samples;        /* samples per ray, 1 .. 2^20 */
+  double I0;            /* background intensity, output units */
+  int units;            /* 0: erg s^-1 cm^-2 Hz^-1 sr^-1, 1: Jy per pixel */
+} rt_view;
+
+/* Line constants (rigid rotor J_u -> J_u - 1). */
+typedef struct {
+  double nu0_hz;        /* rest frequency */
+  double A_ul;          /* Einstein A [s^-1] */
+  double B_rot_hz;      /* rotational constant; <= 0: nu0 / (2 J_u) */
+  double m_co_amu;      /* emitting molecule mass (thermal width) */
+  double m_mol_amu;     /* mean molecular mass (Mach-mode sound speed) */
+  int J_u;              /* upper level, >= 1 */
+} rt_line;
+
+/*
+ * rt_render -- forward march (Eq. rt-int / Eq. optical_depth, front to back).
+ * Writes the cube [nch][ny][nx] float32 to `cube` (DEVICE, caller-allocated,
+ * nch*ny*nx floats). Arithmetic is FP32 (optical depth summed in blocks of samples). No
+ * device memory is allocated. Returns RT_OK, RT_EINVAL or RT_ECUDA (launch failure).
+ */
+int rt_render(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+              const rt_view *view, const rt_line *line, float *cube, void *stream);
+
+/*
+ * rt_count_gas_samples -- work count of a render: the number of (ray, sample) pairs whose
+ * sample lies inside the gas grid (r >= r_in, |z|/r <= zr_max) on rays that hit the bounding
+ * cylinder, i.e. the samples the march evaluates (sampling rule as in rt_render).
+ * `count` is a DEVICE pointer to one unsigned 64-bit integer, overwritten (stream-ordered).
+ * Field arrays are not read. Returns RT_OK, RT_EINVAL or RT_ECUDA.
+ */
+int rt_count_gas_samples(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                         const rt_view *view, const rt_line *line, unsigned long long *count,
+                         void *stream);
+
+/* Message for the last error on this thread ("" if none). */
+const char *rt_last_error(void);
+
+/* Library version string. */
+const char *rt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

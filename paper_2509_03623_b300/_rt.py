@@ -1,0 +1,162 @@
+"""ctypes binding of librt_b300.so (argument marshalling only).
+
+Every function here fills the C structs of `include/rt.h` from a problem description and
+torch CUDA tensors, then calls the library on the current torch stream. There is no CPU
+fallback: if the shared library is missing or fails to load, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librt_b300.so")
+
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_EBUSY, RT_ETIMEDOUT, RT_ECUDA, RT_ENOTFOUND = (
+    0, -1, -2, -3, -4, -5, -6)
+RT_MAX_CH = 256
+
+
+class RTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rt error {code}: {msg}")
+        self.code = code
+
+
+class rt_grid(C.Structure):
+    _fields_ = [("nr", C.c_int), ("nz", C.c_int), ("r_log", C.c_int),
+                ("r_in_au", C.c_double), ("r_out_au", C.c_double), ("zr_max", C.c_double)]
+
+
+class rt_fields(C.Structure):
+    _fields_ = [("T_K", C.c_void_p), ("n_h2_cm3", C.c_void_p), ("vturb", C.c_void_p),
+                ("h_lo", C.c_void_p), ("h_hi", C.c_void_p), ("x_co", C.c_double),
+                ("edge_w", C.c_double), ("vturb_mach", C.c_int)]
+
+
+class rt_geom(C.Structure):
+    _fields_ = [("incl_deg", C.c_double), ("pa_deg", C.c_double), ("dist_pc", C.c_double),
+                ("mstar_msun", C.c_double), ("vsys_kms", C.c_double)]
+
+
+class rt_view(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("half_fov_au", C.c_double),
+                ("nch", C.c_int), ("v_kms", C.POINTER(C.c_float)), ("n_samples", C.c_int),
+                ("I0", C.c_double), ("units", C.c_int)]
+
+
+class rt_line(C.Structure):
+    _fields_ = [("nu0_hz", C.c_double), ("A_ul", C.c_double), ("B_rot_hz", C.c_double),
+                ("m_co_amu", C.c_double), ("m_mol_amu", C.c_double), ("J_u", C.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load librt_b300.so (after torch, so that one CUDA runtime serves both)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with `python -m paper_2509_03623_b300.build`"
+                    " (there is no CPU fallback)")
+            import torch  # noqa: F401  (loads libcudart first)
+            L = C.CDLL(LIB_PATH, mode=C.RTLD_GLOBAL)
+            P = C.POINTER
+            base = [P(rt_grid), P(rt_fields), P(rt_geom), P(rt_view), P(rt_line)]
+            L.rt_render.argtypes = base + [C.c_void_p, C.c_void_p]
+            L.rt_render.restype = C.c_int
+            L.rt_count_gas_samples.argtypes = base + [C.c_void_p, C.c_void_p]
+            L.rt_count_gas_samples.restype = C.c_int
+            L.rt_last_error.restype = C.c_char_p
+            L.rt_version.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def check(rc: int):
+    if rc != RT_OK:
+        raise RTError(rc, lib().rt_last_error().decode())
+
+
+def stream_handle(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class DeviceDisk:
+    """Device-resident float32 node fields and surfaces of one problem."""
+
+    FIELDS = ("T", "n_h2", "vturb", "h_lo", "h_hi")
+
+    def __init__(self, problem, device="cuda"):
+        import torch
+        self.problem = problem
+        self.device = torch.device(device)
+        for k in self.FIELDS:
+            setattr(self, k, torch.as_tensor(
+                np.ascontiguousarray(getattr(problem, k), dtype=np.float32), device=self.device))
+
+    def tensors(self):
+        return tuple(getattr(self, k) for k in self.FIELDS)
+
+
+def structs(problem, T, n, vt, hlo, hhi):
+    """C structs for `problem` with field tensors (CUDA float32, contiguous)."""
+    for t, shp in ((T, (problem.nz, problem.nr)), (n, (problem.nz, problem.nr)),
+                   (vt, (problem.nz, problem.nr)), (hlo, (problem.nr,)), (hhi, (problem.nr,))):
+        if (not t.is_cuda or t.dtype.itemsize != 4 or not t.is_floating_point()
+                or not t.is_contiguous() or tuple(t.shape) != shp):
+            raise ValueError(f"field tensors must be contiguous CUDA float32 of shape {shp}")
+    g = rt_grid(int(problem.nr), int(problem.nz), int(problem.r_log), float(problem.r_in_au),
+                float(problem.r_out_au), float(problem.zr_max))
+    f = rt_fields(T.data_ptr(), n.data_ptr(), vt.data_ptr(), hlo.data_ptr(), hhi.data_ptr(),
+                  float(problem.x_co), float(problem.edge_w), int(problem.vturb_mach))
+    o = rt_geom(float(problem.incl_deg), float(problem.pa_deg), float(problem.dist_pc),
+                float(problem.mstar_msun), float(problem.vsys_kms))
+    v = np.ascontiguousarray(np.asarray(problem.v_kms, dtype=np.float32))
+    vw = rt_view(int(problem.nx), int(problem.ny), float(problem.half_fov_au), int(v.size),
+                 v.ctypes.data_as(C.POINTER(C.c_float)), int(problem.n_samples),
+                 float(problem.I0), int(problem.units))
+    ln = rt_line(float(problem.nu0_hz), float(problem.A_ul), float(problem.B_rot_hz),
+                 float(problem.m_co_amu), float(problem.m_mol_amu), int(problem.J_u))
+    return g, f, o, vw, ln, v
+
+
+def rt_render(problem, fields=None, out=None, stream=None):
+    """Forward render through the C ABI; returns the cube tensor [nch][ny][nx] float32."""
+    import torch
+    dd = fields if fields is not None else DeviceDisk(problem)
+    T, n, vt, hlo, hhi = dd.tensors()
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    if out is None:
+        out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=T.device)
+    check(lib().rt_render(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                          C.c_void_p(out.data_ptr()), stream_handle(stream)))
+    return out
+
+
+def rt_count_gas_samples(problem, fields=None, stream=None) -> int:
+    """Number of (ray, sample) pairs inside the gas grid (executed samples of a render)."""
+    import torch
+    dd = fields if fields is not None else DeviceDisk(problem)
+    T, n, vt, hlo, hhi = dd.tensors()
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    cnt = torch.zeros(1, dtype=torch.int64, device=T.device)
+    check(lib().rt_count_gas_samples(C.byref(g), C.byref(f), C.byref(o), C.byref(vw),
+                                     C.byref(ln), C.c_void_p(cnt.data_ptr()),
+                                     stream_handle(stream)))
+    return int(cnt.item())
+
+
+def version() -> str:
+    return lib().rt_version().decode()

@@ -1,0 +1,249 @@
+// C-ABI entry points, argument validation, error reporting and the host-side construction
+// of the per-launch parameter block (unit conversions, molecular constants, LTE table).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "rt_internal.cuh"
+
+namespace rtb {
+
+// CGS constants (CODATA 2018 exact SI-defining values; IAU 2012/2015 nominal values).
+static const double kH = 6.62607015e-27;       // erg s
+static const double kK = 1.380649e-16;         // erg / K
+static const double kC = 2.99792458e10;        // cm / s
+static const double kAmu = 1.66053906660e-24;  // g
+static const double kGMsun = 1.3271244e26;     // cm^3 s^-2
+static const double kAu = 1.495978707e13;      // cm
+static const double kPi = 3.14159265358979323846;
+static const double kLog2e = 1.4426950408889634;
+
+static thread_local char g_err[512] = "";
+
+int set_error(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+static bool finite(double x) { return isfinite(x) != 0; }
+
+// Rigid-rotor level statistics at temperature T: lower-level fraction
+// f_l = g_l exp(-E_l/kT)/Z and mean level energy <E>.
+static void rotor_stats(double T, double B, int Jl, double *fl, double *meanE) {
+  double Z = 0.0, EZ = 0.0;
+  for (int J = 0; J < 200000; J++) {
+    double E = kH * B * J * (J + 1.0);
+    double w = (2.0 * J + 1.0) * exp(-E / (kK * T));
+    Z += w;
+    EZ += E * w;
+    if (J > Jl + 2 && w < 1e-18 * Z) break;
+  }
+  double El = kH * B * Jl * (Jl + 1.0);
+  *fl = (2.0 * Jl + 1.0) * exp(-El / (kK * T)) / Z;
+  *meanE = EZ / Z;
+}
+
+// LTE opacity factor F(T) = f_l(T) (1 - exp(-dE/kT)) as Phi = log2 F on t = log2 T, with
+// dPhi/dt = d ln F / d ln T = (E_l - <E>)/kT - x e^-x / (1 - e^-x), x = dE/kT; cubic Hermite
+// segments in Horner form.
+static void build_table(double B, int Ju, float *tab) {
+  int Jl = Ju - 1;
+  double El = kH * B * Jl * (Jl + 1.0);
+  double dE = kH * B * (Ju * (Ju + 1.0) - Jl * (Jl + 1.0));
+  double y[kTabN], m[kTabN];
+  const double h = 1.0 / kTabInvH;
+  for (int i = 0; i < kTabN; i++) {
+    double T = exp2(kTabT0 + i * h);
+    double fl, mE;
+    rotor_stats(T, B, Jl, &fl, &mE);
+    double x = dE / (kK * T);
+    double one_m = -expm1(-x);
+    y[i] = log2(fl * one_m);
+    m[i] = ((El - mE) / (kK * T) - x * exp(-x) / one_m) * h;
+  }
+  for (int i = 0; i < kTabSeg; i++) {
+    double y0 = y[i], y1 = y[i + 1], m0 = m[i], m1 = m[i + 1];
+    tab[4 * i + 0] = (float)y0;
+    tab[4 * i + 1] = (float)m0;
+    tab[4 * i + 2] = (float)(3.0 * (y1 - y0) - 2.0 * m0 - m1);
+    tab[4 * i + 3] = (float)(2.0 * (y0 - y1) + m0 + m1);
+  }
+}
+
+int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                 const rt_view *view, const rt_line *line, MarchParams *P) {
+  if (!grid || !fields || !geom || !view || !line || !P)
+    return set_error(RT_EINVAL, "null argument struct");
+  const rt_grid &g = *grid;
+  const rt_fields &f = *fields;
+  const rt_geom &o = *geom;
+  const rt_view &v = *view;
+  const rt_line &l = *line;
+  if (g.nr < 2 || g.nz < 2 || (long long)g.nr * g.nz > (1LL << 28))
+    return set_error(RT_EINVAL, "grid needs 2 <= nr, nz and nr*nz <= 2^28 (got %d x %d)", g.nr,
+                     g.nz);
+  if (!finite(g.r_in_au) || !finite(g.r_out_au) || !(g.r_in_au > 0) ||
+      !(g.r_out_au > g.r_in_au))
+    return set_error(RT_EINVAL, "grid radii need 0 < r_in < r_out");
+  if (!finite(g.zr_max) || !(g.zr_max > 0)) return set_error(RT_EINVAL, "zr_max must be > 0");
+  if (!f.T_K || !f.n_h2_cm3 || !f.vturb || !f.h_lo || !f.h_hi)
+    return set_error(RT_EINVAL, "null field pointer");
+  if (!finite(f.x_co) || f.x_co < 0) return set_error(RT_EINVAL, "x_co must be finite and >= 0");
+  if (!finite(f.edge_w) || f.edge_w < 0) return set_error(RT_EINVAL, "edge_w must be >= 0");
+  if (!finite(o.incl_deg) || !finite(o.pa_deg) || !finite(o.mstar_msun) || o.mstar_msun < 0 ||
+      !finite(o.vsys_kms))
+    return set_error(RT_EINVAL, "geometry must be finite with mstar >= 0");
+  if (v.nx < 0 || v.ny < 0) return set_error(RT_EINVAL, "negative image size");
+  if (v.nch < 0 || v.nch > RT_MAX_CH)
+    return set_error(RT_EINVAL, "nch must be in [0, %d] (got %d)", RT_MAX_CH, v.nch);
+  if (v.nch > 0 && !v.v_kms) return set_error(RT_EINVAL, "null channel velocities");
+  if (v.n_samples < 1 || v.n_samples > (1 << 20))
+    return set_error(RT_EINVAL, "n_samples must be in [1, 2^20]");
+  if (!finite(v.I0) || !finite(v.half_fov_au)) return set_error(RT_EINVAL, "non-finite view");
+  if (v.units != 0 && v.units != 1) return set_error(RT_EINVAL, "units must be 0 or 1");
+  if (v.units == 1 && !(finite(o.dist_pc) && o.dist_pc > 0))
+    return set_error(RT_EINVAL, "dist_pc must be > 0 for Jy per pixel");
+  if (!(finite(l.nu0_hz) && l.nu0_hz > 0) || !(finite(l.A_ul) && l.A_ul >= 0) || l.J_u < 1 ||
+      !(finite(l.m_co_amu) && l.m_co_amu > 0) || !(finite(l.m_mol_amu) && l.m_mol_amu > 0) ||
+      !finite(l.B_rot_hz))
+    return set_error(RT_EINVAL, "invalid line constants");
+  for (int c = 0; c < v.nch; c++)
+    if (!finite(v.v_kms[c])) return set_error(RT_EINVAL, "non-finite channel velocity %d", c);
+
+  memset(P, 0, sizeof(*P));
+  P->nr = g.nr;
+  P->nz = g.nz;
+  P->r_log = g.r_log ? 1 : 0;
+  if (P->r_log) {
+    P->lr_scale = (float)(0.5 * (g.nr - 1) / log2(g.r_out_au / g.r_in_au));
+    P->lr_off = 0.0f;
+  } else {
+    double s = (g.nr - 1) / (g.r_out_au - g.r_in_au);
+    P->lr_scale = (float)s;
+    P->lr_off = (float)(-g.r_in_au * s);
+  }
+  P->r_in2 = (float)(g.r_in_au * g.r_in_au);
+  P->inv_rin2 = (float)(1.0 / (g.r_in_au * g.r_in_au));
+  P->zr_max = (float)g.zr_max;
+  P->w_scale = (float)((g.nz - 1) / g.zr_max);
+  P->T = f.T_K;
+  P->n = f.n_h2_cm3;
+  P->vt = f.vturb;
+  P->hlo = f.h_lo;
+  P->hhi = f.h_hi;
+  P->x_co = (float)f.x_co;
+  P->hard_edge = f.edge_w > 0 ? 0 : 1;
+  P->edge_k = f.edge_w > 0 ? (float)(kLog2e / f.edge_w) : 0.0f;
+  P->vturb_mach = f.vturb_mach ? 1 : 0;
+  P->c_th = (float)(2.0 * kK / (l.m_co_amu * kAmu) / 1e10);
+  P->c_mach = (float)(2.0 * kK / (l.m_mol_amu * kAmu) / 1e10);
+
+  double inc = o.incl_deg * kPi / 180.0, pa = o.pa_deg * kPi / 180.0;
+  P->sin_i = sin(inc);
+  P->cos_i = cos(inc);
+  P->sin_pa = sin(pa);
+  P->cos_pa = cos(pa);
+  P->R_cyl = g.r_out_au;
+  P->H_cyl = g.zr_max * g.r_out_au;
+  double hf = v.half_fov_au > 0 ? v.half_fov_au : 1.1 * g.r_out_au;
+  P->px = v.nx > 0 ? 2.0 * hf / v.nx : 0.0;
+  P->py = v.ny > 0 ? 2.0 * hf / v.ny : 0.0;
+  P->vk = (float)(sqrt(kGMsun * o.mstar_msun / kAu) / 1e5);
+  P->vsys = (float)o.vsys_kms;
+
+  P->nx = v.nx;
+  P->ny = v.ny;
+  P->nch = v.nch;
+  P->n_samples = v.n_samples;
+  int kb = 0;
+  while ((1LL << kb) < (long long)v.n_samples) kb++;  // bits of the largest sample index
+  P->step_bits = 24 - kb;
+  double B_nu = 2.0 * kH * pow(l.nu0_hz, 3) / (kC * kC);  // 2 h nu0^3 / c^2
+  double conv = 1.0;
+  if (v.units == 1) {
+    double arcsec = kPi / 648000.0;
+    conv = (P->px / o.dist_pc * arcsec) * (P->py / o.dist_pc * arcsec) * 1e23;
+  }
+  P->out_scale = (float)(B_nu * conv);
+  P->I0 = (float)v.I0;
+
+  double B = l.B_rot_hz > 0 ? l.B_rot_hz : l.nu0_hz / (2.0 * l.J_u);
+  int Ju = l.J_u, Jl = l.J_u - 1;
+  double dE = kH * B * (Ju * (Ju + 1.0) - Jl * (Jl + 1.0));
+  // B_ul = A c^2 / (2 h nu0^3), B_lu = (g_u/g_l) B_ul; optical depth per
+  // (n_CO F inv_alpha[s/km] ds[au]) = (h nu0 / 4 pi) B_lu c / (nu0 sqrt(pi)) / 1e5 * au
+  double Bul = l.A_ul * kC * kC / (2.0 * kH * pow(l.nu0_hz, 3));
+  double Blu = (2.0 * Ju + 1.0) / (2.0 * Jl + 1.0) * Bul;
+  double kap = kH * l.nu0_hz / (4.0 * kPi) * Blu * kC / (l.nu0_hz * sqrt(kPi)) / 1e5 * kAu;
+  P->kappa_k = (float)(kap * kLog2e);
+  P->theta_s = (float)(dE / kK * kLog2e);
+  for (int c = 0; c < v.nch; c++) P->v[c] = v.v_kms[c];
+  // Equal spacing (to float rounding) lets the kernels form v_c = v0 + c dv in registers.
+  P->v_uniform = 0;
+  if (v.nch >= 2) {
+    double v0 = v.v_kms[0], dv = ((double)v.v_kms[v.nch - 1] - v0) / (v.nch - 1);
+    bool uni = dv != 0.0;
+    for (int c = 0; c < v.nch && uni; c++) {
+      double e = fabs((double)v.v_kms[c] - (v0 + c * dv));
+      if (e > 4e-7 * (fabs(v0) + fabs(dv) * v.nch)) uni = false;
+    }
+    if (uni) {
+      P->v_uniform = 1;
+      P->v0 = (float)v0;
+      P->dv = (float)dv;
+    }
+  }
+  build_table(B, Ju, P->tab);
+  return RT_OK;
+}
+
+}  // namespace rtb
+
+using namespace rtb;
+
+extern "C" int rt_render(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                         const rt_view *view, const rt_line *line, float *cube, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params(grid, fields, geom, view, line, P);
+  if (rc == RT_OK) {
+    long long n = (long long)P->nx * P->ny * P->nch;
+    if (n > 0 && !cube)
+      rc = set_error(RT_EINVAL, "null cube pointer");
+    else
+      rc = launch_forward(*P, cube, (cudaStream_t)stream);
+  }
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+extern "C" int rt_count_gas_samples(const rt_grid *grid, const rt_fields *fields,
+                                    const rt_geom *geom, const rt_view *view,
+                                    const rt_line *line, unsigned long long *count,
+                                    void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params(grid, fields, geom, view, line, P);
+  if (rc == RT_OK) {
+    if (!count)
+      rc = set_error(RT_EINVAL, "null count pointer");
+    else
+      rc = launch_count(*P, count, (cudaStream_t)stream);
+  }
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+extern "C" const char *rt_last_error(void) { return g_err; }
+
+extern "C" const char *rt_version(void) { return "b300-linert 0.1 (sm_103a)"; }

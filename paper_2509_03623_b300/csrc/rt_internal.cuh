@@ -1,0 +1,215 @@
+// Internal declarations of the B300 line radiative-transfer library: the per-launch
+// parameter block (passed by value as a __grid_constant__ kernel argument, so a launch
+// needs no device allocation or copy), fast-math device helpers, the per-ray setup and the
+// field lookup shared by the forward and adjoint kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rt.h"
+
+namespace rtb {
+
+// Tabulated LTE opacity factor Phi(t) = log2[ f_l(T) (1 - exp(-dE/kT)) ], t = log2(T/K),
+// f_l = g_l exp(-E_l/kT)/Z(T). Cubic Hermite segments stored as Horner coefficients.
+constexpr int kTabN = 232;  // nodes t = 0, 1/16, ..., 14.4375 (1 K .. 22 kK)
+constexpr float kTabT0 = 0.0f;
+constexpr float kTabInvH = 16.0f;
+constexpr int kTabSeg = kTabN - 1;
+
+struct MarchParams {
+  // grid
+  int nr, nz, r_log, hard_edge;
+  float lr_scale, lr_off;   // u = lg2(r^2/r_in^2)*lr_scale (log grid) or r*lr_scale+lr_off
+  float r_in2, inv_rin2;    // r_in^2 [au^2] and its reciprocal
+  float zr_max, w_scale;    // w = (z/r) * w_scale
+  const float *T, *n, *vt, *hlo, *hhi;
+  float x_co, edge_k;       // edge_k = log2(e) / edge_w
+  int vturb_mach;
+  float c_th, c_mach;       // alpha^2 [km^2 s^-2] = c_th T + vt^2  |  T (c_th + c_mach vt^2)
+  // geometry (double: per-ray setup only)
+  double sin_i, cos_i, cos_pa, sin_pa, R_cyl, H_cyl, px, py;
+  float vk;                 // sqrt(G M) [km s^-1 au^1/2]
+  float vsys;
+  // view
+  int nx, ny, nch, n_samples;
+  int step_bits;            // significant bits of the per-sample step (k * step exact)
+  float out_scale, I0;
+  // line
+  float kappa_k;            // dtau (log2 units) = kappa_k n_CO 2^Phi inv_alpha ds
+  float theta_s;            // (E_u - E_l)/k * log2(e) [K]
+  int v_uniform;            // channel velocities equally spaced: v_c = v0 + c dv
+  float v0, dv;
+  float v[RT_MAX_CH];
+  float tab[kTabSeg * 4];
+};
+
+// ---------------------------------------------------------------------------------------
+// Hardware approximations (MUFU). ex2 runs at 32/clk/SM on B300, the others at 16/clk/SM.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsq(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Per-ray setup: pixel -> ray origin on the sky plane and chord through the cylinder, in
+// double precision (once per ray). Sample positions are then formed in FP32 from a high
+// part of the step with few enough significant bits that k * step is exact, so a position
+// carries about one rounding of its own magnitude.
+struct Ray {
+  float x;                 // constant disk-frame x along the ray
+  float yb, zb, yb2, zb2;  // first-sample position (midpoint of segment 0), high + low parts
+  float dy, dz, dy2, dz2;  // step per sample, high part + remainder
+  float ds;                // segment length [au]
+  float vfac;              // sqrt(GM) sin i x  [km s^-1 au^{1/2}]
+  int hit;                 // ray crosses the bounding cylinder
+};
+
+// Round v to `bits` significant bits.
+__host__ __device__ __forceinline__ double round_bits(double v, int bits) {
+  if (v == 0.0) return 0.0;
+  int e;
+  frexp(v, &e);
+  double q = ldexp(1.0, e - bits);
+  return nearbyint(v / q) * q;
+}
+
+__device__ __forceinline__ float sample_coord(float kf, float base, float base2, float step,
+                                              float step2) {
+  return fmaf(kf, step, base) + fmaf(kf, step2, base2);
+}
+
+__device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, bool active) {
+  Ray R;
+  double X = ((double)ix + 0.5 - 0.5 * P.nx) * P.px;
+  double Y = ((double)iy + 0.5 - 0.5 * P.ny) * P.py;
+  double xs = X * P.cos_pa + Y * P.sin_pa;
+  double ys = -X * P.sin_pa + Y * P.cos_pa;
+  double P0y = ys * P.cos_i, P0z = ys * P.sin_i;
+  double wy = P.sin_i, wz = -P.cos_i;
+  double lo = -1e300, hi = 1e300;
+  bool ok = active;
+  if (wz != 0.0) {
+    double t1 = (-P.H_cyl - P0z) / wz, t2 = (P.H_cyl - P0z) / wz;
+    lo = fmax(lo, fmin(t1, t2));
+    hi = fmin(hi, fmax(t1, t2));
+  } else if (fabs(P0z) > P.H_cyl) {
+    ok = false;
+  }
+  double c = xs * xs + P0y * P0y - P.R_cyl * P.R_cyl;
+  if (wy != 0.0) {
+    double a = wy * wy, b = 2.0 * P0y * wy;
+    double disc = b * b - 4.0 * a * c;
+    if (disc < 0.0) {
+      ok = false;
+    } else {
+      double sq = sqrt(disc);
+      lo = fmax(lo, (-b - sq) / (2.0 * a));
+      hi = fmin(hi, (-b + sq) / (2.0 * a));
+    }
+  } else if (c > 0.0) {
+    ok = false;
+  }
+  ok = ok && (hi > lo);
+  if (!ok) {
+    lo = 0.0;
+    hi = 0.0;
+  }
+  double ds = (hi - lo) / P.n_samples;
+  double s0 = lo + 0.5 * ds;
+  double yb = P0y + s0 * wy, zb = P0z + s0 * wz, dy = ds * wy, dz = ds * wz;
+  R.x = (float)xs;
+  R.yb = (float)yb;
+  R.yb2 = (float)(yb - (double)R.yb);
+  R.zb = (float)zb;
+  R.zb2 = (float)(zb - (double)R.zb);
+  double dyh = round_bits(dy, P.step_bits), dzh = round_bits(dz, P.step_bits);
+  R.dy = (float)dyh;
+  R.dy2 = (float)(dy - dyh);
+  R.dz = (float)dzh;
+  R.dz2 = (float)(dz - dzh);
+  R.ds = (float)ds;
+  R.vfac = (float)((double)P.vk * P.sin_i * xs);
+  R.hit = ok ? 1 : 0;
+  return R;
+}
+
+__device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+// Field lookup state, also used by the adjoint to scatter gradients.
+struct Cell {
+  int i0, j0;
+  float fr, fz;
+  float zr;
+  bool gas;
+};
+
+__device__ __forceinline__ Cell locate(const MarchParams &P, float z, float r2) {
+  Cell c;
+  float ir = rsq(r2);
+  float zr = fabsf(z) * ir;
+  c.gas = (r2 >= P.r_in2) && (zr <= P.zr_max);
+  float u = P.r_log ? lg2(r2 * P.inv_rin2) * P.lr_scale : fmaf(r2 * ir, P.lr_scale, P.lr_off);
+  u = fminf(fmaxf(u, 0.0f), (float)(P.nr - 1));
+  int i0 = min((int)u, P.nr - 2);
+  float w = fminf(fmaxf(zr * P.w_scale, 0.0f), (float)(P.nz - 1));
+  int j0 = min((int)w, P.nz - 2);
+  c.i0 = i0;
+  c.j0 = j0;
+  c.fr = u - (float)i0;
+  c.fz = w - (float)j0;
+  c.zr = zr;
+  return c;
+}
+
+__device__ __forceinline__ float bilerp(const float *__restrict__ F, int nr, const Cell &c) {
+  const float *p = F + c.j0 * nr + c.i0;
+  float f00 = __ldg(p), f01 = __ldg(p + 1), f10 = __ldg(p + nr), f11 = __ldg(p + nr + 1);
+  return lerpf(lerpf(f00, f01, c.fr), lerpf(f10, f11, c.fr), c.fz);
+}
+
+// Keplerian factor (r^2 + z^2)^{-3/4} with a refined reciprocal square root (the profile
+// argument scales the relative error of v_los by v_los / alpha).
+__device__ __forceinline__ float kepler_q(float d2) {
+  float q = rsq(d2);
+  q = q * fmaf(-0.5f * d2 * q, q, 1.5f);  // one Newton step
+  return q * sqrtf(q);
+}
+
+// Hermite table evaluation: returns Phi and (optionally) dPhi/dt per unit t = log2 T.
+__device__ __forceinline__ float lte_phi(const float *__restrict__ tab, float t, float *dphi) {
+  float xt = (t - kTabT0) * kTabInvH;
+  xt = fminf(fmaxf(xt, 0.0f), (float)kTabSeg);
+  int i = min((int)xt, kTabSeg - 1);
+  float f = xt - (float)i;
+  float4 c = reinterpret_cast<const float4 *>(tab)[i];
+  if (dphi) *dphi = fmaf(f, fmaf(f, 3.0f * c.w, 2.0f * c.z), c.y) * kTabInvH;
+  return fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
+}
+
+// Host-side helpers (rt_api.cu, rt_forward.cu)
+int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                 const rt_view *view, const rt_line *line, MarchParams *P);
+int set_error(int code, const char *fmt, ...);
+void clear_error();
+int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream);
+int launch_count(const MarchParams &P, unsigned long long *count, cudaStream_t stream);
+
+}  // namespace rtb

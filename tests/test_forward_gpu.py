@@ -1,0 +1,127 @@
+"""Parity of the CUDA forward march with the FP64 oracle (through the C ABI)."""
+
+import numpy as np
+import pytest
+
+from paper_2509_03623_b300 import synth
+from tests.cubecheck import assert_cube_close, cube_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_03623_b300 import _rt, build
+    build.build()
+    _rt.lib()
+    return _rt
+
+
+def gpu_cube(rt, p):
+    import torch
+    out = rt.rt_render(p)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_small_disk_full_cube(rt, orc, seed):
+    """64x32 grid, 64x64 px, 16 channels, 128 samples: every voxel against the oracle."""
+    p = synth.config_small(seed)
+    e = assert_cube_close(gpu_cube(rt, p), orc.render(p), label=f"seed {seed}")
+    print(f"small disk seed {seed}: {e}")
+
+
+@pytest.mark.parametrize("case", [
+    dict(nx=37, ny=23, v_kms=np.linspace(-3.7, 4.1, 13)),            # ragged tiles / lanes
+    dict(incl_deg=0.0),                                               # face-on
+    dict(incl_deg=89.0, pa_deg=250.0),                                # nearly edge-on
+    dict(units=1, I0=0.05),                                           # Jy/pixel + background
+    dict(vsys_kms=1.3, v_kms=np.linspace(-2, 5, 40)),                 # 2 channels per lane
+    dict(v_kms=np.array([-3.0, -0.4, 0.1, 0.15, 2.5, 3.9])),          # unequal spacing
+    dict(v_kms=np.linspace(-4, 4, 5), n_samples=1),                   # one sample per ray
+    dict(half_fov_au=900.0, n_samples=333),                           # misses around the disk
+])
+def test_small_disk_variants(rt, orc, case):
+    p = synth.config_small(11).replace(**case)
+    e = assert_cube_close(gpu_cube(rt, p), orc.render(p), label=str(case))
+    print(f"variant {list(case)}: {e}")
+
+
+def test_mach_mode_and_linear_grid(rt, orc):
+    p = synth.config_small(12)
+    p = p.replace(vturb_mach=1, vturb=np.full_like(p.vturb, 0.3), r_log=0)
+    assert_cube_close(gpu_cube(rt, p), orc.render(p), label="mach/linear")
+
+
+def test_hard_edges_flip_tolerant(rt, orc):
+    """Hard CO edges: a sample within FP32 rounding of a surface may land on the other side;
+    voxels that disagree must be rare (a flipped sample changes a ray by about 1/N_s)."""
+    p = synth.config_small(13).replace(edge_w=0.0)
+    g = gpu_cube(rt, p)
+    r = orc.render(p)
+    peak = np.abs(r).max()
+    big = np.abs(r) > 1e-3 * peak
+    bad = big & (np.abs(g - r) > 1e-4 * np.abs(r))
+    assert bad.sum() <= 0.002 * big.sum(), cube_errors(g, r)
+
+
+def test_empty_and_max_channels(rt, orc):
+    import torch
+    p = synth.config_small(14)
+    out = rt.rt_render(p.replace(nx=0))
+    assert out.numel() == 0
+    q = p.replace(nx=16, ny=8, v_kms=np.linspace(-6, 6, 256), n_samples=64)
+    assert_cube_close(gpu_cube(rt, q), orc.render(q), label="256 channels")
+    with pytest.raises(rt.RTError):
+        rt.rt_render(p.replace(v_kms=np.linspace(-6, 6, 257)))
+    torch.cuda.synchronize()
+
+
+def test_gas_sample_count(rt, orc):
+    """The executed-sample count equals a direct count from the oracle's ray geometry."""
+    p = synth.config_small(15).replace(nx=24, ny=20, n_samples=50)
+    n = rt.rt_count_gas_samples(p)
+    ref = 0
+    for iy in range(p.ny):
+        for ix in range(p.nx):
+            hit, s0, s1, P0, om = orc.ray(p, ix, iy)
+            if not hit:
+                continue
+            ds = (s1 - s0) / p.n_samples
+            s = s0 + (np.arange(p.n_samples) + 0.5) * ds
+            P = P0[None, :] + s[:, None] * om[None, :]
+            r = np.hypot(P[:, 0], P[:, 1])
+            ref += int(((r >= p.r_in_au) & (np.abs(P[:, 2]) <= p.zr_max * r)).sum())
+    assert abs(n - ref) <= max(2, ref // 100000)
+
+
+def test_observation_scale_sampled_pixels(rt, orc):
+    """The 512x256-grid, 256^2-px, 64-channel, 512-sample workload in the benchmark's launch
+    configuration; the oracle computes 160 sampled spectra one by one."""
+    p = synth.config_observation(0)
+    g = gpu_cube(rt, p)
+    rng = np.random.default_rng(0)
+    flux = g.sum(axis=0).ravel()
+    bright = np.argsort(flux)[::-1][:80]
+    rand = rng.choice(p.nx * p.ny, size=80, replace=False)
+    pix = np.unique(np.concatenate([bright, rand]))
+    ref = orc.render_pixels(p, pix)                     # [npix][nch]
+    got = g.reshape(p.nch, -1)[:, pix].T
+    peak = float(np.abs(ref).max())
+    big = np.abs(ref) > 1e-3 * peak
+    rel = np.abs(got - ref)[big] / np.abs(ref)[big]
+    assert big.sum() > 1000
+    print(f"observation scale: {big.sum()} voxels, max rel {rel.max():.3e}, "
+          f"p99 {np.percentile(rel, 99):.3e}")
+    if rel.max() > 1e-4:
+        bi = np.argwhere(big)
+        worst = np.argsort(rel)[::-1][:8]
+        info = [(int(pix[bi[w][0]]), int(bi[w][1]), float(ref[tuple(bi[w])] / peak),
+                 float(rel[w])) for w in worst]
+        raise AssertionError(f"max rel {rel.max():.3e}; worst (pixel, channel, I/peak, rel): "
+                             f"{info}")
+    assert (np.abs(got - ref)[~big] <= 3e-7 * peak).all()
