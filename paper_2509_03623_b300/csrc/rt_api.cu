@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "rt_internal.cuh"
@@ -76,6 +77,35 @@ static void build_table(double B, int Ju, float *tab) {
     tab[4 * i + 2] = (float)(3.0 * (y1 - y0) - 2.0 * m0 - m1);
     tab[4 * i + 3] = (float)(2.0 * (y0 - y1) + m0 + m1);
   }
+}
+
+// The table depends only on (B, J_u); the last few are cached so that repeated renders of
+// the same line do not recompute ~10^5 exponentials on the host.
+static void lte_table(double B, int Ju, float *tab) {
+  struct Entry {
+    double B;
+    int Ju;
+    float tab[kTabSeg * 4];
+  };
+  static std::mutex mu;
+  static Entry cache[4];
+  static int n_cached = 0, next = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (int i = 0; i < n_cached; i++)
+      if (cache[i].B == B && cache[i].Ju == Ju) {
+        memcpy(tab, cache[i].tab, sizeof(cache[i].tab));
+        return;
+      }
+  }
+  build_table(B, Ju, tab);
+  std::lock_guard<std::mutex> lk(mu);
+  Entry &e = cache[next];
+  e.B = B;
+  e.Ju = Ju;
+  memcpy(e.tab, tab, sizeof(e.tab));
+  next = (next + 1) % 4;
+  if (n_cached < 4) n_cached++;
 }
 
 int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
@@ -201,7 +231,7 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
       P->dv = (float)dv;
     }
   }
-  build_table(B, Ju, P->tab);
+  lte_table(B, Ju, P->tab);
   return RT_OK;
 }
 
