@@ -1,26 +1,28 @@
 // Forward march kernel.
 //
-// Mapping: a warp owns a tile of kTileRays consecutive pixels. Their ray setups (double
-// precision chord through the bounding cylinder) are computed once, one lane per ray, and
-// kept in shared memory. The warp then marches R = 32/LPR rays at a time: the LPR lanes of a
-// ray split its channels (lane q holds channels q, q+LPR, q+2 LPR, ... in registers).
-// Samples advance in batches of LPR: in the physics phase lane q evaluates the
-// channel-independent physics of sample kb+q of its ray (fields, CO layer, Keplerian
-// velocity, line width, LTE source and opacity) once and publishes it in shared memory; in
-// the channel phase every lane walks, in order and four at a time, the batch's samples that
-// carry gas (warp ballot), evaluating the Doppler-shifted Gaussian profile and advancing
-// optical depth, transmittance and intensity front to back (Eq. rt-int with
-// Eq. optical_depth; the source is constant over each segment).
+// Mapping: a warp marches R = 32/LPR neighbouring rays at a time (one work unit); the LPR
+// lanes of a ray split its channels (lane q holds channels q, q+LPR, ... in registers, CPL
+// of them). The grid is persistent (one wave) and work units are interleaved over its warps;
+// the double-precision ray setups (chord through the bounding cylinder) of 32 rays are
+// computed at once, one per lane, and kept in shared memory. Samples advance in batches of
+// LPR: in the physics phase lane q evaluates the channel-independent physics of sample kb+q
+// of its ray (fields, CO layer, Keplerian velocity, line width, LTE source and opacity) once
+// and publishes it in shared memory; batches without gas on any ray are skipped (warp vote);
+// in the channel phase every lane walks the batch's samples in order (fully unrolled),
+// evaluating the Doppler-shifted Gaussian profile and advancing optical depth, transmittance
+// and intensity front to back (Eq. rt-int with Eq. optical_depth; the source is constant
+// over each segment).
 //
 // Per sample-channel evaluation: 7 FP32 operations and 2 MUFU.EX2. The optical depth is
 // summed per batch and folded into a per-channel base at the end of every batch (blocked
 // summation: about 2 N_s / LPR roundings instead of N_s).
+#include <mutex>
+
 #include "rt_internal.cuh"
 
 namespace rtb {
 
-constexpr int kWarps = 4;      // warps per block
-constexpr int kTileRays = 8;   // rays per warp tile
+constexpr int kWarps = 4;  // warps per block
 
 // Channel-independent physics of sample k of a ray: {kd, a, b, S} with
 //   kd  optical depth per unit profile (log2 units): dtau_c = kd 2^{-d_c^2}, 0 without gas
@@ -69,22 +71,19 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
 template <int LPR, int CPL, bool UNIF>
 __global__ void __launch_bounds__(kWarps * 32)
     march_fwd_kernel(const __grid_constant__ MarchParams P, float *__restrict__ cube) {
-  constexpr int R = 32 / LPR;  // rays marched together by one warp
+  constexpr int R = 32 / LPR;  // rays marched together by one warp (one work unit)
+  constexpr int G = 32 / R;    // work units whose ray setups are computed together
   __shared__ __align__(16) float s_tab[kTabSeg * 4];
   __shared__ float4 s_ph[kWarps][32];
-  __shared__ Ray s_ray[kWarps][kTileRays];
+  __shared__ Ray s_ray[kWarps][32];
   for (int i = threadIdx.x; i < kTabSeg * 4; i += blockDim.x) s_tab[i] = P.tab[i];
+  __syncthreads();
 
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int q = lane % LPR, rr = lane / LPR;
   const long long npix = (long long)P.nx * P.ny;
-  const long long tile0 = ((long long)blockIdx.x * kWarps + wib) * kTileRays;
-  if (lane < kTileRays) {
-    long long pix = tile0 + lane;
-    bool act = pix < npix;
-    s_ray[wib][lane] = setup_ray(P, act ? (int)(pix % P.nx) : 0, act ? (int)(pix / P.nx) : 0, act);
-  }
-  __syncthreads();
+  const long long nunits = (npix + R - 1) / R;
+  const long long W = (long long)gridDim.x * kWarps;  // warps in the grid
   float4 *ph = s_ph[wib];
 
   float vr[UNIF ? 1 : CPL];
@@ -95,98 +94,136 @@ __global__ void __launch_bounds__(kWarps * 32)
   const float vq = P.v0 + (float)q * P.dv;  // velocity of this lane's first channel
   const float dvs = (float)LPR * P.dv;      // spacing between this lane's channels
 
-  for (int it = 0; it < kTileRays / R; it++) {
-    const int ri = it * R + rr;
-    const long long pix = tile0 + ri;
-    const Ray ray = s_ray[wib][ri];
-    float tl[CPL], tb[CPL], Tr[CPL], I[CPL];
-#pragma unroll
-    for (int j = 0; j < CPL; j++) {
-      tl[j] = 0.0f;
-      tb[j] = 0.0f;
-      Tr[j] = 1.0f;
-      I[j] = 0.0f;
-    }
-    const int nsamp = __any_sync(0xffffffffu, ray.hit) ? P.n_samples : 0;
-    for (int kb = 0; kb < nsamp; kb += LPR) {
-      float4 mine = sample_physics(P, s_tab, ray, kb + q);
-      unsigned gm = __ballot_sync(0xffffffffu, mine.x > 0.0f);
-      if (gm == 0u) continue;  // no gas in this batch on any ray of the warp
-      ph[lane] = mine;
+  // Work units u = gw, gw + W, gw + 2W, ... (interleaved over the grid for balance); the
+  // setups of G units (32 rays) are computed at once, one ray per lane.
+  for (long long u0 = (long long)blockIdx.x * kWarps + wib; u0 < nunits; u0 += W * G) {
+    {
+      long long pix = (u0 + (long long)(lane / R) * W) * R + lane % R;
+      bool act = pix < npix;
+      Ray s = setup_ray(P, act ? (int)(pix % P.nx) : 0, act ? (int)(pix / P.nx) : 0, act);
       __syncwarp();
-      unsigned m = gm;
+      s_ray[wib][lane] = s;
+      __syncwarp();
+    }
+    for (int g = 0; g < G; g++) {
+      const long long u = u0 + (long long)g * W;
+      if (u >= nunits) break;
+      const long long pix = u * R + rr;
+      const Ray ray = s_ray[wib][g * R + rr];
+      float tl[CPL], tb[CPL], Tr[CPL], I[CPL];
 #pragma unroll
-      for (int s = 1; s < R; s++) m |= gm >> (s * LPR);
-      if (LPR < 32) m &= (1u << (LPR & 31)) - 1u;
-      while (m) {
-        // next four gas samples (in order); missing ones are exact no-ops (kd = 0)
-        float4 p[4];
-        float dc[4], db[4];
+      for (int j = 0; j < CPL; j++) {
+        tl[j] = 0.0f;
+        tb[j] = 0.0f;
+        Tr[j] = 1.0f;
+        I[j] = 0.0f;
+      }
+      const int nsamp = __any_sync(0xffffffffu, ray.hit) ? P.n_samples : 0;
+      for (int kb = 0; kb < nsamp; kb += LPR) {
+        const float4 mine = sample_physics(P, s_tab, ray, kb + q);
+        if (!__any_sync(0xffffffffu, mine.x > 0.0f)) continue;  // no gas in this batch
+        ph[lane] = mine;
+        __syncwarp();
+        // every sample of the batch in order; samples without gas are exact no-ops
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-          int t = __ffs(m) - 1;
-          m &= m - 1;
-          p[u] = t >= 0 ? ph[rr * LPR + t] : make_float4(0.0f, 0.0f, 1.0f, 0.0f);
-          dc[u] = fmaf(vq, p[u].z, -p[u].y);
-          db[u] = dvs * p[u].z;
-        }
+        for (int t = 0; t < LPR; t++) {
+          const float4 p = ph[rr * LPR + t];  // kd, a, b, S of sample kb+t of this ray
+          const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
 #pragma unroll
-        for (int j = 0; j < CPL; j++) {
-          float dt[4];
-#pragma unroll
-          for (int u = 0; u < 4; u++) {
-            float d = UNIF ? fmaf((float)j, db[u], dc[u]) : fmaf(vr[j], p[u].z, -p[u].y);
-            dt[u] = p[u].x * ex2(d * -d);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; u++) {
-            tl[j] += dt[u];
+          for (int j = 0; j < CPL; j++) {
+            float d = UNIF ? fmaf((float)j, db, dc) : fmaf(vr[j], p.z, -p.y);
+            tl[j] = fmaf(p.x, ex2(d * -d), tl[j]);
             float Tn = ex2(-tb[j] - tl[j]);
-            I[j] = fmaf(p[u].w, Tr[j] - Tn, I[j]);
+            I[j] = fmaf(p.w, Tr[j] - Tn, I[j]);
             Tr[j] = Tn;
           }
         }
-      }
 #pragma unroll
-      for (int j = 0; j < CPL; j++) {
-        tb[j] += tl[j];
-        tl[j] = 0.0f;
+        for (int j = 0; j < CPL; j++) {
+          tb[j] += tl[j];
+          tl[j] = 0.0f;
+        }
+        __syncwarp();
       }
-      __syncwarp();
-    }
-    if (pix < npix) {
+      if (pix < npix) {
 #pragma unroll
-      for (int j = 0; j < CPL; j++) {
-        int ch = q + LPR * j;
-        if (ch < P.nch) cube[(long long)ch * npix + pix] = fmaf(I[j], P.out_scale, P.I0 * Tr[j]);
+        for (int j = 0; j < CPL; j++) {
+          int ch = q + LPR * j;
+          if (ch < P.nch) cube[(long long)ch * npix + pix] = fmaf(I[j], P.out_scale, P.I0 * Tr[j]);
+        }
       }
     }
   }
 }
 
+// Blocks of a kernel resident on the whole device at once (queried once per kernel and
+// device, then cached).
+static int resident_blocks(const void *kernel) {
+  struct Entry {
+    const void *k;
+    int dev, blocks;
+  };
+  static std::mutex mu;
+  static Entry cache[64];
+  static int n = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (int i = 0; i < n; i++)
+      if (cache[i].k == kernel && cache[i].dev == dev) return cache[i].blocks;
+  }
+  int nb = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kWarps * 32, 0) != cudaSuccess ||
+      nb < 1)
+    nb = 1;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+    nsm = 1;
+  std::lock_guard<std::mutex> lk(mu);
+  if (n < 64) cache[n++] = Entry{kernel, dev, nb * nsm};
+  return nb * nsm;
+}
+
+template <int LPR, int CPL, bool UNIF>
+static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
+  auto kern = march_fwd_kernel<LPR, CPL, UNIF>;
+  long long npix = (long long)P.nx * P.ny;
+  long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
+  long long need = (units + kWarps - 1) / kWarps;
+  long long cap = resident_blocks((const void *)kern);
+  long long blocks = need < cap ? need : cap;
+  kern<<<(unsigned)blocks, kWarps * 32, 0, stream>>>(P, cube);
+}
+
 template <int LPR, int CPL>
-static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream, unsigned blocks) {
+static void launch_u(const MarchParams &P, float *cube, cudaStream_t stream) {
   if (P.v_uniform)
-    march_fwd_kernel<LPR, CPL, true><<<blocks, kWarps * 32, 0, stream>>>(P, cube);
+    launch_t<LPR, CPL, true>(P, cube, stream);
   else
-    march_fwd_kernel<LPR, CPL, false><<<blocks, kWarps * 32, 0, stream>>>(P, cube);
+    launch_t<LPR, CPL, false>(P, cube, stream);
+}
+
+// Channels per lane (4, or 8 above 128 channels) and lanes per ray (power of two).
+void lane_layout(int nch, int *lpr, int *cpl) {
+  int c = nch > 128 ? 8 : 4;
+  int need = (nch + c - 1) / c, l = 1;
+  while (l < need) l *= 2;
+  *lpr = l;
+  *cpl = c;
 }
 
 int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream) {
   long long npix = (long long)P.nx * P.ny;
   if (npix == 0 || P.nch == 0) return RT_OK;
-  int LPR = P.nch <= 8 ? 8 : (P.nch <= 16 ? 16 : 32);
-  int CPL = (P.nch + LPR - 1) / LPR;
-  long long per_block = (long long)kWarps * kTileRays;
-  long long blocks = (npix + per_block - 1) / per_block;
-  if (blocks > 0x7fffffffLL) return set_error(RT_EINVAL, "image too large");
-  unsigned b = (unsigned)blocks;
-  if (LPR == 8) launch_t<8, 1>(P, cube, stream, b);
-  else if (LPR == 16) launch_t<16, 1>(P, cube, stream, b);
-  else if (CPL == 1) launch_t<32, 1>(P, cube, stream, b);
-  else if (CPL == 2) launch_t<32, 2>(P, cube, stream, b);
-  else if (CPL <= 4) launch_t<32, 4>(P, cube, stream, b);
-  else launch_t<32, 8>(P, cube, stream, b);
+  int LPR, CPL;
+  lane_layout(P.nch, &LPR, &CPL);
+  if (CPL == 8) launch_u<32, 8>(P, cube, stream);
+  else if (LPR == 32) launch_u<32, 4>(P, cube, stream);
+  else if (LPR == 16) launch_u<16, 4>(P, cube, stream);
+  else if (LPR == 8) launch_u<8, 4>(P, cube, stream);
+  else if (LPR == 4) launch_u<4, 4>(P, cube, stream);
+  else if (LPR == 2) launch_u<2, 4>(P, cube, stream);
+  else launch_u<1, 4>(P, cube, stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "forward launch: %s", cudaGetErrorString(e));
   return RT_OK;
