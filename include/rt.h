@@ -129,6 +129,48 @@ int rt_count_gas_samples(const rt_grid *grid, const rt_fields *fields, const rt_
                          const rt_view *view, const rt_line *line, unsigned long long *count,
                          void *stream);
 
+/* Gradient outputs of rt_render_adjoint: DEVICE float64 arrays, overwritten by the call. */
+typedef struct {
+  double *dT;       /* [nz][nr] dL/dT_K */
+  double *dn;       /* [nz][nr] dL/dn_h2 */
+  double *dvt;      /* [nz][nr] dL/dvturb */
+  double *dh_lo;    /* [nr] dL/dh_lo */
+  double *dh_hi;    /* [nr] dL/dh_hi */
+  double *loss;     /* 1 value: sum over voxels of (cube - target)^2 when a target is given;
+                       may be NULL */
+} rt_grads;
+
+/*
+ * rt_render_adjoint -- forward march plus its reverse-mode gradient (the paper obtains the
+ * same gradient by automatic differentiation of the renderer, Methods, "Line Radiative
+ * Transfer with RadJAX" and Fig. 2; here it is a hand-written fused adjoint).
+ * Seed: exactly one of
+ *   dL_dcube  DEVICE [nch][ny][nx] float32, the gradient of a scalar loss w.r.t. the cube, or
+ *   target    DEVICE [nch][ny][nx] float32; the loss is L = sum (cube - target)^2 and
+ *             dL/dcube = 2 (cube - target) is formed in the kernel (the loss value goes to
+ *             grads->loss if non-NULL).
+ * cube_out (DEVICE, may be NULL) receives the rendered cube (same values as rt_render up to
+ * FP32 rounding). Gradients w.r.t. every node of T, n_H2, v_turb and both surfaces are
+ * accumulated in FP64 (the arrays are zeroed by the call). The optical depth is checkpointed
+ * every 64 samples in a device scratch buffer that the call allocates and frees on `stream`
+ * (stream-ordered, cudaMallocAsync); the reverse march recomputes everything else.
+ * Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
+ */
+int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                      const rt_view *view, const rt_line *line, const float *dL_dcube,
+                      const float *target, float *cube_out, const rt_grads *grads, void *stream);
+
+/*
+ * rt_surface_powerlaw_grad -- chain rule from surface-node gradients to the parameters of a
+ * power-law surface h(r) = c (r / 100 au)^p m(r) (m: any fixed modulation):
+ *   out[0] = dL/dc = sum_i dL/dh_i h_i / c,   out[1] = dL/dp = sum_i dL/dh_i h_i ln(r_i/100 au),
+ * with r_i the grid's r nodes. dh: DEVICE [nr] float64; h: DEVICE [nr] float32 (the surface
+ * values used in the render); out: DEVICE 2 float64 (overwritten). Returns RT_OK, RT_EINVAL or
+ * RT_ECUDA.
+ */
+int rt_surface_powerlaw_grad(const rt_grid *grid, const double *dh, const float *h, double c,
+                             double *out, void *stream);
+
 /* Message for the last error on this thread ("" if none). */
 const char *rt_last_error(void);
 

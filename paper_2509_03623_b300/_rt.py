@@ -54,6 +54,11 @@ class rt_line(C.Structure):
                 ("m_co_amu", C.c_double), ("m_mol_amu", C.c_double), ("J_u", C.c_int)]
 
 
+class rt_grads(C.Structure):
+    _fields_ = [("dT", C.c_void_p), ("dn", C.c_void_p), ("dvt", C.c_void_p),
+                ("dh_lo", C.c_void_p), ("dh_hi", C.c_void_p), ("loss", C.c_void_p)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -75,6 +80,12 @@ def lib():
             L.rt_render.restype = C.c_int
             L.rt_count_gas_samples.argtypes = base + [C.c_void_p, C.c_void_p]
             L.rt_count_gas_samples.restype = C.c_int
+            L.rt_render_adjoint.argtypes = base + [C.c_void_p, C.c_void_p, C.c_void_p,
+                                                   P(rt_grads), C.c_void_p]
+            L.rt_render_adjoint.restype = C.c_int
+            L.rt_surface_powerlaw_grad.argtypes = [P(rt_grid), C.c_void_p, C.c_void_p,
+                                                   C.c_double, C.c_void_p, C.c_void_p]
+            L.rt_surface_powerlaw_grad.restype = C.c_int
             L.rt_last_error.restype = C.c_char_p
             L.rt_version.restype = C.c_char_p
             _lib = L
@@ -156,6 +167,62 @@ def rt_count_gas_samples(problem, fields=None, stream=None) -> int:
                                      C.byref(ln), C.c_void_p(cnt.data_ptr()),
                                      stream_handle(stream)))
     return int(cnt.item())
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _cube_arg(t, shape, name):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype.itemsize != 4 or not t.is_contiguous() or tuple(t.shape) != shape:
+        raise ValueError(f"{name} must be a contiguous CUDA float32 tensor of shape {shape}")
+    return t
+
+
+def rt_render_adjoint(problem, fields=None, dL_dcube=None, target=None, cube_out=True,
+                      stream=None):
+    """Fused forward + reverse march through the C ABI.
+
+    Give exactly one of dL_dcube (gradient of a loss w.r.t. the cube) or target (loss =
+    sum (cube - target)^2). Returns (cube or None, grads) with grads a dict of float64 CUDA
+    tensors T, n_h2, vturb [nz][nr], h_lo, h_hi [nr] and loss (1 element)."""
+    import torch
+    dd = fields if fields is not None else DeviceDisk(problem)
+    T, n, vt, hlo, hhi = dd.tensors()
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    shape = (vw.nch, vw.ny, vw.nx)
+    dL_dcube = _cube_arg(dL_dcube, shape, "dL_dcube")
+    target = _cube_arg(target, shape, "target")
+    dev = T.device
+    cube = None
+    if cube_out is True:
+        cube = torch.empty(shape, dtype=torch.float32, device=dev)
+    elif cube_out is not None and cube_out is not False:
+        cube = _cube_arg(cube_out, shape, "cube_out")
+    out = {k: torch.empty(tuple(t.shape), dtype=torch.float64, device=dev)
+           for k, t in zip(DeviceDisk.FIELDS, (T, n, vt, hlo, hhi))}
+    out["loss"] = torch.empty(1, dtype=torch.float64, device=dev)
+    gr = rt_grads(out["T"].data_ptr(), out["n_h2"].data_ptr(), out["vturb"].data_ptr(),
+                  out["h_lo"].data_ptr(), out["h_hi"].data_ptr(), out["loss"].data_ptr())
+    check(lib().rt_render_adjoint(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                                  _ptr(dL_dcube), _ptr(target), _ptr(cube), C.byref(gr),
+                                  stream_handle(stream)))
+    return cube, out
+
+
+def rt_surface_powerlaw_grad(problem, dh, h, c, stream=None):
+    """(dL/dc, dL/dp) of a surface h = c (r/100 au)^p m(r) from node gradients dh."""
+    import torch
+    g = rt_grid(int(problem.nr), int(problem.nz), int(problem.r_log), float(problem.r_in_au),
+                float(problem.r_out_au), float(problem.zr_max))
+    dh = dh.contiguous().to(torch.float64)
+    h = h.contiguous().to(torch.float32)
+    out = torch.empty(2, dtype=torch.float64, device=dh.device)
+    check(lib().rt_surface_powerlaw_grad(C.byref(g), _ptr(dh), _ptr(h), float(c), _ptr(out),
+                                         stream_handle(stream)))
+    return out
 
 
 def version() -> str:

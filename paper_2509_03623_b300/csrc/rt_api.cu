@@ -34,7 +34,7 @@ int set_error(int code, const char *fmt, ...) {
 
 void clear_error() { g_err[0] = 0; }
 
-static bool finite(double x) { return isfinite(x) != 0; }
+static bool is_finite(double x) { return isfinite(x) != 0; }
 
 // Rigid-rotor level statistics at temperature T: lower-level fraction
 // f_l = g_l exp(-E_l/kT)/Z and mean level energy <E>.
@@ -120,16 +120,16 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
   if (g.nr < 2 || g.nz < 2 || (long long)g.nr * g.nz > (1LL << 28))
     return set_error(RT_EINVAL, "grid needs 2 <= nr, nz and nr*nz <= 2^28 (got %d x %d)", g.nr,
                      g.nz);
-  if (!finite(g.r_in_au) || !finite(g.r_out_au) || !(g.r_in_au > 0) ||
+  if (!is_finite(g.r_in_au) || !is_finite(g.r_out_au) || !(g.r_in_au > 0) ||
       !(g.r_out_au > g.r_in_au))
     return set_error(RT_EINVAL, "grid radii need 0 < r_in < r_out");
-  if (!finite(g.zr_max) || !(g.zr_max > 0)) return set_error(RT_EINVAL, "zr_max must be > 0");
+  if (!is_finite(g.zr_max) || !(g.zr_max > 0)) return set_error(RT_EINVAL, "zr_max must be > 0");
   if (!f.T_K || !f.n_h2_cm3 || !f.vturb || !f.h_lo || !f.h_hi)
     return set_error(RT_EINVAL, "null field pointer");
-  if (!finite(f.x_co) || f.x_co < 0) return set_error(RT_EINVAL, "x_co must be finite and >= 0");
-  if (!finite(f.edge_w) || f.edge_w < 0) return set_error(RT_EINVAL, "edge_w must be >= 0");
-  if (!finite(o.incl_deg) || !finite(o.pa_deg) || !finite(o.mstar_msun) || o.mstar_msun < 0 ||
-      !finite(o.vsys_kms))
+  if (!is_finite(f.x_co) || f.x_co < 0) return set_error(RT_EINVAL, "x_co must be finite and >= 0");
+  if (!is_finite(f.edge_w) || f.edge_w < 0) return set_error(RT_EINVAL, "edge_w must be >= 0");
+  if (!is_finite(o.incl_deg) || !is_finite(o.pa_deg) || !is_finite(o.mstar_msun) || o.mstar_msun < 0 ||
+      !is_finite(o.vsys_kms))
     return set_error(RT_EINVAL, "geometry must be finite with mstar >= 0");
   if (v.nx < 0 || v.ny < 0) return set_error(RT_EINVAL, "negative image size");
   if (v.nch < 0 || v.nch > RT_MAX_CH)
@@ -137,16 +137,16 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
   if (v.nch > 0 && !v.v_kms) return set_error(RT_EINVAL, "null channel velocities");
   if (v.n_samples < 1 || v.n_samples > (1 << 20))
     return set_error(RT_EINVAL, "n_samples must be in [1, 2^20]");
-  if (!finite(v.I0) || !finite(v.half_fov_au)) return set_error(RT_EINVAL, "non-finite view");
+  if (!is_finite(v.I0) || !is_finite(v.half_fov_au)) return set_error(RT_EINVAL, "non-finite view");
   if (v.units != 0 && v.units != 1) return set_error(RT_EINVAL, "units must be 0 or 1");
-  if (v.units == 1 && !(finite(o.dist_pc) && o.dist_pc > 0))
+  if (v.units == 1 && !(is_finite(o.dist_pc) && o.dist_pc > 0))
     return set_error(RT_EINVAL, "dist_pc must be > 0 for Jy per pixel");
-  if (!(finite(l.nu0_hz) && l.nu0_hz > 0) || !(finite(l.A_ul) && l.A_ul >= 0) || l.J_u < 1 ||
-      !(finite(l.m_co_amu) && l.m_co_amu > 0) || !(finite(l.m_mol_amu) && l.m_mol_amu > 0) ||
-      !finite(l.B_rot_hz))
+  if (!(is_finite(l.nu0_hz) && l.nu0_hz > 0) || !(is_finite(l.A_ul) && l.A_ul >= 0) || l.J_u < 1 ||
+      !(is_finite(l.m_co_amu) && l.m_co_amu > 0) || !(is_finite(l.m_mol_amu) && l.m_mol_amu > 0) ||
+      !is_finite(l.B_rot_hz))
     return set_error(RT_EINVAL, "invalid line constants");
   for (int c = 0; c < v.nch; c++)
-    if (!finite(v.v_kms[c])) return set_error(RT_EINVAL, "non-finite channel velocity %d", c);
+    if (!is_finite(v.v_kms[c])) return set_error(RT_EINVAL, "non-finite channel velocity %d", c);
 
   memset(P, 0, sizeof(*P));
   P->nr = g.nr;
@@ -270,6 +270,43 @@ extern "C" int rt_count_gas_samples(const rt_grid *grid, const rt_fields *fields
       rc = launch_count(*P, count, (cudaStream_t)stream);
   }
   delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+// Shared validation of the adjoint seeds and gradient outputs.
+int rtb::check_adjoint_args(const MarchParams &P, const float *dL_dcube, const float *target,
+                       const rt_grads *grads) {
+  if (!grads || !grads->dT || !grads->dn || !grads->dvt || !grads->dh_lo || !grads->dh_hi)
+    return set_error(RT_EINVAL, "null gradient output");
+  long long n = (long long)P.nx * P.ny * P.nch;
+  if (n > 0 && ((dL_dcube == nullptr) == (target == nullptr)))
+    return set_error(RT_EINVAL, "give exactly one of dL_dcube and target");
+  return RT_OK;
+}
+
+extern "C" int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields,
+                                 const rt_geom *geom, const rt_view *view, const rt_line *line,
+                                 const float *dL_dcube, const float *target, float *cube_out,
+                                 const rt_grads *grads, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params(grid, fields, geom, view, line, P);
+  if (rc == RT_OK) rc = check_adjoint_args(*P, dL_dcube, target, grads);
+  if (rc == RT_OK)
+    rc = launch_adjoint(*P, dL_dcube, target, cube_out, *grads, (cudaStream_t)stream);
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+extern "C" int rt_surface_powerlaw_grad(const rt_grid *grid, const double *dh, const float *h,
+                                        double c, double *out, void *stream) {
+  if (!grid || !dh || !h || !out) return set_error(RT_EINVAL, "null argument");
+  if (grid->nr < 2 || !(grid->r_in_au > 0) || !(grid->r_out_au > grid->r_in_au))
+    return set_error(RT_EINVAL, "invalid grid");
+  if (!is_finite(c) || c == 0.0) return set_error(RT_EINVAL, "surface coefficient must be non-zero");
+  int rc = launch_surface_grad(*grid, dh, h, c, out, (cudaStream_t)stream);
   if (rc == RT_OK) clear_error();
   return rc;
 }

@@ -24,50 +24,6 @@ namespace rtb {
 
 constexpr int kWarps = 4;  // warps per block
 
-// Channel-independent physics of sample k of a ray: {kd, a, b, S} with
-//   kd  optical depth per unit profile (log2 units): dtau_c = kd 2^{-d_c^2}, 0 without gas
-//   a,b profile argument d_c = v_c b - a (b = sqrt(log2 e)/alpha, a = v_los b)
-//   S   LTE source function in units of 2 h nu0^3 / c^2
-__device__ __forceinline__ float4 sample_physics(const MarchParams &P, const float *tab,
-                                                 const Ray &R, int k) {
-  float kf = (float)k;
-  float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
-  float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
-  float r2 = fmaf(R.x, R.x, y * y);
-  Cell c = locate(P, z, r2);
-  float4 out = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
-  if (!(c.gas && R.hit && k < P.n_samples)) return out;
-  float T = bilerp(P.T, P.nr, c);
-  float n = bilerp(P.n, P.nr, c);
-  float vt = bilerp(P.vt, P.nr, c);
-  const float *hl = P.hlo + c.i0;
-  const float *hh = P.hhi + c.i0;
-  float hlo = lerpf(__ldg(hl), __ldg(hl + 1), c.fr);
-  float hhi = lerpf(__ldg(hh), __ldg(hh + 1), c.fr);
-  float X;
-  if (P.hard_edge) {
-    X = (c.zr >= hlo && c.zr <= hhi) ? P.x_co : 0.0f;
-  } else {
-    float ea = ex2((hlo - c.zr) * P.edge_k);
-    float eb = ex2((c.zr - hhi) * P.edge_k);
-    X = P.x_co * rcp((1.0f + ea) * (1.0f + eb));
-  }
-  // Keplerian rotation: v_los = sqrt(GM) sin i x (r^2 + z^2)^{-3/4} + v_sys
-  float vlos = fmaf(R.vfac, kepler_q(fmaf(z, z, r2)), P.vsys);
-  // line width
-  float Tg = fmaxf(T, 1e-3f);
-  float a2 = P.vturb_mach ? Tg * fmaf(P.c_mach, vt * vt, P.c_th) : fmaf(P.c_th, Tg, vt * vt);
-  float ia = rsq(a2);
-  // LTE: source function and tabulated lower-level opacity factor
-  float phi = lte_phi(tab, lg2(Tg), nullptr);
-  float eS = ex2(-P.theta_s * rcp(Tg));
-  out.w = eS * rcp(1.0f - eS);
-  out.x = P.kappa_k * (X * n) * ex2(phi) * ia * R.ds;
-  out.z = ia * 1.2011224087864498f;  // b = sqrt(log2 e) / alpha
-  out.y = vlos * out.z;              // a = v_los b
-  return out;
-}
-
 template <int LPR, int CPL, bool UNIF>
 __global__ void __launch_bounds__(kWarps * 32)
     march_fwd_kernel(const __grid_constant__ MarchParams P, float *__restrict__ cube) {
@@ -158,10 +114,10 @@ __global__ void __launch_bounds__(kWarps * 32)
 
 // Blocks of a kernel resident on the whole device at once (queried once per kernel and
 // device, then cached).
-static int resident_blocks(const void *kernel) {
+int resident_blocks(const void *kernel, int threads) {
   struct Entry {
     const void *k;
-    int dev, blocks;
+    int dev, threads, blocks;
   };
   static std::mutex mu;
   static Entry cache[64];
@@ -171,16 +127,17 @@ static int resident_blocks(const void *kernel) {
   {
     std::lock_guard<std::mutex> lk(mu);
     for (int i = 0; i < n; i++)
-      if (cache[i].k == kernel && cache[i].dev == dev) return cache[i].blocks;
+      if (cache[i].k == kernel && cache[i].dev == dev && cache[i].threads == threads)
+        return cache[i].blocks;
   }
   int nb = 0, nsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kWarps * 32, 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess ||
       nb < 1)
     nb = 1;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
     nsm = 1;
   std::lock_guard<std::mutex> lk(mu);
-  if (n < 64) cache[n++] = Entry{kernel, dev, nb * nsm};
+  if (n < 64) cache[n++] = Entry{kernel, dev, threads, nb * nsm};
   return nb * nsm;
 }
 
@@ -190,7 +147,7 @@ static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
   long long npix = (long long)P.nx * P.ny;
   long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
   long long need = (units + kWarps - 1) / kWarps;
-  long long cap = resident_blocks((const void *)kern);
+  long long cap = resident_blocks((const void *)kern, kWarps * 32);
   long long blocks = need < cap ? need : cap;
   kern<<<(unsigned)blocks, kWarps * 32, 0, stream>>>(P, cube);
 }

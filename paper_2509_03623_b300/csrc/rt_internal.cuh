@@ -204,12 +204,64 @@ __device__ __forceinline__ float lte_phi(const float *__restrict__ tab, float t,
   return fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
 }
 
-// Host-side helpers (rt_api.cu, rt_forward.cu)
+// Channel-independent physics of sample k of a ray: {kd, a, b, S} with
+//   kd  optical depth per unit profile (log2 units): dtau_c = kd 2^{-d_c^2}, 0 without gas
+//   a,b profile argument d_c = v_c b - a (b = sqrt(log2 e)/alpha, a = v_los b)
+//   S   LTE source function in units of 2 h nu0^3 / c^2
+__device__ __forceinline__ float4 sample_physics(const MarchParams &P, const float *tab,
+                                                 const Ray &R, int k) {
+  float kf = (float)k;
+  float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
+  float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
+  float r2 = fmaf(R.x, R.x, y * y);
+  Cell c = locate(P, z, r2);
+  float4 out = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+  if (!(c.gas && R.hit && k < P.n_samples)) return out;
+  float T = bilerp(P.T, P.nr, c);
+  float n = bilerp(P.n, P.nr, c);
+  float vt = bilerp(P.vt, P.nr, c);
+  const float *hl = P.hlo + c.i0;
+  const float *hh = P.hhi + c.i0;
+  float hlo = lerpf(__ldg(hl), __ldg(hl + 1), c.fr);
+  float hhi = lerpf(__ldg(hh), __ldg(hh + 1), c.fr);
+  float X;
+  if (P.hard_edge) {
+    X = (c.zr >= hlo && c.zr <= hhi) ? P.x_co : 0.0f;
+  } else {
+    float ea = ex2((hlo - c.zr) * P.edge_k);
+    float eb = ex2((c.zr - hhi) * P.edge_k);
+    X = P.x_co * rcp((1.0f + ea) * (1.0f + eb));
+  }
+  // Keplerian rotation: v_los = sqrt(GM) sin i x (r^2 + z^2)^{-3/4} + v_sys
+  float vlos = fmaf(R.vfac, kepler_q(fmaf(z, z, r2)), P.vsys);
+  // line width
+  float Tg = fmaxf(T, 1e-3f);
+  float a2 = P.vturb_mach ? Tg * fmaf(P.c_mach, vt * vt, P.c_th) : fmaf(P.c_th, Tg, vt * vt);
+  float ia = rsq(a2);
+  // LTE: source function and tabulated lower-level opacity factor
+  float phi = lte_phi(tab, lg2(Tg), nullptr);
+  float eS = ex2(-P.theta_s * rcp(Tg));
+  out.w = eS * rcp(1.0f - eS);
+  out.x = P.kappa_k * (X * n) * ex2(phi) * ia * R.ds;
+  out.z = ia * 1.2011224087864498f;  // b = sqrt(log2 e) / alpha
+  out.y = vlos * out.z;              // a = v_los b
+  return out;
+}
+
+// Host-side helpers (rt_api.cu, rt_forward.cu, rt_adjoint.cu)
 int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
                  const rt_view *view, const rt_line *line, MarchParams *P);
 int set_error(int code, const char *fmt, ...);
 void clear_error();
 int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream);
 int launch_count(const MarchParams &P, unsigned long long *count, cudaStream_t stream);
+void lane_layout(int nch, int *lpr, int *cpl);
+int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target, float *cube_out,
+                   const rt_grads &G, cudaStream_t stream);
+int check_adjoint_args(const MarchParams &P, const float *dL_dcube, const float *target,
+                       const rt_grads *grads);
+int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, double c,
+                        double *out, cudaStream_t stream);
+int resident_blocks(const void *kernel, int threads);
 
 }  // namespace rtb
