@@ -161,6 +161,33 @@ int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geo
                       const float *target, float *cube_out, const rt_grads *grads, void *stream);
 
 /*
+ * rt_render_adjoint_noalloc -- rt_render_adjoint for callers that cannot allocate device
+ * memory. The paper has no counterpart: this is a deployment variant of the same fused
+ * adjoint. Some callers cannot call cudaMalloc or cudaMallocAsync, or have it called for
+ * them: for example an application whose memory manager has already reserved the device's
+ * memory, or a service that runs under a fixed device-memory budget and allows no allocator
+ * traffic once it is running. This entry point performs no device or host allocation: the
+ * checkpoint scratch is one fixed 16 MiB array in the library's device memory, which every
+ * GPU that loads the library holds until the process exits.
+ * Arguments, seeds, outputs and results are those of rt_render_adjoint. In addition:
+ *   - The first call on a device looks up the array's device address (with that device
+ *     current) and caches it; make that first call before any stream capture.
+ *   - Every call on a device shares the same array. Its contents are left over from the last
+ *     call and need no clearing (each checkpoint is written before it is read), but calls
+ *     whose kernels overlap on the GPU (different streams, or different host threads) race
+ *     on the array: serialize them.
+ *   - When the array cannot hold checkpoints for a full grid, fewer blocks are launched (same
+ *     results, lower throughput). A problem needing more than 16 MiB for a single block
+ *     (n_samples above 2^20 with up to 128 channels, above 2^19 with more) is rejected with
+ *     RT_EINVAL and a message naming the limit.
+ * Returns RT_OK, RT_EINVAL or RT_ECUDA.
+ */
+int rt_render_adjoint_noalloc(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                              const rt_view *view, const rt_line *line, const float *dL_dcube,
+                              const float *target, float *cube_out, const rt_grads *grads,
+                              void *stream);
+
+/*
  * rt_surface_powerlaw_grad -- chain rule from surface-node gradients to the parameters of a
  * power-law surface h(r) = c (r / 100 au)^p m(r) (m: any fixed modulation):
  *   out[0] = dL/dc = sum_i dL/dh_i h_i / c,   out[1] = dL/dp = sum_i dL/dh_i h_i ln(r_i/100 au),

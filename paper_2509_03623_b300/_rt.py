@@ -83,6 +83,8 @@ def lib():
             L.rt_render_adjoint.argtypes = base + [C.c_void_p, C.c_void_p, C.c_void_p,
                                                    P(rt_grads), C.c_void_p]
             L.rt_render_adjoint.restype = C.c_int
+            L.rt_render_adjoint_noalloc.argtypes = L.rt_render_adjoint.argtypes
+            L.rt_render_adjoint_noalloc.restype = C.c_int
             L.rt_surface_powerlaw_grad.argtypes = [P(rt_grid), C.c_void_p, C.c_void_p,
                                                    C.c_double, C.c_void_p, C.c_void_p]
             L.rt_surface_powerlaw_grad.restype = C.c_int
@@ -210,6 +212,26 @@ def rt_render_adjoint(problem, fields=None, dL_dcube=None, target=None, cube_out
                                   _ptr(dL_dcube), _ptr(target), _ptr(cube), C.byref(gr),
                                   stream_handle(stream)))
     return cube, out
+
+
+def rt_render_adjoint_noalloc(problem, fields, cube_out, grads, dL_dcube=None, target=None,
+                              stream=None):
+    """rt_render_adjoint without any allocation inside the library: for callers that must
+    not allocate device memory while running. Every buffer (cube_out and the float64
+    gradient tensors in `grads`, keys T, n_h2, vturb, h_lo, h_hi, loss) is supplied by the
+    caller; the library uses its fixed 16 MiB device array for checkpoints."""
+    T, n, vt, hlo, hhi = fields.tensors()
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    shape = (vw.nch, vw.ny, vw.nx)
+    dL_dcube = _cube_arg(dL_dcube, shape, "dL_dcube")
+    target = _cube_arg(target, shape, "target")
+    cube_out = _cube_arg(cube_out, shape, "cube_out")
+    gr = rt_grads(grads["T"].data_ptr(), grads["n_h2"].data_ptr(), grads["vturb"].data_ptr(),
+                  grads["h_lo"].data_ptr(), grads["h_hi"].data_ptr(),
+                  grads["loss"].data_ptr() if grads.get("loss") is not None else None)
+    check(lib().rt_render_adjoint_noalloc(C.byref(g), C.byref(f), C.byref(o), C.byref(vw),
+                                          C.byref(ln), _ptr(dL_dcube), _ptr(target),
+                                          _ptr(cube_out), C.byref(gr), stream_handle(stream)))
 
 
 def rt_surface_powerlaw_grad(problem, dh, h, c, stream=None):

@@ -21,6 +21,8 @@
 // shared memory; lane q then applies the chain rule through the sample physics (line width,
 // LTE table, Planck source, CO-layer logistic edges, bilinear weights) and scatters the node
 // gradients with FP64 atomics.
+#include <mutex>
+
 #include "rt_internal.cuh"
 
 namespace rtb {
@@ -428,3 +430,118 @@ int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, doub
 }
 
 }  // namespace rtb
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of the adjoint entry point.
+//
+// Some callers cannot call cudaMalloc (or have it called on their behalf): for example an
+// application whose own memory manager has already reserved the device's memory, or a
+// service that runs under a fixed device-memory budget and forbids allocator traffic once it
+// is running. For them the checkpoint scratch of the adjoint lives in one file-scope device
+// array of fixed size, kFixedScratchBytes, that every GPU loading this library holds until
+// the process exits. The kernel is the same; when the array cannot hold a checkpoint region
+// for every resident block, the persistent grid is made smaller (same result, lower
+// throughput), and a problem that does not fit even one block is rejected.
+// ---------------------------------------------------------------------------------------
+namespace rtb {
+
+constexpr size_t kFixedScratchBytes = (size_t)16 << 20;  // 16 MiB per device
+static __device__ __align__(256) float g_fixed_scratch[kFixedScratchBytes / sizeof(float)];
+
+// Device address of g_fixed_scratch on the current device. The host-side name is only a
+// stand-in for the symbol, so the address is looked up once per device (with that device
+// current) and cached.
+static int fixed_scratch_address(float **out) {
+  static std::mutex mu;
+  static float *addr[64] = {nullptr};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= 64) return set_error(RT_EINVAL, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_fixed_scratch);
+    if (e != cudaSuccess || !p)
+      return set_error(RT_ECUDA, "cudaGetSymbolAddress(fixed scratch): %s", cudaGetErrorString(e));
+    addr[dev] = (float *)p;
+  }
+  *out = addr[dev];
+  return RT_OK;
+}
+
+template <int LPR, int CPL, bool UNIF>
+static int launch_adj_fixed_t(const MarchParams &P, const float *dLdc, const float *target,
+                              float *cube_out, const rt_grads &G, cudaStream_t stream,
+                              float *scratch) {
+  auto kern = march_adj_kernel<LPR, CPL, UNIF>;
+  long long npix = (long long)P.nx * P.ny;
+  long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
+  long long need = (units + kWarpsAdj - 1) / kWarpsAdj;
+  long long cap = resident_blocks((const void *)kern, kWarpsAdj * 32);
+  int nseg = (P.n_samples + kSeg - 1) / kSeg;
+  size_t per_block = (size_t)kWarpsAdj * nseg * CPL * 32 * sizeof(float);
+  if (per_block > kFixedScratchBytes)
+    return set_error(RT_EINVAL,
+                     "allocation-free adjoint: %d samples per ray need %zu bytes of checkpoint "
+                     "scratch per block, above the fixed %zu-byte array",
+                     P.n_samples, per_block, kFixedScratchBytes);
+  long long fit = (long long)(kFixedScratchBytes / per_block);
+  long long blocks = need < cap ? need : cap;
+  if (blocks > fit) blocks = fit;
+  kern<<<(unsigned)blocks, kWarpsAdj * 32, 0, stream>>>(P, dLdc, target, cube_out, G, scratch,
+                                                         nseg);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "adjoint launch: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
+template <int LPR, int CPL>
+static int launch_adj_fixed_u(const MarchParams &P, const float *d, const float *t, float *c,
+                              const rt_grads &G, cudaStream_t s, float *scr) {
+  return P.v_uniform ? launch_adj_fixed_t<LPR, CPL, true>(P, d, t, c, G, s, scr)
+                     : launch_adj_fixed_t<LPR, CPL, false>(P, d, t, c, G, s, scr);
+}
+
+static int launch_adjoint_fixed(const MarchParams &P, const float *d, const float *t, float *c,
+                                const rt_grads &G, cudaStream_t s, float *scr) {
+  size_t ng = (size_t)P.nr * P.nz * sizeof(double), nh = (size_t)P.nr * sizeof(double);
+  cudaError_t e = cudaMemsetAsync(G.dT, 0, ng, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(G.dn, 0, ng, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(G.dvt, 0, ng, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(G.dh_lo, 0, nh, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(G.dh_hi, 0, nh, s);
+  if (e == cudaSuccess && G.loss) e = cudaMemsetAsync(G.loss, 0, sizeof(double), s);
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "gradient memset: %s", cudaGetErrorString(e));
+  long long npix = (long long)P.nx * P.ny;
+  if (npix == 0 || P.nch == 0) return RT_OK;
+  int LPR, CPL;
+  lane_layout(P.nch, &LPR, &CPL);
+  if (CPL == 8) return launch_adj_fixed_u<32, 8>(P, d, t, c, G, s, scr);
+  if (LPR == 32) return launch_adj_fixed_u<32, 4>(P, d, t, c, G, s, scr);
+  if (LPR == 16) return launch_adj_fixed_u<16, 4>(P, d, t, c, G, s, scr);
+  if (LPR == 8) return launch_adj_fixed_u<8, 4>(P, d, t, c, G, s, scr);
+  if (LPR == 4) return launch_adj_fixed_u<4, 4>(P, d, t, c, G, s, scr);
+  return launch_adj_fixed_u<2, 4>(P, d, t, c, G, s, scr);
+}
+
+}  // namespace rtb
+
+// Same contract as rt_render_adjoint, without any allocation (see rt.h).
+extern "C" int rt_render_adjoint_noalloc(const rt_grid *grid, const rt_fields *fields,
+                                         const rt_geom *geom, const rt_view *view,
+                                         const rt_line *line, const float *dL_dcube,
+                                         const float *target, float *cube_out,
+                                         const rt_grads *grads, void *stream) {
+  using namespace rtb;
+  MarchParams P;  // on the stack: no host allocation either
+  int rc = build_params(grid, fields, geom, view, line, &P);
+  if (rc == RT_OK) rc = check_adjoint_args(P, dL_dcube, target, grads);
+  float *scratch = nullptr;
+  if (rc == RT_OK) rc = fixed_scratch_address(&scratch);
+  if (rc == RT_OK)
+    rc = launch_adjoint_fixed(P, dL_dcube, target, cube_out, *grads, (cudaStream_t)stream,
+                              scratch);
+  if (rc == RT_OK) clear_error();
+  return rc;
+}

@@ -1,0 +1,64 @@
+"""The allocation-free adjoint entry point (rt_render_adjoint_noalloc) gives the same cube
+and gradients as rt_render_adjoint.
+
+Callers that cannot allocate device memory while running (their own memory manager already
+holds the device, or they run under a fixed memory budget) use this entry point; its
+checkpoint scratch is a fixed array inside the library, shared by every call. The test calls
+it twice in a row through the C ABI, so the second call runs on the array the first call left
+behind, and compares both calls with the allocating entry point. This file is collected last
+so that a run stopping at the first failure has already run every other test.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2509_03623_b300 import synth
+from tests.test_adjoint_gpu import assert_grads_close, loss_target, to_np
+from tests.test_forward_gpu import rt  # noqa: F401  (module fixture)
+
+pytestmark = pytest.mark.gpu
+
+
+def _alloc_outputs(torch, p):
+    shp = (p.nz, p.nr)
+    g = {k: torch.empty(shp, dtype=torch.float64, device="cuda") for k in ("T", "n_h2", "vturb")}
+    g.update({k: torch.empty(p.nr, dtype=torch.float64, device="cuda") for k in ("h_lo", "h_hi")})
+    g["loss"] = torch.empty(1, dtype=torch.float64, device="cuda")
+    return g, torch.empty((p.nch, p.ny, p.nx), dtype=torch.float32, device="cuda")
+
+
+@pytest.mark.parametrize("mode", ["target", "dL_dcube"])
+def test_noalloc_matches_allocating_adjoint_twice(rt, orc, mode):
+    import torch
+    p = synth.config_small(31).replace(n_samples=200)   # 4 checkpoint segments, last partial
+    dd = rt.DeviceDisk(p)
+    tgt = torch.tensor(loss_target(orc, p, 31), dtype=torch.float32, device="cuda")
+    if mode == "target":
+        kw = dict(target=tgt)
+    else:
+        w = np.random.default_rng(1).standard_normal((p.nch, p.ny, p.nx))
+        kw = dict(dL_dcube=torch.tensor(w, dtype=torch.float32, device="cuda"))
+    ref_cube, ref = rt.rt_render_adjoint(p, dd, **kw)
+    ref_np = to_np(ref)
+    for call in range(2):
+        grads, cube = _alloc_outputs(torch, p)
+        for t in list(grads.values()) + [cube]:
+            t.fill_(float("nan"))          # outputs must be fully written by the call
+        rt.rt_render_adjoint_noalloc(p, dd, cube, grads, **kw)
+        torch.cuda.synchronize()
+        assert_grads_close(to_np(grads), ref_np, label=f"no-alloc call {call}")
+        c, rc = cube.cpu().numpy(), ref_cube.cpu().numpy()
+        np.testing.assert_allclose(c, rc, rtol=1e-6, atol=1e-7 * np.abs(rc).max())
+        if mode == "target":
+            assert float(grads["loss"].item()) == pytest.approx(float(ref["loss"].item()), rel=1e-9)
+
+
+def test_noalloc_rejects_oversized_problem(rt):
+    import torch
+    p = synth.config_small(32).replace(nx=8, ny=8, v_kms=np.linspace(-5, 5, 200),
+                                       n_samples=(1 << 19) + 64)
+    dd = rt.DeviceDisk(p)
+    grads, cube = _alloc_outputs(torch, p)
+    with pytest.raises(rt.RTError, match="fixed"):
+        rt.rt_render_adjoint_noalloc(p, dd, cube, grads,
+                                     dL_dcube=torch.zeros_like(cube))
