@@ -201,6 +201,22 @@ def run_ours(args):
     barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
 
+    # forward + fused adjoint (sum-of-squares loss against a fixed target cube)
+    target = (cube * 1.05).contiguous()
+    adj_steps = max(3, args.steps // 4)
+    for _ in range(2):
+        _rt.rt_render_adjoint(p, dd, target=target, cube_out=None)
+    barrier()
+    ea = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(adj_steps)]
+    for i in range(adj_steps):
+        flush.fill_(float(i))
+        ea[i][0].record(stream)
+        _rt.rt_render_adjoint(p, dd, target=target, cube_out=None)
+        ea[i][1].record(stream)
+    barrier()
+    adj_ms = sum(a.elapsed_time(b) for a, b in ea) / adj_steps
+
     # end to end through the public API: pinned host fields -> device, render, cube -> host
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k), dtype=np.float32)).pin_memory()
             for k in _rt.DeviceDisk.FIELDS}
@@ -222,12 +238,12 @@ def run_ours(args):
     clocks = clk.stop()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
 
-    t_max, e2e_max = ms, e2e_ms
+    t_max, e2e_max, adj_max = ms, e2e_ms, adj_ms
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms, e2e_ms], device=dev)
+        t = torch.tensor([ms, e2e_ms, adj_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max, e2e_max = float(t[0]), float(t[1])
+        t_max, e2e_max, adj_max = float(t[0]), float(t[1]), float(t[2])
     evals = p.evals * world
     value = evals / (t_max * 1e-3) / 1e9
     if rank == 0:
@@ -253,6 +269,10 @@ def run_ours(args):
             "e2e": {"value": evals / (e2e_max * 1e-3) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
+            "fwd_adjoint": {"value": evals / (adj_max * 1e-3) / 1e9, "unit": UNIT,
+                            "ms_per_step": adj_max, "steps": adj_steps,
+                            "note": "fused forward + reverse march with FP64 node gradients, "
+                                    "loss sum (I - I*)^2 formed in the kernel; nominal evals"},
             "clocks": clocks,
         }
         if world == 1 and not args.no_cpu_baseline:
