@@ -198,6 +198,88 @@ int rt_render_adjoint_noalloc(const rt_grid *grid, const rt_fields *fields, cons
 int rt_surface_powerlaw_grad(const rt_grid *grid, const double *dh, const float *h, double c,
                              double *out, void *stream);
 
+/* ------------------------------------------------------------------------------------- */
+/* Serving: a continuous-batching request loop                                            */
+/* ------------------------------------------------------------------------------------- */
+/*
+ * The paper evaluates the renderer many times over independent parameter sets (MCMC over
+ * disk parameters, Methods, "MCMC Inference of HD 163296"; neural-field training steps);
+ * the server below runs such independent renders and gradients as they arrive. A request is
+ * admitted when the number of requests on the device is below max_inflight and its device
+ * footprint fits in the memory budget (first come, first served; a request never jumps the
+ * queue). Admitted requests are launched at once, each on its own stream of a pool, so that
+ * the work of requests that arrive while others run overlaps on the device. Completion is
+ * signalled by a host callback enqueued after the request's work; nothing waits on the
+ * device. All functions are thread-safe.
+ */
+typedef struct rt_server rt_server;
+
+#define RT_REQ_RENDER 0   /* rt_render */
+#define RT_REQ_ADJOINT 1  /* rt_render_adjoint */
+
+#define RT_STATE_QUEUED 0
+#define RT_STATE_RUNNING 1
+#define RT_STATE_DONE 2
+#define RT_STATE_FAILED 3
+#define RT_STATE_CANCELLED 4
+
+#define RT_SERVER_FAKE_DEVICE 1  /* flag: run no GPU work; requests finish after fake_us */
+
+typedef struct {
+  int kind;                 /* RT_REQ_RENDER or RT_REQ_ADJOINT */
+  rt_grid grid;
+  rt_fields fields;         /* DEVICE fields; must stay valid until the request finishes */
+  rt_geom geom;
+  rt_view view;             /* v_kms (HOST) is copied at submit */
+  rt_line line;
+  float *cube;              /* DEVICE output [nch][ny][nx]; required for renders, may be NULL
+                               for gradients */
+  const float *dL_dcube;    /* gradients: exactly one of dL_dcube / target (DEVICE) */
+  const float *target;
+  rt_grads grads;           /* gradients: DEVICE outputs as for rt_render_adjoint */
+  int fake_us;              /* RT_SERVER_FAKE_DEVICE only: simulated run time */
+} rt_request;
+
+/*
+ * rt_server_create -- a server on the current device. mem_budget_bytes bounds the summed
+ * footprint of the requests on the device (cube, seed and gradient buffers they touch plus
+ * the checkpoint scratch the server allocates for gradients); max_inflight (>= 1) bounds how
+ * many run at once (one stream each); max_queue (>= 1) bounds the requests waiting for
+ * admission. flags: 0 or RT_SERVER_FAKE_DEVICE. Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
+ */
+int rt_server_create(size_t mem_budget_bytes, int max_inflight, int max_queue, int flags,
+                     rt_server **out);
+
+/*
+ * rt_submit -- validate and enqueue a request; *ticket identifies it. Returns RT_OK,
+ * RT_EINVAL (malformed request, nothing enqueued), RT_ENOMEM (footprint above the whole
+ * budget: it could never be admitted) or RT_EBUSY (max_queue requests already waiting).
+ */
+int rt_submit(rt_server *s, const rt_request *req, uint64_t *ticket);
+
+/* rt_poll -- state of a request (RT_STATE_*) and its latency in ms: submit to completion if
+   finished, submit to now otherwise. Never blocks. RT_ENOTFOUND for an unknown ticket. */
+int rt_poll(rt_server *s, uint64_t ticket, int *state, double *latency_ms);
+
+/* rt_wait -- block until the request finishes (DONE, FAILED or CANCELLED) or timeout_ms
+   passes (RT_ETIMEDOUT; the request keeps running). */
+int rt_wait(rt_server *s, uint64_t ticket, double timeout_ms, int *state, double *latency_ms);
+
+/* rt_cancel -- cancel a request that is still queued (RT_OK). A running request cannot be
+   cancelled (RT_EBUSY); a finished one is left as is (RT_OK). */
+int rt_cancel(rt_server *s, uint64_t ticket);
+
+/* Error message of a FAILED request ("" otherwise), copied into buf (size n). */
+int rt_request_error(rt_server *s, uint64_t ticket, char *buf, size_t n);
+
+/* Counters: requests queued and running, bytes of budget in use, requests completed. */
+int rt_server_stats(rt_server *s, int *queued, int *running, size_t *bytes_in_use,
+                    uint64_t *completed);
+
+/* rt_server_destroy -- cancel queued requests, wait for running ones (their device work is
+   finite), release streams and the scheduler thread. */
+int rt_server_destroy(rt_server *s);
+
 /* Message for the last error on this thread ("" if none). */
 const char *rt_last_error(void);
 

@@ -362,17 +362,31 @@ __global__ void surface_powerlaw_kernel(int nr, int r_log, double r_in, double r
   }
 }
 
+// Launch geometry of the adjoint kernel for P: blocks of the persistent grid and the
+// checkpoint scratch they need. cap_blocks <= 0 asks the occupancy calculator.
+template <int LPR, int CPL, bool UNIF>
+static void adj_geometry(const MarchParams &P, long long cap_blocks, long long *blocks,
+                         size_t *bytes) {
+  long long npix = (long long)P.nx * P.ny;
+  long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
+  long long need = (units + kWarpsAdj - 1) / kWarpsAdj;
+  long long cap = cap_blocks > 0
+                      ? cap_blocks
+                      : resident_blocks((const void *)march_adj_kernel<LPR, CPL, UNIF>,
+                                        kWarpsAdj * 32);
+  *blocks = need < cap ? need : cap;
+  int nseg = (P.n_samples + kSeg - 1) / kSeg;
+  *bytes = (size_t)(*blocks) * kWarpsAdj * nseg * CPL * 32 * sizeof(float);
+}
+
 template <int LPR, int CPL, bool UNIF>
 static int launch_adj_t(const MarchParams &P, const float *dLdc, const float *target,
                         float *cube_out, const rt_grads &G, cudaStream_t stream) {
   auto kern = march_adj_kernel<LPR, CPL, UNIF>;
-  long long npix = (long long)P.nx * P.ny;
-  long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
-  long long need = (units + kWarpsAdj - 1) / kWarpsAdj;
-  long long cap = resident_blocks((const void *)kern, kWarpsAdj * 32);
-  long long blocks = need < cap ? need : cap;
+  long long blocks;
+  size_t bytes;
+  adj_geometry<LPR, CPL, UNIF>(P, 0, &blocks, &bytes);
   int nseg = (P.n_samples + kSeg - 1) / kSeg;
-  size_t bytes = (size_t)blocks * kWarpsAdj * nseg * CPL * 32 * sizeof(float);
   float *scratch = nullptr;
   cudaError_t e = cudaMallocAsync((void **)&scratch, bytes, stream);
   if (e != cudaSuccess)
@@ -418,6 +432,29 @@ int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target,
   if (LPR == 2) return launch_adj_u<2, 4>(P, d, t, cube_out, G, stream);
   // one lane per ray would need 65 batch starts per warp in shared memory: use two
   return launch_adj_u<2, 4>(P, d, t, cube_out, G, stream);
+}
+
+// Checkpoint scratch rt_render_adjoint allocates for P (cap_blocks > 0 replaces the device
+// occupancy query, for planning without a GPU).
+size_t adjoint_scratch_bytes(const MarchParams &P, long long cap_blocks) {
+  long long npix = (long long)P.nx * P.ny;
+  if (npix == 0 || P.nch == 0) return 0;
+  int LPR, CPL;
+  lane_layout(P.nch, &LPR, &CPL);
+  long long b;
+  size_t bytes = 0;
+  const bool u = P.v_uniform != 0;
+#define RTB_GEOM(L, C)                                               \
+  (u ? adj_geometry<L, C, true>(P, cap_blocks, &b, &bytes)           \
+     : adj_geometry<L, C, false>(P, cap_blocks, &b, &bytes))
+  if (CPL == 8) RTB_GEOM(32, 8);
+  else if (LPR == 32) RTB_GEOM(32, 4);
+  else if (LPR == 16) RTB_GEOM(16, 4);
+  else if (LPR == 8) RTB_GEOM(8, 4);
+  else if (LPR == 4) RTB_GEOM(4, 4);
+  else RTB_GEOM(2, 4);
+#undef RTB_GEOM
+  return bytes;
 }
 
 int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, double c,

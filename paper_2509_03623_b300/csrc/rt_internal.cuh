@@ -258,6 +258,7 @@ int launch_count(const MarchParams &P, unsigned long long *count, cudaStream_t s
 void lane_layout(int nch, int *lpr, int *cpl);
 int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target, float *cube_out,
                    const rt_grads &G, cudaStream_t stream);
+size_t adjoint_scratch_bytes(const MarchParams &P, long long cap_blocks);
 int check_adjoint_args(const MarchParams &P, const float *dL_dcube, const float *target,
                        const rt_grads *grads);
 int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, double c,
