@@ -135,6 +135,65 @@ def config_of(p, extra=None):
     return c
 
 
+def serving_leg(dev, n=256, rate_hz=200.0, budget=40 << 30, max_inflight=8):
+    """Poisson-arriving mix of renders and gradients (sizes drawn per request) through the
+    continuous-batching server; the same requests run back to back is the serial baseline."""
+    import torch
+    from paper_2509_03623_b300 import _rt, serve, synth
+    mix = synth.request_mix(n, seed=0, rate_hz=rate_hz)
+    prep = []
+    for rq in mix:
+        p = rq.problem
+        dd = _rt.DeviceDisk(p, dev)
+        shape = (p.nch, p.ny, p.nx)
+        if rq.adjoint:
+            tgt = torch.zeros(shape, dtype=torch.float32, device=dev)
+            g = {k: torch.empty(tuple(t.shape), dtype=torch.float64, device=dev)
+                 for k, t in zip(("T", "n_h2", "vturb", "h_lo", "h_hi"), dd.tensors())}
+            g["loss"] = torch.empty(1, dtype=torch.float64, device=dev)
+            prep.append((rq, dd, tgt, g, None))
+        else:
+            prep.append((rq, dd, None, None, torch.empty(shape, dtype=torch.float32, device=dev)))
+    evals = sum(rq.problem.evals for rq in mix)
+    torch.cuda.synchronize()
+    # serial baseline: one request after another on one stream
+    t0 = time.perf_counter()
+    for rq, dd, tgt, g, cube in prep:
+        if rq.adjoint:
+            _rt.rt_render_adjoint(rq.problem, dd, target=tgt, cube_out=None)
+        else:
+            _rt.rt_render(rq.problem, dd, cube)
+    torch.cuda.synchronize()
+    serial_s = time.perf_counter() - t0
+    # served: submit at the arrival times
+    with serve.Server(mem_budget_bytes=budget, max_inflight=max_inflight) as srv:
+        tickets = []
+        t0 = time.perf_counter()
+        for rq, dd, tgt, g, cube in prep:
+            delay = t0 + rq.t_arrival_s - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            if rq.adjoint:
+                tickets.append(srv.submit_adjoint(rq.problem, dd, g, target=tgt))
+            else:
+                tickets.append(srv.submit_render(rq.problem, dd, cube))
+        lat = []
+        for t in tickets:
+            state, ms = srv.wait(t, 600000)
+            if state != "done":
+                raise RuntimeError(f"request failed: {srv.error(t)}")
+            lat.append(ms)
+        wall = time.perf_counter() - t0
+    lat = np.array(lat)
+    return {"requests": n, "arrival_rate_hz": rate_hz, "adjoint_requests": int(sum(r.adjoint for r in mix)),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "throughput": evals / wall / 1e9, "unit": UNIT,
+            "wall_s": wall, "serial_throughput": evals / serial_s / 1e9, "serial_s": serial_s,
+            "nominal_evals": evals, "max_inflight": max_inflight, "budget_bytes": budget,
+            "workload": "256 requests, Poisson 200/s, pixels {128,256,512}^2, channels "
+                        "{32,64,128}, samples {128,256,1024}, 30% gradients, 40 GB budget"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -275,6 +334,8 @@ def run_ours(args):
                                     "loss sum (I - I*)^2 formed in the kernel; nominal evals"},
             "clocks": clocks,
         }
+        if world == 1 and not args.no_serving:
+            out["serving"] = serving_leg(dev)
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_oracle_sample(p, args.cpu_budget)
             out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -293,6 +354,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

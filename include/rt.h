@@ -199,6 +199,35 @@ int rt_surface_powerlaw_grad(const rt_grid *grid, const double *dh, const float 
                              double *out, void *stream);
 
 /* ------------------------------------------------------------------------------------- */
+/* Neural field (Methods, "Neural Temperature Recovery": T(r,|z|) = MLP_w(gamma(r,|z|)))    */
+/* ------------------------------------------------------------------------------------- */
+/* Network: inputs x = (rhat, zhat), the normalised grid coordinates of a sample (rhat =
+ * fractional r node index / (nr-1), zhat = (|z|/r) / zr_max); features
+ * [sin 2 pi B x, cos 2 pi B x] for n_freq directions B; Linear layers with SiLU after every
+ * hidden layer. Supported shape: n_freq = 32, hidden = 4 layers of width 128, n_out = 4.
+ * Outputs o modulate the grid fields at each sample: T <- T e^{o0}, n_H2 <- n_H2 e^{o1},
+ * h_lo <- h_lo + h_scale o2, h_hi <- h_hi + h_scale o3. */
+typedef struct {
+  int n_freq, width, hidden, n_out;
+  const float *B;     /* DEVICE [n_freq][2] */
+  const float *W[5];  /* DEVICE float32 master weights per Linear layer, [out][in] */
+  const float *b[5];  /* DEVICE float32 biases [out] */
+  double h_scale;     /* surface offset scale */
+} rt_mlp;
+
+/*
+ * rt_mlp_eval -- network outputs for n inputs xy [n][2] (DEVICE float32) into out [n][4]
+ * (DEVICE float32). Runs on the tensor cores (tcgen05.mma, BF16 operands rounded from the
+ * FP32 master weights, FP32 accumulation in tensor memory, SiLU from the hardware tanh).
+ * Returns RT_OK, RT_EINVAL or RT_ECUDA.
+ */
+int rt_mlp_eval(const rt_mlp *mlp, const float *xy, float *out, long long n, void *stream);
+
+/* rt_mlp_status -- synchronous: 1 in *timed_out if a tensor-core MMA wait ever expired in this
+   process (the kernel then stops early and its outputs are incomplete), else 0. */
+int rt_mlp_status(int *timed_out);
+
+/* ------------------------------------------------------------------------------------- */
 /* Serving: a continuous-batching request loop                                            */
 /* ------------------------------------------------------------------------------------- */
 /*

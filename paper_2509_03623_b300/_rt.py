@@ -59,6 +59,12 @@ class rt_grads(C.Structure):
                 ("dh_lo", C.c_void_p), ("dh_hi", C.c_void_p), ("loss", C.c_void_p)]
 
 
+class rt_mlp(C.Structure):
+    _fields_ = [("n_freq", C.c_int), ("width", C.c_int), ("hidden", C.c_int), ("n_out", C.c_int),
+                ("B", C.c_void_p), ("W", C.c_void_p * 5), ("b", C.c_void_p * 5),
+                ("h_scale", C.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -88,6 +94,10 @@ def lib():
             L.rt_surface_powerlaw_grad.argtypes = [P(rt_grid), C.c_void_p, C.c_void_p,
                                                    C.c_double, C.c_void_p, C.c_void_p]
             L.rt_surface_powerlaw_grad.restype = C.c_int
+            L.rt_mlp_eval.argtypes = [P(rt_mlp), C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]
+            L.rt_mlp_eval.restype = C.c_int
+            L.rt_mlp_status.argtypes = [P(C.c_int)]
+            L.rt_mlp_status.restype = C.c_int
             L.rt_last_error.restype = C.c_char_p
             L.rt_version.restype = C.c_char_p
             _lib = L
@@ -245,6 +255,50 @@ def rt_surface_powerlaw_grad(problem, dh, h, c, stream=None):
     check(lib().rt_surface_powerlaw_grad(C.byref(g), _ptr(dh), _ptr(h), float(c), _ptr(out),
                                          stream_handle(stream)))
     return out
+
+
+class DeviceMLP:
+    """Device-resident float32 network (master weights) in the layout of rt_mlp."""
+
+    def __init__(self, w, device="cuda"):
+        import torch
+        self.B = torch.as_tensor(np.ascontiguousarray(w.B, dtype=np.float32), device=device)
+        self.W = [torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32), device=device)
+                  for x in w.W]
+        self.b = [torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32), device=device)
+                  for x in w.b]
+        self.h_scale = float(getattr(w, "h_scale", 0.02))
+
+    def struct(self):
+        m = rt_mlp()
+        m.n_freq = int(self.B.shape[0])
+        m.width = int(self.W[0].shape[0])
+        m.hidden = len(self.W) - 1
+        m.n_out = int(self.W[-1].shape[0])
+        m.B = self.B.data_ptr()
+        for i in range(5):
+            m.W[i] = self.W[i].data_ptr() if i < len(self.W) else None
+            m.b[i] = self.b[i].data_ptr() if i < len(self.b) else None
+        m.h_scale = self.h_scale
+        return m
+
+
+def rt_mlp_eval(net, xy, out=None, stream=None):
+    """Tensor-core (BF16, FP32 accumulate) network outputs [n][4] for inputs xy [n][2]."""
+    import torch
+    xy = xy.contiguous().float()
+    n = xy.shape[0]
+    if out is None:
+        out = torch.empty((n, 4), dtype=torch.float32, device=xy.device)
+    m = net.struct()
+    check(lib().rt_mlp_eval(C.byref(m), _ptr(xy), _ptr(out), int(n), stream_handle(stream)))
+    return out
+
+
+def rt_mlp_status() -> int:
+    v = C.c_int()
+    check(lib().rt_mlp_status(C.byref(v)))
+    return v.value
 
 
 def version() -> str:

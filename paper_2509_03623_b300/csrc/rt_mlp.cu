@@ -1,0 +1,360 @@
+// Neural-field MLP on the 5th-generation tensor cores (tcgen05), BF16 operands, FP32
+// accumulation in tensor memory (arXiv 2509.03623, Methods, "Neural Temperature Recovery":
+// T(r,|z|) = MLP_w(gamma(r,|z|)) with a sinusoidal encoding gamma; the network shape here is
+// 64 Fourier features -> 4 x 128 SiLU -> 4 outputs).
+//
+// One persistent CTA per SM (128 threads, ~150 KB of shared memory). At start the CTA
+// converts the FP32 master weights to BF16 into shared memory in the no-swizzle K-major
+// "core matrix" layout (8 rows x 16 bytes per core matrix) and allocates 128 columns of
+// tensor memory. Per tile of 128 samples:
+//   thread m computes the features of sample m (range-reduced sin/cos) into the A buffer;
+//   thread 0 issues the K/16 tcgen05.mma of the layer (M=128, N=128 or 16 for the last layer)
+//   and commits them to an mbarrier; every thread waits (bounded), reads its accumulator row
+//   back with tcgen05.ld, adds the bias, applies SiLU and writes the BF16 activations in place
+//   into the A buffer for the next layer; after the last layer it writes 4 FP32 outputs.
+// Waits on the mbarrier are bounded: on expiry the CTA records an error and stops after
+// releasing its tensor memory.
+#include <cuda_bf16.h>
+
+#include "rt_internal.cuh"
+
+namespace rtb {
+
+constexpr int kMlpF = 64;      // features (2 x 32 Fourier directions)
+constexpr int kMlpW = 128;     // hidden width
+constexpr int kMlpOut = 4;     // outputs
+constexpr int kMlpOutPad = 16; // last layer padded to the smallest MMA N
+constexpr int kMlpTile = 128;  // samples per tile (MMA M)
+constexpr unsigned kSpinLimit = 1u << 26;
+
+struct MlpParamsDev {
+  const float *B;     // [32][2]
+  const float *W[5];  // [out][in] fp32
+  const float *b[5];
+};
+
+struct __align__(1024) MlpSmem {
+  __nv_bfloat16 W1[kMlpW * kMlpF];          // 16 KB
+  __nv_bfloat16 Wh[3][kMlpW * kMlpW];       // 96 KB
+  __nv_bfloat16 W5[kMlpOutPad * kMlpW];     // 4 KB
+  __nv_bfloat16 A[kMlpTile * kMlpW];        // 32 KB
+  float bias[4][kMlpW];
+  float bias5[kMlpOutPad];
+  float Bf[32][2];
+  unsigned long long mbar;
+  unsigned tmem_base;
+  int abort;
+};
+
+static __device__ int g_mlp_error;  // set when a bounded wait expires
+
+// Element offset of (row r, column k) in a rows x K tile stored as core matrices of 8 rows x 8
+// bf16 (16 bytes), core matrix (r/8, k/8) at ((r/8) (K/8) + k/8) x 64 elements.
+__device__ __forceinline__ int cm_off(int r, int k, int K) {
+  return (((r >> 3) * (K >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor, no swizzle, K-major: LBO = distance between core
+// matrices along K (128 B), SBO = distance between 8-row groups ((K/8) x 128 B).
+__device__ __forceinline__ unsigned long long mma_desc(unsigned addr, int K) {
+  unsigned long long lbo = 128 >> 4, sbo = (unsigned long long)((K >> 3) * 128) >> 4;
+  return (unsigned long long)((addr >> 4) & 0x3FFF) | ((lbo & 0x3FFF) << 16) |
+         ((sbo & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128.
+__host__ __device__ constexpr unsigned idesc_bf16(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned tmem_d, unsigned long long a,
+                                         unsigned long long b, unsigned idesc, int accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(unsigned mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned phase) {
+  for (unsigned it = 0; it < kSpinLimit; it++) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void proxy_fence() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 32 consecutive accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float *v) {
+  unsigned r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+}
+
+// SiLU(x) = x sigma(x) = 0.5 x (1 + tanh(x/2)) (hardware tanh; the result is rounded to BF16).
+__device__ __forceinline__ float silu(float x) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * x));
+  float h = 0.5f * x;
+  return fmaf(h, t, h);
+}
+
+// Store 8 consecutive BF16 values of row m starting at column k (k multiple of 8).
+__device__ __forceinline__ void store8(__nv_bfloat16 *A, int m, int k, int K, const float *v) {
+  __nv_bfloat162 p[4];
+#pragma unroll
+  for (int j = 0; j < 4; j++) p[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+  *reinterpret_cast<uint4 *>(A + cm_off(m, k, K)) = *reinterpret_cast<uint4 *>(p);
+}
+
+// Fourier features of x = (rhat, zhat): [sin 2 pi B x, cos 2 pi B x], phases reduced to
+// [-1/2, 1/2) cycles before the hardware sin/cos.
+__device__ __forceinline__ void features(const MlpSmem &S, float rh, float zh, float *f) {
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    float ph = fmaf(S.Bf[i][0], rh, S.Bf[i][1] * zh);
+    ph -= rintf(ph);
+    float a = 6.283185307179586f * ph;
+    f[i] = __sinf(a);
+    f[32 + i] = __cosf(a);
+  }
+}
+
+// Input supplier: network inputs of sample `s` (returns false when it is not needed).
+struct XYInput {
+  const float *xy;
+  long long n;
+  __device__ bool get(long long s, float *rh, float *zh) const {
+    if (s >= n) return false;
+    float2 v = reinterpret_cast<const float2 *>(xy)[s];
+    *rh = v.x;
+    *zh = v.y;
+    return true;
+  }
+};
+
+template <class In>
+__global__ void __launch_bounds__(128, 1)
+    mlp_bf16_kernel(const MlpParamsDev Wp, In in, float *__restrict__ out, long long n) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  MlpSmem &S = *reinterpret_cast<MlpSmem *>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  // ---- one-time setup: weights to BF16 core-matrix layout, biases, TMEM, mbarrier ----
+  for (int i = tid; i < kMlpW * kMlpF; i += 128) {
+    int o = i / kMlpF, k = i % kMlpF;
+    S.W1[cm_off(o, k, kMlpF)] = __float2bfloat16_rn(Wp.W[0][i]);
+  }
+  for (int l = 0; l < 3; l++)
+    for (int i = tid; i < kMlpW * kMlpW; i += 128) {
+      int o = i / kMlpW, k = i % kMlpW;
+      S.Wh[l][cm_off(o, k, kMlpW)] = __float2bfloat16_rn(Wp.W[l + 1][i]);
+    }
+  for (int i = tid; i < kMlpOutPad * kMlpW; i += 128) {
+    int o = i / kMlpW, k = i % kMlpW;
+    S.W5[cm_off(o, k, kMlpW)] = __float2bfloat16_rn(o < kMlpOut ? Wp.W[4][o * kMlpW + k] : 0.0f);
+  }
+  for (int i = tid; i < 4 * kMlpW; i += 128) S.bias[i / kMlpW][i % kMlpW] = Wp.b[i / kMlpW][i % kMlpW];
+  if (tid < kMlpOutPad) S.bias5[tid] = tid < kMlpOut ? Wp.b[4][tid] : 0.0f;
+  if (tid < 64) S.Bf[tid >> 1][tid & 1] = Wp.B[tid];
+  if (tid == 0) {
+    S.abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar)), "r"(1));
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&S.tmem_base)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = S.tmem_base;
+  const unsigned tlane = tmem + ((unsigned)(warp * 32) << 16);  // this warp's TMEM lanes
+  const unsigned mbar = smem_u32(&S.mbar);
+  const unsigned aA = smem_u32(S.A);
+  unsigned phase = 0;
+
+  const long long ntiles = (n + kMlpTile - 1) / kMlpTile;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long s = tile * kMlpTile + tid;
+    float rh = 0.0f, zh = 0.0f;
+    const bool need = in.get(s, &rh, &zh);
+    if (!__syncthreads_or(need)) continue;
+    {
+      float f[kMlpF];
+      features(S, rh, zh, f);
+#pragma unroll
+      for (int k = 0; k < kMlpF; k += 8) store8(S.A, tid, k, kMlpF, f + k);
+    }
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    bool ok = true;
+    for (int l = 0; l < 5 && ok; l++) {
+      const int K = l == 0 ? kMlpF : kMlpW;
+      const int N = l == 4 ? kMlpOutPad : kMlpW;
+      if (tid == 0) {
+        tc_fence_after();
+        const unsigned bB = l == 0 ? smem_u32(S.W1) : (l == 4 ? smem_u32(S.W5) : smem_u32(S.Wh[l - 1]));
+        for (int ks = 0; ks < K / 16; ks++)
+          mma_bf16(tmem, mma_desc(aA + ks * 256, K), mma_desc(bB + ks * 256, K), idesc_bf16(N),
+                   ks > 0);
+        mma_commit(mbar);
+      }
+      ok = mbar_wait(mbar, phase);
+      phase ^= 1;
+      tc_fence_after();
+      if (!ok) {
+        S.abort = 1;
+        atomicExch(&g_mlp_error, 1);
+      }
+      if (ok && l < 4) {
+#pragma unroll
+        for (int c0 = 0; c0 < kMlpW; c0 += 32) {
+          float v[32];
+          tmem_ld32(tlane + c0, v);
+#pragma unroll
+          for (int j = 0; j < 32; j++) v[j] = silu(v[j] + S.bias[l][c0 + j]);
+#pragma unroll
+          for (int k = 0; k < 32; k += 8) store8(S.A, tid, c0 + k, kMlpW, v + k);
+        }
+      } else if (ok) {
+        float v[16];
+        tmem_ld16(tlane, v);
+        if (need) {
+          float4 o = make_float4(v[0] + S.bias5[0], v[1] + S.bias5[1], v[2] + S.bias5[2],
+                                 v[3] + S.bias5[3]);
+          reinterpret_cast<float4 *>(out)[s] = o;
+        }
+      }
+      proxy_fence();
+      tc_fence_before();
+      __syncthreads();
+      ok = !S.abort;
+    }
+    if (S.abort) break;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+  }
+}
+
+static int mlp_check(const rt_mlp *m) {
+  if (!m) return set_error(RT_EINVAL, "null network");
+  if (m->n_freq != 32 || m->width != kMlpW || m->hidden != 4 || m->n_out != kMlpOut)
+    return set_error(RT_EINVAL, "network shape must be 32 Fourier directions, 4 hidden layers "
+                     "of 128, 4 outputs (got %d, %d x %d, %d)", m->n_freq, m->hidden, m->width,
+                     m->n_out);
+  if (!m->B) return set_error(RT_EINVAL, "null Fourier directions");
+  for (int l = 0; l < 5; l++)
+    if (!m->W[l] || !m->b[l]) return set_error(RT_EINVAL, "null weight or bias of layer %d", l);
+  return RT_OK;
+}
+
+static MlpParamsDev mlp_dev(const rt_mlp *m) {
+  MlpParamsDev d;
+  d.B = m->B;
+  for (int l = 0; l < 5; l++) {
+    d.W[l] = m->W[l];
+    d.b[l] = m->b[l];
+  }
+  return d;
+}
+
+template <class In>
+static int launch_mlp(const rt_mlp *m, const In &in, float *out, long long n,
+                      cudaStream_t stream) {
+  if (n <= 0) return RT_OK;
+  auto kern = mlp_bf16_kernel<In>;
+  size_t smem = sizeof(MlpSmem);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "mlp smem attribute: %s", cudaGetErrorString(e));
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  long long tiles = (n + kMlpTile - 1) / kMlpTile;
+  long long blocks = tiles < nsm ? tiles : nsm;
+  kern<<<(unsigned)blocks, 128, smem, stream>>>(mlp_dev(m), in, out, n);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "mlp launch: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
+}  // namespace rtb
+
+using namespace rtb;
+
+extern "C" int rt_mlp_eval(const rt_mlp *mlp, const float *xy, float *out, long long n,
+                           void *stream) {
+  int rc = mlp_check(mlp);
+  if (rc == RT_OK && n < 0) rc = set_error(RT_EINVAL, "negative sample count");
+  if (rc == RT_OK && n > 0 && (!xy || !out)) rc = set_error(RT_EINVAL, "null input or output");
+  if (rc == RT_OK) rc = launch_mlp(mlp, XYInput{xy, n}, out, n, (cudaStream_t)stream);
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+extern "C" int rt_mlp_status(int *timed_out) {
+  if (!timed_out) return set_error(RT_EINVAL, "null output");
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_mlp_error, sizeof(int));
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "mlp status: %s", cudaGetErrorString(e));
+  *timed_out = v;
+  return RT_OK;
+}
