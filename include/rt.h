@@ -207,21 +207,56 @@ int rt_surface_powerlaw_grad(const rt_grid *grid, const double *dh, const float 
  * hidden layer. Supported shape: n_freq = 32, hidden = 4 layers of width 128, n_out = 4.
  * Outputs o modulate the grid fields at each sample: T <- T e^{o0}, n_H2 <- n_H2 e^{o1},
  * h_lo <- h_lo + h_scale o2, h_hi <- h_hi + h_scale o3. */
+#define RT_MLP_F16 0   /* tensor-core operands in FP16 (10-bit mantissa) */
+#define RT_MLP_BF16 1  /* tensor-core operands in BF16 (7-bit mantissa) */
+
 typedef struct {
   int n_freq, width, hidden, n_out;
   const float *B;     /* DEVICE [n_freq][2] */
   const float *W[5];  /* DEVICE float32 master weights per Linear layer, [out][in] */
   const float *b[5];  /* DEVICE float32 biases [out] */
   double h_scale;     /* surface offset scale */
+  int precision;      /* RT_MLP_F16 or RT_MLP_BF16: 16-bit format of the weights, features
+                         and hidden activations fed to the tensor cores (FP32 accumulation) */
 } rt_mlp;
 
 /*
  * rt_mlp_eval -- network outputs for n inputs xy [n][2] (DEVICE float32) into out [n][4]
- * (DEVICE float32). Runs on the tensor cores (tcgen05.mma, BF16 operands rounded from the
- * FP32 master weights, FP32 accumulation in tensor memory, SiLU from the hardware tanh).
+ * (DEVICE float32). Runs on the tensor cores (tcgen05.mma; weights, features and hidden
+ * activations rounded to the 16-bit format of mlp->precision, FP32 accumulation in tensor
+ * memory, SiLU from the hardware tanh).
  * Returns RT_OK, RT_EINVAL or RT_ECUDA.
  */
 int rt_mlp_eval(const rt_mlp *mlp, const float *xy, float *out, long long n, void *stream);
+
+/*
+ * rt_render_mlp -- forward render with the neural field: the network is evaluated on the
+ * tensor cores (as rt_mlp_eval) at every (pixel, sample) inside the gas grid, its outputs
+ * modulate the interpolated grid fields there (see rt_mlp), and the march proceeds as in
+ * rt_render. The per-sample outputs go through a device buffer of 16 n_pix n_samples bytes
+ * that the call allocates and frees on `stream` (stream-ordered). Returns RT_OK, RT_EINVAL,
+ * RT_ENOMEM or RT_ECUDA.
+ */
+int rt_render_mlp(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                  const rt_view *view, const rt_line *line, const rt_mlp *mlp, float *cube,
+                  void *stream);
+
+/*
+ * rt_sample_coords -- network inputs (rhat, zhat) of every (pixel, sample) as
+ * xy [n_pix][n_samples][2] float32 (DEVICE), (-1, -1) where the sample has no gas. With
+ * rt_render_modulated it lets any other evaluation of the network (e.g. in FP32) drive the
+ * same march. Field arrays are not read. Returns RT_OK, RT_EINVAL or RT_ECUDA.
+ */
+int rt_sample_coords(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                     const rt_view *view, const rt_line *line, float *xy, void *stream);
+
+/*
+ * rt_render_modulated -- rt_render with per-sample network outputs mod [n_pix][n_samples][4]
+ * float32 (DEVICE) applied as in rt_render_mlp with surface offset scale h_scale.
+ */
+int rt_render_modulated(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                        const rt_view *view, const rt_line *line, const float *mod,
+                        double h_scale, float *cube, void *stream);
 
 /* rt_mlp_status -- synchronous: 1 in *timed_out if a tensor-core MMA wait ever expired in this
    process (the kernel then stops early and its outputs are incomplete), else 0. */

@@ -62,7 +62,10 @@ class rt_grads(C.Structure):
 class rt_mlp(C.Structure):
     _fields_ = [("n_freq", C.c_int), ("width", C.c_int), ("hidden", C.c_int), ("n_out", C.c_int),
                 ("B", C.c_void_p), ("W", C.c_void_p * 5), ("b", C.c_void_p * 5),
-                ("h_scale", C.c_double)]
+                ("h_scale", C.c_double), ("precision", C.c_int)]
+
+
+RT_MLP_F16, RT_MLP_BF16 = 0, 1
 
 
 _lock = threading.Lock()
@@ -96,6 +99,13 @@ def lib():
             L.rt_surface_powerlaw_grad.restype = C.c_int
             L.rt_mlp_eval.argtypes = [P(rt_mlp), C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]
             L.rt_mlp_eval.restype = C.c_int
+            L.rt_render_mlp.argtypes = base + [P(rt_mlp), C.c_void_p, C.c_void_p]
+            L.rt_render_mlp.restype = C.c_int
+            L.rt_sample_coords.argtypes = base + [C.c_void_p, C.c_void_p]
+            L.rt_sample_coords.restype = C.c_int
+            L.rt_render_modulated.argtypes = base + [C.c_void_p, C.c_double, C.c_void_p,
+                                                     C.c_void_p]
+            L.rt_render_modulated.restype = C.c_int
             L.rt_mlp_status.argtypes = [P(C.c_int)]
             L.rt_mlp_status.restype = C.c_int
             L.rt_last_error.restype = C.c_char_p
@@ -260,8 +270,9 @@ def rt_surface_powerlaw_grad(problem, dh, h, c, stream=None):
 class DeviceMLP:
     """Device-resident float32 network (master weights) in the layout of rt_mlp."""
 
-    def __init__(self, w, device="cuda"):
+    def __init__(self, w, device="cuda", precision="f16"):
         import torch
+        self.precision = {"f16": RT_MLP_F16, "bf16": RT_MLP_BF16}[precision]
         self.B = torch.as_tensor(np.ascontiguousarray(w.B, dtype=np.float32), device=device)
         self.W = [torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32), device=device)
                   for x in w.W]
@@ -280,6 +291,7 @@ class DeviceMLP:
             m.W[i] = self.W[i].data_ptr() if i < len(self.W) else None
             m.b[i] = self.b[i].data_ptr() if i < len(self.b) else None
         m.h_scale = self.h_scale
+        m.precision = self.precision
         return m
 
 
@@ -292,6 +304,44 @@ def rt_mlp_eval(net, xy, out=None, stream=None):
         out = torch.empty((n, 4), dtype=torch.float32, device=xy.device)
     m = net.struct()
     check(lib().rt_mlp_eval(C.byref(m), _ptr(xy), _ptr(out), int(n), stream_handle(stream)))
+    return out
+
+
+def rt_render_mlp(problem, fields, net, out=None, stream=None):
+    """Forward render with the tensor-core neural field modulating the grid fields."""
+    import torch
+    T, n, vt, hlo, hhi = fields.tensors()
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    if out is None:
+        out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=T.device)
+    m = net.struct()
+    check(lib().rt_render_mlp(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                              C.byref(m), _ptr(out), stream_handle(stream)))
+    return out
+
+
+def rt_sample_coords(problem, fields, out=None, stream=None):
+    """Network inputs (rhat, zhat) of every (pixel, sample): [npix][n_samples][2]."""
+    import torch
+    T, n, vt, hlo, hhi = fields.tensors()
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    if out is None:
+        out = torch.empty((vw.nx * vw.ny, vw.n_samples, 2), dtype=torch.float32, device=T.device)
+    check(lib().rt_sample_coords(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                                 _ptr(out), stream_handle(stream)))
+    return out
+
+
+def rt_render_modulated(problem, fields, mod, h_scale, out=None, stream=None):
+    """Forward render with per-sample network outputs mod [npix][n_samples][4]."""
+    import torch
+    T, n, vt, hlo, hhi = fields.tensors()
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    if out is None:
+        out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=T.device)
+    mod = mod.contiguous().float()
+    check(lib().rt_render_modulated(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                                    _ptr(mod), float(h_scale), _ptr(out), stream_handle(stream)))
     return out
 
 

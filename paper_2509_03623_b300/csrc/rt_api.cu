@@ -311,6 +311,69 @@ extern "C" int rt_surface_powerlaw_grad(const rt_grid *grid, const double *dh, c
   return rc;
 }
 
+extern "C" int rt_sample_coords(const rt_grid *grid, const rt_fields *fields,
+                                const rt_geom *geom, const rt_view *view, const rt_line *line,
+                                float *xy, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params(grid, fields, geom, view, line, P);
+  if (rc == RT_OK && (long long)P->nx * P->ny > 0 && !xy) rc = set_error(RT_EINVAL, "null output");
+  if (rc == RT_OK) rc = launch_coords(*P, reinterpret_cast<float2 *>(xy), (cudaStream_t)stream);
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+extern "C" int rt_render_modulated(const rt_grid *grid, const rt_fields *fields,
+                                   const rt_geom *geom, const rt_view *view, const rt_line *line,
+                                   const float *mod, double h_scale, float *cube, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params(grid, fields, geom, view, line, P);
+  long long n = rc == RT_OK ? (long long)P->nx * P->ny * P->nch : 0;
+  if (rc == RT_OK && n > 0 && (!cube || !mod)) rc = set_error(RT_EINVAL, "null cube or modulation");
+  if (rc == RT_OK && !is_finite(h_scale)) rc = set_error(RT_EINVAL, "non-finite h_scale");
+  if (rc == RT_OK) {
+    P->mod = reinterpret_cast<const float4 *>(mod);
+    P->h_scale = (float)h_scale;
+    rc = launch_forward(*P, cube, (cudaStream_t)stream);
+  }
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+extern "C" int rt_render_mlp(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                             const rt_view *view, const rt_line *line, const rt_mlp *mlp,
+                             float *cube, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params(grid, fields, geom, view, line, P);
+  if (rc == RT_OK) rc = mlp_validate(mlp);
+  long long npix = rc == RT_OK ? (long long)P->nx * P->ny : 0;
+  if (rc == RT_OK && npix * P->nch > 0 && !cube) rc = set_error(RT_EINVAL, "null cube pointer");
+  if (rc == RT_OK && npix * P->nch > 0) {
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = (size_t)npix * P->n_samples * sizeof(float4);
+    float4 *mod = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&mod, bytes, st);
+    if (e != cudaSuccess) {
+      rc = set_error(RT_ENOMEM, "modulation buffer (%zu bytes): %s", bytes, cudaGetErrorString(e));
+    } else {
+      rc = launch_mlp_rays(mlp, *P, mod, st);
+      if (rc == RT_OK) {
+        P->mod = mod;
+        P->h_scale = (float)mlp->h_scale;
+        rc = launch_forward(*P, cube, st);
+      }
+      cudaFreeAsync(mod, st);
+    }
+  }
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
 extern "C" const char *rt_last_error(void) { return g_err; }
 
 extern "C" const char *rt_version(void) { return "b300-linert 0.1 (sm_103a)"; }

@@ -41,6 +41,10 @@ struct MarchParams {
   float theta_s;            // (E_u - E_l)/k * log2(e) [K]
   int v_uniform;            // channel velocities equally spaced: v_c = v0 + c dv
   float v0, dv;
+  // neural-field modulation per (pixel, sample): {o0, o1, o2, o3} with T e^{o0}, n e^{o1},
+  // h_lo + h_scale o2, h_hi + h_scale o3; nullptr for grid fields alone
+  const float4 *mod;
+  float h_scale;
   float v[RT_MAX_CH];
   float tab[kTabSeg * 4];
 };
@@ -80,6 +84,7 @@ struct Ray {
   float ds;                // segment length [au]
   float vfac;              // sqrt(GM) sin i x  [km s^-1 au^{1/2}]
   int hit;                 // ray crosses the bounding cylinder
+  int pix;                 // pixel index iy * nx + ix
 };
 
 // Round v to `bits` significant bits.
@@ -148,6 +153,7 @@ __device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, b
   R.ds = (float)ds;
   R.vfac = (float)((double)P.vk * P.sin_i * xs);
   R.hit = ok ? 1 : 0;
+  R.pix = iy * P.nx + ix;
   return R;
 }
 
@@ -224,6 +230,13 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
   const float *hh = P.hhi + c.i0;
   float hlo = lerpf(__ldg(hl), __ldg(hl + 1), c.fr);
   float hhi = lerpf(__ldg(hh), __ldg(hh + 1), c.fr);
+  if (P.mod) {
+    const float4 o = __ldg(P.mod + (long long)R.pix * P.n_samples + k);
+    T *= ex2(o.x * 1.4426950408889634f);
+    n *= ex2(o.y * 1.4426950408889634f);
+    hlo = fmaf(P.h_scale, o.z, hlo);
+    hhi = fmaf(P.h_scale, o.w, hhi);
+  }
   float X;
   if (P.hard_edge) {
     X = (c.zr >= hlo && c.zr <= hhi) ? P.x_co : 0.0f;
@@ -261,6 +274,9 @@ int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target,
 size_t adjoint_scratch_bytes(const MarchParams &P, long long cap_blocks);
 int check_adjoint_args(const MarchParams &P, const float *dL_dcube, const float *target,
                        const rt_grads *grads);
+int launch_mlp_rays(const rt_mlp *m, const MarchParams &P, float4 *mod, cudaStream_t stream);
+int mlp_validate(const rt_mlp *m);
+int launch_coords(const MarchParams &P, float2 *xy, cudaStream_t stream);
 int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, double c,
                         double *out, cudaStream_t stream);
 int resident_blocks(const void *kernel, int threads);

@@ -1,20 +1,21 @@
-// Neural-field MLP on the 5th-generation tensor cores (tcgen05), BF16 operands, FP32
-// accumulation in tensor memory (arXiv 2509.03623, Methods, "Neural Temperature Recovery":
+// Neural-field MLP on the 5th-generation tensor cores (tcgen05), 16-bit operands (FP16 or
+// BF16), FP32 accumulation in tensor memory (arXiv 2509.03623, Methods, "Neural Temperature Recovery":
 // T(r,|z|) = MLP_w(gamma(r,|z|)) with a sinusoidal encoding gamma; the network shape here is
 // 64 Fourier features -> 4 x 128 SiLU -> 4 outputs).
 //
-// One persistent CTA per SM (128 threads, ~150 KB of shared memory). At start the CTA
-// converts the FP32 master weights to BF16 into shared memory in the no-swizzle K-major
+// One persistent CTA per SM (128 threads, ~160 KB of shared memory). At start the CTA
+// converts the FP32 master weights to 16 bits into shared memory in the no-swizzle K-major
 // "core matrix" layout (8 rows x 16 bytes per core matrix) and allocates 128 columns of
 // tensor memory. Per tile of 128 samples:
 //   thread m computes the features of sample m (range-reduced sin/cos) into the A buffer;
 //   thread 0 issues the K/16 tcgen05.mma of the layer (M=128, N=128 or 16 for the last layer)
 //   and commits them to an mbarrier; every thread waits (bounded), reads its accumulator row
-//   back with tcgen05.ld, adds the bias, applies SiLU and writes the BF16 activations in place
+//   back with tcgen05.ld, adds the bias, applies SiLU and writes the 16-bit activations in place
 //   into the A buffer for the next layer; after the last layer it writes 4 FP32 outputs.
 // Waits on the mbarrier are bounded: on expiry the CTA records an error and stops after
 // releasing its tensor memory.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "rt_internal.cuh"
 
@@ -33,11 +34,14 @@ struct MlpParamsDev {
   const float *b[5];
 };
 
+// 16-bit operands (BF16 or FP16 bit patterns, chosen by the kernel's F16 parameter).
+typedef unsigned short h16;
+
 struct __align__(1024) MlpSmem {
-  __nv_bfloat16 W1[kMlpW * kMlpF];          // 16 KB
-  __nv_bfloat16 Wh[3][kMlpW * kMlpW];       // 96 KB
-  __nv_bfloat16 W5[kMlpOutPad * kMlpW];     // 4 KB
-  __nv_bfloat16 A[kMlpTile * kMlpW];        // 32 KB
+  h16 W1[kMlpW * kMlpF];          // 16 KB
+  h16 Wh[3][kMlpW * kMlpW];       // 96 KB
+  h16 W5[kMlpOutPad * kMlpW];     // 4 KB
+  h16 A[kMlpTile * kMlpW];        // 32 KB
   float bias[4][kMlpW];
   float bias5[kMlpOutPad];
   float Bf[32][2];
@@ -66,9 +70,17 @@ __device__ __forceinline__ unsigned long long mma_desc(unsigned addr, int K) {
          ((sbo & 0x3FFF) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128.
-__host__ __device__ constexpr unsigned idesc_bf16(int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16 (format 1) or FP16 (format 0),
+// both K-major, M = 128.
+__host__ __device__ constexpr unsigned idesc_16(int N, bool f16) {
+  return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) |
+         ((unsigned)(N >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+template <bool F16>
+__device__ __forceinline__ h16 to16(float x) {
+  if (F16) return __half_as_ushort(__float2half_rn(x));
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
 __device__ __forceinline__ void mma_bf16(unsigned tmem_d, unsigned long long a,
@@ -149,12 +161,14 @@ __device__ __forceinline__ float silu(float x) {
   return fmaf(h, t, h);
 }
 
-// Store 8 consecutive BF16 values of row m starting at column k (k multiple of 8).
-__device__ __forceinline__ void store8(__nv_bfloat16 *A, int m, int k, int K, const float *v) {
-  __nv_bfloat162 p[4];
+// Store 8 consecutive 16-bit values of row m starting at column k (k multiple of 8).
+template <bool F16>
+__device__ __forceinline__ void store8(h16 *A, int m, int k, int K, const float *v) {
+  unsigned p[4];
 #pragma unroll
-  for (int j = 0; j < 4; j++) p[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-  *reinterpret_cast<uint4 *>(A + cm_off(m, k, K)) = *reinterpret_cast<uint4 *>(p);
+  for (int j = 0; j < 4; j++)
+    p[j] = (unsigned)to16<F16>(v[2 * j]) | ((unsigned)to16<F16>(v[2 * j + 1]) << 16);
+  *reinterpret_cast<uint4 *>(A + cm_off(m, k, K)) = make_uint4(p[0], p[1], p[2], p[3]);
 }
 
 // Fourier features of x = (rhat, zhat): [sin 2 pi B x, cos 2 pi B x], phases reduced to
@@ -170,39 +184,82 @@ __device__ __forceinline__ void features(const MlpSmem &S, float rh, float zh, f
   }
 }
 
-// Input supplier: network inputs of sample `s` (returns false when it is not needed).
+// Input suppliers: the network inputs of sample s0 + tid of a tile (false when the sample
+// needs no evaluation). Called by every thread of the CTA.
 struct XYInput {
   const float *xy;
   long long n;
-  __device__ bool get(long long s, float *rh, float *zh) const {
-    if (s >= n) return false;
-    float2 v = reinterpret_cast<const float2 *>(xy)[s];
-    *rh = v.x;
-    *zh = v.y;
-    return true;
-  }
 };
 
-template <class In>
+__device__ __forceinline__ bool tile_input(const XYInput &in, Ray *, long long s0, int tid,
+                                           float *rh, float *zh) {
+  long long s = s0 + tid;
+  if (s >= in.n) return false;
+  float2 v = reinterpret_cast<const float2 *>(in.xy)[s];
+  *rh = v.x;
+  *zh = v.y;
+  return true;
+}
+
+// Samples of rays: s = pixel * n_samples + k. The setups of the (at most 128) rays a tile
+// touches are computed once, one per thread, into shared memory.
+struct RayInput {
+  MarchParams P;
+};
+
+__device__ __forceinline__ void sample_coords(const MarchParams &P, const Ray &R, int k,
+                                              bool *gas, float *rh, float *zh) {
+  float kf = (float)k;
+  float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
+  float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
+  Cell c = locate(P, z, fmaf(R.x, R.x, y * y));
+  *gas = c.gas && R.hit;
+  *rh = ((float)c.i0 + c.fr) / (float)(P.nr - 1);
+  *zh = c.zr / P.zr_max;
+}
+
+__device__ __forceinline__ bool tile_input(const RayInput &in, Ray *rays, long long s0, int tid,
+                                           float *rh, float *zh) {
+  const MarchParams &P = in.P;
+  const long long npix = (long long)P.nx * P.ny, n = npix * P.n_samples;
+  const long long pix0 = s0 / P.n_samples;
+  long long last = s0 + kMlpTile - 1 < n ? s0 + kMlpTile - 1 : n - 1;
+  const int nr = (int)(last / P.n_samples - pix0 + 1);
+  if (tid < nr) {
+    long long pix = pix0 + tid;
+    rays[tid] = setup_ray(P, (int)(pix % P.nx), (int)(pix / P.nx), true);
+  }
+  __syncthreads();
+  long long s = s0 + tid;
+  if (s >= n) return false;
+  const Ray &R = rays[s / P.n_samples - pix0];
+  bool gas;
+  sample_coords(P, R, (int)(s % P.n_samples), &gas, rh, zh);
+  return gas;
+}
+
+template <class In, bool F16>
 __global__ void __launch_bounds__(128, 1)
-    mlp_bf16_kernel(const MlpParamsDev Wp, In in, float *__restrict__ out, long long n) {
+    mlp_tc_kernel(const MlpParamsDev Wp, const __grid_constant__ In in, float *__restrict__ out,
+                    long long n) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   MlpSmem &S = *reinterpret_cast<MlpSmem *>(smem_raw);
+  Ray *rays = reinterpret_cast<Ray *>(smem_raw + sizeof(MlpSmem));
   const int tid = threadIdx.x, warp = tid >> 5;
 
   // ---- one-time setup: weights to BF16 core-matrix layout, biases, TMEM, mbarrier ----
   for (int i = tid; i < kMlpW * kMlpF; i += 128) {
     int o = i / kMlpF, k = i % kMlpF;
-    S.W1[cm_off(o, k, kMlpF)] = __float2bfloat16_rn(Wp.W[0][i]);
+    S.W1[cm_off(o, k, kMlpF)] = to16<F16>(Wp.W[0][i]);
   }
   for (int l = 0; l < 3; l++)
     for (int i = tid; i < kMlpW * kMlpW; i += 128) {
       int o = i / kMlpW, k = i % kMlpW;
-      S.Wh[l][cm_off(o, k, kMlpW)] = __float2bfloat16_rn(Wp.W[l + 1][i]);
+      S.Wh[l][cm_off(o, k, kMlpW)] = to16<F16>(Wp.W[l + 1][i]);
     }
   for (int i = tid; i < kMlpOutPad * kMlpW; i += 128) {
     int o = i / kMlpW, k = i % kMlpW;
-    S.W5[cm_off(o, k, kMlpW)] = __float2bfloat16_rn(o < kMlpOut ? Wp.W[4][o * kMlpW + k] : 0.0f);
+    S.W5[cm_off(o, k, kMlpW)] = to16<F16>(o < kMlpOut ? Wp.W[4][o * kMlpW + k] : 0.0f);
   }
   for (int i = tid; i < 4 * kMlpW; i += 128) S.bias[i / kMlpW][i % kMlpW] = Wp.b[i / kMlpW][i % kMlpW];
   if (tid < kMlpOutPad) S.bias5[tid] = tid < kMlpOut ? Wp.b[4][tid] : 0.0f;
@@ -231,13 +288,13 @@ __global__ void __launch_bounds__(128, 1)
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long s = tile * kMlpTile + tid;
     float rh = 0.0f, zh = 0.0f;
-    const bool need = in.get(s, &rh, &zh);
+    const bool need = tile_input(in, rays, tile * kMlpTile, tid, &rh, &zh);
     if (!__syncthreads_or(need)) continue;
     {
       float f[kMlpF];
       features(S, rh, zh, f);
 #pragma unroll
-      for (int k = 0; k < kMlpF; k += 8) store8(S.A, tid, k, kMlpF, f + k);
+      for (int k = 0; k < kMlpF; k += 8) store8<F16>(S.A, tid, k, kMlpF, f + k);
     }
     proxy_fence();
     tc_fence_before();
@@ -250,7 +307,7 @@ __global__ void __launch_bounds__(128, 1)
         tc_fence_after();
         const unsigned bB = l == 0 ? smem_u32(S.W1) : (l == 4 ? smem_u32(S.W5) : smem_u32(S.Wh[l - 1]));
         for (int ks = 0; ks < K / 16; ks++)
-          mma_bf16(tmem, mma_desc(aA + ks * 256, K), mma_desc(bB + ks * 256, K), idesc_bf16(N),
+          mma_bf16(tmem, mma_desc(aA + ks * 256, K), mma_desc(bB + ks * 256, K), idesc_16(N, F16),
                    ks > 0);
         mma_commit(mbar);
       }
@@ -269,7 +326,7 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
           for (int j = 0; j < 32; j++) v[j] = silu(v[j] + S.bias[l][c0 + j]);
 #pragma unroll
-          for (int k = 0; k < 32; k += 8) store8(S.A, tid, c0 + k, kMlpW, v + k);
+          for (int k = 0; k < 32; k += 8) store8<F16>(S.A, tid, c0 + k, kMlpW, v + k);
         }
       } else if (ok) {
         float v[16];
@@ -294,13 +351,18 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
-static int mlp_check(const rt_mlp *m) {
+int mlp_validate(const rt_mlp *m);
+static int mlp_check(const rt_mlp *m) { return mlp_validate(m); }
+
+int mlp_validate(const rt_mlp *m) {
   if (!m) return set_error(RT_EINVAL, "null network");
   if (m->n_freq != 32 || m->width != kMlpW || m->hidden != 4 || m->n_out != kMlpOut)
     return set_error(RT_EINVAL, "network shape must be 32 Fourier directions, 4 hidden layers "
                      "of 128, 4 outputs (got %d, %d x %d, %d)", m->n_freq, m->hidden, m->width,
                      m->n_out);
   if (!m->B) return set_error(RT_EINVAL, "null Fourier directions");
+  if (m->precision != RT_MLP_F16 && m->precision != RT_MLP_BF16)
+    return set_error(RT_EINVAL, "precision must be RT_MLP_F16 or RT_MLP_BF16");
   for (int l = 0; l < 5; l++)
     if (!m->W[l] || !m->b[l]) return set_error(RT_EINVAL, "null weight or bias of layer %d", l);
   return RT_OK;
@@ -316,12 +378,11 @@ static MlpParamsDev mlp_dev(const rt_mlp *m) {
   return d;
 }
 
-template <class In>
-static int launch_mlp(const rt_mlp *m, const In &in, float *out, long long n,
-                      cudaStream_t stream) {
-  if (n <= 0) return RT_OK;
-  auto kern = mlp_bf16_kernel<In>;
-  size_t smem = sizeof(MlpSmem);
+template <class In, bool F16>
+static int launch_mlp_t(const rt_mlp *m, const In &in, float *out, long long n,
+                        cudaStream_t stream) {
+  auto kern = mlp_tc_kernel<In, F16>;
+  size_t smem = sizeof(MlpSmem) + kMlpTile * sizeof(Ray);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return set_error(RT_ECUDA, "mlp smem attribute: %s", cudaGetErrorString(e));
@@ -333,6 +394,45 @@ static int launch_mlp(const rt_mlp *m, const In &in, float *out, long long n,
   kern<<<(unsigned)blocks, 128, smem, stream>>>(mlp_dev(m), in, out, n);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "mlp launch: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
+template <class In>
+static int launch_mlp(const rt_mlp *m, const In &in, float *out, long long n,
+                      cudaStream_t stream) {
+  if (n <= 0) return RT_OK;
+  return m->precision == RT_MLP_BF16 ? launch_mlp_t<In, false>(m, in, out, n, stream)
+                                     : launch_mlp_t<In, true>(m, in, out, n, stream);
+}
+
+int launch_mlp_rays(const rt_mlp *m, const MarchParams &P, float4 *mod, cudaStream_t stream) {
+  long long n = (long long)P.nx * P.ny * P.n_samples;
+  RayInput in;
+  in.P = P;
+  return launch_mlp(m, in, reinterpret_cast<float *>(mod), n, stream);
+}
+
+// Network inputs (rhat, zhat) of every (pixel, sample): [npix][n_samples] float2, (-1, -1)
+// where the sample has no gas.
+__global__ void coords_kernel(const __grid_constant__ MarchParams P, float2 *__restrict__ xy) {
+  const long long npix = (long long)P.nx * P.ny;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  Ray R = setup_ray(P, (int)(pix % P.nx), (int)(pix / P.nx), true);
+  for (int k = 0; k < P.n_samples; k++) {
+    bool gas;
+    float rh, zh;
+    sample_coords(P, R, k, &gas, &rh, &zh);
+    xy[pix * P.n_samples + k] = gas ? make_float2(rh, zh) : make_float2(-1.0f, -1.0f);
+  }
+}
+
+int launch_coords(const MarchParams &P, float2 *xy, cudaStream_t stream) {
+  long long npix = (long long)P.nx * P.ny;
+  if (npix == 0) return RT_OK;
+  coords_kernel<<<(unsigned)((npix + 127) / 128), 128, 0, stream>>>(P, xy);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "coords launch: %s", cudaGetErrorString(e));
   return RT_OK;
 }
 
