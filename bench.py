@@ -194,6 +194,41 @@ def serving_leg(dev, n=256, rate_hz=200.0, budget=40 << 30, max_inflight=8):
                         "{32,64,128}, samples {128,256,1024}, 30% gradients, 40 GB budget"}
 
 
+def neural_leg(dev, flush, reps=5):
+    """Neural-field workload (512x512 px, 128 channels, 256 samples): tensor-core network
+    with FP16 and BF16 operands, the FP32 network (cuBLAS, no TF32) driving the same march, and
+    the grid-field march alone."""
+    import torch
+    from paper_2509_03623_b300 import _rt, neural, synth
+    p = synth.config_neural(0)
+    w = synth.mlp_weights(7)
+    dd = _rt.DeviceDisk(p, dev)
+    cube = torch.empty((p.nch, p.ny, p.nx), dtype=torch.float32, device=dev)
+    nets = {k: _rt.DeviceMLP(w, dev, precision=k) for k in ("f16", "bf16")}
+    runs = {
+        "grid_only": lambda: _rt.rt_render(p, dd, cube),
+        "mlp_f16": lambda: _rt.rt_render_mlp(p, dd, nets["f16"], cube),
+        "mlp_bf16": lambda: _rt.rt_render_mlp(p, dd, nets["bf16"], cube),
+        "mlp_fp32": lambda: neural.render_mlp_fp32(p, dd, nets["f16"], cube),
+    }
+    out = {"workload": p.name, "nominal_evals": p.evals,
+           "mlp_samples": p.nx * p.ny * p.n_samples, "unit": UNIT}
+    for name, fn in runs.items():
+        fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for i in range(reps):
+            flush.fill_(float(i))
+            ev[i][0].record()
+            fn()
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / reps
+        out[name] = {"ms": ms, "value": p.evals / (ms * 1e-3) / 1e9}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -335,6 +370,7 @@ def run_ours(args):
             "clocks": clocks,
         }
         if world == 1 and not args.no_serving:
+            out["neural"] = neural_leg(dev, flush)
             out["serving"] = serving_leg(dev)
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_oracle_sample(p, args.cpu_budget)
