@@ -354,13 +354,14 @@ extern "C" int rt_render_mlp(const rt_grid *grid, const rt_fields *fields, const
   if (rc == RT_OK && npix * P->nch > 0 && !cube) rc = set_error(RT_EINVAL, "null cube pointer");
   if (rc == RT_OK && npix * P->nch > 0) {
     cudaStream_t st = (cudaStream_t)stream;
-    size_t bytes = (size_t)npix * P->n_samples * sizeof(float4);
+    size_t mod_bytes = (size_t)npix * P->n_samples * sizeof(float4);
+    size_t bytes = mod_bytes + ray_buffer_bytes(npix);
     float4 *mod = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&mod, bytes, st);
     if (e != cudaSuccess) {
       rc = set_error(RT_ENOMEM, "modulation buffer (%zu bytes): %s", bytes, cudaGetErrorString(e));
     } else {
-      rc = launch_mlp_rays(mlp, *P, mod, st);
+      rc = launch_mlp_rays(mlp, *P, mod, reinterpret_cast<char *>(mod) + mod_bytes, st);
       if (rc == RT_OK) {
         P->mod = mod;
         P->h_scale = (float)mlp->h_scale;

@@ -274,7 +274,9 @@ int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target,
 size_t adjoint_scratch_bytes(const MarchParams &P, long long cap_blocks);
 int check_adjoint_args(const MarchParams &P, const float *dL_dcube, const float *target,
                        const rt_grads *grads);
-int launch_mlp_rays(const rt_mlp *m, const MarchParams &P, float4 *mod, cudaStream_t stream);
+int launch_mlp_rays(const rt_mlp *m, const MarchParams &P, float4 *mod, void *ray_buf,
+                    cudaStream_t stream);
+size_t ray_buffer_bytes(long long npix);
 int mlp_validate(const rt_mlp *m);
 int launch_coords(const MarchParams &P, float2 *xy, cudaStream_t stream);
 int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, double c,

@@ -3,15 +3,20 @@
 // T(r,|z|) = MLP_w(gamma(r,|z|)) with a sinusoidal encoding gamma; the network shape here is
 // 64 Fourier features -> 4 x 128 SiLU -> 4 outputs).
 //
-// One persistent CTA per SM (128 threads, ~160 KB of shared memory). At start the CTA
-// converts the FP32 master weights to 16 bits into shared memory in the no-swizzle K-major
-// "core matrix" layout (8 rows x 16 bytes per core matrix) and allocates 128 columns of
-// tensor memory. Per tile of 128 samples:
-//   thread m computes the features of sample m (range-reduced sin/cos) into the A buffer;
-//   thread 0 issues the K/16 tcgen05.mma of the layer (M=128, N=128 or 16 for the last layer)
-//   and commits them to an mbarrier; every thread waits (bounded), reads its accumulator row
-//   back with tcgen05.ld, adds the bias, applies SiLU and writes the 16-bit activations in place
-//   into the A buffer for the next layer; after the last layer it writes 4 FP32 outputs.
+// One persistent CTA per SM (two tile groups of 8 warps, ~185 KB of shared memory); the
+// groups work on different tiles so that one group's MMAs overlap the other's epilogue. At
+// start the CTA converts the FP32 master weights to 16 bits into shared memory in the
+// no-swizzle K-major "core matrix" layout (8 rows x 16 bytes per core matrix) and allocates
+// 128 columns of tensor memory per group. Per tile of 128 samples, with two warps on each
+// TMEM lane quadrant (one per half of the columns, so row m belongs to two threads):
+//   the two threads of row m compute half of the features of sample m each (range-reduced
+//   sin/cos) into the A buffer;
+//   one thread issues the K/16 tcgen05.mma of the layer (M=128, N=128 or 16 for the last
+//   layer) and commits them to an mbarrier; every thread waits (bounded), reads its half of
+//   the accumulator row back with tcgen05.ld, adds the bias, applies SiLU in packed 16-bit
+//   arithmetic and writes the activations in place into the A buffer for the next layer;
+//   after the last layer one thread per row writes the 4 FP32 outputs.
+// Ray setups (double precision) come from a pre-pass, one thread per ray.
 // Waits on the mbarrier are bounded: on expiry the CTA records an error and stops after
 // releasing its tensor memory.
 #include <cuda_bf16.h>
@@ -37,17 +42,21 @@ struct MlpParamsDev {
 // 16-bit operands (BF16 or FP16 bit patterns, chosen by the kernel's F16 parameter).
 typedef unsigned short h16;
 
+constexpr int kTG = 2;        // tile groups per CTA, one tile in flight per group
+constexpr int kGW = 8;        // warps per group: two per TMEM lane quadrant (column halves)
+constexpr int kGT = kGW * 32; // threads per group
+
 struct __align__(1024) MlpSmem {
   h16 W1[kMlpW * kMlpF];          // 16 KB
   h16 Wh[3][kMlpW * kMlpW];       // 96 KB
   h16 W5[kMlpOutPad * kMlpW];     // 4 KB
-  h16 A[kMlpTile * kMlpW];        // 32 KB
+  h16 A[kTG][kMlpTile * kMlpW];   // 2 x 32 KB, one activation buffer per tile group
   float bias[4][kMlpW];
   float bias5[kMlpOutPad];
   float Bf[32][2];
-  unsigned long long mbar;
+  unsigned long long mbar[kTG];
   unsigned tmem_base;
-  int abort;
+  int abort[kTG];  // per tile group: written before, read after the group's barrier
 };
 
 static __device__ int g_mlp_error;  // set when a bounded wait expires
@@ -161,6 +170,25 @@ __device__ __forceinline__ float silu(float x) {
   return fmaf(h, t, h);
 }
 
+// SiLU of two pre-activations in the 16-bit format, packed: h = z/2 (exact), t = tanh(h)
+// (hardware, packed), SiLU = h + h t (one packed FMA); the result is the next layer's operand.
+template <bool F16>
+__device__ __forceinline__ unsigned silu2(float z0, float z1) {
+  unsigned z, h, t, r;
+  if (F16) {
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(z) : "f"(z1), "f"(z0));
+    asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(h) : "r"(z), "r"(0x38003800u));
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h));
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(h), "r"(t), "r"(h));
+  } else {
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(z) : "f"(z1), "f"(z0));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(h) : "r"(z), "r"(0x3F003F00u));
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(h), "r"(t), "r"(h));
+  }
+  return r;
+}
+
 // Store 8 consecutive 16-bit values of row m starting at column k (k multiple of 8).
 template <bool F16>
 __device__ __forceinline__ void store8(h16 *A, int m, int k, int K, const float *v) {
@@ -171,16 +199,19 @@ __device__ __forceinline__ void store8(h16 *A, int m, int k, int K, const float 
   *reinterpret_cast<uint4 *>(A + cm_off(m, k, K)) = make_uint4(p[0], p[1], p[2], p[3]);
 }
 
-// Fourier features of x = (rhat, zhat): [sin 2 pi B x, cos 2 pi B x], phases reduced to
-// [-1/2, 1/2) cycles before the hardware sin/cos.
-__device__ __forceinline__ void features(const MlpSmem &S, float rh, float zh, float *f) {
+// Fourier features of x = (rhat, zhat) for directions [16 half, 16 half + 16):
+// sin 2 pi B x into f[0..15], cos into f[16..31]; phases reduced to [-1/2, 1/2) cycles before
+// the hardware sin/cos.
+__device__ __forceinline__ void features(const MlpSmem &S, float rh, float zh, int half,
+                                         float *f) {
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
+  for (int j = 0; j < 16; j++) {
+    const int i = 16 * half + j;
     float ph = fmaf(S.Bf[i][0], rh, S.Bf[i][1] * zh);
     ph -= rintf(ph);
     float a = 6.283185307179586f * ph;
-    f[i] = __sinf(a);
-    f[32 + i] = __cosf(a);
+    f[j] = __sinf(a);
+    f[16 + j] = __cosf(a);
   }
 }
 
@@ -192,7 +223,7 @@ struct XYInput {
 };
 
 __device__ __forceinline__ bool tile_input(const XYInput &in, Ray *, long long s0, int tid,
-                                           float *rh, float *zh) {
+                                           float *rh, float *zh, int) {
   long long s = s0 + tid;
   if (s >= in.n) return false;
   float2 v = reinterpret_cast<const float2 *>(in.xy)[s];
@@ -201,10 +232,11 @@ __device__ __forceinline__ bool tile_input(const XYInput &in, Ray *, long long s
   return true;
 }
 
-// Samples of rays: s = pixel * n_samples + k. The setups of the (at most 128) rays a tile
-// touches are computed once, one per thread, into shared memory.
+// Samples of rays: s = pixel * n_samples + k; the ray setups come from a pre-pass (one thread
+// per ray, double precision) in device memory.
 struct RayInput {
   MarchParams P;
+  const Ray *rays;
 };
 
 __device__ __forceinline__ void sample_coords(const MarchParams &P, const Ray &R, int k,
@@ -218,94 +250,115 @@ __device__ __forceinline__ void sample_coords(const MarchParams &P, const Ray &R
   *zh = c.zr / P.zr_max;
 }
 
-__device__ __forceinline__ bool tile_input(const RayInput &in, Ray *rays, long long s0, int tid,
-                                           float *rh, float *zh) {
+__device__ __forceinline__ bool tile_input(const RayInput &in, Ray *, long long s0, int tid,
+                                           float *rh, float *zh, int) {
   const MarchParams &P = in.P;
-  const long long npix = (long long)P.nx * P.ny, n = npix * P.n_samples;
-  const long long pix0 = s0 / P.n_samples;
-  long long last = s0 + kMlpTile - 1 < n ? s0 + kMlpTile - 1 : n - 1;
-  const int nr = (int)(last / P.n_samples - pix0 + 1);
-  if (tid < nr) {
-    long long pix = pix0 + tid;
-    rays[tid] = setup_ray(P, (int)(pix % P.nx), (int)(pix / P.nx), true);
-  }
-  __syncthreads();
+  const long long n = (long long)P.nx * P.ny * P.n_samples;
   long long s = s0 + tid;
   if (s >= n) return false;
-  const Ray &R = rays[s / P.n_samples - pix0];
+  const Ray R = in.rays[s / P.n_samples];
   bool gas;
   sample_coords(P, R, (int)(s % P.n_samples), &gas, rh, zh);
   return gas;
 }
 
+// Ray setups of every pixel (one thread per ray).
+__global__ void rays_kernel(const __grid_constant__ MarchParams P, Ray *__restrict__ rays) {
+  const long long npix = (long long)P.nx * P.ny;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix < npix) rays[pix] = setup_ray(P, (int)(pix % P.nx), (int)(pix / P.nx), true);
+}
+
 template <class In, bool F16>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kGT * kTG, 1)
     mlp_tc_kernel(const MlpParamsDev Wp, const __grid_constant__ In in, float *__restrict__ out,
-                    long long n) {
+                  long long n) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   MlpSmem &S = *reinterpret_cast<MlpSmem *>(smem_raw);
-  Ray *rays = reinterpret_cast<Ray *>(smem_raw + sizeof(MlpSmem));
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int tg = tid / kGT;                       // tile group
+  const int q = warp & 3;                         // TMEM lane quadrant of this warp
+  const int half = (warp >> 2) & 1;               // column half handled by this warp
+  const int t = q * 32 + (tid & 31);              // row (= sample) of the tile
+  const int gt = tid % kGT;                       // thread index within the group
+  Ray *rays = nullptr;
 
-  // ---- one-time setup: weights to BF16 core-matrix layout, biases, TMEM, mbarrier ----
-  for (int i = tid; i < kMlpW * kMlpF; i += 128) {
+  // ---- one-time setup: weights to the 16-bit core-matrix layout, biases, TMEM, mbarriers ----
+  const int nt = blockDim.x;
+  for (int i = tid; i < kMlpW * kMlpF; i += nt) {
     int o = i / kMlpF, k = i % kMlpF;
     S.W1[cm_off(o, k, kMlpF)] = to16<F16>(Wp.W[0][i]);
   }
   for (int l = 0; l < 3; l++)
-    for (int i = tid; i < kMlpW * kMlpW; i += 128) {
+    for (int i = tid; i < kMlpW * kMlpW; i += nt) {
       int o = i / kMlpW, k = i % kMlpW;
       S.Wh[l][cm_off(o, k, kMlpW)] = to16<F16>(Wp.W[l + 1][i]);
     }
-  for (int i = tid; i < kMlpOutPad * kMlpW; i += 128) {
+  for (int i = tid; i < kMlpOutPad * kMlpW; i += nt) {
     int o = i / kMlpW, k = i % kMlpW;
     S.W5[cm_off(o, k, kMlpW)] = to16<F16>(o < kMlpOut ? Wp.W[4][o * kMlpW + k] : 0.0f);
   }
-  for (int i = tid; i < 4 * kMlpW; i += 128) S.bias[i / kMlpW][i % kMlpW] = Wp.b[i / kMlpW][i % kMlpW];
+  for (int i = tid; i < 4 * kMlpW; i += nt) S.bias[i / kMlpW][i % kMlpW] = Wp.b[i / kMlpW][i % kMlpW];
   if (tid < kMlpOutPad) S.bias5[tid] = tid < kMlpOut ? Wp.b[4][tid] : 0.0f;
   if (tid < 64) S.Bf[tid >> 1][tid & 1] = Wp.B[tid];
   if (tid == 0) {
-    S.abort = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar)), "r"(1));
+    for (int g = 0; g < kTG; g++) S.abort[g] = 0;
+    for (int g = 0; g < kTG; g++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar[g])), "r"(1));
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&S.tmem_base)),
-                 "r"(128));
+                 "r"(128 * kTG));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   proxy_fence();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const unsigned tmem = S.tmem_base;
-  const unsigned tlane = tmem + ((unsigned)(warp * 32) << 16);  // this warp's TMEM lanes
-  const unsigned mbar = smem_u32(&S.mbar);
-  const unsigned aA = smem_u32(S.A);
+  const unsigned tmem = S.tmem_base + 128 * tg;             // this group's columns
+  const unsigned tlane = tmem + ((unsigned)(q * 32) << 16);  // this warp's lanes
+  const unsigned mbar = smem_u32(&S.mbar[tg]);
+  h16 *A = S.A[tg];
+  const unsigned aA = smem_u32(A);
   unsigned phase = 0;
+  // named barrier of the tile group (ids 1, 2; 0 is __syncthreads)
+  auto gsync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(1 + tg), "r"(kGT) : "memory"); };
 
   const long long ntiles = (n + kMlpTile - 1) / kMlpTile;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long s = tile * kMlpTile + tid;
+  for (long long tile = (long long)blockIdx.x * kTG + tg; tile < ntiles;
+       tile += (long long)gridDim.x * kTG) {
+    const long long s = tile * kMlpTile + t;
     float rh = 0.0f, zh = 0.0f;
-    const bool need = tile_input(in, rays, tile * kMlpTile, tid, &rh, &zh);
-    if (!__syncthreads_or(need)) continue;
+    const bool need = tile_input(in, rays, tile * kMlpTile, t, &rh, &zh, tg);
+    // any sample of the tile needs the network? (group-wide vote through shared memory)
+    int any;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+        " bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(any)
+        : "r"((unsigned)need), "r"(1 + tg), "r"(kGT)
+        : "memory");
+    if (!any) continue;
     {
-      float f[kMlpF];
-      features(S, rh, zh, f);
-#pragma unroll
-      for (int k = 0; k < kMlpF; k += 8) store8<F16>(S.A, tid, k, kMlpF, f + k);
+      float f[32];
+      features(S, rh, zh, half, f);
+      store8<F16>(A, t, 16 * half, kMlpF, f);
+      store8<F16>(A, t, 16 * half + 8, kMlpF, f + 8);
+      store8<F16>(A, t, 32 + 16 * half, kMlpF, f + 16);
+      store8<F16>(A, t, 32 + 16 * half + 8, kMlpF, f + 24);
     }
     proxy_fence();
     tc_fence_before();
-    __syncthreads();
+    gsync();
     bool ok = true;
     for (int l = 0; l < 5 && ok; l++) {
       const int K = l == 0 ? kMlpF : kMlpW;
       const int N = l == 4 ? kMlpOutPad : kMlpW;
-      if (tid == 0) {
+      if (gt == 0) {
         tc_fence_after();
-        const unsigned bB = l == 0 ? smem_u32(S.W1) : (l == 4 ? smem_u32(S.W5) : smem_u32(S.Wh[l - 1]));
+        const unsigned bB =
+            l == 0 ? smem_u32(S.W1) : (l == 4 ? smem_u32(S.W5) : smem_u32(S.Wh[l - 1]));
         for (int ks = 0; ks < K / 16; ks++)
           mma_bf16(tmem, mma_desc(aA + ks * 256, K), mma_desc(bB + ks * 256, K), idesc_16(N, F16),
                    ks > 0);
@@ -315,23 +368,27 @@ __global__ void __launch_bounds__(128, 1)
       phase ^= 1;
       tc_fence_after();
       if (!ok) {
-        S.abort = 1;
+        S.abort[tg] = 1;
         atomicExch(&g_mlp_error, 1);
       }
       if (ok && l < 4) {
 #pragma unroll
-        for (int c0 = 0; c0 < kMlpW; c0 += 32) {
+        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
           float v[32];
           tmem_ld32(tlane + c0, v);
+          unsigned p[16];
 #pragma unroll
-          for (int j = 0; j < 32; j++) v[j] = silu(v[j] + S.bias[l][c0 + j]);
+          for (int j = 0; j < 16; j++)
+            p[j] = silu2<F16>(v[2 * j] + S.bias[l][c0 + 2 * j], v[2 * j + 1] + S.bias[l][c0 + 2 * j + 1]);
 #pragma unroll
-          for (int k = 0; k < 32; k += 8) store8<F16>(S.A, tid, c0 + k, kMlpW, v + k);
+          for (int k = 0; k < 4; k++)
+            *reinterpret_cast<uint4 *>(A + cm_off(t, c0 + 8 * k, kMlpW)) =
+                make_uint4(p[4 * k], p[4 * k + 1], p[4 * k + 2], p[4 * k + 3]);
         }
       } else if (ok) {
         float v[16];
         tmem_ld16(tlane, v);
-        if (need) {
+        if (need && half == 0) {
           float4 o = make_float4(v[0] + S.bias5[0], v[1] + S.bias5[1], v[2] + S.bias5[2],
                                  v[3] + S.bias5[3]);
           reinterpret_cast<float4 *>(out)[s] = o;
@@ -339,15 +396,16 @@ __global__ void __launch_bounds__(128, 1)
       }
       proxy_fence();
       tc_fence_before();
-      __syncthreads();
-      ok = !S.abort;
+      gsync();
+      ok = !S.abort[tg];
     }
-    if (S.abort) break;
+    if (S.abort[tg]) break;
   }
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base),
+                 "r"(128 * kTG));
   }
 }
 
@@ -382,7 +440,7 @@ template <class In, bool F16>
 static int launch_mlp_t(const rt_mlp *m, const In &in, float *out, long long n,
                         cudaStream_t stream) {
   auto kern = mlp_tc_kernel<In, F16>;
-  size_t smem = sizeof(MlpSmem) + kMlpTile * sizeof(Ray);
+  size_t smem = sizeof(MlpSmem);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return set_error(RT_ECUDA, "mlp smem attribute: %s", cudaGetErrorString(e));
@@ -390,8 +448,9 @@ static int launch_mlp_t(const rt_mlp *m, const In &in, float *out, long long n,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   long long tiles = (n + kMlpTile - 1) / kMlpTile;
-  long long blocks = tiles < nsm ? tiles : nsm;
-  kern<<<(unsigned)blocks, 128, smem, stream>>>(mlp_dev(m), in, out, n);
+  long long groups = (tiles + kTG - 1) / kTG;
+  long long blocks = groups < nsm ? groups : nsm;
+  kern<<<(unsigned)blocks, kGT * kTG, smem, stream>>>(mlp_dev(m), in, out, n);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "mlp launch: %s", cudaGetErrorString(e));
   return RT_OK;
@@ -405,12 +464,22 @@ static int launch_mlp(const rt_mlp *m, const In &in, float *out, long long n,
                                      : launch_mlp_t<In, true>(m, in, out, n, stream);
 }
 
-int launch_mlp_rays(const rt_mlp *m, const MarchParams &P, float4 *mod, cudaStream_t stream) {
-  long long n = (long long)P.nx * P.ny * P.n_samples;
+int launch_mlp_rays(const rt_mlp *m, const MarchParams &P, float4 *mod, void *ray_buf,
+                    cudaStream_t stream) {
+  long long npix = (long long)P.nx * P.ny;
+  long long n = npix * P.n_samples;
+  if (n == 0) return RT_OK;
+  Ray *rays = reinterpret_cast<Ray *>(ray_buf);
+  rays_kernel<<<(unsigned)((npix + 127) / 128), 128, 0, stream>>>(P, rays);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "ray setup launch: %s", cudaGetErrorString(e));
   RayInput in;
   in.P = P;
+  in.rays = rays;
   return launch_mlp(m, in, reinterpret_cast<float *>(mod), n, stream);
 }
+
+size_t ray_buffer_bytes(long long npix) { return (size_t)npix * sizeof(Ray); }
 
 // Network inputs (rhat, zhat) of every (pixel, sample): [npix][n_samples] float2, (-1, -1)
 // where the sample has no gas.
