@@ -151,9 +151,13 @@ typedef struct {
  *             grads->loss if non-NULL).
  * cube_out (DEVICE, may be NULL) receives the rendered cube (same values as rt_render up to
  * FP32 rounding). Gradients w.r.t. every node of T, n_H2, v_turb and both surfaces are
- * accumulated in FP64 (the arrays are zeroed by the call). The optical depth is checkpointed
- * every 64 samples in a device scratch buffer that the call allocates and frees on `stream`
- * (stream-ordered, cudaMallocAsync); the reverse march recomputes everything else.
+ * accumulated in FP64 and overwrite the arrays. The call allocates and frees one device
+ * scratch buffer on `stream` (stream-ordered, cudaMallocAsync) holding the optical-depth
+ * checkpoints (every 64 samples; the reverse march recomputes everything else) and up to 32
+ * replicated copies of the node-gradient arrays (at most 32 MiB) plus up to 128 of the
+ * surface-gradient arrays, summed in FP64 into the outputs at the end: FP64 atomics on one
+ * address are applied one after another, and without the copies the surface entries, which
+ * every sample at a given radius updates, serialize the kernel.
  * Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
  */
 int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
@@ -166,19 +170,22 @@ int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geo
  * adjoint. Some callers cannot call cudaMalloc or cudaMallocAsync, or have it called for
  * them: for example an application whose memory manager has already reserved the device's
  * memory, or a service that runs under a fixed device-memory budget and allows no allocator
- * traffic once it is running. This entry point performs no device or host allocation: the
- * checkpoint scratch is one fixed 16 MiB array in the library's device memory, which every
- * GPU that loads the library holds until the process exits.
+ * traffic once it is running. This entry point performs no device or host allocation: its
+ * scratch (checkpoints, and replicated gradient accumulators where room is left) is one
+ * fixed 16 MiB array in the library's device memory, which every GPU that loads the library
+ * holds until the process exits.
  * Arguments, seeds, outputs and results are those of rt_render_adjoint. In addition:
  *   - The first call on a device looks up the array's device address (with that device
  *     current) and caches it; make that first call before any stream capture.
- *   - Every call on a device shares the same array. Its contents are left over from the last
- *     call and need no clearing (each checkpoint is written before it is read), but calls
- *     whose kernels overlap on the GPU (different streams, or different host threads) race
- *     on the array: serialize them.
- *   - When the array cannot hold checkpoints for a full grid, fewer blocks are launched (same
- *     results, lower throughput). A problem needing more than 16 MiB for a single block
- *     (n_samples above 2^20 with up to 128 channels, above 2^19 with more) is rejected with
+ *   - Every call on a device shares the same array. Each call clears what it needs (the
+ *     checkpoints are written before they are read, the gradient copies are zeroed on
+ *     `stream`), but calls whose kernels overlap on the GPU (different streams, or different
+ *     host threads) race on the array: serialize them.
+ *   - Checkpoints get at most 12 MiB of the array. When that cannot hold checkpoints for a
+ *     full grid, fewer blocks are launched; where fewer gradient copies fit (or none: then
+ *     the kernel adds straight into the output arrays), the FP64 sums run in another order.
+ *     Same results, lower throughput. A problem whose single block needs more than 12 MiB
+ *     of checkpoints (above about 196,000 samples per ray at the earliest) is rejected with
  *     RT_EINVAL and a message naming the limit.
  * Returns RT_OK, RT_EINVAL or RT_ECUDA.
  */
@@ -307,7 +314,7 @@ typedef struct {
 /*
  * rt_server_create -- a server on the current device. mem_budget_bytes bounds the summed
  * footprint of the requests on the device (cube, seed and gradient buffers they touch plus
- * the checkpoint scratch the server allocates for gradients); max_inflight (>= 1) bounds how
+ * the scratch the adjoint allocates for gradients); max_inflight (>= 1) bounds how
  * many run at once (one stream each); max_queue (>= 1) bounds the requests waiting for
  * admission. flags: 0 or RT_SERVER_FAKE_DEVICE. Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
  */

@@ -1,141 +1,254 @@
-// Fused adjoint of the march: forward march with optical-depth checkpoints, then a reverse
-// march that recomputes the transmittance and propagates dL/dcube back to every node of the
-// (r, z/r) fields and the CO surfaces.
+// Fused adjoint of the march: a forward march that renders the cube, forms the loss seed and
+// stores optical-depth checkpoints every 64 samples, then a reverse march that propagates
+// dL/dcube back to every node of the (r, z/r) fields and the CO surfaces (and, for
+// neural-field renders, to the per-sample network outputs).
 //
-// Reverse recursion (per channel; T_k transmittance before sample k, e_k = 2^-dt_k its
-// factor over the segment, S_k the source, gI = dL/dI, g = dL/dT_{k+1} from the later part
-// of the ray, seeded with dL/dcube * I0 at the far end):
-//   G      = g - gI S_k                      full dL/dT_{k+1} (T_{k+1} also enters step k)
-//   dL/dS_k  = gI T_k (1 - e_k)
-//   dL/ddt_k = -ln2 G T_{k+1}                (dt in log2 units)
-//   g     <- g - G (1 - e_k)                 (= G e_k + gI S_k: a convex update, no division)
-// with 1 - e_k from a series for small dt (no cancellation). The reverse march runs over
-// 64-sample segments from the last to the first: each segment's optical depth at its start
-// was checkpointed by the forward pass (device scratch); the batch starts inside the segment
-// are recomputed forward into shared memory; the batches are then walked backward, the
-// transmittance being rebuilt from the batch-end optical depth by subtracting the recomputed
-// per-sample increments.
+// Gradient of one channel. With T_k = 2^-tau_k the transmittance in front of sample k,
+// dt_k its optical depth (log2 units), S_k its source and S_N the background, the intensity
+// is I = sum_k S_k (T_k - T_{k+1}) + S_N T_N, and
+//   dI/dS_k  = T_k - T_{k+1}
+//   dI/ddt_k = -ln2 A_k,   A_k = sum_{m>k} (S_m - S_{m-1}) T_m = A_{k+1} + (S_{k+1} - S_k) T_{k+1}.
+// A is a suffix sum, accumulated back to front from small terms (it vanishes behind optically
+// thick gas, where a front-to-back form I - prefix would leave rounding noise of order I).
+// Samples without gas (dt = 0 in every channel) drop out exactly, so they are skipped and
+// S_{k+1} means the source of the next sample with gas.
 //
-// Per sample, the per-channel partial derivatives (w.r.t. the optical-depth factor kd, the
-// profile terms a and b and the source S) are summed over the lanes of the ray through
-// shared memory; lane q then applies the chain rule through the sample physics (line width,
-// LTE table, Planck source, CO-layer logistic edges, bilinear weights) and scatters the node
-// gradients with FP64 atomics.
+// The transmittance of the reverse march comes from optical depths summed front to back: per
+// 64-sample segment (last to first) the batch starts are recomputed forward from the
+// segment's checkpoint into the warp's scratch, and within a batch of LPR samples the
+// optical depth is rebuilt by subtracting the recomputed increments from the batch end.
+//
+// Per sample, lane q of a ray computes the channel-independent physics of its sample with
+// the local partial derivatives (kept in shared memory); the per-channel sums
+//   ax = sum_c gI_c A_c g_c,  ay = sum_c gI_c A_c g_c d_c^2,  aS = sum_c gI_c (T_k - T_{k+1})
+// (g_c = 2^-d_c^2 the profile, gI_c = dL/dI_c) are reduced over the lanes of the ray through
+// shared memory, and lane q applies the chain rule through the line width, the LTE table,
+// the Planck source, the CO-layer edges and the bilinear weights, scattering the node
+// gradients with FP64 atomics into replicated accumulators.
 #include <mutex>
 
 #include "rt_internal.cuh"
 
 namespace rtb {
 
-constexpr int kWarpsAdj = 2;  // warps per block
-constexpr int kSeg = 64;      // samples per checkpoint segment
+// warps per block: 4, or 2 where the per-warp shared memory is large (16 or 32 lanes per ray)
+template <int LPR>
+constexpr int adj_wpb() {
+  return LPR >= 16 ? 2 : 4;
+}
+constexpr int kSeg = 64;  // samples per checkpoint segment
+
+// Per-warp scratch in floats: checkpoints of each segment, then the batch starts of the
+// segment being reversed, each CPL x 32 (lane-contiguous).
+template <int LPR, int CPL>
+__host__ __device__ constexpr long long adj_warp_floats(int nseg) {
+  return (long long)(nseg + kSeg / LPR + 1) * CPL * 32;
+}
 constexpr float kLn2 = 0.6931471805599453f;
 
-// 1 - 2^-x for x >= 0 without cancellation: series of 1 - e^-y (y = x ln 2) up to y^4 below
-// y = 0.05 (relative truncation < 6e-8), 1 - ex2(-x) above.
-__device__ __forceinline__ float one_minus_ex2neg(float x) {
-  if (x < 0.0721347520f)
-    return x * fmaf(x, fmaf(x, fmaf(x, -0.00961812910762848f, 0.0555041086648216f),
-                            -0.240226506959101f),
-                    0.693147180559945f);
-  return 1.0f - ex2(-x);
-}
+// Per-sample local derivatives kept in shared memory between the physics and the chain rule.
+enum {
+  J_KDN,   // kd / n
+  J_DPHI,  // d ln(2^Phi) / dT = Phi'(log2 T) / T           (0 where T is clamped)
+  J_QT,    // -1/2 ia^2 d(alpha^2)/dT                         (0 where T is clamped)
+  J_QV,    // -1/2 ia^2 d(alpha^2)/dv_turb
+  J_DS,    // dS/dT                                          (0 where T is clamped)
+  J_SA,    // d ln X / d h_lo
+  J_SB,    // d ln X / d h_hi
+  J_FR,    // bilinear weights
+  J_FZ,
+  J_CELL,  // node index j0 * nr + i0 (int bits)
+  J_I0,    // radial node index i0 (int bits)
+  J_MT,    // network factor on T (e^{o0}; 1 for grid fields)
+  J_MN,    // network factor on n (e^{o1})
+  J_T,     // T and n after the network factors
+  J_N,
+  kJ
+};
 
-// Chain rule of one sample: given dL/dkd, dL/da, dL/db and dL/dS of sample k of ray R,
-// accumulate dL/d(node values) with FP64 atomics.
-__device__ __forceinline__ void sample_grad(const MarchParams &P, const float *tab, const Ray &R,
-                                            int k, float gkd, float ga, float gb, float gS,
-                                            const rt_grads &G) {
-  float kf = (float)k;
-  float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
-  float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
-  float r2 = fmaf(R.x, R.x, y * y);
-  Cell c = locate(P, z, r2);
-  if (!(c.gas && R.hit && k < P.n_samples)) return;
+// Channel-independent physics of sample k with its local derivatives (written to J[e * 32]).
+// Returns {kd, a, b, S} as sample_physics does for a sample with gas, and zeros (b = 0 marks
+// "no gas") otherwise. The arithmetic of kd, a, b and S is the same as sample_physics'.
+__device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float *tab,
+                                              const Ray &R, int k, float *J) {
+  const float kf = (float)k;
+  const float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
+  const float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
+  const float r2 = fmaf(R.x, R.x, y * y);
+  const Cell c = locate(P, z, r2);
+  if (!(c.gas && R.hit && k < P.n_samples)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   float T = bilerp(P.T, P.nr, c);
   float n = bilerp(P.n, P.nr, c);
-  float vt = bilerp(P.vt, P.nr, c);
+  const float vt = bilerp(P.vt, P.nr, c);
   const float *hl = P.hlo + c.i0;
   const float *hh = P.hhi + c.i0;
   float hlo = lerpf(__ldg(hl), __ldg(hl + 1), c.fr);
   float hhi = lerpf(__ldg(hh), __ldg(hh + 1), c.fr);
-  float X, dX_dhlo = 0.0f, dX_dhhi = 0.0f;
+  float mT = 1.0f, mn = 1.0f;
+  if (P.mod) {
+    const float4 o = __ldg(P.mod + (long long)R.pix * P.n_samples + k);
+    mT = ex2(o.x * 1.4426950408889634f);
+    mn = ex2(o.y * 1.4426950408889634f);
+    T *= mT;
+    n *= mn;
+    hlo = fmaf(P.h_scale, o.z, hlo);
+    hhi = fmaf(P.h_scale, o.w, hhi);
+  }
+  float X, sa = 0.0f, sb = 0.0f;
   if (P.hard_edge) {
     X = (c.zr >= hlo && c.zr <= hhi) ? P.x_co : 0.0f;
   } else {
-    float ea = ex2((hlo - c.zr) * P.edge_k);
-    float eb = ex2((c.zr - hhi) * P.edge_k);
-    float ia_ = rcp(1.0f + ea), ib_ = rcp(1.0f + eb);
-    X = P.x_co * ia_ * ib_;
-    // X = x_co / ((1 + ea)(1 + eb)), ea = 2^{(hlo - z/r) k}, eb = 2^{(z/r - hhi) k}
-    dX_dhlo = -X * (ea * ia_) * P.edge_k * kLn2;
-    dX_dhhi = X * (eb * ib_) * P.edge_k * kLn2;
+    // X = x_co / ((1 + ea)(1 + eb)), ea = 2^{(h_lo - z/r) k}, eb = 2^{(z/r - h_hi) k}
+    const float ea = ex2((hlo - c.zr) * P.edge_k);
+    const float eb = ex2((c.zr - hhi) * P.edge_k);
+    const float pa = 1.0f + ea, pb = 1.0f + eb;
+    const float rr = rcp(pa * pb);
+    X = P.x_co * rr;
+    const float kl = P.edge_k * kLn2;
+    sa = -ea * pb * rr * kl;
+    sb = eb * pa * rr * kl;
   }
-  float vlos = fmaf(R.vfac, kepler_q(fmaf(z, z, r2)), P.vsys);
-  bool clampT = T < 1e-3f;
-  float Tg = fmaxf(T, 1e-3f);
-  float a2 = P.vturb_mach ? Tg * fmaf(P.c_mach, vt * vt, P.c_th) : fmaf(P.c_th, Tg, vt * vt);
-  float ia = rsq(a2);
-  float dphi;
-  float phi = lte_phi(tab, lg2(Tg), &dphi);
-  float iT = rcp(Tg);
-  float eS = ex2(-P.theta_s * iT);
-  float F = ex2(phi);
-  const float cb = 1.2011224087864498f;  // b = cb ia, a = vlos b
-  // kd = kappa X n F ia ds
-  float base = P.kappa_k * F * R.ds;      // kd / (X n ia)
-  float kd = base * X * n * ia;
-  float g_ia = gkd * base * X * n + (gb + ga * vlos) * cb;
-  float g_a2 = g_ia * (-0.5f * ia * ia * ia);
-  float dT = 0.0f, dvt;
+  const float vlos = fmaf(R.vfac, kepler_q(fmaf(z, z, r2)), P.vsys);
+  const bool clampT = T < 1e-3f;
+  const float Tg = fmaxf(T, 1e-3f);
+  float a2, da2T, da2v;
   if (P.vturb_mach) {
-    dT = g_a2 * fmaf(P.c_mach, vt * vt, P.c_th);
-    dvt = g_a2 * Tg * P.c_mach * 2.0f * vt;
+    const float m = fmaf(P.c_mach, vt * vt, P.c_th);
+    a2 = Tg * m;
+    da2T = m;
+    da2v = Tg * P.c_mach * 2.0f * vt;
   } else {
-    dT = g_a2 * P.c_th;
-    dvt = g_a2 * 2.0f * vt;
+    a2 = fmaf(P.c_th, Tg, vt * vt);
+    da2T = P.c_th;
+    da2v = 2.0f * vt;
   }
-  // d 2^Phi(log2 T) / dT = 2^Phi Phi'(t) / T
-  dT += gkd * kd * dphi * iT;
+  const float ia = rsq(a2);
+  float dphi;
+  const float phi = lte_phi(tab, lg2(Tg), &dphi);
+  const float iT = rcp(Tg);
+  const float eS = ex2(-P.theta_s * iT);
+  const float om = rcp(1.0f - eS);
+  const float F = ex2(phi);
+  const float q = -0.5f * ia * ia;
+  J[J_KDN * 32] = P.kappa_k * X * F * ia * R.ds;
+  J[J_DPHI * 32] = clampT ? 0.0f : dphi * iT;
+  J[J_QT * 32] = clampT ? 0.0f : q * da2T;
+  J[J_QV * 32] = q * da2v;
   // S = eS / (1 - eS), eS = 2^{-theta/T}: dS/dT = eS ln2 theta / (T^2 (1 - eS)^2)
-  float om = rcp(1.0f - eS);
-  dT += gS * eS * om * om * kLn2 * P.theta_s * iT * iT;
-  if (clampT) dT = 0.0f;
-  float dn = gkd * base * X * ia;
-  float dX = gkd * base * n * ia;
-  float dhlo = dX * dX_dhlo, dhhi = dX * dX_dhhi;
-  // bilinear scatter
-  int nr = P.nr;
-  int i00 = c.j0 * nr + c.i0;
-  float w00 = (1.0f - c.fr) * (1.0f - c.fz), w01 = c.fr * (1.0f - c.fz);
-  float w10 = (1.0f - c.fr) * c.fz, w11 = c.fr * c.fz;
-  int idx[4] = {i00, i00 + 1, i00 + nr, i00 + nr + 1};
-  float w[4] = {w00, w01, w10, w11};
+  J[J_DS * 32] = clampT ? 0.0f : eS * om * om * kLn2 * P.theta_s * iT * iT;
+  J[J_SA * 32] = sa;
+  J[J_SB * 32] = sb;
+  J[J_FR * 32] = c.fr;
+  J[J_FZ * 32] = c.fz;
+  J[J_CELL * 32] = __int_as_float(c.j0 * P.nr + c.i0);
+  J[J_I0 * 32] = __int_as_float(c.i0);
+  J[J_MT * 32] = mT;
+  J[J_MN * 32] = mn;
+  J[J_T * 32] = T;
+  J[J_N * 32] = n;
+  float4 out;
+  out.x = P.kappa_k * (X * n) * F * ia * R.ds;
+  out.z = ia * 1.2011224087864498f;  // b = sqrt(log2 e) / alpha
+  out.y = vlos * out.z;              // a = v_los b
+  out.w = eS * om;
+  return out;
+}
+
+// Chain rule of one sample from the reduced channel sums (ax, ay, aS; see the file header)
+// and the local derivatives J; node gradients by FP64 atomics, and the gradient with respect
+// to the four network outputs of the sample when dmod is given.
+__device__ __forceinline__ void scatter_grad(const MarchParams &P, const float *J, float kd,
+                                             float ax, float ay, float aS, const rt_grads &G,
+                                             float4 *dmod) {
+  const float gx = -kLn2 * ax;                       // dL/dkd
+  const float GB = 2.0f * kLn2 * kLn2 * kd * ay;     // b dL/db (a = v_los b included)
+  const float gk = fmaf(gx, kd, GB);                 // alpha dL/d(1/alpha) ... times ia
+  const float gT = fmaf(gx * kd, J[J_DPHI * 32], fmaf(gk, J[J_QT * 32], aS * J[J_DS * 32]));
+  const float gv = gk * J[J_QV * 32];
+  const float gn = gx * J[J_KDN * 32];
+  const float gl = gx * kd * J[J_SA * 32];
+  const float gh = gx * kd * J[J_SB * 32];
+  if (dmod)
+    *dmod = make_float4(gT * J[J_T * 32], gn * J[J_N * 32], gl * P.h_scale, gh * P.h_scale);
+  const float dT = gT * J[J_MT * 32], dn = gn * J[J_MN * 32];
+  const float fr = J[J_FR * 32], fz = J[J_FZ * 32];
+  const int i00 = __float_as_int(J[J_CELL * 32]), i0 = __float_as_int(J[J_I0 * 32]);
+  const int nr = P.nr;
+  const int idx[4] = {i00, i00 + 1, i00 + nr, i00 + nr + 1};
+  const float w[4] = {(1.0f - fr) * (1.0f - fz), fr * (1.0f - fz), (1.0f - fr) * fz, fr * fz};
 #pragma unroll
   for (int a = 0; a < 4; a++) {
     atomicAdd(G.dT + idx[a], (double)(dT * w[a]));
     atomicAdd(G.dn + idx[a], (double)(dn * w[a]));
-    atomicAdd(G.dvt + idx[a], (double)(dvt * w[a]));
+    atomicAdd(G.dvt + idx[a], (double)(gv * w[a]));
   }
-  atomicAdd(G.dh_lo + c.i0, (double)(dhlo * (1.0f - c.fr)));
-  atomicAdd(G.dh_lo + c.i0 + 1, (double)(dhlo * c.fr));
-  atomicAdd(G.dh_hi + c.i0, (double)(dhhi * (1.0f - c.fr)));
-  atomicAdd(G.dh_hi + c.i0 + 1, (double)(dhhi * c.fr));
+  atomicAdd(G.dh_lo + i0, (double)(gl * (1.0f - fr)));
+  atomicAdd(G.dh_lo + i0 + 1, (double)(gl * fr));
+  atomicAdd(G.dh_hi + i0, (double)(gh * (1.0f - fr)));
+  atomicAdd(G.dh_hi + i0 + 1, (double)(gh * fr));
+}
+
+// Replicated FP64 gradient accumulators. Thousands of samples land on every node (and all
+// samples of a radius on the same two surface entries), and FP64 atomics on one address are
+// applied one after another; block b therefore accumulates into copy b % k of each array and
+// a final pass sums the copies in FP64. g == nullptr (or h == nullptr) means the block adds
+// straight into the caller's arrays.
+struct GradCopies {
+  double *g;  // kg copies of [dT | dn | dvt], gstride doubles apart
+  double *h;  // kh copies of [dh_lo | dh_hi], hstride doubles apart
+  long long gstride, hstride;
+  int kg, kh;
+};
+
+__device__ __forceinline__ rt_grads block_sink(const MarchParams &P, const rt_grads &G,
+                                               const GradCopies &C) {
+  rt_grads S = G;
+  if (C.g) {
+    double *b = C.g + (long long)(blockIdx.x % C.kg) * C.gstride;
+    const long long m = (long long)P.nr * P.nz;
+    S.dT = b;
+    S.dn = b + m;
+    S.dvt = b + 2 * m;
+  }
+  if (C.h) {
+    double *b = C.h + (long long)(blockIdx.x % C.kh) * C.hstride;
+    S.dh_lo = b;
+    S.dh_hi = b + P.nr;
+  }
+  return S;
+}
+
+// out_{i / n_each}[i % n_each] = sum over the k copies of element i (fixed order, FP64).
+__global__ void sum_copies_kernel(const double *__restrict__ cop, int k, long long stride,
+                                  long long n_each, int nout, double *o0, double *o1,
+                                  double *o2) {
+  const long long n = n_each * nout;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < k; c++) acc += cop[(long long)c * stride + i];
+    const long long w = i / n_each, j = i - w * n_each;
+    double *o = w == 0 ? o0 : (w == 1 ? o1 : o2);
+    o[j] = acc;
+  }
 }
 
 template <int LPR, int CPL, bool UNIF>
-__global__ void __launch_bounds__(kWarpsAdj * 32)
+__global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
     march_adj_kernel(const __grid_constant__ MarchParams P, const float *__restrict__ dLdc,
                      const float *__restrict__ target, float *__restrict__ cube_out,
-                     const rt_grads G, float *__restrict__ scratch, int nseg) {
-  constexpr int R = 32 / LPR;
+                     const rt_grads G, float *__restrict__ scratch, int nseg,
+                     float4 *__restrict__ dmod, const GradCopies GC) {
+  constexpr int WPB = adj_wpb<LPR>();
+  constexpr int R = 32 / LPR;          // rays per warp
   constexpr int NG = 32 / R;           // work units whose setups are computed together
   constexpr int NB = kSeg / LPR;       // batches per segment
   __shared__ __align__(16) float s_tab[kTabSeg * 4];
-  __shared__ float4 s_ph[kWarpsAdj][32];
-  __shared__ Ray s_ray[kWarpsAdj][32];
-  __shared__ float4 s_part[kWarpsAdj][LPR][32];
-  __shared__ float s_tbb[kWarpsAdj][NB + 1][CPL][32];
+  __shared__ float4 s_ph[WPB][32];
+  __shared__ Ray s_ray[WPB][32];
+  // per-sample channel sums of each lane, [sample t][lane ^ (t & 7)] (conflict-free both ways)
+  __shared__ float4 s_part[WPB][LPR][32];
+  __shared__ float s_jac[WPB][kJ][32];
   for (int i = threadIdx.x; i < kTabSeg * 4; i += blockDim.x) s_tab[i] = P.tab[i];
   __syncthreads();
 
@@ -143,17 +256,22 @@ __global__ void __launch_bounds__(kWarpsAdj * 32)
   const int q = lane % LPR, rr = lane / LPR;
   const long long npix = (long long)P.nx * P.ny;
   const long long nunits = (npix + R - 1) / R;
-  const long long W = (long long)gridDim.x * kWarpsAdj;
-  const long long gw = (long long)blockIdx.x * kWarpsAdj + wib;
-  float *ck = scratch + gw * (long long)nseg * CPL * 32;  // this warp's checkpoints
+  const long long W = (long long)gridDim.x * WPB;
+  const long long gw = (long long)blockIdx.x * WPB + wib;
+  float *ck = scratch + gw * adj_warp_floats<LPR, CPL>(nseg);  // this warp's checkpoints
+  float *bs = ck + (long long)nseg * CPL * 32;                  // and batch starts
   float4 *ph = s_ph[wib];
+  float4(*part)[32] = s_part[wib];
+  float *Jl = &s_jac[wib][0][lane];
   float vc[CPL];
 #pragma unroll
   for (int j = 0; j < CPL; j++)
     vc[j] = UNIF ? fmaf((float)(q + LPR * j), P.dv, P.v0) : P.v[min(q + LPR * j, RT_MAX_CH - 1)];
   const float vq = P.v0 + (float)q * P.dv;
   const float dvs = (float)LPR * P.dv;
+  const float S_bg = P.I0 / P.out_scale;  // background in internal intensity units
   double loss = 0.0;
+  const rt_grads Gb = block_sink(P, G, GC);
 
   for (long long u0 = gw; u0 < nunits; u0 += W * NG) {
     {
@@ -190,7 +308,7 @@ __global__ void __launch_bounds__(kWarpsAdj * 32)
         if (!__any_sync(0xffffffffu, mine.x > 0.0f)) continue;
         ph[lane] = mine;
         __syncwarp();
-#pragma unroll
+#pragma unroll 4
         for (int t = 0; t < LPR; t++) {
           const float4 p = ph[rr * LPR + t];
           const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
@@ -212,7 +330,7 @@ __global__ void __launch_bounds__(kWarpsAdj * 32)
       }
 
       // ---------------- loss seed ----------------
-      float gI[CPL], g[CPL];
+      float gI[CPL];
 #pragma unroll
       for (int j = 0; j < CPL; j++) {
         const int ch = q + LPR * j;
@@ -230,97 +348,99 @@ __global__ void __launch_bounds__(kWarpsAdj * 32)
           }
         }
         gI[j] = go * P.out_scale;  // dL/d(internal intensity)
-        g[j] = go * P.I0;          // dL/dT at the far end (background term)
       }
       if (nsamp == 0) continue;
 
       // ---------------- reverse march over segments ----------------
       const int nseg_ray = (P.n_samples + kSeg - 1) / kSeg;
+      float A[CPL];
+#pragma unroll
+      for (int j = 0; j < CPL; j++) A[j] = 0.0f;
+      float Snext = S_bg;
       for (int seg = nseg_ray - 1; seg >= 0; seg--) {
         const int k0 = seg * kSeg;
         const int nb = min(NB, (P.n_samples - k0 + LPR - 1) / LPR);
-        // forward recompute of the batch starts of this segment
+        // batch starts of the segment, summed forward from its checkpoint
         float tbs[CPL];
 #pragma unroll
         for (int j = 0; j < CPL; j++) tbs[j] = ck[(seg * CPL + j) * 32 + lane];
         for (int b = 0; b < nb; b++) {
 #pragma unroll
-          for (int j = 0; j < CPL; j++) s_tbb[wib][b][j][lane] = tbs[j];
+          for (int j = 0; j < CPL; j++) bs[(b * CPL + j) * 32 + lane] = tbs[j];
           const float4 mine = sample_physics(P, s_tab, ray, k0 + b * LPR + q);
           if (!__any_sync(0xffffffffu, mine.x > 0.0f)) continue;
           ph[lane] = mine;
           __syncwarp();
-          float ts[CPL];
-#pragma unroll
-          for (int j = 0; j < CPL; j++) ts[j] = 0.0f;
-#pragma unroll
+#pragma unroll 4
           for (int t = 0; t < LPR; t++) {
             const float4 p = ph[rr * LPR + t];
             const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
 #pragma unroll
             for (int j = 0; j < CPL; j++) {
-              float d = UNIF ? fmaf((float)j, db, dc) : fmaf(vc[j], p.z, -p.y);
-              ts[j] = fmaf(p.x, ex2(d * -d), ts[j]);
+              const float d = UNIF ? fmaf((float)j, db, dc) : fmaf(vc[j], p.z, -p.y);
+              tbs[j] = fmaf(p.x, ex2(d * -d), tbs[j]);
             }
           }
-#pragma unroll
-          for (int j = 0; j < CPL; j++) tbs[j] += ts[j];
           __syncwarp();
         }
 #pragma unroll
-        for (int j = 0; j < CPL; j++) s_tbb[wib][nb][j][lane] = tbs[j];
-        __syncwarp();
+        for (int j = 0; j < CPL; j++) bs[(nb * CPL + j) * 32 + lane] = tbs[j];
 
         // backward over the batches of the segment
         for (int b = nb - 1; b >= 0; b--) {
           const int kb = k0 + b * LPR;
-          const float4 mine = sample_physics(P, s_tab, ray, kb + q);
-          if (!__any_sync(0xffffffffu, mine.x > 0.0f)) continue;  // identity batch
+          const float4 mine = physics_jac(P, s_tab, ray, kb + q, Jl);
+          if (!__any_sync(0xffffffffu, mine.z > 0.0f)) continue;  // no gas in the batch
           ph[lane] = mine;
           float cur[CPL], Tn[CPL];
 #pragma unroll
           for (int j = 0; j < CPL; j++) {
-            cur[j] = s_tbb[wib][b + 1][j][lane];
+            cur[j] = bs[((b + 1) * CPL + j) * 32 + lane];
             Tn[j] = ex2(-cur[j]);
           }
           __syncwarp();
-#pragma unroll
+#pragma unroll 1
           for (int t = LPR - 1; t >= 0; t--) {
             const float4 p = ph[rr * LPR + t];
+            const bool gas = p.z > 0.0f;
+            const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
+            Snext = gas ? p.w : Snext;
             const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
             float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
             for (int j = 0; j < CPL; j++) {
               const float d = UNIF ? fmaf((float)j, db, dc) : fmaf(vc[j], p.z, -p.y);
-              const float gg = ex2(d * -d);
+              const float d2 = d * d;
+              const float gg = ex2(-d2);
+              A[j] = fmaf(cs, Tn[j], A[j]);
+              const float ug = gI[j] * A[j] * gg;
+              acc.x += ug;
+              acc.y = fmaf(ug, d2, acc.y);
               const float dt = p.x * gg;
               cur[j] -= dt;
               const float T0 = ex2(-cur[j]);
-              const float om = one_minus_ex2neg(dt);
-              const float Gf = g[j] - gI[j] * p.w;
-              const float dtl = -kLn2 * Gf * Tn[j];  // dL/d dt
-              acc.w = fmaf(gI[j] * T0, om, acc.w);   // dL/dS
-              g[j] = fmaf(-Gf, om, g[j]);
+              // T_k - T_{k+1} = T_{k+1} (2^dt - 1): series below dt = 0.07 (the difference of
+              // two rounded transmittances would lose the small optical depths)
+              const float dTk = dt < 0.07f ? Tn[j] * dt * fmaf(fmaf(dt, 0.0555041087f, 0.240226507f),
+                                                               dt, 0.693147181f)
+                                           : T0 - Tn[j];
+              acc.w = fmaf(gI[j], dTk, acc.w);
               Tn[j] = T0;
-              acc.x = fmaf(dtl, gg, acc.x);          // dL/dkd
-              const float dd = dtl * dt * (-2.0f * kLn2) * d;  // dL/dd
-              acc.y -= dd;                           // d = v b - a
-              acc.z = fmaf(dd, vc[j], acc.z);
             }
-            s_part[wib][t][lane] = acc;
+            part[t][lane ^ (t & 7)] = acc;
           }
           __syncwarp();
-          // sum the partials of sample kb+q over the lanes of this ray, then the chain rule
           float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-#pragma unroll
+#pragma unroll 8
           for (int i = 0; i < LPR; i++) {
-            const float4 v = s_part[wib][q][rr * LPR + i];
+            const float4 v = part[q][(rr * LPR + i) ^ (q & 7)];
             s.x += v.x;
             s.y += v.y;
-            s.z += v.z;
             s.w += v.w;
           }
-          if (active && mine.x > 0.0f) sample_grad(P, s_tab, ray, kb + q, s.x, s.y, s.z, s.w, G);
+          if (active && mine.z > 0.0f)
+            scatter_grad(P, Jl, mine.x, s.x, s.y, s.w, Gb,
+                         dmod ? dmod + (long long)pix * P.n_samples + kb + q : nullptr);
           __syncwarp();
         }
       }
@@ -330,6 +450,17 @@ __global__ void __launch_bounds__(kWarpsAdj * 32)
     for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
     if (lane == 0 && loss != 0.0) atomicAdd(G.loss, loss);
   }
+}
+
+// Lane layout of the adjoint: CPL channels per lane (8 from 32 channels up), LPR lanes per
+// ray (a power of two, at least 2).
+void adj_layout(int nch, int *lpr, int *cpl) {
+  int c = nch >= 32 ? 8 : 4;
+  int need = (nch + c - 1) / c;
+  int l = 2;
+  while (l < need) l <<= 1;
+  *lpr = l;
+  *cpl = c;
 }
 
 // Chain rule to power-law surface parameters (one block).
@@ -362,99 +493,188 @@ __global__ void surface_powerlaw_kernel(int nr, int r_log, double r_in, double r
   }
 }
 
-// Launch geometry of the adjoint kernel for P: blocks of the persistent grid and the
-// checkpoint scratch they need. cap_blocks <= 0 asks the occupancy calculator.
+// Layouts the adjoint is compiled for (lanes per ray, channels per lane); adj_layout picks one.
+#define RTB_ADJ_LAYOUTS(X) X(2, 4) X(4, 4) X(8, 4) X(4, 8) X(8, 8) X(16, 8) X(32, 8)
+
+// Blocks of the persistent grid of the adjoint kernel for P (cap_blocks <= 0 asks the
+// occupancy calculator).
 template <int LPR, int CPL, bool UNIF>
-static void adj_geometry(const MarchParams &P, long long cap_blocks, long long *blocks,
-                         size_t *bytes) {
+static long long adj_blocks(const MarchParams &P, long long cap_blocks) {
+  constexpr int WPB = adj_wpb<LPR>();
   long long npix = (long long)P.nx * P.ny;
   long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
-  long long need = (units + kWarpsAdj - 1) / kWarpsAdj;
+  long long need = (units + WPB - 1) / WPB;
   long long cap = cap_blocks > 0
                       ? cap_blocks
-                      : resident_blocks((const void *)march_adj_kernel<LPR, CPL, UNIF>,
-                                        kWarpsAdj * 32);
-  *blocks = need < cap ? need : cap;
+                      : resident_blocks((const void *)march_adj_kernel<LPR, CPL, UNIF>, WPB * 32);
+  return need < cap ? need : cap;
+}
+
+// Bytes of per-warp scratch (checkpoints and batch starts) one block needs.
+template <int LPR, int CPL>
+static size_t adj_block_bytes(const MarchParams &P) {
   int nseg = (P.n_samples + kSeg - 1) / kSeg;
-  *bytes = (size_t)(*blocks) * kWarpsAdj * nseg * CPL * 32 * sizeof(float);
+  return (size_t)adj_wpb<LPR>() * adj_warp_floats<LPR, CPL>(nseg) * sizeof(float);
+}
+
+// Scratch of one adjoint launch: the warps' checkpoints, then the gradient copies.
+struct AdjScratch {
+  size_t ck_bytes, g_off, h_off, total;
+  int kg, kh;
+};
+
+constexpr size_t kCopyBudget = (size_t)32 << 20;  // bytes of grid-gradient copies at most
+constexpr int kMaxGridCopies = 32;
+constexpr int kMaxSurfCopies = 128;
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Layout for `blocks` blocks with ck_bytes of checkpoints; gradient copies within `avail`
+// bytes in total (0: no limit).
+static AdjScratch plan_scratch(const MarchParams &P, long long blocks, size_t ck_bytes,
+                               size_t avail) {
+  AdjScratch a;
+  a.ck_bytes = align256(ck_bytes);
+  const size_t gcopy = (size_t)3 * P.nr * P.nz * sizeof(double);
+  const size_t hcopy = (size_t)2 * P.nr * sizeof(double);
+  long long kg = (long long)(kCopyBudget / gcopy);
+  if (kg > kMaxGridCopies) kg = kMaxGridCopies;
+  if (kg > blocks) kg = blocks;
+  long long kh = kMaxSurfCopies < blocks ? kMaxSurfCopies : blocks;
+  if (avail) {
+    size_t left = avail > a.ck_bytes ? avail - a.ck_bytes : 0;
+    while (kh > 0 && (size_t)kh * hcopy > left / 4) kh /= 2;
+    left -= (size_t)kh * hcopy;
+    while (kg > 0 && (size_t)kg * gcopy + 256 > left) kg /= 2;
+  }
+  a.kg = kg > 1 ? (int)kg : 0;  // one copy buys nothing over the caller's arrays
+  a.kh = kh > 1 ? (int)kh : 0;
+  a.g_off = a.ck_bytes;
+  a.h_off = a.g_off + align256((size_t)a.kg * gcopy);
+  a.total = a.h_off + (size_t)a.kh * hcopy;
+  return a;
+}
+
+static int zero_grads(const MarchParams &P, const rt_grads &G, const AdjScratch &a,
+                      char *scratch, cudaStream_t stream) {
+  size_t ng = (size_t)P.nr * P.nz * sizeof(double), nh = (size_t)P.nr * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (a.kg) {
+    e = cudaMemsetAsync(scratch + a.g_off, 0, a.h_off - a.g_off, stream);
+  } else {
+    e = cudaMemsetAsync(G.dT, 0, ng, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(G.dn, 0, ng, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(G.dvt, 0, ng, stream);
+  }
+  if (e == cudaSuccess && a.kh) {
+    e = cudaMemsetAsync(scratch + a.h_off, 0, a.total - a.h_off, stream);
+  } else if (e == cudaSuccess) {
+    e = cudaMemsetAsync(G.dh_lo, 0, nh, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(G.dh_hi, 0, nh, stream);
+  }
+  if (e == cudaSuccess && G.loss) e = cudaMemsetAsync(G.loss, 0, sizeof(double), stream);
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "gradient memset: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
+static GradCopies copies_of(const MarchParams &P, const AdjScratch &a, char *scratch) {
+  GradCopies c;
+  c.g = a.kg ? reinterpret_cast<double *>(scratch + a.g_off) : nullptr;
+  c.h = a.kh ? reinterpret_cast<double *>(scratch + a.h_off) : nullptr;
+  c.gstride = 3LL * P.nr * P.nz;
+  c.hstride = 2LL * P.nr;
+  c.kg = a.kg > 0 ? a.kg : 1;
+  c.kh = a.kh > 0 ? a.kh : 1;
+  return c;
+}
+
+static int sum_copies(const MarchParams &P, const rt_grads &G, const GradCopies &c,
+                      const AdjScratch &a, cudaStream_t stream) {
+  if (a.kg) {
+    long long m = (long long)P.nr * P.nz;
+    long long nb = (3 * m + 255) / 256;
+    sum_copies_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, stream>>>(
+        c.g, a.kg, c.gstride, m, 3, G.dT, G.dn, G.dvt);
+  }
+  if (a.kh) {
+    long long nb = (2LL * P.nr + 255) / 256;
+    sum_copies_kernel<<<(unsigned)nb, 256, 0, stream>>>(c.h, a.kh, c.hstride, P.nr, 2, G.dh_lo,
+                                                         G.dh_hi, nullptr);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "gradient sum: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
+// Zero, march, sum: one adjoint launch on `scratch` (laid out by a).
+template <int LPR, int CPL, bool UNIF>
+static int run_adj(const MarchParams &P, const float *dLdc, const float *target, float *cube_out,
+                   const rt_grads &G, float4 *dmod, long long blocks, const AdjScratch &a,
+                   char *scratch, cudaStream_t stream) {
+  int rc = zero_grads(P, G, a, scratch, stream);
+  if (rc != RT_OK) return rc;
+  const GradCopies c = copies_of(P, a, scratch);
+  const int nseg = (P.n_samples + kSeg - 1) / kSeg;
+  march_adj_kernel<LPR, CPL, UNIF><<<(unsigned)blocks, adj_wpb<LPR>() * 32, 0, stream>>>(
+      P, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "adjoint launch: %s", cudaGetErrorString(e));
+  return sum_copies(P, G, c, a, stream);
 }
 
 template <int LPR, int CPL, bool UNIF>
 static int launch_adj_t(const MarchParams &P, const float *dLdc, const float *target,
-                        float *cube_out, const rt_grads &G, cudaStream_t stream) {
-  auto kern = march_adj_kernel<LPR, CPL, UNIF>;
-  long long blocks;
-  size_t bytes;
-  adj_geometry<LPR, CPL, UNIF>(P, 0, &blocks, &bytes);
-  int nseg = (P.n_samples + kSeg - 1) / kSeg;
-  float *scratch = nullptr;
-  cudaError_t e = cudaMallocAsync((void **)&scratch, bytes, stream);
+                        float *cube_out, const rt_grads &G, float4 *dmod, cudaStream_t stream) {
+  const long long blocks = adj_blocks<LPR, CPL, UNIF>(P, 0);
+  const AdjScratch a = plan_scratch(P, blocks, blocks * adj_block_bytes<LPR, CPL>(P), 0);
+  char *scratch = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&scratch, a.total, stream);
   if (e != cudaSuccess)
-    return set_error(RT_ENOMEM, "adjoint scratch (%zu bytes): %s", bytes, cudaGetErrorString(e));
-  kern<<<(unsigned)blocks, kWarpsAdj * 32, 0, stream>>>(P, dLdc, target, cube_out, G, scratch,
-                                                         nseg);
-  e = cudaGetLastError();
+    return set_error(RT_ENOMEM, "adjoint scratch (%zu bytes): %s", a.total,
+                     cudaGetErrorString(e));
+  int rc = run_adj<LPR, CPL, UNIF>(P, dLdc, target, cube_out, G, dmod, blocks, a, scratch,
+                                   stream);
   cudaFreeAsync(scratch, stream);
-  if (e != cudaSuccess) return set_error(RT_ECUDA, "adjoint launch: %s", cudaGetErrorString(e));
-  return RT_OK;
+  return rc;
 }
 
-template <int LPR, int CPL>
-static int launch_adj_u(const MarchParams &P, const float *dLdc, const float *target,
-                        float *cube_out, const rt_grads &G, cudaStream_t s) {
-  return P.v_uniform ? launch_adj_t<LPR, CPL, true>(P, dLdc, target, cube_out, G, s)
-                     : launch_adj_t<LPR, CPL, false>(P, dLdc, target, cube_out, G, s);
-}
-
-// Zeroes the gradient outputs and launches the fused adjoint.
+// Launches the fused adjoint (the gradient outputs are overwritten, not accumulated into).
+// dmod (optional, [pixel][sample] float4) receives dL/d(network outputs) for samples with gas
+// and is left untouched elsewhere.
 int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target,
-                   float *cube_out, const rt_grads &G, cudaStream_t stream) {
-  size_t ng = (size_t)P.nr * P.nz * sizeof(double), nh = (size_t)P.nr * sizeof(double);
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMemsetAsync(G.dT, 0, ng, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(G.dn, 0, ng, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(G.dvt, 0, ng, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(G.dh_lo, 0, nh, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(G.dh_hi, 0, nh, stream);
-  if (e == cudaSuccess && G.loss) e = cudaMemsetAsync(G.loss, 0, sizeof(double), stream);
-  if (e != cudaSuccess) return set_error(RT_ECUDA, "gradient memset: %s", cudaGetErrorString(e));
+                   float *cube_out, const rt_grads &G, cudaStream_t stream, float4 *dmod) {
   long long npix = (long long)P.nx * P.ny;
-  if (npix == 0 || P.nch == 0) return RT_OK;
+  if (npix == 0 || P.nch == 0) return zero_grads(P, G, plan_scratch(P, 1, 0, 0), nullptr, stream);
   int LPR, CPL;
-  lane_layout(P.nch, &LPR, &CPL);
-  const float *d = dLdc;
-  const float *t = target;
-  if (CPL == 8) return launch_adj_u<32, 8>(P, d, t, cube_out, G, stream);
-  if (LPR == 32) return launch_adj_u<32, 4>(P, d, t, cube_out, G, stream);
-  if (LPR == 16) return launch_adj_u<16, 4>(P, d, t, cube_out, G, stream);
-  if (LPR == 8) return launch_adj_u<8, 4>(P, d, t, cube_out, G, stream);
-  if (LPR == 4) return launch_adj_u<4, 4>(P, d, t, cube_out, G, stream);
-  if (LPR == 2) return launch_adj_u<2, 4>(P, d, t, cube_out, G, stream);
-  // one lane per ray would need 65 batch starts per warp in shared memory: use two
-  return launch_adj_u<2, 4>(P, d, t, cube_out, G, stream);
+  adj_layout(P.nch, &LPR, &CPL);
+  const bool u = P.v_uniform != 0;
+#define X(L, C)                                                                         \
+  if (LPR == L && CPL == C)                                                             \
+    return u ? launch_adj_t<L, C, true>(P, dLdc, target, cube_out, G, dmod, stream)     \
+             : launch_adj_t<L, C, false>(P, dLdc, target, cube_out, G, dmod, stream);
+  RTB_ADJ_LAYOUTS(X)
+#undef X
+  return set_error(RT_EINVAL, "no adjoint layout for %d channels", P.nch);
 }
 
-// Checkpoint scratch rt_render_adjoint allocates for P (cap_blocks > 0 replaces the device
-// occupancy query, for planning without a GPU).
+// Scratch rt_render_adjoint allocates for P (cap_blocks > 0 replaces the device occupancy
+// query, for planning without a GPU).
 size_t adjoint_scratch_bytes(const MarchParams &P, long long cap_blocks) {
   long long npix = (long long)P.nx * P.ny;
   if (npix == 0 || P.nch == 0) return 0;
   int LPR, CPL;
-  lane_layout(P.nch, &LPR, &CPL);
-  long long b;
-  size_t bytes = 0;
+  adj_layout(P.nch, &LPR, &CPL);
+  long long b = 1;
+  size_t per = 0;
   const bool u = P.v_uniform != 0;
-#define RTB_GEOM(L, C)                                               \
-  (u ? adj_geometry<L, C, true>(P, cap_blocks, &b, &bytes)           \
-     : adj_geometry<L, C, false>(P, cap_blocks, &b, &bytes))
-  if (CPL == 8) RTB_GEOM(32, 8);
-  else if (LPR == 32) RTB_GEOM(32, 4);
-  else if (LPR == 16) RTB_GEOM(16, 4);
-  else if (LPR == 8) RTB_GEOM(8, 4);
-  else if (LPR == 4) RTB_GEOM(4, 4);
-  else RTB_GEOM(2, 4);
-#undef RTB_GEOM
-  return bytes;
+#define X(L, C)                                                                            \
+  if (LPR == L && CPL == C) {                                                              \
+    b = u ? adj_blocks<L, C, true>(P, cap_blocks) : adj_blocks<L, C, false>(P, cap_blocks); \
+    per = adj_block_bytes<L, C>(P);                                                        \
+  }
+  RTB_ADJ_LAYOUTS(X)
+#undef X
+  return plan_scratch(P, b, b * per, 0).total;
 }
 
 int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, double c,
@@ -474,11 +694,13 @@ int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, doub
 // Some callers cannot call cudaMalloc (or have it called on their behalf): for example an
 // application whose own memory manager has already reserved the device's memory, or a
 // service that runs under a fixed device-memory budget and forbids allocator traffic once it
-// is running. For them the checkpoint scratch of the adjoint lives in one file-scope device
-// array of fixed size, kFixedScratchBytes, that every GPU loading this library holds until
-// the process exits. The kernel is the same; when the array cannot hold a checkpoint region
-// for every resident block, the persistent grid is made smaller (same result, lower
-// throughput), and a problem that does not fit even one block is rejected.
+// is running. For them the scratch of the adjoint (checkpoints, then as many gradient copies
+// as fit) lives in one file-scope device array of fixed size, kFixedScratchBytes, that every
+// GPU loading this library holds until the process exits. The kernel is the same; when the
+// array cannot hold a checkpoint region for every resident block, the persistent grid is
+// made smaller, and where fewer gradient copies fit (or none: then the blocks add straight
+// into the caller's arrays) the FP64 sums run in another order: same results, lower
+// throughput. A problem whose single block does not fit is rejected.
 // ---------------------------------------------------------------------------------------
 namespace rtb {
 
@@ -511,55 +733,36 @@ template <int LPR, int CPL, bool UNIF>
 static int launch_adj_fixed_t(const MarchParams &P, const float *dLdc, const float *target,
                               float *cube_out, const rt_grads &G, cudaStream_t stream,
                               float *scratch) {
-  auto kern = march_adj_kernel<LPR, CPL, UNIF>;
-  long long npix = (long long)P.nx * P.ny;
-  long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
-  long long need = (units + kWarpsAdj - 1) / kWarpsAdj;
-  long long cap = resident_blocks((const void *)kern, kWarpsAdj * 32);
-  int nseg = (P.n_samples + kSeg - 1) / kSeg;
-  size_t per_block = (size_t)kWarpsAdj * nseg * CPL * 32 * sizeof(float);
-  if (per_block > kFixedScratchBytes)
+  // checkpoints get at most three quarters of the array, gradient copies what is left
+  const size_t ck_room = kFixedScratchBytes / 4 * 3;
+  const size_t per_block = adj_block_bytes<LPR, CPL>(P);
+  if (per_block > ck_room)
     return set_error(RT_EINVAL,
                      "allocation-free adjoint: %d samples per ray need %zu bytes of checkpoint "
-                     "scratch per block, above the fixed %zu-byte array",
-                     P.n_samples, per_block, kFixedScratchBytes);
-  long long fit = (long long)(kFixedScratchBytes / per_block);
-  long long blocks = need < cap ? need : cap;
+                     "scratch per block, above the %zu bytes the fixed array gives them",
+                     P.n_samples, per_block, ck_room);
+  long long blocks = adj_blocks<LPR, CPL, UNIF>(P, 0);
+  const long long fit = (long long)(ck_room / per_block);
   if (blocks > fit) blocks = fit;
-  kern<<<(unsigned)blocks, kWarpsAdj * 32, 0, stream>>>(P, dLdc, target, cube_out, G, scratch,
-                                                         nseg);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return set_error(RT_ECUDA, "adjoint launch: %s", cudaGetErrorString(e));
-  return RT_OK;
-}
-
-template <int LPR, int CPL>
-static int launch_adj_fixed_u(const MarchParams &P, const float *d, const float *t, float *c,
-                              const rt_grads &G, cudaStream_t s, float *scr) {
-  return P.v_uniform ? launch_adj_fixed_t<LPR, CPL, true>(P, d, t, c, G, s, scr)
-                     : launch_adj_fixed_t<LPR, CPL, false>(P, d, t, c, G, s, scr);
+  const AdjScratch a = plan_scratch(P, blocks, blocks * per_block, kFixedScratchBytes);
+  return run_adj<LPR, CPL, UNIF>(P, dLdc, target, cube_out, G, nullptr, blocks, a,
+                                 reinterpret_cast<char *>(scratch), stream);
 }
 
 static int launch_adjoint_fixed(const MarchParams &P, const float *d, const float *t, float *c,
                                 const rt_grads &G, cudaStream_t s, float *scr) {
-  size_t ng = (size_t)P.nr * P.nz * sizeof(double), nh = (size_t)P.nr * sizeof(double);
-  cudaError_t e = cudaMemsetAsync(G.dT, 0, ng, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(G.dn, 0, ng, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(G.dvt, 0, ng, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(G.dh_lo, 0, nh, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(G.dh_hi, 0, nh, s);
-  if (e == cudaSuccess && G.loss) e = cudaMemsetAsync(G.loss, 0, sizeof(double), s);
-  if (e != cudaSuccess) return set_error(RT_ECUDA, "gradient memset: %s", cudaGetErrorString(e));
   long long npix = (long long)P.nx * P.ny;
-  if (npix == 0 || P.nch == 0) return RT_OK;
+  if (npix == 0 || P.nch == 0) return zero_grads(P, G, plan_scratch(P, 1, 0, 0), nullptr, s);
   int LPR, CPL;
-  lane_layout(P.nch, &LPR, &CPL);
-  if (CPL == 8) return launch_adj_fixed_u<32, 8>(P, d, t, c, G, s, scr);
-  if (LPR == 32) return launch_adj_fixed_u<32, 4>(P, d, t, c, G, s, scr);
-  if (LPR == 16) return launch_adj_fixed_u<16, 4>(P, d, t, c, G, s, scr);
-  if (LPR == 8) return launch_adj_fixed_u<8, 4>(P, d, t, c, G, s, scr);
-  if (LPR == 4) return launch_adj_fixed_u<4, 4>(P, d, t, c, G, s, scr);
-  return launch_adj_fixed_u<2, 4>(P, d, t, c, G, s, scr);
+  adj_layout(P.nch, &LPR, &CPL);
+  const bool u = P.v_uniform != 0;
+#define X(L, C)                                                           \
+  if (LPR == L && CPL == C)                                               \
+    return u ? launch_adj_fixed_t<L, C, true>(P, d, t, c, G, s, scr)      \
+             : launch_adj_fixed_t<L, C, false>(P, d, t, c, G, s, scr);
+  RTB_ADJ_LAYOUTS(X)
+#undef X
+  return set_error(RT_EINVAL, "no adjoint layout for %d channels", P.nch);
 }
 
 }  // namespace rtb

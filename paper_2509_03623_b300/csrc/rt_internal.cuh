@@ -270,7 +270,8 @@ int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream);
 int launch_count(const MarchParams &P, unsigned long long *count, cudaStream_t stream);
 void lane_layout(int nch, int *lpr, int *cpl);
 int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target, float *cube_out,
-                   const rt_grads &G, cudaStream_t stream);
+                   const rt_grads &G, cudaStream_t stream, float4 *dmod = nullptr);
+void adj_layout(int nch, int *lpr, int *cpl);
 size_t adjoint_scratch_bytes(const MarchParams &P, long long cap_blocks);
 int check_adjoint_args(const MarchParams &P, const float *dL_dcube, const float *target,
                        const rt_grads *grads);

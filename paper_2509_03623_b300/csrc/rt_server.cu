@@ -77,7 +77,7 @@ struct rt_server {
 
 namespace {
 
-// Device footprint of a request: buffers it touches plus the checkpoint scratch of gradients.
+// Device footprint of a request: buffers it touches plus the adjoint scratch of gradients.
 int footprint(const rt_request &r, bool fake, size_t *bytes) {
   rtb::MarchParams *P = new (std::nothrow) rtb::MarchParams;
   if (!P) return rtb::set_error(RT_ENOMEM, "host allocation failed");

@@ -2,10 +2,11 @@
 and gradients as rt_render_adjoint.
 
 Callers that cannot allocate device memory while running (their own memory manager already
-holds the device, or they run under a fixed memory budget) use this entry point; its
-checkpoint scratch is a fixed array inside the library, shared by every call. The test calls
-it twice in a row through the C ABI, so the second call runs on the array the first call left
-behind, and compares both calls with the allocating entry point. This file is collected last
+holds the device, or they run under a fixed memory budget) use this entry point; its scratch
+(checkpoints and replicated gradient accumulators) is a fixed array inside the library, shared
+by every call.
+The test calls it twice in a row through the C ABI, so the second call runs on the array the
+first call left behind, and compares both calls with the allocating entry point. This file is collected last
 so that a run stopping at the first failure has already run every other test.
 """
 
@@ -30,7 +31,7 @@ def _alloc_outputs(torch, p):
 @pytest.mark.parametrize("mode", ["target", "dL_dcube"])
 def test_noalloc_matches_allocating_adjoint_twice(rt, orc, mode):
     import torch
-    p = synth.config_small(31).replace(n_samples=200)   # 4 checkpoint segments, last partial
+    p = synth.config_small(31).replace(n_samples=200)   # ragged last batch
     dd = rt.DeviceDisk(p)
     tgt = torch.tensor(loss_target(orc, p, 31), dtype=torch.float32, device="cuda")
     if mode == "target":
@@ -51,6 +52,26 @@ def test_noalloc_matches_allocating_adjoint_twice(rt, orc, mode):
         np.testing.assert_allclose(c, rc, rtol=1e-6, atol=1e-7 * np.abs(rc).max())
         if mode == "target":
             assert float(grads["loss"].item()) == pytest.approx(float(ref["loss"].item()), rel=1e-9)
+
+
+def test_noalloc_large_grid_without_room_for_copies(rt):
+    """A 1024x512 grid: one copy of the node gradients (12.6 MB) leaves no room for a second
+    in the fixed array, so the kernel adds straight into the outputs; same gradients up to
+    the order of the FP64 sums."""
+    import torch
+    p = synth.disk(33, nr=1024, nz=512, nx=24, ny=24, nch=16, n_samples=128)
+    dd = rt.DeviceDisk(p)
+    w = np.random.default_rng(2).standard_normal((p.nch, p.ny, p.nx))
+    dl = torch.tensor(w, dtype=torch.float32, device="cuda")
+    _, ref = rt.rt_render_adjoint(p, dd, dL_dcube=dl)
+    grads, cube = _alloc_outputs(torch, p)
+    for t in grads.values():
+        t.fill_(float("nan"))
+    rt.rt_render_adjoint_noalloc(p, dd, cube, grads, dL_dcube=dl)
+    torch.cuda.synchronize()
+    for k in ("T", "n_h2", "vturb", "h_lo", "h_hi"):
+        a, b = grads[k].cpu().numpy(), ref[k].cpu().numpy()
+        np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-12 * np.abs(b).max(), err_msg=k)
 
 
 def test_noalloc_rejects_oversized_problem(rt):
