@@ -2,20 +2,22 @@
 //
 // Mapping: a warp marches R = 32/LPR neighbouring rays at a time (one work unit); the LPR
 // lanes of a ray split its channels (lane q holds channels q, q+LPR, ... in registers, CPL
-// of them). The grid is persistent (one wave) and work units are interleaved over its warps;
-// the double-precision ray setups (chord through the bounding cylinder) of 32 rays are
-// computed at once, one per lane, and kept in shared memory. Samples advance in batches of
-// LPR: in the physics phase lane q evaluates the channel-independent physics of sample kb+q
-// of its ray (fields, CO layer, Keplerian velocity, line width, LTE source and opacity) once
-// and publishes it in shared memory; batches without gas on any ray are skipped (warp vote);
-// in the channel phase every lane walks the batch's samples in order (fully unrolled),
-// evaluating the Doppler-shifted Gaussian profile and advancing optical depth, transmittance
-// and intensity front to back (Eq. rt-int with Eq. optical_depth; the source is constant
-// over each segment).
+// of them, as CPL/2 pairs). The grid is persistent (one wave) and work units are interleaved
+// over its warps; the double-precision ray setups (chord through the bounding cylinder) of 32
+// rays are computed at once, one per lane, and kept in shared memory. Samples advance in
+// batches of LPR: in the physics phase lane q evaluates the channel-independent physics of
+// sample kb+q of its ray (fields, CO layer, Keplerian velocity, line width, LTE source and
+// opacity) once and publishes it in shared memory; batches without gas on any ray are
+// skipped (warp vote); in the channel phase every lane walks the batch's samples in order
+// (fully unrolled), evaluating the Doppler-shifted Gaussian profile and advancing optical
+// depth, transmittance and intensity front to back (Eq. rt-int with Eq. optical_depth; the
+// source is constant over each segment).
 //
-// Per sample-channel evaluation: 7 FP32 operations and 2 MUFU.EX2. The optical depth is
-// summed per batch and folded into a per-channel base at the end of every batch (blocked
-// summation: about 2 N_s / LPR roundings instead of N_s).
+// Per sample-channel evaluation: 6 FP32 operations, issued as 3 packed two-channel
+// instructions (FFMA2/FMUL2/FADD2), and 2 MUFU.EX2, so the MUFU pipe rather than instruction
+// issue bounds the loop. The optical depth is kept negated (so no negation is needed before
+// the exponential) and summed per batch, then folded into a per-channel base at the end of
+// every batch (blocked summation: about 2 N_s / LPR roundings instead of N_s).
 #include <mutex>
 
 #include "rt_internal.cuh"
@@ -24,13 +26,16 @@ namespace rtb {
 
 constexpr int kWarps = 4;  // warps per block
 
-template <int LPR, int CPL, bool UNIF>
+template <int LPR, int CPL, int SPL>
 __global__ void __launch_bounds__(kWarps * 32)
     march_fwd_kernel(const __grid_constant__ MarchParams P, float *__restrict__ cube) {
   constexpr int R = 32 / LPR;  // rays marched together by one warp (one work unit)
   constexpr int G = 32 / R;    // work units whose ray setups are computed together
+  constexpr int H = CPL / 2;   // channel pairs per lane
+  constexpr int NB = SPL * LPR;  // samples per batch (SPL per lane in the physics phase)
   __shared__ __align__(16) float s_tab[kTabSeg * 4];
-  __shared__ float4 s_ph[kWarps][32];
+  // per sample: {-kd, -kd, S, S} and {b, b, -a, -a} (pairs ready for the packed arithmetic)
+  __shared__ float4 s_ph[kWarps][2][32 * SPL];
   __shared__ Ray s_ray[kWarps][32];
   for (int i = threadIdx.x; i < kTabSeg * 4; i += blockDim.x) s_tab[i] = P.tab[i];
   __syncthreads();
@@ -40,15 +45,18 @@ __global__ void __launch_bounds__(kWarps * 32)
   const long long npix = (long long)P.nx * P.ny;
   const long long nunits = (npix + R - 1) / R;
   const long long W = (long long)gridDim.x * kWarps;  // warps in the grid
-  float4 *ph = s_ph[wib];
+  float4 *ph0 = s_ph[wib][0];
+  float4 *ph1 = s_ph[wib][1];
 
-  float vr[UNIF ? 1 : CPL];
-  if (!UNIF) {
+  // velocities of this lane's channel pairs (q + LPR (2m), q + LPR (2m + 1))
+  float2 vp[H];
 #pragma unroll
-    for (int j = 0; j < CPL; j++) vr[j] = P.v[min(q + LPR * j, RT_MAX_CH - 1)];
+  for (int m = 0; m < H; m++) {
+    const int c0 = q + LPR * (2 * m), c1 = c0 + LPR;
+    vp[m] = P.v_uniform ? make_float2(fmaf((float)c0, P.dv, P.v0), fmaf((float)c1, P.dv, P.v0))
+                        : make_float2(P.v[min(c0, RT_MAX_CH - 1)], P.v[min(c1, RT_MAX_CH - 1)]);
   }
-  const float vq = P.v0 + (float)q * P.dv;  // velocity of this lane's first channel
-  const float dvs = (float)LPR * P.dv;      // spacing between this lane's channels
+  const float2 mone = make_float2(-1.0f, -1.0f);
 
   // Work units u = gw, gw + W, gw + 2W, ... (interleaved over the grid for balance); the
   // setups of G units (32 rays) are computed at once, one ray per lane.
@@ -66,46 +74,65 @@ __global__ void __launch_bounds__(kWarps * 32)
       if (u >= nunits) break;
       const long long pix = u * R + rr;
       const Ray ray = s_ray[wib][g * R + rr];
-      float tl[CPL], tb[CPL], Tr[CPL], I[CPL];
+      // negated optical depth: batch part and base; transmittance; intensity
+      float2 nl[H], nb[H], Tr[H], I[H];
 #pragma unroll
-      for (int j = 0; j < CPL; j++) {
-        tl[j] = 0.0f;
-        tb[j] = 0.0f;
-        Tr[j] = 1.0f;
-        I[j] = 0.0f;
+      for (int m = 0; m < H; m++) {
+        nl[m] = make_float2(0.0f, 0.0f);
+        nb[m] = make_float2(0.0f, 0.0f);
+        Tr[m] = make_float2(1.0f, 1.0f);
+        I[m] = make_float2(0.0f, 0.0f);
       }
       const int nsamp = __any_sync(0xffffffffu, ray.hit) ? P.n_samples : 0;
-      for (int kb = 0; kb < nsamp; kb += LPR) {
-        const float4 mine = sample_physics(P, s_tab, ray, kb + q);
-        if (!__any_sync(0xffffffffu, mine.x > 0.0f)) continue;  // no gas in this batch
-        ph[lane] = mine;
+      for (int kb = 0; kb < nsamp; kb += NB) {
+        float4 mine[SPL];
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < SPL; i++) {
+          mine[i] = sample_physics(P, s_tab, ray, kb + i * LPR + q);
+          any = any || mine[i].x > 0.0f;
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;  // no gas in this batch
+#pragma unroll
+        for (int i = 0; i < SPL; i++) {
+          const int o = rr * NB + i * LPR + q;
+          ph0[o] = make_float4(-mine[i].x, -mine[i].x, mine[i].w, mine[i].w);
+          ph1[o] = make_float4(mine[i].z, mine[i].z, -mine[i].y, -mine[i].y);
+        }
         __syncwarp();
         // every sample of the batch in order; samples without gas are exact no-ops
 #pragma unroll
-        for (int t = 0; t < LPR; t++) {
-          const float4 p = ph[rr * LPR + t];  // kd, a, b, S of sample kb+t of this ray
-          const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
+        for (int t = 0; t < NB; t++) {
+          const float4 p0 = ph0[rr * NB + t];  // -kd, -kd, S, S of sample kb+t of this ray
+          const float4 p1 = ph1[rr * NB + t];  // b, b, -a, -a
+          const float2 nkd = make_float2(p0.x, p0.y), S = make_float2(p0.z, p0.w);
+          const float2 b = make_float2(p1.x, p1.y), na = make_float2(p1.z, p1.w);
 #pragma unroll
-          for (int j = 0; j < CPL; j++) {
-            float d = UNIF ? fmaf((float)j, db, dc) : fmaf(vr[j], p.z, -p.y);
-            tl[j] = fmaf(p.x, ex2(d * -d), tl[j]);
-            float Tn = ex2(-tb[j] - tl[j]);
-            I[j] = fmaf(p.w, Tr[j] - Tn, I[j]);
-            Tr[j] = Tn;
+          for (int m = 0; m < H; m++) {
+            const float2 d = __ffma2_rn(vp[m], b, na);  // (v_c - v_los) / alpha (scaled)
+            const float2 d2 = __fmul2_rn(d, d);
+            const float2 g = make_float2(ex2(-d2.x), ex2(-d2.y));
+            nl[m] = __ffma2_rn(nkd, g, nl[m]);
+            const float2 nt = __fadd2_rn(nb[m], nl[m]);
+            const float2 Tn = make_float2(ex2(nt.x), ex2(nt.y));
+            const float2 df = __ffma2_rn(Tn, mone, Tr[m]);  // T_k - T_{k+1}
+            I[m] = __ffma2_rn(S, df, I[m]);
+            Tr[m] = Tn;
           }
         }
 #pragma unroll
-        for (int j = 0; j < CPL; j++) {
-          tb[j] += tl[j];
-          tl[j] = 0.0f;
+        for (int m = 0; m < H; m++) {
+          nb[m] = __fadd2_rn(nb[m], nl[m]);
+          nl[m] = make_float2(0.0f, 0.0f);
         }
         __syncwarp();
       }
       if (pix < npix) {
 #pragma unroll
-        for (int j = 0; j < CPL; j++) {
-          int ch = q + LPR * j;
-          if (ch < P.nch) cube[(long long)ch * npix + pix] = fmaf(I[j], P.out_scale, P.I0 * Tr[j]);
+        for (int m = 0; m < H; m++) {
+          const int c0 = q + LPR * (2 * m), c1 = c0 + LPR;
+          if (c0 < P.nch) cube[(long long)c0 * npix + pix] = fmaf(I[m].x, P.out_scale, P.I0 * Tr[m].x);
+          if (c1 < P.nch) cube[(long long)c1 * npix + pix] = fmaf(I[m].y, P.out_scale, P.I0 * Tr[m].y);
         }
       }
     }
@@ -141,9 +168,9 @@ int resident_blocks(const void *kernel, int threads) {
   return nb * nsm;
 }
 
-template <int LPR, int CPL, bool UNIF>
+template <int LPR, int CPL>
 static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
-  auto kern = march_fwd_kernel<LPR, CPL, UNIF>;
+  auto kern = march_fwd_kernel<LPR, CPL, 1>;
   long long npix = (long long)P.nx * P.ny;
   long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
   long long need = (units + kWarps - 1) / kWarps;
@@ -152,17 +179,9 @@ static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
   kern<<<(unsigned)blocks, kWarps * 32, 0, stream>>>(P, cube);
 }
 
-template <int LPR, int CPL>
-static void launch_u(const MarchParams &P, float *cube, cudaStream_t stream) {
-  if (P.v_uniform)
-    launch_t<LPR, CPL, true>(P, cube, stream);
-  else
-    launch_t<LPR, CPL, false>(P, cube, stream);
-}
-
-// Channels per lane (4, or 8 above 128 channels) and lanes per ray (power of two).
+// Channels per lane (4, or 8 above 64 channels) and lanes per ray (power of two).
 void lane_layout(int nch, int *lpr, int *cpl) {
-  int c = nch > 128 ? 8 : 4;
+  int c = nch > 64 ? 8 : 4;
   int need = (nch + c - 1) / c, l = 1;
   while (l < need) l *= 2;
   *lpr = l;
@@ -174,13 +193,16 @@ int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream) {
   if (npix == 0 || P.nch == 0) return RT_OK;
   int LPR, CPL;
   lane_layout(P.nch, &LPR, &CPL);
-  if (CPL == 8) launch_u<32, 8>(P, cube, stream);
-  else if (LPR == 32) launch_u<32, 4>(P, cube, stream);
-  else if (LPR == 16) launch_u<16, 4>(P, cube, stream);
-  else if (LPR == 8) launch_u<8, 4>(P, cube, stream);
-  else if (LPR == 4) launch_u<4, 4>(P, cube, stream);
-  else if (LPR == 2) launch_u<2, 4>(P, cube, stream);
-  else launch_u<1, 4>(P, cube, stream);
+  if (CPL == 8) {
+    if (LPR == 32) launch_t<32, 8>(P, cube, stream);
+    else launch_t<16, 8>(P, cube, stream);
+  } else {
+    if (LPR == 16) launch_t<16, 4>(P, cube, stream);
+    else if (LPR == 8) launch_t<8, 4>(P, cube, stream);
+    else if (LPR == 4) launch_t<4, 4>(P, cube, stream);
+    else if (LPR == 2) launch_t<2, 4>(P, cube, stream);
+    else launch_t<1, 4>(P, cube, stream);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "forward launch: %s", cudaGetErrorString(e));
   return RT_OK;
