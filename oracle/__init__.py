@@ -79,6 +79,8 @@ def _load():
             lib.orc_mlp_eval.argtypes = [C.POINTER(_MLP), dp, C.c_int, dp]
             lib.orc_render_mlp.argtypes = [pp, C.POINTER(_MLP), C.POINTER(C.c_longlong),
                                            C.c_int, dp, C.c_int]
+            lib.orc_render_mlp_adjoint.argtypes = [pp, C.POINTER(_MLP), dp, dp, dp, dp, dp, dp,
+                                                   dp, dp, dp, C.c_int]
             _lib = lib
     return _lib
 
@@ -243,3 +245,31 @@ def render_mlp(p, w, pix=None, nthreads: int = 0) -> np.ndarray:
     if rc:
         raise ValueError("oracle: invalid problem or network")
     return out
+
+
+def render_mlp_adjoint(p, w, dL_dcube: np.ndarray, nthreads: int = 0):
+    """(cube, grads): grads = dict(T, n_h2, vturb [nz][nr], h_lo, h_hi [nr] w.r.t. the grid
+    fields under the network modulation, W = [dL/dW_l], b = [dL/db_l])."""
+    lib = _load()
+    pk = _Packed(p)
+    pm = _PackedMLP(w)
+    g = np.ascontiguousarray(np.asarray(dL_dcube, dtype=np.float64))
+    cube = np.zeros((pk.nch, int(p.ny), int(p.nx)), dtype=np.float64)
+    shp = (int(p.nz), int(p.nr))
+    dT, dn, dvt = np.zeros(shp), np.zeros(shp), np.zeros(shp)
+    dlo, dhi = np.zeros(int(p.nr)), np.zeros(int(p.nr))
+    shapes = [np.asarray(x).shape for x in w.W]
+    dW = np.zeros(sum(a * b for a, b in shapes))
+    db = np.zeros(sum(a for a, _ in shapes))
+    rc = lib.orc_render_mlp_adjoint(C.byref(pk.s), C.byref(pm.m), _dptr(g), _dptr(cube),
+                                    _dptr(dT), _dptr(dn), _dptr(dvt), _dptr(dlo), _dptr(dhi),
+                                    _dptr(dW), _dptr(db), _threads(nthreads))
+    if rc:
+        raise ValueError("oracle: invalid problem or network")
+    Ws, bs, ow, ob = [], [], 0, 0
+    for a, b in shapes:
+        Ws.append(dW[ow:ow + a * b].reshape(a, b))
+        bs.append(db[ob:ob + a])
+        ow += a * b
+        ob += a
+    return cube, dict(T=dT, n_h2=dn, vturb=dvt, h_lo=dlo, h_hi=dhi, W=Ws, b=bs)

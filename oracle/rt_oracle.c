@@ -164,6 +164,9 @@ typedef struct {
   double nco, nu_, nl_;       /* n_CO, n_u, n_l */
   double D;                   /* n_l B_lu - n_u B_ul */
   double S;                   /* j/beta */
+  /* neural field (when a network is given): inputs, outputs and the factors exp(o0), exp(o1)
+     applied to T and n */
+  double xin[2], o[4], mT, mn;
 } pt;
 
 static double bilerp(const double *F, int nr, int i0, int j0, double fr, double fz) {
@@ -216,12 +219,19 @@ static void eval_point(const orc_problem *p, const orc_mlp *m, const double P[3]
     /* Neural field: outputs modulate the grid fields (log T, log n residuals and surface
        offsets). Inputs are the normalised grid coordinates. */
     double xin[2] = {u / (p->nr - 1), zr / p->zr_max};
-    double o[8];
+    double o[64];
     mlp_forward(m, xin, o);
-    st->T *= exp(o[0]);
-    st->n *= exp(o[1]);
+    st->xin[0] = xin[0];
+    st->xin[1] = xin[1];
+    for (int a = 0; a < 4; a++) st->o[a] = o[a];
+    st->mT = exp(o[0]);
+    st->mn = exp(o[1]);
+    st->T *= st->mT;
+    st->n *= st->mn;
     st->hlo += m->h_scale * o[2];
     st->hhi += m->h_scale * o[3];
+  } else {
+    st->mT = st->mn = 1.0;
   }
   /* CO layer between the two surfaces (stand-in for the freeze-out / photodissociation
      gates of Eq. co_layer): logistic edges of width edge_w in z/r, or hard steps. */
@@ -407,10 +417,14 @@ int orc_render_pixels(const orc_problem *p, const long long *pix, int npix, doub
 
 typedef struct {
   double *gT, *gn, *gvt, *ghlo, *ghhi;
+  double *gW, *gb; /* network parameters, flat in layer order (NULL without a network) */
 } grads;
 
-static void adjoint_pixel(const orc_problem *p, int ix, int iy, const double *gout,
-                          double *I, grads *g) {
+static void mlp_backward(const orc_mlp *m, const double xin[2], const double *gout,
+                         double *gW, double *gb);
+
+static void adjoint_pixel(const orc_problem *p, const orc_mlp *m, int ix, int iy,
+                          const double *gout, double *I, grads *g) {
   double P0[3], om[3], s0, s1;
   ray_setup(p, ix, iy, P0, om);
   double conv = unit_conv(p);
@@ -432,7 +446,7 @@ static void adjoint_pixel(const orc_problem *p, int ix, int iy, const double *go
   for (int k = 0; k < N; k++) {
     double s = s0 + (k + 0.5) * ds;
     double P[3] = {P0[0] + s * om[0], P0[1] + s * om[1], P0[2] + s * om[2]};
-    eval_point(p, NULL, P, om, &st[k]);
+    eval_point(p, m, P, om, &st[k]);
     for (int c = 0; c < C; c++) {
       double tr = Tr[k * C + c];
       phi[k * C + c] = 0.0;
@@ -515,6 +529,18 @@ static void adjoint_pixel(const orc_problem *p, int ix, int iy, const double *go
       ghlo = gX * p->x_co * q->sb * q->sa * (1.0 - q->sa) * (-1.0 / p->edge_w);
       ghhi = gX * p->x_co * q->sa * q->sb * (1.0 - q->sb) * (1.0 / p->edge_w);
     }
+    /* Neural field: T = T_grid exp(o0), n = n_grid exp(o1), h = h_grid + h_scale o2,3; the
+       gradients above are with respect to the modulated values. */
+    if (m) {
+      double go[64] = {0};
+      go[0] = gT * q->T;
+      go[1] = gn * q->n;
+      go[2] = ghlo * m->h_scale;
+      go[3] = ghhi * m->h_scale;
+      mlp_backward(m, q->xin, go, g->gW, g->gb);
+    }
+    gT *= q->mT;
+    gn *= q->mn;
     /* bilinear scatter to the nodes */
     int nr = p->nr, i0 = q->i0, j0 = q->j0;
     double fr = q->fr, fz = q->fz;
@@ -540,17 +566,37 @@ static void adjoint_pixel(const orc_problem *p, int ix, int iy, const double *go
   free(Ic);
 }
 
-int orc_render_adjoint(const orc_problem *p, const double *dL_dcube, double *cube,
-                       double *dT, double *dn, double *dvt, double *dh_lo, double *dh_hi,
-                       int nthreads) {
+static int mlp_check(const orc_mlp *m);
+
+static long long mlp_nw(const orc_mlp *m) {
+  long long n = 0;
+  for (int l = 0; l < m->n_layers; l++) n += (long long)m->dims[l + 1] * m->dims[l];
+  return n;
+}
+
+static long long mlp_nb(const orc_mlp *m) {
+  long long n = 0;
+  for (int l = 0; l < m->n_layers; l++) n += m->dims[l + 1];
+  return n;
+}
+
+static int render_adjoint_impl(const orc_problem *p, const orc_mlp *m, const double *dL_dcube,
+                               double *cube, double *dT, double *dn, double *dvt, double *dh_lo,
+                               double *dh_hi, double *dW, double *db, int nthreads) {
   if (check(p) || !dL_dcube) return -1;
+  if (m && (mlp_check(m) || m->dims[m->n_layers] < 4 || m->dims[m->n_layers] > 64)) return -1;
   int G = p->nr * p->nz;
   long long npix = (long long)p->nx * p->ny;
+  long long nw = m ? mlp_nw(m) : 0, nb = m ? mlp_nb(m) : 0;
   memset(dT, 0, sizeof(double) * G);
   memset(dn, 0, sizeof(double) * G);
   memset(dvt, 0, sizeof(double) * G);
   memset(dh_lo, 0, sizeof(double) * p->nr);
   memset(dh_hi, 0, sizeof(double) * p->nr);
+  if (m) {
+    memset(dW, 0, sizeof(double) * nw);
+    memset(db, 0, sizeof(double) * nb);
+  }
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel
@@ -562,6 +608,8 @@ int orc_render_adjoint(const orc_problem *p, const double *dL_dcube, double *cub
     g.gvt = (double *)calloc(G, sizeof(double));
     g.ghlo = (double *)calloc(p->nr, sizeof(double));
     g.ghhi = (double *)calloc(p->nr, sizeof(double));
+    g.gW = m ? (double *)calloc(nw, sizeof(double)) : NULL;
+    g.gb = m ? (double *)calloc(nb, sizeof(double)) : NULL;
     double *gout = (double *)malloc(sizeof(double) * (p->nch > 0 ? p->nch : 1));
     double *I = (double *)malloc(sizeof(double) * (p->nch > 0 ? p->nch : 1));
 #ifdef _OPENMP
@@ -571,7 +619,7 @@ int orc_render_adjoint(const orc_problem *p, const double *dL_dcube, double *cub
       for (int ix = 0; ix < p->nx; ix++) {
         long long pix = (long long)iy * p->nx + ix;
         for (int c = 0; c < p->nch; c++) gout[c] = dL_dcube[c * npix + pix];
-        adjoint_pixel(p, ix, iy, gout, I, &g);
+        adjoint_pixel(p, m, ix, iy, gout, I, &g);
         if (cube)
           for (int c = 0; c < p->nch; c++) cube[c * npix + pix] = I[c];
       }
@@ -589,17 +637,36 @@ int orc_render_adjoint(const orc_problem *p, const double *dL_dcube, double *cub
         dh_lo[a] += g.ghlo[a];
         dh_hi[a] += g.ghhi[a];
       }
+      for (long long a = 0; a < nw; a++) dW[a] += g.gW[a];
+      for (long long a = 0; a < nb; a++) db[a] += g.gb[a];
     }
     free(g.gT);
     free(g.gn);
     free(g.gvt);
     free(g.ghlo);
     free(g.ghhi);
+    free(g.gW);
+    free(g.gb);
     free(gout);
     free(I);
   }
   (void)nthreads;
   return 0;
+}
+
+int orc_render_adjoint(const orc_problem *p, const double *dL_dcube, double *cube,
+                       double *dT, double *dn, double *dvt, double *dh_lo, double *dh_hi,
+                       int nthreads) {
+  return render_adjoint_impl(p, NULL, dL_dcube, cube, dT, dn, dvt, dh_lo, dh_hi, NULL, NULL,
+                             nthreads);
+}
+
+int orc_render_mlp_adjoint(const orc_problem *p, const orc_mlp *m, const double *dL_dcube,
+                           double *cube, double *dT, double *dn, double *dvt, double *dh_lo,
+                           double *dh_hi, double *dW, double *db, int nthreads) {
+  if (!m || !dW || !db) return -1;
+  return render_adjoint_impl(p, m, dL_dcube, cube, dT, dn, dvt, dh_lo, dh_hi, dW, db,
+                             nthreads);
 }
 
 /* ---------------------------------------------------------------------------------------- */
@@ -629,6 +696,71 @@ static void mlp_forward(const orc_mlp *m, const double xin[2], double *out) {
     h2 = t;
   }
   for (int o = 0; o < m->dims[m->n_layers]; o++) out[o] = h[o];
+}
+
+/* Reverse mode of mlp_forward at input xin for output gradient gout: accumulates
+   dL/dW (flat, layer after layer, each [dims[l+1]][dims[l]]) and dL/db. SiLU'(z) =
+   s (1 + z (1 - s)) with s the logistic function of z. */
+static void mlp_backward(const orc_mlp *m, const double xin[2], const double *gout,
+                         double *gW, double *gb) {
+  int L = m->n_layers;
+  double *act = (double *)malloc(sizeof(double) * (L + 1) * ORC_MLP_MAXW); /* a_0 .. a_L */
+  double *pre = (double *)malloc(sizeof(double) * (L + 1) * ORC_MLP_MAXW); /* z_1 .. z_L */
+  double *d = (double *)malloc(sizeof(double) * ORC_MLP_MAXW);
+  double *d2 = (double *)malloc(sizeof(double) * ORC_MLP_MAXW);
+  for (int f = 0; f < m->n_freq; f++) {
+    double a = 2.0 * M_PI * (m->B[2 * f] * xin[0] + m->B[2 * f + 1] * xin[1]);
+    act[f] = sin(a);
+    act[m->n_freq + f] = cos(a);
+  }
+  for (int l = 0; l < L; l++) {
+    int din = m->dims[l], dout = m->dims[l + 1];
+    const double *a = act + (long long)l * ORC_MLP_MAXW;
+    double *z = pre + (long long)(l + 1) * ORC_MLP_MAXW;
+    double *an = act + (long long)(l + 1) * ORC_MLP_MAXW;
+    for (int o = 0; o < dout; o++) {
+      double acc = m->b[l][o];
+      for (int i = 0; i < din; i++) acc += m->W[l][(long long)o * din + i] * a[i];
+      z[o] = acc;
+      an[o] = (l < L - 1) ? acc / (1.0 + exp(-acc)) : acc;
+    }
+  }
+  /* offsets of each layer in the flat gradient arrays */
+  long long offW = 0, offb = 0;
+  for (int l = 0; l < L - 1; l++) {
+    offW += (long long)m->dims[l + 1] * m->dims[l];
+    offb += m->dims[l + 1];
+  }
+  for (int o = 0; o < m->dims[L]; o++) d[o] = gout[o]; /* dL/da_L (identity output layer) */
+  for (int l = L - 1; l >= 0; l--) {
+    int din = m->dims[l], dout = m->dims[l + 1];
+    const double *a = act + (long long)l * ORC_MLP_MAXW;
+    const double *z = pre + (long long)(l + 1) * ORC_MLP_MAXW;
+    /* dL/dz_{l+1} */
+    if (l < L - 1)
+      for (int o = 0; o < dout; o++) {
+        double sg = 1.0 / (1.0 + exp(-z[o]));
+        d[o] *= sg * (1.0 + z[o] * (1.0 - sg));
+      }
+    for (int o = 0; o < dout; o++) {
+      gb[offb + o] += d[o];
+      for (int i = 0; i < din; i++) gW[offW + (long long)o * din + i] += d[o] * a[i];
+    }
+    if (l > 0) {
+      for (int i = 0; i < din; i++) {
+        double acc = 0.0;
+        for (int o = 0; o < dout; o++) acc += m->W[l][(long long)o * din + i] * d[o];
+        d2[i] = acc;
+      }
+      for (int i = 0; i < din; i++) d[i] = d2[i];
+      offW -= (long long)m->dims[l] * m->dims[l - 1];
+      offb -= m->dims[l];
+    }
+  }
+  free(act);
+  free(pre);
+  free(d);
+  free(d2);
 }
 
 static int mlp_check(const orc_mlp *m) {

@@ -99,6 +99,14 @@ int orc_mlp_eval(const orc_mlp *m, const double *x, int npts, double *out);
 int orc_render_mlp(const orc_problem *p, const orc_mlp *m, const long long *pix, int npix,
                    double *out, int nthreads);
 
+/* Reverse mode of orc_render_mlp for the full cube: as orc_render_adjoint (node gradients are
+   with respect to the grid fields before the network modulation), plus dL/dW and dL/db of the
+   network, flat in layer order (layer l: [dims[l+1]][dims[l]] and [dims[l+1]]). Every
+   gradient array is overwritten. The Fourier directions B are not differentiated. */
+int orc_render_mlp_adjoint(const orc_problem *p, const orc_mlp *m, const double *dL_dcube,
+                           double *cube, double *dT, double *dn, double *dvt, double *dh_lo,
+                           double *dh_hi, double *dW, double *db, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif
