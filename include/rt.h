@@ -265,6 +265,45 @@ int rt_render_modulated(const rt_grid *grid, const rt_fields *fields, const rt_g
                         const rt_view *view, const rt_line *line, const float *mod,
                         double h_scale, float *cube, void *stream);
 
+/* Gradients of a scalar loss with respect to the network parameters (DEVICE float64, same
+ * shapes as rt_mlp.W and rt_mlp.b; overwritten by the calls below). The Fourier directions B
+ * are fixed features and get no gradient. */
+typedef struct {
+  double *dW[5];
+  double *db[5];
+} rt_mlp_grads;
+
+/*
+ * rt_mlp_backward -- reverse mode of rt_mlp_eval: given inputs xy [n][2] and dL/d(outputs)
+ * dout [n][4] (both DEVICE float32), writes dL/dW and dL/db summed over the n inputs.
+ * Runs on the tensor cores: per tile of 128 inputs the forward pass is recomputed, then
+ * weight gradients delta^T a (accumulated in tensor memory across all tiles of a CTA), bias
+ * gradients and the delta of the layer below, with operands in the 16-bit format of
+ * mlp->precision and FP32 accumulation; each CTA adds its sums to the FP64 outputs. The
+ * per-input gradients are scaled by a power of two (from their largest magnitude) before
+ * they are rounded to 16 bits, and the results unscaled. Scratch (pre-activations of the
+ * tile in flight, 128 KiB per SM) is allocated and freed on `stream`. Returns RT_OK,
+ * RT_EINVAL, RT_ENOMEM or RT_ECUDA.
+ */
+int rt_mlp_backward(const rt_mlp *mlp, const float *xy, const float *dout, long long n,
+                    const rt_mlp_grads *grads, void *stream);
+
+/*
+ * rt_render_mlp_adjoint -- rt_render_adjoint for the neural-field render of rt_render_mlp
+ * (the paper trains the network by differentiating through the renderer): seeds, cube_out and
+ * the grid gradients are as in rt_render_adjoint, the grid gradients being taken with respect
+ * to the grid fields before the network's modulation. In addition mlp_grads receives dL/dW
+ * and dL/db of the network. Steps: the network forward at every sample (as rt_render_mlp),
+ * the fused march adjoint with the modulation, which also writes dL/d(outputs) per sample,
+ * then rt_mlp_backward over those samples. Device buffers of 32 n_pix n_samples bytes plus
+ * the scratch of both steps are allocated and freed on `stream`. Returns RT_OK, RT_EINVAL,
+ * RT_ENOMEM or RT_ECUDA.
+ */
+int rt_render_mlp_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                          const rt_view *view, const rt_line *line, const rt_mlp *mlp,
+                          const float *dL_dcube, const float *target, float *cube_out,
+                          const rt_grads *grads, const rt_mlp_grads *mlp_grads, void *stream);
+
 /* rt_mlp_status -- synchronous: 1 in *timed_out if a tensor-core MMA wait ever expired in this
    process (the kernel then stops early and its outputs are incomplete), else 0. */
 int rt_mlp_status(int *timed_out);

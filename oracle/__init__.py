@@ -77,6 +77,7 @@ def _load():
             lib.orc_partition.restype = C.c_double
             lib.orc_render_adjoint.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
             lib.orc_mlp_eval.argtypes = [C.POINTER(_MLP), dp, C.c_int, dp]
+            lib.orc_mlp_grad.argtypes = [C.POINTER(_MLP), dp, dp, C.c_int, dp, dp]
             lib.orc_render_mlp.argtypes = [pp, C.POINTER(_MLP), C.POINTER(C.c_longlong),
                                            C.c_int, dp, C.c_int]
             lib.orc_render_mlp_adjoint.argtypes = [pp, C.POINTER(_MLP), dp, dp, dp, dp, dp, dp,
@@ -273,3 +274,25 @@ def render_mlp_adjoint(p, w, dL_dcube: np.ndarray, nthreads: int = 0):
         ow += a * b
         ob += a
     return cube, dict(T=dT, n_h2=dn, vturb=dvt, h_lo=dlo, h_hi=dhi, W=Ws, b=bs)
+
+
+def mlp_grad(w, x: np.ndarray, gout: np.ndarray):
+    """(dW list, db list) of sum_i gout[i] . net(x[i]) with respect to the weights."""
+    lib = _load()
+    pm = _PackedMLP(w)
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 2))
+    gout = np.ascontiguousarray(np.asarray(gout, dtype=np.float64).reshape(x.shape[0], -1))
+    shapes = [np.asarray(a).shape for a in w.W]
+    dW = np.zeros(sum(a * b for a, b in shapes))
+    db = np.zeros(sum(a for a, _ in shapes))
+    rc = lib.orc_mlp_grad(C.byref(pm.m), _dptr(x), _dptr(gout), int(x.shape[0]), _dptr(dW),
+                          _dptr(db))
+    if rc:
+        raise ValueError("oracle: invalid network")
+    Ws, bs, ow, ob = [], [], 0, 0
+    for a, b in shapes:
+        Ws.append(dW[ow:ow + a * b].reshape(a, b))
+        bs.append(db[ob:ob + a])
+        ow += a * b
+        ob += a
+    return Ws, bs

@@ -782,6 +782,16 @@ int orc_mlp_eval(const orc_mlp *m, const double *x, int npts, double *out) {
   return 0;
 }
 
+int orc_mlp_grad(const orc_mlp *m, const double *x, const double *gout, int npts, double *dW,
+                 double *db) {
+  if (mlp_check(m) || m->dims[m->n_layers] > 64) return -1;
+  int no = m->dims[m->n_layers];
+  memset(dW, 0, sizeof(double) * mlp_nw(m));
+  memset(db, 0, sizeof(double) * mlp_nb(m));
+  for (int i = 0; i < npts; i++) mlp_backward(m, x + 2 * i, gout + (long long)i * no, dW, db);
+  return 0;
+}
+
 int orc_render_mlp(const orc_problem *p, const orc_mlp *m, const long long *pix, int npix,
                    double *out, int nthreads) {
   if (check(p) || mlp_check(m) || m->dims[m->n_layers] < 4) return -1;

@@ -92,6 +92,12 @@ typedef struct {
 /* Network outputs for npts inputs x[i] = (rhat, zhat): out [npts][dims[n_layers]]. */
 int orc_mlp_eval(const orc_mlp *m, const double *x, int npts, double *out);
 
+/* Reverse mode of orc_mlp_eval: dL/dW and dL/db (flat, layer after layer as in
+   orc_render_mlp_adjoint; overwritten) summed over npts inputs x with output gradients
+   gout [npts][dims[n_layers]]. */
+int orc_mlp_grad(const orc_mlp *m, const double *x, const double *gout, int npts, double *dW,
+                 double *db);
+
 /* Cube rendered with the neural field: at every sample the grid values are modulated by the
    network outputs o: T <- T exp(o0), n <- n exp(o1), h_lo <- h_lo + h_scale o2,
    h_hi <- h_hi + h_scale o3. pix/npix select pixels as in orc_render_pixels (pix=NULL: all,

@@ -68,6 +68,10 @@ class rt_mlp(C.Structure):
 RT_MLP_F16, RT_MLP_BF16 = 0, 1
 
 
+class rt_mlp_grads(C.Structure):
+    _fields_ = [("dW", C.c_void_p * 5), ("db", C.c_void_p * 5)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -101,6 +105,13 @@ def lib():
             L.rt_mlp_eval.restype = C.c_int
             L.rt_render_mlp.argtypes = base + [P(rt_mlp), C.c_void_p, C.c_void_p]
             L.rt_render_mlp.restype = C.c_int
+            L.rt_mlp_backward.argtypes = [P(rt_mlp), C.c_void_p, C.c_void_p, C.c_longlong,
+                                          P(rt_mlp_grads), C.c_void_p]
+            L.rt_mlp_backward.restype = C.c_int
+            L.rt_render_mlp_adjoint.argtypes = base + [P(rt_mlp), C.c_void_p, C.c_void_p,
+                                                       C.c_void_p, P(rt_grads),
+                                                       P(rt_mlp_grads), C.c_void_p]
+            L.rt_render_mlp_adjoint.restype = C.c_int
             L.rt_sample_coords.argtypes = base + [C.c_void_p, C.c_void_p]
             L.rt_sample_coords.restype = C.c_int
             L.rt_render_modulated.argtypes = base + [C.c_void_p, C.c_double, C.c_void_p,
@@ -318,6 +329,61 @@ def rt_render_mlp(problem, fields, net, out=None, stream=None):
     check(lib().rt_render_mlp(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
                               C.byref(m), _ptr(out), stream_handle(stream)))
     return out
+
+
+def _mlp_grad_buffers(net):
+    """float64 CUDA tensors shaped like the network's weights and biases, and their rt_mlp_grads."""
+    import torch
+    dW = [torch.empty(tuple(w.shape), dtype=torch.float64, device=w.device) for w in net.W]
+    db = [torch.empty(tuple(b.shape), dtype=torch.float64, device=b.device) for b in net.b]
+    g = rt_mlp_grads()
+    for i in range(5):
+        g.dW[i] = dW[i].data_ptr() if i < len(dW) else None
+        g.db[i] = db[i].data_ptr() if i < len(db) else None
+    return dW, db, g
+
+
+def rt_mlp_backward(net, xy, dout, stream=None):
+    """Reverse mode of rt_mlp_eval on the tensor cores: (dW, db) summed over the inputs xy
+    [n][2] for dL/d(outputs) dout [n][4] (float64 CUDA tensors shaped like the weights)."""
+    xy = xy.contiguous().float()
+    dout = dout.contiguous().float()
+    dW, db, g = _mlp_grad_buffers(net)
+    m = net.struct()
+    check(lib().rt_mlp_backward(C.byref(m), _ptr(xy), _ptr(dout), int(xy.shape[0]), C.byref(g),
+                                stream_handle(stream)))
+    return dW, db
+
+
+def rt_render_mlp_adjoint(problem, fields, net, dL_dcube=None, target=None, cube_out=True,
+                          stream=None):
+    """Neural-field render plus its adjoint: (cube or None, grads, (dW, db)) with grads as in
+    rt_render_adjoint (w.r.t. the grid fields under the modulation) and the network's
+    parameter gradients."""
+    import torch
+    T, n, vt, hlo, hhi = fields.tensors()
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    shape = (vw.nch, vw.ny, vw.nx)
+    dL_dcube = _cube_arg(dL_dcube, shape, "dL_dcube")
+    target = _cube_arg(target, shape, "target")
+    dev = T.device
+    cube = None
+    if cube_out is True:
+        cube = torch.empty(shape, dtype=torch.float32, device=dev)
+    elif cube_out is not None and cube_out is not False:
+        cube = _cube_arg(cube_out, shape, "cube_out")
+    out = {k: torch.empty(tuple(t.shape), dtype=torch.float64, device=dev)
+           for k, t in zip(DeviceDisk.FIELDS, (T, n, vt, hlo, hhi))}
+    out["loss"] = torch.empty(1, dtype=torch.float64, device=dev)
+    gr = rt_grads(out["T"].data_ptr(), out["n_h2"].data_ptr(), out["vturb"].data_ptr(),
+                  out["h_lo"].data_ptr(), out["h_hi"].data_ptr(), out["loss"].data_ptr())
+    dW, db, mg = _mlp_grad_buffers(net)
+    m = net.struct()
+    check(lib().rt_render_mlp_adjoint(C.byref(g), C.byref(f), C.byref(o), C.byref(vw),
+                                      C.byref(ln), C.byref(m), _ptr(dL_dcube), _ptr(target),
+                                      _ptr(cube), C.byref(gr), C.byref(mg),
+                                      stream_handle(stream)))
+    return cube, out, (dW, db)
 
 
 def rt_sample_coords(problem, fields, out=None, stream=None):

@@ -156,8 +156,9 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
 
 // Chain rule of one sample from the reduced channel sums (ax, ay, aS; see the file header)
 // and the local derivatives J; node gradients by FP64 atomics, and the gradient with respect
-// to the four network outputs of the sample when dmod is given.
-__device__ __forceinline__ void scatter_grad(const MarchParams &P, const float *J, float kd,
+// to the four network outputs of the sample when dmod is given (returns its largest
+// magnitude, 0 otherwise).
+__device__ __forceinline__ float scatter_grad(const MarchParams &P, const float *J, float kd,
                                              float ax, float ay, float aS, const rt_grads &G,
                                              float4 *dmod) {
   const float gx = -kLn2 * ax;                       // dL/dkd
@@ -168,8 +169,12 @@ __device__ __forceinline__ void scatter_grad(const MarchParams &P, const float *
   const float gn = gx * J[J_KDN * 32];
   const float gl = gx * kd * J[J_SA * 32];
   const float gh = gx * kd * J[J_SB * 32];
-  if (dmod)
-    *dmod = make_float4(gT * J[J_T * 32], gn * J[J_N * 32], gl * P.h_scale, gh * P.h_scale);
+  float dm = 0.0f;
+  if (dmod) {
+    const float4 o = make_float4(gT * J[J_T * 32], gn * J[J_N * 32], gl * P.h_scale, gh * P.h_scale);
+    *dmod = o;
+    dm = fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fmaxf(fabsf(o.z), fabsf(o.w)));
+  }
   const float dT = gT * J[J_MT * 32], dn = gn * J[J_MN * 32];
   const float fr = J[J_FR * 32], fz = J[J_FZ * 32];
   const int i00 = __float_as_int(J[J_CELL * 32]), i0 = __float_as_int(J[J_I0 * 32]);
@@ -186,6 +191,7 @@ __device__ __forceinline__ void scatter_grad(const MarchParams &P, const float *
   atomicAdd(G.dh_lo + i0 + 1, (double)(gl * fr));
   atomicAdd(G.dh_hi + i0, (double)(gh * (1.0f - fr)));
   atomicAdd(G.dh_hi + i0 + 1, (double)(gh * fr));
+  return dm;
 }
 
 // Replicated FP64 gradient accumulators. Thousands of samples land on every node (and all
@@ -238,7 +244,8 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
     march_adj_kernel(const __grid_constant__ MarchParams P, const float *__restrict__ dLdc,
                      const float *__restrict__ target, float *__restrict__ cube_out,
                      const rt_grads G, float *__restrict__ scratch, int nseg,
-                     float4 *__restrict__ dmod, const GradCopies GC) {
+                     float4 *__restrict__ dmod, unsigned *__restrict__ dmax,
+                     const GradCopies GC) {
   constexpr int WPB = adj_wpb<LPR>();
   constexpr int R = 32 / LPR;          // rays per warp
   constexpr int NG = 32 / R;           // work units whose setups are computed together
@@ -271,6 +278,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
   const float dvs = (float)LPR * P.dv;
   const float S_bg = P.I0 / P.out_scale;  // background in internal intensity units
   double loss = 0.0;
+  float dmx = 0.0f;  // largest |dL/d(network output)| this lane wrote
   const rt_grads Gb = block_sink(P, G, GC);
 
   for (long long u0 = gw; u0 < nunits; u0 += W * NG) {
@@ -439,8 +447,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             s.w += v.w;
           }
           if (active && mine.z > 0.0f)
-            scatter_grad(P, Jl, mine.x, s.x, s.y, s.w, Gb,
-                         dmod ? dmod + (long long)pix * P.n_samples + kb + q : nullptr);
+            dmx = fmaxf(dmx, scatter_grad(P, Jl, mine.x, s.x, s.y, s.w, Gb,
+                                          dmod ? dmod + (long long)pix * P.n_samples + kb + q
+                                               : nullptr));
           __syncwarp();
         }
       }
@@ -449,6 +458,10 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
   if (G.loss && target) {
     for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
     if (lane == 0 && loss != 0.0) atomicAdd(G.loss, loss);
+  }
+  if (dmax) {
+    for (int o = 16; o > 0; o >>= 1) dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
+    if (lane == 0 && dmx > 0.0f) atomicMax(dmax, __float_as_uint(dmx));
   }
 }
 
@@ -609,14 +622,14 @@ static int sum_copies(const MarchParams &P, const rt_grads &G, const GradCopies 
 // Zero, march, sum: one adjoint launch on `scratch` (laid out by a).
 template <int LPR, int CPL, bool UNIF>
 static int run_adj(const MarchParams &P, const float *dLdc, const float *target, float *cube_out,
-                   const rt_grads &G, float4 *dmod, long long blocks, const AdjScratch &a,
-                   char *scratch, cudaStream_t stream) {
+                   const rt_grads &G, float4 *dmod, unsigned *dmax, long long blocks,
+                   const AdjScratch &a, char *scratch, cudaStream_t stream) {
   int rc = zero_grads(P, G, a, scratch, stream);
   if (rc != RT_OK) return rc;
   const GradCopies c = copies_of(P, a, scratch);
   const int nseg = (P.n_samples + kSeg - 1) / kSeg;
   march_adj_kernel<LPR, CPL, UNIF><<<(unsigned)blocks, adj_wpb<LPR>() * 32, 0, stream>>>(
-      P, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, c);
+      P, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, dmax, c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "adjoint launch: %s", cudaGetErrorString(e));
   return sum_copies(P, G, c, a, stream);
@@ -624,7 +637,8 @@ static int run_adj(const MarchParams &P, const float *dLdc, const float *target,
 
 template <int LPR, int CPL, bool UNIF>
 static int launch_adj_t(const MarchParams &P, const float *dLdc, const float *target,
-                        float *cube_out, const rt_grads &G, float4 *dmod, cudaStream_t stream) {
+                        float *cube_out, const rt_grads &G, float4 *dmod, unsigned *dmax,
+                        cudaStream_t stream) {
   const long long blocks = adj_blocks<LPR, CPL, UNIF>(P, 0);
   const AdjScratch a = plan_scratch(P, blocks, blocks * adj_block_bytes<LPR, CPL>(P), 0);
   char *scratch = nullptr;
@@ -632,17 +646,19 @@ static int launch_adj_t(const MarchParams &P, const float *dLdc, const float *ta
   if (e != cudaSuccess)
     return set_error(RT_ENOMEM, "adjoint scratch (%zu bytes): %s", a.total,
                      cudaGetErrorString(e));
-  int rc = run_adj<LPR, CPL, UNIF>(P, dLdc, target, cube_out, G, dmod, blocks, a, scratch,
-                                   stream);
+  int rc = run_adj<LPR, CPL, UNIF>(P, dLdc, target, cube_out, G, dmod, dmax, blocks, a,
+                                   scratch, stream);
   cudaFreeAsync(scratch, stream);
   return rc;
 }
 
 // Launches the fused adjoint (the gradient outputs are overwritten, not accumulated into).
 // dmod (optional, [pixel][sample] float4) receives dL/d(network outputs) for samples with gas
-// and is left untouched elsewhere.
+// and is left untouched elsewhere; dmax (optional, zeroed by the caller) their largest
+// magnitude as float bits.
 int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target,
-                   float *cube_out, const rt_grads &G, cudaStream_t stream, float4 *dmod) {
+                   float *cube_out, const rt_grads &G, cudaStream_t stream, float4 *dmod,
+                   unsigned *dmax) {
   long long npix = (long long)P.nx * P.ny;
   if (npix == 0 || P.nch == 0) return zero_grads(P, G, plan_scratch(P, 1, 0, 0), nullptr, stream);
   int LPR, CPL;
@@ -650,8 +666,8 @@ int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target,
   const bool u = P.v_uniform != 0;
 #define X(L, C)                                                                         \
   if (LPR == L && CPL == C)                                                             \
-    return u ? launch_adj_t<L, C, true>(P, dLdc, target, cube_out, G, dmod, stream)     \
-             : launch_adj_t<L, C, false>(P, dLdc, target, cube_out, G, dmod, stream);
+    return u ? launch_adj_t<L, C, true>(P, dLdc, target, cube_out, G, dmod, dmax, stream) \
+             : launch_adj_t<L, C, false>(P, dLdc, target, cube_out, G, dmod, dmax, stream);
   RTB_ADJ_LAYOUTS(X)
 #undef X
   return set_error(RT_EINVAL, "no adjoint layout for %d channels", P.nch);
@@ -745,7 +761,7 @@ static int launch_adj_fixed_t(const MarchParams &P, const float *dLdc, const flo
   const long long fit = (long long)(ck_room / per_block);
   if (blocks > fit) blocks = fit;
   const AdjScratch a = plan_scratch(P, blocks, blocks * per_block, kFixedScratchBytes);
-  return run_adj<LPR, CPL, UNIF>(P, dLdc, target, cube_out, G, nullptr, blocks, a,
+  return run_adj<LPR, CPL, UNIF>(P, dLdc, target, cube_out, G, nullptr, nullptr, blocks, a,
                                  reinterpret_cast<char *>(scratch), stream);
 }
 

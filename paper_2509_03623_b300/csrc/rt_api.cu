@@ -375,6 +375,56 @@ extern "C" int rt_render_mlp(const rt_grid *grid, const rt_fields *fields, const
   return rc;
 }
 
+extern "C" int rt_render_mlp_adjoint(const rt_grid *grid, const rt_fields *fields,
+                                     const rt_geom *geom, const rt_view *view,
+                                     const rt_line *line, const rt_mlp *mlp,
+                                     const float *dL_dcube, const float *target,
+                                     float *cube_out, const rt_grads *grads,
+                                     const rt_mlp_grads *mlp_grads, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params(grid, fields, geom, view, line, P);
+  if (rc == RT_OK) rc = mlp_validate(mlp);
+  if (rc == RT_OK) rc = mlp_grads_validate(mlp_grads);
+  if (rc == RT_OK) rc = check_adjoint_args(*P, dL_dcube, target, grads);
+  const long long npix = rc == RT_OK ? (long long)P->nx * P->ny : 0;
+  const long long ns = npix * (rc == RT_OK ? P->n_samples : 0);
+  if (rc == RT_OK) {
+    cudaStream_t st = (cudaStream_t)stream;
+    // one buffer: network outputs, dL/d(outputs), ray setups, backward scratch, gradient scale
+    const size_t mod_bytes = (size_t)ns * sizeof(float4);
+    const size_t ray_bytes = (ray_buffer_bytes(npix) + 255) & ~(size_t)255;
+    const size_t spill_bytes = mlp_bwd_scratch_bytes(ns);
+    const size_t bytes = 2 * mod_bytes + ray_bytes + spill_bytes + 256;
+    char *buf = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&buf, bytes, st);
+    if (e != cudaSuccess) {
+      rc = set_error(RT_ENOMEM, "neural adjoint buffers (%zu bytes): %s", bytes,
+                     cudaGetErrorString(e));
+    } else {
+      float4 *mod = reinterpret_cast<float4 *>(buf);
+      float4 *dmod = reinterpret_cast<float4 *>(buf + mod_bytes);
+      char *rays = buf + 2 * mod_bytes;
+      char *spill = rays + ray_bytes;
+      unsigned *dmax = reinterpret_cast<unsigned *>(spill + spill_bytes);
+      e = cudaMemsetAsync(dmod, 0, mod_bytes, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, sizeof(unsigned), st);
+      if (e != cudaSuccess) rc = set_error(RT_ECUDA, "memset: %s", cudaGetErrorString(e));
+      if (rc == RT_OK && ns > 0) rc = launch_mlp_rays(mlp, *P, mod, rays, st);
+      if (rc == RT_OK) {
+        P->mod = ns > 0 ? mod : nullptr;
+        P->h_scale = (float)mlp->h_scale;
+        rc = launch_adjoint(*P, dL_dcube, target, cube_out, *grads, st, dmod, dmax);
+      }
+      if (rc == RT_OK) rc = launch_mlp_bwd_rays(mlp, *P, rays, dmod, dmax, spill, mlp_grads, st);
+      cudaFreeAsync(buf, st);
+    }
+  }
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
 extern "C" const char *rt_last_error(void) { return g_err; }
 
 extern "C" const char *rt_version(void) { return "b300-linert 0.1 (sm_103a)"; }

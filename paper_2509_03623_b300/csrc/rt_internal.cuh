@@ -270,7 +270,8 @@ int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream);
 int launch_count(const MarchParams &P, unsigned long long *count, cudaStream_t stream);
 void lane_layout(int nch, int *lpr, int *cpl);
 int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target, float *cube_out,
-                   const rt_grads &G, cudaStream_t stream, float4 *dmod = nullptr);
+                   const rt_grads &G, cudaStream_t stream, float4 *dmod = nullptr,
+                   unsigned *dmax = nullptr);
 void adj_layout(int nch, int *lpr, int *cpl);
 size_t adjoint_scratch_bytes(const MarchParams &P, long long cap_blocks);
 int check_adjoint_args(const MarchParams &P, const float *dL_dcube, const float *target,
@@ -279,6 +280,11 @@ int launch_mlp_rays(const rt_mlp *m, const MarchParams &P, float4 *mod, void *ra
                     cudaStream_t stream);
 size_t ray_buffer_bytes(long long npix);
 int mlp_validate(const rt_mlp *m);
+int mlp_grads_validate(const rt_mlp_grads *g);
+size_t mlp_bwd_scratch_bytes(long long n);
+int launch_mlp_bwd_rays(const rt_mlp *m, const MarchParams &P, const void *ray_buf,
+                        const float4 *dmod, const unsigned *dmax, void *spill,
+                        const rt_mlp_grads *g, cudaStream_t stream);
 int launch_coords(const MarchParams &P, float2 *xy, cudaStream_t stream);
 int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, double c,
                         double *out, cudaStream_t stream);

@@ -80,10 +80,23 @@ __device__ __forceinline__ unsigned long long mma_desc(unsigned addr, int K) {
 }
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16 (format 1) or FP16 (format 0),
-// both K-major, M = 128.
-__host__ __device__ constexpr unsigned idesc_16(int N, bool f16) {
+// M = 128; A (bit 15) and B (bit 16) K-major (0) or MN-major (1).
+__host__ __device__ constexpr unsigned idesc_16(int N, bool f16, bool a_mn = false,
+                                                bool b_mn = false) {
   return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) |
-         ((unsigned)(N >> 3) << 17) | ((128u >> 4) << 24);
+         ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) | ((unsigned)(N >> 3) << 17) |
+         ((128u >> 4) << 24);
+}
+
+// Shared-memory matrix descriptor, no swizzle, MN-major: the 16-byte rows of a core matrix run
+// along M (or N), its 8 rows along K; mn_stride and k_stride are the distances between core
+// matrices along MN and along K. Without swizzling the leading-dimension offset is the K
+// stride and the stride-dimension offset the MN stride, in either major order.
+__device__ __forceinline__ unsigned long long mma_desc_mn(unsigned addr, unsigned mn_stride,
+                                                          unsigned k_stride) {
+  unsigned long long lbo = k_stride >> 4, sbo = mn_stride >> 4;
+  return (unsigned long long)((addr >> 4) & 0x3FFF) | ((lbo & 0x3FFF) << 16) |
+         ((sbo & 0x3FFF) << 32) | (1ull << 46);
 }
 
 template <bool F16>
@@ -162,31 +175,55 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v) {
   for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
 }
 
-// SiLU(x) = x sigma(x) = 0.5 x (1 + tanh(x/2)) (hardware tanh; the result is rounded to BF16).
-__device__ __forceinline__ float silu(float x) {
-  float t;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * x));
-  float h = 0.5f * x;
-  return fmaf(h, t, h);
+// Two FP32 values rounded to the 16-bit format and packed (a in the low half).
+template <bool F16>
+__device__ __forceinline__ unsigned pack16(float a, float b) {
+  unsigned z;
+  if (F16)
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(z) : "f"(b), "f"(a));
+  else
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(z) : "f"(b), "f"(a));
+  return z;
 }
 
-// SiLU of two pre-activations in the 16-bit format, packed: h = z/2 (exact), t = tanh(h)
-// (hardware, packed), SiLU = h + h t (one packed FMA); the result is the next layer's operand.
 template <bool F16>
-__device__ __forceinline__ unsigned silu2(float z0, float z1) {
-  unsigned z, h, t, r;
+__device__ __forceinline__ float2 unpack16(unsigned z) {
   if (F16) {
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(z) : "f"(z1), "f"(z0));
+    __half2 h = *reinterpret_cast<__half2 *>(&z);
+    return __half22float2(h);
+  }
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&z);
+  return __bfloat1622float2(h);
+}
+
+// SiLU of two packed 16-bit pre-activations: h = z/2 (exact), t = tanh(h) (hardware, packed),
+// SiLU = h + h t (one packed FMA); the result is the next layer's operand.
+template <bool F16>
+__device__ __forceinline__ unsigned silu2p(unsigned z) {
+  unsigned h, t, r;
+  if (F16) {
     asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(h) : "r"(z), "r"(0x38003800u));
     asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h));
     asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(h), "r"(t), "r"(h));
   } else {
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(z) : "f"(z1), "f"(z0));
     asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(h) : "r"(z), "r"(0x3F003F00u));
     asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
     asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(h), "r"(t), "r"(h));
   }
   return r;
+}
+
+template <bool F16>
+__device__ __forceinline__ unsigned silu2(float z0, float z1) {
+  return silu2p<F16>(pack16<F16>(z0, z1));
+}
+
+// SiLU'(z) = s (1 + z (1 - s)), s = sigma(z) = (1 + tanh(z/2)) / 2.
+__device__ __forceinline__ float dsilu(float z) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
+  const float s = fmaf(0.5f, t, 0.5f);
+  return s * fmaf(z, 1.0f - s, 1.0f);
 }
 
 // Store 8 consecutive 16-bit values of row m starting at column k (k multiple of 8).
@@ -202,12 +239,12 @@ __device__ __forceinline__ void store8(h16 *A, int m, int k, int K, const float 
 // Fourier features of x = (rhat, zhat) for directions [16 half, 16 half + 16):
 // sin 2 pi B x into f[0..15], cos into f[16..31]; phases reduced to [-1/2, 1/2) cycles before
 // the hardware sin/cos.
-__device__ __forceinline__ void features(const MlpSmem &S, float rh, float zh, int half,
+__device__ __forceinline__ void features(const float (*Bf)[2], float rh, float zh, int half,
                                          float *f) {
 #pragma unroll
   for (int j = 0; j < 16; j++) {
     const int i = 16 * half + j;
-    float ph = fmaf(S.Bf[i][0], rh, S.Bf[i][1] * zh);
+    float ph = fmaf(Bf[i][0], rh, Bf[i][1] * zh);
     ph -= rintf(ph);
     float a = 6.283185307179586f * ph;
     f[j] = __sinf(a);
@@ -342,7 +379,7 @@ __global__ void __launch_bounds__(kGT * kTG, 1)
     if (!any) continue;
     {
       float f[32];
-      features(S, rh, zh, half, f);
+      features(S.Bf, rh, zh, half, f);
       store8<F16>(A, t, 16 * half, kMlpF, f);
       store8<F16>(A, t, 16 * half + 8, kMlpF, f + 8);
       store8<F16>(A, t, 32 + 16 * half, kMlpF, f + 16);
@@ -505,6 +542,503 @@ int launch_coords(const MarchParams &P, float2 *xy, cudaStream_t stream) {
   return RT_OK;
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Backward pass of the network: dL/dW and dL/db of every layer from per-sample dL/d(outputs)
+// (reverse mode of the network written out by hand, on the tensor cores).
+//
+// One persistent CTA per SM, 8 warps (two per TMEM lane quadrant). Tensor memory (512
+// columns) holds the weight-gradient accumulators for the whole run of the CTA -- dW2..dW4
+// (128 columns each) and dW5^T (16) -- and an 80-column working accumulator; dW1 (128 x 64)
+// is staged through the working columns once per tile and summed in registers. Per tile of
+// 128 samples:
+//   forward: features -> 4 SiLU layers, each as two 64-column MMA chunks (M = samples); the
+//     16-bit pre-activations go to a per-CTA scratch in global memory (L2-resident);
+//   backward: delta_5 = dL/d(outputs) (scaled by a power of two so that the largest is below
+//     one: FP16 has no room for raw gradients), then per layer l = 5..1
+//       dW_l += delta_l^T a_{l-1}            (M = out features, K = samples, MN-major operands)
+//       db_l += delta_l^T 1                  (an MMA against a block of ones)
+//       delta_{l-1} = (delta_l W_l) SiLU'(z_{l-1})   (M = samples, K = out features; W_l read
+//                                                      MN-major from the same shared copy)
+//     with a_{l-1} recomputed from the stored pre-activations where it was overwritten.
+// A single thread issues the MMAs; the working accumulator is read with tcgen05.ld and freed
+// (barrier) before the epilogue arithmetic, so the next chunk's MMA overlaps it. At the end
+// each CTA adds its accumulators, unscaled, to the FP64 outputs with atomics. Waits on the
+// mbarrier are bounded: on expiry the CTA records an error, stops and releases its tensor
+// memory.
+// ---------------------------------------------------------------------------------------
+constexpr int kBwdThreads = 256;
+constexpr unsigned kColW2 = 0, kColW3 = 128, kColW4 = 256, kColW5 = 384, kColWork = 400;
+constexpr unsigned kColDb = kColWork + 64;  // bias sums (16 columns) inside the working range
+constexpr int kChunk = 64;                  // columns per layer-output MMA chunk
+
+struct __align__(1024) BwdSmem {
+  h16 P[kMlpTile * kMlpW];          // activations / deltas, rows = samples (32 KB)
+  h16 Q[kMlpTile * kMlpW];          // (32 KB)
+  h16 F[kMlpTile * kMlpF];          // Fourier features (16 KB)
+  h16 D5[kMlpTile * kMlpOutPad];    // output-layer deltas, 4 of 16 columns used (4 KB)
+  h16 ONES[kMlpOutPad * kMlpTile];  // all ones [16][samples]: bias sums as an MMA (4 KB)
+  h16 W5[kMlpOutPad * kMlpW];       // (4 KB)
+  h16 W1[kMlpW * kMlpF];            // (16 KB)
+  h16 Wh[3][kMlpW * kMlpW];         // W2..W4 (96 KB)
+  float bias[4][kMlpW];
+  float Bf[32][2];
+  unsigned long long mbar;
+  unsigned tmem_base;
+  int abort;
+};
+
+// One past the highest byte an MN-major operand touches: base offset, largest per-instruction
+// offset, extents in core matrices along MN and K, and the strides along MN and K.
+constexpr size_t mn_reach(size_t off, size_t step, size_t nmn, size_t nk, size_t smn,
+                          size_t sk) {
+  return off + step + (nmn - 1) * smn + (nk - 1) * sk + 128;
+}
+constexpr size_t kActBytes = sizeof(h16) * kMlpTile * kMlpW;
+// every MN-major read stays inside the array it addresses
+static_assert(mn_reach(0, 1024 + 7 * 4096, 8, 2, 128, 2048) <= kActBytes, "W_l (MN-major) reach");
+static_assert(mn_reach(0, 1024, 8, 2, 128, 2048) <= sizeof(h16) * kMlpOutPad * kMlpW,
+              "W5 (MN-major) reach");
+static_assert(mn_reach(0, 7 * 4096, 16, 2, 128, 2048) <= kActBytes, "activations (MN-major) reach");
+static_assert(mn_reach(0, 7 * 2048, 8, 2, 128, 1024) <= sizeof(h16) * kMlpTile * kMlpF,
+              "features (MN-major) reach");
+static_assert(mn_reach(0, 7 * 512, 2, 2, 128, 256) <= sizeof(h16) * kMlpTile * kMlpOutPad,
+              "output deltas (MN-major) reach");
+static_assert(sizeof(BwdSmem) <= 227 * 1024, "shared memory");
+static_assert(kColDb + 16 <= 512, "tensor memory");
+
+struct MlpGradsDev {
+  double *dW[5];
+  double *db[5];
+};
+
+// 32 accumulator columns of a layer-output chunk -> the 16 pairs this thread stores.
+template <bool F16>
+__device__ __forceinline__ void store32(h16 *A, int t, int f0, const unsigned *p) {
+#pragma unroll
+  for (int k = 0; k < 4; k++)
+    *reinterpret_cast<uint4 *>(A + cm_off(t, f0 + 8 * k, kMlpW)) =
+        make_uint4(p[4 * k], p[4 * k + 1], p[4 * k + 2], p[4 * k + 3]);
+}
+
+template <class In, bool F16>
+__global__ void __launch_bounds__(kBwdThreads, 1)
+    mlp_bwd_kernel(const MlpParamsDev Wp, const __grid_constant__ In in,
+                   const float4 *__restrict__ gout, long long n,
+                   const unsigned *__restrict__ gmax, h16 *__restrict__ spill,
+                   const MlpGradsDev G) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  BwdSmem &S = *reinterpret_cast<BwdSmem *>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3, half = warp >> 2;
+  const int t = q * 32 + lane;  // tile row: sample (or output feature of a weight gradient)
+  h16 *Z = spill + (size_t)blockIdx.x * (4 * kMlpTile * kMlpW);  // this CTA's pre-activations
+
+  // ---- one-time setup ----
+  for (int i = tid; i < kMlpW * kMlpF; i += kBwdThreads)
+    S.W1[cm_off(i / kMlpF, i % kMlpF, kMlpF)] = to16<F16>(Wp.W[0][i]);
+  for (int l = 0; l < 3; l++)
+    for (int i = tid; i < kMlpW * kMlpW; i += kBwdThreads)
+      S.Wh[l][cm_off(i / kMlpW, i % kMlpW, kMlpW)] = to16<F16>(Wp.W[l + 1][i]);
+  for (int i = tid; i < kMlpOutPad * kMlpW; i += kBwdThreads) {
+    int o = i / kMlpW, k = i % kMlpW;
+    S.W5[cm_off(o, k, kMlpW)] = to16<F16>(o < kMlpOut ? Wp.W[4][o * kMlpW + k] : 0.0f);
+  }
+  for (int i = tid; i < kMlpOutPad * kMlpTile; i += kBwdThreads) {
+    S.ONES[i] = to16<F16>(1.0f);
+    S.D5[i] = 0;  // columns 4..15 stay zero
+  }
+  for (int i = tid; i < 4 * kMlpW; i += kBwdThreads) S.bias[i / kMlpW][i % kMlpW] = Wp.b[i / kMlpW][i % kMlpW];
+  if (tid < 64) S.Bf[tid >> 1][tid & 1] = Wp.B[tid];
+  if (tid == 0) {
+    S.abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar)), "r"(1));
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&S.tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tm = S.tmem_base;
+  const unsigned tl = tm + ((unsigned)(q * 32) << 16);  // this warp's lanes
+  const unsigned mbar = smem_u32(&S.mbar);
+  unsigned phase = 0;
+  // power-of-two scale that brings the largest |dL/d(output)| below one
+  int ex = 0;
+  {
+    const float gm = __uint_as_float(*gmax);
+    if (gm > 0.0f && gm < 3.0e38f) frexpf(gm, &ex);
+    ex = max(-120, min(120, ex));
+  }
+  const float scale = ldexpf(1.0f, -ex);
+  float dw1[32];                               // dW1[t][32 half + j]
+#pragma unroll
+  for (int j = 0; j < 32; j++) dw1[j] = 0.0f;
+  float dbacc[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // db_l of output feature t (half 0)
+  float db5acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // db_5 over this warp's rows (lane 0, half 0)
+  bool first = true;
+  const unsigned aP = smem_u32(S.P), aQ = smem_u32(S.Q), aF = smem_u32(S.F);
+  const unsigned aD5 = smem_u32(S.D5), aONE = smem_u32(S.ONES), aW5 = smem_u32(S.W5);
+
+  // bounded wait for the last commit; records a failure in S.abort
+  auto wait_mma = [&]() {
+    const bool ok = mbar_wait(mbar, phase);
+    phase ^= 1;
+    tc_fence_after();
+    if (!ok) {
+      S.abort = 1;
+      atomicExch(&g_mlp_error, 1);
+    }
+  };
+  // z (16-bit, packed pairs) of layer index L, chunk c, this thread's half and row: 4 x uint4
+  auto zrow = [&](int L, int c) {
+    return reinterpret_cast<uint4 *>(Z + ((size_t)((L * 2 + c) * 2 + half) * kMlpTile + t) * 32);
+  };
+
+  const long long ntiles = (n + kMlpTile - 1) / kMlpTile;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    float rh = 0.0f, zh = 0.0f;
+    const bool need = tile_input(in, nullptr, tile * kMlpTile, t, &rh, &zh, 0);
+    if (!__syncthreads_or(need)) continue;
+    const long long s = tile * kMlpTile + t;
+    float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (need) {
+      g = gout[s];
+      g.x *= scale;
+      g.y *= scale;
+      g.z *= scale;
+      g.w *= scale;
+    }
+    {
+      float f[32];
+      features(S.Bf, rh, zh, half, f);
+      store8<F16>(S.F, t, 16 * half, kMlpF, f);
+      store8<F16>(S.F, t, 16 * half + 8, kMlpF, f + 8);
+      store8<F16>(S.F, t, 32 + 16 * half, kMlpF, f + 16);
+      store8<F16>(S.F, t, 32 + 16 * half + 8, kMlpF, f + 24);
+    }
+    if (half == 0) {
+      const float d[8] = {g.x, g.y, g.z, g.w, 0.0f, 0.0f, 0.0f, 0.0f};
+      store8<F16>(S.D5, t, 0, kMlpOutPad, d);
+      float r[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+      for (int o = 0; o < 4; o++)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) r[o] += __shfl_xor_sync(0xffffffffu, r[o], off);
+      if (lane == 0)
+#pragma unroll
+        for (int o = 0; o < 4; o++) db5acc[o] += r[o];
+    }
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+
+    // ---------------- forward: a1..a4 (P, Q, P, Q), pre-activations to the scratch ----------------
+    for (int l = 0; l < 4; l++) {
+      const int K = l == 0 ? kMlpF : kMlpW;
+      const unsigned ain = l == 0 ? aF : ((l & 1) ? aP : aQ);
+      h16 *Aout = (l & 1) ? S.Q : S.P;
+      const unsigned wl = l == 0 ? smem_u32(S.W1) : smem_u32(S.Wh[l - 1]);
+      auto issue = [&](int c) {
+        tc_fence_after();
+        const unsigned b0 = wl + (unsigned)(c * 8 * (K / 8) * 128);  // rows 64c.. of W_l
+        for (int ks = 0; ks < K / 16; ks++)
+          mma_bf16(tm + kColWork, mma_desc(ain + ks * 256, K), mma_desc(b0 + ks * 256, K),
+                   idesc_16(kChunk, F16), ks > 0);
+        mma_commit(mbar);
+      };
+      if (tid == 0) issue(0);
+      for (int c = 0; c < 2; c++) {
+        wait_mma();
+        float v[32];
+        tmem_ld32(tl + kColWork + 32 * half, v);
+        tc_fence_before();
+        __syncthreads();  // working columns free
+        if (S.abort) goto done;
+        if (tid == 0 && c == 0) issue(1);
+        const int f0 = kChunk * c + 32 * half;
+        unsigned zp[16], ap[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          zp[j] = pack16<F16>(v[2 * j] + S.bias[l][f0 + 2 * j], v[2 * j + 1] + S.bias[l][f0 + 2 * j + 1]);
+          ap[j] = silu2p<F16>(zp[j]);
+        }
+        uint4 *zr = zrow(l, c);
+#pragma unroll
+        for (int k = 0; k < 4; k++) zr[k] = make_uint4(zp[4 * k], zp[4 * k + 1], zp[4 * k + 2], zp[4 * k + 3]);
+        store32<F16>(Aout, t, f0, ap);
+      }
+      proxy_fence();
+      tc_fence_before();
+      __syncthreads();
+    }
+
+    // ---------------- output layer: dW5^T += a4^T delta5, delta4 = (delta5 W5) SiLU'(z4) ----------------
+    {
+      auto issue = [&](int c) {
+        tc_fence_after();
+        mma_bf16(tm + kColWork, mma_desc(aD5, kMlpOutPad), mma_desc_mn(aW5 + c * 1024, 128, 2048),
+                 idesc_16(kChunk, F16, false, true), 0);
+        mma_commit(mbar);
+      };
+      if (tid == 0) {
+        tc_fence_after();
+        for (int ks = 0; ks < kMlpTile / 16; ks++)
+          mma_bf16(tm + kColW5, mma_desc_mn(aQ + ks * 4096, 128, 2048),
+                   mma_desc_mn(aD5 + ks * 512, 128, 256), idesc_16(16, F16, true, true),
+                   !first || ks > 0);
+        issue(0);
+      }
+      for (int c = 0; c < 2; c++) {
+        const uint4 *zr = zrow(3, c);
+        uint4 zq[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) zq[k] = zr[k];
+        wait_mma();
+        float v[32];
+        tmem_ld32(tl + kColWork + 32 * half, v);
+        tc_fence_before();
+        __syncthreads();
+        if (S.abort) goto done;
+        if (tid == 0 && c == 0) issue(1);
+        const int f0 = kChunk * c + 32 * half;
+        const unsigned *zz = reinterpret_cast<const unsigned *>(zq);
+        unsigned dp[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          const float2 z = unpack16<F16>(zz[j]);
+          dp[j] = pack16<F16>(v[2 * j] * dsilu(z.x), v[2 * j + 1] * dsilu(z.y));
+        }
+        store32<F16>(S.Q, t, f0, dp);
+      }
+      proxy_fence();
+      tc_fence_before();
+      __syncthreads();
+    }
+
+    // ---------------- hidden layers l = 4..1 ----------------
+    for (int l = 4; l >= 1; l--) {
+      const unsigned ay = (l & 1) ? aP : aQ;                            // delta_l
+      h16 *X = (l & 1) ? S.Q : S.P;                                     // a_{l-1} (l >= 2)
+      const unsigned ax = l == 1 ? aF : smem_u32(X);
+      const int Kin = l == 1 ? kMlpF : kMlpW;
+      if (l == 3 || l == 2) {  // a_{l-1} was overwritten: recompute it from z_{l-1}
+        for (int c = 0; c < 2; c++) {
+          const uint4 *zr = zrow(l - 2, c);
+          unsigned ap[16];
+#pragma unroll
+          for (int k = 0; k < 4; k++) {
+            const uint4 z = zr[k];
+            ap[4 * k] = silu2p<F16>(z.x);
+            ap[4 * k + 1] = silu2p<F16>(z.y);
+            ap[4 * k + 2] = silu2p<F16>(z.z);
+            ap[4 * k + 3] = silu2p<F16>(z.w);
+          }
+          store32<F16>(X, t, kChunk * c + 32 * half, ap);
+        }
+        proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+      }
+      if (tid == 0) {
+        tc_fence_after();
+        // dW_l (persistent columns; dW1 goes through the working columns once per tile)
+        const unsigned colw = l == 1 ? kColWork : (l == 2 ? kColW2 : (l == 3 ? kColW3 : kColW4));
+        const unsigned kst = (unsigned)(Kin / 8) * 128;  // distance between 8-sample groups of X
+        for (int ks = 0; ks < kMlpTile / 16; ks++)
+          mma_bf16(tm + colw, mma_desc_mn(ay + ks * 4096, 128, 2048),
+                   mma_desc_mn(ax + ks * 2 * kst, 128, kst), idesc_16(Kin, F16, true, true),
+                   (l > 1 && !first) || ks > 0);
+        for (int ks = 0; ks < kMlpTile / 16; ks++)
+          mma_bf16(tm + kColDb, mma_desc_mn(ay + ks * 4096, 128, 2048),
+                   mma_desc(aONE + ks * 256, kMlpTile), idesc_16(16, F16, true, false), ks > 0);
+        mma_commit(mbar);
+      }
+      wait_mma();
+      if (half == 0) {
+        float v[16];
+        tmem_ld16(tl + kColDb, v);
+        dbacc[l - 1] += v[0];
+      }
+      if (l == 1) {
+        float v[32];
+        tmem_ld32(tl + kColWork + 32 * half, v);
+#pragma unroll
+        for (int j = 0; j < 32; j++) dw1[j] += v[j];
+      }
+      tc_fence_before();
+      __syncthreads();
+      if (S.abort) goto done;
+      if (l == 1) break;
+      const unsigned wl = smem_u32(S.Wh[l - 2]);  // W_l
+      auto issue = [&](int c) {
+        tc_fence_after();
+        for (int ks = 0; ks < kMlpW / 16; ks++)
+          mma_bf16(tm + kColWork, mma_desc(ay + ks * 256, kMlpW),
+                   mma_desc_mn(wl + c * 1024 + ks * 4096, 128, 2048),
+                   idesc_16(kChunk, F16, false, true), ks > 0);
+        mma_commit(mbar);
+      };
+      if (tid == 0) issue(0);
+      for (int c = 0; c < 2; c++) {
+        const uint4 *zr = zrow(l - 2, c);
+        uint4 zq[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) zq[k] = zr[k];
+        wait_mma();
+        float v[32];
+        tmem_ld32(tl + kColWork + 32 * half, v);
+        tc_fence_before();
+        __syncthreads();
+        if (S.abort) goto done;
+        if (tid == 0 && c == 0) issue(1);
+        const int f0 = kChunk * c + 32 * half;
+        const unsigned *zz = reinterpret_cast<const unsigned *>(zq);
+        unsigned dp[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          const float2 z = unpack16<F16>(zz[j]);
+          dp[j] = pack16<F16>(v[2 * j] * dsilu(z.x), v[2 * j + 1] * dsilu(z.y));
+        }
+        store32<F16>(X, t, f0, dp);
+      }
+      proxy_fence();
+      tc_fence_before();
+      __syncthreads();
+    }
+    first = false;
+  }
+
+done:
+  __syncthreads();
+  if (S.abort) {
+    // let an MMA still in flight finish (bounded) before the tensor memory is released
+    if (tid == 0) mbar_wait(mbar, phase);
+  } else if (!first) {
+    tc_fence_after();
+    const double un = ldexp(1.0, ex);
+#pragma unroll
+    for (int j = 0; j < 32; j++) atomicAdd(G.dW[0] + t * kMlpF + 32 * half + j, (double)dw1[j] * un);
+    for (int L = 1; L < 4; L++) {
+      const unsigned col = kColW2 + (unsigned)(L - 1) * 128;
+      for (int cc = 0; cc < 2; cc++) {
+        float v[32];
+        tmem_ld32(tl + col + 64 * half + 32 * cc, v);
+#pragma unroll
+        for (int j = 0; j < 32; j++)
+          atomicAdd(G.dW[L] + t * kMlpW + 64 * half + 32 * cc + j, (double)v[j] * un);
+      }
+    }
+    if (half == 0) {
+      float v[16];
+      tmem_ld16(tl + kColW5, v);  // row = input feature t, columns = outputs
+#pragma unroll
+      for (int o = 0; o < kMlpOut; o++) atomicAdd(G.dW[4] + o * kMlpW + t, (double)v[o] * un);
+#pragma unroll
+      for (int l = 0; l < 4; l++) atomicAdd(G.db[l] + t, (double)dbacc[l] * un);
+      if (lane == 0)
+#pragma unroll
+        for (int o = 0; o < kMlpOut; o++) atomicAdd(G.db[4] + o, (double)db5acc[o] * un);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(512));
+  }
+}
+
+// max |x| over n float4 values into *out (float bits; out zeroed by the caller)
+__global__ void absmax_kernel(const float4 *__restrict__ x, long long n, unsigned *out) {
+  float m = 0.0f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float4 v = x[i];
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(out, __float_as_uint(m));
+}
+
+static size_t mlp_spill_bytes(long long blocks) {
+  return (size_t)blocks * 4 * kMlpTile * kMlpW * sizeof(h16);
+}
+
+// Zeroes the gradient outputs and runs the backward kernel over n samples; spill must hold
+// mlp_spill_bytes(blocks) with blocks = mlp_bwd_blocks(n).
+static long long mlp_bwd_blocks(long long n) {
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  long long tiles = (n + kMlpTile - 1) / kMlpTile;
+  return tiles < nsm ? (tiles > 0 ? tiles : 1) : nsm;
+}
+
+template <class In, bool F16>
+static int launch_mlp_bwd_t(const rt_mlp *m, const In &in, const float4 *gout, long long n,
+                            const unsigned *gmax, h16 *spill, const rt_mlp_grads *g,
+                            cudaStream_t stream) {
+  auto kern = mlp_bwd_kernel<In, F16>;
+  const size_t smem = sizeof(BwdSmem);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess)
+    return set_error(RT_ECUDA, "mlp backward smem attribute: %s", cudaGetErrorString(e));
+  const int din[5] = {kMlpF, kMlpW, kMlpW, kMlpW, kMlpW};
+  const int dout[5] = {kMlpW, kMlpW, kMlpW, kMlpW, kMlpOut};
+  MlpGradsDev G;
+  for (int l = 0; l < 5; l++) {
+    G.dW[l] = g->dW[l];
+    G.db[l] = g->db[l];
+    e = cudaMemsetAsync(g->dW[l], 0, sizeof(double) * din[l] * dout[l], stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->db[l], 0, sizeof(double) * dout[l], stream);
+    if (e != cudaSuccess) return set_error(RT_ECUDA, "gradient memset: %s", cudaGetErrorString(e));
+  }
+  if (n <= 0) return RT_OK;
+  kern<<<(unsigned)mlp_bwd_blocks(n), kBwdThreads, smem, stream>>>(mlp_dev(m), in, gout, n, gmax,
+                                                                   spill, G);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "mlp backward launch: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
+template <class In>
+static int launch_mlp_bwd(const rt_mlp *m, const In &in, const float4 *gout, long long n,
+                          const unsigned *gmax, h16 *spill, const rt_mlp_grads *g,
+                          cudaStream_t stream) {
+  return m->precision == RT_MLP_BF16
+             ? launch_mlp_bwd_t<In, false>(m, in, gout, n, gmax, spill, g, stream)
+             : launch_mlp_bwd_t<In, true>(m, in, gout, n, gmax, spill, g, stream);
+}
+
+int mlp_grads_validate(const rt_mlp_grads *g) {
+  if (!g) return set_error(RT_EINVAL, "null network gradients");
+  for (int l = 0; l < 5; l++)
+    if (!g->dW[l] || !g->db[l])
+      return set_error(RT_EINVAL, "null weight or bias gradient of layer %d", l);
+  return RT_OK;
+}
+
+size_t mlp_bwd_scratch_bytes(long long n) { return mlp_spill_bytes(mlp_bwd_blocks(n)); }
+
+// Backward pass over the samples of a render (rays from the forward's pre-pass in ray_buf,
+// per-sample dL/d(outputs) in dmod, their largest magnitude in *dmax).
+int launch_mlp_bwd_rays(const rt_mlp *m, const MarchParams &P, const void *ray_buf,
+                        const float4 *dmod, const unsigned *dmax, void *spill,
+                        const rt_mlp_grads *g, cudaStream_t stream) {
+  RayInput in;
+  in.P = P;
+  in.rays = reinterpret_cast<const Ray *>(ray_buf);
+  long long n = (long long)P.nx * P.ny * P.n_samples;
+  return launch_mlp_bwd(m, in, dmod, n, dmax, reinterpret_cast<h16 *>(spill), g, stream);
+}
+
 }  // namespace rtb
 
 using namespace rtb;
@@ -526,4 +1060,43 @@ extern "C" int rt_mlp_status(int *timed_out) {
   if (e != cudaSuccess) return set_error(RT_ECUDA, "mlp status: %s", cudaGetErrorString(e));
   *timed_out = v;
   return RT_OK;
+}
+
+// Backward pass at explicit inputs (see rt.h).
+extern "C" int rt_mlp_backward(const rt_mlp *mlp, const float *xy, const float *dout,
+                               long long n, const rt_mlp_grads *grads, void *stream) {
+  using namespace rtb;
+  int rc = mlp_check(mlp);
+  if (rc == RT_OK) rc = mlp_grads_validate(grads);
+  if (rc == RT_OK && n < 0) rc = set_error(RT_EINVAL, "negative point count");
+  if (rc == RT_OK && n > 0 && (!xy || !dout)) rc = set_error(RT_EINVAL, "null inputs");
+  if (rc != RT_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long blocks = mlp_bwd_blocks(n);
+  const size_t sp = mlp_spill_bytes(blocks);
+  char *buf = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&buf, sp + 256, st);
+  if (e != cudaSuccess)
+    return set_error(RT_ENOMEM, "mlp backward scratch (%zu bytes): %s", sp + 256,
+                     cudaGetErrorString(e));
+  unsigned *gmax = reinterpret_cast<unsigned *>(buf + sp);
+  e = cudaMemsetAsync(gmax, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess && n > 0) {
+    long long nb = (n + 255) / 256;
+    absmax_kernel<<<(unsigned)(nb < 1184 ? nb : 1184), 256, 0, st>>>(
+        reinterpret_cast<const float4 *>(dout), n, gmax);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    rc = set_error(RT_ECUDA, "gradient scale: %s", cudaGetErrorString(e));
+  } else {
+    XYInput in;
+    in.xy = xy;
+    in.n = n;
+    rc = launch_mlp_bwd(mlp, in, reinterpret_cast<const float4 *>(dout), n, gmax,
+                        reinterpret_cast<h16 *>(buf), grads, st);
+  }
+  cudaFreeAsync(buf, st);
+  if (rc == RT_OK) clear_error();
+  return rc;
 }

@@ -332,6 +332,36 @@ def test_p12_mlp_matches_torch(orc):
     np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-13)
 
 
+def test_p12_mlp_gradients_match_torch_autograd(orc):
+    """Reverse mode of the oracle network vs torch FP64 autograd of the same Sequential."""
+    torch = pytest.importorskip("torch")
+    w = synth.mlp_weights(12)
+    rng = np.random.default_rng(1)
+    w.b = [rng.uniform(-0.1, 0.1, size=b.shape) for b in w.b]
+    x = rng.uniform(0, 1, size=(93, 2))
+    gout = rng.standard_normal((93, 4))
+    dW, db = orc.mlp_grad(w, x, gout)
+    layers = []
+    for l, (W, b) in enumerate(zip(w.W, w.b)):
+        lin = torch.nn.Linear(W.shape[1], W.shape[0]).double()
+        with torch.no_grad():
+            lin.weight.copy_(torch.from_numpy(np.asarray(W, dtype=np.float64)))
+            lin.bias.copy_(torch.from_numpy(np.asarray(b, dtype=np.float64)))
+        layers.append(lin)
+        if l < len(w.W) - 1:
+            layers.append(torch.nn.SiLU())
+    net = torch.nn.Sequential(*layers)
+    proj = 2 * math.pi * torch.from_numpy(x) @ torch.from_numpy(w.B.astype(np.float64)).T
+    feats = torch.cat([torch.sin(proj), torch.cos(proj)], dim=1)
+    (net(feats) * torch.from_numpy(gout)).sum().backward()
+    lins = [m for m in net if isinstance(m, torch.nn.Linear)]
+    for l, lin in enumerate(lins):
+        np.testing.assert_allclose(dW[l], lin.weight.grad.numpy(), rtol=1e-11,
+                                   atol=1e-13 * np.abs(dW[l]).max(), err_msg=f"W{l}")
+        np.testing.assert_allclose(db[l], lin.bias.grad.numpy(), rtol=1e-11,
+                                   atol=1e-13 * np.abs(db[l]).max(), err_msg=f"b{l}")
+
+
 def test_mlp_render_zero_network_equals_grid_render(orc):
     p = synth.config_small(6).replace(nx=12, ny=12, n_samples=40)
     w = synth.mlp_weights(1, width=16, hidden=2)
