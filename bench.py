@@ -34,9 +34,20 @@ sys.path.insert(0, ROOT)
 METRIC = "G sample*channel evals/s (forward render)"
 UNIT = "Gevals/s"
 L2_BYTES = 126 * 2 ** 20
-# B300 FP32 pipe model (measured: 128 FFMA/clk/SM, 32 MUFU.EX2/clk/SM); the algorithmic
-# per-evaluation work is 8 FP32 operations + 2 EX2, i.e. 16 evaluations/clk/SM on both pipes.
-EVALS_PER_CLK_SM = 16.0
+# B300 pipe model (measured: 128 FFMA lanes/clk/SM, 32 MUFU.EX2/clk/SM). Per forward
+# evaluation 6 FP32 operations (issued packed, two channels per instruction) + 2 EX2.
+EVALS_PER_CLK_SM = 16.0      # forward: 2 MUFU.EX2 per eval at 32/clk/SM (FP32 ops packed x2)
+ADJ_EVALS_PER_CLK_SM = 128.0 / 24.0  # adjoint: 24 FP32 ops per eval at 128/clk/SM (5 EX2: below)
+try:
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as _f:
+        PEAKS = json.load(_f)
+except (OSError, ValueError):
+    PEAKS = {}
+# FLOPs of one network evaluation on the tensor cores (64 -> 4 x 128 -> 16 padded outputs)
+MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 16)
+# DRAM bytes of one forward launch on the observation-scale workload (ncu, dram__bytes_read +
+# dram__bytes_write; the cube stays in L2 at the end of the launch)
+FWD_DRAM_BYTES = 1_401_856 + 41_728
 N_SM = 148
 SM_MAX_MHZ = 2032.0
 
@@ -197,7 +208,8 @@ def serving_leg(dev, n=256, rate_hz=200.0, budget=40 << 30, max_inflight=8):
 def neural_leg(dev, flush, reps=5):
     """Neural-field workload (512x512 px, 128 channels, 256 samples): tensor-core network
     with FP16 and BF16 operands, the FP32 network (cuBLAS, no TF32) driving the same march, and
-    the grid-field march alone."""
+    the grid-field march alone; then forward plus adjoint through the march and the network
+    (loss sum (I - I*)^2 against a fixed target) with FP16 and BF16 operands."""
     import torch
     from paper_2509_03623_b300 import _rt, neural, synth
     p = synth.config_neural(0)
@@ -205,14 +217,41 @@ def neural_leg(dev, flush, reps=5):
     dd = _rt.DeviceDisk(p, dev)
     cube = torch.empty((p.nch, p.ny, p.nx), dtype=torch.float32, device=dev)
     nets = {k: _rt.DeviceMLP(w, dev, precision=k) for k in ("f16", "bf16")}
+    tgt = (_rt.rt_render_mlp(p, dd, nets["f16"]) * 1.05).contiguous()
     runs = {
         "grid_only": lambda: _rt.rt_render(p, dd, cube),
         "mlp_f16": lambda: _rt.rt_render_mlp(p, dd, nets["f16"], cube),
         "mlp_bf16": lambda: _rt.rt_render_mlp(p, dd, nets["bf16"], cube),
         "mlp_fp32": lambda: neural.render_mlp_fp32(p, dd, nets["f16"], cube),
+        "fwd_adjoint_f16": lambda: _rt.rt_render_mlp_adjoint(p, dd, nets["f16"], target=tgt,
+                                                             cube_out=cube),
+        "fwd_adjoint_bf16": lambda: _rt.rt_render_mlp_adjoint(p, dd, nets["bf16"], target=tgt,
+                                                              cube_out=cube),
     }
     out = {"workload": p.name, "nominal_evals": p.evals,
            "mlp_samples": p.nx * p.ny * p.n_samples, "unit": UNIT}
+    # the network kernel alone on as many points as the render has samples (tensor roofline)
+    nmlp = p.nx * p.ny * p.n_samples
+    xy = torch.rand((nmlp, 2), device=dev)
+    yo = torch.empty((nmlp, 4), device=dev)
+    _rt.rt_mlp_eval(nets["f16"], xy, yo)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        _rt.rt_mlp_eval(nets["f16"], xy, yo)
+    e1.record()
+    torch.cuda.synchronize()
+    mlp_ms = e0.elapsed_time(e1) / reps
+    tf = nmlp * MLP_FLOP / (mlp_ms * 1e-3) / 1e12
+    out["mlp_kernel_roofline"] = {
+        "bound": "tensor", "achieved": tf, "peak": PEAKS.get("bf16_tflops", 1800.0),
+        "unit": "TFLOP/s", "frac": tf / PEAKS.get("bf16_tflops", 1800.0), "traffic": None,
+        "ms": mlp_ms, "points": nmlp,
+        "note": "rt_mlp_eval (FP16 operands, FP32 accumulate) on random inputs; FLOPs "
+                "2 x (64x128 + 3x128x128 + 128x16) per point; peak = measured bf16 burst "
+                "(FP16 has the same dense rate)"}
+    del xy, yo
     for name, fn in runs.items():
         fn()
         torch.cuda.synchronize()
@@ -354,11 +393,12 @@ def run_ours(args):
                                     "l2": "flushed between timed steps (256 MB write)",
                                     "parallelism": f"independent disks x{world}"}),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": FWD_DRAM_BYTES,
                          "note": "achieved = executed sample-channel evals (samples inside the "
                                  "gas grid) / kernel time; peak = 16 evals/clk/SM x 148 SMs x "
-                                 "2032 MHz (8 FP32 + 2 EX2 per eval on 128 FFMA + 32 EX2 "
-                                 "lanes/clk/SM, measured)",
+                                 "2032 MHz: 2 MUFU.EX2 per eval at 32 lanes/clk/SM (measured), "
+                                 "the 6 FP32 ops per eval issued as 3 packed FFMA2-class "
+                                 "instructions; traffic = DRAM bytes of one launch (ncu)",
                          "frac_at_measured_clock": achieved / (peak * f_mhz / SM_MAX_MHZ)},
             "e2e": {"value": evals / (e2e_max * 1e-3) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -366,7 +406,20 @@ def run_ours(args):
             "fwd_adjoint": {"value": evals / (adj_max * 1e-3) / 1e9, "unit": UNIT,
                             "ms_per_step": adj_max, "steps": adj_steps,
                             "note": "fused forward + reverse march with FP64 node gradients, "
-                                    "loss sum (I - I*)^2 formed in the kernel; nominal evals"},
+                                    "loss sum (I - I*)^2 formed in the kernel; nominal evals",
+                            "roofline": {
+                                "bound": "alu",
+                                "achieved": executed / (adj_ms * 1e-3) / 1e9,
+                                "peak": ADJ_EVALS_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e9,
+                                "unit": UNIT,
+                                "frac": (executed / (adj_ms * 1e-3) / 1e9)
+                                        / (ADJ_EVALS_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e9),
+                                "traffic": None,
+                                "note": "executed evals / step time (memsets, march kernel, "
+                                        "gradient-copy sums); peak: 24 FP32 ops per eval "
+                                        "(forward 6, batch-start recompute 3, reverse 15) at 128 "
+                                        "lanes/clk/SM, the binding pipe (5 MUFU.EX2 per eval need "
+                                        "0.156 of 0.1875 clk)"}},
             "clocks": clocks,
         }
         if world == 1 and not args.no_serving:
