@@ -435,6 +435,42 @@ def run_ours(args):
     return 0
 
 
+def run_profile(args):
+    """Run one workload a few times and exit (for an ncu capture; prints no bench line)."""
+    import torch
+    from paper_2509_03623_b300 import _rt, build, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    name = args.profile
+    if name in ("forward", "adjoint"):
+        p = workload(0)
+    elif name == "small_adjoint":
+        p = synth.config_small(0)
+    else:
+        px = args.profile_px
+        p = synth.config_neural(0).replace(nx=px, ny=px)
+    dd = _rt.DeviceDisk(p, dev)
+    if name in ("neural", "neural_adjoint", "mlp_eval"):
+        net = _rt.DeviceMLP(synth.mlp_weights(7), dev, precision="f16")
+    cube = _rt.rt_render(p, dd) if name not in ("neural", "neural_adjoint", "mlp_eval") else \
+        _rt.rt_render_mlp(p, dd, net)
+    tgt = (cube * 1.05).contiguous()
+    xy = torch.rand((p.nx * p.ny * p.n_samples, 2), device=dev) if name == "mlp_eval" else None
+    for _ in range(args.profile_reps):
+        if name == "forward":
+            _rt.rt_render(p, dd, cube)
+        elif name in ("adjoint", "small_adjoint"):
+            _rt.rt_render_adjoint(p, dd, target=tgt, cube_out=None)
+        elif name == "neural":
+            _rt.rt_render_mlp(p, dd, net, cube)
+        elif name == "neural_adjoint":
+            _rt.rt_render_mlp_adjoint(p, dd, net, target=tgt, cube_out=None)
+        else:
+            _rt.rt_mlp_eval(net, xy)
+    torch.cuda.synchronize()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -444,7 +480,16 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--profile", default=None,
+                    choices=["forward", "adjoint", "small_adjoint", "neural", "neural_adjoint",
+                             "mlp_eval"],
+                    help="run one workload --profile-reps times for an ncu capture and exit")
+    ap.add_argument("--profile-reps", type=int, default=3)
+    ap.add_argument("--profile-px", type=int, default=128,
+                    help="image size of the neural-field workload in --profile mode")
     args = ap.parse_args()
+    if args.profile:
+        return run_profile(args)
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
