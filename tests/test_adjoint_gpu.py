@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2509_03623_b300 import synth
+from tests.cubecheck import assert_cube_close
 from tests.test_forward_gpu import rt  # noqa: F401  (module fixture)
 
 pytestmark = pytest.mark.gpu
@@ -58,8 +59,12 @@ def test_adjoint_vs_oracle_adjoint(rt, orc, seed):
     torch.cuda.synchronize()
     e = assert_grads_close(to_np(g), g_ref, label=f"seed {seed}")
     print(f"adjoint seed {seed}: {e}")
+    # the adjoint's own forward pass and the forward kernel are two FP32 evaluations of the
+    # same march (different lane layouts and operation order): both are held to the parity
+    # criterion against the oracle, and to it against each other
     fwd = rt.rt_render(p).cpu().numpy()
-    np.testing.assert_allclose(cube.cpu().numpy(), fwd, rtol=2e-6, atol=1e-7 * np.abs(fwd).max())
+    assert_cube_close(cube.cpu().numpy(), fwd, label="adjoint cube vs forward")
+    assert_cube_close(cube.cpu().numpy(), ref_cube, label="adjoint cube vs oracle")
 
 
 def test_fused_loss_target_mode(rt, orc):
