@@ -355,13 +355,16 @@ extern "C" int rt_render_mlp(const rt_grid *grid, const rt_fields *fields, const
   if (rc == RT_OK && npix * P->nch > 0) {
     cudaStream_t st = (cudaStream_t)stream;
     size_t mod_bytes = (size_t)npix * P->n_samples * sizeof(float4);
-    size_t bytes = mod_bytes + ray_buffer_bytes(npix);
+    size_t ray_bytes = (ray_buffer_bytes(npix) + 255) & ~(size_t)255;
+    size_t list_bytes = sample_list_bytes(npix, P->n_samples);
+    size_t bytes = mod_bytes + ray_bytes + list_bytes;
     float4 *mod = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&mod, bytes, st);
     if (e != cudaSuccess) {
       rc = set_error(RT_ENOMEM, "modulation buffer (%zu bytes): %s", bytes, cudaGetErrorString(e));
     } else {
-      rc = launch_mlp_rays(mlp, *P, mod, reinterpret_cast<char *>(mod) + mod_bytes, st);
+      char *rays = reinterpret_cast<char *>(mod) + mod_bytes;
+      rc = launch_mlp_rays(mlp, *P, mod, rays, list_bytes ? rays + ray_bytes : nullptr, st);
       if (rc == RT_OK) {
         P->mod = mod;
         P->h_scale = (float)mlp->h_scale;
@@ -394,8 +397,9 @@ extern "C" int rt_render_mlp_adjoint(const rt_grid *grid, const rt_fields *field
     // one buffer: network outputs, dL/d(outputs), ray setups, backward scratch, gradient scale
     const size_t mod_bytes = (size_t)ns * sizeof(float4);
     const size_t ray_bytes = (ray_buffer_bytes(npix) + 255) & ~(size_t)255;
+    const size_t list_bytes = (sample_list_bytes(npix, P->n_samples) + 255) & ~(size_t)255;
     const size_t spill_bytes = mlp_bwd_scratch_bytes(ns);
-    const size_t bytes = 2 * mod_bytes + ray_bytes + spill_bytes + 256;
+    const size_t bytes = 2 * mod_bytes + ray_bytes + list_bytes + spill_bytes + 256;
     char *buf = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&buf, bytes, st);
     if (e != cudaSuccess) {
@@ -405,18 +409,21 @@ extern "C" int rt_render_mlp_adjoint(const rt_grid *grid, const rt_fields *field
       float4 *mod = reinterpret_cast<float4 *>(buf);
       float4 *dmod = reinterpret_cast<float4 *>(buf + mod_bytes);
       char *rays = buf + 2 * mod_bytes;
-      char *spill = rays + ray_bytes;
+      char *list = list_bytes ? rays + ray_bytes : nullptr;
+      char *spill = rays + ray_bytes + list_bytes;
       unsigned *dmax = reinterpret_cast<unsigned *>(spill + spill_bytes);
       e = cudaMemsetAsync(dmod, 0, mod_bytes, st);
       if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, sizeof(unsigned), st);
       if (e != cudaSuccess) rc = set_error(RT_ECUDA, "memset: %s", cudaGetErrorString(e));
-      if (rc == RT_OK && ns > 0) rc = launch_mlp_rays(mlp, *P, mod, rays, st);
+      if (rc == RT_OK && ns > 0) rc = launch_mlp_rays(mlp, *P, mod, rays, list, st);
       if (rc == RT_OK) {
         P->mod = ns > 0 ? mod : nullptr;
         P->h_scale = (float)mlp->h_scale;
         rc = launch_adjoint(*P, dL_dcube, target, cube_out, *grads, st, dmod, dmax);
       }
-      if (rc == RT_OK) rc = launch_mlp_bwd_rays(mlp, *P, rays, dmod, dmax, spill, mlp_grads, st);
+      if (rc == RT_OK)
+        rc = launch_mlp_bwd_rays(mlp, *P, rays, ns > 0 ? list : nullptr, dmod, dmax, spill,
+                                 mlp_grads, st);
       cudaFreeAsync(buf, st);
     }
   }

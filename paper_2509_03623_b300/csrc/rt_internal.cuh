@@ -277,14 +277,15 @@ size_t adjoint_scratch_bytes(const MarchParams &P, long long cap_blocks);
 int check_adjoint_args(const MarchParams &P, const float *dL_dcube, const float *target,
                        const rt_grads *grads);
 int launch_mlp_rays(const rt_mlp *m, const MarchParams &P, float4 *mod, void *ray_buf,
-                    cudaStream_t stream);
+                    void *list_buf, cudaStream_t stream);
 size_t ray_buffer_bytes(long long npix);
+size_t sample_list_bytes(long long npix, int n_samples);
 int mlp_validate(const rt_mlp *m);
 int mlp_grads_validate(const rt_mlp_grads *g);
 size_t mlp_bwd_scratch_bytes(long long n);
 int launch_mlp_bwd_rays(const rt_mlp *m, const MarchParams &P, const void *ray_buf,
-                        const float4 *dmod, const unsigned *dmax, void *spill,
-                        const rt_mlp_grads *g, cudaStream_t stream);
+                        const void *list_buf, const float4 *dmod, const unsigned *dmax,
+                        void *spill, const rt_mlp_grads *g, cudaStream_t stream);
 int launch_coords(const MarchParams &P, float2 *xy, cudaStream_t stream);
 int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, double c,
                         double *out, cudaStream_t stream);

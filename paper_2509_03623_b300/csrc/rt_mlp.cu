@@ -252,16 +252,20 @@ __device__ __forceinline__ void features(const float (*Bf)[2], float rh, float z
   }
 }
 
-// Input suppliers: the network inputs of sample s0 + tid of a tile (false when the sample
-// needs no evaluation). Called by every thread of the CTA.
+// Input suppliers: the network inputs of row `tid` of the tile starting at s0 (false when
+// the row needs no evaluation) and the index of its output / output gradient. Called by every
+// thread of the CTA; in_count bounds the rows.
 struct XYInput {
   const float *xy;
   long long n;
 };
 
-__device__ __forceinline__ bool tile_input(const XYInput &in, Ray *, long long s0, int tid,
-                                           float *rh, float *zh, int) {
+__device__ __forceinline__ long long in_count(const XYInput &in, long long n) { return n; }
+
+__device__ __forceinline__ bool tile_input(const XYInput &in, long long s0, int tid, float *rh,
+                                           float *zh, long long *idx) {
   long long s = s0 + tid;
+  *idx = s;
   if (s >= in.n) return false;
   float2 v = reinterpret_cast<const float2 *>(in.xy)[s];
   *rh = v.x;
@@ -287,15 +291,42 @@ __device__ __forceinline__ void sample_coords(const MarchParams &P, const Ray &R
   *zh = c.zr / P.zr_max;
 }
 
-__device__ __forceinline__ bool tile_input(const RayInput &in, Ray *, long long s0, int tid,
-                                           float *rh, float *zh, int) {
+__device__ __forceinline__ long long in_count(const RayInput &in, long long n) { return n; }
+
+__device__ __forceinline__ bool tile_input(const RayInput &in, long long s0, int tid, float *rh,
+                                           float *zh, long long *idx) {
   const MarchParams &P = in.P;
   const long long n = (long long)P.nx * P.ny * P.n_samples;
   long long s = s0 + tid;
+  *idx = s;
   if (s >= n) return false;
   const Ray R = in.rays[s / P.n_samples];
   bool gas;
   sample_coords(P, R, (int)(s % P.n_samples), &gas, rh, zh);
+  return gas;
+}
+
+// Only the samples with gas, in ray order: list[i] = pixel * n_samples + k (built by
+// build_sample_list), *count of them.
+struct ListInput {
+  MarchParams P;
+  const Ray *rays;
+  const unsigned *list;
+  const unsigned *count;
+};
+
+__device__ __forceinline__ long long in_count(const ListInput &in, long long) { return *in.count; }
+
+__device__ __forceinline__ bool tile_input(const ListInput &in, long long s0, int tid, float *rh,
+                                           float *zh, long long *idx) {
+  const long long s = s0 + tid;
+  *idx = 0;
+  if (s >= (long long)*in.count) return false;
+  const unsigned v = in.list[s];
+  const unsigned ns = (unsigned)in.P.n_samples;
+  *idx = v;
+  bool gas;
+  sample_coords(in.P, in.rays[v / ns], (int)(v % ns), &gas, rh, zh);
   return gas;
 }
 
@@ -318,7 +349,6 @@ __global__ void __launch_bounds__(kGT * kTG, 1)
   const int half = (warp >> 2) & 1;               // column half handled by this warp
   const int t = q * 32 + (tid & 31);              // row (= sample) of the tile
   const int gt = tid % kGT;                       // thread index within the group
-  Ray *rays = nullptr;
 
   // ---- one-time setup: weights to the 16-bit core-matrix layout, biases, TMEM, mbarriers ----
   const int nt = blockDim.x;
@@ -362,12 +392,12 @@ __global__ void __launch_bounds__(kGT * kTG, 1)
   // named barrier of the tile group (ids 1, 2; 0 is __syncthreads)
   auto gsync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(1 + tg), "r"(kGT) : "memory"); };
 
-  const long long ntiles = (n + kMlpTile - 1) / kMlpTile;
+  const long long ntiles = (in_count(in, n) + kMlpTile - 1) / kMlpTile;
   for (long long tile = (long long)blockIdx.x * kTG + tg; tile < ntiles;
        tile += (long long)gridDim.x * kTG) {
-    const long long s = tile * kMlpTile + t;
+    long long s;
     float rh = 0.0f, zh = 0.0f;
-    const bool need = tile_input(in, rays, tile * kMlpTile, t, &rh, &zh, tg);
+    const bool need = tile_input(in, tile * kMlpTile, t, &rh, &zh, &s);
     // any sample of the tile needs the network? (group-wide vote through shared memory)
     int any;
     asm volatile(
@@ -501,8 +531,156 @@ static int launch_mlp(const rt_mlp *m, const In &in, float *out, long long n,
                                      : launch_mlp_t<In, true>(m, in, out, n, stream);
 }
 
+// ---- list of the samples with gas (the rows the network needs) ----
+// counts[pix] = samples of ray pix with gas
+__global__ void gas_count_kernel(const __grid_constant__ MarchParams P, const Ray *__restrict__ rays,
+                                 unsigned *__restrict__ counts) {
+  const long long npix = (long long)P.nx * P.ny;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  const Ray R = rays[pix];
+  unsigned c = 0;
+  if (R.hit)
+    for (int k = 0; k < P.n_samples; k++) {
+      bool gas;
+      float rh, zh;
+      sample_coords(P, R, k, &gas, &rh, &zh);
+      c += gas ? 1u : 0u;
+    }
+  counts[pix] = c;
+}
+
+// In-place exclusive scan of 1024-element blocks; block totals to bsum.
+__global__ void scan_block_kernel(unsigned *__restrict__ v, long long n, unsigned *__restrict__ bsum) {
+  __shared__ unsigned warp_tot[32];
+  const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned x = i < n ? v[i] : 0u;
+  unsigned incl = x;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    unsigned t = warp_tot[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_tot[lane] = t;  // inclusive over warps
+  }
+  __syncthreads();
+  const unsigned before = (w > 0 ? warp_tot[w - 1] : 0u) + incl - x;
+  if (i < n) v[i] = before;
+  if (threadIdx.x == 1023) bsum[blockIdx.x] = warp_tot[31];
+}
+
+// Exclusive scan of the nb block totals by one block (chunks of 1024), the grand total to
+// *total; then every element gets its block's offset.
+__global__ void scan_sums_kernel(unsigned *__restrict__ bsum, long long nb, unsigned *__restrict__ total) {
+  __shared__ unsigned warp_tot[32];
+  __shared__ unsigned carry;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (long long b0 = 0; b0 < nb; b0 += 1024) {
+    const long long i = b0 + threadIdx.x;
+    const unsigned x = i < nb ? bsum[i] : 0u;
+    unsigned incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      unsigned t = warp_tot[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const unsigned before = carry + (w > 0 ? warp_tot[w - 1] : 0u) + incl - x;
+    if (i < nb) bsum[i] = before;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_tot[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+// list[offset[pix] + j] = pix * n_samples + k for the j-th sample k of ray pix with gas
+__global__ void gas_fill_kernel(const __grid_constant__ MarchParams P, const Ray *__restrict__ rays,
+                                const unsigned *__restrict__ offsets,
+                                const unsigned *__restrict__ boff, unsigned *__restrict__ list) {
+  const long long npix = (long long)P.nx * P.ny;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  const Ray R = rays[pix];
+  if (!R.hit) return;
+  unsigned o = offsets[pix] + boff[pix / 1024];
+  const unsigned base = (unsigned)(pix * P.n_samples);
+  for (int k = 0; k < P.n_samples; k++) {
+    bool gas;
+    float rh, zh;
+    sample_coords(P, R, k, &gas, &rh, &zh);
+    if (gas) list[o++] = base + (unsigned)k;
+  }
+}
+
+// Bytes of the sample-list buffers for n_pix rays of n_samples (0 when the sample index does
+// not fit 32 bits: the network then runs over every sample).
+size_t sample_list_bytes(long long npix, int n_samples) {
+  const long long ns = npix * n_samples;
+  if (npix <= 0 || ns >= (1LL << 32)) return 0;
+  const long long nb = (npix + 1023) / 1024;
+  return ((size_t)npix + (size_t)nb + 64 + (size_t)ns) * sizeof(unsigned);
+}
+
+struct SampleList {
+  const unsigned *list = nullptr;
+  const unsigned *count = nullptr;
+};
+
+// Layout of the list buffer: counts / offsets [npix], block sums [nb], total (64 words
+// reserved), list [n_pix n_samples].
+static SampleList sample_list_view(const MarchParams &P, const void *buf) {
+  const long long npix = (long long)P.nx * P.ny;
+  const long long nb = (npix + 1023) / 1024;
+  const unsigned *total = reinterpret_cast<const unsigned *>(buf) + npix + nb;
+  SampleList v;
+  v.count = total;
+  v.list = total + 64;
+  return v;
+}
+
+static int build_sample_list(const MarchParams &P, const Ray *rays, void *buf, SampleList *out,
+                             cudaStream_t stream) {
+  const long long npix = (long long)P.nx * P.ny;
+  const long long nb = (npix + 1023) / 1024;
+  unsigned *counts = reinterpret_cast<unsigned *>(buf);
+  unsigned *bsum = counts + npix;
+  unsigned *total = bsum + nb;  // 64 words reserved
+  unsigned *list = total + 64;
+  gas_count_kernel<<<(unsigned)((npix + 127) / 128), 128, 0, stream>>>(P, rays, counts);
+  scan_block_kernel<<<(unsigned)nb, 1024, 0, stream>>>(counts, npix, bsum);
+  scan_sums_kernel<<<1, 1024, 0, stream>>>(bsum, nb, total);
+  gas_fill_kernel<<<(unsigned)((npix + 127) / 128), 128, 0, stream>>>(P, rays, counts, bsum, list);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "sample list: %s", cudaGetErrorString(e));
+  out->list = list;
+  out->count = total;
+  return RT_OK;
+}
+
+// Ray setups, the list of samples with gas (when list_buf is given) and the network outputs
+// of those samples into mod ([pixel][sample] float4; other entries are left untouched).
 int launch_mlp_rays(const rt_mlp *m, const MarchParams &P, float4 *mod, void *ray_buf,
-                    cudaStream_t stream) {
+                    void *list_buf, cudaStream_t stream) {
   long long npix = (long long)P.nx * P.ny;
   long long n = npix * P.n_samples;
   if (n == 0) return RT_OK;
@@ -510,6 +688,17 @@ int launch_mlp_rays(const rt_mlp *m, const MarchParams &P, float4 *mod, void *ra
   rays_kernel<<<(unsigned)((npix + 127) / 128), 128, 0, stream>>>(P, rays);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "ray setup launch: %s", cudaGetErrorString(e));
+  if (list_buf) {
+    SampleList sl;
+    int rc = build_sample_list(P, rays, list_buf, &sl, stream);
+    if (rc != RT_OK) return rc;
+    ListInput in;
+    in.P = P;
+    in.rays = rays;
+    in.list = sl.list;
+    in.count = sl.count;
+    return launch_mlp(m, in, reinterpret_cast<float *>(mod), n, stream);
+  }
   RayInput in;
   in.P = P;
   in.rays = rays;
@@ -700,12 +889,12 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
     return reinterpret_cast<uint4 *>(Z + ((size_t)((L * 2 + c) * 2 + half) * kMlpTile + t) * 32);
   };
 
-  const long long ntiles = (n + kMlpTile - 1) / kMlpTile;
+  const long long ntiles = (in_count(in, n) + kMlpTile - 1) / kMlpTile;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    long long s;
     float rh = 0.0f, zh = 0.0f;
-    const bool need = tile_input(in, nullptr, tile * kMlpTile, t, &rh, &zh, 0);
+    const bool need = tile_input(in, tile * kMlpTile, t, &rh, &zh, &s);
     if (!__syncthreads_or(need)) continue;
-    const long long s = tile * kMlpTile + t;
     float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (need) {
       g = gout[s];
@@ -1030,12 +1219,21 @@ size_t mlp_bwd_scratch_bytes(long long n) { return mlp_spill_bytes(mlp_bwd_block
 // Backward pass over the samples of a render (rays from the forward's pre-pass in ray_buf,
 // per-sample dL/d(outputs) in dmod, their largest magnitude in *dmax).
 int launch_mlp_bwd_rays(const rt_mlp *m, const MarchParams &P, const void *ray_buf,
-                        const float4 *dmod, const unsigned *dmax, void *spill,
-                        const rt_mlp_grads *g, cudaStream_t stream) {
+                        const void *list_buf, const float4 *dmod, const unsigned *dmax,
+                        void *spill, const rt_mlp_grads *g, cudaStream_t stream) {
+  long long n = (long long)P.nx * P.ny * P.n_samples;
+  if (list_buf) {
+    const SampleList sl = sample_list_view(P, list_buf);
+    ListInput in;
+    in.P = P;
+    in.rays = reinterpret_cast<const Ray *>(ray_buf);
+    in.list = sl.list;
+    in.count = sl.count;
+    return launch_mlp_bwd(m, in, dmod, n, dmax, reinterpret_cast<h16 *>(spill), g, stream);
+  }
   RayInput in;
   in.P = P;
   in.rays = reinterpret_cast<const Ray *>(ray_buf);
-  long long n = (long long)P.nx * P.ny * P.n_samples;
   return launch_mlp_bwd(m, in, dmod, n, dmax, reinterpret_cast<h16 *>(spill), g, stream);
 }
 
