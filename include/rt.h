@@ -112,8 +112,12 @@ typedef struct {
 /*
  * rt_render -- forward march (Eq. rt-int / Eq. optical_depth, front to back).
  * Writes the cube [nch][ny][nx] float32 to `cube` (DEVICE, caller-allocated,
- * nch*ny*nx floats). Arithmetic is FP32 (optical depth summed in blocks of samples). No
- * device memory is allocated. Returns RT_OK, RT_EINVAL or RT_ECUDA (launch failure).
+ * nch*ny*nx floats). Arithmetic is FP32 (optical depth summed in blocks of samples). With
+ * equally spaced channels each sample's optical depth is evaluated only in the channel blocks
+ * where kd 2^{-d^2} can reach 2^-40 (d the profile argument; below that a whole ray of
+ * contributions moves a transmittance by less than 1e-9, far below FP32 relevance); the
+ * result is the dense march's. No device memory is allocated. Returns RT_OK, RT_EINVAL or
+ * RT_ECUDA (launch failure).
  */
 int rt_render(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
               const rt_view *view, const rt_line *line, float *cube, void *stream);
@@ -139,6 +143,16 @@ typedef struct {
   double *loss;     /* 1 value: sum over voxels of (cube - target)^2 when a target is given;
                        may be NULL */
 } rt_grads;
+
+/*
+ * rt_render_work -- rt_render that also counts its work into work (DEVICE, 2 x uint64,
+ * overwritten): work[0] = samples with gas whose channel-independent physics was evaluated,
+ * work[1] = sample-channel evaluations computed (after the channel window). For roofline
+ * accounting; the cube is identical to rt_render's. Returns as rt_render.
+ */
+int rt_render_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                   const rt_view *view, const rt_line *line, float *cube,
+                   unsigned long long *work, void *stream);
 
 /*
  * rt_render_adjoint -- forward march plus its reverse-mode gradient (the paper obtains the

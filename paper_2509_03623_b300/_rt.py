@@ -93,6 +93,8 @@ def lib():
             L.rt_render.restype = C.c_int
             L.rt_count_gas_samples.argtypes = base + [C.c_void_p, C.c_void_p]
             L.rt_count_gas_samples.restype = C.c_int
+            L.rt_render_work.argtypes = base + [C.c_void_p, C.c_void_p, C.c_void_p]
+            L.rt_render_work.restype = C.c_int
             L.rt_render_adjoint.argtypes = base + [C.c_void_p, C.c_void_p, C.c_void_p,
                                                    P(rt_grads), C.c_void_p]
             L.rt_render_adjoint.restype = C.c_int
@@ -212,6 +214,22 @@ def _cube_arg(t, shape, name):
     if not t.is_cuda or t.dtype.itemsize != 4 or not t.is_contiguous() or tuple(t.shape) != shape:
         raise ValueError(f"{name} must be a contiguous CUDA float32 tensor of shape {shape}")
     return t
+
+
+def rt_render_work(problem, fields=None, out=None, stream=None):
+    """rt_render plus its work counts: (cube, physics samples with gas, sample-channel
+    evaluations computed after the channel window)."""
+    import torch
+    dd = fields if fields is not None else DeviceDisk(problem)
+    T, n, vt, hlo, hhi = dd.tensors()
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    if out is None:
+        out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=T.device)
+    work = torch.zeros(2, dtype=torch.int64, device=T.device)
+    check(lib().rt_render_work(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                               _ptr(out), _ptr(work), stream_handle(stream)))
+    w = work.cpu().tolist()
+    return out, int(w[0]), int(w[1])
 
 
 def rt_render_adjoint(problem, fields=None, dL_dcube=None, target=None, cube_out=True,

@@ -256,6 +256,30 @@ extern "C" int rt_render(const rt_grid *grid, const rt_fields *fields, const rt_
   return rc;
 }
 
+extern "C" int rt_render_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                              const rt_view *view, const rt_line *line, float *cube,
+                              unsigned long long *work, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params(grid, fields, geom, view, line, P);
+  if (rc == RT_OK && !work) rc = set_error(RT_EINVAL, "null work counters");
+  if (rc == RT_OK) {
+    long long n = (long long)P->nx * P->ny * P->nch;
+    cudaError_t e = cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+      rc = set_error(RT_ECUDA, "memset: %s", cudaGetErrorString(e));
+    } else if (n > 0 && !cube) {
+      rc = set_error(RT_EINVAL, "null cube pointer");
+    } else {
+      P->work = work;
+      rc = launch_forward(*P, cube, (cudaStream_t)stream);
+    }
+  }
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
 extern "C" int rt_count_gas_samples(const rt_grid *grid, const rt_fields *fields,
                                     const rt_geom *geom, const rt_view *view,
                                     const rt_line *line, unsigned long long *count,

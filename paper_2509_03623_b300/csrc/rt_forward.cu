@@ -1,41 +1,51 @@
 // Forward march kernel.
 //
 // Mapping: a warp marches R = 32/LPR neighbouring rays at a time (one work unit); the LPR
-// lanes of a ray split its channels (lane q holds channels q, q+LPR, ... in registers, CPL
-// of them, as CPL/2 pairs). The grid is persistent (one wave) and work units are interleaved
-// over its warps; the double-precision ray setups (chord through the bounding cylinder) of 32
-// rays are computed at once, one per lane, and kept in shared memory. Samples advance in
-// batches of LPR: in the physics phase lane q evaluates the channel-independent physics of
-// sample kb+q of its ray (fields, CO layer, Keplerian velocity, line width, LTE source and
-// opacity) once and publishes it in shared memory; batches without gas on any ray are
-// skipped (warp vote); in the channel phase every lane walks the batch's samples in order
-// (fully unrolled), evaluating the Doppler-shifted Gaussian profile and advancing optical
-// depth, transmittance and intensity front to back (Eq. rt-int with Eq. optical_depth; the
-// source is constant over each segment).
+// lanes of a ray split its channels: lane q holds channels q + LPR j, j < CPL, as CPL/2 pairs,
+// pair m = channels (q + 2m LPR, q + (2m+1) LPR), so that pair m of all lanes covers the
+// contiguous channel block [2m LPR, (2m+2) LPR). The grid is persistent (one wave) and work
+// units are interleaved over its warps; the double-precision ray setups (chord through the
+// bounding cylinder) of 32 rays are computed at once, one per lane, and kept in shared memory.
+// Samples advance in batches of LPR: in the physics phase lane q evaluates the channel-
+// independent physics of sample kb+q of its ray (fields, CO layer, Keplerian velocity, line
+// width, LTE source and opacity) once and publishes it in shared memory; in the channel phase
+// every lane walks the batch's samples in order, evaluating the Doppler-shifted Gaussian
+// profile and advancing optical depth, transmittance and intensity front to back (Eq. rt-int
+// with Eq. optical_depth; the source is constant over each segment).
+//
+// Channel window. A sample's optical depth in channel c is kd 2^{-d_c^2}; it is below 2^-40
+// (so that a whole ray of skipped contributions changes a transmittance by less than 1e-9)
+// once |v_c - v_los| > sqrt(40 + log2 kd) / b. With equally spaced channels each lane turns
+// that velocity window of its sample into a range of (fractional) channel indices in the
+// physics phase, and a warp vote per channel block decides which blocks any sample of the
+// batch reaches; only those blocks are marched (a warp-uniform branch, so the skipped work
+// is not issued). Batches without gas reach no block.
 //
 // Per sample-channel evaluation: 6 FP32 operations, issued as 3 packed two-channel
-// instructions (FFMA2/FMUL2/FADD2), and 2 MUFU.EX2, so the MUFU pipe rather than instruction
-// issue bounds the loop. The optical depth is kept negated (so no negation is needed before
-// the exponential) and summed per batch, then folded into a per-channel base at the end of
-// every batch (blocked summation: about 2 N_s / LPR roundings instead of N_s).
+// instructions (FFMA2/FMUL2/FADD2), and 2 MUFU.EX2. The optical depth is kept negated (so no
+// negation is needed before the exponential) and summed per batch, then folded into a
+// per-channel base at the end of every batch (blocked summation: about 2 N_s / LPR roundings
+// instead of N_s).
 #include <mutex>
 
 #include "rt_internal.cuh"
 
 namespace rtb {
 
-constexpr int kWarps = 4;  // warps per block
+constexpr int kWarps = 4;        // warps per block
+constexpr float kWinLog2 = 40.0f;  // skipped optical depths are below 2^-40 per sample
 
-template <int LPR, int CPL, int SPL>
-__global__ void __launch_bounds__(kWarps * 32)
+// Blocks per SM the register budget is sized for: 6 (at most 85 registers) with 8 channels
+// per lane, 7 with 4.
+template <int LPR, int CPL>
+__global__ void __launch_bounds__(kWarps * 32, CPL == 8 ? 6 : 7)
     march_fwd_kernel(const __grid_constant__ MarchParams P, float *__restrict__ cube) {
   constexpr int R = 32 / LPR;  // rays marched together by one warp (one work unit)
   constexpr int G = 32 / R;    // work units whose ray setups are computed together
-  constexpr int H = CPL / 2;   // channel pairs per lane
-  constexpr int NB = SPL * LPR;  // samples per batch (SPL per lane in the physics phase)
+  constexpr int H = CPL / 2;   // channel pairs per lane = channel blocks
   __shared__ __align__(16) float s_tab[kTabSeg * 4];
   // per sample: {-kd, -kd, S, S} and {b, b, -a, -a} (pairs ready for the packed arithmetic)
-  __shared__ float4 s_ph[kWarps][2][32 * SPL];
+  __shared__ float4 s_ph[kWarps][2][32];
   __shared__ Ray s_ray[kWarps][32];
   for (int i = threadIdx.x; i < kTabSeg * 4; i += blockDim.x) s_tab[i] = P.tab[i];
   __syncthreads();
@@ -48,7 +58,7 @@ __global__ void __launch_bounds__(kWarps * 32)
   float4 *ph0 = s_ph[wib][0];
   float4 *ph1 = s_ph[wib][1];
 
-  // velocities of this lane's channel pairs (q + LPR (2m), q + LPR (2m + 1))
+  // velocities of this lane's channel pairs
   float2 vp[H];
 #pragma unroll
   for (int m = 0; m < H; m++) {
@@ -56,7 +66,14 @@ __global__ void __launch_bounds__(kWarps * 32)
     vp[m] = P.v_uniform ? make_float2(fmaf((float)c0, P.dv, P.v0), fmaf((float)c1, P.dv, P.v0))
                         : make_float2(P.v[min(c0, RT_MAX_CH - 1)], P.v[min(c1, RT_MAX_CH - 1)]);
   }
+  // the window test needs equally spaced channels; otherwise every block is marched
+  // the window is tested in channel-index space; without equal spacing every block is marched
+  const bool windowed = P.v_uniform && P.dv != 0.0f;
+  const float idv = windowed ? 1.0f / P.dv : 0.0f;
   const float2 mone = make_float2(-1.0f, -1.0f);
+  // work counters (lane 0; only with P.work): samples whose physics found gas, channel
+  // evaluations computed (every lane of an active block, LPR samples x 2 channels each)
+  unsigned long long wc_phys = 0, wc_eval = 0;
 
   // Work units u = gw, gw + W, gw + 2W, ... (interleaved over the grid for balance); the
   // setups of G units (32 rays) are computed at once, one ray per lane.
@@ -84,44 +101,61 @@ __global__ void __launch_bounds__(kWarps * 32)
         I[m] = make_float2(0.0f, 0.0f);
       }
       const int nsamp = __any_sync(0xffffffffu, ray.hit) ? P.n_samples : 0;
-      for (int kb = 0; kb < nsamp; kb += NB) {
-        float4 mine[SPL];
-        bool any = false;
-#pragma unroll
-        for (int i = 0; i < SPL; i++) {
-          mine[i] = sample_physics(P, s_tab, ray, kb + i * LPR + q);
-          any = any || mine[i].x > 0.0f;
+      for (int kb = 0; kb < nsamp; kb += LPR) {
+        const float4 mine = sample_physics(P, s_tab, ray, kb + q);
+        // channel window of this sample (empty without gas): fractional channel indices
+        // where kd 2^{-d^2} >= 2^-40
+        float clo = 1.0f, chi = -1.0f;
+        if (mine.x > 0.0f) {
+          const float w2 = kWinLog2 + lg2(mine.x);
+          if (w2 > 0.0f) {
+            const float ib = rcp(mine.z);
+            const float hw = sqrtf(w2) * ib;
+            const float vl = mine.y * ib;  // v_los = a / b
+            const float e0 = (vl - hw - P.v0) * idv, e1 = (vl + hw - P.v0) * idv;
+            clo = fminf(e0, e1) - 0.01f;  // slack for the rounding of the edges
+            chi = fmaxf(e0, e1) + 0.01f;
+          }
         }
-        if (!__any_sync(0xffffffffu, any)) continue;  // no gas in this batch
+        unsigned act = 0;
+        if (windowed) {
 #pragma unroll
-        for (int i = 0; i < SPL; i++) {
-          const int o = rr * NB + i * LPR + q;
-          ph0[o] = make_float4(-mine[i].x, -mine[i].x, mine[i].w, mine[i].w);
-          ph1[o] = make_float4(mine[i].z, mine[i].z, -mine[i].y, -mine[i].y);
+          for (int m = 0; m < H; m++)
+            if (__any_sync(0xffffffffu, chi >= (float)(2 * m * LPR) &&
+                                            clo <= (float)((2 * m + 2) * LPR - 1)))
+              act |= 1u << m;
+        } else if (__any_sync(0xffffffffu, mine.x > 0.0f)) {
+          act = (1u << H) - 1;
         }
+        if (P.work) {
+          const unsigned gl = __ballot_sync(0xffffffffu, mine.x > 0.0f);
+          wc_phys += __popc(gl);
+          wc_eval += (unsigned long long)__popc(act) * 64 * LPR;
+        }
+        if (!act) continue;  // no channel of any ray reached in this batch
+        ph0[lane] = make_float4(-mine.x, -mine.x, mine.w, mine.w);
+        ph1[lane] = make_float4(mine.z, mine.z, -mine.y, -mine.y);
         __syncwarp();
-        // every sample of the batch in order; samples without gas are exact no-ops
 #pragma unroll
-        for (int t = 0; t < NB; t++) {
-          const float4 p0 = ph0[rr * NB + t];  // -kd, -kd, S, S of sample kb+t of this ray
-          const float4 p1 = ph1[rr * NB + t];  // b, b, -a, -a
-          const float2 nkd = make_float2(p0.x, p0.y), S = make_float2(p0.z, p0.w);
-          const float2 b = make_float2(p1.x, p1.y), na = make_float2(p1.z, p1.w);
+        for (int m = 0; m < H; m++) {
+          if (!(act & (1u << m))) continue;  // warp-uniform: block m outside every window
+          // every sample of the batch in order; samples without gas are exact no-ops
 #pragma unroll
-          for (int m = 0; m < H; m++) {
+          for (int t = 0; t < LPR; t++) {
+            const float4 p0 = ph0[rr * LPR + t];  // -kd, -kd, S, S of sample kb+t of this ray
+            const float4 p1 = ph1[rr * LPR + t];  // b, b, -a, -a
+            const float2 nkd = make_float2(p0.x, p0.y), S = make_float2(p0.z, p0.w);
+            const float2 b = make_float2(p1.x, p1.y), na = make_float2(p1.z, p1.w);
             const float2 d = __ffma2_rn(vp[m], b, na);  // (v_c - v_los) / alpha (scaled)
             const float2 d2 = __fmul2_rn(d, d);
-            const float2 g = make_float2(ex2(-d2.x), ex2(-d2.y));
-            nl[m] = __ffma2_rn(nkd, g, nl[m]);
+            const float2 gp = make_float2(ex2(-d2.x), ex2(-d2.y));
+            nl[m] = __ffma2_rn(nkd, gp, nl[m]);
             const float2 nt = __fadd2_rn(nb[m], nl[m]);
             const float2 Tn = make_float2(ex2(nt.x), ex2(nt.y));
             const float2 df = __ffma2_rn(Tn, mone, Tr[m]);  // T_k - T_{k+1}
             I[m] = __ffma2_rn(S, df, I[m]);
             Tr[m] = Tn;
           }
-        }
-#pragma unroll
-        for (int m = 0; m < H; m++) {
           nb[m] = __fadd2_rn(nb[m], nl[m]);
           nl[m] = make_float2(0.0f, 0.0f);
         }
@@ -136,6 +170,10 @@ __global__ void __launch_bounds__(kWarps * 32)
         }
       }
     }
+  }
+  if (P.work && lane == 0) {
+    atomicAdd(P.work, wc_phys);
+    atomicAdd(P.work + 1, wc_eval);
   }
 }
 
@@ -170,7 +208,7 @@ int resident_blocks(const void *kernel, int threads) {
 
 template <int LPR, int CPL>
 static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
-  auto kern = march_fwd_kernel<LPR, CPL, 1>;
+  auto kern = march_fwd_kernel<LPR, CPL>;
   long long npix = (long long)P.nx * P.ny;
   long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
   long long need = (units + kWarps - 1) / kWarps;
@@ -179,9 +217,9 @@ static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
   kern<<<(unsigned)blocks, kWarps * 32, 0, stream>>>(P, cube);
 }
 
-// Channels per lane (4, or 8 above 64 channels) and lanes per ray (power of two).
+// Channels per lane (4, or 8 from 32 channels up) and lanes per ray (power of two).
 void lane_layout(int nch, int *lpr, int *cpl) {
-  int c = nch > 64 ? 8 : 4;
+  int c = nch >= 32 ? 8 : 4;
   int need = (nch + c - 1) / c, l = 1;
   while (l < need) l *= 2;
   *lpr = l;
@@ -195,10 +233,11 @@ int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream) {
   lane_layout(P.nch, &LPR, &CPL);
   if (CPL == 8) {
     if (LPR == 32) launch_t<32, 8>(P, cube, stream);
-    else launch_t<16, 8>(P, cube, stream);
+    else if (LPR == 16) launch_t<16, 8>(P, cube, stream);
+    else if (LPR == 8) launch_t<8, 8>(P, cube, stream);
+    else launch_t<4, 8>(P, cube, stream);
   } else {
-    if (LPR == 16) launch_t<16, 4>(P, cube, stream);
-    else if (LPR == 8) launch_t<8, 4>(P, cube, stream);
+    if (LPR == 8) launch_t<8, 4>(P, cube, stream);
     else if (LPR == 4) launch_t<4, 4>(P, cube, stream);
     else if (LPR == 2) launch_t<2, 4>(P, cube, stream);
     else launch_t<1, 4>(P, cube, stream);

@@ -45,6 +45,9 @@ struct MarchParams {
   // h_lo + h_scale o2, h_hi + h_scale o3; nullptr for grid fields alone
   const float4 *mod;
   float h_scale;
+  // optional work counters of the forward kernel (device, 2 x u64): samples with gas whose
+  // physics was evaluated, channel evaluations computed; nullptr for none
+  unsigned long long *work;
   float v[RT_MAX_CH];
   float tab[kTabSeg * 4];
 };

@@ -125,3 +125,18 @@ def test_observation_scale_sampled_pixels(rt, orc):
         raise AssertionError(f"max rel {rel.max():.3e}; worst (pixel, channel, I/peak, rel): "
                              f"{info}")
     assert (np.abs(got - ref)[~big] <= 3e-7 * peak).all()
+
+
+def test_render_work_counts_and_identical_cube(rt):
+    """rt_render_work: same cube as rt_render, physics count = samples with gas, computed
+    evaluations within (0, dense count of the batches)."""
+    import torch
+    p = synth.config_small(2)
+    dd = rt.DeviceDisk(p)
+    a = rt.rt_render(p, dd)
+    b, phys, comp = rt.rt_render_work(p, dd)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    gas = rt.rt_count_gas_samples(p, dd)
+    assert 0 < phys <= gas
+    assert 0 < comp <= p.nx * p.ny * p.n_samples * 2 * p.nch
