@@ -239,6 +239,35 @@ __global__ void sum_copies_kernel(const double *__restrict__ cop, int k, long lo
   }
 }
 
+// Channel window (as in the forward march): slot j of every lane is the channel block
+// [LPR j, LPR j + LPR); bit j is set when some sample of the warp's batch has
+// kd 2^{-d^2} >= 2^-40 in a channel of the block. Without equally spaced channels every block
+// of a batch with gas is set. Skipped optical depths move a transmittance by less than 1e-9
+// over a whole ray, and their gradient terms are smaller than the kept ones by 2^-40.
+template <int LPR, int CPL>
+__device__ __forceinline__ unsigned adj_window(const MarchParams &P, const float4 &mine,
+                                               bool windowed, float idv) {
+  if (!windowed) return __any_sync(0xffffffffu, mine.x > 0.0f) ? (1u << CPL) - 1 : 0u;
+  float clo = 1.0f, chi = -1.0f;
+  if (mine.x > 0.0f) {
+    const float w2 = 40.0f + lg2(mine.x);
+    if (w2 > 0.0f) {
+      const float ib = rcp(mine.z);
+      const float hw = sqrtf(w2) * ib;
+      const float vl = mine.y * ib;  // v_los = a / b
+      const float e0 = (vl - hw - P.v0) * idv, e1 = (vl + hw - P.v0) * idv;
+      clo = fminf(e0, e1) - 0.01f;
+      chi = fmaxf(e0, e1) + 0.01f;
+    }
+  }
+  unsigned act = 0;
+#pragma unroll
+  for (int j = 0; j < CPL; j++)
+    if (__any_sync(0xffffffffu, chi >= (float)(LPR * j) && clo <= (float)(LPR * j + LPR - 1)))
+      act |= 1u << j;
+  return act;
+}
+
 template <int LPR, int CPL, bool UNIF>
 __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
     march_adj_kernel(const __grid_constant__ MarchParams P, const float *__restrict__ dLdc,
@@ -276,6 +305,8 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
     vc[j] = UNIF ? fmaf((float)(q + LPR * j), P.dv, P.v0) : P.v[min(q + LPR * j, RT_MAX_CH - 1)];
   const float vq = P.v0 + (float)q * P.dv;
   const float dvs = (float)LPR * P.dv;
+  const bool windowed = UNIF && P.dv != 0.0f;
+  const float idv = windowed ? 1.0f / P.dv : 0.0f;
   const float S_bg = P.I0 / P.out_scale;  // background in internal intensity units
   double loss = 0.0;
   float dmx = 0.0f;  // largest |dL/d(network output)| this lane wrote
@@ -313,7 +344,8 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
           for (int j = 0; j < CPL; j++) ck[((kb / kSeg) * CPL + j) * 32 + lane] = tb[j];
         }
         const float4 mine = sample_physics(P, s_tab, ray, kb + q);
-        if (!__any_sync(0xffffffffu, mine.x > 0.0f)) continue;
+        const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
+        if (!act) continue;
         ph[lane] = mine;
         __syncwarp();
 #pragma unroll 4
@@ -322,6 +354,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
           const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
 #pragma unroll
           for (int j = 0; j < CPL; j++) {
+            if (!(act & (1u << j))) continue;  // warp-uniform
             float d = UNIF ? fmaf((float)j, db, dc) : fmaf(vc[j], p.z, -p.y);
             tl[j] = fmaf(p.x, ex2(d * -d), tl[j]);
             float Tn = ex2(-tb[j] - tl[j]);
@@ -376,7 +409,8 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
 #pragma unroll
           for (int j = 0; j < CPL; j++) bs[(b * CPL + j) * 32 + lane] = tbs[j];
           const float4 mine = sample_physics(P, s_tab, ray, k0 + b * LPR + q);
-          if (!__any_sync(0xffffffffu, mine.x > 0.0f)) continue;
+          const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
+          if (!act) continue;
           ph[lane] = mine;
           __syncwarp();
 #pragma unroll 4
@@ -385,6 +419,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
 #pragma unroll
             for (int j = 0; j < CPL; j++) {
+              if (!(act & (1u << j))) continue;  // warp-uniform
               const float d = UNIF ? fmaf((float)j, db, dc) : fmaf(vc[j], p.z, -p.y);
               tbs[j] = fmaf(p.x, ex2(d * -d), tbs[j]);
             }
@@ -399,6 +434,8 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
           const int kb = k0 + b * LPR;
           const float4 mine = physics_jac(P, s_tab, ray, kb + q, Jl);
           if (!__any_sync(0xffffffffu, mine.z > 0.0f)) continue;  // no gas in the batch
+          const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
+          const float Sbefore = Snext;
           ph[lane] = mine;
           float cur[CPL], Tn[CPL];
 #pragma unroll
@@ -417,6 +454,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
             for (int j = 0; j < CPL; j++) {
+              if (!(act & (1u << j))) continue;  // warp-uniform
               const float d = UNIF ? fmaf((float)j, db, dc) : fmaf(vc[j], p.z, -p.y);
               const float d2 = d * d;
               const float gg = ex2(-d2);
@@ -437,6 +475,11 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             }
             part[t][lane ^ (t & 7)] = acc;
           }
+          // blocks outside every window: T is constant over the batch, so the suffix sums
+          // advance by T (S before the batch - S of its first sample with gas)
+#pragma unroll
+          for (int j = 0; j < CPL; j++)
+            if (!(act & (1u << j))) A[j] = fmaf(Sbefore - Snext, Tn[j], A[j]);
           __syncwarp();
           float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll 8
