@@ -164,14 +164,19 @@ int rt_render_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *
  *             dL/dcube = 2 (cube - target) is formed in the kernel (the loss value goes to
  *             grads->loss if non-NULL).
  * cube_out (DEVICE, may be NULL) receives the rendered cube (same values as rt_render up to
- * FP32 rounding). Gradients w.r.t. every node of T, n_H2, v_turb and both surfaces are
- * accumulated in FP64 and overwrite the arrays. The call allocates and frees one device
- * scratch buffer on `stream` (stream-ordered, cudaMallocAsync) holding the optical-depth
- * checkpoints (every 64 samples; the reverse march recomputes everything else) and up to 32
- * replicated copies of the node-gradient arrays (at most 32 MiB) plus up to 128 of the
- * surface-gradient arrays, summed in FP64 into the outputs at the end: FP64 atomics on one
+ * FP32 rounding). Gradients w.r.t. every node of T, n_H2, v_turb and both surfaces
+ * overwrite the FP64 arrays. The call allocates and frees one device scratch buffer on
+ * `stream` (stream-ordered, cudaMallocAsync) holding the optical-depth checkpoints (every 64
+ * samples; the reverse march recomputes everything else) and up to 32 replicated FP32
+ * copies of the node gradients (at most 32 MiB, {dT, dn, dvt} interleaved per node) plus up
+ * to 128 of the surface gradients: each block of the kernel reduces into one copy, and the
+ * copies are summed in FP64, in a fixed order, into the outputs at the end. Atomics on one
  * address are applied one after another, and without the copies the surface entries, which
- * every sample at a given radius updates, serialize the kernel.
+ * every sample at a given radius updates, serialize the kernel. Each copy entry sums a few
+ * hundred contributions in FP32 in an order the device does not fix, so repeated calls agree
+ * to about 1e-7 of the largest gradient, not bit for bit (the cube is reproducible bit for
+ * bit, the loss to FP64 rounding). Where no copies are used, contributions go straight into the outputs as
+ * FP64 atomics.
  * Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
  */
 int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
@@ -197,8 +202,9 @@ int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geo
  *     host threads) race on the array: serialize them.
  *   - Checkpoints get at most 12 MiB of the array. When that cannot hold checkpoints for a
  *     full grid, fewer blocks are launched; where fewer gradient copies fit (or none: then
- *     the kernel adds straight into the output arrays), the FP64 sums run in another order.
- *     Same results, lower throughput. A problem whose single block needs more than 12 MiB
+ *     the kernel adds straight into the FP64 output arrays), the sums run in another order.
+ *     Same results up to that rounding (about 1e-7 of the largest gradient), lower
+ *     throughput. A problem whose single block needs more than 12 MiB
  *     of checkpoints (above about 196,000 samples per ray at the earliest) is rejected with
  *     RT_EINVAL and a message naming the limit.
  * Returns RT_OK, RT_EINVAL or RT_ECUDA.

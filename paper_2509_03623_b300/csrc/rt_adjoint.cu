@@ -154,12 +154,78 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   return out;
 }
 
+// Replicated gradient accumulators. Thousands of samples land on every node (and all samples
+// of a radius on the same two surface entries), and atomics on one address are applied one
+// after another; block b therefore accumulates into copy b % k and a final pass sums the
+// copies in FP64 in a fixed order. A copy interleaves the node fields as float4
+// {dT, dn, dvt, 0} and the surface entries as float2 {dh_lo, dh_hi}, so one sample adds to
+// the grid with four 16-byte reductions and to the surfaces with two 8-byte ones (FP32 sums
+// within a copy: a few hundred terms each, against 16 FP64 atomics whose FP32-to-FP64
+// conversions run on the narrow FP64 pipe). g == nullptr (or h == nullptr) means the block
+// adds straight into the caller's FP64 arrays.
+struct GradCopies {
+  float4 *g;  // kg copies of [nr * nz] {dT, dn, dvt, 0}, gstride float4 apart
+  float2 *h;  // kh copies of [nr] {dh_lo, dh_hi}, hstride float2 apart
+  long long gstride, hstride;
+  int kg, kh;
+};
+
+// Where one block's gradient contributions go.
+struct GradSink {
+  rt_grads G;  // caller's FP64 arrays (used where the copies below are absent)
+  float4 *g;   // this block's grid copy, or nullptr
+  float2 *h;   // this block's surface copy, or nullptr
+};
+
+__device__ __forceinline__ GradSink block_sink(const rt_grads &G, const GradCopies &C) {
+  GradSink S;
+  S.G = G;
+  S.g = C.g ? C.g + (long long)(blockIdx.x % C.kg) * C.gstride : nullptr;
+  S.h = C.h ? C.h + (long long)(blockIdx.x % C.kh) * C.hstride : nullptr;
+  return S;
+}
+
+// Sums of the copies in FP64, in copy order:
+//   grid:    dT[i], dn[i], dvt[i] = sum_c cop[c][i].{x, y, z}
+//   surface: dh_lo[i], dh_hi[i]   = sum_c cop[c][i].{x, y}
+__global__ void sum_grid_copies_kernel(const float4 *__restrict__ cop, int k, long long stride,
+                                       long long n, double *dT, double *dn, double *dvt) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int j = 0; j < k; j++) {
+      const float4 v = cop[(long long)j * stride + i];
+      a += v.x;
+      b += v.y;
+      c += v.z;
+    }
+    dT[i] = a;
+    dn[i] = b;
+    dvt[i] = c;
+  }
+}
+
+__global__ void sum_surface_copies_kernel(const float2 *__restrict__ cop, int k, long long stride,
+                                          long long n, double *dlo, double *dhi) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int j = 0; j < k; j++) {
+      const float2 v = cop[(long long)j * stride + i];
+      a += v.x;
+      b += v.y;
+    }
+    dlo[i] = a;
+    dhi[i] = b;
+  }
+}
+
 // Chain rule of one sample from the reduced channel sums (ax, ay, aS; see the file header)
-// and the local derivatives J; node gradients by FP64 atomics, and the gradient with respect
+// and the local derivatives J; node gradients into the block's sink, and the gradient with respect
 // to the four network outputs of the sample when dmod is given (returns its largest
 // magnitude, 0 otherwise).
 __device__ __forceinline__ float scatter_grad(const MarchParams &P, const float *J, float kd,
-                                             float ax, float ay, float aS, const rt_grads &G,
+                                             float ax, float ay, float aS, const GradSink &G,
                                              float4 *dmod) {
   const float gx = -kLn2 * ax;                       // dL/dkd
   const float GB = 2.0f * kLn2 * kLn2 * kd * ay;     // b dL/db (a = v_los b included)
@@ -181,62 +247,28 @@ __device__ __forceinline__ float scatter_grad(const MarchParams &P, const float 
   const int nr = P.nr;
   const int idx[4] = {i00, i00 + 1, i00 + nr, i00 + nr + 1};
   const float w[4] = {(1.0f - fr) * (1.0f - fz), fr * (1.0f - fz), (1.0f - fr) * fz, fr * fz};
+  if (G.g) {
 #pragma unroll
-  for (int a = 0; a < 4; a++) {
-    atomicAdd(G.dT + idx[a], (double)(dT * w[a]));
-    atomicAdd(G.dn + idx[a], (double)(dn * w[a]));
-    atomicAdd(G.dvt + idx[a], (double)(gv * w[a]));
+    for (int a = 0; a < 4; a++)
+      atomicAdd(G.g + idx[a], make_float4(dT * w[a], dn * w[a], gv * w[a], 0.0f));
+  } else {
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      atomicAdd(G.G.dT + idx[a], (double)(dT * w[a]));
+      atomicAdd(G.G.dn + idx[a], (double)(dn * w[a]));
+      atomicAdd(G.G.dvt + idx[a], (double)(gv * w[a]));
+    }
   }
-  atomicAdd(G.dh_lo + i0, (double)(gl * (1.0f - fr)));
-  atomicAdd(G.dh_lo + i0 + 1, (double)(gl * fr));
-  atomicAdd(G.dh_hi + i0, (double)(gh * (1.0f - fr)));
-  atomicAdd(G.dh_hi + i0 + 1, (double)(gh * fr));
+  if (G.h) {
+    atomicAdd(G.h + i0, make_float2(gl * (1.0f - fr), gh * (1.0f - fr)));
+    atomicAdd(G.h + i0 + 1, make_float2(gl * fr, gh * fr));
+  } else {
+    atomicAdd(G.G.dh_lo + i0, (double)(gl * (1.0f - fr)));
+    atomicAdd(G.G.dh_lo + i0 + 1, (double)(gl * fr));
+    atomicAdd(G.G.dh_hi + i0, (double)(gh * (1.0f - fr)));
+    atomicAdd(G.G.dh_hi + i0 + 1, (double)(gh * fr));
+  }
   return dm;
-}
-
-// Replicated FP64 gradient accumulators. Thousands of samples land on every node (and all
-// samples of a radius on the same two surface entries), and FP64 atomics on one address are
-// applied one after another; block b therefore accumulates into copy b % k of each array and
-// a final pass sums the copies in FP64. g == nullptr (or h == nullptr) means the block adds
-// straight into the caller's arrays.
-struct GradCopies {
-  double *g;  // kg copies of [dT | dn | dvt], gstride doubles apart
-  double *h;  // kh copies of [dh_lo | dh_hi], hstride doubles apart
-  long long gstride, hstride;
-  int kg, kh;
-};
-
-__device__ __forceinline__ rt_grads block_sink(const MarchParams &P, const rt_grads &G,
-                                               const GradCopies &C) {
-  rt_grads S = G;
-  if (C.g) {
-    double *b = C.g + (long long)(blockIdx.x % C.kg) * C.gstride;
-    const long long m = (long long)P.nr * P.nz;
-    S.dT = b;
-    S.dn = b + m;
-    S.dvt = b + 2 * m;
-  }
-  if (C.h) {
-    double *b = C.h + (long long)(blockIdx.x % C.kh) * C.hstride;
-    S.dh_lo = b;
-    S.dh_hi = b + P.nr;
-  }
-  return S;
-}
-
-// out_{i / n_each}[i % n_each] = sum over the k copies of element i (fixed order, FP64).
-__global__ void sum_copies_kernel(const double *__restrict__ cop, int k, long long stride,
-                                  long long n_each, int nout, double *o0, double *o1,
-                                  double *o2) {
-  const long long n = n_each * nout;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int c = 0; c < k; c++) acc += cop[(long long)c * stride + i];
-    const long long w = i / n_each, j = i - w * n_each;
-    double *o = w == 0 ? o0 : (w == 1 ? o1 : o2);
-    o[j] = acc;
-  }
 }
 
 // Channel window (as in the forward march): slot j of every lane is the channel block
@@ -310,7 +342,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
   const float S_bg = P.I0 / P.out_scale;  // background in internal intensity units
   double loss = 0.0;
   float dmx = 0.0f;  // largest |dL/d(network output)| this lane wrote
-  const rt_grads Gb = block_sink(P, G, GC);
+  const GradSink Gb = block_sink(G, GC);
 
   for (long long u0 = gw; u0 < nunits; u0 += W * NG) {
     {
@@ -591,8 +623,8 @@ static AdjScratch plan_scratch(const MarchParams &P, long long blocks, size_t ck
                                size_t avail) {
   AdjScratch a;
   a.ck_bytes = align256(ck_bytes);
-  const size_t gcopy = (size_t)3 * P.nr * P.nz * sizeof(double);
-  const size_t hcopy = (size_t)2 * P.nr * sizeof(double);
+  const size_t gcopy = (size_t)P.nr * P.nz * sizeof(float4);
+  const size_t hcopy = (size_t)P.nr * sizeof(float2);
   long long kg = (long long)(kCopyBudget / gcopy);
   if (kg > kMaxGridCopies) kg = kMaxGridCopies;
   if (kg > blocks) kg = blocks;
@@ -635,10 +667,10 @@ static int zero_grads(const MarchParams &P, const rt_grads &G, const AdjScratch 
 
 static GradCopies copies_of(const MarchParams &P, const AdjScratch &a, char *scratch) {
   GradCopies c;
-  c.g = a.kg ? reinterpret_cast<double *>(scratch + a.g_off) : nullptr;
-  c.h = a.kh ? reinterpret_cast<double *>(scratch + a.h_off) : nullptr;
-  c.gstride = 3LL * P.nr * P.nz;
-  c.hstride = 2LL * P.nr;
+  c.g = a.kg ? reinterpret_cast<float4 *>(scratch + a.g_off) : nullptr;
+  c.h = a.kh ? reinterpret_cast<float2 *>(scratch + a.h_off) : nullptr;
+  c.gstride = (long long)P.nr * P.nz;
+  c.hstride = P.nr;
   c.kg = a.kg > 0 ? a.kg : 1;
   c.kh = a.kh > 0 ? a.kh : 1;
   return c;
@@ -648,14 +680,14 @@ static int sum_copies(const MarchParams &P, const rt_grads &G, const GradCopies 
                       const AdjScratch &a, cudaStream_t stream) {
   if (a.kg) {
     long long m = (long long)P.nr * P.nz;
-    long long nb = (3 * m + 255) / 256;
-    sum_copies_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, stream>>>(
-        c.g, a.kg, c.gstride, m, 3, G.dT, G.dn, G.dvt);
+    long long nb = (m + 255) / 256;
+    sum_grid_copies_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, stream>>>(
+        c.g, a.kg, c.gstride, m, G.dT, G.dn, G.dvt);
   }
   if (a.kh) {
-    long long nb = (2LL * P.nr + 255) / 256;
-    sum_copies_kernel<<<(unsigned)nb, 256, 0, stream>>>(c.h, a.kh, c.hstride, P.nr, 2, G.dh_lo,
-                                                         G.dh_hi, nullptr);
+    long long nb = (P.nr + 255) / 256;
+    sum_surface_copies_kernel<<<(unsigned)nb, 256, 0, stream>>>(c.h, a.kh, c.hstride, P.nr,
+                                                                 G.dh_lo, G.dh_hi);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "gradient sum: %s", cudaGetErrorString(e));

@@ -101,8 +101,10 @@ def test_queue_full_and_destroy_with_pending(serve):
 
 @pytest.mark.gpu
 def test_results_identical_alone_and_in_mix(serve, orc):
-    """Renders and gradients of differently sized disks submitted together (overlapping on
-    the device) equal the same requests run alone."""
+    """Renders of differently sized disks submitted together (overlapping on the device)
+    equal the same requests run alone bit for bit; gradients agree to the rounding of the
+    adjoint's FP32 per-block partial sums (their order on the device is not fixed): 1e-6 of
+    the largest entry."""
     import torch
     from paper_2509_03623_b300 import _rt
     if not torch.cuda.is_available():
@@ -150,5 +152,5 @@ def test_results_identical_alone_and_in_mix(serve, orc):
         if g is not None:
             for k in ("T", "n_h2", "vturb", "h_lo", "h_hi"):
                 a, b = g[k].cpu().numpy(), ref_g[k]
-                assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max(), k
+                assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max(), k
             assert float(g["loss"].item()) == pytest.approx(float(ref_g["loss"][0]), rel=1e-12)

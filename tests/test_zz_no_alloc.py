@@ -55,9 +55,10 @@ def test_noalloc_matches_allocating_adjoint_twice(rt, orc, mode):
 
 
 def test_noalloc_large_grid_without_room_for_copies(rt):
-    """A 1024x512 grid: one copy of the node gradients (12.6 MB) leaves no room for a second
-    in the fixed array, so the kernel adds straight into the outputs; same gradients up to
-    the order of the FP64 sums."""
+    """A 1024x512 grid: one copy of the node gradients (8.4 MB) leaves no room for a second
+    in the fixed array, so the kernel adds straight into the FP64 outputs. The allocating
+    call sums FP32 per-block copies (a few hundred terms each) in FP64, so the two agree to
+    the FP32 rounding of those partial sums: 1e-6 of the largest entry."""
     import torch
     p = synth.disk(33, nr=1024, nz=512, nx=24, ny=24, nch=16, n_samples=128)
     dd = rt.DeviceDisk(p)
@@ -71,7 +72,7 @@ def test_noalloc_large_grid_without_room_for_copies(rt):
     torch.cuda.synchronize()
     for k in ("T", "n_h2", "vturb", "h_lo", "h_hi"):
         a, b = grads[k].cpu().numpy(), ref[k].cpu().numpy()
-        np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-12 * np.abs(b).max(), err_msg=k)
+        np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max(), err_msg=k)
 
 
 def test_noalloc_rejects_oversized_problem(rt):
