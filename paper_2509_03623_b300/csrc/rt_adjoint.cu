@@ -26,6 +26,7 @@
 // the Planck source, the CO-layer edges and the bilinear weights, scattering the node
 // gradients with FP64 atomics into replicated accumulators.
 #include <mutex>
+#include <new>
 
 #include "rt_internal.cuh"
 
@@ -77,13 +78,9 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   const float r2 = fmaf(R.x, R.x, y * y);
   const Cell c = locate(P, z, r2);
   if (!(c.gas && R.hit && k < P.n_samples)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  float T = bilerp(P.T, P.nr, c);
-  float n = bilerp(P.n, P.nr, c);
-  const float vt = bilerp(P.vt, P.nr, c);
-  const float *hl = P.hlo + c.i0;
-  const float *hh = P.hhi + c.i0;
-  float hlo = lerpf(__ldg(hl), __ldg(hl + 1), c.fr);
-  float hhi = lerpf(__ldg(hh), __ldg(hh + 1), c.fr);
+  const NodeVals f = fields_at(P, c);
+  float T = f.T, n = f.n, hlo = f.hlo, hhi = f.hhi;
+  const float vt = f.vt;
   float mT = 1.0f, mn = 1.0f;
   if (P.mod) {
     const float4 o = __ldg(P.mod + (long long)R.pix * P.n_samples + k);
@@ -605,9 +602,10 @@ static size_t adj_block_bytes(const MarchParams &P) {
   return (size_t)adj_wpb<LPR>() * adj_warp_floats<LPR, CPL>(nseg) * sizeof(float);
 }
 
-// Scratch of one adjoint launch: the warps' checkpoints, then the gradient copies.
+// Scratch of one adjoint launch: the warps' checkpoints, the gradient copies, then the
+// corner quads of the fields (cell_bytes; 0 when the kernel reads the node arrays).
 struct AdjScratch {
-  size_t ck_bytes, g_off, h_off, total;
+  size_t ck_bytes, g_off, h_off, cell_off, cell_bytes, total;
   int kg, kh;
 };
 
@@ -629,17 +627,23 @@ static AdjScratch plan_scratch(const MarchParams &P, long long blocks, size_t ck
   if (kg > kMaxGridCopies) kg = kMaxGridCopies;
   if (kg > blocks) kg = blocks;
   long long kh = kMaxSurfCopies < blocks ? kMaxSurfCopies : blocks;
+  a.cell_bytes = align256(cell_bytes(P));
   if (avail) {
+    // surface copies first (small, and without them every radius serializes), then the
+    // corner quads, then grid copies in what is left
     size_t left = avail > a.ck_bytes ? avail - a.ck_bytes : 0;
     while (kh > 0 && (size_t)kh * hcopy > left / 4) kh /= 2;
-    left -= (size_t)kh * hcopy;
+    left -= align256((size_t)kh * hcopy);
+    if (a.cell_bytes + 256 > left) a.cell_bytes = 0;
+    left -= a.cell_bytes;
     while (kg > 0 && (size_t)kg * gcopy + 256 > left) kg /= 2;
   }
   a.kg = kg > 1 ? (int)kg : 0;  // one copy buys nothing over the caller's arrays
   a.kh = kh > 1 ? (int)kh : 0;
   a.g_off = a.ck_bytes;
   a.h_off = a.g_off + align256((size_t)a.kg * gcopy);
-  a.total = a.h_off + (size_t)a.kh * hcopy;
+  a.cell_off = a.h_off + align256((size_t)a.kh * hcopy);
+  a.total = a.cell_off + a.cell_bytes;
   return a;
 }
 
@@ -655,7 +659,7 @@ static int zero_grads(const MarchParams &P, const rt_grads &G, const AdjScratch 
     if (e == cudaSuccess) e = cudaMemsetAsync(G.dvt, 0, ng, stream);
   }
   if (e == cudaSuccess && a.kh) {
-    e = cudaMemsetAsync(scratch + a.h_off, 0, a.total - a.h_off, stream);
+    e = cudaMemsetAsync(scratch + a.h_off, 0, a.cell_off - a.h_off, stream);
   } else if (e == cudaSuccess) {
     e = cudaMemsetAsync(G.dh_lo, 0, nh, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(G.dh_hi, 0, nh, stream);
@@ -703,8 +707,21 @@ static int run_adj(const MarchParams &P, const float *dLdc, const float *target,
   if (rc != RT_OK) return rc;
   const GradCopies c = copies_of(P, a, scratch);
   const int nseg = (P.n_samples + kSeg - 1) / kSeg;
+  const MarchParams *Q = &P;
+  MarchParams *packed = nullptr;
+  if (a.cell_bytes) {
+    packed = new (std::nothrow) MarchParams(P);
+    if (!packed) return set_error(RT_ENOMEM, "host allocation failed");
+    rc = pack_cells(*packed, scratch + a.cell_off, stream);
+    if (rc != RT_OK) {
+      delete packed;
+      return rc;
+    }
+    Q = packed;
+  }
   march_adj_kernel<LPR, CPL, UNIF><<<(unsigned)blocks, adj_wpb<LPR>() * 32, 0, stream>>>(
-      P, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, dmax, c);
+      *Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, dmax, c);
+  delete packed;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "adjoint launch: %s", cudaGetErrorString(e));
   return sum_copies(P, G, c, a, stream);
@@ -786,7 +803,7 @@ int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, doub
 // application whose own memory manager has already reserved the device's memory, or a
 // service that runs under a fixed device-memory budget and forbids allocator traffic once it
 // is running. For them the scratch of the adjoint (checkpoints, then as many gradient copies
-// as fit) lives in one file-scope device array of fixed size, kFixedScratchBytes, that every
+// and, room permitting, the corner quads of the fields) lives in one file-scope device array of fixed size, kFixedScratchBytes, that every
 // GPU loading this library holds until the process exits. The kernel is the same; when the
 // array cannot hold a checkpoint region for every resident block, the persistent grid is
 // made smaller, and where fewer gradient copies fit (or none: then the blocks add straight
@@ -824,7 +841,8 @@ template <int LPR, int CPL, bool UNIF>
 static int launch_adj_fixed_t(const MarchParams &P, const float *dLdc, const float *target,
                               float *cube_out, const rt_grads &G, cudaStream_t stream,
                               float *scratch) {
-  // checkpoints get at most three quarters of the array, gradient copies what is left
+  // checkpoints get at most three quarters of the array; surface copies, corner quads and
+  // grid copies share what is left
   const size_t ck_room = kFixedScratchBytes / 4 * 3;
   const size_t per_block = adj_block_bytes<LPR, CPL>(P);
   if (per_block > ck_room)

@@ -48,6 +48,12 @@ struct MarchParams {
   // optional work counters of the forward kernel (device, 2 x u64): samples with gas whose
   // physics was evaluated, channel evaluations computed; nullptr for none
   unsigned long long *work;
+  // optional corner quads (pack_cells): per grid cell (i, j) the four nodes its bilinear
+  // interpolation reads, {f(i,j), f(i+1,j), f(i,j+1), f(i+1,j+1)}, for T, n_H2 and v_turb
+  // (three float4 per cell, cells in [j][i] order), and per radial interval i
+  // {h_lo(i), h_lo(i+1), h_hi(i), h_hi(i+1)}: four 16-byte loads per sample instead of 16
+  // scalar ones. nullptr: the kernels read the node arrays (same values, same rounding).
+  const float4 *cell, *hcell;
   float v[RT_MAX_CH];
   float tab[kTabSeg * 4];
 };
@@ -194,6 +200,38 @@ __device__ __forceinline__ float bilerp(const float *__restrict__ F, int nr, con
   return lerpf(lerpf(f00, f01, c.fr), lerpf(f10, f11, c.fr), c.fz);
 }
 
+__device__ __forceinline__ float quad_lerp(const float4 &q, const Cell &c) {
+  return lerpf(lerpf(q.x, q.y, c.fr), lerpf(q.z, q.w, c.fr), c.fz);
+}
+
+// Interpolated node fields at a located sample (the arithmetic of bilerp either way).
+struct NodeVals {
+  float T, n, vt, hlo, hhi;
+};
+
+__device__ __forceinline__ NodeVals fields_at(const MarchParams &P, const Cell &c) {
+  NodeVals v;
+  if (P.cell) {
+    const float4 *q = P.cell + 3 * ((long long)c.j0 * (P.nr - 1) + c.i0);
+    const float4 qT = __ldg(q), qn = __ldg(q + 1), qv = __ldg(q + 2);
+    const float4 qh = __ldg(P.hcell + c.i0);
+    v.T = quad_lerp(qT, c);
+    v.n = quad_lerp(qn, c);
+    v.vt = quad_lerp(qv, c);
+    v.hlo = lerpf(qh.x, qh.y, c.fr);
+    v.hhi = lerpf(qh.z, qh.w, c.fr);
+  } else {
+    v.T = bilerp(P.T, P.nr, c);
+    v.n = bilerp(P.n, P.nr, c);
+    v.vt = bilerp(P.vt, P.nr, c);
+    const float *hl = P.hlo + c.i0;
+    const float *hh = P.hhi + c.i0;
+    v.hlo = lerpf(__ldg(hl), __ldg(hl + 1), c.fr);
+    v.hhi = lerpf(__ldg(hh), __ldg(hh + 1), c.fr);
+  }
+  return v;
+}
+
 // Keplerian factor (r^2 + z^2)^{-3/4} with a refined reciprocal square root (the profile
 // argument scales the relative error of v_los by v_los / alpha).
 __device__ __forceinline__ float kepler_q(float d2) {
@@ -226,13 +264,8 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
   Cell c = locate(P, z, r2);
   float4 out = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
   if (!(c.gas && R.hit && k < P.n_samples)) return out;
-  float T = bilerp(P.T, P.nr, c);
-  float n = bilerp(P.n, P.nr, c);
-  float vt = bilerp(P.vt, P.nr, c);
-  const float *hl = P.hlo + c.i0;
-  const float *hh = P.hhi + c.i0;
-  float hlo = lerpf(__ldg(hl), __ldg(hl + 1), c.fr);
-  float hhi = lerpf(__ldg(hh), __ldg(hh + 1), c.fr);
+  const NodeVals f = fields_at(P, c);
+  float T = f.T, n = f.n, vt = f.vt, hlo = f.hlo, hhi = f.hhi;
   if (P.mod) {
     const float4 o = __ldg(P.mod + (long long)R.pix * P.n_samples + k);
     T *= ex2(o.x * 1.4426950408889634f);
@@ -270,6 +303,8 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
 int set_error(int code, const char *fmt, ...);
 void clear_error();
 int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream);
+size_t cell_bytes(const MarchParams &P);
+int pack_cells(MarchParams &P, void *buf, cudaStream_t stream);
 int launch_count(const MarchParams &P, unsigned long long *count, cudaStream_t stream);
 void lane_layout(int nch, int *lpr, int *cpl);
 int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target, float *cube_out,

@@ -87,7 +87,7 @@ int footprint(const rt_request &r, bool fake, size_t *bytes) {
     size_t b = 0;
     if (r.kind == RT_REQ_RENDER) {
       if (cube > 0 && !r.cube) rc = rtb::set_error(RT_EINVAL, "render request without a cube");
-      b = cube;
+      b = cube + rtb::cell_bytes(*P);
     } else if (r.kind == RT_REQ_ADJOINT) {
       rc = rtb::check_adjoint_args(*P, r.dL_dcube, r.target, &r.grads);
       size_t grads = (size_t)(3 * P->nr * P->nz + 2 * P->nr + 1) * sizeof(double);
