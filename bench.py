@@ -52,7 +52,7 @@ except (OSError, ValueError):
 MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 16)
 # DRAM bytes of one forward launch on the observation-scale workload (ncu, dram__bytes_read +
 # dram__bytes_write; the cube stays in L2 at the end of the launch)
-FWD_DRAM_BYTES = 1_401_856 + 41_728
+FWD_DRAM_BYTES = 3_323_648 + 29_952
 N_SM = 148
 SM_MAX_MHZ = 2032.0
 
@@ -424,7 +424,8 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "fwd_adjoint": {"value": evals / (adj_max * 1e-3) / 1e9, "unit": UNIT,
                             "ms_per_step": adj_max, "steps": adj_steps,
-                            "note": "fused forward + reverse march with FP64 node gradients, "
+                            "note": "fused forward + reverse march, node gradients summed in per-block "
+                                    "FP32 copies and reduced in FP64, "
                                     "loss sum (I - I*)^2 formed in the kernel; nominal evals",
                             "roofline": {
                                 "bound": "alu",

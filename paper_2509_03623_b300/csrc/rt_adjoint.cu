@@ -182,9 +182,9 @@ __device__ __forceinline__ GradSink block_sink(const rt_grads &G, const GradCopi
   return S;
 }
 
-// Sums of the copies in FP64, in copy order:
-//   grid:    dT[i], dn[i], dvt[i] = sum_c cop[c][i].{x, y, z}
-//   surface: dh_lo[i], dh_hi[i]   = sum_c cop[c][i].{x, y}
+// Sums of the copies in FP64, in a fixed order:
+//   grid:    dT[i], dn[i], dvt[i] = sum_c cop[c][i].{x, y, z}  (one thread per node, copy order)
+//   surface: dh_lo[i], dh_hi[i]   = sum_c cop[c][i].{x, y}     (one warp per entry, below)
 __global__ void sum_grid_copies_kernel(const float4 *__restrict__ cop, int k, long long stride,
                                        long long n, double *dT, double *dn, double *dvt) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -202,18 +202,29 @@ __global__ void sum_grid_copies_kernel(const float4 *__restrict__ cop, int k, lo
   }
 }
 
+// One warp per surface entry (there are few entries and up to 128 copies each): lane l sums
+// copies l, l + 32, ... in order, then a fixed butterfly adds the lanes' partial sums, so the
+// result does not depend on scheduling.
 __global__ void sum_surface_copies_kernel(const float2 *__restrict__ cop, int k, long long stride,
                                           long long n, double *dlo, double *dhi) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = w0; i < n; i += nw) {
     double a = 0.0, b = 0.0;
-    for (int j = 0; j < k; j++) {
+    for (int j = lane; j < k; j += 32) {
       const float2 v = cop[(long long)j * stride + i];
       a += v.x;
       b += v.y;
     }
-    dlo[i] = a;
-    dhi[i] = b;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      dlo[i] = a;
+      dhi[i] = b;
+    }
   }
 }
 
@@ -377,7 +388,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
         if (!act) continue;
         ph[lane] = mine;
         __syncwarp();
-#pragma unroll 4
+#pragma unroll 1
         for (int t = 0; t < LPR; t++) {
           const float4 p = ph[rr * LPR + t];
           const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
@@ -442,7 +453,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
           if (!act) continue;
           ph[lane] = mine;
           __syncwarp();
-#pragma unroll 4
+#pragma unroll 1
           for (int t = 0; t < LPR; t++) {
             const float4 p = ph[rr * LPR + t];
             const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
@@ -689,9 +700,9 @@ static int sum_copies(const MarchParams &P, const rt_grads &G, const GradCopies 
         c.g, a.kg, c.gstride, m, G.dT, G.dn, G.dvt);
   }
   if (a.kh) {
-    long long nb = (P.nr + 255) / 256;
-    sum_surface_copies_kernel<<<(unsigned)nb, 256, 0, stream>>>(c.h, a.kh, c.hstride, P.nr,
-                                                                 G.dh_lo, G.dh_hi);
+    long long nb = (P.nr + 7) / 8;  // 8 warps (entries) per block
+    sum_surface_copies_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, stream>>>(
+        c.h, a.kh, c.hstride, P.nr, G.dh_lo, G.dh_hi);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "gradient sum: %s", cudaGetErrorString(e));

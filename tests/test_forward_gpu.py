@@ -140,3 +140,13 @@ def test_render_work_counts_and_identical_cube(rt):
     gas = rt.rt_count_gas_samples(p, dd)
     assert 0 < phys <= gas
     assert 0 < comp <= p.nx * p.ny * p.n_samples * 2 * p.nch
+
+
+def test_corner_quads_full_cube(rt, orc):
+    """From 4M samples the march reads its fields from packed corner quads (the smaller cases
+    above read the node arrays): the 512x256-grid disk at 128^2 px x 256 samples (4.19 M
+    samples, 64 channels) takes that path; full cube against the oracle."""
+    p = synth.config_observation(3).replace(nx=128, ny=128, n_samples=256)
+    assert p.nx * p.ny * p.n_samples >= 1 << 22
+    g = gpu_cube(rt, p)
+    assert_cube_close(g, orc.render(p), label="corner quads vs oracle")
