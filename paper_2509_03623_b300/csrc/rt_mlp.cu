@@ -1034,9 +1034,19 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
         tc_fence_before();
         __syncthreads();
       }
+      // dW_l (persistent columns; dW1 goes through the working columns once per tile) and
+      // db_l; for l >= 2 the first delta_{l-1} chunk is issued behind them under the same
+      // commit (the tensor pipe runs them in order, so its completion also means dW_l has
+      // finished reading a_{l-1}, which the delta epilogue overwrites)
+      const unsigned wl = l >= 2 ? smem_u32(S.Wh[l - 2]) : 0u;  // W_l
+      auto issue_delta = [&](int c) {
+        for (int ks = 0; ks < kMlpW / 16; ks++)
+          mma_bf16(tm + kColWork, mma_desc(ay + ks * 256, kMlpW),
+                   mma_desc_mn(wl + c * 1024 + ks * 4096, 128, 2048),
+                   idesc_16(kChunk, F16, false, true), ks > 0);
+      };
       if (tid == 0) {
         tc_fence_after();
-        // dW_l (persistent columns; dW1 goes through the working columns once per tile)
         const unsigned colw = l == 1 ? kColWork : (l == 2 ? kColW2 : (l == 3 ? kColW3 : kColW4));
         const unsigned kst = (unsigned)(Kin / 8) * 128;  // distance between 8-sample groups of X
         for (int ks = 0; ks < kMlpTile / 16; ks++)
@@ -1046,46 +1056,46 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
         for (int ks = 0; ks < kMlpTile / 16; ks++)
           mma_bf16(tm + kColDb, mma_desc_mn(ay + ks * 4096, 128, 2048),
                    mma_desc(aONE + ks * 256, kMlpTile), idesc_16(16, F16, true, false), ks > 0);
+        if (l >= 2) issue_delta(0);
         mma_commit(mbar);
       }
-      wait_mma();
-      if (half == 0) {
-        float v[16];
-        tmem_ld16(tl + kColDb, v);
-        dbacc[l - 1] += v[0];
-      }
       if (l == 1) {
+        wait_mma();
+        if (half == 0) {
+          float v[16];
+          tmem_ld16(tl + kColDb, v);
+          dbacc[0] += v[0];
+        }
         float v[32];
         tmem_ld32(tl + kColWork + 32 * half, v);
 #pragma unroll
         for (int j = 0; j < 32; j++) dw1[j] += v[j];
+        tc_fence_before();
+        __syncthreads();
+        if (S.abort) goto done;
+        break;
       }
-      tc_fence_before();
-      __syncthreads();
-      if (S.abort) goto done;
-      if (l == 1) break;
-      const unsigned wl = smem_u32(S.Wh[l - 2]);  // W_l
-      auto issue = [&](int c) {
-        tc_fence_after();
-        for (int ks = 0; ks < kMlpW / 16; ks++)
-          mma_bf16(tm + kColWork, mma_desc(ay + ks * 256, kMlpW),
-                   mma_desc_mn(wl + c * 1024 + ks * 4096, 128, 2048),
-                   idesc_16(kChunk, F16, false, true), ks > 0);
-        mma_commit(mbar);
-      };
-      if (tid == 0) issue(0);
       for (int c = 0; c < 2; c++) {
         const uint4 *zr = zrow(l - 2, c);
         uint4 zq[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) zq[k] = zr[k];
         wait_mma();
+        if (c == 0 && half == 0) {
+          float v[16];
+          tmem_ld16(tl + kColDb, v);
+          dbacc[l - 1] += v[0];
+        }
         float v[32];
         tmem_ld32(tl + kColWork + 32 * half, v);
         tc_fence_before();
         __syncthreads();
         if (S.abort) goto done;
-        if (tid == 0 && c == 0) issue(1);
+        if (tid == 0 && c == 0) {
+          tc_fence_after();
+          issue_delta(1);
+          mma_commit(mbar);
+        }
         const int f0 = kChunk * c + 32 * half;
         const unsigned *zz = reinterpret_cast<const unsigned *>(zq);
         unsigned dp[16];
