@@ -736,7 +736,8 @@ int launch_coords(const MarchParams &P, float2 *xy, cudaStream_t stream) {
 // Backward pass of the network: dL/dW and dL/db of every layer from per-sample dL/d(outputs)
 // (reverse mode of the network written out by hand, on the tensor cores).
 //
-// One persistent CTA per SM, 8 warps (two per TMEM lane quadrant). Tensor memory (512
+// One persistent CTA per SM, 16 warps (four per TMEM lane quadrant, each reading 16 of every
+// 64 accumulator columns: the epilogues are latency-bound, so more threads share them). Tensor memory (512
 // columns) holds the weight-gradient accumulators for the whole run of the CTA -- dW2..dW4
 // (128 columns each) and dW5^T (16) -- and an 80-column working accumulator; dW1 (128 x 64)
 // is staged through the working columns once per tile and summed in registers. Per tile of
@@ -756,7 +757,7 @@ int launch_coords(const MarchParams &P, float2 *xy, cudaStream_t stream) {
 // mbarrier are bounded: on expiry the CTA records an error, stops and releases its tensor
 // memory.
 // ---------------------------------------------------------------------------------------
-constexpr int kBwdThreads = 256;
+constexpr int kBwdThreads = 512;
 constexpr unsigned kColW2 = 0, kColW3 = 128, kColW4 = 256, kColW5 = 384, kColWork = 400;
 constexpr unsigned kColDb = kColWork + 64;  // bias sums (16 columns) inside the working range
 constexpr int kChunk = 64;                  // columns per layer-output MMA chunk
@@ -801,13 +802,27 @@ struct MlpGradsDev {
   double *db[5];
 };
 
-// 32 accumulator columns of a layer-output chunk -> the 16 pairs this thread stores.
-template <bool F16>
-__device__ __forceinline__ void store32(h16 *A, int t, int f0, const unsigned *p) {
+// 16 accumulator columns of a layer-output chunk -> the 8 pairs this thread stores.
+__device__ __forceinline__ void store16(h16 *A, int t, int f0, const unsigned *p) {
 #pragma unroll
-  for (int k = 0; k < 4; k++)
+  for (int k = 0; k < 2; k++)
     *reinterpret_cast<uint4 *>(A + cm_off(t, f0 + 8 * k, kMlpW)) =
         make_uint4(p[4 * k], p[4 * k + 1], p[4 * k + 2], p[4 * k + 3]);
+}
+
+// Fourier features for directions [8 qt, 8 qt + 8): sin into f[0..7], cos into f[8..15]
+// (the arithmetic of features()).
+__device__ __forceinline__ void features8(const float (*Bf)[2], float rh, float zh, int qt,
+                                          float *f) {
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int i = 8 * qt + j;
+    float ph = fmaf(Bf[i][0], rh, Bf[i][1] * zh);
+    ph -= rintf(ph);
+    float a = 6.283185307179586f * ph;
+    f[j] = __sinf(a);
+    f[8 + j] = __cosf(a);
+  }
 }
 
 template <class In, bool F16>
@@ -819,7 +834,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   BwdSmem &S = *reinterpret_cast<BwdSmem *>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int q = warp & 3, half = warp >> 2;
+  const int q = warp & 3, qt = warp >> 2;  // TMEM lane quadrant; quarter of every chunk
   const int t = q * 32 + lane;  // tile row: sample (or output feature of a weight gradient)
   h16 *Z = spill + (size_t)blockIdx.x * (4 * kMlpTile * kMlpW);  // this CTA's pre-activations
 
@@ -865,11 +880,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
     ex = max(-120, min(120, ex));
   }
   const float scale = ldexpf(1.0f, -ex);
-  float dw1[32];                               // dW1[t][32 half + j]
+  float dw1[16];                               // dW1[t][16 qt + j]
 #pragma unroll
-  for (int j = 0; j < 32; j++) dw1[j] = 0.0f;
-  float dbacc[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // db_l of output feature t (half 0)
-  float db5acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // db_5 over this warp's rows (lane 0, half 0)
+  for (int j = 0; j < 16; j++) dw1[j] = 0.0f;
+  float dbacc[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // db_l of output feature t (quarter 0)
+  float db5acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // db_5 over this warp's rows (lane 0, quarter 0)
   bool first = true;
   const unsigned aP = smem_u32(S.P), aQ = smem_u32(S.Q), aF = smem_u32(S.F);
   const unsigned aD5 = smem_u32(S.D5), aONE = smem_u32(S.ONES), aW5 = smem_u32(S.W5);
@@ -884,9 +899,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       atomicExch(&g_mlp_error, 1);
     }
   };
-  // z (16-bit, packed pairs) of layer index L, chunk c, this thread's half and row: 4 x uint4
+  // z (16-bit, packed pairs) of layer index L, chunk c, this thread's quarter and row: 2 x uint4
   auto zrow = [&](int L, int c) {
-    return reinterpret_cast<uint4 *>(Z + ((size_t)((L * 2 + c) * 2 + half) * kMlpTile + t) * 32);
+    return reinterpret_cast<uint4 *>(Z + ((size_t)((L * 2 + c) * 4 + qt) * kMlpTile + t) * 16);
   };
 
   const long long ntiles = (in_count(in, n) + kMlpTile - 1) / kMlpTile;
@@ -904,14 +919,12 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       g.w *= scale;
     }
     {
-      float f[32];
-      features(S.Bf, rh, zh, half, f);
-      store8<F16>(S.F, t, 16 * half, kMlpF, f);
-      store8<F16>(S.F, t, 16 * half + 8, kMlpF, f + 8);
-      store8<F16>(S.F, t, 32 + 16 * half, kMlpF, f + 16);
-      store8<F16>(S.F, t, 32 + 16 * half + 8, kMlpF, f + 24);
+      float f[16];
+      features8(S.Bf, rh, zh, qt, f);
+      store8<F16>(S.F, t, 8 * qt, kMlpF, f);
+      store8<F16>(S.F, t, 32 + 8 * qt, kMlpF, f + 8);
     }
-    if (half == 0) {
+    if (qt == 0) {
       const float d[8] = {g.x, g.y, g.z, g.w, 0.0f, 0.0f, 0.0f, 0.0f};
       store8<F16>(S.D5, t, 0, kMlpOutPad, d);
       float r[4] = {g.x, g.y, g.z, g.w};
@@ -944,23 +957,23 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       if (tid == 0) issue(0);
       for (int c = 0; c < 2; c++) {
         wait_mma();
-        float v[32];
-        tmem_ld32(tl + kColWork + 32 * half, v);
+        float v[16];
+        tmem_ld16(tl + kColWork + 16 * qt, v);
         tc_fence_before();
         __syncthreads();  // working columns free
         if (S.abort) goto done;
         if (tid == 0 && c == 0) issue(1);
-        const int f0 = kChunk * c + 32 * half;
-        unsigned zp[16], ap[16];
+        const int f0 = kChunk * c + 16 * qt;
+        unsigned zp[8], ap[8];
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
+        for (int j = 0; j < 8; j++) {
           zp[j] = pack16<F16>(v[2 * j] + S.bias[l][f0 + 2 * j], v[2 * j + 1] + S.bias[l][f0 + 2 * j + 1]);
           ap[j] = silu2p<F16>(zp[j]);
         }
         uint4 *zr = zrow(l, c);
 #pragma unroll
-        for (int k = 0; k < 4; k++) zr[k] = make_uint4(zp[4 * k], zp[4 * k + 1], zp[4 * k + 2], zp[4 * k + 3]);
-        store32<F16>(Aout, t, f0, ap);
+        for (int k = 0; k < 2; k++) zr[k] = make_uint4(zp[4 * k], zp[4 * k + 1], zp[4 * k + 2], zp[4 * k + 3]);
+        store16(Aout, t, f0, ap);
       }
       proxy_fence();
       tc_fence_before();
@@ -985,25 +998,25 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       }
       for (int c = 0; c < 2; c++) {
         const uint4 *zr = zrow(3, c);
-        uint4 zq[4];
+        uint4 zq[2];
 #pragma unroll
-        for (int k = 0; k < 4; k++) zq[k] = zr[k];
+        for (int k = 0; k < 2; k++) zq[k] = zr[k];
         wait_mma();
-        float v[32];
-        tmem_ld32(tl + kColWork + 32 * half, v);
+        float v[16];
+        tmem_ld16(tl + kColWork + 16 * qt, v);
         tc_fence_before();
         __syncthreads();
         if (S.abort) goto done;
         if (tid == 0 && c == 0) issue(1);
-        const int f0 = kChunk * c + 32 * half;
+        const int f0 = kChunk * c + 16 * qt;
         const unsigned *zz = reinterpret_cast<const unsigned *>(zq);
-        unsigned dp[16];
+        unsigned dp[8];
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
+        for (int j = 0; j < 8; j++) {
           const float2 z = unpack16<F16>(zz[j]);
           dp[j] = pack16<F16>(v[2 * j] * dsilu(z.x), v[2 * j + 1] * dsilu(z.y));
         }
-        store32<F16>(S.Q, t, f0, dp);
+        store16(S.Q, t, f0, dp);
       }
       proxy_fence();
       tc_fence_before();
@@ -1019,16 +1032,16 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       if (l == 3 || l == 2) {  // a_{l-1} was overwritten: recompute it from z_{l-1}
         for (int c = 0; c < 2; c++) {
           const uint4 *zr = zrow(l - 2, c);
-          unsigned ap[16];
+          unsigned ap[8];
 #pragma unroll
-          for (int k = 0; k < 4; k++) {
+          for (int k = 0; k < 2; k++) {
             const uint4 z = zr[k];
             ap[4 * k] = silu2p<F16>(z.x);
             ap[4 * k + 1] = silu2p<F16>(z.y);
             ap[4 * k + 2] = silu2p<F16>(z.z);
             ap[4 * k + 3] = silu2p<F16>(z.w);
           }
-          store32<F16>(X, t, kChunk * c + 32 * half, ap);
+          store16(X, t, kChunk * c + 16 * qt, ap);
         }
         proxy_fence();
         tc_fence_before();
@@ -1061,15 +1074,15 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       }
       if (l == 1) {
         wait_mma();
-        if (half == 0) {
+        if (qt == 0) {
           float v[16];
           tmem_ld16(tl + kColDb, v);
           dbacc[0] += v[0];
         }
-        float v[32];
-        tmem_ld32(tl + kColWork + 32 * half, v);
+        float v[16];
+        tmem_ld16(tl + kColWork + 16 * qt, v);
 #pragma unroll
-        for (int j = 0; j < 32; j++) dw1[j] += v[j];
+        for (int j = 0; j < 16; j++) dw1[j] += v[j];
         tc_fence_before();
         __syncthreads();
         if (S.abort) goto done;
@@ -1077,17 +1090,17 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       }
       for (int c = 0; c < 2; c++) {
         const uint4 *zr = zrow(l - 2, c);
-        uint4 zq[4];
+        uint4 zq[2];
 #pragma unroll
-        for (int k = 0; k < 4; k++) zq[k] = zr[k];
+        for (int k = 0; k < 2; k++) zq[k] = zr[k];
         wait_mma();
-        if (c == 0 && half == 0) {
+        if (c == 0 && qt == 0) {
           float v[16];
           tmem_ld16(tl + kColDb, v);
           dbacc[l - 1] += v[0];
         }
-        float v[32];
-        tmem_ld32(tl + kColWork + 32 * half, v);
+        float v[16];
+        tmem_ld16(tl + kColWork + 16 * qt, v);
         tc_fence_before();
         __syncthreads();
         if (S.abort) goto done;
@@ -1096,15 +1109,15 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
           issue_delta(1);
           mma_commit(mbar);
         }
-        const int f0 = kChunk * c + 32 * half;
+        const int f0 = kChunk * c + 16 * qt;
         const unsigned *zz = reinterpret_cast<const unsigned *>(zq);
-        unsigned dp[16];
+        unsigned dp[8];
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
+        for (int j = 0; j < 8; j++) {
           const float2 z = unpack16<F16>(zz[j]);
           dp[j] = pack16<F16>(v[2 * j] * dsilu(z.x), v[2 * j + 1] * dsilu(z.y));
         }
-        store32<F16>(X, t, f0, dp);
+        store16(X, t, f0, dp);
       }
       proxy_fence();
       tc_fence_before();
@@ -1122,18 +1135,18 @@ done:
     tc_fence_after();
     const double un = ldexp(1.0, ex);
 #pragma unroll
-    for (int j = 0; j < 32; j++) atomicAdd(G.dW[0] + t * kMlpF + 32 * half + j, (double)dw1[j] * un);
+    for (int j = 0; j < 16; j++) atomicAdd(G.dW[0] + t * kMlpF + 16 * qt + j, (double)dw1[j] * un);
     for (int L = 1; L < 4; L++) {
       const unsigned col = kColW2 + (unsigned)(L - 1) * 128;
       for (int cc = 0; cc < 2; cc++) {
-        float v[32];
-        tmem_ld32(tl + col + 64 * half + 32 * cc, v);
+        float v[16];
+        tmem_ld16(tl + col + 32 * qt + 16 * cc, v);
 #pragma unroll
-        for (int j = 0; j < 32; j++)
-          atomicAdd(G.dW[L] + t * kMlpW + 64 * half + 32 * cc + j, (double)v[j] * un);
+        for (int j = 0; j < 16; j++)
+          atomicAdd(G.dW[L] + t * kMlpW + 32 * qt + 16 * cc + j, (double)v[j] * un);
       }
     }
-    if (half == 0) {
+    if (qt == 0) {
       float v[16];
       tmem_ld16(tl + kColW5, v);  // row = input feature t, columns = outputs
 #pragma unroll
