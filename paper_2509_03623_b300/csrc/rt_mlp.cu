@@ -99,6 +99,10 @@ __device__ __forceinline__ unsigned long long mma_desc_mn(unsigned addr, unsigne
          ((sbo & 0x3FFF) << 32) | (1ull << 46);
 }
 
+// Shared-memory addresses stay below 2^18 bytes, so the 14-bit start-address field of a
+// descriptor never wraps: the descriptor of addr + 16 j is the descriptor of addr plus j. The
+// MMA issue loops below step descriptors this way (one 64-bit add per instruction), which
+// keeps the single issuing thread off a long dependent chain per MMA.
 template <bool F16>
 __device__ __forceinline__ h16 to16(float x) {
   if (F16) return __half_as_ushort(__float2half_rn(x));
@@ -426,9 +430,10 @@ __global__ void __launch_bounds__(kGT * kTG, 1)
         tc_fence_after();
         const unsigned bB =
             l == 0 ? smem_u32(S.W1) : (l == 4 ? smem_u32(S.W5) : smem_u32(S.Wh[l - 1]));
+        const unsigned long long dA = mma_desc(aA, K), dB = mma_desc(bB, K);
+        const unsigned id = N == kMlpW ? idesc_16(kMlpW, F16) : idesc_16(kMlpOutPad, F16);
         for (int ks = 0; ks < K / 16; ks++)
-          mma_bf16(tmem, mma_desc(aA + ks * 256, K), mma_desc(bB + ks * 256, K), idesc_16(N, F16),
-                   ks > 0);
+          mma_bf16(tmem, dA + 16u * ks, dB + 16u * ks, id, ks > 0);
         mma_commit(mbar);
       }
       ok = mbar_wait(mbar, phase);
@@ -949,9 +954,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       auto issue = [&](int c) {
         tc_fence_after();
         const unsigned b0 = wl + (unsigned)(c * 8 * (K / 8) * 128);  // rows 64c.. of W_l
+        const unsigned long long dA = mma_desc(ain, K), dB = mma_desc(b0, K);
         for (int ks = 0; ks < K / 16; ks++)
-          mma_bf16(tm + kColWork, mma_desc(ain + ks * 256, K), mma_desc(b0 + ks * 256, K),
-                   idesc_16(kChunk, F16), ks > 0);
+          mma_bf16(tm + kColWork, dA + 16u * ks, dB + 16u * ks, idesc_16(kChunk, F16), ks > 0);
         mma_commit(mbar);
       };
       if (tid == 0) issue(0);
@@ -990,9 +995,10 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       };
       if (tid == 0) {
         tc_fence_after();
+        const unsigned long long dA = mma_desc_mn(aQ, 128, 2048), dB = mma_desc_mn(aD5, 128, 256);
+#pragma unroll
         for (int ks = 0; ks < kMlpTile / 16; ks++)
-          mma_bf16(tm + kColW5, mma_desc_mn(aQ + ks * 4096, 128, 2048),
-                   mma_desc_mn(aD5 + ks * 512, 128, 256), idesc_16(16, F16, true, true),
+          mma_bf16(tm + kColW5, dA + 256u * ks, dB + 32u * ks, idesc_16(16, F16, true, true),
                    !first || ks > 0);
         issue(0);
       }
@@ -1053,22 +1059,29 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       // finished reading a_{l-1}, which the delta epilogue overwrites)
       const unsigned wl = l >= 2 ? smem_u32(S.Wh[l - 2]) : 0u;  // W_l
       auto issue_delta = [&](int c) {
+        const unsigned long long dA = mma_desc(ay, kMlpW);
+        const unsigned long long dB = mma_desc_mn(wl + c * 1024, 128, 2048);
+#pragma unroll
         for (int ks = 0; ks < kMlpW / 16; ks++)
-          mma_bf16(tm + kColWork, mma_desc(ay + ks * 256, kMlpW),
-                   mma_desc_mn(wl + c * 1024 + ks * 4096, 128, 2048),
+          mma_bf16(tm + kColWork, dA + 16u * ks, dB + 256u * ks,
                    idesc_16(kChunk, F16, false, true), ks > 0);
       };
       if (tid == 0) {
         tc_fence_after();
         const unsigned colw = l == 1 ? kColWork : (l == 2 ? kColW2 : (l == 3 ? kColW3 : kColW4));
         const unsigned kst = (unsigned)(Kin / 8) * 128;  // distance between 8-sample groups of X
+        const unsigned long long dY = mma_desc_mn(ay, 128, 2048), dX = mma_desc_mn(ax, 128, kst);
+        const unsigned long long dO = mma_desc(aONE, kMlpTile);
+        const unsigned idw = l == 1 ? idesc_16(kMlpF, F16, true, true) : idesc_16(kMlpW, F16, true, true);
+        const bool acc = l > 1 && !first;
+#pragma unroll
         for (int ks = 0; ks < kMlpTile / 16; ks++)
-          mma_bf16(tm + colw, mma_desc_mn(ay + ks * 4096, 128, 2048),
-                   mma_desc_mn(ax + ks * 2 * kst, 128, kst), idesc_16(Kin, F16, true, true),
-                   (l > 1 && !first) || ks > 0);
+          mma_bf16(tm + colw, dY + 256u * ks, dX + (unsigned long long)(ks * 2 * kst >> 4), idw,
+                   acc || ks > 0);
+#pragma unroll
         for (int ks = 0; ks < kMlpTile / 16; ks++)
-          mma_bf16(tm + kColDb, mma_desc_mn(ay + ks * 4096, 128, 2048),
-                   mma_desc(aONE + ks * 256, kMlpTile), idesc_16(16, F16, true, false), ks > 0);
+          mma_bf16(tm + kColDb, dY + 256u * ks, dO + 16u * ks, idesc_16(16, F16, true, false),
+                   ks > 0);
         if (l >= 2) issue_delta(0);
         mma_commit(mbar);
       }
