@@ -3,11 +3,11 @@
 // T(r,|z|) = MLP_w(gamma(r,|z|)) with a sinusoidal encoding gamma; the network shape here is
 // 64 Fourier features -> 4 x 128 SiLU -> 4 outputs).
 //
-// One persistent CTA per SM (two tile groups of 8 warps, ~185 KB of shared memory); the
-// groups work on different tiles so that one group's MMAs overlap the other's epilogue. At
+// One persistent CTA per SM (three tile groups of 8 warps, ~215 KB of shared memory); the
+// groups work on different tiles so that one group's MMAs overlap the others' epilogues. At
 // start the CTA converts the FP32 master weights to 16 bits into shared memory in the
 // no-swizzle K-major "core matrix" layout (8 rows x 16 bytes per core matrix) and allocates
-// 128 columns of tensor memory per group. Per tile of 128 samples, with two warps on each
+// tensor memory, 128 columns per group. Per tile of 128 samples, with two warps on each
 // TMEM lane quadrant (one per half of the columns, so row m belongs to two threads):
 //   the two threads of row m compute half of the features of sample m each (range-reduced
 //   sin/cos) into the A buffer;
@@ -42,15 +42,17 @@ struct MlpParamsDev {
 // 16-bit operands (BF16 or FP16 bit patterns, chosen by the kernel's F16 parameter).
 typedef unsigned short h16;
 
-constexpr int kTG = 2;        // tile groups per CTA, one tile in flight per group
+constexpr int kTG = 3;        // tile groups per CTA, one tile in flight per group
 constexpr int kGW = 8;        // warps per group: two per TMEM lane quadrant (column halves)
 constexpr int kGT = kGW * 32; // threads per group
+// tensor-memory columns allocated (a power of two holding 128 per group)
+constexpr int kTmemCols = kTG <= 2 ? 256 : 512;
 
 struct __align__(1024) MlpSmem {
   h16 W1[kMlpW * kMlpF];          // 16 KB
   h16 Wh[3][kMlpW * kMlpW];       // 96 KB
   h16 W5[kMlpOutPad * kMlpW];     // 4 KB
-  h16 A[kTG][kMlpTile * kMlpW];   // 2 x 32 KB, one activation buffer per tile group
+  h16 A[kTG][kMlpTile * kMlpW];   // 32 KB per tile group
   float bias[4][kMlpW];
   float bias5[kMlpOutPad];
   float Bf[32][2];
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(kGT * kTG, 1)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&S.tmem_base)),
-                 "r"(128 * kTG));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   proxy_fence();
@@ -477,9 +479,12 @@ __global__ void __launch_bounds__(kGT * kTG, 1)
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base),
-                 "r"(128 * kTG));
+                 "r"(kTmemCols));
   }
 }
+
+static_assert(sizeof(MlpSmem) <= 227 * 1024, "shared memory");
+static_assert(128 * kTG <= kTmemCols && kTmemCols <= 512, "tensor memory");
 
 int mlp_validate(const rt_mlp *m);
 static int mlp_check(const rt_mlp *m) { return mlp_validate(m); }
