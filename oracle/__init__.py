@@ -62,6 +62,13 @@ class _MLP(C.Structure):
     ]
 
 
+class _Chain(C.Structure):
+    _fields_ = [
+        ("sigma0_gcm2", C.c_double), ("r_c_au", C.c_double), ("gamma", C.c_double),
+        ("T_freeze", C.c_double), ("N_dissoc_cm2", C.c_double),
+    ]
+
+
 def _load():
     global _lib
     with _lock:
@@ -82,6 +89,7 @@ def _load():
                                            C.c_int, dp, C.c_int]
             lib.orc_render_mlp_adjoint.argtypes = [pp, C.POINTER(_MLP), dp, dp, dp, dp, dp, dp,
                                                    dp, dp, dp, C.c_int]
+            lib.orc_field_chain.argtypes = [pp, C.POINTER(_Chain), dp, dp, dp, dp, dp]
             _lib = lib
     return _lib
 
@@ -296,3 +304,24 @@ def mlp_grad(w, x: np.ndarray, gout: np.ndarray):
         ow += a * b
         ob += a
     return Ws, bs
+
+
+def field_chain(p, chain, T=None):
+    """Physics-constrained field chain (rt_oracle.h, orc_field_chain) on the grid of p with
+    the temperature grid T [nz][nr] (p.T when None): dict(n_h2, N_h2 [nz][nr], h_lo, h_hi
+    [nr]). `chain` has the attributes sigma0_gcm2, r_c_au, gamma, T_freeze, N_dissoc_cm2."""
+    lib = _load()
+    q = p if T is None else p.replace(T=np.asarray(T, dtype=np.float64))
+    pk = _Packed(q)
+    Tg = np.ascontiguousarray(np.asarray(q.T, dtype=np.float64))
+    c = _Chain(float(chain.sigma0_gcm2), float(chain.r_c_au), float(chain.gamma),
+               float(chain.T_freeze), float(chain.N_dissoc_cm2))
+    n = np.zeros((q.nz, q.nr))
+    N = np.zeros((q.nz, q.nr))
+    lo = np.zeros(q.nr)
+    hi = np.zeros(q.nr)
+    rc = lib.orc_field_chain(C.byref(pk.s), C.byref(c), _dptr(Tg), _dptr(n), _dptr(N),
+                             _dptr(lo), _dptr(hi))
+    if rc != 0:
+        raise ValueError("orc_field_chain: invalid arguments")
+    return dict(n_h2=n, N_h2=N, h_lo=lo, h_hi=hi)

@@ -816,3 +816,84 @@ int orc_render_mlp(const orc_problem *p, const orc_mlp *m, const long long *pix,
   (void)nthreads;
   return 0;
 }
+
+/* ------------------------------------------------------------------------------------------
+ * Physics-constrained field chain (see rt_oracle.h): hydrostatic density from a temperature
+ * grid, H2 column above each node, CO-layer surfaces. One radius column at a time, nodes in
+ * order; every integral is the trapezoid rule on the grid nodes.
+ * ------------------------------------------------------------------------------------------ */
+int orc_field_chain(const orc_problem *p, const orc_chain *c, const double *T, double *n_h2,
+                    double *N_h2, double *h_lo, double *h_hi) {
+  if (!p || !c || !T || !n_h2 || !h_lo || !h_hi || p->nr < 2 || p->nz < 2) return -1;
+  const int nr = p->nr, nz = p->nz;
+  const double GM = GM_SUN * p->mstar_msun;          /* cm^3 s^-2 */
+  const double m_mol = p->m_mol_amu * AMU_G;         /* g */
+  double *z = (double *)malloc(sizeof(double) * nz); /* node heights [cm] */
+  double *lnrho = (double *)malloc(sizeof(double) * nz);
+  double *N = (double *)malloc(sizeof(double) * nz);
+  if (!z || !lnrho || !N) {
+    free(z);
+    free(lnrho);
+    free(N);
+    return -1;
+  }
+  for (int i = 0; i < nr; i++) {
+    double r_au = p->r_log ? p->r_in_au * pow(p->r_out_au / p->r_in_au, (double)i / (nr - 1))
+                           : p->r_in_au + (p->r_out_au - p->r_in_au) * i / (nr - 1);
+    double r = r_au * AU_CM;
+    for (int j = 0; j < nz; j++) z[j] = p->zr_max * j / (nz - 1) * r;
+    /* Eq. gas_density_temp: the gravity term by the trapezoid rule, the temperature term
+       integrates to -ln(T_j / T_0) */
+    double grav_prev = 0.0, I = 0.0;
+    for (int j = 0; j < nz; j++) {
+      double Tj = T[(long long)j * nr + i];
+      double d3 = pow(r * r + z[j] * z[j], 1.5);
+      double grav = GM * z[j] / d3 * m_mol / (K_BOLTZ * Tj);
+      if (j > 0) I += 0.5 * (z[j] - z[j - 1]) * (grav_prev + grav);
+      grav_prev = grav;
+      lnrho[j] = -I - log(Tj / T[i]);
+    }
+    /* normalisation: 2 int_0^{z_max} rho dz = Sigma(r) */
+    double x = r_au / c->r_c_au;
+    double sigma = c->sigma0_gcm2 * pow(x, -c->gamma) * exp(-pow(x, 2.0 - c->gamma));
+    double S = 0.0;
+    for (int j = 1; j < nz; j++) S += 0.5 * (z[j] - z[j - 1]) * (exp(lnrho[j - 1]) + exp(lnrho[j]));
+    for (int j = 0; j < nz; j++)
+      n_h2[(long long)j * nr + i] = sigma / (2.0 * S) * exp(lnrho[j]) / m_mol;
+    /* Eq. column_density: N(z_j) = int_{z_j}^{z_max} n dz */
+    N[nz - 1] = 0.0;
+    for (int j = nz - 2; j >= 0; j--)
+      N[j] = N[j + 1] + 0.5 * (z[j + 1] - z[j]) *
+                            (n_h2[(long long)j * nr + i] + n_h2[(long long)(j + 1) * nr + i]);
+    if (N_h2)
+      for (int j = 0; j < nz; j++) N_h2[(long long)j * nr + i] = N[j];
+    /* Eq. co_layer as two surfaces (w = z/r) */
+    double dw = p->zr_max / (nz - 1);
+    double lo = p->zr_max;
+    if (T[i] > c->T_freeze) {
+      lo = 0.0;
+    } else {
+      for (int j = 1; j < nz; j++) {
+        double Ta = T[(long long)(j - 1) * nr + i], Tb = T[(long long)j * nr + i];
+        if (Tb > c->T_freeze) {
+          lo = dw * ((j - 1) + (c->T_freeze - Ta) / (Tb - Ta));
+          break;
+        }
+      }
+    }
+    double hi = 0.0;
+    for (int j = nz - 2; j >= 0; j--) {
+      if (0.706 * N[j] > c->N_dissoc_cm2) {
+        double Na = 0.706 * N[j], Nb = 0.706 * N[j + 1];
+        hi = dw * (j + (Na - c->N_dissoc_cm2) / (Na - Nb));
+        break;
+      }
+    }
+    h_lo[i] = lo;
+    h_hi[i] = hi;
+  }
+  free(z);
+  free(lnrho);
+  free(N);
+  return 0;
+}

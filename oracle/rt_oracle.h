@@ -113,6 +113,29 @@ int orc_render_mlp_adjoint(const orc_problem *p, const orc_mlp *m, const double 
                            double *cube, double *dT, double *dn, double *dvt, double *dh_lo,
                            double *dh_hi, double *dW, double *db, int nthreads);
 
+/* Physics-constrained field chain (Methods, "Parametric Disk Modeling": Eq. gas_density_temp,
+   the surface-density profile Sigma(r), Eq. column_density and Eq. co_layer; applied to a
+   temperature grid as in "Neural Temperature Recovery", physics-informed constraints).
+   Per radius node r_i, on the nodes z_j = w_j r_i (w_j = j zr_max / (nz - 1)):
+     d ln rho / dz = -G M z m_mol / ((r^2 + z^2)^{3/2} k T) - d ln T / dz, integrated upward
+       from the midplane with the trapezoid rule on the nodes (the ln T term exactly);
+     rho normalised so that 2 int_0^{z_max} rho dz (trapezoid, mirror symmetry) = Sigma(r),
+       Sigma(r) = Sigma0 (r/r_c)^-gamma exp(-(r/r_c)^{2 - gamma});
+     n_H2 = rho / m_mol;  N_H2(z_j) = int_{z_j}^{z_max} n_H2 dz (trapezoid);
+     CO where T > T_freeze and 0.706 N_H2 > N_dissoc, returned as the two surfaces of the
+     layer in z/r: h_lo = lowest w with T > T_freeze (T linear between nodes; 0 if the
+     midplane node is warmer, zr_max if no node is), h_hi = highest w with
+     0.706 N_H2 > N_dissoc (N_H2 linear between nodes; 0 if no node qualifies).
+   Uses p->nr, nz, r_log, r_in_au, r_out_au, zr_max, mstar_msun, m_mol_amu. Outputs
+   n_h2, N_h2 [nz][nr] (cm^-3, cm^-2; N_h2 may be NULL), h_lo, h_hi [nr]. */
+typedef struct {
+  double sigma0_gcm2, r_c_au, gamma;
+  double T_freeze, N_dissoc_cm2;
+} orc_chain;
+
+int orc_field_chain(const orc_problem *p, const orc_chain *c, const double *T, double *n_h2,
+                    double *N_h2, double *h_lo, double *h_hi);
+
 #ifdef __cplusplus
 }
 #endif

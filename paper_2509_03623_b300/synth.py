@@ -128,6 +128,33 @@ class Problem:
         return dataclasses.replace(self, **kw)
 
 
+@dataclasses.dataclass
+class Chain:
+    """Parameters of the physics-constrained field chain: surface density
+    Sigma(r) = Sigma0 (r/r_c)^-gamma exp(-(r/r_c)^(2-gamma)), freeze-out temperature and the
+    photodissociation column applied to 0.706 N_H2."""
+    sigma0_gcm2: float
+    r_c_au: float
+    gamma: float
+    T_freeze: float
+    N_dissoc_cm2: float
+
+
+def chain_params(p: "Problem", m_gas_msun: float = 0.09, r_c_au: float = 212.0,
+                 gamma: float = 0.8, T_freeze: float = 19.0,
+                 N_dissoc_cm2: float = 1.3e21) -> Chain:
+    """Chain parameters for the grid of p: r_c = 10^2.326 au (the HD 163296 value in the
+    paper's parameter table), gamma = 0.8, T_freeze = 19 K (the freeze-out threshold the paper
+    quotes), N_dissoc = 1.3e21 cm^-2; Sigma0 holds M_gas between r_in and r_out, from the
+    closed-form integral 2 pi Sigma0 r_c^2 / (2 - gamma) [exp(-x_in^(2-gamma)) -
+    exp(-x_out^(2-gamma))], x = r / r_c."""
+    k = 2.0 - gamma
+    xi, xo = p.r_in_au / r_c_au, p.r_out_au / r_c_au
+    mass_per_sigma0 = (2.0 * math.pi * (r_c_au * AU_CM) ** 2 / k
+                       * (math.exp(-xi ** k) - math.exp(-xo ** k)))
+    return Chain(m_gas_msun * M_SUN_G / mass_per_sigma0, r_c_au, gamma, T_freeze, N_dissoc_cm2)
+
+
 def _sigma0_from_mass(m_gas_msun: float, r_in: float, r_out: float) -> float:
     """Sigma0 [g cm^-2] of Sigma = Sigma0 (r/100 au)^-1 exp(-r/300 au) holding M_gas
     between r_in and r_out (closed-form integral of 2 pi r Sigma dr)."""
