@@ -210,6 +210,37 @@ def serving_leg(dev, n=256, rate_hz=200.0, budget=40 << 30, max_inflight=8):
                         "{32,64,128}, samples {128,256,1024}, 30% gradients, 40 GB budget"}
 
 
+def chain_leg(dev, reps=50):
+    """Field chain (hydrostatic density, H2 column, CO-layer surfaces) on the 512x256 grid of
+    the observation workload: CUDA-event time per call, warm L2 (the grid is 0.5 MB)."""
+    import torch
+    from paper_2509_03623_b300 import _rt, synth
+    p = synth.config_observation(0)
+    c = synth.chain_params(p)
+    T = torch.tensor(np.ascontiguousarray(p.T, dtype=np.float32), device=dev)
+    for _ in range(3):
+        _rt.rt_field_chain(p, T, c)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        _rt.rt_field_chain(p, T, c, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nodes = p.nr * p.nz
+    gbs = 12.0 * nodes / (ms * 1e-3) / 1e9
+    return {"workload": f"chain_grid{p.nr}x{p.nz}", "ms": ms, "nodes": nodes,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": PEAKS.get("hbm_gbs", 6400.0),
+                         "unit": "GB/s", "frac": gbs / PEAKS.get("hbm_gbs", 6400.0),
+                         "traffic": None,
+                         "note": "12 algorithmic bytes per node (T read, n_H2 and N_H2 written); "
+                                 "one warp per radius column, so a 512-column grid is "
+                                 "latency-bound (two dependent scans over the column)"}}
+
+
 def neural_leg(dev, flush, reps=5):
     """Neural-field workload (512x512 px, 128 channels, 256 samples): tensor-core network
     with FP16 and BF16 operands, the FP32 network (cuBLAS, no TF32) driving the same march, and
@@ -443,6 +474,7 @@ def run_ours(args):
             "clocks": clocks,
         }
         if world == 1 and not args.no_serving:
+            out["field_chain"] = chain_leg(dev)
             out["neural"] = neural_leg(dev, flush)
             out["serving"] = serving_leg(dev)
         if world == 1 and not args.no_cpu_baseline:

@@ -215,6 +215,41 @@ int rt_render_adjoint_noalloc(const rt_grid *grid, const rt_fields *fields, cons
                               void *stream);
 
 /*
+ * rt_field_chain -- physics-constrained field chain: from a temperature grid to the H2
+ * density, the H2 column and the CO layer that the march reads (Methods, "Parametric Disk
+ * Modeling": Eq. gas_density_temp, the surface-density profile Sigma(r), Eq. column_density
+ * and Eq. co_layer; "Neural Temperature Recovery" derives these fields from the temperature).
+ * Per radius node r_i, on the node heights z_j = w_j r_i (w_j = j zr_max / (nz - 1)):
+ *   d ln rho / dz = -G M z m_mol / ((r^2 + z^2)^{3/2} k T) - d ln T / dz, integrated upward
+ *     from the midplane by the trapezoid rule on the nodes (the ln T term exactly);
+ *   rho scaled so that 2 int_0^{z_max} rho dz (trapezoid, mirror symmetry) = Sigma(r),
+ *     Sigma(r) = sigma0 (r / r_c)^-gamma exp(-(r / r_c)^{2 - gamma});
+ *   n_h2 = rho / m_mol (line->m_mol_amu);  N_h2(z_j) = int_{z_j}^{z_max} n_h2 dz (trapezoid);
+ *   the CO layer {T > T_freeze, 0.706 N_h2 > N_dissoc} as two surfaces in z/r:
+ *     h_lo = lowest w with T > T_freeze (T linear between nodes; 0 if the midplane node is
+ *            warmer, zr_max if no node is),
+ *     h_hi = highest w with 0.706 N_h2 > N_dissoc (N_h2 linear between nodes; 0 if none).
+ * grid: nodes and r spacing as for the render; geom->mstar_msun: M (>= 0).
+ * T: DEVICE [nz][nr] float32, > 0. Outputs (DEVICE, caller-allocated, overwritten):
+ *   n_h2 [nz][nr] float32 [cm^-3], N_h2 [nz][nr] float32 [cm^-2] (may be NULL),
+ *   h_lo, h_hi [nr] float32 (z/r; usable as rt_fields surfaces).
+ * FP32 arithmetic (the per-column r and Sigma in FP64); one warp per radius column.
+ * Returns RT_OK, RT_EINVAL (null pointer, grid with fewer than 2 nodes per axis, non-finite
+ * or out-of-range parameter) or RT_ECUDA.
+ */
+typedef struct {
+  double sigma0_gcm2;   /* Sigma0 [g cm^-2], >= 0 */
+  double r_c_au;        /* characteristic radius [au], > 0 */
+  double gamma;         /* surface-density power-law index, < 2 */
+  double T_freeze_K;    /* freeze-out temperature [K] */
+  double N_dissoc_cm2;  /* photodissociation threshold on 0.706 N_H2 [cm^-2], >= 0 */
+} rt_chain;
+
+int rt_field_chain(const rt_grid *grid, const rt_geom *geom, const rt_line *line,
+                   const rt_chain *chain, const float *T_K, float *n_h2, float *N_h2,
+                   float *h_lo, float *h_hi, void *stream);
+
+/*
  * rt_surface_powerlaw_grad -- chain rule from surface-node gradients to the parameters of a
  * power-law surface h(r) = c (r / 100 au)^p m(r) (m: any fixed modulation):
  *   out[0] = dL/dc = sum_i dL/dh_i h_i / c,   out[1] = dL/dp = sum_i dL/dh_i h_i ln(r_i/100 au),

@@ -76,6 +76,11 @@ _lock = threading.Lock()
 _lib = None
 
 
+class rt_chain(C.Structure):
+    _fields_ = [("sigma0_gcm2", C.c_double), ("r_c_au", C.c_double), ("gamma", C.c_double),
+                ("T_freeze_K", C.c_double), ("N_dissoc_cm2", C.c_double)]
+
+
 def lib():
     """Load librt_b300.so (after torch, so that one CUDA runtime serves both)."""
     global _lib
@@ -119,6 +124,10 @@ def lib():
             L.rt_render_modulated.argtypes = base + [C.c_void_p, C.c_double, C.c_void_p,
                                                      C.c_void_p]
             L.rt_render_modulated.restype = C.c_int
+            L.rt_field_chain.argtypes = [P(rt_grid), P(rt_geom), P(rt_line), P(rt_chain),
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p]
+            L.rt_field_chain.restype = C.c_int
             L.rt_mlp_status.argtypes = [P(C.c_int)]
             L.rt_mlp_status.restype = C.c_int
             L.rt_last_error.restype = C.c_char_p
@@ -294,6 +303,32 @@ def rt_surface_powerlaw_grad(problem, dh, h, c, stream=None):
     check(lib().rt_surface_powerlaw_grad(C.byref(g), _ptr(dh), _ptr(h), float(c), _ptr(out),
                                          stream_handle(stream)))
     return out
+
+
+def rt_field_chain(problem, T, chain, column=True, stream=None):
+    """Physics-constrained field chain on the grid of `problem` from the temperature grid T
+    (CUDA float32 [nz][nr]): dict(n_h2, N_h2 (None unless column), h_lo, h_hi). `chain` has
+    the attributes sigma0_gcm2, r_c_au, gamma, T_freeze, N_dissoc_cm2."""
+    import torch
+    shp = (int(problem.nz), int(problem.nr))
+    if not T.is_cuda or T.dtype != torch.float32 or not T.is_contiguous() or tuple(T.shape) != shp:
+        raise ValueError(f"T must be a contiguous CUDA float32 tensor of shape {shp}")
+    g = rt_grid(int(problem.nr), int(problem.nz), int(problem.r_log), float(problem.r_in_au),
+                float(problem.r_out_au), float(problem.zr_max))
+    o = rt_geom(float(problem.incl_deg), float(problem.pa_deg), float(problem.dist_pc),
+                float(problem.mstar_msun), float(problem.vsys_kms))
+    ln = rt_line(float(problem.nu0_hz), float(problem.A_ul), float(problem.B_rot_hz),
+                 float(problem.m_co_amu), float(problem.m_mol_amu), int(problem.J_u))
+    c = rt_chain(float(chain.sigma0_gcm2), float(chain.r_c_au), float(chain.gamma),
+                 float(chain.T_freeze), float(chain.N_dissoc_cm2))
+    n = torch.empty(shp, dtype=torch.float32, device=T.device)
+    N = torch.empty(shp, dtype=torch.float32, device=T.device) if column else None
+    lo = torch.empty(shp[1], dtype=torch.float32, device=T.device)
+    hi = torch.empty(shp[1], dtype=torch.float32, device=T.device)
+    check(lib().rt_field_chain(C.byref(g), C.byref(o), C.byref(ln), C.byref(c), _ptr(T),
+                               _ptr(n), _ptr(N) if N is not None else None, _ptr(lo), _ptr(hi),
+                               stream_handle(stream)))
+    return dict(n_h2=n, N_h2=N, h_lo=lo, h_hi=hi)
 
 
 class DeviceMLP:

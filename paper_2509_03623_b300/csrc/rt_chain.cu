@@ -1,0 +1,185 @@
+// Physics-constrained field chain (arXiv 2509.03623, Methods: "Parametric Disk Modeling",
+// Eq. gas_density_temp (vertical hydrostatic equilibrium), the surface-density profile
+// Sigma(r), Eq. column_density (H2 column above a point) and Eq. co_layer (freeze-out and
+// photodissociation); "Neural Temperature Recovery" derives these secondary fields from the
+// temperature, so this is the step that turns a temperature grid into the density and CO
+// layer the march reads).
+//
+// Per radius node r_i, on the node heights z_j = w_j r_i (w_j = j zr_max / (nz - 1)):
+//   ln rho_j = ln rho_0 - I_j - ln(T_j / T_0),  I_j = int_0^{z_j} G M m_mol z / ((r^2+z^2)^{3/2} k T) dz
+//     (trapezoid rule on the nodes; the d ln T / dz term integrates exactly);
+//   rho normalised so that 2 int_0^{z_max} rho dz (trapezoid) = Sigma(r);
+//   n_H2 = rho / m_mol;  N_H2(z_j) = int_{z_j}^{z_max} n_H2 dz (trapezoid);
+//   the CO layer {T > T_freeze, 0.706 N_H2 > N_dissoc} as two surfaces in z/r: h_lo at the
+//   first upward crossing of T_freeze (T linear between nodes), h_hi where 0.706 N_H2 falls to
+//   N_dissoc (N_H2 linear between nodes).
+//
+// One warp per radius column: lanes take 32 consecutive nodes at a time, the two running
+// integrals are warp scans (upward for I, downward for N) with a carry between chunks, and
+// the surfaces come from warp ballots. FP32 throughout except the per-column constants
+// (r_i, Sigma(r_i)), which lane 0 forms in double precision. Pass 1 leaves the unnormalised
+// density in n_h2; pass 2 scales it and integrates the column from the top.
+#include "rt_internal.cuh"
+
+namespace rtb {
+
+struct ChainDev {
+  int nr, nz, r_log;
+  double r_in, r_out, zr_max;
+  double sigma0, r_c, gamma;
+  float A;         // G M m_mol / (k au) [K au]: gravity term per au of height, times 1/T
+  float m_mol_g;   // mean molecular mass [g]
+  float T_freeze, N_dissoc;
+};
+
+constexpr double kChainGMsun = 1.3271244e26;    // cm^3 s^-2
+constexpr double kChainK = 1.380649e-16;        // erg / K
+constexpr double kChainAmu = 1.66053906660e-24; // g
+constexpr double kChainAu = 1.495978707e13;     // cm
+
+__global__ void field_chain_kernel(const ChainDev C, const float *__restrict__ T,
+                                   float *__restrict__ n_out, float *__restrict__ N_out,
+                                   float *__restrict__ h_lo, float *__restrict__ h_hi) {
+  const int lane = threadIdx.x & 31;
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i >= C.nr) return;  // warp-uniform
+  const unsigned full = 0xffffffffu;
+  const int nr = C.nr, nz = C.nz;
+  const int nchunk = (nz + 31) / 32;
+
+  // per-column constants in double precision (one lane), broadcast
+  float r = 0.0f, sig = 0.0f;
+  if (lane == 0) {
+    const double t = (double)i / (nr - 1);
+    const double rd = C.r_log ? C.r_in * pow(C.r_out / C.r_in, t) : C.r_in + (C.r_out - C.r_in) * t;
+    const double x = rd / C.r_c;
+    r = (float)rd;
+    sig = (float)(C.sigma0 * pow(x, -C.gamma) * exp(-pow(x, 2.0 - C.gamma)));
+  }
+  r = __shfl_sync(full, r, 0);
+  sig = __shfl_sync(full, sig, 0);
+  const float dw = (float)(C.zr_max / (nz - 1));
+  const float dz = dw * r;  // au
+  const float r2 = r * r;
+  const float T0 = __ldg(T + i);
+
+  // ---- pass 1 (upward): I_j, unnormalised density e_j, trapezoid sum, freeze-out crossing ----
+  float I_carry = 0.0f, g_carry = 0.0f, S = 0.0f;
+  int j_warm = -1;  // first node with T > T_freeze
+  for (int c = 0; c < nchunk; c++) {
+    const int j = 32 * c + lane;
+    const bool valid = j < nz;
+    const float Tj = valid ? __ldg(T + (long long)j * nr + i) : 1.0f;
+    const float z = dw * (float)j * r;
+    const float d = fmaf(z, z, r2);
+    const float g = C.A * z / (d * sqrtf(d) * Tj);  // [1/au]
+    float gprev = __shfl_up_sync(full, g, 1);
+    if (lane == 0) gprev = g_carry;
+    float inc = (valid && j > 0) ? 0.5f * dz * (gprev + g) : 0.0f;
+    // inclusive warp scan of the trapezoid increments
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float v = __shfl_up_sync(full, inc, o);
+      if (lane >= o) inc += v;
+    }
+    const float I = I_carry + inc;
+    const float e = expf(-I - logf(Tj / T0));
+    if (valid) {
+      n_out[(long long)j * nr + i] = e;
+      S += (j == 0 || j == nz - 1) ? 0.5f * e : e;
+    }
+    I_carry = __shfl_sync(full, I, 31);
+    g_carry = __shfl_sync(full, g, 31);
+    if (j_warm < 0) {
+      const unsigned warm = __ballot_sync(full, valid && Tj > C.T_freeze);
+      if (warm) j_warm = 32 * c + __ffs(warm) - 1;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(full, S, o);
+  S *= dz;  // trapezoid integral of e over [0, z_max] in au
+
+  // freeze-out surface
+  if (lane == 0) {
+    float lo;
+    if (j_warm < 0) {
+      lo = (float)C.zr_max;
+    } else if (j_warm == 0) {
+      lo = 0.0f;
+    } else {
+      const float Ta = __ldg(T + (long long)(j_warm - 1) * nr + i);
+      const float Tb = __ldg(T + (long long)j_warm * nr + i);
+      lo = dw * ((float)(j_warm - 1) + (C.T_freeze - Ta) / (Tb - Ta));
+    }
+    h_lo[i] = lo;
+  }
+
+  // ---- pass 2 (downward): n = e * Sigma / (2 S m_mol), column N, photodissociation ----
+  __syncwarp();
+  const float scale = sig / (2.0f * S * (float)kChainAu * C.m_mol_g);  // [cm^-3] per unit e
+  const float dzc = dz * (float)kChainAu;                               // cm
+  float N_carry = 0.0f, n_carry = 0.0f;  // N and n at the first node of the chunk above
+  bool found = false;
+  float hi = 0.0f;
+  for (int c = nchunk - 1; c >= 0; c--) {
+    const int j = 32 * c + lane;
+    const bool valid = j < nz;
+    const float n = valid ? n_out[(long long)j * nr + i] * scale : 0.0f;
+    if (valid) n_out[(long long)j * nr + i] = n;
+    float nnext = __shfl_down_sync(full, n, 1);
+    if (lane == 31) nnext = n_carry;
+    float seg = (valid && j < nz - 1) ? 0.5f * dzc * (n + nnext) : 0.0f;
+    // inclusive suffix scan: seg_j + seg_{j+1} + ... within the chunk
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float v = __shfl_down_sync(full, seg, o);
+      if (lane + o < 32) seg += v;
+    }
+    const float N = N_carry + seg;
+    if (valid && N_out) N_out[(long long)j * nr + i] = N;
+    if (!found) {
+      const unsigned thick = __ballot_sync(full, valid && 0.706f * N > C.N_dissoc);
+      if (thick) {
+        found = true;
+        const int top = 31 - __clz(thick);  // highest qualifying node of the chunk
+        float Nb = __shfl_down_sync(full, N, 1);
+        if (lane == 31) Nb = N_carry;
+        const float Na = __shfl_sync(full, N, top);
+        Nb = __shfl_sync(full, Nb, top);
+        const float a = 0.706f * Na, b = 0.706f * Nb;
+        hi = dw * ((float)(32 * c + top) + (a - C.N_dissoc) / (a - b));
+      }
+    }
+    N_carry = __shfl_sync(full, N, 0);
+    n_carry = __shfl_sync(full, n, 0);
+  }
+  if (lane == 0) h_hi[i] = hi;
+}
+
+int launch_field_chain(const rt_grid &g, const rt_geom &geo, const rt_line &line,
+                       const rt_chain &c, const float *T, float *n, float *N, float *h_lo,
+                       float *h_hi, cudaStream_t stream) {
+  ChainDev C;
+  C.nr = g.nr;
+  C.nz = g.nz;
+  C.r_log = g.r_log;
+  C.r_in = g.r_in_au;
+  C.r_out = g.r_out_au;
+  C.zr_max = g.zr_max;
+  C.sigma0 = c.sigma0_gcm2;
+  C.r_c = c.r_c_au;
+  C.gamma = c.gamma;
+  const double m = line.m_mol_amu * kChainAmu;
+  C.A = (float)(kChainGMsun * geo.mstar_msun * m / (kChainK * kChainAu));
+  C.m_mol_g = (float)m;
+  C.T_freeze = (float)c.T_freeze_K;
+  C.N_dissoc = (float)c.N_dissoc_cm2;
+  const int threads = 256;  // 8 columns per block
+  const long long blocks = ((long long)g.nr * 32 + threads - 1) / threads;
+  field_chain_kernel<<<(unsigned)blocks, threads, 0, stream>>>(C, T, n, N, h_lo, h_hi);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "field chain launch: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
+}  // namespace rtb

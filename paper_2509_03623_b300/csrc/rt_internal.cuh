@@ -304,6 +304,9 @@ int set_error(int code, const char *fmt, ...);
 void clear_error();
 int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream);
 size_t cell_bytes(const MarchParams &P);
+int launch_field_chain(const rt_grid &g, const rt_geom &geo, const rt_line &line,
+                       const rt_chain &c, const float *T, float *n, float *N, float *h_lo,
+                       float *h_hi, cudaStream_t stream);
 int pack_cells(MarchParams &P, void *buf, cudaStream_t stream);
 int launch_count(const MarchParams &P, unsigned long long *count, cudaStream_t stream);
 void lane_layout(int nch, int *lpr, int *cpl);

@@ -1,0 +1,112 @@
+"""Field chain on the GPU (hydrostatic density, H2 column, CO-layer surfaces) vs the FP64
+oracle on the same float32 temperature grid.
+
+Tolerances from the FP32 arithmetic: the height integral I_j is a warp scan (depth
+log2(32) plus one carry per 32-node chunk, ~13 roundings), so the exponent -I_j carries
+about 13 x 2^-24 |I_j|; where the density is above 1e-6 of its column maximum |I_j| <= ~15,
+giving ~1.2e-5 relative plus the expf/logf ulps; the normalisation and the column add a few
+1e-6. Required: 1e-4 relative there, 1e-9 of the column maximum below it; surfaces to 1e-5
+in z/r (a crossing moves by the relative error of N_H2 times N_H2 / |dN_H2/dw| < 0.1).
+"""
+
+import numpy as np
+import pytest
+
+from paper_2509_03623_b300 import synth
+from tests.cubecheck import assert_cube_close
+from tests.test_forward_gpu import rt  # noqa: F401  (module fixture)
+
+pytestmark = pytest.mark.gpu
+
+
+def check_chain(got, ref, label=""):
+    n, nr_ = got["n_h2"], ref["n_h2"]
+    colmax = nr_.max(axis=0, keepdims=True)
+    big = nr_ > 1e-6 * colmax
+    rel = np.abs(n - nr_)[big] / nr_[big]
+    assert rel.max() <= 1e-4, f"{label} n_h2 rel {rel.max():.2e}"
+    assert (np.abs(n - nr_)[~big] <= 1e-9 * np.broadcast_to(colmax, n.shape)[~big]).all(), label
+    if got["N_h2"] is not None:
+        N, Nr = got["N_h2"], ref["N_h2"]
+        bigN = Nr > 1e-6 * Nr[0:1]
+        relN = np.abs(N - Nr)[bigN] / Nr[bigN]
+        assert relN.max() <= 1e-4, f"{label} N_h2 rel {relN.max():.2e}"
+    for k in ("h_lo", "h_hi"):
+        d = np.abs(got[k] - ref[k]).max()
+        assert d <= 1e-5, f"{label} {k} max diff {d:.2e}"
+    return float(rel.max())
+
+
+def run_both(rt, orc, p, T, chain, column=True):
+    import torch
+    T32 = np.ascontiguousarray(T, dtype=np.float32)
+    out = rt.rt_field_chain(p, torch.tensor(T32, device="cuda"), chain, column=column)
+    torch.cuda.synchronize()
+    got = {k: (v.cpu().numpy().astype(np.float64) if v is not None else None)
+           for k, v in out.items()}
+    ref = orc.field_chain(p, chain, T32.astype(np.float64))
+    return got, ref
+
+
+def test_observation_grid(rt, orc):
+    p = synth.config_observation(0)
+    got, ref = run_both(rt, orc, p, p.T, synth.chain_params(p))
+    print("chain obs grid: n rel", check_chain(got, ref, "obs"))
+
+
+@pytest.mark.parametrize("nr,nz,r_log", [(7, 45, 1), (5, 33, 0), (3, 2, 1), (9, 32, 1),
+                                         (6, 97, 1)])
+def test_ragged_grids(rt, orc, nr, nz, r_log):
+    p = synth.config_small(3)
+    rng = np.random.default_rng(nr * 100 + nz)
+    T = 12.0 + 50.0 * rng.random((nz, nr)) + 30.0 * np.linspace(0, 1, nz)[:, None]
+    q = p.replace(nr=nr, nz=nz, r_log=r_log, T=T, n_h2=np.zeros((nz, nr)),
+                  vturb=np.zeros((nz, nr)), h_lo=np.zeros(nr), h_hi=np.zeros(nr))
+    got, ref = run_both(rt, orc, q, T, synth.chain_params(q), column=(nz != 45))
+    check_chain(got, ref, f"{nr}x{nz}")
+
+
+def test_surface_edge_cases(rt, orc):
+    p = synth.config_small(4)
+    nz, nr = p.nz, p.nr
+    w = p.zr_nodes()[:, None]
+    T = np.empty((nz, nr))
+    T[:, :10] = 25.0 + 20.0 * w                  # warm from the midplane: h_lo = 0
+    T[:, 10:20] = 8.0 + 5.0 * w                  # always frozen: h_lo = zr_max
+    T[:, 20:] = 10.0 + 60.0 * w                  # crossing inside the column
+    c = synth.chain_params(p)
+    got, ref = run_both(rt, orc, p, T, c)
+    check_chain(got, ref, "edges")
+    assert np.all(got["h_lo"][:10] == 0.0) and np.all(got["h_lo"][10:20] == np.float32(p.zr_max))
+    thin = synth.chain_params(p, m_gas_msun=1e-12)  # column never reaches N_dissoc: h_hi = 0
+    got, ref = run_both(rt, orc, p, T, thin)
+    check_chain(got, ref, "thin")
+    assert np.all(got["h_hi"] == 0.0)
+
+
+def test_rejects_bad_arguments(rt):
+    import torch
+    p = synth.config_small(0)
+    T = torch.full((p.nz, p.nr), 30.0, device="cuda")
+    with pytest.raises(rt.RTError):
+        rt.rt_field_chain(p, T, synth.chain_params(p, gamma=2.5))
+    with pytest.raises(rt.RTError):
+        rt.rt_field_chain(p.replace(nz=1), torch.full((1, p.nr), 30.0, device="cuda"),
+                          synth.chain_params(p))
+
+
+def test_chain_then_render_matches_oracle_chain_then_render(rt, orc):
+    """End to end: the density and CO layer from the chain, rendered; the oracle does both
+    steps in FP64 from the same temperature grid."""
+    import torch
+    p = synth.config_small(5)
+    c = synth.chain_params(p)
+    T32 = np.ascontiguousarray(p.T, dtype=np.float32)
+    out = rt.rt_field_chain(p, torch.tensor(T32, device="cuda"), c, column=False)
+    dd = rt.DeviceDisk(p)
+    dd.T = torch.tensor(T32, device="cuda")
+    dd.n_h2, dd.h_lo, dd.h_hi = out["n_h2"], out["h_lo"], out["h_hi"]
+    cube = rt.rt_render(p, dd).cpu().numpy()
+    ref = orc.field_chain(p, c, T32.astype(np.float64))
+    q = p.replace(T=T32.astype(np.float64), n_h2=ref["n_h2"], h_lo=ref["h_lo"], h_hi=ref["h_hi"])
+    assert_cube_close(cube, orc.render(q), label="chain + render")
