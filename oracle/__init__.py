@@ -51,6 +51,7 @@ class _Problem(C.Structure):
         ("units", C.c_int),
         ("nu0_hz", C.c_double), ("A_ul", C.c_double), ("B_rot_hz", C.c_double),
         ("m_co_amu", C.c_double), ("m_mol_amu", C.c_double), ("J_u", C.c_int),
+        ("vphi", C.POINTER(C.c_double)),
     ]
 
 
@@ -90,6 +91,7 @@ def _load():
             lib.orc_render_mlp_adjoint.argtypes = [pp, C.POINTER(_MLP), dp, dp, dp, dp, dp, dp,
                                                    dp, dp, dp, C.c_int]
             lib.orc_field_chain.argtypes = [pp, C.POINTER(_Chain), dp, dp, dp, dp, dp]
+            lib.orc_pressure_vphi.argtypes = [pp, dp, dp, dp]
             _lib = lib
     return _lib
 
@@ -123,6 +125,8 @@ class _Packed:
         s.n_samples, s.I0, s.units = int(p.n_samples), float(p.I0), int(p.units)
         s.nu0_hz, s.A_ul, s.B_rot_hz = float(p.nu0_hz), float(p.A_ul), float(p.B_rot_hz)
         s.m_co_amu, s.m_mol_amu, s.J_u = float(p.m_co_amu), float(p.m_mol_amu), int(p.J_u)
+        vphi = getattr(p, "vphi", None)
+        s.vphi = arr(vphi) if vphi is not None else C.POINTER(C.c_double)()
         self.s = s
         self.nch = s.nch
 
@@ -325,3 +329,16 @@ def field_chain(p, chain, T=None):
     if rc != 0:
         raise ValueError("orc_field_chain: invalid arguments")
     return dict(n_h2=n, N_h2=N, h_lo=lo, h_hi=hi)
+
+
+def pressure_vphi(p, n_h2=None, T=None):
+    """Pressure-corrected rotation [nz][nr] km/s (rt_oracle.h, orc_pressure_vphi) from the
+    node fields n_h2 and T (p's when None)."""
+    lib = _load()
+    pk = _Packed(p)
+    n = np.ascontiguousarray(np.asarray(p.n_h2 if n_h2 is None else n_h2, dtype=np.float64))
+    Tg = np.ascontiguousarray(np.asarray(p.T if T is None else T, dtype=np.float64))
+    out = np.zeros((p.nz, p.nr))
+    if lib.orc_pressure_vphi(C.byref(pk.s), _dptr(n), _dptr(Tg), _dptr(out)) != 0:
+        raise ValueError("orc_pressure_vphi: invalid arguments")
+    return out

@@ -246,7 +246,10 @@ static void eval_point(const orc_problem *p, const orc_mlp *m, const double P[3]
   /* Keplerian rotation (first term of Eq. gas_velocity_pressure), counter-clockwise about
      +z: v = v_phi (-y/r, x/r, 0). Line-of-sight velocity omega.v plus systemic velocity. */
   double rc = r * AU_CM, zc = z * AU_CM;
-  double vphi = sqrt(GM_SUN * p->mstar_msun * rc * rc / pow(rc * rc + zc * zc, 1.5));
+  /* with a rotation field (pressure-corrected, Eq. gas_velocity_pressure): its bilinear
+     interpolation, km/s -> cm/s */
+  double vphi = p->vphi ? 1e5 * bilerp(p->vphi, p->nr, i0, j0, st->fr, st->fz)
+                        : sqrt(GM_SUN * p->mstar_msun * rc * rc / pow(rc * rc + zc * zc, 1.5));
   double v[3] = {-vphi * y / r, vphi * x / r, 0.0};
   st->vlos = om[0] * v[0] + om[1] * v[1] + om[2] * v[2] + p->vsys_kms * 1e5;
   /* Line width: thermal + turbulent. Absolute mode (v_turb in km/s) or the paper's Mach
@@ -895,5 +898,54 @@ int orc_field_chain(const orc_problem *p, const orc_chain *c, const double *T, d
   free(z);
   free(lnrho);
   free(N);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Pressure-corrected rotation (see rt_oracle.h), node by node.
+ * ------------------------------------------------------------------------------------------ */
+static double node_r_au(const orc_problem *p, int i) {
+  return p->r_log ? p->r_in_au * pow(p->r_out_au / p->r_in_au, (double)i / (p->nr - 1))
+                  : p->r_in_au + (p->r_out_au - p->r_in_au) * i / (p->nr - 1);
+}
+
+/* derivative of f along an axis of n uniformly spaced nodes (spacing h) at node k, from
+   the values f(k') = F[k' * stride] */
+static double axis_diff(const double *F, long long stride, int n, int k, double h) {
+  if (n == 2) return (F[stride] - F[0]) / h;
+  if (k == 0) return (-3.0 * F[0] + 4.0 * F[stride] - F[2 * stride]) / (2.0 * h);
+  if (k == n - 1)
+    return (3.0 * F[k * stride] - 4.0 * F[(k - 1) * stride] + F[(k - 2) * stride]) / (2.0 * h);
+  return (F[(k + 1) * stride] - F[(k - 1) * stride]) / (2.0 * h);
+}
+
+int orc_pressure_vphi(const orc_problem *p, const double *n_h2, const double *T, double *vphi) {
+  if (!p || !n_h2 || !T || !vphi || p->nr < 2 || p->nz < 2) return -1;
+  const int nr = p->nr, nz = p->nz;
+  double *P = (double *)malloc(sizeof(double) * (size_t)nr * nz);
+  if (!P) return -1;
+  for (long long k = 0; k < (long long)nr * nz; k++) P[k] = n_h2[k] * K_BOLTZ * T[k];
+  const double hu = p->r_log ? log(p->r_out_au / p->r_in_au) / (nr - 1)
+                             : (p->r_out_au - p->r_in_au) * AU_CM / (nr - 1);
+  const double hw = p->zr_max / (nz - 1);
+  const double GM = GM_SUN * p->mstar_msun, m = p->m_mol_amu * AMU_G;
+  for (int j = 0; j < nz; j++) {
+    const double w = hw * j;
+    for (int i = 0; i < nr; i++) {
+      const double r = node_r_au(p, i) * AU_CM, z = w * r;
+      const double kep = GM * r * r / pow(r * r + z * z, 1.5);
+      const long long k = (long long)j * nr + i;
+      double v2 = kep;
+      if (n_h2[k] > 0.0) {
+        const double dPu = axis_diff(P + (long long)j * nr, 1, nr, i, hu);
+        const double dPw = axis_diff(P + i, nr, nz, j, hw);
+        const double dudr = p->r_log ? 1.0 / r : 1.0;
+        const double dPdr = dudr * dPu - (w / r) * dPw;
+        v2 += r / (m * n_h2[k]) * dPdr;
+      }
+      vphi[k] = v2 > 0.0 ? sqrt(v2) / 1e5 : 0.0;
+    }
+  }
+  free(P);
   return 0;
 }

@@ -47,6 +47,10 @@ typedef struct {
   /* line (rigid rotor, J_u -> J_u-1) */
   double nu0_hz, A_ul, B_rot_hz, m_co_amu, m_mol_amu;
   int J_u;
+  /* optional rotation field [nz][nr] in km/s (Eq. gas_velocity_pressure with the pressure
+     term, e.g. from orc_pressure_vphi), interpolated like the other node fields; NULL: the
+     Keplerian term alone, evaluated exactly at each point */
+  const double *vphi;
 } orc_problem;
 
 /* Full cube [nch][ny][nx]. Returns 0, or -1 on invalid arguments. */
@@ -135,6 +139,16 @@ typedef struct {
 
 int orc_field_chain(const orc_problem *p, const orc_chain *c, const double *T, double *n_h2,
                     double *N_h2, double *h_lo, double *h_hi);
+
+/* Pressure-corrected rotation on the nodes (Eq. gas_velocity_pressure):
+     v_phi^2 = G M r^2 / (r^2 + z^2)^{3/2} + (r / rho) dP/dr |_z,  P = n_H2 k T,  rho = m_mol n_H2,
+   with dP/dr at constant z from the grid coordinates (u = ln r or r, w = z/r):
+     dP/dr |_z = (du/dr) dP/du |_w - (w / r) dP/dw |_u,
+   each derivative a second-order central difference (second-order one-sided at the first and
+   last node; first-order when the axis has two nodes). v_phi^2 < 0 (pressure support beyond
+   gravity) gives v_phi = 0; a node without gas (n_H2 = 0) keeps the Keplerian term. Uses
+   p->nr, nz, r_log, r_in_au, r_out_au, zr_max, mstar_msun, m_mol_amu. vphi [nz][nr] km/s. */
+int orc_pressure_vphi(const orc_problem *p, const double *n_h2, const double *T, double *vphi);
 
 #ifdef __cplusplus
 }

@@ -95,6 +95,8 @@ class Problem:
     m_co_amu: float = CO_MASS_AMU
     m_mol_amu: float = MEAN_MOL_AMU
     J_u: int = 2
+    # optional rotation field [nz][nr] km/s (pressure-corrected); None: Keplerian
+    vphi: Optional[np.ndarray] = None
     # provenance
     name: str = ""
     seed: int = 0
