@@ -232,7 +232,31 @@ def chain_leg(dev, reps=50):
     ms = e0.elapsed_time(e1) / reps
     nodes = p.nr * p.nz
     gbs = 12.0 * nodes / (ms * 1e-3) / 1e9
+    # pressure-corrected rotation from the chain's density, and the observation-scale march
+    # driven by it (one more corner quad per sample)
+    ch = _rt.rt_field_chain(p, T, c, column=False)
+    vphi = _rt.rt_pressure_vphi(p, ch["n_h2"], T)
+    e0.record(st)
+    for _ in range(reps):
+        _rt.rt_pressure_vphi(p, ch["n_h2"], T, out=vphi, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_vphi = e0.elapsed_time(e1) / reps
+    dd = _rt.DeviceDisk(p, dev)
+    dd.n_h2, dd.h_lo, dd.h_hi, dd.vphi = ch["n_h2"], ch["h_lo"], ch["h_hi"], vphi
+    cube = torch.empty((p.nch, p.ny, p.nx), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        _rt.rt_render(p, dd, cube, stream=st)
+    e0.record(st)
+    for _ in range(10):
+        _rt.rt_render(p, dd, cube, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_render = e0.elapsed_time(e1) / 10
     return {"workload": f"chain_grid{p.nr}x{p.nz}", "ms": ms, "nodes": nodes,
+            "rotation_ms": ms_vphi,
+            "render_chain_fields_rotation_ms": ms_render,
+            "render_chain_fields_rotation_gevals": p.evals / (ms_render * 1e-3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": PEAKS.get("hbm_gbs", 6400.0),
                          "unit": "GB/s", "frac": gbs / PEAKS.get("hbm_gbs", 6400.0),
                          "traffic": None,

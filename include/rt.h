@@ -78,6 +78,12 @@ typedef struct {
   double x_co;            /* CO abundance between the surfaces */
   double edge_w;          /* logistic edge width in z/r (0: hard steps) */
   int vturb_mach;         /* 0: alpha^2 = 2kT/m_CO + v_turb^2; 1: + v_turb^2 2kT/m_mol */
+  const float *vphi_kms;  /* optional rotation speed v_phi [km/s], [nz][nr] (Eq.
+                             gas_velocity_pressure with the pressure term, e.g. from
+                             rt_pressure_vphi), interpolated like the other fields and
+                             projected as v_los = v_phi (x / r) sin i + v_sys; NULL: the
+                             Keplerian term alone, evaluated at each sample. The adjoint
+                             entry points reject a non-NULL vphi_kms (forward only). */
 } rt_fields;
 
 /* Viewing geometry and kinematics. */
@@ -248,6 +254,25 @@ typedef struct {
 int rt_field_chain(const rt_grid *grid, const rt_geom *geom, const rt_line *line,
                    const rt_chain *chain, const float *T_K, float *n_h2, float *N_h2,
                    float *h_lo, float *h_hi, void *stream);
+
+/*
+ * rt_pressure_vphi -- pressure-corrected rotation on the nodes (Methods, "Parametric Disk
+ * Modeling", Eq. gas_velocity_pressure; "Neural Temperature Recovery" derives v_phi from
+ * the density and temperature this way):
+ *   v_phi^2 = G M r^2 / (r^2 + z^2)^{3/2} + (r / rho) dP/dr |_z,  P = n_H2 k T,
+ *   rho = m_mol n_H2 (line->m_mol_amu), M = geom->mstar_msun,
+ * with dP/dr at constant z from the grid coordinates (u = ln r on a log grid, r on a linear
+ * one; w = z/r): dP/dr |_z = (du/dr) dP/du |_w - (w / r) dP/dw |_u, each a second-order
+ * central difference over the nodes (second-order one-sided at the first and last node,
+ * first order on a two-node axis). Where v_phi^2 < 0 (pressure support beyond gravity) the
+ * result is 0; a node with n_H2 = 0 keeps the Keplerian term.
+ * n_h2, T_K: DEVICE [nz][nr] float32; vphi_kms: DEVICE [nz][nr] float32, overwritten (km/s,
+ * usable as rt_fields.vphi_kms). FP32, one thread per node.
+ * Returns RT_OK, RT_EINVAL (null pointer, grid with fewer than 2 nodes per axis, invalid
+ * extent, mass or molecular mass) or RT_ECUDA.
+ */
+int rt_pressure_vphi(const rt_grid *grid, const rt_geom *geom, const rt_line *line,
+                     const float *n_h2, const float *T_K, float *vphi_kms, void *stream);
 
 /*
  * rt_surface_powerlaw_grad -- chain rule from surface-node gradients to the parameters of a

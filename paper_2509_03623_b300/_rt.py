@@ -35,7 +35,7 @@ class rt_grid(C.Structure):
 class rt_fields(C.Structure):
     _fields_ = [("T_K", C.c_void_p), ("n_h2_cm3", C.c_void_p), ("vturb", C.c_void_p),
                 ("h_lo", C.c_void_p), ("h_hi", C.c_void_p), ("x_co", C.c_double),
-                ("edge_w", C.c_double), ("vturb_mach", C.c_int)]
+                ("edge_w", C.c_double), ("vturb_mach", C.c_int), ("vphi_kms", C.c_void_p)]
 
 
 class rt_geom(C.Structure):
@@ -128,6 +128,9 @@ def lib():
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p]
             L.rt_field_chain.restype = C.c_int
+            L.rt_pressure_vphi.argtypes = [P(rt_grid), P(rt_geom), P(rt_line), C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p]
+            L.rt_pressure_vphi.restype = C.c_int
             L.rt_mlp_status.argtypes = [P(C.c_int)]
             L.rt_mlp_status.restype = C.c_int
             L.rt_last_error.restype = C.c_char_p
@@ -160,13 +163,17 @@ class DeviceDisk:
         for k in self.FIELDS:
             setattr(self, k, torch.as_tensor(
                 np.ascontiguousarray(getattr(problem, k), dtype=np.float32), device=self.device))
+        vphi = getattr(problem, "vphi", None)  # optional rotation field (None: Keplerian)
+        self.vphi = (torch.as_tensor(np.ascontiguousarray(vphi, dtype=np.float32),
+                                     device=self.device) if vphi is not None else None)
 
     def tensors(self):
         return tuple(getattr(self, k) for k in self.FIELDS)
 
 
-def structs(problem, T, n, vt, hlo, hhi):
-    """C structs for `problem` with field tensors (CUDA float32, contiguous)."""
+def structs(problem, T, n, vt, hlo, hhi, vphi=None):
+    """C structs for `problem` with field tensors (CUDA float32, contiguous); vphi: optional
+    rotation field [nz][nr] km/s (None: Keplerian)."""
     for t, shp in ((T, (problem.nz, problem.nr)), (n, (problem.nz, problem.nr)),
                    (vt, (problem.nz, problem.nr)), (hlo, (problem.nr,)), (hhi, (problem.nr,))):
         if (not t.is_cuda or t.dtype.itemsize != 4 or not t.is_floating_point()
@@ -174,8 +181,12 @@ def structs(problem, T, n, vt, hlo, hhi):
             raise ValueError(f"field tensors must be contiguous CUDA float32 of shape {shp}")
     g = rt_grid(int(problem.nr), int(problem.nz), int(problem.r_log), float(problem.r_in_au),
                 float(problem.r_out_au), float(problem.zr_max))
+    if vphi is not None and (not vphi.is_cuda or vphi.dtype.itemsize != 4 or not vphi.is_contiguous()
+                             or tuple(vphi.shape) != (problem.nz, problem.nr)):
+        raise ValueError("vphi must be a contiguous CUDA float32 tensor of shape [nz][nr]")
     f = rt_fields(T.data_ptr(), n.data_ptr(), vt.data_ptr(), hlo.data_ptr(), hhi.data_ptr(),
-                  float(problem.x_co), float(problem.edge_w), int(problem.vturb_mach))
+                  float(problem.x_co), float(problem.edge_w), int(problem.vturb_mach),
+                  vphi.data_ptr() if vphi is not None else None)
     o = rt_geom(float(problem.incl_deg), float(problem.pa_deg), float(problem.dist_pc),
                 float(problem.mstar_msun), float(problem.vsys_kms))
     v = np.ascontiguousarray(np.asarray(problem.v_kms, dtype=np.float32))
@@ -192,7 +203,8 @@ def rt_render(problem, fields=None, out=None, stream=None):
     import torch
     dd = fields if fields is not None else DeviceDisk(problem)
     T, n, vt, hlo, hhi = dd.tensors()
-    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi,
+                                       getattr(dd, "vphi", None))
     if out is None:
         out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=T.device)
     check(lib().rt_render(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
@@ -205,7 +217,8 @@ def rt_count_gas_samples(problem, fields=None, stream=None) -> int:
     import torch
     dd = fields if fields is not None else DeviceDisk(problem)
     T, n, vt, hlo, hhi = dd.tensors()
-    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi,
+                                       getattr(dd, "vphi", None))
     cnt = torch.zeros(1, dtype=torch.int64, device=T.device)
     check(lib().rt_count_gas_samples(C.byref(g), C.byref(f), C.byref(o), C.byref(vw),
                                      C.byref(ln), C.c_void_p(cnt.data_ptr()),
@@ -231,7 +244,8 @@ def rt_render_work(problem, fields=None, out=None, stream=None):
     import torch
     dd = fields if fields is not None else DeviceDisk(problem)
     T, n, vt, hlo, hhi = dd.tensors()
-    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi,
+                                       getattr(dd, "vphi", None))
     if out is None:
         out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=T.device)
     work = torch.zeros(2, dtype=torch.int64, device=T.device)
@@ -251,7 +265,8 @@ def rt_render_adjoint(problem, fields=None, dL_dcube=None, target=None, cube_out
     import torch
     dd = fields if fields is not None else DeviceDisk(problem)
     T, n, vt, hlo, hhi = dd.tensors()
-    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi,
+                                       getattr(dd, "vphi", None))
     shape = (vw.nch, vw.ny, vw.nx)
     dL_dcube = _cube_arg(dL_dcube, shape, "dL_dcube")
     target = _cube_arg(target, shape, "target")
@@ -279,7 +294,8 @@ def rt_render_adjoint_noalloc(problem, fields, cube_out, grads, dL_dcube=None, t
     gradient tensors in `grads`, keys T, n_h2, vturb, h_lo, h_hi, loss) is supplied by the
     caller; the library uses its fixed 16 MiB device array for checkpoints and gradient copies."""
     T, n, vt, hlo, hhi = fields.tensors()
-    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi,
+                                       getattr(fields, "vphi", None))
     shape = (vw.nch, vw.ny, vw.nx)
     dL_dcube = _cube_arg(dL_dcube, shape, "dL_dcube")
     target = _cube_arg(target, shape, "target")
@@ -331,6 +347,27 @@ def rt_field_chain(problem, T, chain, column=True, stream=None):
     return dict(n_h2=n, N_h2=N, h_lo=lo, h_hi=hi)
 
 
+def rt_pressure_vphi(problem, n_h2, T, out=None, stream=None):
+    """Pressure-corrected rotation [nz][nr] km/s from the node fields n_h2 and T (CUDA
+    float32 [nz][nr])."""
+    import torch
+    shp = (int(problem.nz), int(problem.nr))
+    for t in (n_h2, T):
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shp:
+            raise ValueError(f"n_h2 and T must be contiguous CUDA float32 tensors of shape {shp}")
+    g = rt_grid(int(problem.nr), int(problem.nz), int(problem.r_log), float(problem.r_in_au),
+                float(problem.r_out_au), float(problem.zr_max))
+    o = rt_geom(float(problem.incl_deg), float(problem.pa_deg), float(problem.dist_pc),
+                float(problem.mstar_msun), float(problem.vsys_kms))
+    ln = rt_line(float(problem.nu0_hz), float(problem.A_ul), float(problem.B_rot_hz),
+                 float(problem.m_co_amu), float(problem.m_mol_amu), int(problem.J_u))
+    if out is None:
+        out = torch.empty(shp, dtype=torch.float32, device=T.device)
+    check(lib().rt_pressure_vphi(C.byref(g), C.byref(o), C.byref(ln), _ptr(n_h2), _ptr(T),
+                                 _ptr(out), stream_handle(stream)))
+    return out
+
+
 class DeviceMLP:
     """Device-resident float32 network (master weights) in the layout of rt_mlp."""
 
@@ -375,7 +412,8 @@ def rt_render_mlp(problem, fields, net, out=None, stream=None):
     """Forward render with the tensor-core neural field modulating the grid fields."""
     import torch
     T, n, vt, hlo, hhi = fields.tensors()
-    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi,
+                                       getattr(fields, "vphi", None))
     if out is None:
         out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=T.device)
     m = net.struct()
@@ -415,7 +453,8 @@ def rt_render_mlp_adjoint(problem, fields, net, dL_dcube=None, target=None, cube
     parameter gradients."""
     import torch
     T, n, vt, hlo, hhi = fields.tensors()
-    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi,
+                                       getattr(fields, "vphi", None))
     shape = (vw.nch, vw.ny, vw.nx)
     dL_dcube = _cube_arg(dL_dcube, shape, "dL_dcube")
     target = _cube_arg(target, shape, "target")
@@ -443,7 +482,8 @@ def rt_sample_coords(problem, fields, out=None, stream=None):
     """Network inputs (rhat, zhat) of every (pixel, sample): [npix][n_samples][2]."""
     import torch
     T, n, vt, hlo, hhi = fields.tensors()
-    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi,
+                                       getattr(fields, "vphi", None))
     if out is None:
         out = torch.empty((vw.nx * vw.ny, vw.n_samples, 2), dtype=torch.float32, device=T.device)
     check(lib().rt_sample_coords(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
@@ -455,7 +495,8 @@ def rt_render_modulated(problem, fields, mod, h_scale, out=None, stream=None):
     """Forward render with per-sample network outputs mod [npix][n_samples][4]."""
     import torch
     T, n, vt, hlo, hhi = fields.tensors()
-    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi)
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi,
+                                       getattr(fields, "vphi", None))
     if out is None:
         out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=T.device)
     mod = mod.contiguous().float()

@@ -169,6 +169,7 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
   P->vt = f.vturb;
   P->hlo = f.h_lo;
   P->hhi = f.h_hi;
+  P->vphi = f.vphi_kms;
   P->x_co = (float)f.x_co;
   P->hard_edge = f.edge_w > 0 ? 0 : 1;
   P->edge_k = f.edge_w > 0 ? (float)(kLog2e / f.edge_w) : 0.0f;
@@ -178,6 +179,7 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
 
   double inc = o.incl_deg * kPi / 180.0, pa = o.pa_deg * kPi / 180.0;
   P->sin_i = sin(inc);
+  P->sin_if = (float)P->sin_i;
   P->cos_i = cos(inc);
   P->sin_pa = sin(pa);
   P->cos_pa = cos(pa);
@@ -303,6 +305,9 @@ int rtb::check_adjoint_args(const MarchParams &P, const float *dL_dcube, const f
                        const rt_grads *grads) {
   if (!grads || !grads->dT || !grads->dn || !grads->dvt || !grads->dh_lo || !grads->dh_hi)
     return set_error(RT_EINVAL, "null gradient output");
+  if (P.vphi)
+    return set_error(RT_EINVAL, "the adjoint takes the Keplerian rotation only (vphi_kms must "
+                                "be NULL)");
   long long n = (long long)P.nx * P.ny * P.nch;
   if (n > 0 && ((dL_dcube == nullptr) == (target == nullptr)))
     return set_error(RT_EINVAL, "give exactly one of dL_dcube and target");
@@ -320,6 +325,24 @@ extern "C" int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields,
   if (rc == RT_OK)
     rc = launch_adjoint(*P, dL_dcube, target, cube_out, *grads, (cudaStream_t)stream);
   delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+extern "C" int rt_pressure_vphi(const rt_grid *grid, const rt_geom *geom, const rt_line *line,
+                                const float *n_h2, const float *T_K, float *vphi_kms,
+                                void *stream) {
+  if (!grid || !geom || !line || !n_h2 || !T_K || !vphi_kms)
+    return set_error(RT_EINVAL, "null argument");
+  if (grid->nr < 2 || grid->nz < 2) return set_error(RT_EINVAL, "grid needs >= 2 nodes per axis");
+  if (!(grid->r_in_au > 0) || !(grid->r_out_au > grid->r_in_au) || !(grid->zr_max > 0) ||
+      !is_finite(grid->r_out_au) || !is_finite(grid->zr_max))
+    return set_error(RT_EINVAL, "invalid grid extent");
+  if (!(geom->mstar_msun >= 0) || !is_finite(geom->mstar_msun))
+    return set_error(RT_EINVAL, "stellar mass must be finite and >= 0");
+  if (!(line->m_mol_amu > 0) || !is_finite(line->m_mol_amu))
+    return set_error(RT_EINVAL, "mean molecular mass must be > 0");
+  int rc = launch_pressure_vphi(*grid, *geom, *line, n_h2, T_K, vphi_kms, (cudaStream_t)stream);
   if (rc == RT_OK) clear_error();
   return rc;
 }

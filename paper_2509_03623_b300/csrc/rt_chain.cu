@@ -156,6 +156,89 @@ __global__ void field_chain_kernel(const ChainDev C, const float *__restrict__ T
   if (lane == 0) h_hi[i] = hi;
 }
 
+// ---------------------------------------------------------------------------------------
+// Pressure-corrected rotation (Eq. gas_velocity_pressure) on the nodes:
+//   v_phi^2 = G M r^2 / (r^2 + z^2)^{3/2} + (r / rho) dP/dr |_z,  P = n k T,  rho = m_mol n,
+// dP/dr at constant z from the grid coordinates (u = ln r or r, w = z/r):
+//   dP/dr |_z = (du/dr) dP/du |_w - (w / r) dP/dw |_u,
+// second-order central differences (second-order one-sided at the first and last node,
+// first order on a two-node axis); v_phi^2 < 0 gives 0, a node without gas keeps the
+// Keplerian term. One thread per node (a 5-point stencil of n T), FP32 with the
+// gravitational term from per-node FP32 geometry; output in km/s.
+// ---------------------------------------------------------------------------------------
+struct VphiDev {
+  int nr, nz, r_log;
+  float r_in, r_out;
+  float lnratio;  // ln(r_out / r_in)
+  float hu, hw;   // node spacings in u (ln r, or r in au) and w
+  float gm;       // G M / au [km^2 s^-2]: v^2 = gm r^2 / (r^2+z^2)^{3/2} with r, z in au
+  float kpm;      // k / (m_mol) [km^2 s^-2 K^-1]
+};
+
+__device__ __forceinline__ float nT_at(const float *__restrict__ n, const float *__restrict__ T,
+                                       long long k) {
+  return __ldg(n + k) * __ldg(T + k);
+}
+
+// derivative of n T along an axis of `cnt` nodes spaced h at node index a (stride s)
+__device__ __forceinline__ float axis_d(const float *__restrict__ n, const float *__restrict__ T,
+                                        long long base, long long s, int cnt, int a, float h) {
+  if (cnt == 2) return (nT_at(n, T, base + s) - nT_at(n, T, base)) / h;
+  if (a == 0)
+    return (-3.0f * nT_at(n, T, base) + 4.0f * nT_at(n, T, base + s) - nT_at(n, T, base + 2 * s)) /
+           (2.0f * h);
+  const long long k = base + a * s;
+  if (a == cnt - 1)
+    return (3.0f * nT_at(n, T, k) - 4.0f * nT_at(n, T, k - s) + nT_at(n, T, k - 2 * s)) / (2.0f * h);
+  return (nT_at(n, T, k + s) - nT_at(n, T, k - s)) / (2.0f * h);
+}
+
+__global__ void pressure_vphi_kernel(const VphiDev V, const float *__restrict__ n,
+                                     const float *__restrict__ T, float *__restrict__ vphi) {
+  const long long total = (long long)V.nr * V.nz;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(k / V.nr), i = (int)(k - (long long)j * V.nr);
+    const float t = (float)i / (float)(V.nr - 1);
+    const float r = V.r_log ? V.r_in * expf(V.lnratio * t) : fmaf(V.r_out - V.r_in, t, V.r_in);
+    const float w = V.hw * (float)j;
+    const float d = fmaf(w * w, r * r, r * r);  // r^2 + z^2 [au^2]
+    float v2 = V.gm * r * r / (d * sqrtf(d));
+    const float nk = __ldg(n + k);
+    if (nk > 0.0f) {
+      const float dPu = axis_d(n, T, (long long)j * V.nr, 1, V.nr, i, V.hu);
+      const float dPw = axis_d(n, T, i, V.nr, V.nz, j, V.hw);
+      const float dudr = V.r_log ? 1.0f / r : 1.0f;  // per au
+      const float dPdr = fmaf(dudr, dPu, -(w / r) * dPw);  // d(nT)/dr per au
+      v2 = fmaf(r / nk, V.kpm * dPdr, v2);
+    }
+    vphi[k] = v2 > 0.0f ? sqrtf(v2) : 0.0f;
+  }
+}
+
+int launch_pressure_vphi(const rt_grid &g, const rt_geom &geo, const rt_line &line,
+                         const float *n, const float *T, float *vphi, cudaStream_t stream) {
+  VphiDev V;
+  V.nr = g.nr;
+  V.nz = g.nz;
+  V.r_log = g.r_log;
+  V.r_in = (float)g.r_in_au;
+  V.r_out = (float)g.r_out_au;
+  V.lnratio = (float)log(g.r_out_au / g.r_in_au);
+  V.hu = g.r_log ? (float)(log(g.r_out_au / g.r_in_au) / (g.nr - 1))
+                 : (float)((g.r_out_au - g.r_in_au) / (g.nr - 1));
+  V.hw = (float)(g.zr_max / (g.nz - 1));
+  V.gm = (float)(kChainGMsun * geo.mstar_msun / kChainAu / 1e10);
+  V.kpm = (float)(kChainK / (line.m_mol_amu * kChainAmu) / 1e10);
+  const long long total = (long long)g.nr * g.nz;
+  const long long blocks = (total + 255) / 256;
+  pressure_vphi_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, stream>>>(V, n, T,
+                                                                                      vphi);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "rotation launch: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
 int launch_field_chain(const rt_grid &g, const rt_geom &geo, const rt_line &line,
                        const rt_chain &c, const float *T, float *n, float *N, float *h_lo,
                        float *h_hi, cudaStream_t stream) {

@@ -232,16 +232,19 @@ void lane_layout(int nch, int *lpr, int *cpl) {
 // each field that the cell's bilinear interpolation reads.
 __global__ void pack_cells_kernel(const float *__restrict__ T, const float *__restrict__ n,
                                   const float *__restrict__ vt, const float *__restrict__ hlo,
-                                  const float *__restrict__ hhi, int nr, int nz,
+                                  const float *__restrict__ hhi,
+                                  const float *__restrict__ vphi, int nr, int nz,
                                   float4 *__restrict__ cell, float4 *__restrict__ hcell) {
   const long long m = (long long)(nr - 1) * (nz - 1);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(i / (nr - 1)), r = (int)(i - (long long)j * (nr - 1));
     const long long b = (long long)j * nr + r;  // node (r, j); the cell's nodes end at b+nr+1
-    cell[3 * i] = make_float4(T[b], T[b + 1], T[b + nr], T[b + nr + 1]);
-    cell[3 * i + 1] = make_float4(n[b], n[b + 1], n[b + nr], n[b + nr + 1]);
-    cell[3 * i + 2] = make_float4(vt[b], vt[b + 1], vt[b + nr], vt[b + nr + 1]);
+    cell[4 * i] = make_float4(T[b], T[b + 1], T[b + nr], T[b + nr + 1]);
+    cell[4 * i + 1] = make_float4(n[b], n[b + 1], n[b + nr], n[b + nr + 1]);
+    cell[4 * i + 2] = make_float4(vt[b], vt[b + 1], vt[b + nr], vt[b + nr + 1]);
+    cell[4 * i + 3] = vphi ? make_float4(vphi[b], vphi[b + 1], vphi[b + nr], vphi[b + nr + 1])
+                           : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (j == 0) hcell[r] = make_float4(hlo[r], hlo[r + 1], hhi[r], hhi[r + 1]);
   }
 }
@@ -257,7 +260,7 @@ size_t cell_bytes(const MarchParams &P) {
   const long long samples = (long long)P.nx * P.ny * P.n_samples;
   const long long cells = (long long)(P.nr - 1) * (P.nz - 1);
   if (samples < kCellMinSamples || samples < 8 * cells) return 0;
-  return (size_t)(3 * cells + (P.nr - 1)) * sizeof(float4);
+  return (size_t)(4 * cells + (P.nr - 1)) * sizeof(float4);
 }
 
 // Packs the corner quads into buf (cell_bytes(P) bytes, 16-byte aligned) on `stream` and
@@ -265,10 +268,10 @@ size_t cell_bytes(const MarchParams &P) {
 int pack_cells(MarchParams &P, void *buf, cudaStream_t stream) {
   const long long cells = (long long)(P.nr - 1) * (P.nz - 1);
   float4 *cell = reinterpret_cast<float4 *>(buf);
-  float4 *hcell = cell + 3 * cells;
+  float4 *hcell = cell + 4 * cells;
   const long long nb = (cells + 255) / 256;
   pack_cells_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, stream>>>(
-      P.T, P.n, P.vt, P.hlo, P.hhi, P.nr, P.nz, cell, hcell);
+      P.T, P.n, P.vt, P.hlo, P.hhi, P.vphi, P.nr, P.nz, cell, hcell);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "cell packing: %s", cudaGetErrorString(e));
   P.cell = cell;

@@ -25,6 +25,8 @@ struct MarchParams {
   float r_in2, inv_rin2;    // r_in^2 [au^2] and its reciprocal
   float zr_max, w_scale;    // w = (z/r) * w_scale
   const float *T, *n, *vt, *hlo, *hhi;
+  const float *vphi;        // optional rotation field [km/s]; nullptr: Keplerian
+  float sin_if;             // sin i (FP32, for v_los = v_phi x sin i / r)
   float x_co, edge_k;       // edge_k = log2(e) / edge_w
   int vturb_mach;
   float c_th, c_mach;       // alpha^2 [km^2 s^-2] = c_th T + vt^2  |  T (c_th + c_mach vt^2)
@@ -49,8 +51,9 @@ struct MarchParams {
   // physics was evaluated, channel evaluations computed; nullptr for none
   unsigned long long *work;
   // optional corner quads (pack_cells): per grid cell (i, j) the four nodes its bilinear
-  // interpolation reads, {f(i,j), f(i+1,j), f(i,j+1), f(i+1,j+1)}, for T, n_H2 and v_turb
-  // (three float4 per cell, cells in [j][i] order), and per radial interval i
+  // interpolation reads, {f(i,j), f(i+1,j), f(i,j+1), f(i+1,j+1)}, for T, n_H2, v_turb and
+  // the rotation field when there is one (four float4, 64 B per cell, cells in [j][i]
+  // order), and per radial interval i
   // {h_lo(i), h_lo(i+1), h_hi(i), h_hi(i+1)}: four 16-byte loads per sample instead of 16
   // scalar ones. nullptr: the kernels read the node arrays (same values, same rounding).
   const float4 *cell, *hcell;
@@ -173,6 +176,7 @@ struct Cell {
   int i0, j0;
   float fr, fz;
   float zr;
+  float ir;  // 1 / r
   bool gas;
 };
 
@@ -191,6 +195,7 @@ __device__ __forceinline__ Cell locate(const MarchParams &P, float z, float r2) 
   c.fr = u - (float)i0;
   c.fz = w - (float)j0;
   c.zr = zr;
+  c.ir = ir;
   return c;
 }
 
@@ -207,13 +212,15 @@ __device__ __forceinline__ float quad_lerp(const float4 &q, const Cell &c) {
 // Interpolated node fields at a located sample (the arithmetic of bilerp either way).
 struct NodeVals {
   float T, n, vt, hlo, hhi;
+  float vphi;  // rotation field (only with P.vphi)
 };
 
 __device__ __forceinline__ NodeVals fields_at(const MarchParams &P, const Cell &c) {
   NodeVals v;
   if (P.cell) {
-    const float4 *q = P.cell + 3 * ((long long)c.j0 * (P.nr - 1) + c.i0);
+    const float4 *q = P.cell + 4 * ((long long)c.j0 * (P.nr - 1) + c.i0);
     const float4 qT = __ldg(q), qn = __ldg(q + 1), qv = __ldg(q + 2);
+    v.vphi = P.vphi ? quad_lerp(__ldg(q + 3), c) : 0.0f;
     const float4 qh = __ldg(P.hcell + c.i0);
     v.T = quad_lerp(qT, c);
     v.n = quad_lerp(qn, c);
@@ -224,6 +231,7 @@ __device__ __forceinline__ NodeVals fields_at(const MarchParams &P, const Cell &
     v.T = bilerp(P.T, P.nr, c);
     v.n = bilerp(P.n, P.nr, c);
     v.vt = bilerp(P.vt, P.nr, c);
+    v.vphi = P.vphi ? bilerp(P.vphi, P.nr, c) : 0.0f;
     const float *hl = P.hlo + c.i0;
     const float *hh = P.hhi + c.i0;
     v.hlo = lerpf(__ldg(hl), __ldg(hl + 1), c.fr);
@@ -282,7 +290,8 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
     X = P.x_co * rcp((1.0f + ea) * (1.0f + eb));
   }
   // Keplerian rotation: v_los = sqrt(GM) sin i x (r^2 + z^2)^{-3/4} + v_sys
-  float vlos = fmaf(R.vfac, kepler_q(fmaf(z, z, r2)), P.vsys);
+  float vlos = P.vphi ? fmaf(f.vphi * (P.sin_if * R.x), c.ir, P.vsys)
+                     : fmaf(R.vfac, kepler_q(fmaf(z, z, r2)), P.vsys);
   // line width
   float Tg = fmaxf(T, 1e-3f);
   float a2 = P.vturb_mach ? Tg * fmaf(P.c_mach, vt * vt, P.c_th) : fmaf(P.c_th, Tg, vt * vt);
@@ -304,6 +313,8 @@ int set_error(int code, const char *fmt, ...);
 void clear_error();
 int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream);
 size_t cell_bytes(const MarchParams &P);
+int launch_pressure_vphi(const rt_grid &g, const rt_geom &geo, const rt_line &line,
+                         const float *n, const float *T, float *vphi, cudaStream_t stream);
 int launch_field_chain(const rt_grid &g, const rt_geom &geo, const rt_line &line,
                        const rt_chain &c, const float *T, float *n, float *N, float *h_lo,
                        float *h_hi, cudaStream_t stream);

@@ -66,7 +66,8 @@ class Server:
         else:
             if fields is None:
                 raise ValueError("fields are required")
-            g, f, o, vw, ln, v = _rt.structs(problem, *fields.tensors())
+            g, f, o, vw, ln, v = _rt.structs(problem, *fields.tensors(),
+                                             getattr(fields, "vphi", None))
         r = rt_request()
         r.kind, r.grid, r.fields, r.geom, r.view, r.line = kind, g, f, o, vw, ln
         r.cube, r.dL_dcube, r.target = _addr(cube), _addr(dL_dcube), _addr(target)
