@@ -78,7 +78,7 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   const float r2 = fmaf(R.x, R.x, y * y);
   const Cell c = locate(P, z, r2);
   if (!(c.gas && R.hit && k < P.n_samples)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  const NodeVals f = fields_at(P, c);
+  const NodeVals f = fields_at<false>(P, c);  // the adjoint takes Keplerian rotation
   float T = f.T, n = f.n, hlo = f.hlo, hhi = f.hhi;
   const float vt = f.vt;
   float mT = 1.0f, mn = 1.0f;

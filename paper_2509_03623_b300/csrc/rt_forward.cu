@@ -38,7 +38,7 @@ constexpr float kWinLog2 = 40.0f;  // skipped optical depths are below 2^-40 per
 
 // Blocks per SM the register budget is sized for: 6 (at most 85 registers) with 8 channels
 // per lane, 7 with 4.
-template <int LPR, int CPL>
+template <int LPR, int CPL, bool ROT>
 __global__ void __launch_bounds__(kWarps * 32, CPL == 8 ? 6 : 7)
     march_fwd_kernel(const __grid_constant__ MarchParams P, float *__restrict__ cube) {
   constexpr int R = 32 / LPR;  // rays marched together by one warp (one work unit)
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kWarps * 32, CPL == 8 ? 6 : 7)
       }
       const int nsamp = __any_sync(0xffffffffu, ray.hit) ? P.n_samples : 0;
       for (int kb = 0; kb < nsamp; kb += LPR) {
-        const float4 mine = sample_physics(P, s_tab, ray, kb + q);
+        const float4 mine = sample_physics<ROT>(P, s_tab, ray, kb + q);
         // channel window of this sample (empty without gas): fractional channel indices
         // where kd 2^{-d^2} >= 2^-40
         float clo = 1.0f, chi = -1.0f;
@@ -209,7 +209,7 @@ int resident_blocks(const void *kernel, int threads) {
 
 template <int LPR, int CPL>
 static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
-  auto kern = march_fwd_kernel<LPR, CPL>;
+  auto kern = P.vphi ? march_fwd_kernel<LPR, CPL, true> : march_fwd_kernel<LPR, CPL, false>;
   long long npix = (long long)P.nx * P.ny;
   long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
   long long need = (units + kWarps - 1) / kWarps;
@@ -240,11 +240,12 @@ __global__ void pack_cells_kernel(const float *__restrict__ T, const float *__re
        i += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(i / (nr - 1)), r = (int)(i - (long long)j * (nr - 1));
     const long long b = (long long)j * nr + r;  // node (r, j); the cell's nodes end at b+nr+1
-    cell[4 * i] = make_float4(T[b], T[b + 1], T[b + nr], T[b + nr + 1]);
-    cell[4 * i + 1] = make_float4(n[b], n[b + 1], n[b + nr], n[b + nr + 1]);
-    cell[4 * i + 2] = make_float4(vt[b], vt[b + 1], vt[b + nr], vt[b + nr + 1]);
-    cell[4 * i + 3] = vphi ? make_float4(vphi[b], vphi[b + 1], vphi[b + nr], vphi[b + nr + 1])
-                           : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const int nq = vphi ? 4 : 3;
+    float4 *cq = cell + nq * i;
+    cq[0] = make_float4(T[b], T[b + 1], T[b + nr], T[b + nr + 1]);
+    cq[1] = make_float4(n[b], n[b + 1], n[b + nr], n[b + nr + 1]);
+    cq[2] = make_float4(vt[b], vt[b + 1], vt[b + nr], vt[b + nr + 1]);
+    if (vphi) cq[3] = make_float4(vphi[b], vphi[b + 1], vphi[b + nr], vphi[b + nr + 1]);
     if (j == 0) hcell[r] = make_float4(hlo[r], hlo[r + 1], hhi[r], hhi[r + 1]);
   }
 }
@@ -260,7 +261,7 @@ size_t cell_bytes(const MarchParams &P) {
   const long long samples = (long long)P.nx * P.ny * P.n_samples;
   const long long cells = (long long)(P.nr - 1) * (P.nz - 1);
   if (samples < kCellMinSamples || samples < 8 * cells) return 0;
-  return (size_t)(4 * cells + (P.nr - 1)) * sizeof(float4);
+  return (size_t)((P.vphi ? 4 : 3) * cells + (P.nr - 1)) * sizeof(float4);
 }
 
 // Packs the corner quads into buf (cell_bytes(P) bytes, 16-byte aligned) on `stream` and
@@ -268,7 +269,7 @@ size_t cell_bytes(const MarchParams &P) {
 int pack_cells(MarchParams &P, void *buf, cudaStream_t stream) {
   const long long cells = (long long)(P.nr - 1) * (P.nz - 1);
   float4 *cell = reinterpret_cast<float4 *>(buf);
-  float4 *hcell = cell + 4 * cells;
+  float4 *hcell = cell + (P.vphi ? 4 : 3) * cells;
   const long long nb = (cells + 255) / 256;
   pack_cells_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, stream>>>(
       P.T, P.n, P.vt, P.hlo, P.hhi, P.vphi, P.nr, P.nz, cell, hcell);

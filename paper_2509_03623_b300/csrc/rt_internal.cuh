@@ -52,7 +52,7 @@ struct MarchParams {
   unsigned long long *work;
   // optional corner quads (pack_cells): per grid cell (i, j) the four nodes its bilinear
   // interpolation reads, {f(i,j), f(i+1,j), f(i,j+1), f(i+1,j+1)}, for T, n_H2, v_turb and
-  // the rotation field when there is one (four float4, 64 B per cell, cells in [j][i]
+  // the rotation field when there is one (three or four float4 per cell, cells in [j][i]
   // order), and per radial interval i
   // {h_lo(i), h_lo(i+1), h_hi(i), h_hi(i+1)}: four 16-byte loads per sample instead of 16
   // scalar ones. nullptr: the kernels read the node arrays (same values, same rounding).
@@ -215,12 +215,15 @@ struct NodeVals {
   float vphi;  // rotation field (only with P.vphi)
 };
 
+// ROT: the problem has a rotation field (then the corner quads hold four fields per cell,
+// otherwise three).
+template <bool ROT>
 __device__ __forceinline__ NodeVals fields_at(const MarchParams &P, const Cell &c) {
   NodeVals v;
   if (P.cell) {
-    const float4 *q = P.cell + 4 * ((long long)c.j0 * (P.nr - 1) + c.i0);
+    const float4 *q = P.cell + (ROT ? 4 : 3) * ((long long)c.j0 * (P.nr - 1) + c.i0);
     const float4 qT = __ldg(q), qn = __ldg(q + 1), qv = __ldg(q + 2);
-    v.vphi = P.vphi ? quad_lerp(__ldg(q + 3), c) : 0.0f;
+    v.vphi = ROT ? quad_lerp(__ldg(q + 3), c) : 0.0f;
     const float4 qh = __ldg(P.hcell + c.i0);
     v.T = quad_lerp(qT, c);
     v.n = quad_lerp(qn, c);
@@ -231,7 +234,7 @@ __device__ __forceinline__ NodeVals fields_at(const MarchParams &P, const Cell &
     v.T = bilerp(P.T, P.nr, c);
     v.n = bilerp(P.n, P.nr, c);
     v.vt = bilerp(P.vt, P.nr, c);
-    v.vphi = P.vphi ? bilerp(P.vphi, P.nr, c) : 0.0f;
+    v.vphi = ROT ? bilerp(P.vphi, P.nr, c) : 0.0f;
     const float *hl = P.hlo + c.i0;
     const float *hh = P.hhi + c.i0;
     v.hlo = lerpf(__ldg(hl), __ldg(hl + 1), c.fr);
@@ -263,6 +266,7 @@ __device__ __forceinline__ float lte_phi(const float *__restrict__ tab, float t,
 //   kd  optical depth per unit profile (log2 units): dtau_c = kd 2^{-d_c^2}, 0 without gas
 //   a,b profile argument d_c = v_c b - a (b = sqrt(log2 e)/alpha, a = v_los b)
 //   S   LTE source function in units of 2 h nu0^3 / c^2
+template <bool ROT = false>
 __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const float *tab,
                                                  const Ray &R, int k) {
   float kf = (float)k;
@@ -272,7 +276,7 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
   Cell c = locate(P, z, r2);
   float4 out = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
   if (!(c.gas && R.hit && k < P.n_samples)) return out;
-  const NodeVals f = fields_at(P, c);
+  const NodeVals f = fields_at<ROT>(P, c);
   float T = f.T, n = f.n, vt = f.vt, hlo = f.hlo, hhi = f.hhi;
   if (P.mod) {
     const float4 o = __ldg(P.mod + (long long)R.pix * P.n_samples + k);
@@ -290,8 +294,8 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
     X = P.x_co * rcp((1.0f + ea) * (1.0f + eb));
   }
   // Keplerian rotation: v_los = sqrt(GM) sin i x (r^2 + z^2)^{-3/4} + v_sys
-  float vlos = P.vphi ? fmaf(f.vphi * (P.sin_if * R.x), c.ir, P.vsys)
-                     : fmaf(R.vfac, kepler_q(fmaf(z, z, r2)), P.vsys);
+  float vlos = ROT ? fmaf(f.vphi * (P.sin_if * R.x), c.ir, P.vsys)
+                  : fmaf(R.vfac, kepler_q(fmaf(z, z, r2)), P.vsys);
   // line width
   float Tg = fmaxf(T, 1e-3f);
   float a2 = P.vturb_mach ? Tg * fmaf(P.c_mach, vt * vt, P.c_th) : fmaf(P.c_th, Tg, vt * vt);
