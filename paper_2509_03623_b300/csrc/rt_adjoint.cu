@@ -293,7 +293,7 @@ __device__ __forceinline__ unsigned adj_window(const MarchParams &P, const float
     const float w2 = 40.0f + lg2(mine.x);
     if (w2 > 0.0f) {
       const float ib = rcp(mine.z);
-      const float hw = sqrtf(w2) * ib;
+      const float hw = sqa(w2) * ib;
       const float vl = mine.y * ib;  // v_los = a / b
       const float e0 = (vl - hw - P.v0) * idv, e1 = (vl + hw - P.v0) * idv;
       clo = fminf(e0, e1) - 0.01f;

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kWarps * 32, CPL == 8 ? 6 : 7)
           const float w2 = kWinLog2 + lg2(mine.x);
           if (w2 > 0.0f) {
             const float ib = rcp(mine.z);
-            const float hw = sqrtf(w2) * ib;
+            const float hw = sqa(w2) * ib;
             const float vl = mine.y * ib;  // v_los = a / b
             const float e0 = (vl - hw - P.v0) * idv, e1 = (vl + hw - P.v0) * idv;
             clo = fminf(e0, e1) - 0.01f;  // slack for the rounding of the edges
