@@ -6,10 +6,11 @@
 // contiguous channel block [2m LPR, (2m+2) LPR). The grid is persistent (one wave) and work
 // units are interleaved over its warps; the double-precision ray setups (chord through the
 // bounding cylinder) of 32 rays are computed at once, one per lane, and kept in shared memory.
-// Samples advance in batches of LPR: in the physics phase lane q evaluates the channel-
-// independent physics of sample kb+q of its ray (fields, CO layer, Keplerian velocity, line
-// width, LTE source and opacity) once and publishes it in shared memory; in the channel phase
-// every lane walks the batch's samples in order, evaluating the Doppler-shifted Gaussian
+// Samples advance in batches of 2 LPR: in the physics phase lane q evaluates the channel-
+// independent physics of samples kb+q and kb+LPR+q of its ray (fields, CO layer, Keplerian
+// velocity, line width, LTE source and opacity; two independent evaluations per lane for
+// instruction-level parallelism) once and publishes them in shared memory; in the channel
+// phase every lane walks the batch's samples in order, evaluating the Doppler-shifted Gaussian
 // profile and advancing optical depth, transmittance and intensity front to back (Eq. rt-int
 // with Eq. optical_depth; the source is constant over each segment).
 //
@@ -36,17 +37,17 @@ namespace rtb {
 constexpr int kWarps = 4;        // warps per block
 constexpr float kWinLog2 = 40.0f;  // skipped optical depths are below 2^-40 per sample
 
-// Blocks per SM the register budget is sized for: 6 (at most 85 registers) with 8 channels
-// per lane, 7 with 4.
+// Blocks per SM the register budget is sized for: 5 (at most 102 registers) with 8 channels
+// per lane, 6 with 4.
 template <int LPR, int CPL, bool ROT>
-__global__ void __launch_bounds__(kWarps * 32, CPL == 8 ? 6 : 7)
+__global__ void __launch_bounds__(kWarps * 32, CPL == 8 ? 5 : 6)
     march_fwd_kernel(const __grid_constant__ MarchParams P, float *__restrict__ cube) {
   constexpr int R = 32 / LPR;  // rays marched together by one warp (one work unit)
   constexpr int G = 32 / R;    // work units whose ray setups are computed together
   constexpr int H = CPL / 2;   // channel pairs per lane = channel blocks
   __shared__ __align__(16) float s_tab[kTabSeg * 4];
   // per sample: {-kd, -kd, S, S} and {b, b, -a, -a} (pairs ready for the packed arithmetic)
-  __shared__ float4 s_ph[kWarps][2][32];
+  __shared__ float4 s_ph[kWarps][2][64];
   __shared__ Ray s_ray[kWarps][32];
   for (int i = threadIdx.x; i < kTabSeg * 4; i += blockDim.x) s_tab[i] = P.tab[i];
   __syncthreads();
@@ -102,22 +103,31 @@ __global__ void __launch_bounds__(kWarps * 32, CPL == 8 ? 6 : 7)
         I[m] = make_float2(0.0f, 0.0f);
       }
       const int nsamp = __any_sync(0xffffffffu, ray.hit) ? P.n_samples : 0;
-      for (int kb = 0; kb < nsamp; kb += LPR) {
+      for (int kb = 0; kb < nsamp; kb += 2 * LPR) {
         const float4 mine = sample_physics<ROT>(P, s_tab, ray, kb + q);
-        // channel window of this sample (empty without gas): fractional channel indices
-        // where kd 2^{-d^2} >= 2^-40
-        float clo = 1.0f, chi = -1.0f;
-        if (mine.x > 0.0f) {
-          const float w2 = kWinLog2 + lg2(mine.x);
-          if (w2 > 0.0f) {
-            const float ib = rcp(mine.z);
-            const float hw = sqa(w2) * ib;
-            const float vl = mine.y * ib;  // v_los = a / b
-            const float e0 = (vl - hw - P.v0) * idv, e1 = (vl + hw - P.v0) * idv;
-            clo = fminf(e0, e1) - 0.01f;  // slack for the rounding of the edges
-            chi = fmaxf(e0, e1) + 0.01f;
+        const float4 mine2 = sample_physics<ROT>(P, s_tab, ray, kb + LPR + q);
+        // channel window of a sample (empty without gas): fractional channel indices where
+        // kd 2^{-d^2} >= 2^-40; the lane votes with the union of its two samples' windows
+        auto window = [&](const float4 &m4, float &lo, float &hi) {
+          lo = 1e30f;
+          hi = -1e30f;
+          if (m4.x > 0.0f) {
+            const float w2 = kWinLog2 + lg2(m4.x);
+            if (w2 > 0.0f) {
+              const float ib = rcp(m4.z);
+              const float hw = sqa(w2) * ib;
+              const float vl = m4.y * ib;
+              const float e0 = (vl - hw - P.v0) * idv, e1 = (vl + hw - P.v0) * idv;
+              lo = fminf(e0, e1) - 0.01f;
+              hi = fmaxf(e0, e1) + 0.01f;
+            }
           }
-        }
+        };
+        float clo, chi, clo2, chi2;
+        window(mine, clo, chi);
+        window(mine2, clo2, chi2);
+        clo = fminf(clo, clo2);
+        chi = fmaxf(chi, chi2);
         unsigned act = 0;
         if (windowed) {
 #pragma unroll
@@ -125,26 +135,29 @@ __global__ void __launch_bounds__(kWarps * 32, CPL == 8 ? 6 : 7)
             if (__any_sync(0xffffffffu, chi >= (float)(2 * m * LPR) &&
                                             clo <= (float)((2 * m + 2) * LPR - 1)))
               act |= 1u << m;
-        } else if (__any_sync(0xffffffffu, mine.x > 0.0f)) {
+        } else if (__any_sync(0xffffffffu, mine.x > 0.0f || mine2.x > 0.0f)) {
           act = (1u << H) - 1;
         }
         if (P.work) {
           const unsigned gl = __ballot_sync(0xffffffffu, mine.x > 0.0f);
-          wc_phys += __popc(gl);
-          wc_eval += (unsigned long long)__popc(act) * 64 * LPR;
+          const unsigned gl2 = __ballot_sync(0xffffffffu, mine2.x > 0.0f);
+          wc_phys += __popc(gl) + __popc(gl2);
+          wc_eval += (unsigned long long)__popc(act) * 128 * LPR;
         }
         if (!act) continue;  // no channel of any ray reached in this batch
-        ph0[lane] = make_float4(-mine.x, -mine.x, mine.w, mine.w);
-        ph1[lane] = make_float4(mine.z, mine.z, -mine.y, -mine.y);
+        ph0[rr * 2 * LPR + q] = make_float4(-mine.x, -mine.x, mine.w, mine.w);
+        ph1[rr * 2 * LPR + q] = make_float4(mine.z, mine.z, -mine.y, -mine.y);
+        ph0[rr * 2 * LPR + LPR + q] = make_float4(-mine2.x, -mine2.x, mine2.w, mine2.w);
+        ph1[rr * 2 * LPR + LPR + q] = make_float4(mine2.z, mine2.z, -mine2.y, -mine2.y);
         __syncwarp();
 #pragma unroll
         for (int m = 0; m < H; m++) {
           if (!(act & (1u << m))) continue;  // warp-uniform: block m outside every window
           // every sample of the batch in order; samples without gas are exact no-ops
 #pragma unroll
-          for (int t = 0; t < LPR; t++) {
-            const float4 p0 = ph0[rr * LPR + t];  // -kd, -kd, S, S of sample kb+t of this ray
-            const float4 p1 = ph1[rr * LPR + t];  // b, b, -a, -a
+          for (int t = 0; t < 2 * LPR; t++) {
+            const float4 p0 = ph0[rr * 2 * LPR + t];
+            const float4 p1 = ph1[rr * 2 * LPR + t];
             const float2 nkd = make_float2(p0.x, p0.y), S = make_float2(p0.z, p0.w);
             const float2 b = make_float2(p1.x, p1.y), na = make_float2(p1.z, p1.w);
             const float2 d = __ffma2_rn(vp[m], b, na);  // (v_c - v_los) / alpha (scaled)
