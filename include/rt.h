@@ -239,7 +239,7 @@ int rt_render_adjoint_noalloc(const rt_grid *grid, const rt_fields *fields, cons
  * T: DEVICE [nz][nr] float32, > 0. Outputs (DEVICE, caller-allocated, overwritten):
  *   n_h2 [nz][nr] float32 [cm^-3], N_h2 [nz][nr] float32 [cm^-2] (may be NULL),
  *   h_lo, h_hi [nr] float32 (z/r; usable as rt_fields surfaces).
- * FP32 arithmetic (the per-column r and Sigma in FP64); one warp per radius column.
+ * FP32 arithmetic; one warp per radius column.
  * Returns RT_OK, RT_EINVAL (null pointer, grid with fewer than 2 nodes per axis, non-finite
  * or out-of-range parameter) or RT_ECUDA.
  */

@@ -321,10 +321,11 @@ def rt_surface_powerlaw_grad(problem, dh, h, c, stream=None):
     return out
 
 
-def rt_field_chain(problem, T, chain, column=True, stream=None):
+def rt_field_chain(problem, T, chain, column=True, stream=None, out=None):
     """Physics-constrained field chain on the grid of `problem` from the temperature grid T
-    (CUDA float32 [nz][nr]): dict(n_h2, N_h2 (None unless column), h_lo, h_hi). `chain` has
-    the attributes sigma0_gcm2, r_c_au, gamma, T_freeze, N_dissoc_cm2."""
+    (CUDA float32 [nz][nr]): dict(n_h2, N_h2 (None unless column), h_lo, h_hi), written into
+    `out` (a dict of that form) when given. `chain` has the attributes sigma0_gcm2, r_c_au,
+    gamma, T_freeze, N_dissoc_cm2."""
     import torch
     shp = (int(problem.nz), int(problem.nr))
     if not T.is_cuda or T.dtype != torch.float32 or not T.is_contiguous() or tuple(T.shape) != shp:
@@ -337,10 +338,13 @@ def rt_field_chain(problem, T, chain, column=True, stream=None):
                  float(problem.m_co_amu), float(problem.m_mol_amu), int(problem.J_u))
     c = rt_chain(float(chain.sigma0_gcm2), float(chain.r_c_au), float(chain.gamma),
                  float(chain.T_freeze), float(chain.N_dissoc_cm2))
-    n = torch.empty(shp, dtype=torch.float32, device=T.device)
-    N = torch.empty(shp, dtype=torch.float32, device=T.device) if column else None
-    lo = torch.empty(shp[1], dtype=torch.float32, device=T.device)
-    hi = torch.empty(shp[1], dtype=torch.float32, device=T.device)
+    if out is not None:
+        n, N, lo, hi = out["n_h2"], out["N_h2"], out["h_lo"], out["h_hi"]
+    else:
+        n = torch.empty(shp, dtype=torch.float32, device=T.device)
+        N = torch.empty(shp, dtype=torch.float32, device=T.device) if column else None
+        lo = torch.empty(shp[1], dtype=torch.float32, device=T.device)
+        hi = torch.empty(shp[1], dtype=torch.float32, device=T.device)
     check(lib().rt_field_chain(C.byref(g), C.byref(o), C.byref(ln), C.byref(c), _ptr(T),
                                _ptr(n), _ptr(N) if N is not None else None, _ptr(lo), _ptr(hi),
                                stream_handle(stream)))

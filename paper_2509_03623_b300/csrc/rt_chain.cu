@@ -16,8 +16,7 @@
 //
 // One warp per radius column: lanes take 32 consecutive nodes at a time, the two running
 // integrals are warp scans (upward for I, downward for N) with a carry between chunks, and
-// the surfaces come from warp ballots. FP32 throughout except the per-column constants
-// (r_i, Sigma(r_i)), which lane 0 forms in double precision. Pass 1 leaves the unnormalised
+// the surfaces come from warp ballots. FP32 throughout. Pass 1 leaves the unnormalised
 // density in n_h2; pass 2 scales it and integrates the column from the top.
 #include "rt_internal.cuh"
 
@@ -25,8 +24,9 @@ namespace rtb {
 
 struct ChainDev {
   int nr, nz, r_log;
-  double r_in, r_out, zr_max;
-  double sigma0, r_c, gamma;
+  float r_in, r_out;
+  double zr_max;
+  float sigma0, r_c, gamma;
   float A;         // G M m_mol / (k au) [K au]: gravity term per au of height, times 1/T
   float m_mol_g;   // mean molecular mass [g]
   float T_freeze, N_dissoc;
@@ -47,17 +47,11 @@ __global__ void field_chain_kernel(const ChainDev C, const float *__restrict__ T
   const int nr = C.nr, nz = C.nz;
   const int nchunk = (nz + 31) / 32;
 
-  // per-column constants in double precision (one lane), broadcast
-  float r = 0.0f, sig = 0.0f;
-  if (lane == 0) {
-    const double t = (double)i / (nr - 1);
-    const double rd = C.r_log ? C.r_in * pow(C.r_out / C.r_in, t) : C.r_in + (C.r_out - C.r_in) * t;
-    const double x = rd / C.r_c;
-    r = (float)rd;
-    sig = (float)(C.sigma0 * pow(x, -C.gamma) * exp(-pow(x, 2.0 - C.gamma)));
-  }
-  r = __shfl_sync(full, r, 0);
-  sig = __shfl_sync(full, sig, 0);
+  // per-column constants (FP32 library functions, a few ulp: far inside the tolerance)
+  const float t = (float)i / (float)(nr - 1);
+  const float r = C.r_log ? C.r_in * powf(C.r_out / C.r_in, t) : fmaf(C.r_out - C.r_in, t, C.r_in);
+  const float x = r / C.r_c;
+  const float sig = C.sigma0 * powf(x, -C.gamma) * expf(-powf(x, 2.0f - C.gamma));
   const float dw = (float)(C.zr_max / (nz - 1));
   const float dz = dw * r;  // au
   const float r2 = r * r;
@@ -246,12 +240,12 @@ int launch_field_chain(const rt_grid &g, const rt_geom &geo, const rt_line &line
   C.nr = g.nr;
   C.nz = g.nz;
   C.r_log = g.r_log;
-  C.r_in = g.r_in_au;
-  C.r_out = g.r_out_au;
+  C.r_in = (float)g.r_in_au;
+  C.r_out = (float)g.r_out_au;
   C.zr_max = g.zr_max;
-  C.sigma0 = c.sigma0_gcm2;
-  C.r_c = c.r_c_au;
-  C.gamma = c.gamma;
+  C.sigma0 = (float)c.sigma0_gcm2;
+  C.r_c = (float)c.r_c_au;
+  C.gamma = (float)c.gamma;
   const double m = line.m_mol_amu * kChainAmu;
   C.A = (float)(kChainGMsun * geo.mstar_msun * m / (kChainK * kChainAu));
   C.m_mol_g = (float)m;

@@ -950,6 +950,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
     tc_fence_before();
     __syncthreads();
 
+    uint4 zn[4];  // this thread's pre-activations of the next backward layer (2 chunks x 2)
     // ---------------- forward: a1..a4 (P, Q, P, Q), pre-activations to the scratch ----------------
     for (int l = 0; l < 4; l++) {
       const int K = l == 0 ? kMlpF : kMlpW;
@@ -1029,6 +1030,13 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
         }
         store16(S.Q, t, f0, dp);
       }
+      // pre-activations z_2 for layer 4's delta epilogue, loaded ahead of the barrier
+#pragma unroll
+      for (int c = 0; c < 2; c++) {
+        const uint4 *zr = zrow(2, c);
+        zn[2 * c] = zr[0];
+        zn[2 * c + 1] = zr[1];
+      }
       proxy_fence();
       tc_fence_before();
       __syncthreads();
@@ -1040,13 +1048,13 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       h16 *X = (l & 1) ? S.Q : S.P;                                     // a_{l-1} (l >= 2)
       const unsigned ax = l == 1 ? aF : smem_u32(X);
       const int Kin = l == 1 ? kMlpF : kMlpW;
-      if (l == 3 || l == 2) {  // a_{l-1} was overwritten: recompute it from z_{l-1}
+      if (l == 3 || l == 2) {  // a_{l-1} was overwritten: recompute it from z_{l-1} (in zn)
+#pragma unroll
         for (int c = 0; c < 2; c++) {
-          const uint4 *zr = zrow(l - 2, c);
           unsigned ap[8];
 #pragma unroll
           for (int k = 0; k < 2; k++) {
-            const uint4 z = zr[k];
+            const uint4 z = zn[2 * c + k];
             ap[4 * k] = silu2p<F16>(z.x);
             ap[4 * k + 1] = silu2p<F16>(z.y);
             ap[4 * k + 2] = silu2p<F16>(z.z);
@@ -1106,11 +1114,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
         if (S.abort) goto done;
         break;
       }
-      for (int c = 0; c < 2; c++) {
-        const uint4 *zr = zrow(l - 2, c);
-        uint4 zq[2];
 #pragma unroll
-        for (int k = 0; k < 2; k++) zq[k] = zr[k];
+      for (int c = 0; c < 2; c++) {
+        const uint4 zq[2] = {zn[2 * c], zn[2 * c + 1]};  // z_{l-1}, loaded a layer ahead
         wait_mma();
         if (c == 0 && qt == 0) {
           float v[16];
@@ -1136,6 +1142,14 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
           dp[j] = pack16<F16>(v[2 * j] * dsilu(z.x), v[2 * j + 1] * dsilu(z.y));
         }
         store16(X, t, f0, dp);
+      }
+      if (l >= 3) {  // z_{l-2} for the next layer, loaded ahead of the barrier
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+          const uint4 *zr = zrow(l - 3, c);
+          zn[2 * c] = zr[0];
+          zn[2 * c + 1] = zr[1];
+        }
       }
       proxy_fence();
       tc_fence_before();
