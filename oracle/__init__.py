@@ -52,6 +52,19 @@ class _Problem(C.Structure):
         ("nu0_hz", C.c_double), ("A_ul", C.c_double), ("B_rot_hz", C.c_double),
         ("m_co_amu", C.c_double), ("m_mol_amu", C.c_double), ("J_u", C.c_int),
         ("vphi", C.POINTER(C.c_double)),
+        ("g3", C.c_void_p),
+    ]
+
+
+class _Grid3(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+        ("z0", C.c_double), ("z1", C.c_double),
+        ("T", C.POINTER(C.c_double)), ("n_h2", C.POINTER(C.c_double)),
+        ("vturb", C.POINTER(C.c_double)), ("x_co", C.POINTER(C.c_double)),
+        ("vx", C.POINTER(C.c_double)), ("vy", C.POINTER(C.c_double)),
+        ("vz", C.POINTER(C.c_double)),
     ]
 
 
@@ -127,6 +140,17 @@ class _Packed:
         s.m_co_amu, s.m_mol_amu, s.J_u = float(p.m_co_amu), float(p.m_mol_amu), int(p.J_u)
         vphi = getattr(p, "vphi", None)
         s.vphi = arr(vphi) if vphi is not None else C.POINTER(C.c_double)()
+        g3 = getattr(p, "g3", None)
+        if g3 is not None:
+            g = _Grid3()
+            g.nx, g.ny, g.nz = int(g3.nx), int(g3.ny), int(g3.nz)
+            g.x0, g.x1, g.y0, g.y1, g.z0, g.z1 = (float(v) for v in g3.extent)
+            g.T, g.n_h2, g.vturb, g.x_co = arr(g3.T), arr(g3.n_h2), arr(g3.vturb), arr(g3.x_co)
+            g.vx, g.vy, g.vz = arr(g3.vx), arr(g3.vy), arr(g3.vz)
+            self.keep.append(g)
+            s.g3 = C.cast(C.pointer(g), C.c_void_p)
+        else:
+            s.g3 = None
         self.s = s
         self.nch = s.nch
 

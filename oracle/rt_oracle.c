@@ -79,8 +79,14 @@ static double mean_energy(double T, double B) {
 /* Geometry                                                                                */
 /* ---------------------------------------------------------------------------------------- */
 
+static double box_reach(const orc_grid3 *g) {
+  double m = fmax(fmax(fabs(g->x0), fabs(g->x1)), fmax(fabs(g->y0), fabs(g->y1)));
+  return fmax(m, fmax(fabs(g->z0), fabs(g->z1)));
+}
+
 static double half_fov(const orc_problem *p) {
-  return p->half_fov_au > 0 ? p->half_fov_au : 1.1 * p->r_out_au;
+  if (p->half_fov_au > 0) return p->half_fov_au;
+  return 1.1 * (p->g3 ? box_reach(p->g3) : p->r_out_au);
 }
 
 /* Ray through pixel (ix, iy). Disk frame: +z along the disk angular momentum. Observer
@@ -108,6 +114,25 @@ static void ray_setup(const orc_problem *p, int ix, int iy, double P0[3], double
    (sampling rule: the paper does not state one). */
 static int chord(const orc_problem *p, const double P0[3], const double om[3], double *s0,
                  double *s1) {
+  if (p->g3) {
+    /* 3-D grid: the chord through the box, slab by slab */
+    const double lo3[3] = {p->g3->x0, p->g3->y0, p->g3->z0};
+    const double hi3[3] = {p->g3->x1, p->g3->y1, p->g3->z1};
+    double lo = -INFINITY, hi = INFINITY;
+    for (int a = 0; a < 3; a++) {
+      if (om[a] != 0.0) {
+        double t1 = (lo3[a] - P0[a]) / om[a], t2 = (hi3[a] - P0[a]) / om[a];
+        lo = fmax(lo, fmin(t1, t2));
+        hi = fmin(hi, fmax(t1, t2));
+      } else if (P0[a] < lo3[a] || P0[a] > hi3[a]) {
+        return 0;
+      }
+    }
+    if (!(hi > lo)) return 0;
+    *s0 = lo;
+    *s1 = hi;
+    return 1;
+  }
   double R = p->r_out_au, H = p->zr_max * p->r_out_au;
   double lo = -INFINITY, hi = INFINITY;
   if (om[2] != 0.0) {
@@ -185,6 +210,41 @@ static void eval_point(const orc_problem *p, const orc_mlp *m, const double P[3]
                        const double om[3], pt *st) {
   memset(st, 0, sizeof(*st));
   double x = P[0], y = P[1], z = P[2];
+  if (p->g3) {
+    /* 3-D grid: trilinear interpolation of every field, the abundance from its own field and
+       the line-of-sight velocity from the gas velocity field */
+    const orc_grid3 *g = p->g3;
+    if (x < g->x0 || x > g->x1 || y < g->y0 || y > g->y1 || z < g->z0 || z > g->z1) return;
+    double f[3] = {(x - g->x0) / (g->x1 - g->x0) * (g->nx - 1),
+                   (y - g->y0) / (g->y1 - g->y0) * (g->ny - 1),
+                   (z - g->z0) / (g->z1 - g->z0) * (g->nz - 1)};
+    const int nn[3] = {g->nx, g->ny, g->nz};
+    int i3[3];
+    for (int a = 0; a < 3; a++) {
+      i3[a] = (int)floor(f[a]);
+      if (i3[a] > nn[a] - 2) i3[a] = nn[a] - 2;
+      if (i3[a] < 0) i3[a] = 0;
+      f[a] -= i3[a];
+    }
+    const double *F[7] = {g->T, g->n_h2, g->vturb, g->x_co, g->vx, g->vy, g->vz};
+    double val[7];
+    for (int q = 0; q < 7; q++) {
+      double acc = 0.0;
+      for (int c = 0; c < 8; c++) {
+        int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+        double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+        acc += w * F[q][((long long)(i3[2] + dz) * g->ny + (i3[1] + dy)) * g->nx + (i3[0] + dx)];
+      }
+      val[q] = acc;
+    }
+    st->T = val[0];
+    st->n = val[1];
+    st->vt = val[2];
+    st->X = val[3];
+    st->vlos = 1e5 * (om[0] * val[4] + om[1] * val[5] + om[2] * val[6]) + p->vsys_kms * 1e5;
+    goto line_physics;
+  }
+  {
   double r = sqrt(x * x + y * y);
   double zr = r > 0 ? fabs(z) / r : INFINITY;
   st->zr = zr;
@@ -252,6 +312,8 @@ static void eval_point(const orc_problem *p, const orc_mlp *m, const double P[3]
                         : sqrt(GM_SUN * p->mstar_msun * rc * rc / pow(rc * rc + zc * zc, 1.5));
   double v[3] = {-vphi * y / r, vphi * x / r, 0.0};
   st->vlos = om[0] * v[0] + om[1] * v[1] + om[2] * v[2] + p->vsys_kms * 1e5;
+  }
+line_physics:;
   /* Line width: thermal + turbulent. Absolute mode (v_turb in km/s) or the paper's Mach
      form with c_s^2 = 2kT/m_mol as printed. */
   double mco = p->m_co_amu * AMU_G, mmol = p->m_mol_amu * AMU_G;
@@ -370,6 +432,17 @@ static void march_pixel(const orc_problem *p, const orc_mlp *m, int ix, int iy, 
 }
 
 static int check(const orc_problem *p) {
+  if (p && p->g3) {
+    const orc_grid3 *g = p->g3;
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || !(g->x1 > g->x0) || !(g->y1 > g->y0) ||
+        !(g->z1 > g->z0) || !g->T || !g->n_h2 || !g->vturb || !g->x_co || !g->vx || !g->vy ||
+        !g->vz)
+      return -1;
+    if (p->nx < 1 || p->ny < 1 || p->nch < 0 || p->n_samples < 1 || (p->nch > 0 && !p->v_kms))
+      return -1;
+    if (p->J_u < 1 || !(p->nu0_hz > 0) || !(p->dist_pc > 0)) return -1;
+    return 0;
+  }
   if (!p || p->nr < 2 || p->nz < 2 || p->nx < 1 || p->ny < 1 || p->nch < 0 ||
       p->n_samples < 1)
     return -1;

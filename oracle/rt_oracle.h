@@ -24,6 +24,16 @@
 extern "C" {
 #endif
 
+/* General 3-D Cartesian node grid in the disk frame (the RadJAX setting beyond the
+   axisymmetric disk): nodes uniformly spaced over [x0, x1] x [y0, y1] x [z0, z1] au, fields
+   [nz][ny][nx] (x fastest): T [K], n_H2 [cm^-3], v_turb [km/s or Mach], X_CO (abundance),
+   gas velocity (vx, vy, vz) [km/s]; trilinear interpolation, nothing outside the box. */
+typedef struct {
+  int nx, ny, nz;
+  double x0, x1, y0, y1, z0, z1;
+  const double *T, *n_h2, *vturb, *x_co, *vx, *vy, *vz;
+} orc_grid3;
+
 typedef struct {
   /* (r, z/r) node grid: r log-spaced (r_log=1) or linear (r_log=0) in [r_in, r_out] au,
      z/r linear in [0, zr_max]. */
@@ -51,6 +61,9 @@ typedef struct {
      term, e.g. from orc_pressure_vphi), interpolated like the other node fields; NULL: the
      Keplerian term alone, evaluated exactly at each point */
   const double *vphi;
+  /* optional 3-D grid: when set, the node grid, fields, surfaces, rotation and stellar mass
+     above are not used; rays are clipped to the box (rt_render3d's sampling rule) */
+  const orc_grid3 *g3;
 } orc_problem;
 
 /* Full cube [nch][ny][nx]. Returns 0, or -1 on invalid arguments. */

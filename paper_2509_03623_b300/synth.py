@@ -97,6 +97,8 @@ class Problem:
     J_u: int = 2
     # optional rotation field [nz][nr] km/s (pressure-corrected); None: Keplerian
     vphi: Optional[np.ndarray] = None
+    # optional 3-D Cartesian grid (rt_render3d); when set the fields above are unused
+    g3: Optional["Grid3"] = None
     # provenance
     name: str = ""
     seed: int = 0
@@ -236,6 +238,96 @@ def disk(seed: int = 0, *, nr: int = 64, nz: int = 32, r_in: float = 10.0,
                    incl_deg=incl, pa_deg=pa, dist_pc=dist, mstar_msun=mstar_j,
                    nx=nx, ny=ny, v_kms=np.linspace(-vmax, vmax, nch), n_samples=n_samples,
                    name=name, seed=seed, surf=(c_lo, 0.25, c_hi, 0.25), ring_mod=ring_mod)
+
+
+@dataclasses.dataclass
+class Grid3:
+    """3-D Cartesian node grid in the disk frame: nodes uniformly spaced over
+    extent = (x0, x1, y0, y1, z0, z1) au; fields [nz][ny][nx] float64: T [K], n_h2 [cm^-3],
+    vturb [km/s], x_co (CO abundance), vx, vy, vz [km/s]."""
+    nx: int
+    ny: int
+    nz: int
+    extent: tuple
+    T: np.ndarray
+    n_h2: np.ndarray
+    vturb: np.ndarray
+    x_co: np.ndarray
+    vx: np.ndarray
+    vy: np.ndarray
+    vz: np.ndarray
+
+    def nodes(self):
+        x0, x1, y0, y1, z0, z1 = self.extent
+        return (np.linspace(x0, x1, self.nx), np.linspace(y0, y1, self.ny),
+                np.linspace(z0, z1, self.nz))
+
+
+def box3d(seed: int = 0, *, n3=(64, 64, 32), half_xy: float = 600.0, half_z: float = 150.0,
+          nx: int = 64, ny: int = 64, nch: int = 32, vmax: float = 6.0, n_samples: int = 256,
+          incl: float = 45.0, pa: float = 0.0, mstar: float = 2.0, turb: float = 0.2,
+          r_in: float = 10.0, name: str = "") -> Problem:
+    """A 3-D box [-half_xy, half_xy]^2 x [-half_z, half_z] au standing in for a hydrodynamic
+    simulation: the parametric disk's temperature and density (same family as `disk`, no
+    axisymmetry imposed on the perturbations) evaluated at the nodes and multiplied by
+    exp(turb f(x)) with f a seeded sum of 6 Fourier modes (wavelengths 100-400 au), a CO
+    abundance layer 1e-4 exp(-((|z|/r - 0.2)/0.08)^2 / 2), Keplerian rotation
+    sqrt(G M r^2 / (r^2+z^2)^{3/2}) (-y/r, x/r, 0) plus seeded velocity modes of 0.1 km/s
+    amplitude in all three components, and v_turb = 0.05 km/s. No gas inside r_in."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gx, gy, gz = n3
+    xs = np.linspace(-half_xy, half_xy, gx)
+    ys = np.linspace(-half_xy, half_xy, gy)
+    zs = np.linspace(-half_z, half_z, gz)
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")  # [nz][ny][nx]
+    R = np.sqrt(X * X + Y * Y)
+    Rs = np.maximum(R, r_in)
+    sigma0 = _sigma0_from_mass(0.09, r_in, half_xy)
+    T_mid0, T_atm0 = 20.0, 60.0
+    T_mid = T_mid0 * (Rs / 100.0) ** -0.5
+    T_atm = T_atm0 * (Rs / 100.0) ** -0.5
+    z_q = 70.0 * (Rs / 150.0) ** 1.3
+    blend = np.where(np.abs(Z) < z_q, np.sin(math.pi * np.abs(Z) / (2.0 * z_q)) ** 2, 1.0)
+    T = T_mid + (T_atm - T_mid) * blend
+    m_mol = MEAN_MOL_AMU * AMU_G
+    cs = np.sqrt(K_BOLTZ * T_mid / m_mol)
+    H = cs / np.sqrt(GM_SUN * mstar / (Rs * AU_CM) ** 3)
+    sig = sigma0 * (Rs / 100.0) ** -1 * np.exp(-Rs / 300.0)
+    n = sig / (math.sqrt(2.0 * math.pi) * H) * np.exp(-(Z * AU_CM) ** 2 / (2.0 * H ** 2)) / m_mol
+
+    def modes(k):
+        f = np.zeros_like(X)
+        for _ in range(k):
+            lam = rng.uniform(100.0, 400.0)
+            d = rng.standard_normal(3)
+            d /= np.linalg.norm(d)
+            ph = rng.uniform(0.0, 2.0 * math.pi)
+            f += np.cos(2.0 * math.pi * (d[0] * X + d[1] * Y + d[2] * Z) / lam + ph)
+        return f / math.sqrt(k)
+
+    T = T * np.exp(turb * modes(6))
+    n = n * np.exp(turb * modes(6))
+    n[R < r_in] = 0.0
+    x_co = 1e-4 * np.exp(-0.5 * ((np.abs(Z) / Rs - 0.2) / 0.08) ** 2)
+    vphi = np.sqrt(GM_SUN * mstar * (Rs * AU_CM) ** 2 / ((Rs * AU_CM) ** 2 + (Z * AU_CM) ** 2) ** 1.5) / 1e5
+    vx = -vphi * Y / Rs + 0.1 * modes(3)
+    vy = vphi * X / Rs + 0.1 * modes(3)
+    vz = 0.1 * modes(3)
+    g3 = Grid3(gx, gy, gz, (-half_xy, half_xy, -half_xy, half_xy, -half_z, half_z),
+               T, n, np.full_like(T, 0.05), x_co, vx, vy, vz)
+    z2 = np.zeros((2, 2))
+    return Problem(nr=2, nz=2, r_in_au=1.0, r_out_au=2.0, zr_max=1.0, r_log=1,
+                   T=z2 + 1.0, n_h2=z2, vturb=z2, h_lo=np.zeros(2), h_hi=np.zeros(2),
+                   incl_deg=incl, pa_deg=pa, mstar_msun=mstar, nx=nx, ny=ny,
+                   half_fov_au=1.05 * half_xy, v_kms=np.linspace(-vmax, vmax, nch),
+                   n_samples=n_samples, g3=g3,
+                   name=name or f"box{gx}x{gy}x{gz}_px{nx}_ch{nch}_ns{n_samples}", seed=seed)
+
+
+def config_box(seed: int = 0) -> Problem:
+    """3-D workload: 128^3-node box (+-600 au in x, y; +-150 au in z), 256^2 px, 64 channels
+    over +-6 km/s, 256 samples, i = 45 deg."""
+    return box3d(seed, n3=(128, 128, 128), nx=256, ny=256, nch=64, n_samples=256)
 
 
 # --------------------------------------------------------------------------------------
