@@ -256,6 +256,39 @@ int rt_field_chain(const rt_grid *grid, const rt_geom *geom, const rt_line *line
                    float *h_lo, float *h_hi, void *stream);
 
 /*
+ * rt_render3d -- forward march through a general 3-D Cartesian grid (the RadJAX setting
+ * beyond the axisymmetric disk: Methods, "Line Radiative Transfer with RadJAX", and the
+ * 3-D grids of its runtime benchmark): the same transfer (Eq. rt-int / Eq. optical_depth),
+ * LTE source and opacity, line width and Doppler-shifted Gaussian profile as rt_render, with
+ * the fields interpolated trilinearly on the nodes and the line-of-sight velocity taken from
+ * a gas velocity field: v_los = omega . v + v_sys (omega = (0, sin i, -cos i)).
+ * Rays are the pixels of rt_view seen at geom's inclination and position angle; each ray's
+ * chord through the box [x0, x1] x [y0, y1] x [z0, z1] (disk frame, au) is split into
+ * n_samples equal segments with midpoint samples; rays missing the box return I0. Default
+ * half field of view: 1.1 times the largest |extent|. geom->mstar_msun is not used.
+ * grid3: nodes uniformly spaced, nx, ny, nz >= 2 each, nx*ny*nz <= 2^28.
+ * fields3: DEVICE float32 [nz][ny][nx] (x fastest): T_K (> 0), n_h2_cm3, vturb (km/s, or the
+ *   Mach number with vturb_mach), x_co (CO abundance per H2), vx, vy, vz (km/s).
+ * cube: DEVICE [nch][ny][nx] float32, caller-allocated, overwritten.
+ * The call packs the node fields into two float4 records per node (a stream-ordered
+ * allocation of 32 bytes per node, freed after the launch). Forward only.
+ * Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
+ */
+typedef struct {
+  int nx, ny, nz;
+  double x0_au, x1_au, y0_au, y1_au, z0_au, z1_au;
+} rt_grid3;
+
+typedef struct {
+  const float *T_K, *n_h2_cm3, *vturb, *x_co;
+  const float *vx_kms, *vy_kms, *vz_kms;
+  int vturb_mach;
+} rt_fields3;
+
+int rt_render3d(const rt_grid3 *grid3, const rt_fields3 *fields3, const rt_geom *geom,
+                const rt_view *view, const rt_line *line, float *cube, void *stream);
+
+/*
  * rt_pressure_vphi -- pressure-corrected rotation on the nodes (Methods, "Parametric Disk
  * Modeling", Eq. gas_velocity_pressure; "Neural Temperature Recovery" derives v_phi from
  * the density and temperature this way):

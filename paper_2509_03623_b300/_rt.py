@@ -76,6 +76,18 @@ _lock = threading.Lock()
 _lib = None
 
 
+class rt_grid3(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("x0_au", C.c_double), ("x1_au", C.c_double), ("y0_au", C.c_double),
+                ("y1_au", C.c_double), ("z0_au", C.c_double), ("z1_au", C.c_double)]
+
+
+class rt_fields3(C.Structure):
+    _fields_ = [("T_K", C.c_void_p), ("n_h2_cm3", C.c_void_p), ("vturb", C.c_void_p),
+                ("x_co", C.c_void_p), ("vx_kms", C.c_void_p), ("vy_kms", C.c_void_p),
+                ("vz_kms", C.c_void_p), ("vturb_mach", C.c_int)]
+
+
 class rt_chain(C.Structure):
     _fields_ = [("sigma0_gcm2", C.c_double), ("r_c_au", C.c_double), ("gamma", C.c_double),
                 ("T_freeze_K", C.c_double), ("N_dissoc_cm2", C.c_double)]
@@ -131,6 +143,9 @@ def lib():
             L.rt_pressure_vphi.argtypes = [P(rt_grid), P(rt_geom), P(rt_line), C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p]
             L.rt_pressure_vphi.restype = C.c_int
+            L.rt_render3d.argtypes = [P(rt_grid3), P(rt_fields3), P(rt_geom), P(rt_view),
+                                      P(rt_line), C.c_void_p, C.c_void_p]
+            L.rt_render3d.restype = C.c_int
             L.rt_mlp_status.argtypes = [P(C.c_int)]
             L.rt_mlp_status.restype = C.c_int
             L.rt_last_error.restype = C.c_char_p
@@ -369,6 +384,49 @@ def rt_pressure_vphi(problem, n_h2, T, out=None, stream=None):
         out = torch.empty(shp, dtype=torch.float32, device=T.device)
     check(lib().rt_pressure_vphi(C.byref(g), C.byref(o), C.byref(ln), _ptr(n_h2), _ptr(T),
                                  _ptr(out), stream_handle(stream)))
+    return out
+
+
+class DeviceGrid3:
+    """Device-resident float32 fields [nz][ny][nx] of a 3-D grid (problem.g3)."""
+
+    FIELDS = ("T", "n_h2", "vturb", "x_co", "vx", "vy", "vz")
+
+    def __init__(self, problem, device="cuda"):
+        import torch
+        g = problem.g3
+        self.problem = problem
+        for k in self.FIELDS:
+            setattr(self, k, torch.as_tensor(np.ascontiguousarray(getattr(g, k), dtype=np.float32),
+                                             device=device))
+
+
+def rt_render3d(problem, grid=None, out=None, stream=None):
+    """Forward render through a 3-D Cartesian grid (problem.g3); returns the cube tensor
+    [nch][ny][nx] float32."""
+    import torch
+    g3 = problem.g3
+    dg = grid if grid is not None else DeviceGrid3(problem)
+    shp = (int(g3.nz), int(g3.ny), int(g3.nx))
+    for k in DeviceGrid3.FIELDS:
+        t = getattr(dg, k)
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shp:
+            raise ValueError(f"3-D field {k} must be a contiguous CUDA float32 tensor of shape {shp}")
+    gg = rt_grid3(*shp[::-1], *(float(v) for v in g3.extent))
+    f = rt_fields3(*(getattr(dg, k).data_ptr() for k in DeviceGrid3.FIELDS),
+                   int(problem.vturb_mach))
+    o = rt_geom(float(problem.incl_deg), float(problem.pa_deg), float(problem.dist_pc),
+                float(problem.mstar_msun), float(problem.vsys_kms))
+    v = np.ascontiguousarray(np.asarray(problem.v_kms, dtype=np.float32))
+    vw = rt_view(int(problem.nx), int(problem.ny), float(problem.half_fov_au), int(v.size),
+                 v.ctypes.data_as(C.POINTER(C.c_float)), int(problem.n_samples),
+                 float(problem.I0), int(problem.units))
+    ln = rt_line(float(problem.nu0_hz), float(problem.A_ul), float(problem.B_rot_hz),
+                 float(problem.m_co_amu), float(problem.m_mol_amu), int(problem.J_u))
+    if out is None:
+        out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=dg.T.device)
+    check(lib().rt_render3d(C.byref(gg), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                            _ptr(out), stream_handle(stream)))
     return out
 
 

@@ -108,26 +108,8 @@ static void lte_table(double B, int Ju, float *tab) {
   if (n_cached < 4) n_cached++;
 }
 
-int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
-                 const rt_view *view, const rt_line *line, MarchParams *P) {
-  if (!grid || !fields || !geom || !view || !line || !P)
-    return set_error(RT_EINVAL, "null argument struct");
-  const rt_grid &g = *grid;
-  const rt_fields &f = *fields;
-  const rt_geom &o = *geom;
-  const rt_view &v = *view;
-  const rt_line &l = *line;
-  if (g.nr < 2 || g.nz < 2 || (long long)g.nr * g.nz > (1LL << 28))
-    return set_error(RT_EINVAL, "grid needs 2 <= nr, nz and nr*nz <= 2^28 (got %d x %d)", g.nr,
-                     g.nz);
-  if (!is_finite(g.r_in_au) || !is_finite(g.r_out_au) || !(g.r_in_au > 0) ||
-      !(g.r_out_au > g.r_in_au))
-    return set_error(RT_EINVAL, "grid radii need 0 < r_in < r_out");
-  if (!is_finite(g.zr_max) || !(g.zr_max > 0)) return set_error(RT_EINVAL, "zr_max must be > 0");
-  if (!f.T_K || !f.n_h2_cm3 || !f.vturb || !f.h_lo || !f.h_hi)
-    return set_error(RT_EINVAL, "null field pointer");
-  if (!is_finite(f.x_co) || f.x_co < 0) return set_error(RT_EINVAL, "x_co must be finite and >= 0");
-  if (!is_finite(f.edge_w) || f.edge_w < 0) return set_error(RT_EINVAL, "edge_w must be >= 0");
+// Validation of the geometry, view and line shared by every render entry point.
+static int check_common(const rt_geom &o, const rt_view &v, const rt_line &l) {
   if (!is_finite(o.incl_deg) || !is_finite(o.pa_deg) || !is_finite(o.mstar_msun) || o.mstar_msun < 0 ||
       !is_finite(o.vsys_kms))
     return set_error(RT_EINVAL, "geometry must be finite with mstar >= 0");
@@ -148,32 +130,13 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
   for (int c = 0; c < v.nch; c++)
     if (!is_finite(v.v_kms[c])) return set_error(RT_EINVAL, "non-finite channel velocity %d", c);
 
-  memset(P, 0, sizeof(*P));
-  P->nr = g.nr;
-  P->nz = g.nz;
-  P->r_log = g.r_log ? 1 : 0;
-  if (P->r_log) {
-    P->lr_scale = (float)(0.5 * (g.nr - 1) / log2(g.r_out_au / g.r_in_au));
-    P->lr_off = 0.0f;
-  } else {
-    double s = (g.nr - 1) / (g.r_out_au - g.r_in_au);
-    P->lr_scale = (float)s;
-    P->lr_off = (float)(-g.r_in_au * s);
-  }
-  P->r_in2 = (float)(g.r_in_au * g.r_in_au);
-  P->inv_rin2 = (float)(1.0 / (g.r_in_au * g.r_in_au));
-  P->zr_max = (float)g.zr_max;
-  P->w_scale = (float)((g.nz - 1) / g.zr_max);
-  P->T = f.T_K;
-  P->n = f.n_h2_cm3;
-  P->vt = f.vturb;
-  P->hlo = f.h_lo;
-  P->hhi = f.h_hi;
-  P->vphi = f.vphi_kms;
-  P->x_co = (float)f.x_co;
-  P->hard_edge = f.edge_w > 0 ? 0 : 1;
-  P->edge_k = f.edge_w > 0 ? (float)(kLog2e / f.edge_w) : 0.0f;
-  P->vturb_mach = f.vturb_mach ? 1 : 0;
+  return RT_OK;
+}
+
+// Parameters shared by every render (geometry, image, channels, line, LTE table); r_fov: the
+// extent whose 1.1 times sets the default half field of view.
+static void fill_common(const rt_geom &o, const rt_view &v, const rt_line &l, double r_fov,
+                        MarchParams *P) {
   P->c_th = (float)(2.0 * kK / (l.m_co_amu * kAmu) / 1e10);
   P->c_mach = (float)(2.0 * kK / (l.m_mol_amu * kAmu) / 1e10);
 
@@ -183,9 +146,7 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
   P->cos_i = cos(inc);
   P->sin_pa = sin(pa);
   P->cos_pa = cos(pa);
-  P->R_cyl = g.r_out_au;
-  P->H_cyl = g.zr_max * g.r_out_au;
-  double hf = v.half_fov_au > 0 ? v.half_fov_au : 1.1 * g.r_out_au;
+  double hf = v.half_fov_au > 0 ? v.half_fov_au : 1.1 * r_fov;
   P->px = v.nx > 0 ? 2.0 * hf / v.nx : 0.0;
   P->py = v.ny > 0 ? 2.0 * hf / v.ny : 0.0;
   P->vk = (float)(sqrt(kGMsun * o.mstar_msun / kAu) / 1e5);
@@ -234,12 +195,160 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
     }
   }
   lte_table(B, Ju, P->tab);
+}
+
+int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                 const rt_view *view, const rt_line *line, MarchParams *P) {
+  if (!grid || !fields || !geom || !view || !line || !P)
+    return set_error(RT_EINVAL, "null argument struct");
+  const rt_grid &g = *grid;
+  const rt_fields &f = *fields;
+  const rt_geom &o = *geom;
+  const rt_view &v = *view;
+  const rt_line &l = *line;
+  if (g.nr < 2 || g.nz < 2 || (long long)g.nr * g.nz > (1LL << 28))
+    return set_error(RT_EINVAL, "grid needs 2 <= nr, nz and nr*nz <= 2^28 (got %d x %d)", g.nr,
+                     g.nz);
+  if (!is_finite(g.r_in_au) || !is_finite(g.r_out_au) || !(g.r_in_au > 0) ||
+      !(g.r_out_au > g.r_in_au))
+    return set_error(RT_EINVAL, "grid radii need 0 < r_in < r_out");
+  if (!is_finite(g.zr_max) || !(g.zr_max > 0)) return set_error(RT_EINVAL, "zr_max must be > 0");
+  if (!f.T_K || !f.n_h2_cm3 || !f.vturb || !f.h_lo || !f.h_hi)
+    return set_error(RT_EINVAL, "null field pointer");
+  if (!is_finite(f.x_co) || f.x_co < 0) return set_error(RT_EINVAL, "x_co must be finite and >= 0");
+  if (!is_finite(f.edge_w) || f.edge_w < 0) return set_error(RT_EINVAL, "edge_w must be >= 0");
+  int rc = check_common(o, v, l);
+  if (rc != RT_OK) return rc;
+
+  memset(P, 0, sizeof(*P));
+  P->nr = g.nr;
+  P->nz = g.nz;
+  P->r_log = g.r_log ? 1 : 0;
+  if (P->r_log) {
+    P->lr_scale = (float)(0.5 * (g.nr - 1) / log2(g.r_out_au / g.r_in_au));
+    P->lr_off = 0.0f;
+  } else {
+    double s = (g.nr - 1) / (g.r_out_au - g.r_in_au);
+    P->lr_scale = (float)s;
+    P->lr_off = (float)(-g.r_in_au * s);
+  }
+  P->r_in2 = (float)(g.r_in_au * g.r_in_au);
+  P->inv_rin2 = (float)(1.0 / (g.r_in_au * g.r_in_au));
+  P->zr_max = (float)g.zr_max;
+  P->w_scale = (float)((g.nz - 1) / g.zr_max);
+  P->T = f.T_K;
+  P->n = f.n_h2_cm3;
+  P->vt = f.vturb;
+  P->hlo = f.h_lo;
+  P->hhi = f.h_hi;
+  P->vphi = f.vphi_kms;
+  P->x_co = (float)f.x_co;
+  P->hard_edge = f.edge_w > 0 ? 0 : 1;
+  P->edge_k = f.edge_w > 0 ? (float)(kLog2e / f.edge_w) : 0.0f;
+  P->vturb_mach = f.vturb_mach ? 1 : 0;
+  P->R_cyl = g.r_out_au;
+  P->H_cyl = g.zr_max * g.r_out_au;
+  fill_common(o, v, l, g.r_out_au, P);
+  return RT_OK;
+}
+
+// Node records of a 3-D grid: {T, n_H2, v_turb, x_co} and {vx, vy, vz, 0} per node.
+__global__ void pack_nodes3_kernel(const rt_fields3 f, long long n, float4 *__restrict__ a,
+                                   float4 *__restrict__ b) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    a[i] = make_float4(f.T_K[i], f.n_h2_cm3[i], f.vturb[i], f.x_co[i]);
+    b[i] = make_float4(f.vx_kms[i], f.vy_kms[i], f.vz_kms[i], 0.0f);
+  }
+}
+
+static int build_params3(const rt_grid3 *grid, const rt_fields3 *fields, const rt_geom *geom,
+                         const rt_view *view, const rt_line *line, MarchParams *P) {
+  if (!grid || !fields || !geom || !view || !line || !P)
+    return set_error(RT_EINVAL, "null argument struct");
+  const rt_grid3 &g = *grid;
+  const rt_fields3 &f = *fields;
+  if (g.nx < 2 || g.ny < 2 || g.nz < 2 || (long long)g.nx * g.ny * g.nz > (1LL << 28))
+    return set_error(RT_EINVAL, "3-D grid needs >= 2 nodes per axis and <= 2^28 nodes "
+                     "(got %d x %d x %d)", g.nx, g.ny, g.nz);
+  const double ext[6] = {g.x0_au, g.x1_au, g.y0_au, g.y1_au, g.z0_au, g.z1_au};
+  for (int k = 0; k < 6; k++)
+    if (!is_finite(ext[k])) return set_error(RT_EINVAL, "non-finite box extent");
+  if (!(g.x1_au > g.x0_au) || !(g.y1_au > g.y0_au) || !(g.z1_au > g.z0_au))
+    return set_error(RT_EINVAL, "box extents need x0 < x1, y0 < y1, z0 < z1");
+  if (!f.T_K || !f.n_h2_cm3 || !f.vturb || !f.x_co || !f.vx_kms || !f.vy_kms || !f.vz_kms)
+    return set_error(RT_EINVAL, "null field pointer");
+  int rc = check_common(*geom, *view, *line);
+  if (rc != RT_OK) return rc;
+  memset(P, 0, sizeof(*P));
+  P->box = 1;
+  P->bx0 = g.x0_au;
+  P->bx1 = g.x1_au;
+  P->by0 = g.y0_au;
+  P->by1 = g.y1_au;
+  P->bz0 = g.z0_au;
+  P->bz1 = g.z1_au;
+  P->n3x = g.nx;
+  P->n3y = g.ny;
+  P->n3z = g.nz;
+  // per axis the node nearest the middle of the box, its position and the nodes per au
+  auto axis = [](double a0, double a1, int n, int *k, float *c, float *s) {
+    const double sc = (n - 1) / (a1 - a0);
+    int kk = (int)floor(-a0 * sc + 0.5);  // node nearest coordinate 0 ...
+    kk = kk < 0 ? 0 : (kk > n - 1 ? n - 1 : kk);  // ... inside the grid
+    *k = kk;
+    *c = (float)(a0 + kk / sc);
+    *s = (float)sc;
+  };
+  axis(g.x0_au, g.x1_au, g.nx, &P->g3kx, &P->g3cx, &P->g3sx);
+  axis(g.y0_au, g.y1_au, g.ny, &P->g3ky, &P->g3cy, &P->g3sy);
+  axis(g.z0_au, g.z1_au, g.nz, &P->g3kz, &P->g3cz, &P->g3sz);
+  P->vturb_mach = f.vturb_mach ? 1 : 0;
+  double reach = 0.0;
+  for (int k = 0; k < 6; k++) reach = fmax(reach, fabs(ext[k]));
+  fill_common(*geom, *view, *line, reach, P);
+  P->cos_if = (float)P->cos_i;
   return RT_OK;
 }
 
 }  // namespace rtb
 
 using namespace rtb;
+
+extern "C" int rt_render3d(const rt_grid3 *grid3, const rt_fields3 *fields3,
+                           const rt_geom *geom, const rt_view *view, const rt_line *line,
+                           float *cube, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params3(grid3, fields3, geom, view, line, P);
+  const long long npix = rc == RT_OK ? (long long)P->nx * P->ny : 0;
+  if (rc == RT_OK && npix * P->nch > 0 && !cube) rc = set_error(RT_EINVAL, "null cube pointer");
+  if (rc == RT_OK && npix * P->nch > 0) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nodes = (long long)grid3->nx * grid3->ny * grid3->nz;
+    float4 *buf = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)nodes * 2 * sizeof(float4), st);
+    if (e != cudaSuccess) {
+      rc = set_error(RT_ENOMEM, "node records (%lld nodes): %s", nodes, cudaGetErrorString(e));
+    } else {
+      const long long nb = (nodes + 255) / 256;
+      pack_nodes3_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(*fields3, nodes, buf,
+                                                                         buf + nodes);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        rc = set_error(RT_ECUDA, "node packing: %s", cudaGetErrorString(e));
+      } else {
+        P->node_a = buf;
+        P->node_b = buf + nodes;
+        rc = launch_forward(*P, cube, st);
+      }
+      cudaFreeAsync(buf, st);
+    }
+  }
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
 
 extern "C" int rt_render(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
                          const rt_view *view, const rt_line *line, float *cube, void *stream) {

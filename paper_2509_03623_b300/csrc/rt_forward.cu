@@ -39,7 +39,7 @@ constexpr float kWinLog2 = 40.0f;  // skipped optical depths are below 2^-40 per
 
 // Blocks per SM the register budget is sized for: 5 (at most 102 registers) with 8 channels
 // per lane, 6 with 4.
-template <int LPR, int CPL, bool ROT>
+template <int LPR, int CPL, int MODE>
 __global__ void __launch_bounds__(kWarps * 32, CPL == 8 ? 5 : 6)
     march_fwd_kernel(const __grid_constant__ MarchParams P, float *__restrict__ cube) {
   constexpr int R = 32 / LPR;  // rays marched together by one warp (one work unit)
@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(kWarps * 32, CPL == 8 ? 5 : 6)
       }
       const int nsamp = __any_sync(0xffffffffu, ray.hit) ? P.n_samples : 0;
       for (int kb = 0; kb < nsamp; kb += 2 * LPR) {
-        const float4 mine = sample_physics<ROT>(P, s_tab, ray, kb + q);
-        const float4 mine2 = sample_physics<ROT>(P, s_tab, ray, kb + LPR + q);
+        const float4 mine = march_physics<MODE>(P, s_tab, ray, kb + q);
+        const float4 mine2 = march_physics<MODE>(P, s_tab, ray, kb + LPR + q);
         // channel window of a sample (empty without gas): fractional channel indices where
         // kd 2^{-d^2} >= 2^-40; the lane votes with the union of its two samples' windows
         auto window = [&](const float4 &m4, float &lo, float &hi) {
@@ -222,7 +222,8 @@ int resident_blocks(const void *kernel, int threads) {
 
 template <int LPR, int CPL>
 static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
-  auto kern = P.vphi ? march_fwd_kernel<LPR, CPL, true> : march_fwd_kernel<LPR, CPL, false>;
+  auto kern = P.box ? march_fwd_kernel<LPR, CPL, 2>
+                    : (P.vphi ? march_fwd_kernel<LPR, CPL, 1> : march_fwd_kernel<LPR, CPL, 0>);
   long long npix = (long long)P.nx * P.ny;
   long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
   long long need = (units + kWarps - 1) / kWarps;

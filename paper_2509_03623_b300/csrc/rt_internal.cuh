@@ -26,6 +26,18 @@ struct MarchParams {
   float zr_max, w_scale;    // w = (z/r) * w_scale
   const float *T, *n, *vt, *hlo, *hhi;
   const float *vphi;        // optional rotation field [km/s]; nullptr: Keplerian
+  // 3-D Cartesian grid (rt_render3d; box != 0): chord box in double (ray setup), node
+  // placement in float, packed node records {T, n, vt, x_co} and {vx, vy, vz, 0}
+  int box;
+  double bx0, bx1, by0, by1, bz0, bz1;
+  int n3x, n3y, n3z;
+  // per axis: a node near the centre of the box (index k and position c [au]) and the nodes
+  // per au; positions are measured from that node so that the fine FP32 resolution of small
+  // coordinates reaches the interpolation weights where the fields change fastest
+  int g3kx, g3ky, g3kz;
+  float g3cx, g3cy, g3cz, g3sx, g3sy, g3sz;
+  float cos_if;                              // cos i (FP32)
+  const float4 *node_a, *node_b;
   float sin_if;             // sin i (FP32, for v_los = v_phi x sin i / r)
   float x_co, edge_k;       // edge_k = log2(e) / edge_w
   int vturb_mach;
@@ -130,7 +142,24 @@ __device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, b
   double wy = P.sin_i, wz = -P.cos_i;
   double lo = -1e300, hi = 1e300;
   bool ok = active;
-  if (wz != 0.0) {
+  if (P.box) {
+    // chord through the box, slab by slab (omega = (0, wy, wz), so x is constant)
+    if (xs < P.bx0 || xs > P.bx1) ok = false;
+    if (wy != 0.0) {
+      double t1 = (P.by0 - P0y) / wy, t2 = (P.by1 - P0y) / wy;
+      lo = fmax(lo, fmin(t1, t2));
+      hi = fmin(hi, fmax(t1, t2));
+    } else if (P0y < P.by0 || P0y > P.by1) {
+      ok = false;
+    }
+    if (wz != 0.0) {
+      double t1 = (P.bz0 - P0z) / wz, t2 = (P.bz1 - P0z) / wz;
+      lo = fmax(lo, fmin(t1, t2));
+      hi = fmin(hi, fmax(t1, t2));
+    } else if (P0z < P.bz0 || P0z > P.bz1) {
+      ok = false;
+    }
+  } else if (wz != 0.0) {
     double t1 = (-P.H_cyl - P0z) / wz, t2 = (P.H_cyl - P0z) / wz;
     lo = fmax(lo, fmin(t1, t2));
     hi = fmin(hi, fmax(t1, t2));
@@ -138,7 +167,9 @@ __device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, b
     ok = false;
   }
   double c = xs * xs + P0y * P0y - P.R_cyl * P.R_cyl;
-  if (wy != 0.0) {
+  if (P.box) {
+    // (the box chord is complete)
+  } else if (wy != 0.0) {
     double a = wy * wy, b = 2.0 * P0y * wy;
     double disc = b * b - 4.0 * a * c;
     if (disc < 0.0) {
@@ -269,6 +300,25 @@ __device__ __forceinline__ float lte_phi(const float *__restrict__ tab, float t,
   return fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
 }
 
+// Line physics of a sample from its primitives: thermal + turbulent width, LTE source and
+// tabulated opacity factor; returns {kd, a, b, S} (see sample_physics).
+__device__ __forceinline__ float4 line_tail(const MarchParams &P, const float *tab, float T,
+                                            float n, float X, float vt, float vlos, float ds) {
+  float4 out;
+  // line width
+  float Tg = fmaxf(T, 1e-3f);
+  float a2 = P.vturb_mach ? Tg * fmaf(P.c_mach, vt * vt, P.c_th) : fmaf(P.c_th, Tg, vt * vt);
+  float ia = rsq(a2);
+  // LTE: source function and tabulated lower-level opacity factor
+  float phi = lte_phi(tab, lg2(Tg), nullptr);
+  float eS = ex2(-P.theta_s * rcp(Tg));
+  out.w = eS * rcp(1.0f - eS);
+  out.x = P.kappa_k * (X * n) * ex2(phi) * ia * ds;
+  out.z = ia * 1.2011224087864498f;  // b = sqrt(log2 e) / alpha
+  out.y = vlos * out.z;              // a = v_los b
+  return out;
+}
+
 // Channel-independent physics of sample k of a ray: {kd, a, b, S} with
 //   kd  optical depth per unit profile (log2 units): dtau_c = kd 2^{-d_c^2}, 0 without gas
 //   a,b profile argument d_c = v_c b - a (b = sqrt(log2 e)/alpha, a = v_los b)
@@ -281,8 +331,7 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
   float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
   float r2 = fmaf(R.x, R.x, y * y);
   Cell c = locate(P, z, r2);
-  float4 out = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
-  if (!(c.gas && R.hit && k < P.n_samples)) return out;
+  if (!(c.gas && R.hit && k < P.n_samples)) return make_float4(0.0f, 0.0f, 1.0f, 0.0f);
   const NodeVals f = fields_at<ROT>(P, c);
   float T = f.T, n = f.n, vt = f.vt, hlo = f.hlo, hhi = f.hhi;
   if (P.mod) {
@@ -303,18 +352,73 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
   // Keplerian rotation: v_los = sqrt(GM) sin i x (r^2 + z^2)^{-3/4} + v_sys
   float vlos = ROT ? fmaf(f.vphi * (P.sin_if * R.x), c.ir, P.vsys)
                   : fmaf(R.vfac, kepler_q(fmaf(z, z, r2)), P.vsys);
-  // line width
-  float Tg = fmaxf(T, 1e-3f);
-  float a2 = P.vturb_mach ? Tg * fmaf(P.c_mach, vt * vt, P.c_th) : fmaf(P.c_th, Tg, vt * vt);
-  float ia = rsq(a2);
-  // LTE: source function and tabulated lower-level opacity factor
-  float phi = lte_phi(tab, lg2(Tg), nullptr);
-  float eS = ex2(-P.theta_s * rcp(Tg));
-  out.w = eS * rcp(1.0f - eS);
-  out.x = P.kappa_k * (X * n) * ex2(phi) * ia * R.ds;
-  out.z = ia * 1.2011224087864498f;  // b = sqrt(log2 e) / alpha
-  out.y = vlos * out.z;              // a = v_los b
-  return out;
+  return line_tail(P, tab, T, n, X, vt, vlos, R.ds);
+}
+
+// Sample physics on a 3-D Cartesian grid (rt_render3d): trilinear interpolation of the
+// packed node records {T, n, vt, x_co} and {vx, vy, vz, 0} (16 loads of 16 bytes), the
+// line-of-sight velocity omega . v + v_sys with omega = (0, sin i, -cos i), then the line
+// physics of every mode. No gas outside the box.
+__device__ __forceinline__ float4 sample_physics_box(const MarchParams &P, const float *tab,
+                                                     const Ray &R, int k) {
+  const float kf = (float)k;
+  const float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
+  const float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
+  float4 out = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+  if (!(R.hit && k < P.n_samples)) return out;
+  // cell index and weight per axis, from the offset to the axis' central node
+  auto axis = [](float pos, float c, float s, int k, int n, int &i, float &w) {
+    const float f = (pos - c) * s;
+    const float fl = floorf(f);
+    i = k + (int)fl;
+    w = f - fl;
+    if (i < 0) {
+      i = 0;
+      w = 0.0f;
+    } else if (i > n - 2) {
+      i = n - 2;
+      w = 1.0f;
+    }
+  };
+  int ix, iy, iz;
+  float wx, wy, wz;
+  axis(R.x, P.g3cx, P.g3sx, P.g3kx, P.n3x, ix, wx);
+  axis(y, P.g3cy, P.g3sy, P.g3ky, P.n3y, iy, wy);
+  axis(z, P.g3cz, P.g3sz, P.g3kz, P.n3z, iz, wz);
+  const long long sy = P.n3x, sz = (long long)P.n3x * P.n3y;
+  const long long b = iz * sz + iy * sy + ix;
+  const long long o[8] = {b, b + 1, b + sy, b + sy + 1, b + sz, b + sz + 1, b + sz + sy,
+                          b + sz + sy + 1};
+  float4 a[8], v[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    a[c] = __ldg(P.node_a + o[c]);
+    v[c] = __ldg(P.node_b + o[c]);
+  }
+  // trilinear: along x, then y, then z
+  auto tri = [&](float f0, float f1, float f2, float f3, float f4, float f5, float f6, float f7) {
+    const float x0 = lerpf(f0, f1, wx), x1 = lerpf(f2, f3, wx);
+    const float x2 = lerpf(f4, f5, wx), x3 = lerpf(f6, f7, wx);
+    return lerpf(lerpf(x0, x1, wy), lerpf(x2, x3, wy), wz);
+  };
+  const float T = tri(a[0].x, a[1].x, a[2].x, a[3].x, a[4].x, a[5].x, a[6].x, a[7].x);
+  const float n = tri(a[0].y, a[1].y, a[2].y, a[3].y, a[4].y, a[5].y, a[6].y, a[7].y);
+  const float vt = tri(a[0].z, a[1].z, a[2].z, a[3].z, a[4].z, a[5].z, a[6].z, a[7].z);
+  const float X = tri(a[0].w, a[1].w, a[2].w, a[3].w, a[4].w, a[5].w, a[6].w, a[7].w);
+  const float vy = tri(v[0].y, v[1].y, v[2].y, v[3].y, v[4].y, v[5].y, v[6].y, v[7].y);
+  const float vz = tri(v[0].z, v[1].z, v[2].z, v[3].z, v[4].z, v[5].z, v[6].z, v[7].z);
+  if (!(X * n > 0.0f)) return out;
+  const float vlos = fmaf(P.sin_if, vy, fmaf(-P.cos_if, vz, P.vsys));
+  return line_tail(P, tab, T, n, X, vt, vlos, R.ds);
+}
+
+// Sample physics of the forward march by mode: 0 axisymmetric grid, Keplerian rotation; 1
+// axisymmetric grid with a rotation field; 2 3-D Cartesian grid.
+template <int MODE>
+__device__ __forceinline__ float4 march_physics(const MarchParams &P, const float *tab,
+                                                const Ray &R, int k) {
+  if (MODE == 2) return sample_physics_box(P, tab, R, k);
+  return sample_physics<MODE == 1>(P, tab, R, k);
 }
 
 // Host-side helpers (rt_api.cu, rt_forward.cu, rt_adjoint.cu)
