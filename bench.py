@@ -278,6 +278,34 @@ def chain_leg(dev, reps=50):
                                  "graph-replayed launches"}}
 
 
+def box_leg(dev, flush, reps=10):
+    """3-D Cartesian grid march (rt_render3d): 128^3-node box, 256^2 px, 64 channels, 256
+    samples; CUDA-event time per render (node packing included), L2 flushed before each."""
+    import torch
+    from paper_2509_03623_b300 import _rt, synth
+    p = synth.config_box(0)
+    dg = _rt.DeviceGrid3(p, dev)
+    cube = torch.empty((p.nch, p.ny, p.nx), dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        _rt.rt_render3d(p, dg, cube, stream=st)
+    ms = []
+    for i in range(reps):
+        flush.fill_(float(i))  # L2 flush before each timed render (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _rt.rt_render3d(p, dg, cube, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    return {"workload": p.name, "ms": t, "value": p.evals / (t * 1e-3) / 1e9,
+            "unit": "Gevals/s", "nodes": p.g3.nx * p.g3.ny * p.g3.nz,
+            "note": "nominal sample-channel evaluations / time; includes packing the 7 node "
+                    "fields into two float4 records (64 MB)"}
+
+
 def neural_leg(dev, flush, reps=5):
     """Neural-field workload (512x512 px, 128 channels, 256 samples): tensor-core network
     with FP16 and BF16 operands, the FP32 network (cuBLAS, no TF32) driving the same march, and
@@ -391,14 +419,21 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        _rt.rt_render(p, dd, cube)
-    barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.2)
+    # warm-up right before the timed steps: at least W steps and at least 100 ms of work, so
+    # the SM clock is back at its boost level after the idle while the clock sampler started
+    t_end = time.time() + 0.1
+    i = 0
+    while i < args.warmup or time.time() < t_end:
+        flush.fill_(float(i))
+        _rt.rt_render(p, dd, cube)
+        if i % 8 == 7:
+            torch.cuda.synchronize()
+        i += 1
     barrier()
     for i in range(args.steps):
         flush.fill_(float(i))  # L2 flush between timed steps (outside the events)
@@ -431,6 +466,11 @@ def run_ours(args):
     h2d = sum(t.numel() * 4 for t in host.values())
     d2h = cube_h.numel() * 4
     e2e_steps = max(3, args.steps // 2)
+    for _ in range(2):  # untimed: first use of the pinned buffers
+        for k, t in host.items():
+            getattr(dd, k).copy_(t, non_blocking=True)
+        _rt.rt_render(p, dd, cube)
+        cube_h.copy_(cube, non_blocking=True)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -512,6 +552,7 @@ def run_ours(args):
         }
         if world == 1 and not args.no_serving:
             out["field_chain"] = chain_leg(dev)
+            out["box3d"] = box_leg(dev, flush)
             out["neural"] = neural_leg(dev, flush)
             out["serving"] = serving_leg(dev)
         if world == 1 and not args.no_cpu_baseline:

@@ -46,6 +46,13 @@
 #include <stddef.h>
 #include <stdint.h>
 
+/*
+ * Scratch memory. Entry points that say they allocate take stream-ordered allocations on
+ * the caller's stream from a memory pool the library creates for each device (on first use)
+ * and free them on that stream after their kernels; the pool keeps up to 1 GiB of freed
+ * memory cached for the next call instead of returning it to the driver.
+ */
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -172,7 +179,7 @@ int rt_render_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *
  * cube_out (DEVICE, may be NULL) receives the rendered cube (same values as rt_render up to
  * FP32 rounding). Gradients w.r.t. every node of T, n_H2, v_turb and both surfaces
  * overwrite the FP64 arrays. The call allocates and frees one device scratch buffer on
- * `stream` (stream-ordered, cudaMallocAsync) holding the optical-depth checkpoints (every 64
+ * `stream` (stream-ordered) holding the optical-depth checkpoints (every 64
  * samples; the reverse march recomputes everything else) and up to 32 replicated FP32
  * copies of the node gradients (at most 32 MiB, {dT, dn, dvt} interleaved per node) plus up
  * to 128 of the surface gradients: each block of the kernel reduces into one copy, and the

@@ -745,7 +745,7 @@ static int launch_adj_t(const MarchParams &P, const float *dLdc, const float *ta
   const long long blocks = adj_blocks<LPR, CPL, UNIF>(P, 0);
   const AdjScratch a = plan_scratch(P, blocks, blocks * adj_block_bytes<LPR, CPL>(P), 0);
   char *scratch = nullptr;
-  cudaError_t e = cudaMallocAsync((void **)&scratch, a.total, stream);
+  cudaError_t e = stream_alloc((void **)&scratch, a.total, stream);
   if (e != cudaSuccess)
     return set_error(RT_ENOMEM, "adjoint scratch (%zu bytes): %s", a.total,
                      cudaGetErrorString(e));

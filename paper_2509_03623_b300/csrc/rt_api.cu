@@ -108,6 +108,35 @@ static void lte_table(double B, int Ju, float *tab) {
   if (n_cached < 4) n_cached++;
 }
 
+cudaError_t stream_alloc(void **p, size_t bytes, cudaStream_t stream) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+      cudaMemPoolProps props;
+      memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&pools[dev], &props);
+      if (e != cudaSuccess) {
+        pools[dev] = nullptr;
+        return e;
+      }
+      unsigned long long keep = kPoolKeepBytes;
+      cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pool = pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, stream);
+}
+
 // Validation of the geometry, view and line shared by every render entry point.
 static int check_common(const rt_geom &o, const rt_view &v, const rt_line &l) {
   if (!is_finite(o.incl_deg) || !is_finite(o.pa_deg) || !is_finite(o.mstar_msun) || o.mstar_msun < 0 ||
@@ -327,7 +356,7 @@ extern "C" int rt_render3d(const rt_grid3 *grid3, const rt_fields3 *fields3,
     cudaStream_t st = (cudaStream_t)stream;
     const long long nodes = (long long)grid3->nx * grid3->ny * grid3->nz;
     float4 *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)nodes * 2 * sizeof(float4), st);
+    cudaError_t e = stream_alloc((void **)&buf, (size_t)nodes * 2 * sizeof(float4), st);
     if (e != cudaSuccess) {
       rc = set_error(RT_ENOMEM, "node records (%lld nodes): %s", nodes, cudaGetErrorString(e));
     } else {
@@ -539,7 +568,7 @@ extern "C" int rt_render_mlp(const rt_grid *grid, const rt_fields *fields, const
     size_t list_bytes = sample_list_bytes(npix, P->n_samples);
     size_t bytes = mod_bytes + ray_bytes + list_bytes;
     float4 *mod = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&mod, bytes, st);
+    cudaError_t e = stream_alloc((void **)&mod, bytes, st);
     if (e != cudaSuccess) {
       rc = set_error(RT_ENOMEM, "modulation buffer (%zu bytes): %s", bytes, cudaGetErrorString(e));
     } else {
@@ -581,7 +610,7 @@ extern "C" int rt_render_mlp_adjoint(const rt_grid *grid, const rt_fields *field
     const size_t spill_bytes = mlp_bwd_scratch_bytes(ns);
     const size_t bytes = 2 * mod_bytes + ray_bytes + list_bytes + spill_bytes + 256;
     char *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, bytes, st);
+    cudaError_t e = stream_alloc((void **)&buf, bytes, st);
     if (e != cudaSuccess) {
       rc = set_error(RT_ENOMEM, "neural adjoint buffers (%zu bytes): %s", bytes,
                      cudaGetErrorString(e));

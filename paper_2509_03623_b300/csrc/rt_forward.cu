@@ -304,7 +304,7 @@ int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream) {
   const size_t cb = P.cell ? 0 : cell_bytes(P);
   if (!cb) return launch_march(P, cube, stream);
   void *buf = nullptr;
-  cudaError_t e = cudaMallocAsync(&buf, cb, stream);
+  cudaError_t e = stream_alloc((void **)&buf, cb, stream);
   if (e != cudaSuccess)
     return set_error(RT_ENOMEM, "corner quads (%zu bytes): %s", cb, cudaGetErrorString(e));
   MarchParams *Q = new (std::nothrow) MarchParams(P);

@@ -427,6 +427,11 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
 int set_error(int code, const char *fmt, ...);
 void clear_error();
 int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream);
+// Stream-ordered allocation from a library-owned pool of the current device, which keeps up
+// to kPoolKeepBytes cached between calls (so repeated renders do not map and unmap their
+// scratch); free with cudaFreeAsync.
+constexpr unsigned long long kPoolKeepBytes = 1ull << 30;
+cudaError_t stream_alloc(void **p, size_t bytes, cudaStream_t stream);
 size_t cell_bytes(const MarchParams &P);
 int launch_pressure_vphi(const rt_grid &g, const rt_geom &geo, const rt_line &line,
                          const float *n, const float *T, float *vphi, cudaStream_t stream);

@@ -1328,7 +1328,7 @@ extern "C" int rt_mlp_backward(const rt_mlp *mlp, const float *xy, const float *
   const long long blocks = mlp_bwd_blocks(n);
   const size_t sp = mlp_spill_bytes(blocks);
   char *buf = nullptr;
-  cudaError_t e = cudaMallocAsync((void **)&buf, sp + 256, st);
+  cudaError_t e = stream_alloc((void **)&buf, sp + 256, st);
   if (e != cudaSuccess)
     return set_error(RT_ENOMEM, "mlp backward scratch (%zu bytes): %s", sp + 256,
                      cudaGetErrorString(e));
