@@ -62,6 +62,24 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def rank_max(values, device):
+    """Element-wise maximum of `values` over the ranks of the default process group (the job's
+    step time is its slowest rank's); the values themselves with one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_rate(evals_per_rank: int, world: int, t_max_ms: float) -> float:
+    """Whole-job throughput of a weak-scaling step [G evals/s]: every rank processes
+    evals_per_rank in the slowest rank's time."""
+    return evals_per_rank * world / (t_max_ms * 1e-3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -485,14 +503,9 @@ def run_ours(args):
     clocks = clk.stop()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
 
-    t_max, e2e_max, adj_max = ms, e2e_ms, adj_ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, e2e_ms, adj_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max, e2e_max, adj_max = float(t[0]), float(t[1]), float(t[2])
+    t_max, e2e_max, adj_max = rank_max([ms, e2e_ms, adj_ms], dev)
     evals = p.evals * world
-    value = evals / (t_max * 1e-3) / 1e9
+    value = job_rate(p.evals, world, t_max)
     if rank == 0:
         f_mhz = clocks["sm_mhz"] or SM_MAX_MHZ
         peak = EVALS_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e9
