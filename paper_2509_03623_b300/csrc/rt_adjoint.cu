@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
       }
 
       // ---------------- loss seed ----------------
-      float gI[CPL];
+      float2 gI[CPL / 2];  // dL/d(internal intensity) of slots (2m, 2m+1)
 #pragma unroll
       for (int j = 0; j < CPL; j++) {
         const int ch = q + LPR * j;
@@ -428,15 +428,18 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             loss += (double)r * (double)r;
           }
         }
-        gI[j] = go * P.out_scale;  // dL/d(internal intensity)
+        if (j & 1)
+          gI[j >> 1].y = go * P.out_scale;
+        else
+          gI[j >> 1].x = go * P.out_scale;
       }
       if (nsamp == 0) continue;
 
       // ---------------- reverse march over segments ----------------
       const int nseg_ray = (P.n_samples + kSeg - 1) / kSeg;
-      float A[CPL];
+      float2 A[CPL / 2];  // suffix sums of channel slots (2m, 2m+1)
 #pragma unroll
-      for (int j = 0; j < CPL; j++) A[j] = 0.0f;
+      for (int m = 0; m < CPL / 2; m++) A[m] = make_float2(0.0f, 0.0f);
       float Snext = S_bg;
       for (int seg = nseg_ray - 1; seg >= 0; seg--) {
         const int k0 = seg * kSeg;
@@ -477,13 +480,21 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
           const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
           const float Sbefore = Snext;
           ph[lane] = mine;
-          float cur[CPL], Tn[CPL];
+          // channel slots in pairs (2m, 2m+1) for the packed two-lane FP32 instructions; a
+          // pair is marched when either slot's block is in the window
+          unsigned act2 = 0;
 #pragma unroll
-          for (int j = 0; j < CPL; j++) {
-            cur[j] = bs[((b + 1) * CPL + j) * 32 + lane];
-            Tn[j] = ex2(-cur[j]);
+          for (int m = 0; m < CPL / 2; m++)
+            if ((act >> (2 * m)) & 3u) act2 |= 1u << m;
+          float2 cur[CPL / 2], Tn[CPL / 2];
+#pragma unroll
+          for (int m = 0; m < CPL / 2; m++) {
+            cur[m] = make_float2(bs[((b + 1) * CPL + 2 * m) * 32 + lane],
+                                 bs[((b + 1) * CPL + 2 * m + 1) * 32 + lane]);
+            Tn[m] = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
           }
           __syncwarp();
+          const float2 mone = make_float2(-1.0f, -1.0f);
 #pragma unroll 1
           for (int t = LPR - 1; t >= 0; t--) {
             const float4 p = ph[rr * LPR + t];
@@ -491,35 +502,46 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
             Snext = gas ? p.w : Snext;
             const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
-            float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            const float2 cs2 = make_float2(cs, cs), kd2 = make_float2(p.x, p.x);
+            float2 ax = make_float2(0.0f, 0.0f), ay = ax, aw = ax;
 #pragma unroll
-            for (int j = 0; j < CPL; j++) {
-              if (!(act & (1u << j))) continue;  // warp-uniform
-              const float d = UNIF ? fmaf((float)j, db, dc) : fmaf(vc[j], p.z, -p.y);
-              const float d2 = d * d;
-              const float gg = ex2(-d2);
-              A[j] = fmaf(cs, Tn[j], A[j]);
-              const float ug = gI[j] * A[j] * gg;
-              acc.x += ug;
-              acc.y = fmaf(ug, d2, acc.y);
-              const float dt = p.x * gg;
-              cur[j] -= dt;
-              const float T0 = ex2(-cur[j]);
+            for (int m = 0; m < CPL / 2; m++) {
+              if (!(act2 & (1u << m))) continue;  // warp-uniform
+              const float2 d =
+                  UNIF ? __ffma2_rn(make_float2((float)(2 * m), (float)(2 * m + 1)),
+                                    make_float2(db, db), make_float2(dc, dc))
+                       : __ffma2_rn(make_float2(vc[2 * m], vc[2 * m + 1]),
+                                    make_float2(p.z, p.z), make_float2(-p.y, -p.y));
+              const float2 d2 = __fmul2_rn(d, d);
+              const float2 gg = make_float2(ex2(-d2.x), ex2(-d2.y));
+              A[m] = __ffma2_rn(cs2, Tn[m], A[m]);
+              const float2 ug = __fmul2_rn(__fmul2_rn(gI[m], A[m]), gg);
+              ax = __fadd2_rn(ax, ug);
+              ay = __ffma2_rn(ug, d2, ay);
+              const float2 dt = __fmul2_rn(kd2, gg);
+              cur[m] = __ffma2_rn(dt, mone, cur[m]);
+              const float2 T0 = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
               // T_k - T_{k+1} = T_{k+1} (2^dt - 1): series below dt = 0.07 (the difference of
               // two rounded transmittances would lose the small optical depths)
-              const float dTk = dt < 0.07f ? Tn[j] * dt * fmaf(fmaf(dt, 0.0555041087f, 0.240226507f),
-                                                               dt, 0.693147181f)
-                                           : T0 - Tn[j];
-              acc.w = fmaf(gI[j], dTk, acc.w);
-              Tn[j] = T0;
+              const float2 poly = __ffma2_rn(
+                  __ffma2_rn(dt, make_float2(0.0555041087f, 0.0555041087f),
+                             make_float2(0.240226507f, 0.240226507f)),
+                  dt, make_float2(0.693147181f, 0.693147181f));
+              const float2 ser = __fmul2_rn(__fmul2_rn(Tn[m], dt), poly);
+              const float2 dif = __ffma2_rn(Tn[m], mone, T0);
+              const float2 dTk = make_float2(dt.x < 0.07f ? ser.x : dif.x,
+                                             dt.y < 0.07f ? ser.y : dif.y);
+              aw = __ffma2_rn(gI[m], dTk, aw);
+              Tn[m] = T0;
             }
-            part[t][lane ^ (t & 7)] = acc;
+            part[t][lane ^ (t & 7)] = make_float4(ax.x + ax.y, ay.x + ay.y, 0.0f, aw.x + aw.y);
           }
           // blocks outside every window: T is constant over the batch, so the suffix sums
           // advance by T (S before the batch - S of its first sample with gas)
+          const float dS = Sbefore - Snext;
 #pragma unroll
-          for (int j = 0; j < CPL; j++)
-            if (!(act & (1u << j))) A[j] = fmaf(Sbefore - Snext, Tn[j], A[j]);
+          for (int m = 0; m < CPL / 2; m++)
+            if (!(act2 & (1u << m))) A[m] = __ffma2_rn(make_float2(dS, dS), Tn[m], A[m]);
           __syncwarp();
           float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll 8
