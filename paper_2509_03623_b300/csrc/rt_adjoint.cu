@@ -370,42 +370,58 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
       const int nsamp = __any_sync(0xffffffffu, ray.hit) ? P.n_samples : 0;
 
       // ---------------- forward march with checkpoints every kSeg samples ----------------
-      float tl[CPL], tb[CPL], Tr[CPL], I[CPL];
+      // channel slots in pairs (2m, 2m+1), packed two-lane FP32 instructions
+      float2 tl[CPL / 2], tb[CPL / 2], Tr[CPL / 2], I[CPL / 2];
 #pragma unroll
-      for (int j = 0; j < CPL; j++) {
-        tl[j] = 0.0f;
-        tb[j] = 0.0f;
-        Tr[j] = 1.0f;
-        I[j] = 0.0f;
+      for (int m = 0; m < CPL / 2; m++) {
+        tl[m] = make_float2(0.0f, 0.0f);
+        tb[m] = make_float2(0.0f, 0.0f);
+        Tr[m] = make_float2(1.0f, 1.0f);
+        I[m] = make_float2(0.0f, 0.0f);
       }
+      const float2 mone = make_float2(-1.0f, -1.0f);
       for (int kb = 0; kb < nsamp; kb += LPR) {
         if (kb % kSeg == 0) {
 #pragma unroll
-          for (int j = 0; j < CPL; j++) ck[((kb / kSeg) * CPL + j) * 32 + lane] = tb[j];
+          for (int m = 0; m < CPL / 2; m++) {
+            ck[((kb / kSeg) * CPL + 2 * m) * 32 + lane] = tb[m].x;
+            ck[((kb / kSeg) * CPL + 2 * m + 1) * 32 + lane] = tb[m].y;
+          }
         }
         const float4 mine = sample_physics(P, s_tab, ray, kb + q);
         const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
         if (!act) continue;
+        unsigned act2 = 0;
+#pragma unroll
+        for (int m = 0; m < CPL / 2; m++)
+          if ((act >> (2 * m)) & 3u) act2 |= 1u << m;
         ph[lane] = mine;
         __syncwarp();
 #pragma unroll 1
         for (int t = 0; t < LPR; t++) {
           const float4 p = ph[rr * LPR + t];
           const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
+          const float2 kd2 = make_float2(p.x, p.x), S2 = make_float2(p.w, p.w);
 #pragma unroll
-          for (int j = 0; j < CPL; j++) {
-            if (!(act & (1u << j))) continue;  // warp-uniform
-            float d = UNIF ? fmaf((float)j, db, dc) : fmaf(vc[j], p.z, -p.y);
-            tl[j] = fmaf(p.x, ex2(d * -d), tl[j]);
-            float Tn = ex2(-tb[j] - tl[j]);
-            I[j] = fmaf(p.w, Tr[j] - Tn, I[j]);
-            Tr[j] = Tn;
+          for (int m = 0; m < CPL / 2; m++) {
+            if (!(act2 & (1u << m))) continue;  // warp-uniform
+            const float2 d =
+                UNIF ? __ffma2_rn(make_float2((float)(2 * m), (float)(2 * m + 1)),
+                                  make_float2(db, db), make_float2(dc, dc))
+                     : __ffma2_rn(make_float2(vc[2 * m], vc[2 * m + 1]),
+                                  make_float2(p.z, p.z), make_float2(-p.y, -p.y));
+            const float2 d2 = __fmul2_rn(d, d);
+            tl[m] = __ffma2_rn(kd2, make_float2(ex2(-d2.x), ex2(-d2.y)), tl[m]);
+            const float2 nt = __fadd2_rn(tb[m], tl[m]);
+            const float2 Tn = make_float2(ex2(-nt.x), ex2(-nt.y));
+            I[m] = __ffma2_rn(S2, __ffma2_rn(Tn, mone, Tr[m]), I[m]);
+            Tr[m] = Tn;
           }
         }
 #pragma unroll
-        for (int j = 0; j < CPL; j++) {
-          tb[j] += tl[j];
-          tl[j] = 0.0f;
+        for (int m = 0; m < CPL / 2; m++) {
+          tb[m] = __fadd2_rn(tb[m], tl[m]);
+          tl[m] = make_float2(0.0f, 0.0f);
         }
         __syncwarp();
       }
@@ -418,7 +434,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
         float go = 0.0f;
         if (active && ch < P.nch) {
           const long long o = (long long)ch * npix + pix;
-          const float out = fmaf(I[j], P.out_scale, P.I0 * Tr[j]);
+          const float Ij = (j & 1) ? I[j >> 1].y : I[j >> 1].x;
+          const float Trj = (j & 1) ? Tr[j >> 1].y : Tr[j >> 1].x;
+          const float out = fmaf(Ij, P.out_scale, P.I0 * Trj);
           if (cube_out) cube_out[o] = out;
           if (dLdc) {
             go = dLdc[o];
