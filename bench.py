@@ -430,6 +430,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     executed = _rt.rt_count_gas_samples(p, dd) * p.nch
     _, phys_samples, computed = _rt.rt_render_work(p, dd, cube)  # untimed: work of one launch
+    launches_per_step = _rt.rt_render_launch_count(p, dd)  # corner-quad packing + march
 
     def barrier():
         if world > 1:
@@ -542,7 +543,7 @@ def run_ours(args):
                          "frac_at_measured_clock": mufu_achieved / (mufu_peak * f_mhz / SM_MAX_MHZ)},
             "e2e": {"value": evals / (e2e_max * 1e-3) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * launches_per_step,
             "fwd_adjoint": {"value": evals / (adj_max * 1e-3) / 1e9, "unit": UNIT,
                             "ms_per_step": adj_max, "steps": adj_steps,
                             "note": "fused forward + reverse march, node gradients summed in per-block "

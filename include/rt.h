@@ -158,6 +158,15 @@ typedef struct {
 } rt_grads;
 
 /*
+ * rt_render_launch_count -- number of kernel launches rt_render makes for this problem
+ * (written to *count, HOST): 0 for an empty image or channel list, 2 when it packs the corner
+ * quads first (from 4M samples, see rt_render), else 1. Nothing is launched. Returns RT_OK or
+ * RT_EINVAL.
+ */
+int rt_render_launch_count(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                           const rt_view *view, const rt_line *line, int *count);
+
+/*
  * rt_render_work -- rt_render that also counts its work into work (DEVICE, 2 x uint64,
  * overwritten): work[0] = samples with gas whose channel-independent physics was evaluated,
  * work[1] = sample-channel evaluations computed (after the channel window). For roofline

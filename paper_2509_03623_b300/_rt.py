@@ -146,6 +146,8 @@ def lib():
             L.rt_render3d.argtypes = [P(rt_grid3), P(rt_fields3), P(rt_geom), P(rt_view),
                                       P(rt_line), C.c_void_p, C.c_void_p]
             L.rt_render3d.restype = C.c_int
+            L.rt_render_launch_count.argtypes = base + [P(C.c_int)]
+            L.rt_render_launch_count.restype = C.c_int
             L.rt_mlp_status.argtypes = [P(C.c_int)]
             L.rt_mlp_status.restype = C.c_int
             L.rt_last_error.restype = C.c_char_p
@@ -225,6 +227,17 @@ def rt_render(problem, fields=None, out=None, stream=None):
     check(lib().rt_render(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
                           C.c_void_p(out.data_ptr()), stream_handle(stream)))
     return out
+
+
+def rt_render_launch_count(problem, fields=None) -> int:
+    """Kernel launches rt_render makes for `problem` (2 with the corner-quad packing)."""
+    dd = fields if fields is not None else DeviceDisk(problem)
+    T, n, vt, hlo, hhi = dd.tensors()
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi, getattr(dd, "vphi", None))
+    c = C.c_int()
+    check(lib().rt_render_launch_count(C.byref(g), C.byref(f), C.byref(o), C.byref(vw),
+                                       C.byref(ln), C.byref(c)))
+    return c.value
 
 
 def rt_count_gas_samples(problem, fields=None, stream=None) -> int:

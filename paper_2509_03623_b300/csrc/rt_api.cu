@@ -396,6 +396,22 @@ extern "C" int rt_render(const rt_grid *grid, const rt_fields *fields, const rt_
   return rc;
 }
 
+extern "C" int rt_render_launch_count(const rt_grid *grid, const rt_fields *fields,
+                                      const rt_geom *geom, const rt_view *view,
+                                      const rt_line *line, int *count) {
+  if (!count) return set_error(RT_EINVAL, "null count pointer");
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params(grid, fields, geom, view, line, P);
+  if (rc == RT_OK) {
+    const long long n = (long long)P->nx * P->ny * P->nch;
+    *count = n == 0 ? 0 : (cell_bytes(*P) ? 2 : 1);
+    clear_error();
+  }
+  delete P;
+  return rc;
+}
+
 extern "C" int rt_render_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
                               const rt_view *view, const rt_line *line, float *cube,
                               unsigned long long *work, void *stream) {

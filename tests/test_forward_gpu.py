@@ -150,3 +150,11 @@ def test_corner_quads_full_cube(rt, orc):
     assert p.nx * p.ny * p.n_samples >= 1 << 22
     g = gpu_cube(rt, p)
     assert_cube_close(g, orc.render(p), label="corner quads vs oracle")
+
+
+def test_render_launch_count(rt):
+    """rt_render launches the march alone below 4M samples and packs corner quads first above
+    it; the benchmark reports launches from this count."""
+    assert rt.rt_render_launch_count(synth.config_small(0)) == 1
+    assert rt.rt_render_launch_count(synth.config_observation(0)) == 2
+    assert rt.rt_render_launch_count(synth.config_small(0).replace(nx=0)) == 0
