@@ -76,8 +76,8 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   const float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
   const float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
   const float r2 = fmaf(R.x, R.x, y * y);
+  if (!(in_gas(P, z, r2) && R.hit && k < P.n_samples)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const Cell c = locate(P, z, r2);
-  if (!(c.gas && R.hit && k < P.n_samples)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const NodeVals f = fields_at<false>(P, c);  // the adjoint takes Keplerian rotation
   float T = f.T, n = f.n, hlo = f.hlo, hhi = f.hhi;
   const float vt = f.vt;

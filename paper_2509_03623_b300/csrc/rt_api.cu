@@ -264,6 +264,7 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
   P->r_in2 = (float)(g.r_in_au * g.r_in_au);
   P->inv_rin2 = (float)(1.0 / (g.r_in_au * g.r_in_au));
   P->zr_max = (float)g.zr_max;
+  P->zr_max2 = (float)(g.zr_max * g.zr_max);
   P->w_scale = (float)((g.nz - 1) / g.zr_max);
   P->T = f.T_K;
   P->n = f.n_h2_cm3;

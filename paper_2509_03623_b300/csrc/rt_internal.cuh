@@ -24,6 +24,7 @@ struct MarchParams {
   float lr_scale, lr_off;   // u = lg2(r^2/r_in^2)*lr_scale (log grid) or r*lr_scale+lr_off
   float r_in2, inv_rin2;    // r_in^2 [au^2] and its reciprocal
   float zr_max, w_scale;    // w = (z/r) * w_scale
+  float zr_max2;            // zr_max^2 (gas test without a square root)
   const float *T, *n, *vt, *hlo, *hhi;
   const float *vphi;        // optional rotation field [km/s]; nullptr: Keplerian
   // 3-D Cartesian grid (rt_render3d; box != 0): chord box in double (ray setup), node
@@ -218,11 +219,16 @@ struct Cell {
   bool gas;
 };
 
+// Gas is inside the grid: r >= r_in and |z|/r <= zr_max (as z^2 <= zr_max^2 r^2).
+__device__ __forceinline__ bool in_gas(const MarchParams &P, float z, float r2) {
+  return (r2 >= P.r_in2) && (z * z <= P.zr_max2 * r2);
+}
+
 __device__ __forceinline__ Cell locate(const MarchParams &P, float z, float r2) {
   Cell c;
   float ir = rsq(r2);
   float zr = fabsf(z) * ir;
-  c.gas = (r2 >= P.r_in2) && (zr <= P.zr_max);
+  c.gas = in_gas(P, z, r2);
   float u = P.r_log ? lg2(r2 * P.inv_rin2) * P.lr_scale : fmaf(r2 * ir, P.lr_scale, P.lr_off);
   u = fminf(fmaxf(u, 0.0f), (float)(P.nr - 1));
   int i0 = min((int)u, P.nr - 2);
@@ -330,8 +336,9 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
   float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
   float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
   float r2 = fmaf(R.x, R.x, y * y);
+  // samples without gas leave before the grid location (two multiplies and compares)
+  if (!(in_gas(P, z, r2) && R.hit && k < P.n_samples)) return make_float4(0.0f, 0.0f, 1.0f, 0.0f);
   Cell c = locate(P, z, r2);
-  if (!(c.gas && R.hit && k < P.n_samples)) return make_float4(0.0f, 0.0f, 1.0f, 0.0f);
   const NodeVals f = fields_at<ROT>(P, c);
   float T = f.T, n = f.n, vt = f.vt, hlo = f.hlo, hhi = f.hhi;
   if (P.mod) {
