@@ -189,7 +189,9 @@ int rt_render_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *
  * FP32 rounding). Gradients w.r.t. every node of T, n_H2, v_turb and both surfaces
  * overwrite the FP64 arrays. The call allocates and frees one device scratch buffer on
  * `stream` (stream-ordered) holding the optical-depth checkpoints (every 64
- * samples; the reverse march recomputes everything else) and up to 32 replicated FP32
+ * samples), the reverse march's per-warp record of the 64-sample segment it is reversing
+ * (recomputed from the segment's checkpoint: batch optical depths, and the physics and local
+ * derivatives of each sample, 80 bytes per sample) and up to 32 replicated FP32
  * copies of the node gradients (at most 32 MiB, {dT, dn, dvt} interleaved per node) plus up
  * to 128 of the surface gradients: each block of the kernel reduces into one copy, and the
  * copies are summed in FP64, in a fixed order, into the outputs at the end. Atomics on one
@@ -213,7 +215,7 @@ int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geo
  * memory, or a service that runs under a fixed device-memory budget and allows no allocator
  * traffic once it is running. This entry point performs no device or host allocation: its
  * scratch (checkpoints, and replicated gradient accumulators where room is left) is one
- * fixed 16 MiB array in the library's device memory, which every GPU that loads the library
+ * fixed 32 MiB array in the library's device memory, which every GPU that loads the library
  * holds until the process exits.
  * Arguments, seeds, outputs and results are those of rt_render_adjoint. In addition:
  *   - The first call on a device looks up the array's device address (with that device
@@ -222,12 +224,12 @@ int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geo
  *     checkpoints are written before they are read, the gradient copies are zeroed on
  *     `stream`), but calls whose kernels overlap on the GPU (different streams, or different
  *     host threads) race on the array: serialize them.
- *   - Checkpoints get at most 12 MiB of the array. When that cannot hold checkpoints for a
+ *   - Checkpoints get at most 24 MiB of the array. When that cannot hold checkpoints for a
  *     full grid, fewer blocks are launched; where fewer gradient copies fit (or none: then
  *     the kernel adds straight into the FP64 output arrays), the sums run in another order.
  *     Same results up to that rounding (about 1e-7 of the largest gradient), lower
- *     throughput. A problem whose single block needs more than 12 MiB
- *     of checkpoints (above about 196,000 samples per ray at the earliest) is rejected with
+ *     throughput. A problem whose single block needs more than 24 MiB
+ *     of checkpoints (above about 389,000 samples per ray at the earliest) is rejected with
  *     RT_EINVAL and a message naming the limit.
  * Returns RT_OK, RT_EINVAL or RT_ECUDA.
  */

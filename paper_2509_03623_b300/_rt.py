@@ -320,7 +320,7 @@ def rt_render_adjoint_noalloc(problem, fields, cube_out, grads, dL_dcube=None, t
     """rt_render_adjoint without any allocation inside the library: for callers that must
     not allocate device memory while running. Every buffer (cube_out and the float64
     gradient tensors in `grads`, keys T, n_h2, vturb, h_lo, h_hi, loss) is supplied by the
-    caller; the library uses its fixed 16 MiB device array for checkpoints and gradient copies."""
+    caller; the library uses its fixed 32 MiB device array for checkpoints and gradient copies."""
     T, n, vt, hlo, hhi = fields.tensors()
     g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi,
                                        getattr(fields, "vphi", None))

@@ -39,11 +39,16 @@ constexpr int adj_wpb() {
 }
 constexpr int kSeg = 64;  // samples per checkpoint segment
 
+// Per-sample record of the segment being reversed: the physics {kd, a, b, S} and the local
+// derivatives (below), five float4 per lane and batch.
+constexpr int kRec = 5;
+
 // Per-warp scratch in floats: checkpoints of each segment, then the batch starts of the
-// segment being reversed, each CPL x 32 (lane-contiguous).
+// segment being reversed, each CPL x 32 (lane-contiguous), then the segment's sample records
+// ([batch][kRec][lane] float4).
 template <int LPR, int CPL>
 __host__ __device__ constexpr long long adj_warp_floats(int nseg) {
-  return (long long)(nseg + kSeg / LPR + 1) * CPL * 32;
+  return (long long)(nseg + kSeg / LPR + 1) * CPL * 32 + (long long)(kSeg / LPR) * kRec * 4 * 32;
 }
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -66,12 +71,14 @@ enum {
   J_N,
   kJ
 };
+static_assert(kJ <= 4 * (kRec - 1), "local derivatives fit the sample record");
 
-// Channel-independent physics of sample k with its local derivatives (written to J[e * 32]).
+// Channel-independent physics of sample k with its local derivatives, written where the sample
+// has gas to the record slots rec[32 (i + 1)], i < kRec - 1 (entries 4i .. 4i + 3 of the enum).
 // Returns {kd, a, b, S} as sample_physics does for a sample with gas, and zeros (b = 0 marks
 // "no gas") otherwise. The arithmetic of kd, a, b and S is the same as sample_physics'.
 __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float *tab,
-                                              const Ray &R, int k, float *J) {
+                                              const Ray &R, int k, float4 *rec) {
   const float kf = (float)k;
   const float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
   const float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
@@ -127,22 +134,27 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   const float om = rcp(1.0f - eS);
   const float F = ex2(phi);
   const float q = -0.5f * ia * ia;
-  J[J_KDN * 32] = P.kappa_k * X * F * ia * R.ds;
-  J[J_DPHI * 32] = clampT ? 0.0f : dphi * iT;
-  J[J_QT * 32] = clampT ? 0.0f : q * da2T;
-  J[J_QV * 32] = q * da2v;
+  float J[4 * (kRec - 1)];
+  J[J_KDN] = P.kappa_k * X * F * ia * R.ds;
+  J[J_DPHI] = clampT ? 0.0f : dphi * iT;
+  J[J_QT] = clampT ? 0.0f : q * da2T;
+  J[J_QV] = q * da2v;
   // S = eS / (1 - eS), eS = 2^{-theta/T}: dS/dT = eS ln2 theta / (T^2 (1 - eS)^2)
-  J[J_DS * 32] = clampT ? 0.0f : eS * om * om * kLn2 * P.theta_s * iT * iT;
-  J[J_SA * 32] = sa;
-  J[J_SB * 32] = sb;
-  J[J_FR * 32] = c.fr;
-  J[J_FZ * 32] = c.fz;
-  J[J_CELL * 32] = __int_as_float(c.j0 * P.nr + c.i0);
-  J[J_I0 * 32] = __int_as_float(c.i0);
-  J[J_MT * 32] = mT;
-  J[J_MN * 32] = mn;
-  J[J_T * 32] = T;
-  J[J_N * 32] = n;
+  J[J_DS] = clampT ? 0.0f : eS * om * om * kLn2 * P.theta_s * iT * iT;
+  J[J_SA] = sa;
+  J[J_SB] = sb;
+  J[J_FR] = c.fr;
+  J[J_FZ] = c.fz;
+  J[J_CELL] = __int_as_float(c.j0 * P.nr + c.i0);
+  J[J_I0] = __int_as_float(c.i0);
+  J[J_MT] = mT;
+  J[J_MN] = mn;
+  J[J_T] = T;
+  J[J_N] = n;
+  for (int e = kJ; e < 4 * (kRec - 1); e++) J[e] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < kRec - 1; i++)
+    rec[(i + 1) * 32] = make_float4(J[4 * i], J[4 * i + 1], J[4 * i + 2], J[4 * i + 3]);
   float4 out;
   out.x = P.kappa_k * (X * n) * F * ia * R.ds;
   out.z = ia * 1.2011224087864498f;  // b = sqrt(log2 e) / alpha
@@ -238,20 +250,20 @@ __device__ __forceinline__ float scatter_grad(const MarchParams &P, const float 
   const float gx = -kLn2 * ax;                       // dL/dkd
   const float GB = 2.0f * kLn2 * kLn2 * kd * ay;     // b dL/db (a = v_los b included)
   const float gk = fmaf(gx, kd, GB);                 // alpha dL/d(1/alpha) ... times ia
-  const float gT = fmaf(gx * kd, J[J_DPHI * 32], fmaf(gk, J[J_QT * 32], aS * J[J_DS * 32]));
-  const float gv = gk * J[J_QV * 32];
-  const float gn = gx * J[J_KDN * 32];
-  const float gl = gx * kd * J[J_SA * 32];
-  const float gh = gx * kd * J[J_SB * 32];
+  const float gT = fmaf(gx * kd, J[J_DPHI], fmaf(gk, J[J_QT], aS * J[J_DS]));
+  const float gv = gk * J[J_QV];
+  const float gn = gx * J[J_KDN];
+  const float gl = gx * kd * J[J_SA];
+  const float gh = gx * kd * J[J_SB];
   float dm = 0.0f;
   if (dmod) {
-    const float4 o = make_float4(gT * J[J_T * 32], gn * J[J_N * 32], gl * P.h_scale, gh * P.h_scale);
+    const float4 o = make_float4(gT * J[J_T], gn * J[J_N], gl * P.h_scale, gh * P.h_scale);
     *dmod = o;
     dm = fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fmaxf(fabsf(o.z), fabsf(o.w)));
   }
-  const float dT = gT * J[J_MT * 32], dn = gn * J[J_MN * 32];
-  const float fr = J[J_FR * 32], fz = J[J_FZ * 32];
-  const int i00 = __float_as_int(J[J_CELL * 32]), i0 = __float_as_int(J[J_I0 * 32]);
+  const float dT = gT * J[J_MT], dn = gn * J[J_MN];
+  const float fr = J[J_FR], fz = J[J_FZ];
+  const int i00 = __float_as_int(J[J_CELL]), i0 = __float_as_int(J[J_I0]);
   const int nr = P.nr;
   const int idx[4] = {i00, i00 + 1, i00 + nr, i00 + nr + 1};
   const float w[4] = {(1.0f - fr) * (1.0f - fz), fr * (1.0f - fz), (1.0f - fr) * fz, fr * fz};
@@ -324,7 +336,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
   __shared__ Ray s_ray[WPB][32];
   // per-sample channel sums of each lane, [sample t][lane ^ (t & 7)] (conflict-free both ways)
   __shared__ float4 s_part[WPB][LPR][32];
-  __shared__ float s_jac[WPB][kJ][32];
+  __shared__ unsigned s_act[WPB][NB];  // window of each batch of the segment being reversed
   for (int i = threadIdx.x; i < kTabSeg * 4; i += blockDim.x) s_tab[i] = P.tab[i];
   __syncthreads();
 
@@ -336,9 +348,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
   const long long gw = (long long)blockIdx.x * WPB + wib;
   float *ck = scratch + gw * adj_warp_floats<LPR, CPL>(nseg);  // this warp's checkpoints
   float *bs = ck + (long long)nseg * CPL * 32;                  // and batch starts
+  float4 *rec = reinterpret_cast<float4 *>(bs + (NB + 1) * CPL * 32) + lane;  // sample records
   float4 *ph = s_ph[wib];
   float4(*part)[32] = s_part[wib];
-  float *Jl = &s_jac[wib][0][lane];
   float vc[CPL];
 #pragma unroll
   for (int j = 0; j < CPL; j++)
@@ -466,11 +478,16 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
         float tbs[CPL];
 #pragma unroll
         for (int j = 0; j < CPL; j++) tbs[j] = ck[(seg * CPL + j) * 32 + lane];
+        __syncwarp();  // the previous segment's reverse pass has read s_act
         for (int b = 0; b < nb; b++) {
 #pragma unroll
           for (int j = 0; j < CPL; j++) bs[(b * CPL + j) * 32 + lane] = tbs[j];
-          const float4 mine = sample_physics(P, s_tab, ray, k0 + b * LPR + q);
+          // physics and local derivatives, kept for the reverse pass over this batch
+          float4 *rb = rec + (long long)b * kRec * 32;
+          const float4 mine = physics_jac(P, s_tab, ray, k0 + b * LPR + q, rb);
+          rb[0] = mine;
           const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
+          if (lane == 0) s_act[wib][b] = act;
           if (!act) continue;
           ph[lane] = mine;
           __syncwarp();
@@ -489,13 +506,15 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
         }
 #pragma unroll
         for (int j = 0; j < CPL; j++) bs[(nb * CPL + j) * 32 + lane] = tbs[j];
+        __syncwarp();  // s_act of the segment
 
         // backward over the batches of the segment
         for (int b = nb - 1; b >= 0; b--) {
           const int kb = k0 + b * LPR;
-          const float4 mine = physics_jac(P, s_tab, ray, kb + q, Jl);
+          const float4 *rb = rec + (long long)b * kRec * 32;
+          const float4 mine = rb[0];
           if (!__any_sync(0xffffffffu, mine.z > 0.0f)) continue;  // no gas in the batch
-          const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
+          const unsigned act = s_act[wib][b];
           const float Sbefore = Snext;
           ph[lane] = mine;
           // channel slots in pairs (2m, 2m+1) for the packed two-lane FP32 instructions; a
@@ -569,10 +588,20 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             s.y += v.y;
             s.w += v.w;
           }
-          if (active && mine.z > 0.0f)
-            dmx = fmaxf(dmx, scatter_grad(P, Jl, mine.x, s.x, s.y, s.w, Gb,
+          if (active && mine.z > 0.0f) {
+            float Jv[4 * (kRec - 1)];
+#pragma unroll
+            for (int i = 0; i < kRec - 1; i++) {
+              const float4 v = rb[(i + 1) * 32];
+              Jv[4 * i] = v.x;
+              Jv[4 * i + 1] = v.y;
+              Jv[4 * i + 2] = v.z;
+              Jv[4 * i + 3] = v.w;
+            }
+            dmx = fmaxf(dmx, scatter_grad(P, Jv, mine.x, s.x, s.y, s.w, Gb,
                                           dmod ? dmod + (long long)pix * P.n_samples + kb + q
                                                : nullptr));
+          }
           __syncwarp();
         }
       }
@@ -863,7 +892,7 @@ int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, doub
 // ---------------------------------------------------------------------------------------
 namespace rtb {
 
-constexpr size_t kFixedScratchBytes = (size_t)16 << 20;  // 16 MiB per device
+constexpr size_t kFixedScratchBytes = (size_t)32 << 20;  // 32 MiB per device
 static __device__ __align__(256) float g_fixed_scratch[kFixedScratchBytes / sizeof(float)];
 
 // Device address of g_fixed_scratch on the current device. The host-side name is only a
