@@ -78,7 +78,7 @@ def test_noalloc_large_grid_without_room_for_copies(rt):
 def test_noalloc_rejects_oversized_problem(rt):
     import torch
     p = synth.config_small(32).replace(nx=8, ny=8, v_kms=np.linspace(-5, 5, 200),
-                                       n_samples=(1 << 19) + 64)
+                                       n_samples=1 << 20)
     dd = rt.DeviceDisk(p)
     grads, cube = _alloc_outputs(torch, p)
     with pytest.raises(rt.RTError, match="fixed"):
