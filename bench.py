@@ -296,32 +296,51 @@ def chain_leg(dev, reps=50):
                                  "graph-replayed launches"}}
 
 
-def box_leg(dev, flush, reps=10):
-    """3-D Cartesian grid march (rt_render3d): 128^3-node box, 256^2 px, 64 channels, 256
-    samples; CUDA-event time per render (node packing included), L2 flushed before each."""
+def _grid3d_time(dev, flush, p, render, dg, reps):
+    """Median CUDA-event time [ms] of render(p, dg, cube, stream) with L2 flushed before
+    each timed call."""
     import torch
-    from paper_2509_03623_b300 import _rt, synth
-    p = synth.config_box(0)
-    dg = _rt.DeviceGrid3(p, dev)
     cube = torch.empty((p.nch, p.ny, p.nx), dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream(dev)
     for _ in range(3):
-        _rt.rt_render3d(p, dg, cube, stream=st)
+        render(p, dg, cube, stream=st)
     ms = []
     for i in range(reps):
         flush.fill_(float(i))  # L2 flush before each timed render (outside the events)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        _rt.rt_render3d(p, dg, cube, stream=st)
+        render(p, dg, cube, stream=st)
         e1.record(st)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
-    t = statistics.median(ms)
+    return statistics.median(ms)
+
+
+def box_leg(dev, flush, reps=10):
+    """3-D Cartesian grid march (rt_render3d): 128^3-node box, 256^2 px, 64 channels, 256
+    samples; CUDA-event time per render (node packing included), L2 flushed before each."""
+    from paper_2509_03623_b300 import _rt, synth
+    p = synth.config_box(0)
+    t = _grid3d_time(dev, flush, p, _rt.rt_render3d, _rt.DeviceGrid3(p, dev), reps)
     return {"workload": p.name, "ms": t, "value": p.evals / (t * 1e-3) / 1e9,
             "unit": "Gevals/s", "nodes": p.g3.nx * p.g3.ny * p.g3.nz,
             "note": "nominal sample-channel evaluations / time; includes packing the 7 node "
                     "fields into two float4 records (64 MB)"}
+
+
+def sph_leg(dev, flush, reps=10):
+    """3-D spherical grid march (rt_render_sph) on the node count of the paper's runtime
+    benchmark, 512 x 96 x 256 (r, theta, phi), 256^2 px, 64 channels, 512 samples;
+    CUDA-event time per render (node packing included), L2 flushed before each."""
+    from paper_2509_03623_b300 import _rt, synth
+    p = synth.config_sph(0)
+    g = p.gs
+    t = _grid3d_time(dev, flush, p, _rt.rt_render_sph, _rt.DeviceGridSph(p, dev), reps)
+    return {"workload": p.name, "ms": t, "value": p.evals / (t * 1e-3) / 1e9,
+            "unit": "Gevals/s", "nodes": g.nr * g.nth * g.nph,
+            "note": "nominal sample-channel evaluations / time; includes packing the 7 node "
+                    "fields into two float4 records (403 MB)"}
 
 
 def neural_leg(dev, flush, reps=5):
@@ -567,6 +586,7 @@ def run_ours(args):
         if world == 1 and not args.no_serving:
             out["field_chain"] = chain_leg(dev)
             out["box3d"] = box_leg(dev, flush)
+            out["sph3d"] = sph_leg(dev, flush)
             out["neural"] = neural_leg(dev, flush)
             out["serving"] = serving_leg(dev)
         if world == 1 and not args.no_cpu_baseline:
@@ -586,6 +606,14 @@ def run_profile(args):
     build.build()
     dev = torch.device("cuda", 0)
     name = args.profile
+    if name == "sph":
+        p = synth.config_sph(0)
+        dg = _rt.DeviceGridSph(p, dev)
+        cube = _rt.rt_render_sph(p, dg)
+        for _ in range(args.profile_reps):
+            _rt.rt_render_sph(p, dg, cube)
+        torch.cuda.synchronize()
+        return 0
     if name in ("forward", "adjoint"):
         p = workload(0)
     elif name == "small_adjoint":
@@ -626,7 +654,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--profile", default=None,
                     choices=["forward", "adjoint", "small_adjoint", "neural", "neural_adjoint",
-                             "mlp_eval"],
+                             "mlp_eval", "sph"],
                     help="run one workload --profile-reps times for an ncu capture and exit")
     ap.add_argument("--profile-reps", type=int, default=3)
     ap.add_argument("--profile-px", type=int, default=128,

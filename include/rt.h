@@ -307,6 +307,46 @@ int rt_render3d(const rt_grid3 *grid3, const rt_fields3 *fields3, const rt_geom 
                 const rt_view *view, const rt_line *line, float *cube, void *stream);
 
 /*
+ * rt_render_sph -- forward march through a 3-D spherical grid centred on the star. RadJAX
+ * runs on regularly or log-spaced Cartesian or spherical grids (Methods, "Line Radiative
+ * Transfer with RadJAX"), and its runtime benchmark renders a hydrodynamic simulation held
+ * on a 512 x 96 x 256 spherical grid. Same transfer (Eq. rt-int / Eq. optical_depth), LTE
+ * source and opacity, line width and Doppler-shifted Gaussian profile as rt_render3d, with
+ * the fields interpolated trilinearly in (radial index, theta, phi), periodic in phi, and
+ *   v_los = omega . v + v_sys,  v = v_r r^ + v_theta theta^ + v_phi phi^,
+ * omega = (0, sin i, -cos i), theta the colatitude from the disk's +z axis, phi = atan2(y, x)
+ * in [0, 2 pi) in the disk frame (on the axis theta^ and phi^ are taken as 0).
+ * Rays are the pixels of rt_view seen at geom's inclination and position angle; each ray's
+ * chord through the sphere r <= r_out is split into n_samples equal segments with midpoint
+ * samples; samples with r < r_in or theta outside [th0, th1] carry no gas; rays missing the
+ * sphere return I0. Default half field of view: 1.1 r_out. geom->mstar_msun is not used.
+ * grid: nr >= 2 radial nodes, log-spaced (r_log = 1, r_in > 0) or linear (r_log = 0,
+ *   r_in >= 0) over [r_in, r_out] au; nth >= 2 colatitude nodes linear over [th0, th1]
+ *   (0 <= th0 < th1 <= pi, radians); nph >= 1 azimuth nodes at phi_k = 2 pi k / nph;
+ *   nr*nth*nph <= 2^28.
+ * fields: DEVICE float32 [nph][nth][nr] (r fastest): T_K (> 0), n_h2_cm3, vturb (km/s, or the
+ *   Mach number with vturb_mach), x_co (CO abundance per H2), and the velocity components
+ *   vr_kms, vth_kms, vph_kms (km/s).
+ * cube: DEVICE [nch][ny][nx] float32, caller-allocated, overwritten.
+ * The call packs the node fields into two float4 records per node (a stream-ordered
+ * allocation of 32 bytes per node, freed after the launch). Forward only.
+ * Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
+ */
+typedef struct {
+  int nr, nth, nph, r_log;
+  double r_in_au, r_out_au, th0_rad, th1_rad;
+} rt_grid_sph;
+
+typedef struct {
+  const float *T_K, *n_h2_cm3, *vturb, *x_co;
+  const float *vr_kms, *vth_kms, *vph_kms;
+  int vturb_mach;
+} rt_fields_sph;
+
+int rt_render_sph(const rt_grid_sph *grid, const rt_fields_sph *fields, const rt_geom *geom,
+                  const rt_view *view, const rt_line *line, float *cube, void *stream);
+
+/*
  * rt_pressure_vphi -- pressure-corrected rotation on the nodes (Methods, "Parametric Disk
  * Modeling", Eq. gas_velocity_pressure; "Neural Temperature Recovery" derives v_phi from
  * the density and temperature this way):

@@ -53,6 +53,7 @@ class _Problem(C.Structure):
         ("m_co_amu", C.c_double), ("m_mol_amu", C.c_double), ("J_u", C.c_int),
         ("vphi", C.POINTER(C.c_double)),
         ("g3", C.c_void_p),
+        ("gs", C.c_void_p),
     ]
 
 
@@ -65,6 +66,17 @@ class _Grid3(C.Structure):
         ("vturb", C.POINTER(C.c_double)), ("x_co", C.POINTER(C.c_double)),
         ("vx", C.POINTER(C.c_double)), ("vy", C.POINTER(C.c_double)),
         ("vz", C.POINTER(C.c_double)),
+    ]
+
+
+class _GridSph(C.Structure):
+    _fields_ = [
+        ("nr", C.c_int), ("nth", C.c_int), ("nph", C.c_int), ("r_log", C.c_int),
+        ("r_in", C.c_double), ("r_out", C.c_double), ("th0", C.c_double), ("th1", C.c_double),
+        ("T", C.POINTER(C.c_double)), ("n_h2", C.POINTER(C.c_double)),
+        ("vturb", C.POINTER(C.c_double)), ("x_co", C.POINTER(C.c_double)),
+        ("vr", C.POINTER(C.c_double)), ("vth", C.POINTER(C.c_double)),
+        ("vph", C.POINTER(C.c_double)),
     ]
 
 
@@ -151,6 +163,18 @@ class _Packed:
             s.g3 = C.cast(C.pointer(g), C.c_void_p)
         else:
             s.g3 = None
+        gs = getattr(p, "gs", None)
+        if gs is not None:
+            g = _GridSph()
+            g.nr, g.nth, g.nph, g.r_log = int(gs.nr), int(gs.nth), int(gs.nph), int(gs.r_log)
+            g.r_in, g.r_out, g.th0, g.th1 = (float(gs.r_in), float(gs.r_out), float(gs.th0),
+                                             float(gs.th1))
+            g.T, g.n_h2, g.vturb, g.x_co = arr(gs.T), arr(gs.n_h2), arr(gs.vturb), arr(gs.x_co)
+            g.vr, g.vth, g.vph = arr(gs.vr), arr(gs.vth), arr(gs.vph)
+            self.keep.append(g)
+            s.gs = C.cast(C.pointer(g), C.c_void_p)
+        else:
+            s.gs = None
         self.s = s
         self.nch = s.nch
 

@@ -86,6 +86,7 @@ static double box_reach(const orc_grid3 *g) {
 
 static double half_fov(const orc_problem *p) {
   if (p->half_fov_au > 0) return p->half_fov_au;
+  if (p->gs) return 1.1 * p->gs->r_out;
   return 1.1 * (p->g3 ? box_reach(p->g3) : p->r_out_au);
 }
 
@@ -114,6 +115,18 @@ static void ray_setup(const orc_problem *p, int ix, int iy, double P0[3], double
    (sampling rule: the paper does not state one). */
 static int chord(const orc_problem *p, const double P0[3], const double om[3], double *s0,
                  double *s1) {
+  if (p->gs) {
+    /* spherical grid: the chord through the sphere r <= r_out, |P0 + s om| = r_out with
+       |om| = 1 */
+    const double R = p->gs->r_out;
+    const double b = P0[0] * om[0] + P0[1] * om[1] + P0[2] * om[2];
+    const double c = P0[0] * P0[0] + P0[1] * P0[1] + P0[2] * P0[2] - R * R;
+    const double disc = b * b - c;
+    if (!(disc > 0.0)) return 0;
+    *s0 = -b - sqrt(disc);
+    *s1 = -b + sqrt(disc);
+    return 1;
+  }
   if (p->g3) {
     /* 3-D grid: the chord through the box, slab by slab */
     const double lo3[3] = {p->g3->x0, p->g3->y0, p->g3->z0};
@@ -210,6 +223,57 @@ static void eval_point(const orc_problem *p, const orc_mlp *m, const double P[3]
                        const double om[3], pt *st) {
   memset(st, 0, sizeof(*st));
   double x = P[0], y = P[1], z = P[2];
+  if (p->gs) {
+    /* spherical grid: (r, theta, phi) of the point, trilinear interpolation (periodic in
+       phi), the gas velocity from its spherical components */
+    const orc_grid_sph *g = p->gs;
+    const double Rc = sqrt(x * x + y * y), r = sqrt(Rc * Rc + z * z);
+    if (!(r >= g->r_in && r <= g->r_out)) return;
+    const double th = atan2(Rc, z);
+    if (!(th >= g->th0 && th <= g->th1)) return;
+    double ph = atan2(y, x);
+    if (ph < 0.0) ph += 2.0 * M_PI;
+    double u = g->r_log ? log(r / g->r_in) / log(g->r_out / g->r_in) * (g->nr - 1)
+                        : (r - g->r_in) / (g->r_out - g->r_in) * (g->nr - 1);
+    double v = (th - g->th0) / (g->th1 - g->th0) * (g->nth - 1);
+    double w = ph / (2.0 * M_PI) * g->nph;
+    if (u > g->nr - 1) u = g->nr - 1;
+    if (u < 0) u = 0;
+    if (v > g->nth - 1) v = g->nth - 1;
+    if (v < 0) v = 0;
+    int i0 = (int)floor(u), j0 = (int)floor(v), k0 = (int)floor(w);
+    if (i0 > g->nr - 2) i0 = g->nr - 2;
+    if (j0 > g->nth - 2) j0 = g->nth - 2;
+    const double f[3] = {u - i0, v - j0, w - k0};
+    k0 %= g->nph;
+    const int k1 = (k0 + 1) % g->nph;
+    const double *F[7] = {g->T, g->n_h2, g->vturb, g->x_co, g->vr, g->vth, g->vph};
+    double val[7];
+    for (int q = 0; q < 7; q++) {
+      double acc = 0.0;
+      for (int c = 0; c < 8; c++) {
+        const int di = c & 1, dj = (c >> 1) & 1, dk = c >> 2;
+        const double wt = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]) *
+                          (dk ? f[2] : 1.0 - f[2]);
+        acc += wt * F[q][((long long)(dk ? k1 : k0) * g->nth + (j0 + dj)) * g->nr + (i0 + di)];
+      }
+      val[q] = acc;
+    }
+    st->T = val[0];
+    st->n = val[1];
+    st->vt = val[2];
+    st->X = val[3];
+    /* unit vectors r^ = (x, y, z)/r, theta^ = (cos th cos ph, cos th sin ph, -sin th),
+       phi^ = (-sin ph, cos ph, 0); on the axis (Rc = 0) theta^ and phi^ are taken as 0, and
+       at the centre (r = 0) r^ as well */
+    const double st_ = r > 0 ? Rc / r : 0.0, ct = r > 0 ? z / r : 0.0;
+    const double cp = Rc > 0 ? x / Rc : 0.0, sp = Rc > 0 ? y / Rc : 0.0;
+    const double vel[3] = {val[4] * st_ * cp + val[5] * ct * cp - val[6] * sp,
+                           val[4] * st_ * sp + val[5] * ct * sp + val[6] * cp,
+                           val[4] * ct - val[5] * st_};
+    st->vlos = 1e5 * (om[0] * vel[0] + om[1] * vel[1] + om[2] * vel[2]) + p->vsys_kms * 1e5;
+    goto line_physics;
+  }
   if (p->g3) {
     /* 3-D grid: trilinear interpolation of every field, the abundance from its own field and
        the line-of-sight velocity from the gas velocity field */
@@ -432,6 +496,18 @@ static void march_pixel(const orc_problem *p, const orc_mlp *m, int ix, int iy, 
 }
 
 static int check(const orc_problem *p) {
+  if (p && p->gs) {
+    const orc_grid_sph *g = p->gs;
+    if (p->g3 || g->nr < 2 || g->nth < 2 || g->nph < 1 || !(g->r_in >= 0) ||
+        !(g->r_out > g->r_in) || (g->r_log && !(g->r_in > 0)) || !(g->th0 >= 0) ||
+        !(g->th1 > g->th0) || !(g->th1 <= M_PI) || !g->T || !g->n_h2 || !g->vturb ||
+        !g->x_co || !g->vr || !g->vth || !g->vph)
+      return -1;
+    if (p->nx < 1 || p->ny < 1 || p->nch < 0 || p->n_samples < 1 || (p->nch > 0 && !p->v_kms))
+      return -1;
+    if (p->J_u < 1 || !(p->nu0_hz > 0) || !(p->dist_pc > 0)) return -1;
+    return 0;
+  }
   if (p && p->g3) {
     const orc_grid3 *g = p->g3;
     if (g->nx < 2 || g->ny < 2 || g->nz < 2 || !(g->x1 > g->x0) || !(g->y1 > g->y0) ||
@@ -659,7 +735,7 @@ static long long mlp_nb(const orc_mlp *m) {
 static int render_adjoint_impl(const orc_problem *p, const orc_mlp *m, const double *dL_dcube,
                                double *cube, double *dT, double *dn, double *dvt, double *dh_lo,
                                double *dh_hi, double *dW, double *db, int nthreads) {
-  if (check(p) || !dL_dcube) return -1;
+  if (check(p) || !dL_dcube || p->g3 || p->gs) return -1; /* axisymmetric grid only */
   if (m && (mlp_check(m) || m->dims[m->n_layers] < 4 || m->dims[m->n_layers] > 64)) return -1;
   int G = p->nr * p->nz;
   long long npix = (long long)p->nx * p->ny;
@@ -870,7 +946,7 @@ int orc_mlp_grad(const orc_mlp *m, const double *x, const double *gout, int npts
 
 int orc_render_mlp(const orc_problem *p, const orc_mlp *m, const long long *pix, int npix,
                    double *out, int nthreads) {
-  if (check(p) || mlp_check(m) || m->dims[m->n_layers] < 4) return -1;
+  if (check(p) || mlp_check(m) || m->dims[m->n_layers] < 4 || p->g3 || p->gs) return -1;
   long long np = pix ? npix : (long long)p->nx * p->ny;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);

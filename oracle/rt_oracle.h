@@ -34,6 +34,19 @@ typedef struct {
   const double *T, *n_h2, *vturb, *x_co, *vx, *vy, *vz;
 } orc_grid3;
 
+/* 3-D spherical node grid centred on the star (the grid of the paper's runtime benchmark):
+   r log-spaced (r_log=1) or linear (r_log=0) in [r_in, r_out] au; colatitude theta (angle
+   from +z) linear in [th0, th1] rad; azimuth phi = atan2(y, x) in [0, 2 pi) with nph nodes at
+   2 pi k / nph, periodic. Fields [nph][nth][nr] (r fastest): T [K], n_H2 [cm^-3], v_turb,
+   X_CO, and the gas velocity in spherical components (v_r, v_theta, v_phi) [km/s]; trilinear
+   interpolation in (radial index, theta, phi); no gas outside r_in <= r <= r_out,
+   th0 <= theta <= th1. Rays are sampled over their chord through the sphere r <= r_out. */
+typedef struct {
+  int nr, nth, nph, r_log;
+  double r_in, r_out, th0, th1;
+  const double *T, *n_h2, *vturb, *x_co, *vr, *vth, *vph;
+} orc_grid_sph;
+
 typedef struct {
   /* (r, z/r) node grid: r log-spaced (r_log=1) or linear (r_log=0) in [r_in, r_out] au,
      z/r linear in [0, zr_max]. */
@@ -64,6 +77,8 @@ typedef struct {
   /* optional 3-D grid: when set, the node grid, fields, surfaces, rotation and stellar mass
      above are not used; rays are clipped to the box (rt_render3d's sampling rule) */
   const orc_grid3 *g3;
+  /* optional spherical grid (used like g3 when set; g3 must then be NULL) */
+  const orc_grid_sph *gs;
 } orc_problem;
 
 /* Full cube [nch][ny][nx]. Returns 0, or -1 on invalid arguments. */

@@ -88,6 +88,18 @@ class rt_fields3(C.Structure):
                 ("vz_kms", C.c_void_p), ("vturb_mach", C.c_int)]
 
 
+class rt_grid_sph(C.Structure):
+    _fields_ = [("nr", C.c_int), ("nth", C.c_int), ("nph", C.c_int), ("r_log", C.c_int),
+                ("r_in_au", C.c_double), ("r_out_au", C.c_double), ("th0_rad", C.c_double),
+                ("th1_rad", C.c_double)]
+
+
+class rt_fields_sph(C.Structure):
+    _fields_ = [("T_K", C.c_void_p), ("n_h2_cm3", C.c_void_p), ("vturb", C.c_void_p),
+                ("x_co", C.c_void_p), ("vr_kms", C.c_void_p), ("vth_kms", C.c_void_p),
+                ("vph_kms", C.c_void_p), ("vturb_mach", C.c_int)]
+
+
 class rt_chain(C.Structure):
     _fields_ = [("sigma0_gcm2", C.c_double), ("r_c_au", C.c_double), ("gamma", C.c_double),
                 ("T_freeze_K", C.c_double), ("N_dissoc_cm2", C.c_double)]
@@ -146,6 +158,9 @@ def lib():
             L.rt_render3d.argtypes = [P(rt_grid3), P(rt_fields3), P(rt_geom), P(rt_view),
                                       P(rt_line), C.c_void_p, C.c_void_p]
             L.rt_render3d.restype = C.c_int
+            L.rt_render_sph.argtypes = [P(rt_grid_sph), P(rt_fields_sph), P(rt_geom),
+                                        P(rt_view), P(rt_line), C.c_void_p, C.c_void_p]
+            L.rt_render_sph.restype = C.c_int
             L.rt_render_launch_count.argtypes = base + [P(C.c_int)]
             L.rt_render_launch_count.restype = C.c_int
             L.rt_mlp_status.argtypes = [P(C.c_int)]
@@ -412,6 +427,56 @@ class DeviceGrid3:
         for k in self.FIELDS:
             setattr(self, k, torch.as_tensor(np.ascontiguousarray(getattr(g, k), dtype=np.float32),
                                              device=device))
+
+
+def _view_line_geom(problem):
+    o = rt_geom(float(problem.incl_deg), float(problem.pa_deg), float(problem.dist_pc),
+                float(problem.mstar_msun), float(problem.vsys_kms))
+    v = np.ascontiguousarray(np.asarray(problem.v_kms, dtype=np.float32))
+    vw = rt_view(int(problem.nx), int(problem.ny), float(problem.half_fov_au), int(v.size),
+                 v.ctypes.data_as(C.POINTER(C.c_float)), int(problem.n_samples),
+                 float(problem.I0), int(problem.units))
+    ln = rt_line(float(problem.nu0_hz), float(problem.A_ul), float(problem.B_rot_hz),
+                 float(problem.m_co_amu), float(problem.m_mol_amu), int(problem.J_u))
+    return o, v, vw, ln
+
+
+class DeviceGridSph:
+    """Device-resident float32 fields [nph][nth][nr] of a spherical grid (problem.gs)."""
+
+    FIELDS = ("T", "n_h2", "vturb", "x_co", "vr", "vth", "vph")
+
+    def __init__(self, problem, device="cuda"):
+        import torch
+        g = problem.gs
+        self.problem = problem
+        for k in self.FIELDS:
+            setattr(self, k, torch.as_tensor(np.ascontiguousarray(getattr(g, k), dtype=np.float32),
+                                             device=device))
+
+
+def rt_render_sph(problem, grid=None, out=None, stream=None):
+    """Forward render through a 3-D spherical grid (problem.gs); returns the cube tensor
+    [nch][ny][nx] float32."""
+    import torch
+    gs = problem.gs
+    dg = grid if grid is not None else DeviceGridSph(problem)
+    shp = (int(gs.nph), int(gs.nth), int(gs.nr))
+    for k in DeviceGridSph.FIELDS:
+        t = getattr(dg, k)
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shp:
+            raise ValueError(f"spherical field {k} must be a contiguous CUDA float32 tensor of "
+                             f"shape {shp}")
+    gg = rt_grid_sph(int(gs.nr), int(gs.nth), int(gs.nph), int(gs.r_log), float(gs.r_in),
+                     float(gs.r_out), float(gs.th0), float(gs.th1))
+    f = rt_fields_sph(*(getattr(dg, k).data_ptr() for k in DeviceGridSph.FIELDS),
+                      int(problem.vturb_mach))
+    o, v, vw, ln = _view_line_geom(problem)
+    if out is None:
+        out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=dg.T.device)
+    check(lib().rt_render_sph(C.byref(gg), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                              _ptr(out), stream_handle(stream)))
+    return out
 
 
 def rt_render3d(problem, grid=None, out=None, stream=None):

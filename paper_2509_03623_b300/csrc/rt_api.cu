@@ -341,9 +341,114 @@ static int build_params3(const rt_grid3 *grid, const rt_fields3 *fields, const r
   return RT_OK;
 }
 
+static int build_params_sph(const rt_grid_sph *grid, const rt_fields_sph *fields,
+                            const rt_geom *geom, const rt_view *view, const rt_line *line,
+                            MarchParams *P) {
+  if (!grid || !fields || !geom || !view || !line || !P)
+    return set_error(RT_EINVAL, "null argument struct");
+  const rt_grid_sph &g = *grid;
+  const rt_fields_sph &f = *fields;
+  if (g.nr < 2 || g.nth < 2 || g.nph < 1 || (long long)g.nr * g.nth * g.nph > (1LL << 28))
+    return set_error(RT_EINVAL, "spherical grid needs nr, nth >= 2, nph >= 1 and <= 2^28 "
+                     "nodes (got %d x %d x %d)", g.nr, g.nth, g.nph);
+  if (!is_finite(g.r_in_au) || !is_finite(g.r_out_au) || !(g.r_in_au >= 0) ||
+      !(g.r_out_au > g.r_in_au) || (g.r_log && !(g.r_in_au > 0)))
+    return set_error(RT_EINVAL, "spherical grid radii need 0 <= r_in < r_out (0 < r_in on a "
+                     "log grid)");
+  if (!is_finite(g.th0_rad) || !is_finite(g.th1_rad) || !(g.th0_rad >= 0) ||
+      !(g.th1_rad > g.th0_rad) || !(g.th1_rad <= 3.14159265358979323846))
+    return set_error(RT_EINVAL, "colatitudes need 0 <= th0 < th1 <= pi");
+  if (!f.T_K || !f.n_h2_cm3 || !f.vturb || !f.x_co || !f.vr_kms || !f.vth_kms || !f.vph_kms)
+    return set_error(RT_EINVAL, "null field pointer");
+  int rc = check_common(*geom, *view, *line);
+  if (rc != RT_OK) return rc;
+  memset(P, 0, sizeof(*P));
+  P->sph = 1;
+  P->snr = g.nr;
+  P->snth = g.nth;
+  P->snph = g.nph;
+  P->r_log = g.r_log ? 1 : 0;
+  if (P->r_log) {
+    P->lr_scale = (float)(0.5 * (g.nr - 1) / log2(g.r_out_au / g.r_in_au));
+    P->lr_off = 0.0f;
+    P->inv_rin2 = (float)(1.0 / (g.r_in_au * g.r_in_au));
+  } else {
+    const double sc = (g.nr - 1) / (g.r_out_au - g.r_in_au);
+    P->lr_scale = (float)sc;
+    P->lr_off = (float)(-g.r_in_au * sc);
+  }
+  P->r_in2 = (float)(g.r_in_au * g.r_in_au);
+  P->r_out2 = (float)(g.r_out_au * g.r_out_au);
+  P->th0 = (float)g.th0_rad;
+  P->th1 = (float)g.th1_rad;
+  P->th_scale = (float)((g.nth - 1) / (g.th1_rad - g.th0_rad));
+  P->ph_scale = (float)(g.nph / (2.0 * 3.14159265358979323846));
+  P->R_cyl = g.r_out_au;
+  P->vturb_mach = f.vturb_mach ? 1 : 0;
+  fill_common(*geom, *view, *line, g.r_out_au, P);
+  P->cos_if = (float)P->cos_i;
+  return RT_OK;
+}
+
+// Node records {T, n, vt, x_co} and three velocity components per node, for the packing
+// kernel (the Cartesian and spherical grids share it).
+static int pack_and_march(const MarchParams &P0, const rt_fields3 &f, long long nodes,
+                          float *cube, cudaStream_t st) {
+  float4 *buf = nullptr;
+  cudaError_t e = stream_alloc((void **)&buf, (size_t)nodes * 2 * sizeof(float4), st);
+  if (e != cudaSuccess)
+    return set_error(RT_ENOMEM, "node records (%lld nodes): %s", nodes, cudaGetErrorString(e));
+  int rc = RT_OK;
+  const long long nb = (nodes + 255) / 256;
+  pack_nodes3_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(f, nodes, buf,
+                                                                     buf + nodes);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    rc = set_error(RT_ECUDA, "node packing: %s", cudaGetErrorString(e));
+  } else {
+    MarchParams *P = new (std::nothrow) MarchParams(P0);
+    if (!P) {
+      rc = set_error(RT_ENOMEM, "host allocation failed");
+    } else {
+      P->node_a = buf;
+      P->node_b = buf + nodes;
+      rc = launch_forward(*P, cube, st);
+      delete P;
+    }
+  }
+  cudaFreeAsync(buf, st);
+  return rc;
+}
+
 }  // namespace rtb
 
 using namespace rtb;
+
+extern "C" int rt_render_sph(const rt_grid_sph *grid, const rt_fields_sph *fields,
+                             const rt_geom *geom, const rt_view *view, const rt_line *line,
+                             float *cube, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params_sph(grid, fields, geom, view, line, P);
+  const long long npix = rc == RT_OK ? (long long)P->nx * P->ny : 0;
+  if (rc == RT_OK && npix * P->nch > 0 && !cube) rc = set_error(RT_EINVAL, "null cube pointer");
+  if (rc == RT_OK && npix * P->nch > 0) {
+    rt_fields3 f3;
+    f3.T_K = fields->T_K;
+    f3.n_h2_cm3 = fields->n_h2_cm3;
+    f3.vturb = fields->vturb;
+    f3.x_co = fields->x_co;
+    f3.vx_kms = fields->vr_kms;
+    f3.vy_kms = fields->vth_kms;
+    f3.vz_kms = fields->vph_kms;
+    f3.vturb_mach = fields->vturb_mach;
+    rc = pack_and_march(*P, f3, (long long)grid->nr * grid->nth * grid->nph, cube,
+                        (cudaStream_t)stream);
+  }
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
 
 extern "C" int rt_render3d(const rt_grid3 *grid3, const rt_fields3 *fields3,
                            const rt_geom *geom, const rt_view *view, const rt_line *line,
@@ -353,28 +458,9 @@ extern "C" int rt_render3d(const rt_grid3 *grid3, const rt_fields3 *fields3,
   int rc = build_params3(grid3, fields3, geom, view, line, P);
   const long long npix = rc == RT_OK ? (long long)P->nx * P->ny : 0;
   if (rc == RT_OK && npix * P->nch > 0 && !cube) rc = set_error(RT_EINVAL, "null cube pointer");
-  if (rc == RT_OK && npix * P->nch > 0) {
-    cudaStream_t st = (cudaStream_t)stream;
-    const long long nodes = (long long)grid3->nx * grid3->ny * grid3->nz;
-    float4 *buf = nullptr;
-    cudaError_t e = stream_alloc((void **)&buf, (size_t)nodes * 2 * sizeof(float4), st);
-    if (e != cudaSuccess) {
-      rc = set_error(RT_ENOMEM, "node records (%lld nodes): %s", nodes, cudaGetErrorString(e));
-    } else {
-      const long long nb = (nodes + 255) / 256;
-      pack_nodes3_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(*fields3, nodes, buf,
-                                                                         buf + nodes);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) {
-        rc = set_error(RT_ECUDA, "node packing: %s", cudaGetErrorString(e));
-      } else {
-        P->node_a = buf;
-        P->node_b = buf + nodes;
-        rc = launch_forward(*P, cube, st);
-      }
-      cudaFreeAsync(buf, st);
-    }
-  }
+  if (rc == RT_OK && npix * P->nch > 0)
+    rc = pack_and_march(*P, *fields3, (long long)grid3->nx * grid3->ny * grid3->nz, cube,
+                        (cudaStream_t)stream);
   delete P;
   if (rc == RT_OK) clear_error();
   return rc;

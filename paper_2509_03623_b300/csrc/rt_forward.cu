@@ -38,9 +38,10 @@ constexpr int kWarps = 4;        // warps per block
 constexpr float kWinLog2 = 40.0f;  // skipped optical depths are below 2^-40 per sample
 
 // Blocks per SM the register budget is sized for: 5 (at most 102 registers) with 8 channels
-// per lane, 6 with 4.
+// per lane, 6 with 4; 4 (128 registers) for the 3-D grids, whose sample physics holds 16
+// node records in flight.
 template <int LPR, int CPL, int MODE>
-__global__ void __launch_bounds__(kWarps * 32, CPL == 8 ? 5 : 6)
+__global__ void __launch_bounds__(kWarps * 32, MODE >= 2 ? 4 : (CPL == 8 ? 5 : 6))
     march_fwd_kernel(const __grid_constant__ MarchParams P, float *__restrict__ cube) {
   constexpr int R = 32 / LPR;  // rays marched together by one warp (one work unit)
   constexpr int G = 32 / R;    // work units whose ray setups are computed together
@@ -222,8 +223,9 @@ int resident_blocks(const void *kernel, int threads) {
 
 template <int LPR, int CPL>
 static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
-  auto kern = P.box ? march_fwd_kernel<LPR, CPL, 2>
-                    : (P.vphi ? march_fwd_kernel<LPR, CPL, 1> : march_fwd_kernel<LPR, CPL, 0>);
+  auto kern = P.sph ? march_fwd_kernel<LPR, CPL, 3>
+               : P.box ? march_fwd_kernel<LPR, CPL, 2>
+                       : (P.vphi ? march_fwd_kernel<LPR, CPL, 1> : march_fwd_kernel<LPR, CPL, 0>);
   long long npix = (long long)P.nx * P.ny;
   long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
   long long need = (units + kWarps - 1) / kWarps;

@@ -39,6 +39,13 @@ struct MarchParams {
   float g3cx, g3cy, g3cz, g3sx, g3sy, g3sz;
   float cos_if;                              // cos i (FP32)
   const float4 *node_a, *node_b;
+  // 3-D spherical grid (rt_render_sph; sph != 0): radial index from r^2 as for the
+  // axisymmetric grid (r_log, lr_scale, lr_off, r_in2, inv_rin2), colatitude index
+  // (theta - th0) th_scale, azimuth index phi ph_scale with phi = atan2(y, x) in [0, 2 pi);
+  // node records node_a / node_b {T, n, vt, x_co} and {v_r, v_theta, v_phi, 0} in
+  // [nph][nth][nr] order; rays are clipped to the sphere of radius R_cyl (= r_out)
+  int sph, snr, snth, snph;
+  float th0, th1, th_scale, ph_scale, r_out2;
   float sin_if;             // sin i (FP32, for v_los = v_phi x sin i / r)
   float x_co, edge_k;       // edge_k = log2(e) / edge_w
   int vturb_mach;
@@ -143,7 +150,19 @@ __device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, b
   double wy = P.sin_i, wz = -P.cos_i;
   double lo = -1e300, hi = 1e300;
   bool ok = active;
-  if (P.box) {
+  if (P.sph) {
+    // chord through the sphere r <= R_cyl: |P0 + s omega|^2 = R_cyl^2 with |omega| = 1
+    const double b = P0y * wy + P0z * wz;
+    const double c = xs * xs + P0y * P0y + P0z * P0z - P.R_cyl * P.R_cyl;
+    const double disc = b * b - c;
+    if (!(disc > 0.0)) {
+      ok = false;
+    } else {
+      const double sq = sqrt(disc);
+      lo = -b - sq;
+      hi = -b + sq;
+    }
+  } else if (P.box) {
     // chord through the box, slab by slab (omega = (0, wy, wz), so x is constant)
     if (xs < P.bx0 || xs > P.bx1) ok = false;
     if (wy != 0.0) {
@@ -168,8 +187,8 @@ __device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, b
     ok = false;
   }
   double c = xs * xs + P0y * P0y - P.R_cyl * P.R_cyl;
-  if (P.box) {
-    // (the box chord is complete)
+  if (P.box || P.sph) {
+    // (the box or sphere chord is complete)
   } else if (wy != 0.0) {
     double a = wy * wy, b = 2.0 * P0y * wy;
     double disc = b * b - 4.0 * a * c;
@@ -419,11 +438,81 @@ __device__ __forceinline__ float4 sample_physics_box(const MarchParams &P, const
   return line_tail(P, tab, T, n, X, vt, vlos, R.ds);
 }
 
+// Sample physics on a 3-D spherical grid (rt_render_sph): (r, theta, phi) of the sample
+// (theta = atan2(R, z) from +z with R = sqrt(x^2 + y^2), phi = atan2(y, x) in [0, 2 pi)),
+// trilinear interpolation of the packed node records in (radial index, theta, phi), periodic
+// in phi (16 loads of 16 bytes), and v_los = omega . v + v_sys for
+// v = v_r r^ + v_theta theta^ + v_phi phi^, omega = (0, sin i, -cos i):
+//   v_y = (v_r sin th + v_theta cos th) sin ph + v_phi cos ph,  v_z = v_r cos th - v_theta sin th.
+// No gas outside r_in <= r <= r_out, th0 <= theta <= th1. On the axis theta^ and phi^ are
+// taken as 0, at the centre r^ as well.
+__device__ __forceinline__ float4 sample_physics_sph(const MarchParams &P, const float *tab,
+                                                     const Ray &R, int k) {
+  const float kf = (float)k;
+  const float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
+  const float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
+  float4 out = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+  if (!(R.hit && k < P.n_samples)) return out;
+  const float Rc2 = fmaf(R.x, R.x, y * y);
+  const float r2 = fmaf(z, z, Rc2);
+  if (!(r2 >= P.r_in2 && r2 <= P.r_out2)) return out;
+  const float iRc = Rc2 > 0.0f ? rsq(Rc2) : 0.0f;
+  const float Rc = Rc2 * iRc;
+  const float th = atan2f(Rc, z);
+  if (!(th >= P.th0 && th <= P.th1)) return out;
+  float ph = atan2f(y, R.x);
+  if (ph < 0.0f) ph += 6.283185307179586f;
+  const float ir = r2 > 0.0f ? rsq(r2) : 0.0f;  // r^ taken as 0 at the centre
+  float u = P.r_log ? lg2(r2 * P.inv_rin2) * P.lr_scale : fmaf(r2 * ir, P.lr_scale, P.lr_off);
+  u = fminf(fmaxf(u, 0.0f), (float)(P.snr - 1));
+  const int i0 = min((int)u, P.snr - 2);
+  const float fr = u - (float)i0;
+  const float v = fminf(fmaxf((th - P.th0) * P.th_scale, 0.0f), (float)(P.snth - 1));
+  const int j0 = min((int)v, P.snth - 2);
+  const float ft = v - (float)j0;
+  const float w = ph * P.ph_scale;
+  int k0 = (int)w;
+  const float fp = w - (float)k0;
+  if (k0 >= P.snph) k0 -= P.snph;  // phi rounded up to 2 pi
+  const int k1 = k0 + 1 == P.snph ? 0 : k0 + 1;
+  const long long sj = P.snr, sk0 = (long long)k0 * P.snth * P.snr,
+                  sk1 = (long long)k1 * P.snth * P.snr;
+  const long long b0 = sk0 + j0 * sj + i0, b1 = sk1 + j0 * sj + i0;
+  const long long o[8] = {b0, b0 + 1, b0 + sj, b0 + sj + 1, b1, b1 + 1, b1 + sj, b1 + sj + 1};
+  float4 a[8], vv[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    a[c] = __ldg(P.node_a + o[c]);
+    vv[c] = __ldg(P.node_b + o[c]);
+  }
+  // trilinear: along r, then theta, then phi
+  auto tri = [&](float f0, float f1, float f2, float f3, float f4, float f5, float f6, float f7) {
+    const float x0 = lerpf(f0, f1, fr), x1 = lerpf(f2, f3, fr);
+    const float x2 = lerpf(f4, f5, fr), x3 = lerpf(f6, f7, fr);
+    return lerpf(lerpf(x0, x1, ft), lerpf(x2, x3, ft), fp);
+  };
+  const float T = tri(a[0].x, a[1].x, a[2].x, a[3].x, a[4].x, a[5].x, a[6].x, a[7].x);
+  const float n = tri(a[0].y, a[1].y, a[2].y, a[3].y, a[4].y, a[5].y, a[6].y, a[7].y);
+  const float vt = tri(a[0].z, a[1].z, a[2].z, a[3].z, a[4].z, a[5].z, a[6].z, a[7].z);
+  const float X = tri(a[0].w, a[1].w, a[2].w, a[3].w, a[4].w, a[5].w, a[6].w, a[7].w);
+  if (!(X * n > 0.0f)) return out;
+  const float vr = tri(vv[0].x, vv[1].x, vv[2].x, vv[3].x, vv[4].x, vv[5].x, vv[6].x, vv[7].x);
+  const float vth = tri(vv[0].y, vv[1].y, vv[2].y, vv[3].y, vv[4].y, vv[5].y, vv[6].y, vv[7].y);
+  const float vph = tri(vv[0].z, vv[1].z, vv[2].z, vv[3].z, vv[4].z, vv[5].z, vv[6].z, vv[7].z);
+  const float sth = Rc * ir, cth = z * ir;                  // sin, cos theta
+  const float sph_ = y * iRc, cph = R.x * iRc;              // sin, cos phi (0 on the axis)
+  const float vy = fmaf(fmaf(vr, sth, vth * cth), sph_, vph * cph);
+  const float vz = fmaf(vr, cth, -vth * sth);
+  const float vlos = fmaf(P.sin_if, vy, fmaf(-P.cos_if, vz, P.vsys));
+  return line_tail(P, tab, T, n, X, vt, vlos, R.ds);
+}
+
 // Sample physics of the forward march by mode: 0 axisymmetric grid, Keplerian rotation; 1
-// axisymmetric grid with a rotation field; 2 3-D Cartesian grid.
+// axisymmetric grid with a rotation field; 2 3-D Cartesian grid; 3 3-D spherical grid.
 template <int MODE>
 __device__ __forceinline__ float4 march_physics(const MarchParams &P, const float *tab,
                                                 const Ray &R, int k) {
+  if (MODE == 3) return sample_physics_sph(P, tab, R, k);
   if (MODE == 2) return sample_physics_box(P, tab, R, k);
   return sample_physics<MODE == 1>(P, tab, R, k);
 }

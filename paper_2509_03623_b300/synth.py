@@ -99,6 +99,8 @@ class Problem:
     vphi: Optional[np.ndarray] = None
     # optional 3-D Cartesian grid (rt_render3d); when set the fields above are unused
     g3: Optional["Grid3"] = None
+    # optional 3-D spherical grid (rt_render_sph); when set the fields above are unused
+    gs: Optional["GridSph"] = None
     # provenance
     name: str = ""
     seed: int = 0
@@ -328,6 +330,115 @@ def config_box(seed: int = 0) -> Problem:
     """3-D workload: 128^3-node box (+-600 au in x, y; +-150 au in z), 256^2 px, 64 channels
     over +-6 km/s, 256 samples, i = 45 deg."""
     return box3d(seed, n3=(128, 128, 128), nx=256, ny=256, nch=64, n_samples=256)
+
+
+@dataclasses.dataclass
+class GridSph:
+    """3-D spherical node grid centred on the star: nr radial nodes log-spaced (r_log=1) or
+    linear (r_log=0) over [r_in, r_out] au, nth colatitudes (from +z) linear over [th0, th1]
+    rad, nph azimuths at 2 pi k / nph; fields [nph][nth][nr] float64 (r fastest): T [K],
+    n_h2 [cm^-3], vturb [km/s], x_co, and the velocity components vr, vth, vph [km/s]."""
+    nr: int
+    nth: int
+    nph: int
+    r_log: int
+    r_in: float
+    r_out: float
+    th0: float
+    th1: float
+    T: np.ndarray
+    n_h2: np.ndarray
+    vturb: np.ndarray
+    x_co: np.ndarray
+    vr: np.ndarray
+    vth: np.ndarray
+    vph: np.ndarray
+
+    def nodes(self):
+        if self.r_log:
+            r = self.r_in * (self.r_out / self.r_in) ** (np.arange(self.nr) / (self.nr - 1))
+        else:
+            r = np.linspace(self.r_in, self.r_out, self.nr)
+        return (r, np.linspace(self.th0, self.th1, self.nth),
+                2.0 * math.pi * np.arange(self.nph) / self.nph)
+
+
+def sphere3d(seed: int = 0, *, nsph=(128, 48, 64), r_in: float = 20.0, r_out: float = 600.0,
+             th_half: float = 0.55, nx: int = 64, ny: int = 64, nch: int = 32,
+             vmax: float = 6.0, n_samples: int = 256, incl: float = 45.0, pa: float = 0.0,
+             mstar: float = 2.0, turb: float = 0.2, spiral: float = 0.3, r_log: int = 1,
+             th_range: Optional[tuple] = None, name: str = "") -> Problem:
+    """A spherical grid (r log-spaced over [r_in, r_out] au, colatitudes within th_half rad of
+    the midplane, full azimuth) standing in for a planet-disk hydrodynamic simulation: the
+    parametric disk's temperature and density (the family of `disk` and `box3d`) at the nodes,
+    multiplied by exp(turb f(x)) with f a seeded sum of 6 Fourier modes (as in `box3d`) and
+    the density by 1 + spiral a, with a = cos(2 (phi - phi_p) + ln(R / 150 au) / tan 15 deg)
+    a two-armed logarithmic spiral of seeded phase; the CO layer of `box3d`; Keplerian
+    v_phi (1 + 0.02 a) plus seeded modes of 0.1 km/s in all three components and 0.1 a km/s
+    in v_r; v_turb = 0.05 km/s. r_log = 0 spaces the radii linearly (r_in may then be 0);
+    th_range = (th0, th1) replaces the midplane wedge."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gnr, gnth, gnph = nsph
+    th0, th1 = th_range if th_range is not None else (0.5 * math.pi - th_half,
+                                                      0.5 * math.pi + th_half)
+    rr = (r_in * (r_out / r_in) ** (np.arange(gnr) / (gnr - 1)) if r_log
+          else np.linspace(r_in, r_out, gnr))
+    ths = np.linspace(th0, th1, gnth)
+    phs = 2.0 * math.pi * np.arange(gnph) / gnph
+    PH, TH, RR = np.meshgrid(phs, ths, rr, indexing="ij")  # [nph][nth][nr]
+    Rc = RR * np.sin(TH)
+    Z = RR * np.cos(TH)
+    X = Rc * np.cos(PH)
+    Y = Rc * np.sin(PH)
+    Rs = np.maximum(Rc, 1.0)
+    sigma0 = _sigma0_from_mass(0.09, r_in, r_out)
+    T_mid = 20.0 * (Rs / 100.0) ** -0.5
+    T_atm = 60.0 * (Rs / 100.0) ** -0.5
+    z_q = 70.0 * (Rs / 150.0) ** 1.3
+    blend = np.where(np.abs(Z) < z_q, np.sin(math.pi * np.abs(Z) / (2.0 * z_q)) ** 2, 1.0)
+    T = T_mid + (T_atm - T_mid) * blend
+    m_mol = MEAN_MOL_AMU * AMU_G
+    cs = np.sqrt(K_BOLTZ * T_mid / m_mol)
+    H = cs / np.sqrt(GM_SUN * mstar / (Rs * AU_CM) ** 3)
+    sig = sigma0 * (Rs / 100.0) ** -1 * np.exp(-Rs / 300.0)
+    n = sig / (math.sqrt(2.0 * math.pi) * H) * np.exp(-(Z * AU_CM) ** 2 / (2.0 * H ** 2)) / m_mol
+
+    def modes(k):
+        f = np.zeros_like(X)
+        for _ in range(k):
+            lam = rng.uniform(100.0, 400.0)
+            d = rng.standard_normal(3)
+            d /= np.linalg.norm(d)
+            ph = rng.uniform(0.0, 2.0 * math.pi)
+            f += np.cos(2.0 * math.pi * (d[0] * X + d[1] * Y + d[2] * Z) / lam + ph)
+        return f / math.sqrt(k)
+
+    phi_p = rng.uniform(0.0, 2.0 * math.pi)
+    arm = np.cos(2.0 * (PH - phi_p) + np.log(Rs / 150.0) / math.tan(math.radians(15.0)))
+    T = T * np.exp(turb * modes(6))
+    n = n * np.exp(turb * modes(6)) * (1.0 + spiral * arm)
+    x_co = 1e-4 * np.exp(-0.5 * ((np.abs(Z) / Rs - 0.2) / 0.08) ** 2)
+    vk = np.sqrt(GM_SUN * mstar * (Rs * AU_CM) ** 2 / ((Rs * AU_CM) ** 2 + (Z * AU_CM) ** 2) ** 1.5) / 1e5
+    vph = vk * (1.0 + 0.02 * arm) + 0.1 * modes(3)
+    vr = 0.1 * arm + 0.1 * modes(3)
+    vth = 0.1 * modes(3)
+    gs = GridSph(gnr, gnth, gnph, 1 if r_log else 0, r_in, r_out, th0, th1, T, n,
+                 np.full_like(T, 0.05), x_co, vr, vth, vph)
+    z2 = np.zeros((2, 2))
+    return Problem(nr=2, nz=2, r_in_au=1.0, r_out_au=2.0, zr_max=1.0, r_log=1,
+                   T=z2 + 1.0, n_h2=z2, vturb=z2, h_lo=np.zeros(2), h_hi=np.zeros(2),
+                   incl_deg=incl, pa_deg=pa, mstar_msun=mstar, nx=nx, ny=ny,
+                   half_fov_au=1.05 * r_out, v_kms=np.linspace(-vmax, vmax, nch),
+                   n_samples=n_samples, gs=gs,
+                   name=name or f"sph{gnr}x{gnth}x{gnph}_px{nx}_ch{nch}_ns{n_samples}", seed=seed)
+
+
+def config_sph(seed: int = 0) -> Problem:
+    """Spherical-grid workload on the node count of the paper's runtime benchmark (512 x 96
+    x 256 in r, theta, phi; r 20-600 au log-spaced, theta within 0.55 rad of the midplane),
+    256^2 px, 64 channels over +-6 km/s, 512 samples, i = 47 deg, PA = 133 deg."""
+    return sphere3d(seed, nsph=(512, 96, 256), nx=256, ny=256, nch=64, n_samples=512,
+                    incl=47.0, pa=133.0)
 
 
 # --------------------------------------------------------------------------------------
