@@ -296,6 +296,34 @@ def chain_leg(dev, reps=50):
                                  "graph-replayed launches"}}
 
 
+def plain_leg(dev, flush, p, dd, fwd_value, reps=5):
+    """The plain FP32 march (rt_render_plain: one thread per pixel-channel, every sample's
+    physics per thread, accurate library functions, no window, no corner quads) on the
+    benchmark's workload; CUDA-event time per render, L2 flushed before each."""
+    import torch
+    from paper_2509_03623_b300 import _rt
+    cube = torch.empty((p.nch, p.ny, p.nx), dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        _rt.rt_render_plain(p, dd, cube, stream=st)
+    ms = []
+    for i in range(reps):
+        flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _rt.rt_render_plain(p, dd, cube, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    v = p.evals / (t * 1e-3) / 1e9
+    return {"workload": p.name, "ms": t, "value": v, "unit": "Gevals/s",
+            "forward_speedup": fwd_value / v,
+            "note": "plain FP32 march on the same GPU (the comparison arm of the metric); "
+                    "forward_speedup = this line's value / plain value"}
+
+
 def _grid3d_time(dev, flush, p, render, dg, reps):
     """Median CUDA-event time [ms] of render(p, dg, cube, stream) with L2 flushed before
     each timed call."""
@@ -583,6 +611,7 @@ def run_ours(args):
                                         "0.156 of 0.1875 clk)"}},
             "clocks": clocks,
         }
+        out["plain_fp32"] = plain_leg(dev, flush, p, dd, value / world)
         if world == 1 and not args.no_serving:
             out["field_chain"] = chain_leg(dev)
             out["box3d"] = box_leg(dev, flush)

@@ -158,6 +158,19 @@ typedef struct {
 } rt_grads;
 
 /*
+ * rt_render_plain -- the plain FP32 march that the forward's throughput is compared against:
+ * the same transfer, physics and sampling as rt_render (Keplerian rotation only), computed
+ * the straightforward way -- one thread per (pixel, channel) evaluating every sample's
+ * physics itself, fields from the node arrays, accurate FP32 library functions, no channel
+ * window, no corner quads, plain FP32 sums. Arguments and output as rt_render; its cube
+ * agrees with rt_render's within the forward parity criterion. A measurement baseline, not a
+ * production path.
+ * Returns RT_OK, RT_EINVAL (as rt_render, or a rotation field) or RT_ECUDA.
+ */
+int rt_render_plain(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                    const rt_view *view, const rt_line *line, float *cube, void *stream);
+
+/*
  * rt_render_launch_count -- number of kernel launches rt_render makes for this problem
  * (written to *count, HOST): 0 for an empty image or channel list, 2 when it packs the corner
  * quads first (from 4M samples, see rt_render), else 1. Nothing is launched. Returns RT_OK or

@@ -161,6 +161,8 @@ def lib():
             L.rt_render_sph.argtypes = [P(rt_grid_sph), P(rt_fields_sph), P(rt_geom),
                                         P(rt_view), P(rt_line), C.c_void_p, C.c_void_p]
             L.rt_render_sph.restype = C.c_int
+            L.rt_render_plain.argtypes = base + [C.c_void_p, C.c_void_p]
+            L.rt_render_plain.restype = C.c_int
             L.rt_render_launch_count.argtypes = base + [P(C.c_int)]
             L.rt_render_launch_count.restype = C.c_int
             L.rt_mlp_status.argtypes = [P(C.c_int)]
@@ -241,6 +243,20 @@ def rt_render(problem, fields=None, out=None, stream=None):
         out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=T.device)
     check(lib().rt_render(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
                           C.c_void_p(out.data_ptr()), stream_handle(stream)))
+    return out
+
+
+def rt_render_plain(problem, fields=None, out=None, stream=None):
+    """The plain FP32 comparison march (rt_render_plain); returns the cube tensor."""
+    import torch
+    dd = fields if fields is not None else DeviceDisk(problem)
+    T, n, vt, hlo, hhi = dd.tensors()
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi,
+                                       getattr(dd, "vphi", None))
+    if out is None:
+        out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=T.device)
+    check(lib().rt_render_plain(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                                C.c_void_p(out.data_ptr()), stream_handle(stream)))
     return out
 
 

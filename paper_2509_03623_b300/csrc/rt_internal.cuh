@@ -523,6 +523,7 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
 int set_error(int code, const char *fmt, ...);
 void clear_error();
 int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream);
+int launch_plain(const MarchParams &P, float *cube, cudaStream_t stream);  // rt_plain.cu
 // Stream-ordered allocation from a library-owned pool of the current device, which keeps up
 // to kPoolKeepBytes cached between calls (so repeated renders do not map and unmap their
 // scratch); free with cudaFreeAsync.

@@ -1,0 +1,43 @@
+"""The plain FP32 comparison march (rt_render_plain) vs the FP64 oracle: it is the arm the
+forward's throughput is measured against, so it must compute the same cube (same parity
+criterion as rt_render: 1e-4 relative above 1e-3 of the peak, 3e-7 of the peak below)."""
+
+import numpy as np
+import pytest
+
+from paper_2509_03623_b300 import synth
+from tests.cubecheck import assert_cube_close
+from tests.test_forward_gpu import rt  # noqa: F401  (module fixture)
+
+pytestmark = pytest.mark.gpu
+
+
+def plain_cube(rt, p):
+    import torch
+    out = rt.rt_render_plain(p)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_plain_small_full_cube(rt, orc, seed):
+    p = synth.config_small(seed)
+    assert_cube_close(plain_cube(rt, p), orc.render(p), label=f"plain small seed {seed}")
+
+
+def test_plain_observation_scale_sampled(rt, orc):
+    p = synth.config_observation(0)
+    g = plain_cube(rt, p)
+    rng = np.random.default_rng(2)
+    flux = g.sum(axis=0).ravel()
+    pix = np.unique(np.concatenate([np.argsort(flux)[::-1][:24],
+                                    rng.choice(p.nx * p.ny, 24, replace=False)]))
+    ref = orc.render_pixels(p, pix)
+    assert_cube_close(g.reshape(p.nch, -1)[:, pix].T, ref, label="plain observation scale")
+
+
+def test_plain_rejects_rotation_field(rt):
+    p = synth.config_small(0)
+    p = p.replace(vphi=np.ones_like(p.T))
+    with pytest.raises(rt.RTError):
+        rt.rt_render_plain(p)
