@@ -53,6 +53,9 @@ MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 16)
 # DRAM bytes of one forward launch on the observation-scale workload (ncu, dram__bytes_read +
 # dram__bytes_write; the cube stays in L2 at the end of the launch)
 FWD_DRAM_BYTES = 3_336_704 + 26_624
+# DRAM bytes (read + write) of one fused-adjoint launch on the same workload (ncu capture of
+# march_adj_kernel<8, 8, 1>; most of it is the per-segment sample records reaching DRAM)
+ADJ_DRAM_BYTES = 77_586_688 + 786_290_432
 N_SM = 148
 SM_MAX_MHZ = 2032.0
 
@@ -621,7 +624,7 @@ def run_ours(args):
                                 "unit": UNIT,
                                 "frac": (executed / (adj_ms * 1e-3) / 1e9)
                                         / (ADJ_EVALS_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e9),
-                                "traffic": None,
+                                "traffic": ADJ_DRAM_BYTES,
                                 "note": "executed evals / step time (memsets, march kernel, "
                                         "gradient-copy sums); peak: 24 FP32 ops per eval "
                                         "(forward 6, batch-start recompute 3, reverse 15) at 128 "
