@@ -90,3 +90,39 @@ def test_empty_image_is_a_no_op(L):
     g, f, o, vw, ln, keep = _structs(vw__nch=0)
     assert L.rt_render(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
                        None, None) == 0
+
+
+@pytest.mark.parametrize("over", [
+    dict(nr=1), dict(nth=1), dict(nph=0), dict(r_in_au=-1.0), dict(r_out_au=5.0),
+    dict(r_log=1, r_in_au=0.0), dict(th0_rad=-0.1), dict(th1_rad=4.0), dict(th1_rad=0.5),
+    dict(r_out_au=float("nan")),
+])
+def test_spherical_grid_invalid_arguments_rejected(L, over):
+    from paper_2509_03623_b300 import _rt
+    _, _, o, vw, ln, keep = _structs()
+    g = _rt.rt_grid_sph(8, 8, 8, 1, 10.0, 600.0, 1.0, 2.0)
+    for k, val in over.items():
+        setattr(g, k, val)
+    f = _rt.rt_fields_sph(16, 16, 16, 16, 16, 16, 16, 0)  # dummy device pointers
+    rc = L.rt_render_sph(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                         C.c_void_p(16), None)
+    assert rc == -1
+    assert len(L.rt_last_error()) > 0
+
+
+def test_spherical_grid_null_field_rejected(L):
+    from paper_2509_03623_b300 import _rt
+    _, _, o, vw, ln, keep = _structs()
+    g = _rt.rt_grid_sph(8, 8, 8, 1, 10.0, 600.0, 1.0, 2.0)
+    f = _rt.rt_fields_sph(16, 16, 16, 16, 16, 0, 16, 0)
+    assert L.rt_render_sph(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                           C.c_void_p(16), None) == -1
+    assert b"field" in L.rt_last_error()
+
+
+def test_plain_march_rejects_rotation_field(L):
+    g, f, o, vw, ln, keep = _structs()
+    f.vphi_kms = 16  # a rotation field: the plain march takes Keplerian rotation only
+    assert L.rt_render_plain(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                             C.c_void_p(16), None) == -1
+    assert b"Keplerian" in L.rt_last_error()
