@@ -367,11 +367,21 @@ def sph_leg(dev, flush, reps=10):
     from paper_2509_03623_b300 import _rt, synth
     p = synth.config_sph(0)
     g = p.gs
-    t = _grid3d_time(dev, flush, p, _rt.rt_render_sph, _rt.DeviceGridSph(p, dev), reps)
+    dg = _rt.DeviceGridSph(p, dev)
+    t = _grid3d_time(dev, flush, p, _rt.rt_render_sph, dg, reps)
+    # the sweeps of the paper's runtime benchmark on this grid: 256^2 px with varying channel
+    # counts, and 20 channels with varying image sizes (channels over +-6 km/s)
+    sweep = []
+    for nx, nch in [(256, 20), (256, 40), (256, 80), (256, 160), (256, 256),
+                    (64, 20), (128, 20), (512, 20)]:
+        q = p.replace(nx=nx, ny=nx, v_kms=np.linspace(-6.0, 6.0, nch))
+        tq = _grid3d_time(dev, flush, q, _rt.rt_render_sph, dg, 5)
+        sweep.append({"px": nx, "channels": nch, "ms": tq,
+                      "value": q.evals / (tq * 1e-3) / 1e9})
     return {"workload": p.name, "ms": t, "value": p.evals / (t * 1e-3) / 1e9,
-            "unit": "Gevals/s", "nodes": g.nr * g.nth * g.nph,
+            "unit": "Gevals/s", "nodes": g.nr * g.nth * g.nph, "sweep": sweep,
             "note": "nominal sample-channel evaluations / time; includes packing the 7 node "
-                    "fields into two float4 records (403 MB)"}
+                    "fields into two float4 records (403 MB); sweep: 512 samples per ray"}
 
 
 def neural_leg(dev, flush, reps=5):
