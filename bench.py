@@ -55,7 +55,7 @@ MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 16)
 FWD_DRAM_BYTES = 3_336_704 + 26_624
 # DRAM bytes (read + write) of one fused-adjoint launch on the same workload (ncu capture of
 # march_adj_kernel<8, 8, 1>; most of it is the per-segment sample records reaching DRAM)
-ADJ_DRAM_BYTES = 77_586_688 + 786_290_432
+ADJ_DRAM_BYTES = 52_802_560 + 501_973_248
 N_SM = 148
 SM_MAX_MHZ = 2032.0
 

@@ -40,7 +40,8 @@ constexpr int adj_wpb() {
 constexpr int kSeg = 64;  // samples per checkpoint segment
 
 // Per-sample record of the segment being reversed: the physics {kd, a, b, S} and the local
-// derivatives (below), five float4 per lane and batch.
+// derivatives (below), five float4 per lane and batch; without a network the fifth (J_MN, J_T,
+// J_N: the network factor on n and the modulated primitives) is neither written nor read.
 constexpr int kRec = 5;
 
 // Per-warp scratch in floats: checkpoints of each segment, then the batch starts of the
@@ -72,6 +73,8 @@ enum {
   kJ
 };
 static_assert(kJ <= 4 * (kRec - 1), "local derivatives fit the sample record");
+static_assert(J_MN == 4 * (kRec - 2) && J_T > J_MN && J_N > J_MN && J_MT < J_MN,
+              "the last record slot starts with the network-only entries");
 
 // Channel-independent physics of sample k with its local derivatives, written where the sample
 // has gas to the record slots rec[32 (i + 1)], i < kRec - 1 (entries 4i .. 4i + 3 of the enum).
@@ -154,7 +157,8 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   for (int e = kJ; e < 4 * (kRec - 1); e++) J[e] = 0.0f;
 #pragma unroll
   for (int i = 0; i < kRec - 1; i++)
-    rec[(i + 1) * 32] = make_float4(J[4 * i], J[4 * i + 1], J[4 * i + 2], J[4 * i + 3]);
+    if (i < kRec - 2 || P.mod)
+      rec[(i + 1) * 32] = make_float4(J[4 * i], J[4 * i + 1], J[4 * i + 2], J[4 * i + 3]);
   float4 out;
   out.x = P.kappa_k * (X * n) * F * ia * R.ds;
   out.z = ia * 1.2011224087864498f;  // b = sqrt(log2 e) / alpha
@@ -592,7 +596,8 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             float Jv[4 * (kRec - 1)];
 #pragma unroll
             for (int i = 0; i < kRec - 1; i++) {
-              const float4 v = rb[(i + 1) * 32];
+              const float4 v = (i < kRec - 2 || P.mod) ? rb[(i + 1) * 32]
+                                                       : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
               Jv[4 * i] = v.x;
               Jv[4 * i + 1] = v.y;
               Jv[4 * i + 2] = v.z;
