@@ -204,7 +204,7 @@ int rt_render_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *
  * `stream` (stream-ordered) holding the optical-depth checkpoints (every 64
  * samples), the reverse march's per-warp record of the 64-sample segment it is reversing
  * (recomputed from the segment's checkpoint: batch optical depths, and the physics and local
- * derivatives of each sample, 80 bytes per sample) and up to 32 replicated FP32
+ * derivatives of each sample, 64 bytes per sample, 80 with a network) and up to 32 replicated FP32
  * copies of the node gradients (at most 32 MiB, {dT, dn, dvt} interleaved per node) plus up
  * to 128 of the surface gradients: each block of the kernel reduces into one copy, and the
  * copies are summed in FP64, in a fixed order, into the outputs at the end. Atomics on one
