@@ -287,6 +287,25 @@ int rt_field_chain(const rt_grid *grid, const rt_geom *geom, const rt_line *line
                    float *h_lo, float *h_hi, void *stream);
 
 /*
+ * rt_field_chain_adjoint -- reverse mode of rt_field_chain for a scalar loss L (the paper
+ * trains its neural temperature through these fields, "Neural Temperature Recovery"): from
+ *   g_n  = dL/dn_h2, DEVICE [nz][nr] float64 (e.g. rt_render_adjoint's grads->dn),
+ *   g_lo = dL/dh_lo, g_hi = dL/dh_hi, DEVICE [nr] float64 (grads->dh_lo, grads->dh_hi),
+ * any of them NULL for zero, writes g_T = dL/dT_K through this chain, DEVICE [nz][nr] float64,
+ * caller-allocated, overwritten: through the hydrostatic integration and its normalisation
+ * (n_h2), the column N_h2 (h_hi) and the freeze-out crossing (h_lo). A surface depends on the
+ * two nodes of the cell where its threshold is crossed, through the linear interpolation in
+ * that cell (which cell is piecewise constant in T); a surface pinned at 0 or zr_max has zero
+ * derivative. The gradient of a render of the chain's fields with respect to T is g_T plus
+ * the render adjoint's own grads->dT. Arguments grid, geom, line, chain and T_K as for
+ * rt_field_chain. FP64, one thread per radius column (the forward quantities are recomputed).
+ * Returns RT_OK, RT_EINVAL (as rt_field_chain, or a null g_T) or RT_ECUDA.
+ */
+int rt_field_chain_adjoint(const rt_grid *grid, const rt_geom *geom, const rt_line *line,
+                           const rt_chain *chain, const float *T_K, const double *g_n,
+                           const double *g_lo, const double *g_hi, double *g_T, void *stream);
+
+/*
  * rt_render3d -- forward march through a general 3-D Cartesian grid (the RadJAX setting
  * beyond the axisymmetric disk: Methods, "Line Radiative Transfer with RadJAX", and the
  * 3-D grids of its runtime benchmark): the same transfer (Eq. rt-int / Eq. optical_depth),

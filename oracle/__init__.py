@@ -117,6 +117,7 @@ def _load():
                                                    dp, dp, dp, C.c_int]
             lib.orc_field_chain.argtypes = [pp, C.POINTER(_Chain), dp, dp, dp, dp, dp]
             lib.orc_pressure_vphi.argtypes = [pp, dp, dp, dp]
+            lib.orc_field_chain_adjoint.argtypes = [pp, C.POINTER(_Chain), dp, dp, dp, dp, dp]
             _lib = lib
     return _lib
 
@@ -377,6 +378,33 @@ def field_chain(p, chain, T=None):
     if rc != 0:
         raise ValueError("orc_field_chain: invalid arguments")
     return dict(n_h2=n, N_h2=N, h_lo=lo, h_hi=hi)
+
+
+def field_chain_adjoint(p, chain, T=None, g_n=None, g_lo=None, g_hi=None):
+    """Reverse mode of field_chain (rt_oracle.h, orc_field_chain_adjoint): dL/dT [nz][nr]
+    from dL/dn_h2 [nz][nr] and dL/dh_lo, dL/dh_hi [nr] (None: zero)."""
+    lib = _load()
+    q = p if T is None else p.replace(T=np.asarray(T, dtype=np.float64))
+    pk = _Packed(q)
+    Tg = np.ascontiguousarray(np.asarray(q.T, dtype=np.float64))
+    c = _Chain(float(chain.sigma0_gcm2), float(chain.r_c_au), float(chain.gamma),
+               float(chain.T_freeze), float(chain.N_dissoc_cm2))
+    keep = []
+
+    def opt(a, shape):
+        if a is None:
+            return C.POINTER(C.c_double)()
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shape))
+        keep.append(a)
+        return _dptr(a)
+
+    gT = np.zeros((q.nz, q.nr))
+    rc = lib.orc_field_chain_adjoint(C.byref(pk.s), C.byref(c), _dptr(Tg),
+                                     opt(g_n, (q.nz, q.nr)), opt(g_lo, (q.nr,)),
+                                     opt(g_hi, (q.nr,)), _dptr(gT))
+    if rc != 0:
+        raise ValueError("orc_field_chain_adjoint: invalid arguments")
+    return gT
 
 
 def pressure_vphi(p, n_h2=None, T=None):

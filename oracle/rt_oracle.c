@@ -1050,6 +1050,108 @@ int orc_field_chain(const orc_problem *p, const orc_chain *c, const double *T, d
   return 0;
 }
 
+/* Reverse mode of orc_field_chain (see rt_oracle.h): per column, the forward quantities
+   again, then their adjoints in the reverse order of the forward steps. */
+int orc_field_chain_adjoint(const orc_problem *p, const orc_chain *c, const double *T,
+                            const double *g_n, const double *g_lo, const double *g_hi,
+                            double *g_T) {
+  if (!p || !c || !T || !g_T || p->nr < 2 || p->nz < 2) return -1;
+  const int nr = p->nr, nz = p->nz;
+  const double GM = GM_SUN * p->mstar_msun;
+  const double m_mol = p->m_mol_amu * AMU_G;
+  double *buf = (double *)malloc(sizeof(double) * 8 * nz);
+  if (!buf) return -1;
+  double *z = buf, *grav = buf + nz, *e = buf + 2 * nz, *n = buf + 3 * nz, *N = buf + 4 * nz;
+  double *gN = buf + 5 * nz, *gn = buf + 6 * nz, *gI = buf + 7 * nz;
+  for (int i = 0; i < nr; i++) {
+    const double r_au = p->r_log ? p->r_in_au * pow(p->r_out_au / p->r_in_au, (double)i / (nr - 1))
+                                 : p->r_in_au + (p->r_out_au - p->r_in_au) * i / (nr - 1);
+    const double r = r_au * AU_CM;
+    const double *Tc = T + i; /* T of node j: Tc[j * nr] */
+    /* forward: gravity term, its trapezoid integral I, rho up to the normalisation (e),
+       the normalisation S, n and the column N */
+    double I = 0.0;
+    for (int j = 0; j < nz; j++) {
+      z[j] = p->zr_max * j / (nz - 1) * r;
+      grav[j] = GM * z[j] / pow(r * r + z[j] * z[j], 1.5) * m_mol / (K_BOLTZ * Tc[(long long)j * nr]);
+      if (j > 0) I += 0.5 * (z[j] - z[j - 1]) * (grav[j - 1] + grav[j]);
+      e[j] = exp(-I - log(Tc[(long long)j * nr] / Tc[0]));
+    }
+    const double x = r_au / c->r_c_au;
+    const double sigma = c->sigma0_gcm2 * pow(x, -c->gamma) * exp(-pow(x, 2.0 - c->gamma));
+    double S = 0.0;
+    for (int j = 1; j < nz; j++) S += 0.5 * (z[j] - z[j - 1]) * (e[j - 1] + e[j]);
+    const double Cn = sigma / (2.0 * S) / m_mol; /* n_j = Cn e_j */
+    for (int j = 0; j < nz; j++) n[j] = Cn * e[j];
+    N[nz - 1] = 0.0;
+    for (int j = nz - 2; j >= 0; j--) N[j] = N[j + 1] + 0.5 * (z[j + 1] - z[j]) * (n[j] + n[j + 1]);
+    for (int j = 0; j < nz; j++) {
+      g_T[(long long)j * nr + i] = 0.0;
+      gN[j] = 0.0;
+      gn[j] = g_n ? g_n[(long long)j * nr + i] : 0.0;
+    }
+    const double dw = p->zr_max / (nz - 1);
+    /* h_hi = dw (j + (Na - Nd) / (Na - Nb)) in the highest cell [j, j+1] with 0.706 N_j > Nd */
+    if (g_hi && g_hi[i] != 0.0) {
+      for (int j = nz - 2; j >= 0; j--) {
+        if (0.706 * N[j] > c->N_dissoc_cm2) {
+          const double Na = 0.706 * N[j], Nb = 0.706 * N[j + 1], Nd = c->N_dissoc_cm2;
+          const double q = (Na - Nb) * (Na - Nb);
+          gN[j] += g_hi[i] * dw * (Nd - Nb) / q * 0.706;
+          gN[j + 1] += g_hi[i] * dw * (Na - Nd) / q * 0.706;
+          break;
+        }
+      }
+    }
+    /* N_j = sum_{k >= j} (dz/2)(n_k + n_{k+1}): dL/dn_k from every N_j with j <= k */
+    double P = 0.0; /* sum_{j <= k} gN_j */
+    for (int k = 0; k < nz; k++) {
+      const double Pprev = P;
+      P += gN[k];
+      if (k <= nz - 2) gn[k] += 0.5 * (z[k + 1] - z[k]) * P;
+      if (k >= 1) gn[k] += 0.5 * (z[k] - z[k - 1]) * Pprev;
+    }
+    /* n_j = Cn e_j, Cn = sigma / (2 S m): dL/de_k = Cn gn_k - (Cn / S) w_k sum_j gn_j e_j,
+       w_k the trapezoid weight of node k in S */
+    double ge_dot = 0.0;
+    for (int j = 0; j < nz; j++) ge_dot += gn[j] * e[j];
+    double gT0 = 0.0;
+    for (int k = 0; k < nz; k++) {
+      const double wk = (k > 0 ? 0.5 * (z[k] - z[k - 1]) : 0.0) + (k < nz - 1 ? 0.5 * (z[k + 1] - z[k]) : 0.0);
+      const double ge = Cn * gn[k] - Cn / S * wk * ge_dot;
+      /* e_k = exp(lnrho_k), lnrho_k = -I_k - ln T_k + ln T_0 */
+      const double glr = ge * e[k];
+      gI[k] = -glr;
+      g_T[(long long)k * nr + i] += -glr / Tc[(long long)k * nr];
+      gT0 += glr / Tc[0];
+    }
+    g_T[i] += gT0;
+    /* I_j = sum_{m=1}^{j} (dz_m / 2)(grav_{m-1} + grav_m); grav_m = a_m / T_m */
+    double Q = 0.0; /* sum_{j >= m + 1} gI_j, accumulated from the top */
+    for (int m = nz - 1; m >= 0; m--) {
+      double gg = 0.0;
+      if (m + 1 <= nz - 1) gg += 0.5 * (z[m + 1] - z[m]) * Q;        /* as grav_{(m+1)-1} */
+      if (m >= 1) gg += 0.5 * (z[m] - z[m - 1]) * (Q + gI[m]);      /* as grav_m, j >= m */
+      Q += gI[m];
+      g_T[(long long)m * nr + i] += -gg * grav[m] / Tc[(long long)m * nr];
+    }
+    /* h_lo = dw ((j - 1) + (Tf - Ta) / (Tb - Ta)) in the lowest cell [j-1, j] with Tb > Tf */
+    if (g_lo && g_lo[i] != 0.0 && !(Tc[0] > c->T_freeze)) {
+      for (int j = 1; j < nz; j++) {
+        const double Ta = Tc[(long long)(j - 1) * nr], Tb = Tc[(long long)j * nr];
+        if (Tb > c->T_freeze) {
+          const double q = (Tb - Ta) * (Tb - Ta), Tf = c->T_freeze;
+          g_T[(long long)(j - 1) * nr + i] += g_lo[i] * dw * (Tf - Tb) / q;
+          g_T[(long long)j * nr + i] += -g_lo[i] * dw * (Tf - Ta) / q;
+          break;
+        }
+      }
+    }
+  }
+  free(buf);
+  return 0;
+}
+
 /* ------------------------------------------------------------------------------------------
  * Pressure-corrected rotation (see rt_oracle.h), node by node.
  * ------------------------------------------------------------------------------------------ */

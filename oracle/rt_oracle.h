@@ -168,6 +168,16 @@ typedef struct {
 int orc_field_chain(const orc_problem *p, const orc_chain *c, const double *T, double *n_h2,
                     double *N_h2, double *h_lo, double *h_hi);
 
+/* Reverse mode of orc_field_chain for a scalar loss L: from dL/dn_h2 [nz][nr] and dL/dh_lo,
+   dL/dh_hi [nr] (any of them NULL: zero) writes dL/dT [nz][nr] (overwritten), through the
+   hydrostatic integration and its normalisation (n_H2), the column N_H2 (h_hi) and the
+   freeze-out crossing (h_lo). A surface depends on the two nodes of the cell where its
+   threshold is crossed, through the linear interpolation inside that cell (the choice of the
+   cell is piecewise constant in T); a surface pinned at 0 or zr_max has zero derivative. */
+int orc_field_chain_adjoint(const orc_problem *p, const orc_chain *c, const double *T,
+                            const double *g_n, const double *g_lo, const double *g_hi,
+                            double *g_T);
+
 /* Pressure-corrected rotation on the nodes (Eq. gas_velocity_pressure):
      v_phi^2 = G M r^2 / (r^2 + z^2)^{3/2} + (r / rho) dP/dr |_z,  P = n_H2 k T,  rho = m_mol n_H2,
    with dP/dr at constant z from the grid coordinates (u = ln r or r, w = z/r):

@@ -152,6 +152,11 @@ def lib():
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p]
             L.rt_field_chain.restype = C.c_int
+            L.rt_field_chain_adjoint.argtypes = [P(rt_grid), P(rt_geom), P(rt_line),
+                                                 P(rt_chain), C.c_void_p, C.c_void_p,
+                                                 C.c_void_p, C.c_void_p, C.c_void_p,
+                                                 C.c_void_p]
+            L.rt_field_chain_adjoint.restype = C.c_int
             L.rt_pressure_vphi.argtypes = [P(rt_grid), P(rt_geom), P(rt_line), C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p]
             L.rt_pressure_vphi.restype = C.c_int
@@ -408,6 +413,36 @@ def rt_field_chain(problem, T, chain, column=True, stream=None, out=None):
                                _ptr(n), _ptr(N) if N is not None else None, _ptr(lo), _ptr(hi),
                                stream_handle(stream)))
     return dict(n_h2=n, N_h2=N, h_lo=lo, h_hi=hi)
+
+
+def rt_field_chain_adjoint(problem, T, chain, g_n=None, g_lo=None, g_hi=None, out=None,
+                           stream=None):
+    """Reverse mode of rt_field_chain: dL/dT (CUDA float64 [nz][nr], written into `out` when
+    given) from dL/dn_h2 (float64 [nz][nr]) and dL/dh_lo, dL/dh_hi (float64 [nr]); None for
+    zero."""
+    import torch
+    shp = (int(problem.nz), int(problem.nr))
+    if not T.is_cuda or T.dtype != torch.float32 or not T.is_contiguous() or tuple(T.shape) != shp:
+        raise ValueError(f"T must be a contiguous CUDA float32 tensor of shape {shp}")
+    for name, t, sh in (("g_n", g_n, shp), ("g_lo", g_lo, shp[1:]), ("g_hi", g_hi, shp[1:])):
+        if t is not None and (not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous()
+                              or tuple(t.shape) != sh):
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of shape {sh}")
+    g = rt_grid(int(problem.nr), int(problem.nz), int(problem.r_log), float(problem.r_in_au),
+                float(problem.r_out_au), float(problem.zr_max))
+    o = rt_geom(float(problem.incl_deg), float(problem.pa_deg), float(problem.dist_pc),
+                float(problem.mstar_msun), float(problem.vsys_kms))
+    ln = rt_line(float(problem.nu0_hz), float(problem.A_ul), float(problem.B_rot_hz),
+                 float(problem.m_co_amu), float(problem.m_mol_amu), int(problem.J_u))
+    c = rt_chain(float(chain.sigma0_gcm2), float(chain.r_c_au), float(chain.gamma),
+                 float(chain.T_freeze), float(chain.N_dissoc_cm2))
+    if out is None:
+        out = torch.empty(shp, dtype=torch.float64, device=T.device)
+    opt = lambda t: _ptr(t) if t is not None else None
+    check(lib().rt_field_chain_adjoint(C.byref(g), C.byref(o), C.byref(ln), C.byref(c), _ptr(T),
+                                       opt(g_n), opt(g_lo), opt(g_hi), _ptr(out),
+                                       stream_handle(stream)))
+    return out
 
 
 def rt_pressure_vphi(problem, n_h2, T, out=None, stream=None):

@@ -608,6 +608,39 @@ extern "C" int rt_pressure_vphi(const rt_grid *grid, const rt_geom *geom, const 
   return rc;
 }
 
+static int check_chain_args(const rt_grid *grid, const rt_geom *geom, const rt_line *line,
+                            const rt_chain *chain) {
+  if (grid->nr < 2 || grid->nz < 2) return set_error(RT_EINVAL, "grid needs >= 2 nodes per axis");
+  if (!(grid->r_in_au > 0) || !(grid->r_out_au > grid->r_in_au) || !(grid->zr_max > 0) ||
+      !is_finite(grid->r_out_au) || !is_finite(grid->zr_max))
+    return set_error(RT_EINVAL, "invalid grid extent");
+  if (!(geom->mstar_msun >= 0) || !is_finite(geom->mstar_msun))
+    return set_error(RT_EINVAL, "stellar mass must be finite and >= 0");
+  if (!(line->m_mol_amu > 0) || !is_finite(line->m_mol_amu))
+    return set_error(RT_EINVAL, "mean molecular mass must be > 0");
+  if (!(chain->sigma0_gcm2 >= 0) || !is_finite(chain->sigma0_gcm2) || !(chain->r_c_au > 0) ||
+      !is_finite(chain->r_c_au) || !(chain->gamma < 2) || !is_finite(chain->gamma) ||
+      !is_finite(chain->T_freeze_K) || !(chain->N_dissoc_cm2 >= 0) ||
+      !is_finite(chain->N_dissoc_cm2))
+    return set_error(RT_EINVAL, "invalid chain parameters");
+  return RT_OK;
+}
+
+extern "C" int rt_field_chain_adjoint(const rt_grid *grid, const rt_geom *geom,
+                                      const rt_line *line, const rt_chain *chain,
+                                      const float *T_K, const double *g_n,
+                                      const double *g_lo, const double *g_hi, double *g_T,
+                                      void *stream) {
+  if (!grid || !geom || !line || !chain || !T_K || !g_T)
+    return set_error(RT_EINVAL, "null argument");
+  int rc = check_chain_args(grid, geom, line, chain);
+  if (rc != RT_OK) return rc;
+  rc = launch_field_chain_adjoint(*grid, *geom, *line, *chain, T_K, g_n, g_lo, g_hi, g_T,
+                                  (cudaStream_t)stream);
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
 extern "C" int rt_field_chain(const rt_grid *grid, const rt_geom *geom, const rt_line *line,
                               const rt_chain *chain, const float *T_K, float *n_h2,
                               float *N_h2, float *h_lo, float *h_hi, void *stream) {

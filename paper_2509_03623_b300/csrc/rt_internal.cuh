@@ -535,6 +535,10 @@ int launch_pressure_vphi(const rt_grid &g, const rt_geom &geo, const rt_line &li
 int launch_field_chain(const rt_grid &g, const rt_geom &geo, const rt_line &line,
                        const rt_chain &c, const float *T, float *n, float *N, float *h_lo,
                        float *h_hi, cudaStream_t stream);
+int launch_field_chain_adjoint(const rt_grid &g, const rt_geom &geo, const rt_line &line,
+                               const rt_chain &c, const float *T, const double *g_n,
+                               const double *g_lo, const double *g_hi, double *g_T,
+                               cudaStream_t stream);
 int pack_cells(MarchParams &P, void *buf, cudaStream_t stream);
 int launch_count(const MarchParams &P, unsigned long long *count, cudaStream_t stream);
 void lane_layout(int nch, int *lpr, int *cpl);

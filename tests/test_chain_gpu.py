@@ -110,3 +110,79 @@ def test_chain_then_render_matches_oracle_chain_then_render(rt, orc):
     ref = orc.field_chain(p, c, T32.astype(np.float64))
     q = p.replace(T=T32.astype(np.float64), n_h2=ref["n_h2"], h_lo=ref["h_lo"], h_hi=ref["h_hi"])
     assert_cube_close(cube, orc.render(q), label="chain + render")
+
+
+def adjoint_both(rt, orc, p, T, chain, gn, glo, ghi):
+    import torch
+    T32 = np.ascontiguousarray(T, dtype=np.float32)
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda") \
+        if a is not None else None
+    got = rt.rt_field_chain_adjoint(p, torch.tensor(T32, device="cuda"), chain, dev(gn),
+                                    dev(glo), dev(ghi))
+    torch.cuda.synchronize()
+    ref = orc.field_chain_adjoint(p, chain, T32.astype(np.float64), gn, glo, ghi)
+    return got.cpu().numpy(), ref
+
+
+@pytest.mark.parametrize("which", ["all", "n", "lo", "hi"])
+def test_chain_adjoint_matches_oracle(rt, orc, which):
+    """FP64 on both sides from the same float32 temperatures: agreement to ~1e-10 of the
+    largest entry (different exp/log/pow implementations, same summation order)."""
+    from tests.test_oracle_chain_adjoint import chain_problem
+    p, rng = chain_problem(nr=37, nz=61, seed=7)
+    c = synth.chain_params(p)
+    nscale = orc.field_chain(p, c, p.T)["n_h2"].max()
+    gn = rng.standard_normal((p.nz, p.nr)) / nscale if which in ("all", "n") else None
+    glo = rng.standard_normal(p.nr) if which in ("all", "lo") else None
+    ghi = rng.standard_normal(p.nr) if which in ("all", "hi") else None
+    got, ref = adjoint_both(rt, orc, p, p.T, c, gn, glo, ghi)
+    scale = np.abs(ref).max()
+    assert scale > 0
+    np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-10 * scale)
+
+
+def test_chain_adjoint_observation_grid(rt, orc):
+    """The 512 x 256 grid of the observation-scale workload (log radii, T over the whole
+    freeze-out range)."""
+    p = synth.config_observation(0)
+    rng = np.random.default_rng(11)
+    c = synth.chain_params(p)
+    nscale = orc.field_chain(p, c, p.T)["n_h2"].max()
+    got, ref = adjoint_both(rt, orc, p, p.T, c, rng.standard_normal((p.nz, p.nr)) / nscale,
+                            rng.standard_normal(p.nr), rng.standard_normal(p.nr))
+    np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-10 * np.abs(ref).max())
+
+
+def test_render_gradient_through_the_chain(rt, orc):
+    """dL/dT of L = sum g * render(chain(T)) on the GPU (rt_field_chain, rt_render_adjoint,
+    rt_field_chain_adjoint, plus the render's own dT) vs the oracle's composition of the same
+    steps; the adjoint criterion of the render (3e-4 of the largest entry, 3e-3 relative
+    above 1 % of it)."""
+    import torch
+    from tests.test_oracle_chain_adjoint import chain_problem
+    p, rng = chain_problem(nr=48, nz=24, seed=9)
+    p = p.replace(nx=24, ny=24, v_kms=np.linspace(-3.0, 3.0, 16), n_samples=96,
+                  half_fov_au=330.0, vturb=np.full((24, 48), 0.05))
+    c = synth.chain_params(p)
+    T32 = np.ascontiguousarray(p.T, dtype=np.float32)
+    Td = torch.tensor(T32, device="cuda")
+    out = rt.rt_field_chain(p, Td, c, column=False)
+    dd = rt.DeviceDisk(p)
+    dd.T = Td
+    dd.n_h2, dd.h_lo, dd.h_hi = out["n_h2"], out["h_lo"], out["h_hi"]
+    cube = rt.rt_render(p, dd)
+    g = rng.standard_normal(tuple(cube.shape)) / float(cube.abs().max())
+    gd = torch.tensor(g.astype(np.float32), device="cuda")
+    _, gr = rt.rt_render_adjoint(p, dd, dL_dcube=gd, cube_out=None)
+    gT = gr["T"] + rt.rt_field_chain_adjoint(p, Td, c, gr["n_h2"], gr["h_lo"], gr["h_hi"])
+    gT = gT.cpu().numpy()
+    ref_f = orc.field_chain(p, c, T32.astype(np.float64))
+    q = p.replace(T=T32.astype(np.float64), n_h2=ref_f["n_h2"], h_lo=ref_f["h_lo"],
+                  h_hi=ref_f["h_hi"])
+    _, rg = orc.render_adjoint(q, g.astype(np.float32).astype(np.float64))
+    ref = rg["T"] + orc.field_chain_adjoint(p, c, T32.astype(np.float64), rg["n_h2"],
+                                            rg["h_lo"], rg["h_hi"])
+    scale = np.abs(ref).max()
+    assert np.abs(gT - ref).max() <= 3e-4 * scale
+    big = np.abs(ref) >= 0.01 * scale
+    assert (np.abs(gT - ref)[big] / np.abs(ref)[big]).max() <= 3e-3
