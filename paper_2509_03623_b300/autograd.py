@@ -1,8 +1,13 @@
-"""Differentiable rendering: a torch.autograd.Function over the C ABI.
+"""Differentiable rendering: torch.autograd.Functions over the C ABI.
 
-forward  -> rt_render (FP32 march)
-backward -> rt_render_adjoint seeded with the incoming cube gradient (fused reverse march,
-            FP64 gradient accumulation, cast to the dtype of the inputs)
+RenderFn: forward  -> rt_render (FP32 march)
+          backward -> rt_render_adjoint seeded with the incoming cube gradient (fused reverse
+                      march, FP64 gradient accumulation, cast to the dtype of the inputs)
+FieldChainFn: forward  -> rt_field_chain (T -> n_H2, h_lo, h_hi)
+              backward -> rt_field_chain_adjoint
+so that with n, h_lo, h_hi = field_chain(problem, chain, T) and
+cube = render(problem, T, n, vt, h_lo, h_hi) a loss differentiates with respect to T through
+both the march and the chain.
 """
 
 from __future__ import annotations
@@ -42,3 +47,28 @@ class RenderFn(torch.autograd.Function):
 def render(problem, T, n, vt, hlo, hhi):
     """Differentiable forward render (CUDA tensors, float32 fields)."""
     return RenderFn.apply(T, n, vt, hlo, hhi, problem)
+
+
+class FieldChainFn(torch.autograd.Function):
+    """(n_H2, h_lo, h_hi) = chain(T) for a fixed grid and chain parameters."""
+
+    @staticmethod
+    def forward(ctx, T, problem, chain):
+        Tf = T.detach().contiguous().float()
+        ctx.save_for_backward(Tf)
+        ctx.problem, ctx.chain, ctx.dtype = problem, chain, T.dtype
+        out = _rt.rt_field_chain(problem, Tf, chain, column=False)
+        return out["n_h2"], out["h_lo"], out["h_hi"]
+
+    @staticmethod
+    def backward(ctx, g_n, g_lo, g_hi):
+        (Tf,) = ctx.saved_tensors
+        as64 = lambda g: g.contiguous().double() if g is not None else None
+        gT = _rt.rt_field_chain_adjoint(ctx.problem, Tf, ctx.chain, as64(g_n), as64(g_lo),
+                                        as64(g_hi))
+        return gT.to(ctx.dtype), None, None
+
+
+def field_chain(problem, chain, T):
+    """Differentiable field chain: (n_H2, h_lo, h_hi) from the temperature grid T (CUDA)."""
+    return FieldChainFn.apply(T, problem, chain)

@@ -234,7 +234,7 @@ int launch_pressure_vphi(const rt_grid &g, const rt_geom &geo, const rt_line &li
 }
 
 // Reverse mode of the chain for a scalar loss: dL/dT per node from dL/dn_H2 and dL/d(surfaces),
-// one thread per radius column in FP64 (the forward quantities are recomputed). With
+// one thread per radius column (the forward quantities are recomputed). With
 // e_j = exp(-I_j - ln(T_j / T_0)), S = sum_j w_j e_j (trapezoid weights w_j), n_j = Cn e_j,
 // Cn = Sigma / (2 S m_mol), and the column N_j = sum_{k >= j} (dz / 2)(n_k + n_{k+1}):
 //   h_hi = dw (j* + (N_a - N_d) / (N_a - N_b)) -> dL/dN at the two nodes of its cell;
@@ -244,101 +244,135 @@ int launch_pressure_vphi(const rt_grid &g, const rt_geom &geo, const rt_line &li
 //   I_j = sum_{m=1}^{j} (dz / 2)(g_{m-1} + g_m), g_m = a_m / T_m -> dL/dg_m from suffix sums
 //     of dL/dI, dL/dT_m += -dL/dg_m g_m / T_m;
 //   h_lo = dw ((j - 1) + (T_f - T_a) / (T_b - T_a)) -> the two nodes of its cell.
-// Pass 1 stores e_j in g_T (overwritten by pass 4), pass 2 finds the h_hi cell, pass 3 forms
-// sum_j dL/dn_j e_j, pass 4 walks down with the suffix sum of dL/dI and writes dL/dT.
+// Pass 1 stores e_j in a float scratch column, pass 2 finds the h_hi cell, pass 3 forms
+// dL/dn_j (kept in a second scratch column) and sum_j dL/dn_j e_j, pass 4 walks down with the
+// suffix sum of dL/dI and writes dL/dT (the FP64 inputs and output are converted once each:
+// conversions run on the FP64 pipe).
+// FP32 arithmetic (B300's FP64 rate is a small fraction of its FP32 rate; a first FP64
+// version took 3.7 ms on the 512 x 256 grid) with compensated running sums for I, S, the
+// column, the dot product and the suffix sum, and heights in units of the node spacing.
 struct ChainAdjDev {
   int nr, nz, r_log;
-  double r_in, r_out, zr_max, sigma0, r_c, gamma;
-  double GMm_k;  // G M m_mol / k [K cm]
-  double m_mol, T_freeze, N_dissoc;
+  float r_in, r_out, zr_max;
+  float sigma0, r_c, gamma;
+  float A;         // G M m_mol / (k au) [K au]: gravity term per au of height, times 1/T
+  float m_mol_g;   // mean molecular mass [g]
+  float T_freeze, N_dissoc;
+};
+
+// Compensated (Kahan-Babuska) running sum.
+struct KSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ float value() const { return s + c; }
 };
 
 __global__ void field_chain_adjoint_kernel(const ChainAdjDev C, const float *__restrict__ T,
                                            const double *__restrict__ g_n,
                                            const double *__restrict__ g_lo,
-                                           const double *__restrict__ g_hi, double *g_T) {
+                                           const double *__restrict__ g_hi, double *g_T,
+                                           float *__restrict__ ev, float *__restrict__ gnv) {
   const int nr = C.nr, nz = C.nz;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
-    const double t = (double)i / (nr - 1);
-    const double r_au = C.r_log ? C.r_in * pow(C.r_out / C.r_in, t) : C.r_in + (C.r_out - C.r_in) * t;
-    const double r = r_au * kChainAu;
-    auto zj = [&](int j) { return C.zr_max * j / (nz - 1) * r; };
-    auto Tj = [&](int j) { return (double)T[(long long)j * nr + i]; };
+    const float t = (float)i / (float)(nr - 1);
+    const float r_au = C.r_log ? C.r_in * powf(C.r_out / C.r_in, t) : C.r_in + (C.r_out - C.r_in) * t;
+    const float dz_au = C.zr_max / (float)(nz - 1) * r_au;  // node spacing [au]
+    const float dz_cm = dz_au * (float)kChainAu;
+    auto Tj = [&](int j) { return T[(long long)j * nr + i]; };
+    // gravity term g_j = A z / (r^2 + z^2)^{3/2} / T_j per au of height (z = j dz)
     auto grav = [&](int j) {
-      const double z = zj(j), d2 = r * r + z * z;
-      return C.GMm_k * z / (d2 * sqrt(d2)) / Tj(j);
+      const float z = dz_au * (float)j, d2 = r_au * r_au + z * z;
+      return C.A * z / (d2 * sqrtf(d2)) / Tj(j);
     };
     double *gT = g_T + i;  // node j: gT[j * nr]
-    const double T0 = Tj(0);
-    // pass 1: e_j and S
-    double I = 0.0, S = 0.0, gprev = 0.0, eprev = 0.0;
+    float *ec = ev + i, *gc = gnv + i;  // scratch columns, node j at [j * nr]
+    const float T0 = Tj(0);
+    // pass 1: e_j (stored) and S / dz
+    KSum I, S;
+    float gprev = 0.0f, eprev = 0.0f;
+    #pragma unroll 8
     for (int j = 0; j < nz; j++) {
-      const double g = grav(j);
-      if (j > 0) I += 0.5 * (zj(j) - zj(j - 1)) * (gprev + g);
-      const double e = exp(-I - log(Tj(j) / T0));
-      if (j > 0) S += 0.5 * (zj(j) - zj(j - 1)) * (eprev + e);
-      gT[(long long)j * nr] = e;
+      const float g = grav(j);
+      if (j > 0) I.add(0.5f * dz_au * (gprev + g));
+      const float e = expf(-I.value() - logf(Tj(j) / T0));
+      if (j > 0) S.add(0.5f * (eprev + e));
+      ec[(long long)j * nr] = e;
       gprev = g;
       eprev = e;
     }
-    const double x = r_au / C.r_c;
-    const double sigma = C.sigma0 * pow(x, -C.gamma) * exp(-pow(x, 2.0 - C.gamma));
-    const double Cn = sigma / (2.0 * S) / C.m_mol;
-    const double dw = C.zr_max / (nz - 1);
+    const float x = r_au / C.r_c;
+    const float sigma = C.sigma0 * powf(x, -C.gamma) * expf(-powf(x, 2.0f - C.gamma));
+    const float Sdz = S.value();                              // S / dz_cm
+    const float Cn = sigma / (2.0f * Sdz * dz_cm) / C.m_mol_g;  // n_j = Cn e_j
+    const float dw = C.zr_max / (float)(nz - 1);
     // pass 2: the h_hi cell (highest j with 0.706 N_j > N_d) and dL/dN at its two nodes
     int js = nz;  // no cell
-    double gNa = 0.0, gNb = 0.0;
-    const double ghi = g_hi ? g_hi[i] : 0.0;
-    if (ghi != 0.0) {
-      double N = 0.0;
+    float gNa = 0.0f, gNb = 0.0f;
+    const float ghi = g_hi ? (float)g_hi[i] : 0.0f;
+    if (ghi != 0.0f) {
+      KSum N;
       for (int j = nz - 2; j >= 0; j--) {
-        const double Nnext = N;
-        N += 0.5 * (zj(j + 1) - zj(j)) * Cn * (gT[(long long)j * nr] + gT[(long long)(j + 1) * nr]);
-        if (0.706 * N > C.N_dissoc) {
-          const double Na = 0.706 * N, Nb = 0.706 * Nnext, q = (Na - Nb) * (Na - Nb);
-          gNa = ghi * dw * (C.N_dissoc - Nb) / q * 0.706;
-          gNb = ghi * dw * (Na - C.N_dissoc) / q * 0.706;
+        const float Nnext = N.value();
+        N.add(0.5f * dz_cm * Cn * (ec[(long long)j * nr] + ec[(long long)(j + 1) * nr]));
+        const float Nj = N.value();
+        if (0.706f * Nj > C.N_dissoc) {
+          // (Na - Nb)^2 would overflow FP32 at column densities ~1e21: divide twice
+          const float Na = 0.706f * Nj, Nb = 0.706f * Nnext, dN = Na - Nb;
+          gNa = ghi * dw * ((C.N_dissoc - Nb) / dN) / dN * 0.706f;
+          gNb = ghi * dw * ((Na - C.N_dissoc) / dN) / dN * 0.706f;
           js = j;
           break;
         }
       }
     }
     // dL/dn_k: the caller's part plus the column's, P_k = sum_{j <= k} dL/dN_j
-    auto Pk = [&](int k) { return (k >= js ? gNa : 0.0) + (k >= js + 1 ? gNb : 0.0); };
     auto gnk = [&](int k) {
-      double v = g_n ? g_n[(long long)k * nr + i] : 0.0;
-      if (k <= nz - 2) v += 0.5 * (zj(k + 1) - zj(k)) * Pk(k);
-      if (k >= 1) v += 0.5 * (zj(k) - zj(k - 1)) * Pk(k - 1);
+      float v = g_n ? (float)g_n[(long long)k * nr + i] : 0.0f;
+      const float Pk = (k >= js ? gNa : 0.0f) + (k >= js + 1 ? gNb : 0.0f);
+      const float Pk1 = (k - 1 >= js ? gNa : 0.0f) + (k >= js + 2 ? gNb : 0.0f);
+      if (k <= nz - 2) v += 0.5f * dz_cm * Pk;
+      if (k >= 1) v += 0.5f * dz_cm * Pk1;
       return v;
     };
-    // pass 3: sum_j dL/dn_j e_j
-    double ge_dot = 0.0;
-    for (int j = 0; j < nz; j++) ge_dot += gnk(j) * gT[(long long)j * nr];
-    // pass 4: downward, with Q = sum_{j > m} dL/dI_j
-    double Q = 0.0, sum_glr = 0.0;
-    for (int m = nz - 1; m >= 0; m--) {
-      const double wk = (m > 0 ? 0.5 * (zj(m) - zj(m - 1)) : 0.0) +
-                        (m < nz - 1 ? 0.5 * (zj(m + 1) - zj(m)) : 0.0);
-      const double e = gT[(long long)m * nr];
-      const double glr = (Cn * gnk(m) - Cn / S * wk * ge_dot) * e;
-      const double gI = -glr;
-      double gg = 0.0;
-      if (m + 1 <= nz - 1) gg += 0.5 * (zj(m + 1) - zj(m)) * Q;
-      if (m >= 1) gg += 0.5 * (zj(m) - zj(m - 1)) * (Q + gI);
-      Q += gI;
-      sum_glr += glr;
-      gT[(long long)m * nr] = -glr / Tj(m) - gg * grav(m) / Tj(m);
+    // pass 3: dL/dn_j and sum_j dL/dn_j e_j
+    KSum dot;
+    #pragma unroll 8
+    for (int j = 0; j < nz; j++) {
+      const float gn = gnk(j);
+      gc[(long long)j * nr] = gn;
+      dot.add(gn * ec[(long long)j * nr]);
     }
-    gT[0] += sum_glr / T0;  // the ln T_0 term (zero up to rounding: the normalisation removes it)
+    const float ge_dot = dot.value();
+    // pass 4: downward, with Q = sum_{j > m} dL/dI_j (I in units of au, so dL/dI per au)
+    KSum Q, sum_glr;
+    #pragma unroll 8
+    for (int m = nz - 1; m >= 0; m--) {
+      const float wk = (m > 0 ? 0.5f : 0.0f) + (m < nz - 1 ? 0.5f : 0.0f);  // w_k / dz
+      const float e = ec[(long long)m * nr];
+      const float glr = (Cn * gc[(long long)m * nr] - Cn / Sdz * wk * ge_dot) * e;
+      const float gI = -glr;
+      const float q = Q.value();
+      float gg = 0.0f;
+      if (m + 1 <= nz - 1) gg += 0.5f * dz_au * q;
+      if (m >= 1) gg += 0.5f * dz_au * (q + gI);
+      Q.add(gI);
+      sum_glr.add(glr);
+      gT[(long long)m * nr] = (double)(-glr / Tj(m) - gg * grav(m) / Tj(m));
+    }
+    gT[0] += (double)(sum_glr.value() / T0);  // the ln T_0 term (zero up to rounding)
     // h_lo: lowest cell [j-1, j] with T_j > T_freeze (none when the midplane node is warmer)
-    const double glo = g_lo ? g_lo[i] : 0.0;
-    if (glo != 0.0 && !(T0 > C.T_freeze)) {
+    const float glo = g_lo ? (float)g_lo[i] : 0.0f;
+    if (glo != 0.0f && !(T0 > C.T_freeze)) {
       for (int j = 1; j < nz; j++) {
-        const double Ta = Tj(j - 1), Tb = Tj(j);
+        const float Ta = Tj(j - 1), Tb = Tj(j);
         if (Tb > C.T_freeze) {
-          const double q = (Tb - Ta) * (Tb - Ta);
-          gT[(long long)(j - 1) * nr] += glo * dw * (C.T_freeze - Tb) / q;
-          gT[(long long)j * nr] += -glo * dw * (C.T_freeze - Ta) / q;
+          const float q = (Tb - Ta) * (Tb - Ta);
+          gT[(long long)(j - 1) * nr] += (double)(glo * dw * (C.T_freeze - Tb) / q);
+          gT[(long long)j * nr] += (double)(-glo * dw * (C.T_freeze - Ta) / q);
           break;
         }
       }
@@ -354,20 +388,28 @@ int launch_field_chain_adjoint(const rt_grid &g, const rt_geom &geo, const rt_li
   C.nr = g.nr;
   C.nz = g.nz;
   C.r_log = g.r_log;
-  C.r_in = g.r_in_au;
-  C.r_out = g.r_out_au;
-  C.zr_max = g.zr_max;
-  C.sigma0 = c.sigma0_gcm2;
-  C.r_c = c.r_c_au;
-  C.gamma = c.gamma;
-  C.m_mol = line.m_mol_amu * kChainAmu;
-  C.GMm_k = kChainGMsun * geo.mstar_msun * C.m_mol / kChainK;
-  C.T_freeze = c.T_freeze_K;
-  C.N_dissoc = c.N_dissoc_cm2;
-  const int threads = 64;
+  C.r_in = (float)g.r_in_au;
+  C.r_out = (float)g.r_out_au;
+  C.zr_max = (float)g.zr_max;
+  C.sigma0 = (float)c.sigma0_gcm2;
+  C.r_c = (float)c.r_c_au;
+  C.gamma = (float)c.gamma;
+  const double m = line.m_mol_amu * kChainAmu;
+  C.A = (float)(kChainGMsun * geo.mstar_msun * m / (kChainK * kChainAu));
+  C.m_mol_g = (float)m;
+  C.T_freeze = (float)c.T_freeze_K;
+  C.N_dissoc = (float)c.N_dissoc_cm2;
+  const size_t col = (size_t)g.nr * g.nz;
+  float *scr = nullptr;
+  cudaError_t e = stream_alloc((void **)&scr, 2 * col * sizeof(float), stream);
+  if (e != cudaSuccess)
+    return set_error(RT_ENOMEM, "chain adjoint scratch: %s", cudaGetErrorString(e));
+  const int threads = 32;  // one warp per block: the columns spread over the SMs
   const long long blocks = (g.nr + threads - 1) / threads;
-  field_chain_adjoint_kernel<<<(unsigned)blocks, threads, 0, stream>>>(C, T, g_n, g_lo, g_hi, g_T);
-  cudaError_t e = cudaGetLastError();
+  field_chain_adjoint_kernel<<<(unsigned)blocks, threads, 0, stream>>>(C, T, g_n, g_lo, g_hi, g_T,
+                                                                       scr, scr + col);
+  e = cudaGetLastError();
+  cudaFreeAsync(scr, stream);
   if (e != cudaSuccess)
     return set_error(RT_ECUDA, "field chain adjoint launch: %s", cudaGetErrorString(e));
   return RT_OK;
