@@ -109,6 +109,7 @@ def _load():
             lib.orc_partition.argtypes = [C.c_double, C.c_double]
             lib.orc_partition.restype = C.c_double
             lib.orc_render_adjoint.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
+            lib.orc_render_adjoint_vphi.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
             lib.orc_mlp_eval.argtypes = [C.POINTER(_MLP), dp, C.c_int, dp]
             lib.orc_mlp_grad.argtypes = [C.POINTER(_MLP), dp, dp, C.c_int, dp, dp]
             lib.orc_render_mlp.argtypes = [pp, C.POINTER(_MLP), C.POINTER(C.c_longlong),
@@ -275,6 +276,23 @@ def render_adjoint(p, dL_dcube: np.ndarray, nthreads: int = 0):
     if rc:
         raise ValueError("oracle: invalid problem")
     return cube, dict(T=dT, n_h2=dn, vturb=dvt, h_lo=dlo, h_hi=dhi)
+
+
+def render_adjoint_vphi(p, dL_dcube: np.ndarray, nthreads: int = 0):
+    """render_adjoint for a problem with a rotation field: grads also hold vphi [nz][nr]."""
+    lib = _load()
+    pk = _Packed(p)
+    g = np.ascontiguousarray(np.asarray(dL_dcube, dtype=np.float64))
+    cube = np.zeros((pk.nch, int(p.ny), int(p.nx)), dtype=np.float64)
+    shp = (int(p.nz), int(p.nr))
+    dT, dn, dvt, dvp = np.zeros(shp), np.zeros(shp), np.zeros(shp), np.zeros(shp)
+    dlo, dhi = np.zeros(int(p.nr)), np.zeros(int(p.nr))
+    rc = lib.orc_render_adjoint_vphi(C.byref(pk.s), _dptr(g), _dptr(cube), _dptr(dT), _dptr(dn),
+                                     _dptr(dvt), _dptr(dlo), _dptr(dhi), _dptr(dvp),
+                                     _threads(nthreads))
+    if rc:
+        raise ValueError("oracle: invalid problem (a rotation field is required)")
+    return cube, dict(T=dT, n_h2=dn, vturb=dvt, h_lo=dlo, h_hi=dhi, vphi=dvp)
 
 
 def mlp_eval(w, x: np.ndarray) -> np.ndarray:

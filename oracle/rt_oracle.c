@@ -205,6 +205,8 @@ typedef struct {
   /* neural field (when a network is given): inputs, outputs and the factors exp(o0), exp(o1)
      applied to T and n */
   double xin[2], o[4], mT, mn;
+  /* d v_los / d(rotation-field value) [cm/s per km/s] with a rotation field, 0 otherwise */
+  double dvlos_dvphi;
 } pt;
 
 static double bilerp(const double *F, int nr, int i0, int j0, double fr, double fz) {
@@ -376,6 +378,7 @@ static void eval_point(const orc_problem *p, const orc_mlp *m, const double P[3]
                         : sqrt(GM_SUN * p->mstar_msun * rc * rc / pow(rc * rc + zc * zc, 1.5));
   double v[3] = {-vphi * y / r, vphi * x / r, 0.0};
   st->vlos = om[0] * v[0] + om[1] * v[1] + om[2] * v[2] + p->vsys_kms * 1e5;
+  st->dvlos_dvphi = p->vphi ? 1e5 * (om[1] * x - om[0] * y) / r : 0.0;
   }
 line_physics:;
   /* Line width: thermal + turbulent. Absolute mode (v_turb in km/s) or the paper's Mach
@@ -570,6 +573,7 @@ int orc_render_pixels(const orc_problem *p, const long long *pix, int npix, doub
 typedef struct {
   double *gT, *gn, *gvt, *ghlo, *ghhi;
   double *gW, *gb; /* network parameters, flat in layer order (NULL without a network) */
+  double *gvphi;   /* rotation field (NULL without one) */
 } grads;
 
 static void mlp_backward(const orc_mlp *m, const double xin[2], const double *gout,
@@ -633,7 +637,7 @@ static void adjoint_pixel(const orc_problem *p, const orc_mlp *m, int ix, int iy
   }
   for (int k = N - 1; k >= 0; k--) {
     const pt *q = &st[k];
-    double gS = 0.0, gD = 0.0, galpha = 0.0;
+    double gS = 0.0, gD = 0.0, galpha = 0.0, gvlos = 0.0;
     for (int c = 0; c < C; c++) {
       double tr = Tr[k * C + c], dt = dtau[k * C + c];
       if (!(dt > 0.0)) continue; /* this step was the identity */
@@ -649,6 +653,8 @@ static void adjoint_pixel(const orc_problem *p, const orc_mlp *m, int ix, int iy
       /* phi = c/(nu0 alpha sqrt(pi)) exp(-x^2), x = Q/alpha: dphi/dalpha = phi (2x^2-1)/alpha */
       double xx = xarg[k * C + c];
       galpha += g_phi * phi[k * C + c] * (2.0 * xx * xx - 1.0) / q->alpha;
+      /* x = (v_los - v_c) / alpha (cm/s): dphi/dv_los = -2 x phi / alpha */
+      gvlos += g_phi * phi[k * C + c] * (-2.0 * xx) / q->alpha;
     }
     if (!q->gas) continue;
     /* S = A_ul n_u / D (both populations scale with n_CO, which cancels) */
@@ -707,6 +713,8 @@ static void adjoint_pixel(const orc_problem *p, const orc_mlp *m, int ix, int iy
     g->ghlo[i0 + 1] += ghlo * fr;
     g->ghhi[i0] += ghhi * (1 - fr);
     g->ghhi[i0 + 1] += ghhi * fr;
+    if (g->gvphi)
+      for (int a = 0; a < 4; a++) g->gvphi[idx[a]] += gvlos * q->dvlos_dvphi * wt[a];
   }
   free(gI);
   free(gTr);
@@ -734,7 +742,8 @@ static long long mlp_nb(const orc_mlp *m) {
 
 static int render_adjoint_impl(const orc_problem *p, const orc_mlp *m, const double *dL_dcube,
                                double *cube, double *dT, double *dn, double *dvt, double *dh_lo,
-                               double *dh_hi, double *dW, double *db, int nthreads) {
+                               double *dh_hi, double *dW, double *db, double *dvphi,
+                               int nthreads) {
   if (check(p) || !dL_dcube || p->g3 || p->gs) return -1; /* axisymmetric grid only */
   if (m && (mlp_check(m) || m->dims[m->n_layers] < 4 || m->dims[m->n_layers] > 64)) return -1;
   int G = p->nr * p->nz;
@@ -745,6 +754,7 @@ static int render_adjoint_impl(const orc_problem *p, const orc_mlp *m, const dou
   memset(dvt, 0, sizeof(double) * G);
   memset(dh_lo, 0, sizeof(double) * p->nr);
   memset(dh_hi, 0, sizeof(double) * p->nr);
+  if (dvphi) memset(dvphi, 0, sizeof(double) * G);
   if (m) {
     memset(dW, 0, sizeof(double) * nw);
     memset(db, 0, sizeof(double) * nb);
@@ -762,6 +772,7 @@ static int render_adjoint_impl(const orc_problem *p, const orc_mlp *m, const dou
     g.ghhi = (double *)calloc(p->nr, sizeof(double));
     g.gW = m ? (double *)calloc(nw, sizeof(double)) : NULL;
     g.gb = m ? (double *)calloc(nb, sizeof(double)) : NULL;
+    g.gvphi = dvphi ? (double *)calloc(G, sizeof(double)) : NULL;
     double *gout = (double *)malloc(sizeof(double) * (p->nch > 0 ? p->nch : 1));
     double *I = (double *)malloc(sizeof(double) * (p->nch > 0 ? p->nch : 1));
 #ifdef _OPENMP
@@ -789,6 +800,8 @@ static int render_adjoint_impl(const orc_problem *p, const orc_mlp *m, const dou
         dh_lo[a] += g.ghlo[a];
         dh_hi[a] += g.ghhi[a];
       }
+      if (dvphi)
+        for (int a = 0; a < G; a++) dvphi[a] += g.gvphi[a];
       for (long long a = 0; a < nw; a++) dW[a] += g.gW[a];
       for (long long a = 0; a < nb; a++) db[a] += g.gb[a];
     }
@@ -799,6 +812,7 @@ static int render_adjoint_impl(const orc_problem *p, const orc_mlp *m, const dou
     free(g.ghhi);
     free(g.gW);
     free(g.gb);
+    free(g.gvphi);
     free(gout);
     free(I);
   }
@@ -810,14 +824,22 @@ int orc_render_adjoint(const orc_problem *p, const double *dL_dcube, double *cub
                        double *dT, double *dn, double *dvt, double *dh_lo, double *dh_hi,
                        int nthreads) {
   return render_adjoint_impl(p, NULL, dL_dcube, cube, dT, dn, dvt, dh_lo, dh_hi, NULL, NULL,
-                             nthreads);
+                             NULL, nthreads);
+}
+
+int orc_render_adjoint_vphi(const orc_problem *p, const double *dL_dcube, double *cube,
+                            double *dT, double *dn, double *dvt, double *dh_lo, double *dh_hi,
+                            double *dvphi, int nthreads) {
+  if (!p || !p->vphi || !dvphi) return -1;
+  return render_adjoint_impl(p, NULL, dL_dcube, cube, dT, dn, dvt, dh_lo, dh_hi, NULL, NULL,
+                             dvphi, nthreads);
 }
 
 int orc_render_mlp_adjoint(const orc_problem *p, const orc_mlp *m, const double *dL_dcube,
                            double *cube, double *dT, double *dn, double *dvt, double *dh_lo,
                            double *dh_hi, double *dW, double *db, int nthreads) {
   if (!m || !dW || !db) return -1;
-  return render_adjoint_impl(p, m, dL_dcube, cube, dT, dn, dvt, dh_lo, dh_hi, dW, db,
+  return render_adjoint_impl(p, m, dL_dcube, cube, dT, dn, dvt, dh_lo, dh_hi, dW, db, NULL,
                              nthreads);
 }
 

@@ -110,6 +110,13 @@ int orc_render_adjoint(const orc_problem *p, const double *dL_dcube, double *cub
                        double *dT, double *dn, double *dvt, double *dh_lo, double *dh_hi,
                        int nthreads);
 
+/* orc_render_adjoint for a problem with a rotation field (p->vphi): also writes
+   dL/d(rotation field) [nz][nr] (per km/s, overwritten) through
+   v_los = v_phi (omega . phi^) + v_sys with the field interpolated bilinearly. */
+int orc_render_adjoint_vphi(const orc_problem *p, const double *dL_dcube, double *cube,
+                            double *dT, double *dn, double *dvt, double *dh_lo, double *dh_hi,
+                            double *dvphi, int nthreads);
+
 /* Neural field (fully connected, SiLU hidden activations, Fourier-feature input). */
 typedef struct {
   int n_freq;              /* number of Fourier directions; features = 2*n_freq */

@@ -128,3 +128,37 @@ def test_adjoint_mach_mode_and_units(orc):
         idx = int(np.argsort(np.abs(g[field]).ravel())[-1 - idx % 5])
         f = fd(orc, p, w, field, idx)
         assert f == pytest.approx(g[field].flat[idx], rel=2e-5, abs=1e-9 * np.abs(g[field]).max())
+
+
+def test_adjoint_through_a_rotation_field(orc):
+    """With a tabulated rotation field (Keplerian speeds plus a perturbation), dL/d(field)
+    from orc_render_adjoint_vphi matches central differences of the forward march at random
+    nodes that carry gradient, and the other fields' gradients are those of a problem whose
+    line-of-sight velocity comes from the field (spot checks)."""
+    from tests.test_oracle_vphi import kepler_kms
+    p = small_problem(2)
+    rng = np.random.default_rng(8)
+    vk = kepler_kms(p) * (1.0 + 0.05 * rng.standard_normal((p.nz, p.nr)))
+    p = p.replace(vphi=vk)
+    w = rng.standard_normal((p.nch, p.ny, p.nx))
+    cube, g = orc.render_adjoint_vphi(p, w)
+    np.testing.assert_allclose(cube, orc.render(p), rtol=1e-14, atol=0)
+    for field, n_cells in (("vphi", 12), ("T", 4), ("n_h2", 4)):
+        gf = g[field]
+        flat = np.abs(gf).ravel()
+        cand = np.flatnonzero(flat >= 0.02 * flat.max())
+        assert cand.size > 0, field
+        rel = 1e-4
+        for idx in rng.choice(cand, size=min(n_cells, cand.size), replace=False):
+            if field == "vphi":
+                # rotation speeds are ~50 line widths, so the second-order stencil's truncation
+                # is ~1e-5 at this step and the FP64 renders' roundoff ~1e-5 at a ten times
+                # smaller one: the fourth-order stencil (truncation O(h^4))
+                f = (4.0 * fd(orc, p, w, field, int(idx), rel)
+                     - fd(orc, p, w, field, int(idx), 2 * rel)) / 3.0
+            else:
+                f = fd(orc, p, w, field, int(idx), rel)
+            h = rel * abs(getattr(p, field).flat[idx])
+            roundoff = 1e-15 * float(np.abs(cube * w).sum()) / h
+            assert abs(f - gf.flat[idx]) <= 1e-5 * abs(gf.flat[idx]) + roundoff, (
+                field, int(idx), f, gf.flat[idx])
