@@ -155,6 +155,8 @@ typedef struct {
   double *dh_hi;    /* [nr] dL/dh_hi */
   double *loss;     /* 1 value: sum over voxels of (cube - target)^2 when a target is given;
                        may be NULL */
+  double *dvphi;    /* [nz][nr] dL/dvphi_kms (per km/s): required when the fields carry a
+                       rotation field (rt_fields.vphi_kms), unused otherwise */
 } rt_grads;
 
 /*
@@ -200,12 +202,13 @@ int rt_render_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *
  *             grads->loss if non-NULL).
  * cube_out (DEVICE, may be NULL) receives the rendered cube (same values as rt_render up to
  * FP32 rounding). Gradients w.r.t. every node of T, n_H2, v_turb and both surfaces
- * overwrite the FP64 arrays. The call allocates and frees one device scratch buffer on
+ * overwrite the FP64 arrays; with a rotation field (fields->vphi_kms) so does its gradient
+ * (grads->dvphi, required then), through v_los = v_phi sin i x / r + v_sys. The call allocates and frees one device scratch buffer on
  * `stream` (stream-ordered) holding the optical-depth checkpoints (every 64
  * samples), the reverse march's per-warp record of the 64-sample segment it is reversing
  * (recomputed from the segment's checkpoint: batch optical depths, and the physics and local
  * derivatives of each sample, 64 bytes per sample, 80 with a network) and up to 32 replicated FP32
- * copies of the node gradients (at most 32 MiB, {dT, dn, dvt} interleaved per node) plus up
+ * copies of the node gradients (at most 32 MiB, {dT, dn, dvt, dvphi} interleaved per node) plus up
  * to 128 of the surface gradients: each block of the kernel reduces into one copy, and the
  * copies are summed in FP64, in a fixed order, into the outputs at the end. Atomics on one
  * address are applied one after another, and without the copies the surface entries, which

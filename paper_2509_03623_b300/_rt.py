@@ -56,7 +56,8 @@ class rt_line(C.Structure):
 
 class rt_grads(C.Structure):
     _fields_ = [("dT", C.c_void_p), ("dn", C.c_void_p), ("dvt", C.c_void_p),
-                ("dh_lo", C.c_void_p), ("dh_hi", C.c_void_p), ("loss", C.c_void_p)]
+                ("dh_lo", C.c_void_p), ("dh_hi", C.c_void_p), ("loss", C.c_void_p),
+                ("dvphi", C.c_void_p)]
 
 
 class rt_mlp(C.Structure):
@@ -343,8 +344,12 @@ def rt_render_adjoint(problem, fields=None, dL_dcube=None, target=None, cube_out
     out = {k: torch.empty(tuple(t.shape), dtype=torch.float64, device=dev)
            for k, t in zip(DeviceDisk.FIELDS, (T, n, vt, hlo, hhi))}
     out["loss"] = torch.empty(1, dtype=torch.float64, device=dev)
+    vp = getattr(dd, "vphi", None)
+    if vp is not None:  # a rotation field: its gradient too
+        out["vphi"] = torch.empty(tuple(vp.shape), dtype=torch.float64, device=dev)
     gr = rt_grads(out["T"].data_ptr(), out["n_h2"].data_ptr(), out["vturb"].data_ptr(),
-                  out["h_lo"].data_ptr(), out["h_hi"].data_ptr(), out["loss"].data_ptr())
+                  out["h_lo"].data_ptr(), out["h_hi"].data_ptr(), out["loss"].data_ptr(),
+                  out["vphi"].data_ptr() if vp is not None else None)
     check(lib().rt_render_adjoint(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
                                   _ptr(dL_dcube), _ptr(target), _ptr(cube), C.byref(gr),
                                   stream_handle(stream)))
@@ -366,7 +371,8 @@ def rt_render_adjoint_noalloc(problem, fields, cube_out, grads, dL_dcube=None, t
     cube_out = _cube_arg(cube_out, shape, "cube_out")
     gr = rt_grads(grads["T"].data_ptr(), grads["n_h2"].data_ptr(), grads["vturb"].data_ptr(),
                   grads["h_lo"].data_ptr(), grads["h_hi"].data_ptr(),
-                  grads["loss"].data_ptr() if grads.get("loss") is not None else None)
+                  grads["loss"].data_ptr() if grads.get("loss") is not None else None,
+                  grads["vphi"].data_ptr() if grads.get("vphi") is not None else None)
     check(lib().rt_render_adjoint_noalloc(C.byref(g), C.byref(f), C.byref(o), C.byref(vw),
                                           C.byref(ln), _ptr(dL_dcube), _ptr(target),
                                           _ptr(cube_out), C.byref(gr), stream_handle(stream)))

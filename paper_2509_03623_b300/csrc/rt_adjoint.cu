@@ -40,8 +40,9 @@ constexpr int adj_wpb() {
 constexpr int kSeg = 64;  // samples per checkpoint segment
 
 // Per-sample record of the segment being reversed: the physics {kd, a, b, S} and the local
-// derivatives (below), five float4 per lane and batch; without a network the fifth (J_MN, J_T,
-// J_N: the network factor on n and the modulated primitives) is neither written nor read.
+// derivatives (below), five float4 per lane and batch; without a network or a rotation field
+// the fifth (J_MN, J_T, J_N, J_VPX: the network factor on n, the modulated primitives and
+// d v_los / d v_phi) is neither written nor read.
 constexpr int kRec = 5;
 
 // Per-warp scratch in floats: checkpoints of each segment, then the batch starts of the
@@ -70,16 +71,18 @@ enum {
   J_MN,    // network factor on n (e^{o1})
   J_T,     // T and n after the network factors
   J_N,
+  J_VPX,   // d v_los / d v_phi = sin i x / r (with a rotation field)
   kJ
 };
 static_assert(kJ <= 4 * (kRec - 1), "local derivatives fit the sample record");
-static_assert(J_MN == 4 * (kRec - 2) && J_T > J_MN && J_N > J_MN && J_MT < J_MN,
-              "the last record slot starts with the network-only entries");
+static_assert(J_MN == 4 * (kRec - 2) && J_T > J_MN && J_N > J_MN && J_VPX > J_MN && J_MT < J_MN,
+              "the last record slot holds the network and rotation-field entries");
 
 // Channel-independent physics of sample k with its local derivatives, written where the sample
 // has gas to the record slots rec[32 (i + 1)], i < kRec - 1 (entries 4i .. 4i + 3 of the enum).
 // Returns {kd, a, b, S} as sample_physics does for a sample with gas, and zeros (b = 0 marks
 // "no gas") otherwise. The arithmetic of kd, a, b and S is the same as sample_physics'.
+template <bool ROT>
 __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float *tab,
                                               const Ray &R, int k, float4 *rec) {
   const float kf = (float)k;
@@ -88,7 +91,7 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   const float r2 = fmaf(R.x, R.x, y * y);
   if (!(in_gas(P, z, r2) && R.hit && k < P.n_samples)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const Cell c = locate(P, z, r2);
-  const NodeVals f = fields_at<false>(P, c);  // the adjoint takes Keplerian rotation
+  const NodeVals f = fields_at<ROT>(P, c);
   float T = f.T, n = f.n, hlo = f.hlo, hhi = f.hhi;
   const float vt = f.vt;
   float mT = 1.0f, mn = 1.0f;
@@ -115,7 +118,10 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
     sa = -ea * pb * rr * kl;
     sb = eb * pa * rr * kl;
   }
-  const float vlos = fmaf(R.vfac, kepler_q(fmaf(z, z, r2)), P.vsys);
+  // v_los as in sample_physics: the rotation field projected, or the Keplerian term
+  const float vpx = P.sin_if * R.x * c.ir;  // d v_los / d v_phi
+  const float vlos = ROT ? fmaf(f.vphi * (P.sin_if * R.x), c.ir, P.vsys)
+                         : fmaf(R.vfac, kepler_q(fmaf(z, z, r2)), P.vsys);
   const bool clampT = T < 1e-3f;
   const float Tg = fmaxf(T, 1e-3f);
   float a2, da2T, da2v;
@@ -154,10 +160,11 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   J[J_MN] = mn;
   J[J_T] = T;
   J[J_N] = n;
+  J[J_VPX] = ROT ? vpx : 0.0f;
   for (int e = kJ; e < 4 * (kRec - 1); e++) J[e] = 0.0f;
 #pragma unroll
   for (int i = 0; i < kRec - 1; i++)
-    if (i < kRec - 2 || P.mod)
+    if (i < kRec - 2 || P.mod || ROT)
       rec[(i + 1) * 32] = make_float4(J[4 * i], J[4 * i + 1], J[4 * i + 2], J[4 * i + 3]);
   float4 out;
   out.x = P.kappa_k * (X * n) * F * ia * R.ds;
@@ -202,19 +209,22 @@ __device__ __forceinline__ GradSink block_sink(const rt_grads &G, const GradCopi
 //   grid:    dT[i], dn[i], dvt[i] = sum_c cop[c][i].{x, y, z}  (one thread per node, copy order)
 //   surface: dh_lo[i], dh_hi[i]   = sum_c cop[c][i].{x, y}     (one warp per entry, below)
 __global__ void sum_grid_copies_kernel(const float4 *__restrict__ cop, int k, long long stride,
-                                       long long n, double *dT, double *dn, double *dvt) {
+                                       long long n, double *dT, double *dn, double *dvt,
+                                       double *dvphi) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    double a = 0.0, b = 0.0, c = 0.0;
+    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
     for (int j = 0; j < k; j++) {
       const float4 v = cop[(long long)j * stride + i];
       a += v.x;
       b += v.y;
       c += v.z;
+      d += v.w;
     }
     dT[i] = a;
     dn[i] = b;
     dvt[i] = c;
+    if (dvphi) dvphi[i] = d;  // the rotation field's gradient (0 without one)
   }
 }
 
@@ -248,9 +258,12 @@ __global__ void sum_surface_copies_kernel(const float2 *__restrict__ cop, int k,
 // and the local derivatives J; node gradients into the block's sink, and the gradient with respect
 // to the four network outputs of the sample when dmod is given (returns its largest
 // magnitude, 0 otherwise).
+// With a rotation field (ROT) also dL/dv_phi: d_c = v_c b - a with a = v_los b, so
+// dL/dv_los = b dL/da = -2 ln2^2 kd b az, az = sum_c gI_c A_c g_c d_c, times d v_los / d v_phi.
+template <bool ROT>
 __device__ __forceinline__ float scatter_grad(const MarchParams &P, const float *J, float kd,
-                                             float ax, float ay, float aS, const GradSink &G,
-                                             float4 *dmod) {
+                                             float b, float ax, float ay, float az, float aS,
+                                             const GradSink &G, float4 *dmod) {
   const float gx = -kLn2 * ax;                       // dL/dkd
   const float GB = 2.0f * kLn2 * kLn2 * kd * ay;     // b dL/db (a = v_los b included)
   const float gk = fmaf(gx, kd, GB);                 // alpha dL/d(1/alpha) ... times ia
@@ -266,6 +279,7 @@ __device__ __forceinline__ float scatter_grad(const MarchParams &P, const float 
     dm = fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fmaxf(fabsf(o.z), fabsf(o.w)));
   }
   const float dT = gT * J[J_MT], dn = gn * J[J_MN];
+  const float gp = ROT ? -2.0f * kLn2 * kLn2 * kd * b * az * J[J_VPX] : 0.0f;  // dL/dv_phi
   const float fr = J[J_FR], fz = J[J_FZ];
   const int i00 = __float_as_int(J[J_CELL]), i0 = __float_as_int(J[J_I0]);
   const int nr = P.nr;
@@ -274,13 +288,14 @@ __device__ __forceinline__ float scatter_grad(const MarchParams &P, const float 
   if (G.g) {
 #pragma unroll
     for (int a = 0; a < 4; a++)
-      atomicAdd(G.g + idx[a], make_float4(dT * w[a], dn * w[a], gv * w[a], 0.0f));
+      atomicAdd(G.g + idx[a], make_float4(dT * w[a], dn * w[a], gv * w[a], gp * w[a]));
   } else {
 #pragma unroll
     for (int a = 0; a < 4; a++) {
       atomicAdd(G.G.dT + idx[a], (double)(dT * w[a]));
       atomicAdd(G.G.dn + idx[a], (double)(dn * w[a]));
       atomicAdd(G.G.dvt + idx[a], (double)(gv * w[a]));
+      if (ROT) atomicAdd(G.G.dvphi + idx[a], (double)(gp * w[a]));
     }
   }
   if (G.h) {
@@ -324,13 +339,15 @@ __device__ __forceinline__ unsigned adj_window(const MarchParams &P, const float
   return act;
 }
 
-template <int LPR, int CPL, bool UNIF>
+template <int LPR, int CPL, int VAR>
 __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
     march_adj_kernel(const __grid_constant__ MarchParams P, const float *__restrict__ dLdc,
                      const float *__restrict__ target, float *__restrict__ cube_out,
                      const rt_grads G, float *__restrict__ scratch, int nseg,
                      float4 *__restrict__ dmod, unsigned *__restrict__ dmax,
                      const GradCopies GC) {
+  constexpr bool UNIF = (VAR & 1) != 0;  // equally spaced channels
+  constexpr bool ROT = (VAR & 2) != 0;   // a rotation field (gradient with respect to it too)
   constexpr int WPB = adj_wpb<LPR>();
   constexpr int R = 32 / LPR;          // rays per warp
   constexpr int NG = 32 / R;           // work units whose setups are computed together
@@ -404,7 +421,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             ck[((kb / kSeg) * CPL + 2 * m + 1) * 32 + lane] = tb[m].y;
           }
         }
-        const float4 mine = sample_physics(P, s_tab, ray, kb + q);
+        const float4 mine = sample_physics<ROT>(P, s_tab, ray, kb + q);
         const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
         if (!act) continue;
         unsigned act2 = 0;
@@ -488,7 +505,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
           for (int j = 0; j < CPL; j++) bs[(b * CPL + j) * 32 + lane] = tbs[j];
           // physics and local derivatives, kept for the reverse pass over this batch
           float4 *rb = rec + (long long)b * kRec * 32;
-          const float4 mine = physics_jac(P, s_tab, ray, k0 + b * LPR + q, rb);
+          const float4 mine = physics_jac<ROT>(P, s_tab, ray, k0 + b * LPR + q, rb);
           rb[0] = mine;
           const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
           if (lane == 0) s_act[wib][b] = act;
@@ -544,7 +561,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             Snext = gas ? p.w : Snext;
             const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
             const float2 cs2 = make_float2(cs, cs), kd2 = make_float2(p.x, p.x);
-            float2 ax = make_float2(0.0f, 0.0f), ay = ax, aw = ax;
+            float2 ax = make_float2(0.0f, 0.0f), ay = ax, aw = ax, az = ax;
 #pragma unroll
             for (int m = 0; m < CPL / 2; m++) {
               if (!(act2 & (1u << m))) continue;  // warp-uniform
@@ -559,6 +576,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
               const float2 ug = __fmul2_rn(__fmul2_rn(gI[m], A[m]), gg);
               ax = __fadd2_rn(ax, ug);
               ay = __ffma2_rn(ug, d2, ay);
+              if (ROT) az = __ffma2_rn(ug, d, az);
               const float2 dt = __fmul2_rn(kd2, gg);
               cur[m] = __ffma2_rn(dt, mone, cur[m]);
               const float2 T0 = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
@@ -575,7 +593,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
               aw = __ffma2_rn(gI[m], dTk, aw);
               Tn[m] = T0;
             }
-            part[t][lane ^ (t & 7)] = make_float4(ax.x + ax.y, ay.x + ay.y, 0.0f, aw.x + aw.y);
+            part[t][lane ^ (t & 7)] = make_float4(ax.x + ax.y, ay.x + ay.y, az.x + az.y, aw.x + aw.y);
           }
           // blocks outside every window: T is constant over the batch, so the suffix sums
           // advance by T (S before the batch - S of its first sample with gas)
@@ -590,20 +608,21 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             const float4 v = part[q][(rr * LPR + i) ^ (q & 7)];
             s.x += v.x;
             s.y += v.y;
+            if (ROT) s.z += v.z;
             s.w += v.w;
           }
           if (active && mine.z > 0.0f) {
             float Jv[4 * (kRec - 1)];
 #pragma unroll
             for (int i = 0; i < kRec - 1; i++) {
-              const float4 v = (i < kRec - 2 || P.mod) ? rb[(i + 1) * 32]
-                                                       : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+              const float4 v = (i < kRec - 2 || P.mod || ROT) ? rb[(i + 1) * 32]
+                                                              : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
               Jv[4 * i] = v.x;
               Jv[4 * i + 1] = v.y;
               Jv[4 * i + 2] = v.z;
               Jv[4 * i + 3] = v.w;
             }
-            dmx = fmaxf(dmx, scatter_grad(P, Jv, mine.x, s.x, s.y, s.w, Gb,
+            dmx = fmaxf(dmx, scatter_grad<ROT>(P, Jv, mine.x, mine.z, s.x, s.y, s.z, s.w, Gb,
                                           dmod ? dmod + (long long)pix * P.n_samples + kb + q
                                                : nullptr));
           }
@@ -620,6 +639,11 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
     for (int o = 16; o > 0; o >>= 1) dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
     if (lane == 0 && dmx > 0.0f) atomicMax(dmax, __float_as_uint(dmx));
   }
+}
+
+// Kernel variant of a problem: bit 0 equally spaced channels, bit 1 a rotation field.
+static int adj_variant(const MarchParams &P) {
+  return (P.v_uniform ? 1 : 0) | (P.vphi ? 2 : 0);
 }
 
 // Lane layout of the adjoint: CPL channels per lane (8 from 32 channels up), LPR lanes per
@@ -668,7 +692,7 @@ __global__ void surface_powerlaw_kernel(int nr, int r_log, double r_in, double r
 
 // Blocks of the persistent grid of the adjoint kernel for P (cap_blocks <= 0 asks the
 // occupancy calculator).
-template <int LPR, int CPL, bool UNIF>
+template <int LPR, int CPL, int VAR>
 static long long adj_blocks(const MarchParams &P, long long cap_blocks) {
   constexpr int WPB = adj_wpb<LPR>();
   long long npix = (long long)P.nx * P.ny;
@@ -676,7 +700,7 @@ static long long adj_blocks(const MarchParams &P, long long cap_blocks) {
   long long need = (units + WPB - 1) / WPB;
   long long cap = cap_blocks > 0
                       ? cap_blocks
-                      : resident_blocks((const void *)march_adj_kernel<LPR, CPL, UNIF>, WPB * 32);
+                      : resident_blocks((const void *)march_adj_kernel<LPR, CPL, VAR>, WPB * 32);
   return need < cap ? need : cap;
 }
 
@@ -742,6 +766,7 @@ static int zero_grads(const MarchParams &P, const rt_grads &G, const AdjScratch 
     e = cudaMemsetAsync(G.dT, 0, ng, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(G.dn, 0, ng, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(G.dvt, 0, ng, stream);
+    if (e == cudaSuccess && P.vphi) e = cudaMemsetAsync(G.dvphi, 0, ng, stream);
   }
   if (e == cudaSuccess && a.kh) {
     e = cudaMemsetAsync(scratch + a.h_off, 0, a.cell_off - a.h_off, stream);
@@ -771,7 +796,7 @@ static int sum_copies(const MarchParams &P, const rt_grads &G, const GradCopies 
     long long m = (long long)P.nr * P.nz;
     long long nb = (m + 255) / 256;
     sum_grid_copies_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, stream>>>(
-        c.g, a.kg, c.gstride, m, G.dT, G.dn, G.dvt);
+        c.g, a.kg, c.gstride, m, G.dT, G.dn, G.dvt, P.vphi ? G.dvphi : nullptr);
   }
   if (a.kh) {
     long long nb = (P.nr + 7) / 8;  // 8 warps (entries) per block
@@ -784,7 +809,7 @@ static int sum_copies(const MarchParams &P, const rt_grads &G, const GradCopies 
 }
 
 // Zero, march, sum: one adjoint launch on `scratch` (laid out by a).
-template <int LPR, int CPL, bool UNIF>
+template <int LPR, int CPL, int VAR>
 static int run_adj(const MarchParams &P, const float *dLdc, const float *target, float *cube_out,
                    const rt_grads &G, float4 *dmod, unsigned *dmax, long long blocks,
                    const AdjScratch &a, char *scratch, cudaStream_t stream) {
@@ -804,7 +829,7 @@ static int run_adj(const MarchParams &P, const float *dLdc, const float *target,
     }
     Q = packed;
   }
-  march_adj_kernel<LPR, CPL, UNIF><<<(unsigned)blocks, adj_wpb<LPR>() * 32, 0, stream>>>(
+  march_adj_kernel<LPR, CPL, VAR><<<(unsigned)blocks, adj_wpb<LPR>() * 32, 0, stream>>>(
       *Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, dmax, c);
   delete packed;
   cudaError_t e = cudaGetLastError();
@@ -812,18 +837,18 @@ static int run_adj(const MarchParams &P, const float *dLdc, const float *target,
   return sum_copies(P, G, c, a, stream);
 }
 
-template <int LPR, int CPL, bool UNIF>
+template <int LPR, int CPL, int VAR>
 static int launch_adj_t(const MarchParams &P, const float *dLdc, const float *target,
                         float *cube_out, const rt_grads &G, float4 *dmod, unsigned *dmax,
                         cudaStream_t stream) {
-  const long long blocks = adj_blocks<LPR, CPL, UNIF>(P, 0);
+  const long long blocks = adj_blocks<LPR, CPL, VAR>(P, 0);
   const AdjScratch a = plan_scratch(P, blocks, blocks * adj_block_bytes<LPR, CPL>(P), 0);
   char *scratch = nullptr;
   cudaError_t e = stream_alloc((void **)&scratch, a.total, stream);
   if (e != cudaSuccess)
     return set_error(RT_ENOMEM, "adjoint scratch (%zu bytes): %s", a.total,
                      cudaGetErrorString(e));
-  int rc = run_adj<LPR, CPL, UNIF>(P, dLdc, target, cube_out, G, dmod, dmax, blocks, a,
+  int rc = run_adj<LPR, CPL, VAR>(P, dLdc, target, cube_out, G, dmod, dmax, blocks, a,
                                    scratch, stream);
   cudaFreeAsync(scratch, stream);
   return rc;
@@ -840,11 +865,14 @@ int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target,
   if (npix == 0 || P.nch == 0) return zero_grads(P, G, plan_scratch(P, 1, 0, 0), nullptr, stream);
   int LPR, CPL;
   adj_layout(P.nch, &LPR, &CPL);
-  const bool u = P.v_uniform != 0;
+  const int v = adj_variant(P);
 #define X(L, C)                                                                         \
-  if (LPR == L && CPL == C)                                                             \
-    return u ? launch_adj_t<L, C, true>(P, dLdc, target, cube_out, G, dmod, dmax, stream) \
-             : launch_adj_t<L, C, false>(P, dLdc, target, cube_out, G, dmod, dmax, stream);
+  if (LPR == L && CPL == C) {                                                           \
+    if (v == 0) return launch_adj_t<L, C, 0>(P, dLdc, target, cube_out, G, dmod, dmax, stream); \
+    if (v == 1) return launch_adj_t<L, C, 1>(P, dLdc, target, cube_out, G, dmod, dmax, stream); \
+    if (v == 2) return launch_adj_t<L, C, 2>(P, dLdc, target, cube_out, G, dmod, dmax, stream); \
+    return launch_adj_t<L, C, 3>(P, dLdc, target, cube_out, G, dmod, dmax, stream);     \
+  }
   RTB_ADJ_LAYOUTS(X)
 #undef X
   return set_error(RT_EINVAL, "no adjoint layout for %d channels", P.nch);
@@ -859,10 +887,13 @@ size_t adjoint_scratch_bytes(const MarchParams &P, long long cap_blocks) {
   adj_layout(P.nch, &LPR, &CPL);
   long long b = 1;
   size_t per = 0;
-  const bool u = P.v_uniform != 0;
+  const int v = adj_variant(P);
 #define X(L, C)                                                                            \
   if (LPR == L && CPL == C) {                                                              \
-    b = u ? adj_blocks<L, C, true>(P, cap_blocks) : adj_blocks<L, C, false>(P, cap_blocks); \
+    b = v == 0 ? adj_blocks<L, C, 0>(P, cap_blocks)                                        \
+               : v == 1 ? adj_blocks<L, C, 1>(P, cap_blocks)                               \
+                        : v == 2 ? adj_blocks<L, C, 2>(P, cap_blocks)                      \
+                                 : adj_blocks<L, C, 3>(P, cap_blocks);                     \
     per = adj_block_bytes<L, C>(P);                                                        \
   }
   RTB_ADJ_LAYOUTS(X)
@@ -922,7 +953,7 @@ static int fixed_scratch_address(float **out) {
   return RT_OK;
 }
 
-template <int LPR, int CPL, bool UNIF>
+template <int LPR, int CPL, int VAR>
 static int launch_adj_fixed_t(const MarchParams &P, const float *dLdc, const float *target,
                               float *cube_out, const rt_grads &G, cudaStream_t stream,
                               float *scratch) {
@@ -935,11 +966,11 @@ static int launch_adj_fixed_t(const MarchParams &P, const float *dLdc, const flo
                      "allocation-free adjoint: %d samples per ray need %zu bytes of checkpoint "
                      "scratch per block, above the %zu bytes the fixed array gives them",
                      P.n_samples, per_block, ck_room);
-  long long blocks = adj_blocks<LPR, CPL, UNIF>(P, 0);
+  long long blocks = adj_blocks<LPR, CPL, VAR>(P, 0);
   const long long fit = (long long)(ck_room / per_block);
   if (blocks > fit) blocks = fit;
   const AdjScratch a = plan_scratch(P, blocks, blocks * per_block, kFixedScratchBytes);
-  return run_adj<LPR, CPL, UNIF>(P, dLdc, target, cube_out, G, nullptr, nullptr, blocks, a,
+  return run_adj<LPR, CPL, VAR>(P, dLdc, target, cube_out, G, nullptr, nullptr, blocks, a,
                                  reinterpret_cast<char *>(scratch), stream);
 }
 
@@ -949,11 +980,14 @@ static int launch_adjoint_fixed(const MarchParams &P, const float *d, const floa
   if (npix == 0 || P.nch == 0) return zero_grads(P, G, plan_scratch(P, 1, 0, 0), nullptr, s);
   int LPR, CPL;
   adj_layout(P.nch, &LPR, &CPL);
-  const bool u = P.v_uniform != 0;
+  const int v = adj_variant(P);
 #define X(L, C)                                                           \
-  if (LPR == L && CPL == C)                                               \
-    return u ? launch_adj_fixed_t<L, C, true>(P, d, t, c, G, s, scr)      \
-             : launch_adj_fixed_t<L, C, false>(P, d, t, c, G, s, scr);
+  if (LPR == L && CPL == C) {                                             \
+    if (v == 0) return launch_adj_fixed_t<L, C, 0>(P, d, t, c, G, s, scr); \
+    if (v == 1) return launch_adj_fixed_t<L, C, 1>(P, d, t, c, G, s, scr); \
+    if (v == 2) return launch_adj_fixed_t<L, C, 2>(P, d, t, c, G, s, scr); \
+    return launch_adj_fixed_t<L, C, 3>(P, d, t, c, G, s, scr);            \
+  }
   RTB_ADJ_LAYOUTS(X)
 #undef X
   return set_error(RT_EINVAL, "no adjoint layout for %d channels", P.nch);

@@ -566,9 +566,8 @@ int rtb::check_adjoint_args(const MarchParams &P, const float *dL_dcube, const f
                        const rt_grads *grads) {
   if (!grads || !grads->dT || !grads->dn || !grads->dvt || !grads->dh_lo || !grads->dh_hi)
     return set_error(RT_EINVAL, "null gradient output");
-  if (P.vphi)
-    return set_error(RT_EINVAL, "the adjoint takes the Keplerian rotation only (vphi_kms must "
-                                "be NULL)");
+  if (P.vphi && !grads->dvphi)
+    return set_error(RT_EINVAL, "a rotation field needs its gradient output (grads->dvphi)");
   long long n = (long long)P.nx * P.ny * P.nch;
   if (n > 0 && ((dL_dcube == nullptr) == (target == nullptr)))
     return set_error(RT_EINVAL, "give exactly one of dL_dcube and target");

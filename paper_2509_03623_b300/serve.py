@@ -73,7 +73,8 @@ class Server:
         r.cube, r.dL_dcube, r.target = _addr(cube), _addr(dL_dcube), _addr(target)
         if grads is not None:
             r.grads = _rt.rt_grads(*[_addr(grads.get(k))
-                                     for k in ("T", "n_h2", "vturb", "h_lo", "h_hi", "loss")])
+                                     for k in ("T", "n_h2", "vturb", "h_lo", "h_hi", "loss",
+                                               "vphi")])
         r.fake_us = int(fake_us)
         return r, (v, fields, cube, dL_dcube, target, grads) + tuple(keep)
 

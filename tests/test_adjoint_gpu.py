@@ -14,9 +14,10 @@ FIELDS = ("T", "n_h2", "vturb", "h_lo", "h_hi")
 
 
 def grad_errors(got, ref):
-    """Per field: max |got - ref| / max |ref| and max relative error on entries >= 1% of max."""
+    """Per field: max |got - ref| / max |ref| and max relative error on entries >= 1% of max
+    (the five node fields, and the rotation field where both sides have it)."""
     out = {}
-    for k in FIELDS:
+    for k in FIELDS + (("vphi",) if "vphi" in got and "vphi" in ref else ()):
         g, r = np.asarray(got[k]), np.asarray(ref[k])
         m = np.abs(r).max()
         if m == 0:

@@ -70,10 +70,48 @@ def test_render_with_rotation_field_corner_quads(rt, orc):
     assert_cube_close(gpu_cube(rt, q), orc.render(q), label="rotation field, corner quads")
 
 
-def test_adjoint_rejects_rotation_field(rt):
+def vphi_adjoint_case(rt, orc, p, seed):
+    """GPU adjoint with a rotation field vs the oracle's (orc_render_adjoint_vphi), seeded with
+    dL/dcube = 2 (I - I*) against a fixed target."""
     import torch
+    from tests.test_adjoint_gpu import assert_grads_close, loss_target
+    tgt = loss_target(orc, p, seed)
+    cube_ref = orc.render(p)
+    dl = 2.0 * (cube_ref - tgt)
+    _, g_ref = orc.render_adjoint_vphi(p, dl)
+    dd = rt.DeviceDisk(p)
+    _, g = rt.rt_render_adjoint(p, dd, dL_dcube=torch.tensor(dl.astype(np.float32), device="cuda"),
+                                cube_out=None)
+    got = {k: g[k].cpu().numpy() for k in ("T", "n_h2", "vturb", "h_lo", "h_hi", "vphi")}
+    return assert_grads_close(got, g_ref, label="rotation field")
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_adjoint_with_rotation_field_vs_oracle(rt, orc, seed):
+    """64x32 grid, 64^2 px, 16 channels, 128 samples, the pressure-corrected rotation of the
+    disk as the field (node-array path)."""
+    p = synth.config_small(seed)
+    q = p.replace(vphi=orc.pressure_vphi(p).astype(np.float32).astype(np.float64))
+    print("rotation-field adjoint", vphi_adjoint_case(rt, orc, q, seed))
+
+
+def test_adjoint_with_rotation_field_corner_quads(rt, orc):
+    """A grid large enough for the corner quads (four per cell with a rotation field), 64
+    channels; the smooth disk of the forward test above."""
+    p = synth.disk(2, nr=256, nz=128, nx=96, ny=96, nch=64, vmax=6.0, n_samples=512,
+                   incl=47.0, pa=133.0, rings=3)
+    q = p.replace(vphi=orc.pressure_vphi(p).astype(np.float32).astype(np.float64))
+    print("rotation-field adjoint, corner quads", vphi_adjoint_case(rt, orc, q, 2))
+
+
+def test_adjoint_with_rotation_field_needs_its_gradient_output(rt):
+    import torch
+    from paper_2509_03623_b300 import _rt
     p = synth.config_small(0)
     q = p.replace(vphi=np.full((p.nz, p.nr), 3.0))
-    with pytest.raises(rt.RTError, match="Keplerian"):
-        rt.rt_render_adjoint(q, rt.DeviceDisk(q),
-                             dL_dcube=torch.zeros((q.nch, q.ny, q.nx), device="cuda"))
+    dd = rt.DeviceDisk(q)
+    grads = {k: torch.zeros(tuple(t.shape), dtype=torch.float64, device="cuda")
+             for k, t in zip(("T", "n_h2", "vturb", "h_lo", "h_hi"), dd.tensors())}
+    with pytest.raises(rt.RTError, match="dvphi"):
+        rt.rt_render_adjoint_noalloc(q, dd, None, grads,
+                                     dL_dcube=torch.zeros((q.nch, q.ny, q.nx), device="cuda"))
