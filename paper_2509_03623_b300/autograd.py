@@ -18,19 +18,22 @@ from . import _rt
 
 
 class _Fields:
-    def __init__(self, T, n, vt, hlo, hhi):
+    def __init__(self, T, n, vt, hlo, hhi, vphi=None):
         self.T, self.n_h2, self.vturb, self.h_lo, self.h_hi = T, n, vt, hlo, hhi
+        self.vphi = vphi
 
     def tensors(self):
         return self.T, self.n_h2, self.vturb, self.h_lo, self.h_hi
 
 
 class RenderFn(torch.autograd.Function):
-    """cube = render(T, n_H2, v_turb, h_lo, h_hi) for a fixed problem geometry/view/line."""
+    """cube = render(T, n_H2, v_turb, h_lo, h_hi[, v_phi]) for a fixed problem geometry/view/
+    line (v_phi: an optional rotation field, Keplerian rotation when None)."""
 
     @staticmethod
-    def forward(ctx, T, n, vt, hlo, hhi, problem):
-        ts = [x.detach().contiguous().float() for x in (T, n, vt, hlo, hhi)]
+    def forward(ctx, T, n, vt, hlo, hhi, vphi, problem):
+        ins = (T, n, vt, hlo, hhi) + ((vphi,) if vphi is not None else ())
+        ts = [x.detach().contiguous().float() for x in ins]
         ctx.save_for_backward(*ts)
         ctx.problem = problem
         return _rt.rt_render(problem, _Fields(*ts))
@@ -40,13 +43,17 @@ class RenderFn(torch.autograd.Function):
         ts = ctx.saved_tensors
         _, g = _rt.rt_render_adjoint(ctx.problem, _Fields(*ts),
                                      dL_dcube=grad_cube.contiguous().float(), cube_out=None)
-        outs = [g[k].to(t.dtype) for k, t in zip(("T", "n_h2", "vturb", "h_lo", "h_hi"), ts)]
+        keys = ("T", "n_h2", "vturb", "h_lo", "h_hi", "vphi")[:len(ts)]
+        outs = [g[k].to(t.dtype) for k, t in zip(keys, ts)]
+        if len(ts) == 5:
+            outs.append(None)
         return (*outs, None)
 
 
-def render(problem, T, n, vt, hlo, hhi):
-    """Differentiable forward render (CUDA tensors, float32 fields)."""
-    return RenderFn.apply(T, n, vt, hlo, hhi, problem)
+def render(problem, T, n, vt, hlo, hhi, vphi=None):
+    """Differentiable forward render (CUDA tensors, float32 fields; vphi an optional rotation
+    field)."""
+    return RenderFn.apply(T, n, vt, hlo, hhi, vphi, problem)
 
 
 class FieldChainFn(torch.autograd.Function):

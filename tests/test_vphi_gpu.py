@@ -115,3 +115,24 @@ def test_adjoint_with_rotation_field_needs_its_gradient_output(rt):
     with pytest.raises(rt.RTError, match="dvphi"):
         rt.rt_render_adjoint_noalloc(q, dd, None, grads,
                                      dL_dcube=torch.zeros((q.nch, q.ny, q.nx), device="cuda"))
+
+
+def test_autograd_render_with_rotation_field(rt, orc):
+    """RenderFn with a rotation field: the rotation field's gradient (and the others) equal
+    those of the explicit adjoint call."""
+    import torch
+    from paper_2509_03623_b300 import autograd
+    p = synth.config_small(3)
+    q = p.replace(vphi=orc.pressure_vphi(p).astype(np.float32).astype(np.float64))
+    dd = rt.DeviceDisk(q)
+    ins = [t.clone().requires_grad_(True) for t in dd.tensors()]
+    vp = dd.vphi.clone().requires_grad_(True)
+    cube = autograd.render(q, *ins, vphi=vp)
+    w = torch.randn(tuple(cube.shape), device="cuda", generator=torch.Generator("cuda").manual_seed(4))
+    (cube * w).sum().backward()
+    _, g = rt.rt_render_adjoint(q, dd, dL_dcube=w.contiguous(), cube_out=None)
+    for got, k in zip(ins + [vp], ("T", "n_h2", "vturb", "h_lo", "h_hi", "vphi")):
+        want = g[k].float()
+        scale = float(want.abs().max())
+        assert scale > 0, k
+        assert float((got.grad - want).abs().max()) <= 1e-5 * scale, k
