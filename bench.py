@@ -52,10 +52,10 @@ except (OSError, ValueError):
 MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 16)
 # DRAM bytes of one forward launch on the observation-scale workload (ncu, dram__bytes_read +
 # dram__bytes_write; the cube stays in L2 at the end of the launch)
-FWD_DRAM_BYTES = 3_336_704 + 26_624
+FWD_DRAM_BYTES = 3_334_912 + 25_600
 # DRAM bytes (read + write) of one fused-adjoint launch on the same workload (ncu capture of
 # march_adj_kernel<8, 8, 1>; most of it is the per-segment sample records reaching DRAM)
-ADJ_DRAM_BYTES = 52_802_560 + 501_973_248
+ADJ_DRAM_BYTES = 52_092_416 + 501_120_768
 N_SM = 148
 SM_MAX_MHZ = 2032.0
 
