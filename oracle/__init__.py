@@ -118,6 +118,7 @@ def _load():
                                                    dp, dp, dp, C.c_int]
             lib.orc_field_chain.argtypes = [pp, C.POINTER(_Chain), dp, dp, dp, dp, dp]
             lib.orc_pressure_vphi.argtypes = [pp, dp, dp, dp]
+            lib.orc_pressure_vphi_adjoint.argtypes = [pp, dp, dp, dp, dp, dp]
             lib.orc_field_chain_adjoint.argtypes = [pp, C.POINTER(_Chain), dp, dp, dp, dp, dp]
             _lib = lib
     return _lib
@@ -423,6 +424,20 @@ def field_chain_adjoint(p, chain, T=None, g_n=None, g_lo=None, g_hi=None):
     if rc != 0:
         raise ValueError("orc_field_chain_adjoint: invalid arguments")
     return gT
+
+
+def pressure_vphi_adjoint(p, g_v, n_h2=None, T=None):
+    """Reverse mode of pressure_vphi: (dL/dn_h2, dL/dT) [nz][nr] from dL/dvphi [nz][nr]."""
+    lib = _load()
+    pk = _Packed(p)
+    n = np.ascontiguousarray(np.asarray(p.n_h2 if n_h2 is None else n_h2, dtype=np.float64))
+    Tg = np.ascontiguousarray(np.asarray(p.T if T is None else T, dtype=np.float64))
+    gv = np.ascontiguousarray(np.asarray(g_v, dtype=np.float64))
+    gn, gT = np.zeros((p.nz, p.nr)), np.zeros((p.nz, p.nr))
+    if lib.orc_pressure_vphi_adjoint(C.byref(pk.s), _dptr(n), _dptr(Tg), _dptr(gv), _dptr(gn),
+                                     _dptr(gT)) != 0:
+        raise ValueError("orc_pressure_vphi_adjoint: invalid arguments")
+    return gn, gT
 
 
 def pressure_vphi(p, n_h2=None, T=None):

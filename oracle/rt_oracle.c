@@ -1192,6 +1192,78 @@ static double axis_diff(const double *F, long long stride, int n, int k, double 
   return (F[(k + 1) * stride] - F[(k - 1) * stride]) / (2.0 * h);
 }
 
+/* adds g c_l to G[l stride] for the coefficients c_l of axis_diff at node k */
+static void axis_diff_adjoint(double *G, long long stride, int n, int k, double h, double g) {
+  if (n == 2) {
+    G[0] += -g / h;
+    G[stride] += g / h;
+  } else if (k == 0) {
+    G[0] += -3.0 * g / (2.0 * h);
+    G[stride] += 4.0 * g / (2.0 * h);
+    G[2 * stride] += -g / (2.0 * h);
+  } else if (k == n - 1) {
+    G[k * stride] += 3.0 * g / (2.0 * h);
+    G[(k - 1) * stride] += -4.0 * g / (2.0 * h);
+    G[(k - 2) * stride] += g / (2.0 * h);
+  } else {
+    G[(k + 1) * stride] += g / (2.0 * h);
+    G[(k - 1) * stride] += -g / (2.0 * h);
+  }
+}
+
+/* Reverse mode of orc_pressure_vphi (see rt_oracle.h). */
+int orc_pressure_vphi_adjoint(const orc_problem *p, const double *n_h2, const double *T,
+                              const double *g_v, double *g_n, double *g_T) {
+  if (!p || !n_h2 || !T || !g_v || !g_n || !g_T || p->nr < 2 || p->nz < 2) return -1;
+  const int nr = p->nr, nz = p->nz;
+  const long long G = (long long)nr * nz;
+  double *P = (double *)malloc(sizeof(double) * G);
+  double *gP = (double *)calloc(G, sizeof(double));
+  if (!P || !gP) {
+    free(P);
+    free(gP);
+    return -1;
+  }
+  for (long long k = 0; k < G; k++) {
+    P[k] = n_h2[k] * K_BOLTZ * T[k];
+    g_n[k] = 0.0;
+    g_T[k] = 0.0;
+  }
+  const double hu = p->r_log ? log(p->r_out_au / p->r_in_au) / (nr - 1)
+                             : (p->r_out_au - p->r_in_au) * AU_CM / (nr - 1);
+  const double hw = p->zr_max / (nz - 1);
+  const double GM = GM_SUN * p->mstar_msun, m = p->m_mol_amu * AMU_G;
+  for (int j = 0; j < nz; j++) {
+    const double w = hw * j;
+    for (int i = 0; i < nr; i++) {
+      const long long k = (long long)j * nr + i;
+      if (!(n_h2[k] > 0.0)) continue; /* the Keplerian term alone: no dependence on n, T */
+      const double r = node_r_au(p, i) * AU_CM, z = w * r;
+      const double kep = GM * r * r / pow(r * r + z * z, 1.5);
+      const double dPu = axis_diff(P + (long long)j * nr, 1, nr, i, hu);
+      const double dPw = axis_diff(P + i, nr, nz, j, hw);
+      const double dudr = p->r_log ? 1.0 / r : 1.0;
+      const double dPdr = dudr * dPu - (w / r) * dPw;
+      const double v2 = kep + r / (m * n_h2[k]) * dPdr;
+      if (!(v2 > 0.0)) continue; /* clamped to 0: zero derivative */
+      /* v [km/s] = sqrt(v2) / 1e5 */
+      const double g2 = g_v[k] / (2.0 * sqrt(v2) * 1e5);
+      g_n[k] += -g2 * r / (m * n_h2[k] * n_h2[k]) * dPdr;
+      const double gdPdr = g2 * r / (m * n_h2[k]);
+      axis_diff_adjoint(gP + (long long)j * nr, 1, nr, i, hu, gdPdr * dudr);
+      axis_diff_adjoint(gP + i, nr, nz, j, hw, -gdPdr * (w / r));
+    }
+  }
+  /* P = n k T */
+  for (long long k = 0; k < G; k++) {
+    g_n[k] += gP[k] * K_BOLTZ * T[k];
+    g_T[k] += gP[k] * K_BOLTZ * n_h2[k];
+  }
+  free(P);
+  free(gP);
+  return 0;
+}
+
 int orc_pressure_vphi(const orc_problem *p, const double *n_h2, const double *T, double *vphi) {
   if (!p || !n_h2 || !T || !vphi || p->nr < 2 || p->nz < 2) return -1;
   const int nr = p->nr, nz = p->nz;

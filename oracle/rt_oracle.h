@@ -195,6 +195,13 @@ int orc_field_chain_adjoint(const orc_problem *p, const orc_chain *c, const doub
    p->nr, nz, r_log, r_in_au, r_out_au, zr_max, mstar_msun, m_mol_amu. vphi [nz][nr] km/s. */
 int orc_pressure_vphi(const orc_problem *p, const double *n_h2, const double *T, double *vphi);
 
+/* Reverse mode of orc_pressure_vphi for a scalar loss L: from dL/dvphi [nz][nr] (per km/s)
+   writes dL/dn_h2 and dL/dT [nz][nr] (overwritten) through the pressure term (the difference
+   stencils transposed and the 1/rho factor); nodes clamped to v_phi = 0 and nodes without gas
+   (Keplerian term only) contribute nothing. */
+int orc_pressure_vphi_adjoint(const orc_problem *p, const double *n_h2, const double *T,
+                              const double *g_v, double *g_n, double *g_T);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,3 +93,29 @@ def test_zero_rotation_field_gives_symmetric_spectrum(orc):
     p = synth.config_small(1).replace(nx=12, ny=12, n_samples=64, v_kms=np.linspace(-3, 3, 13))
     cube = orc.render(p.replace(vphi=np.zeros((p.nz, p.nr))))
     np.testing.assert_allclose(cube, cube[::-1], rtol=1e-9, atol=1e-12 * np.abs(cube).max())
+
+
+@pytest.mark.parametrize("r_log,nr,nz", [(1, 9, 7), (0, 6, 5), (1, 2, 2), (1, 12, 3)])
+def test_rotation_reverse_mode_matches_central_differences(orc, r_log, nr, nz):
+    """dL/dn_H2 and dL/dT of L = sum g v_phi from orc_pressure_vphi_adjoint equal central
+    differences of orc_pressure_vphi on every node (log and linear radii, two-node axes with
+    their first-order stencil, one-sided edges). The fields keep v_phi^2 > 0 away from 0 so no
+    node sits on the clamp."""
+    p = grid_problem(nr=nr, nz=nz, r_log=r_log)
+    rng = np.random.default_rng(nr * 10 + nz)
+    n = 1e7 * np.exp(rng.uniform(-0.3, 0.3, (nz, nr)))
+    T = 30.0 * np.exp(rng.uniform(-0.3, 0.3, (nz, nr)))
+    g = rng.standard_normal((nz, nr))
+    v0 = orc.pressure_vphi(p, n, T)
+    assert np.all(v0 > 0)
+    gn, gT = orc.pressure_vphi_adjoint(p, g, n, T)
+    loss = lambda nn, TT: float((g * orc.pressure_vphi(p, nn, TT)).sum())
+    for arr, grad, is_n in ((n, gn, True), (T, gT, False)):
+        for k in range(arr.size):
+            h = 1e-6 * arr.flat[k]
+            ap, am = arr.copy(), arr.copy()
+            ap.flat[k] += h
+            am.flat[k] -= h
+            fd = ((loss(ap, T) - loss(am, T)) if is_n else (loss(n, ap) - loss(n, am))) / (2 * h)
+            scale = np.abs(grad).max()
+            assert grad.flat[k] == pytest.approx(fd, rel=1e-5, abs=1e-7 * scale), (is_n, k)
