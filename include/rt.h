@@ -403,6 +403,21 @@ int rt_pressure_vphi(const rt_grid *grid, const rt_geom *geom, const rt_line *li
                      const float *n_h2, const float *T_K, float *vphi_kms, void *stream);
 
 /*
+ * rt_pressure_vphi_adjoint -- reverse mode of rt_pressure_vphi for a scalar loss L: from
+ * g_vphi = dL/dvphi_kms (DEVICE [nz][nr] float64, e.g. rt_render_adjoint's grads->dvphi)
+ * writes g_n = dL/dn_h2 and g_T = dL/dT_K (DEVICE [nz][nr] float64, caller-allocated,
+ * overwritten) through the pressure term: the 1/rho factor and the difference stencils
+ * transposed. Nodes clamped to v_phi = 0 and nodes with n_H2 = 0 (Keplerian term only)
+ * contribute nothing. Arguments grid, geom, line, n_h2 and T_K as for rt_pressure_vphi.
+ * FP32 per node, the stencil scatter with FP64 atomics into a stream-ordered scratch of 8 bytes
+ * per node.
+ * Returns RT_OK, RT_EINVAL (as rt_pressure_vphi), RT_ENOMEM or RT_ECUDA.
+ */
+int rt_pressure_vphi_adjoint(const rt_grid *grid, const rt_geom *geom, const rt_line *line,
+                             const float *n_h2, const float *T_K, const double *g_vphi,
+                             double *g_n, double *g_T, void *stream);
+
+/*
  * rt_surface_powerlaw_grad -- chain rule from surface-node gradients to the parameters of a
  * power-law surface h(r) = c (r / 100 au)^p m(r) (m: any fixed modulation):
  *   out[0] = dL/dc = sum_i dL/dh_i h_i / c,   out[1] = dL/dp = sum_i dL/dh_i h_i ln(r_i/100 au),

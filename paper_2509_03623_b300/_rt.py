@@ -161,6 +161,10 @@ def lib():
             L.rt_pressure_vphi.argtypes = [P(rt_grid), P(rt_geom), P(rt_line), C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p]
             L.rt_pressure_vphi.restype = C.c_int
+            L.rt_pressure_vphi_adjoint.argtypes = [P(rt_grid), P(rt_geom), P(rt_line), C.c_void_p,
+                                                   C.c_void_p, C.c_void_p, C.c_void_p,
+                                                   C.c_void_p, C.c_void_p]
+            L.rt_pressure_vphi_adjoint.restype = C.c_int
             L.rt_render3d.argtypes = [P(rt_grid3), P(rt_fields3), P(rt_geom), P(rt_view),
                                       P(rt_line), C.c_void_p, C.c_void_p]
             L.rt_render3d.restype = C.c_int
@@ -449,6 +453,28 @@ def rt_field_chain_adjoint(problem, T, chain, g_n=None, g_lo=None, g_hi=None, ou
                                        opt(g_n), opt(g_lo), opt(g_hi), _ptr(out),
                                        stream_handle(stream)))
     return out
+
+
+def rt_pressure_vphi_adjoint(problem, n_h2, T, g_vphi, stream=None):
+    """Reverse mode of rt_pressure_vphi: (dL/dn_h2, dL/dT), CUDA float64 [nz][nr], from
+    dL/dvphi (CUDA float64 [nz][nr])."""
+    import torch
+    shp = (int(problem.nz), int(problem.nr))
+    for name, t, dt in (("n_h2", n_h2, torch.float32), ("T", T, torch.float32),
+                        ("g_vphi", g_vphi, torch.float64)):
+        if not t.is_cuda or t.dtype != dt or not t.is_contiguous() or tuple(t.shape) != shp:
+            raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor of shape {shp}")
+    g = rt_grid(int(problem.nr), int(problem.nz), int(problem.r_log), float(problem.r_in_au),
+                float(problem.r_out_au), float(problem.zr_max))
+    o = rt_geom(float(problem.incl_deg), float(problem.pa_deg), float(problem.dist_pc),
+                float(problem.mstar_msun), float(problem.vsys_kms))
+    ln = rt_line(float(problem.nu0_hz), float(problem.A_ul), float(problem.B_rot_hz),
+                 float(problem.m_co_amu), float(problem.m_mol_amu), int(problem.J_u))
+    gn = torch.empty(shp, dtype=torch.float64, device=T.device)
+    gT = torch.empty(shp, dtype=torch.float64, device=T.device)
+    check(lib().rt_pressure_vphi_adjoint(C.byref(g), C.byref(o), C.byref(ln), _ptr(n_h2), _ptr(T),
+                                         _ptr(g_vphi), _ptr(gn), _ptr(gT), stream_handle(stream)))
+    return gn, gT
 
 
 def rt_pressure_vphi(problem, n_h2, T, out=None, stream=None):

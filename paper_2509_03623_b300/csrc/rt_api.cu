@@ -607,6 +607,26 @@ extern "C" int rt_pressure_vphi(const rt_grid *grid, const rt_geom *geom, const 
   return rc;
 }
 
+extern "C" int rt_pressure_vphi_adjoint(const rt_grid *grid, const rt_geom *geom,
+                                        const rt_line *line, const float *n_h2,
+                                        const float *T_K, const double *g_vphi, double *g_n,
+                                        double *g_T, void *stream) {
+  if (!grid || !geom || !line || !n_h2 || !T_K || !g_vphi || !g_n || !g_T)
+    return set_error(RT_EINVAL, "null argument");
+  if (grid->nr < 2 || grid->nz < 2) return set_error(RT_EINVAL, "grid needs >= 2 nodes per axis");
+  if (!(grid->r_in_au > 0) || !(grid->r_out_au > grid->r_in_au) || !(grid->zr_max > 0) ||
+      !is_finite(grid->r_out_au) || !is_finite(grid->zr_max))
+    return set_error(RT_EINVAL, "invalid grid extent");
+  if (!(geom->mstar_msun >= 0) || !is_finite(geom->mstar_msun))
+    return set_error(RT_EINVAL, "stellar mass must be finite and >= 0");
+  if (!(line->m_mol_amu > 0) || !is_finite(line->m_mol_amu))
+    return set_error(RT_EINVAL, "mean molecular mass must be > 0");
+  int rc = launch_pressure_vphi_adjoint(*grid, *geom, *line, n_h2, T_K, g_vphi, g_n, g_T,
+                                        (cudaStream_t)stream);
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
 static int check_chain_args(const rt_grid *grid, const rt_geom *geom, const rt_line *line,
                             const rt_chain *chain) {
   if (grid->nr < 2 || grid->nz < 2) return set_error(RT_EINVAL, "grid needs >= 2 nodes per axis");

@@ -233,6 +233,113 @@ int launch_pressure_vphi(const rt_grid &g, const rt_geom &geo, const rt_line &li
   return RT_OK;
 }
 
+// Reverse mode of the rotation: from dL/dv_phi (per km/s) to dL/dn_H2 and dL/dT. Per node with
+// gas and v_phi^2 > 0 (clamped and gas-free nodes contribute nothing): dL/dv^2 = g / (2 v),
+//   the direct 1/n term: dL/dn_k += -dL/dv^2 (r / n_k^2) (k/m) dP/dr,
+//   the pressure gradient: dL/dQ_l += dL/dv^2 (r / n_k) (k/m) (du/dr c^u_l - (w/r) c^w_l) for the
+//   stencil coefficients c of the two differences (Q = n T), scattered with FP64 atomics;
+// then dL/dn_l += dL/dQ_l T_l and dL/dT_l = dL/dQ_l n_l.
+__device__ __forceinline__ void axis_d_adjoint(double *G, long long base, long long s, int cnt,
+                                               int a, float h, float g) {
+  if (cnt == 2) {
+    atomicAdd(G + base, (double)(-g / h));
+    atomicAdd(G + base + s, (double)(g / h));
+    return;
+  }
+  const float c = g / (2.0f * h);
+  if (a == 0) {
+    atomicAdd(G + base, (double)(-3.0f * c));
+    atomicAdd(G + base + s, (double)(4.0f * c));
+    atomicAdd(G + base + 2 * s, (double)(-c));
+    return;
+  }
+  const long long k = base + a * s;
+  if (a == cnt - 1) {
+    atomicAdd(G + k, (double)(3.0f * c));
+    atomicAdd(G + k - s, (double)(-4.0f * c));
+    atomicAdd(G + k - 2 * s, (double)c);
+    return;
+  }
+  atomicAdd(G + k + s, (double)c);
+  atomicAdd(G + k - s, (double)(-c));
+}
+
+__global__ void pressure_vphi_adjoint_kernel(const VphiDev V, const float *__restrict__ n,
+                                             const float *__restrict__ T,
+                                             const double *__restrict__ g_v,
+                                             double *__restrict__ g_n, double *gQ) {
+  const long long total = (long long)V.nr * V.nz;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(k / V.nr), i = (int)(k - (long long)j * V.nr);
+    const float t = (float)i / (float)(V.nr - 1);
+    const float r = V.r_log ? V.r_in * expf(V.lnratio * t) : fmaf(V.r_out - V.r_in, t, V.r_in);
+    const float w = V.hw * (float)j;
+    const float d = fmaf(w * w, r * r, r * r);
+    const float nk = __ldg(n + k);
+    double gnk = 0.0;
+    if (nk > 0.0f) {
+      const float dPu = axis_d(n, T, (long long)j * V.nr, 1, V.nr, i, V.hu);
+      const float dPw = axis_d(n, T, i, V.nr, V.nz, j, V.hw);
+      const float dudr = V.r_log ? 1.0f / r : 1.0f;
+      const float dPdr = fmaf(dudr, dPu, -(w / r) * dPw);
+      const float v2 = fmaf(r / nk, V.kpm * dPdr, V.gm * r * r / (d * sqrtf(d)));
+      if (v2 > 0.0f) {
+        const float g2 = (float)g_v[k] / (2.0f * sqrtf(v2));
+        gnk = (double)(-g2 * (r / (nk * nk)) * V.kpm * dPdr);
+        const float gd = g2 * (r / nk) * V.kpm;
+        axis_d_adjoint(gQ, (long long)j * V.nr, 1, V.nr, i, V.hu, gd * dudr);
+        axis_d_adjoint(gQ, i, V.nr, V.nz, j, V.hw, -gd * (w / r));
+      }
+    }
+    g_n[k] = gnk;
+  }
+}
+
+__global__ void pressure_vphi_adjoint_finish(long long total, const float *__restrict__ n,
+                                             const float *__restrict__ T,
+                                             const double *__restrict__ gQ, double *g_n,
+                                             double *__restrict__ g_T) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    g_n[k] += gQ[k] * (double)__ldg(T + k);
+    g_T[k] = gQ[k] * (double)__ldg(n + k);
+  }
+}
+
+int launch_pressure_vphi_adjoint(const rt_grid &g, const rt_geom &geo, const rt_line &line,
+                                 const float *n, const float *T, const double *g_v, double *g_n,
+                                 double *g_T, cudaStream_t stream) {
+  VphiDev V;
+  V.nr = g.nr;
+  V.nz = g.nz;
+  V.r_log = g.r_log;
+  V.r_in = (float)g.r_in_au;
+  V.r_out = (float)g.r_out_au;
+  V.lnratio = (float)log(g.r_out_au / g.r_in_au);
+  V.hu = g.r_log ? (float)(log(g.r_out_au / g.r_in_au) / (g.nr - 1))
+                 : (float)((g.r_out_au - g.r_in_au) / (g.nr - 1));
+  V.hw = (float)(g.zr_max / (g.nz - 1));
+  V.gm = (float)(kChainGMsun * geo.mstar_msun / kChainAu / 1e10);
+  V.kpm = (float)(kChainK / (line.m_mol_amu * kChainAmu) / 1e10);
+  const long long total = (long long)g.nr * g.nz;
+  double *gQ = nullptr;
+  cudaError_t e = stream_alloc((void **)&gQ, (size_t)total * sizeof(double), stream);
+  if (e != cudaSuccess)
+    return set_error(RT_ENOMEM, "rotation adjoint scratch: %s", cudaGetErrorString(e));
+  e = cudaMemsetAsync(gQ, 0, (size_t)total * sizeof(double), stream);
+  const long long blocks = (total + 255) / 256;
+  const unsigned nb = (unsigned)(blocks < 4096 ? blocks : 4096);
+  if (e == cudaSuccess) {
+    pressure_vphi_adjoint_kernel<<<nb, 256, 0, stream>>>(V, n, T, g_v, g_n, gQ);
+    pressure_vphi_adjoint_finish<<<nb, 256, 0, stream>>>(total, n, T, gQ, g_n, g_T);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(gQ, stream);
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "rotation adjoint: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
 // Reverse mode of the chain for a scalar loss: dL/dT per node from dL/dn_H2 and dL/d(surfaces),
 // one thread per radius column (the forward quantities are recomputed). With
 // e_j = exp(-I_j - ln(T_j / T_0)), S = sum_j w_j e_j (trapezoid weights w_j), n_j = Cn e_j,

@@ -532,6 +532,9 @@ cudaError_t stream_alloc(void **p, size_t bytes, cudaStream_t stream);
 size_t cell_bytes(const MarchParams &P);
 int launch_pressure_vphi(const rt_grid &g, const rt_geom &geo, const rt_line &line,
                          const float *n, const float *T, float *vphi, cudaStream_t stream);
+int launch_pressure_vphi_adjoint(const rt_grid &g, const rt_geom &geo, const rt_line &line,
+                                 const float *n, const float *T, const double *g_v, double *g_n,
+                                 double *g_T, cudaStream_t stream);
 int launch_field_chain(const rt_grid &g, const rt_geom &geo, const rt_line &line,
                        const rt_chain &c, const float *T, float *n, float *N, float *h_lo,
                        float *h_hi, cudaStream_t stream);

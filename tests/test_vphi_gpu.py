@@ -16,6 +16,7 @@ import pytest
 from paper_2509_03623_b300 import synth
 from tests.cubecheck import assert_cube_close
 from tests.test_forward_gpu import gpu_cube, rt  # noqa: F401  (module fixture)
+from tests.test_oracle_vphi import kepler_kms
 
 pytestmark = pytest.mark.gpu
 
@@ -136,3 +137,32 @@ def test_autograd_render_with_rotation_field(rt, orc):
         scale = float(want.abs().max())
         assert scale > 0, k
         assert float((got.grad - want).abs().max()) <= 1e-5 * scale, k
+
+
+@pytest.mark.parametrize("r_log,nr,nz", [(1, 64, 32), (0, 33, 17), (1, 512, 256)])
+def test_rotation_reverse_mode_vs_oracle(rt, orc, r_log, nr, nz):
+    """rt_pressure_vphi_adjoint vs orc_pressure_vphi_adjoint from the same float32 fields. The
+    kernel evaluates the pressure term in FP32 (differences of n T: ~1e-6 relative of the
+    term), so entries above 1 % of the largest agree to 1e-3 relative and all to 1e-5 of it."""
+    import torch
+    p = synth.config_small(4).replace(nr=nr, nz=nz, r_log=r_log, r_in_au=30.0, r_out_au=600.0)
+    rng = np.random.default_rng(nr + nz)
+    # node-to-node noise scaled with the node count, so the pressure term (differences over
+    # the node spacing) stays a correction: near the clamp v_phi -> 0 the derivative grows as
+    # 1 / v_phi and FP32 against FP64 differences there say nothing about the kernel
+    amp = 0.05 * min(1.0, 32.0 / nr)
+    n = (1e7 * np.exp(rng.uniform(-amp, amp, (nz, nr)))).astype(np.float32)
+    T = (30.0 * np.exp(rng.uniform(-amp, amp, (nz, nr)))).astype(np.float32)
+    v = orc.pressure_vphi(p, n.astype(np.float64), T.astype(np.float64))
+    assert np.all(v > 0.5 * kepler_kms(p)), "a node near the clamp"
+    g = rng.standard_normal((nz, nr))
+    gn, gT = rt.rt_pressure_vphi_adjoint(p, torch.tensor(n, device="cuda"),
+                                         torch.tensor(T, device="cuda"),
+                                         torch.tensor(g, device="cuda"))
+    rn, rT = orc.pressure_vphi_adjoint(p, g, n.astype(np.float64), T.astype(np.float64))
+    for got, ref, k in ((gn.cpu().numpy(), rn, "n"), (gT.cpu().numpy(), rT, "T")):
+        scale = np.abs(ref).max()
+        assert scale > 0, k
+        assert np.abs(got - ref).max() <= 1e-5 * scale, k
+        big = np.abs(ref) >= 0.01 * scale
+        assert (np.abs(got - ref)[big] / np.abs(ref)[big]).max() <= 1e-3, k
