@@ -129,9 +129,7 @@ def test_results_identical_alone_and_in_mix(serve, orc):
     outs = []
     with serve.Server(mem_budget_bytes=1 << 30, max_inflight=4) as s:
         tickets = []
-        peak_running = 0
         for (p, adj), (dd, tgt, _, _) in zip(reqs, alone):
-            peak_running = max(peak_running, s.stats()["running"])
             cube = torch.full((p.nch, p.ny, p.nx), float("nan"), device="cuda")
             if adj:
                 g = {k: torch.empty_like(v) for k, v in zip(
@@ -143,12 +141,13 @@ def test_results_identical_alone_and_in_mix(serve, orc):
             else:
                 tickets.append(s.submit_render(p, dd, cube))
                 outs.append((cube, None))
-        peak_running = max([peak_running] + [s.stats()["running"] for _ in range(50)])
         for t in tickets:
             state, lat = s.wait(t, 60000)
             assert state == "done", s.error(t)
             assert lat > 0
-    assert peak_running >= 1
+        # every request went through the server (whether any was seen running depends on how
+        # fast these small renders finish relative to the sampling, so it is not asserted)
+        assert s.stats()["completed"] >= len(tickets)
     for (cube, g), (_, _, ref_cube, ref_g) in zip(outs, alone):
         assert np.array_equal(cube.cpu().numpy(), ref_cube)
         if g is not None:
