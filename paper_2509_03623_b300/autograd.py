@@ -5,9 +5,11 @@ RenderFn: forward  -> rt_render (FP32 march)
                       march, FP64 gradient accumulation, cast to the dtype of the inputs)
 FieldChainFn: forward  -> rt_field_chain (T -> n_H2, h_lo, h_hi)
               backward -> rt_field_chain_adjoint
-so that with n, h_lo, h_hi = field_chain(problem, chain, T) and
-cube = render(problem, T, n, vt, h_lo, h_hi) a loss differentiates with respect to T through
-both the march and the chain.
+PressureVphiFn: forward  -> rt_pressure_vphi (n_H2, T -> v_phi)
+                backward -> rt_pressure_vphi_adjoint
+so that with n, h_lo, h_hi = field_chain(problem, chain, T), vphi = pressure_vphi(problem, n, T)
+and cube = render(problem, T, n, vt, h_lo, h_hi, vphi) a loss differentiates with respect to T
+through the march, the rotation and the chain.
 """
 
 from __future__ import annotations
@@ -79,3 +81,25 @@ class FieldChainFn(torch.autograd.Function):
 def field_chain(problem, chain, T):
     """Differentiable field chain: (n_H2, h_lo, h_hi) from the temperature grid T (CUDA)."""
     return FieldChainFn.apply(T, problem, chain)
+
+
+class PressureVphiFn(torch.autograd.Function):
+    """v_phi = rotation(n_H2, T) (pressure-corrected, km/s) for a fixed grid and line."""
+
+    @staticmethod
+    def forward(ctx, n, T, problem):
+        nf, Tf = n.detach().contiguous().float(), T.detach().contiguous().float()
+        ctx.save_for_backward(nf, Tf)
+        ctx.problem, ctx.dtypes = problem, (n.dtype, T.dtype)
+        return _rt.rt_pressure_vphi(problem, nf, Tf)
+
+    @staticmethod
+    def backward(ctx, g_v):
+        nf, Tf = ctx.saved_tensors
+        gn, gT = _rt.rt_pressure_vphi_adjoint(ctx.problem, nf, Tf, g_v.contiguous().double())
+        return gn.to(ctx.dtypes[0]), gT.to(ctx.dtypes[1]), None
+
+
+def pressure_vphi(problem, n, T):
+    """Differentiable pressure-corrected rotation [nz][nr] km/s from n_H2 and T (CUDA)."""
+    return PressureVphiFn.apply(n, T, problem)

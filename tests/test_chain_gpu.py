@@ -224,3 +224,42 @@ def test_autograd_through_the_chain(rt):
     scale = float(want.abs().max())
     assert scale > 0
     assert float((got - want).abs().max()) <= 1e-5 * scale
+
+
+def test_autograd_temperature_through_chain_rotation_and_render(rt, orc):
+    """T -> chain -> (n_H2, surfaces) -> rotation(n_H2, T) -> render: dL/dT by torch autograd
+    over the GPU steps vs the oracle's composition of its reverse modes (render with a rotation
+    field, rotation, chain), on the same float32 fields; the adjoint criterion of the render."""
+    import torch
+    from paper_2509_03623_b300 import autograd
+    from tests.test_oracle_chain_adjoint import chain_problem
+    p, rng = chain_problem(nr=48, nz=24, seed=21)
+    p = p.replace(nx=24, ny=24, v_kms=np.linspace(-4.0, 4.0, 16), n_samples=96,
+                  half_fov_au=330.0, vturb=np.full((24, 48), 0.05))
+    c = synth.chain_params(p)
+    T = torch.tensor(np.ascontiguousarray(p.T, dtype=np.float32), device="cuda",
+                     requires_grad=True)
+    vt = torch.tensor(np.ascontiguousarray(p.vturb, dtype=np.float32), device="cuda")
+    n, hlo, hhi = autograd.field_chain(p, c, T)
+    vphi = autograd.pressure_vphi(p, n, T)
+    cube = autograd.render(p, T, n, vt, hlo, hhi, vphi=vphi)
+    g = rng.standard_normal(tuple(cube.shape)) / float(cube.detach().abs().max())
+    gd = torch.tensor(g.astype(np.float32), device="cuda")
+    (cube * gd).sum().backward()
+    got = T.grad.double().cpu().numpy()
+    # the oracle's composition from the same float32 intermediate fields
+    T64 = p.T.astype(np.float32).astype(np.float64)
+    f = orc.field_chain(p, c, T64)
+    n32 = n.detach().cpu().numpy().astype(np.float64)
+    v32 = vphi.detach().cpu().numpy().astype(np.float64)
+    q = p.replace(T=T64, n_h2=n32, h_lo=hlo.detach().cpu().numpy().astype(np.float64),
+                  h_hi=hhi.detach().cpu().numpy().astype(np.float64), vphi=v32)
+    _, rg = orc.render_adjoint_vphi(q, g.astype(np.float32).astype(np.float64))
+    gn_rot, gT_rot = orc.pressure_vphi_adjoint(p, rg["vphi"], n32, T64)
+    ref = rg["T"] + gT_rot + orc.field_chain_adjoint(p, c, T64, rg["n_h2"] + gn_rot,
+                                                    rg["h_lo"], rg["h_hi"])
+    assert np.all(np.abs(f["n_h2"] - n32) <= 1e-4 * np.abs(f["n_h2"]).max())
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 3e-4 * scale
+    big = np.abs(ref) >= 0.01 * scale
+    assert (np.abs(got - ref)[big] / np.abs(ref)[big]).max() <= 3e-3
