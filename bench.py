@@ -277,6 +277,8 @@ def chain_leg(dev, reps=50):
     gT = torch.empty((p.nz, p.nr), dtype=torch.float64, device=dev)
     ms_adj = graph_ms(lambda s: _rt.rt_field_chain_adjoint(p, T, c, gn, glo, ghi, out=gT,
                                                            stream=s))
+    gv = torch.tensor(rng.standard_normal((p.nz, p.nr)), device=dev)
+    ms_vadj = graph_ms(lambda s: _rt.rt_pressure_vphi_adjoint(p, ch["n_h2"], T, gv, stream=s))
     nodes = p.nr * p.nz
     gbs = 12.0 * nodes / (ms * 1e-3) / 1e9
     dd = _rt.DeviceDisk(p, dev)
@@ -294,7 +296,7 @@ def chain_leg(dev, reps=50):
     torch.cuda.synchronize()
     ms_render = e0.elapsed_time(e1) / 10
     return {"workload": f"chain_grid{p.nr}x{p.nz}", "ms": ms, "nodes": nodes,
-            "rotation_ms": ms_vphi, "chain_adjoint_ms": ms_adj,
+            "rotation_ms": ms_vphi, "chain_adjoint_ms": ms_adj, "rotation_adjoint_ms": ms_vadj,
             "render_chain_fields_rotation_ms": ms_render,
             "render_chain_fields_rotation_gevals": p.evals / (ms_render * 1e-3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": PEAKS.get("hbm_gbs", 6400.0),
