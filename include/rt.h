@@ -301,9 +301,9 @@ int rt_field_chain(const rt_grid *grid, const rt_geom *geom, const rt_line *line
  * that cell (which cell is piecewise constant in T); a surface pinned at 0 or zr_max has zero
  * derivative. The gradient of a render of the chain's fields with respect to T is g_T plus
  * the render adjoint's own grads->dT. Arguments grid, geom, line, chain and T_K as for
- * rt_field_chain. One thread per radius column, FP32 arithmetic with compensated running sums
- * (the forward quantities are recomputed); a stream-ordered scratch of 8 bytes per node from the
- * library's pool.
+ * rt_field_chain. One warp per radius column, FP32 arithmetic with the running sums as warp
+ * scans (the forward quantities are recomputed); a stream-ordered scratch of 8 bytes per node
+ * from the library's pool.
  * Returns RT_OK, RT_EINVAL (as rt_field_chain, or a null g_T), RT_ENOMEM or RT_ECUDA.
  */
 int rt_field_chain_adjoint(const rt_grid *grid, const rt_geom *geom, const rt_line *line,

@@ -341,7 +341,7 @@ int launch_pressure_vphi_adjoint(const rt_grid &g, const rt_geom &geo, const rt_
 }
 
 // Reverse mode of the chain for a scalar loss: dL/dT per node from dL/dn_H2 and dL/d(surfaces),
-// one thread per radius column (the forward quantities are recomputed). With
+// one warp per radius column (the forward quantities are recomputed). With
 // e_j = exp(-I_j - ln(T_j / T_0)), S = sum_j w_j e_j (trapezoid weights w_j), n_j = Cn e_j,
 // Cn = Sigma / (2 S m_mol), and the column N_j = sum_{k >= j} (dz / 2)(n_k + n_{k+1}):
 //   h_hi = dw (j* + (N_a - N_d) / (N_a - N_b)) -> dL/dN at the two nodes of its cell;
@@ -355,9 +355,9 @@ int launch_pressure_vphi_adjoint(const rt_grid &g, const rt_geom &geo, const rt_
 // dL/dn_j (kept in a second scratch column) and sum_j dL/dn_j e_j, pass 4 walks down with the
 // suffix sum of dL/dI and writes dL/dT (the FP64 inputs and output are converted once each:
 // conversions run on the FP64 pipe).
-// FP32 arithmetic (B300's FP64 rate is a small fraction of its FP32 rate; a first FP64
-// version took 3.7 ms on the 512 x 256 grid) with compensated running sums for I, S, the
-// column, the dot product and the suffix sum, and heights in units of the node spacing.
+// FP32 arithmetic (B300's FP64 rate is a small fraction of its FP32 rate; a first FP64 version
+// with one thread per column took 3.7 ms on the 512 x 256 grid, the FP32 one 0.22 ms), the
+// running sums as warp scans with a carry between 32-node chunks (0.022 ms).
 struct ChainAdjDev {
   int nr, nz, r_log;
   float r_in, r_out, zr_max;
@@ -367,123 +367,169 @@ struct ChainAdjDev {
   float T_freeze, N_dissoc;
 };
 
-// Compensated (Kahan-Babuska) running sum.
-struct KSum {
-  float s = 0.0f, c = 0.0f;
-  __device__ __forceinline__ void add(float x) {
-    const float t = s + x;
-    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
-    s = t;
+// warp scans over the 32 lanes: inclusive prefix (lane l: sum of lanes 0..l) and inclusive
+// suffix (lane l: sum of lanes l..31)
+__device__ __forceinline__ float warp_prefix(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
   }
-  __device__ __forceinline__ float value() const { return s + c; }
-};
+  return v;
+}
+__device__ __forceinline__ float warp_suffix(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float u = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane + o < 32) v += u;
+  }
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
+// One warp per radius column: lane l takes nodes 32 c + l of chunk c; the running integrals
+// (I upward, the column N and the suffix sum of dL/dI downward) are warp scans with a carry
+// between chunks, the crossings come from warp ballots.
 __global__ void field_chain_adjoint_kernel(const ChainAdjDev C, const float *__restrict__ T,
                                            const double *__restrict__ g_n,
                                            const double *__restrict__ g_lo,
                                            const double *__restrict__ g_hi, double *g_T,
                                            float *__restrict__ ev, float *__restrict__ gnv) {
   const int nr = C.nr, nz = C.nz;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int nch = (nz + 31) / 32;
+  for (long long ii = warp; ii < nr; ii += nwarps) {
+    const int i = (int)ii;
     const float t = (float)i / (float)(nr - 1);
     const float r_au = C.r_log ? C.r_in * powf(C.r_out / C.r_in, t) : C.r_in + (C.r_out - C.r_in) * t;
-    const float dz_au = C.zr_max / (float)(nz - 1) * r_au;  // node spacing [au]
+    const float dz_au = C.zr_max / (float)(nz - 1) * r_au;
     const float dz_cm = dz_au * (float)kChainAu;
     auto Tj = [&](int j) { return T[(long long)j * nr + i]; };
-    // gravity term g_j = A z / (r^2 + z^2)^{3/2} / T_j per au of height (z = j dz)
     auto grav = [&](int j) {
       const float z = dz_au * (float)j, d2 = r_au * r_au + z * z;
       return C.A * z / (d2 * sqrtf(d2)) / Tj(j);
     };
-    double *gT = g_T + i;  // node j: gT[j * nr]
-    float *ec = ev + i, *gc = gnv + i;  // scratch columns, node j at [j * nr]
+    auto at = [&](int j) { return (long long)j * nr + i; };
     const float T0 = Tj(0);
-    // pass 1: e_j (stored) and S / dz
-    KSum I, S;
-    float gprev = 0.0f, eprev = 0.0f;
-    #pragma unroll 8
-    for (int j = 0; j < nz; j++) {
-      const float g = grav(j);
-      if (j > 0) I.add(0.5f * dz_au * (gprev + g));
-      const float e = expf(-I.value() - logf(Tj(j) / T0));
-      if (j > 0) S.add(0.5f * (eprev + e));
-      ec[(long long)j * nr] = e;
-      gprev = g;
-      eprev = e;
+    // pass 1 (upward): e_j and S / dz
+    float carryI = 0.0f, gprev = 0.0f, eprev = 0.0f, Ssum = 0.0f;
+    for (int c = 0; c < nch; c++) {
+      const int j = 32 * c + lane;
+      const bool in = j < nz;
+      const float g = in ? grav(j) : 0.0f;
+      float gl = __shfl_up_sync(0xffffffffu, g, 1);
+      if (lane == 0) gl = gprev;
+      const float term = (in && j >= 1) ? 0.5f * dz_au * (gl + g) : 0.0f;
+      const float I = carryI + warp_prefix(term, lane);
+      const float e = in ? expf(-I - logf(Tj(j) / T0)) : 0.0f;
+      if (in) ev[at(j)] = e;
+      float el = __shfl_up_sync(0xffffffffu, e, 1);
+      if (lane == 0) el = eprev;
+      Ssum += warp_sum((in && j >= 1) ? 0.5f * (el + e) : 0.0f);
+      carryI = __shfl_sync(0xffffffffu, I, 31);
+      gprev = __shfl_sync(0xffffffffu, g, 31);
+      eprev = __shfl_sync(0xffffffffu, e, 31);
     }
     const float x = r_au / C.r_c;
     const float sigma = C.sigma0 * powf(x, -C.gamma) * expf(-powf(x, 2.0f - C.gamma));
-    const float Sdz = S.value();                              // S / dz_cm
-    const float Cn = sigma / (2.0f * Sdz * dz_cm) / C.m_mol_g;  // n_j = Cn e_j
+    const float Sdz = Ssum;
+    const float Cn = sigma / (2.0f * Sdz * dz_cm) / C.m_mol_g;
     const float dw = C.zr_max / (float)(nz - 1);
-    // pass 2: the h_hi cell (highest j with 0.706 N_j > N_d) and dL/dN at its two nodes
-    int js = nz;  // no cell
+    __syncwarp();
+    // pass 2 (downward): the h_hi cell and dL/dN at its two nodes
+    int js = nz;
     float gNa = 0.0f, gNb = 0.0f;
     const float ghi = g_hi ? (float)g_hi[i] : 0.0f;
     if (ghi != 0.0f) {
-      KSum N;
-      for (int j = nz - 2; j >= 0; j--) {
-        const float Nnext = N.value();
-        N.add(0.5f * dz_cm * Cn * (ec[(long long)j * nr] + ec[(long long)(j + 1) * nr]));
-        const float Nj = N.value();
-        if (0.706f * Nj > C.N_dissoc) {
-          // (Na - Nb)^2 would overflow FP32 at column densities ~1e21: divide twice
-          const float Na = 0.706f * Nj, Nb = 0.706f * Nnext, dN = Na - Nb;
+      float carryN = 0.0f, eabove = 0.0f;
+      for (int c = nch - 1; c >= 0; c--) {
+        const int j = 32 * c + lane;
+        const bool in = j < nz;
+        const float e = in ? ev[at(j)] : 0.0f;
+        float eu = __shfl_down_sync(0xffffffffu, e, 1);
+        if (lane == 31) eu = eabove;
+        const float u = (in && j <= nz - 2) ? 0.5f * dz_cm * Cn * (e + eu) : 0.0f;
+        const float N = carryN + warp_suffix(u, lane);
+        const unsigned hit = __ballot_sync(0xffffffffu, in && 0.706f * N > C.N_dissoc);
+        if (hit) {
+          const int lh = 31 - __clz(hit);  // highest node of the chunk over the threshold
+          const float Nj = __shfl_sync(0xffffffffu, N, lh);
+          const float uj = __shfl_sync(0xffffffffu, u, lh);
+          const float Na = 0.706f * Nj, Nb = 0.706f * (Nj - uj), dN = Na - Nb;
           gNa = ghi * dw * ((C.N_dissoc - Nb) / dN) / dN * 0.706f;
           gNb = ghi * dw * ((Na - C.N_dissoc) / dN) / dN * 0.706f;
-          js = j;
+          js = 32 * c + lh;
           break;
         }
+        carryN = __shfl_sync(0xffffffffu, N, 0);
+        eabove = __shfl_sync(0xffffffffu, e, 0);
       }
     }
-    // dL/dn_k: the caller's part plus the column's, P_k = sum_{j <= k} dL/dN_j
-    auto gnk = [&](int k) {
-      float v = g_n ? (float)g_n[(long long)k * nr + i] : 0.0f;
-      const float Pk = (k >= js ? gNa : 0.0f) + (k >= js + 1 ? gNb : 0.0f);
-      const float Pk1 = (k - 1 >= js ? gNa : 0.0f) + (k >= js + 2 ? gNb : 0.0f);
-      if (k <= nz - 2) v += 0.5f * dz_cm * Pk;
-      if (k >= 1) v += 0.5f * dz_cm * Pk1;
-      return v;
-    };
-    // pass 3: dL/dn_j and sum_j dL/dn_j e_j
-    KSum dot;
-    #pragma unroll 8
-    for (int j = 0; j < nz; j++) {
-      const float gn = gnk(j);
-      gc[(long long)j * nr] = gn;
-      dot.add(gn * ec[(long long)j * nr]);
+    // pass 3: dL/dn_j (scratch) and sum_j dL/dn_j e_j
+    float dot = 0.0f;
+    for (int c = 0; c < nch; c++) {
+      const int j = 32 * c + lane;
+      if (j < nz) {
+        float v = g_n ? (float)g_n[at(j)] : 0.0f;
+        const float Pk = (j >= js ? gNa : 0.0f) + (j >= js + 1 ? gNb : 0.0f);
+        const float Pk1 = (j - 1 >= js ? gNa : 0.0f) + (j >= js + 2 ? gNb : 0.0f);
+        if (j <= nz - 2) v += 0.5f * dz_cm * Pk;
+        if (j >= 1) v += 0.5f * dz_cm * Pk1;
+        gnv[at(j)] = v;
+        dot += v * ev[at(j)];
+      }
     }
-    const float ge_dot = dot.value();
-    // pass 4: downward, with Q = sum_{j > m} dL/dI_j (I in units of au, so dL/dI per au)
-    KSum Q, sum_glr;
-    #pragma unroll 8
-    for (int m = nz - 1; m >= 0; m--) {
-      const float wk = (m > 0 ? 0.5f : 0.0f) + (m < nz - 1 ? 0.5f : 0.0f);  // w_k / dz
-      const float e = ec[(long long)m * nr];
-      const float glr = (Cn * gc[(long long)m * nr] - Cn / Sdz * wk * ge_dot) * e;
+    const float ge_dot = warp_sum(dot);
+    // pass 4 (downward): Q_m = sum_{j > m} dL/dI_j, dL/dT
+    float carryQ = 0.0f, sglr = 0.0f;
+    for (int c = nch - 1; c >= 0; c--) {
+      const int m = 32 * c + lane;
+      const bool in = m < nz;
+      float glr = 0.0f;
+      if (in) {
+        const float wk = (m > 0 ? 0.5f : 0.0f) + (m < nz - 1 ? 0.5f : 0.0f);
+        glr = (Cn * gnv[at(m)] - Cn / Sdz * wk * ge_dot) * ev[at(m)];
+      }
       const float gI = -glr;
-      const float q = Q.value();
-      float gg = 0.0f;
-      if (m + 1 <= nz - 1) gg += 0.5f * dz_au * q;
-      if (m >= 1) gg += 0.5f * dz_au * (q + gI);
-      Q.add(gI);
-      sum_glr.add(glr);
-      gT[(long long)m * nr] = (double)(-glr / Tj(m) - gg * grav(m) / Tj(m));
+      const float incl = carryQ + warp_suffix(gI, lane);
+      const float Q = incl - gI;  // exclusive: nodes above m
+      if (in) {
+        float gg = 0.0f;
+        if (m + 1 <= nz - 1) gg += 0.5f * dz_au * Q;
+        if (m >= 1) gg += 0.5f * dz_au * (Q + gI);
+        g_T[at(m)] = (double)(-glr / Tj(m) - gg * grav(m) / Tj(m));
+      }
+      sglr += glr;
+      carryQ = __shfl_sync(0xffffffffu, incl, 0);
     }
-    gT[0] += (double)(sum_glr.value() / T0);  // the ln T_0 term (zero up to rounding)
+    sglr = warp_sum(sglr);
+    __syncwarp();
+    if (lane == 0) g_T[at(0)] += (double)(sglr / T0);  // the ln T_0 term (zero up to rounding)
     // h_lo: lowest cell [j-1, j] with T_j > T_freeze (none when the midplane node is warmer)
     const float glo = g_lo ? (float)g_lo[i] : 0.0f;
     if (glo != 0.0f && !(T0 > C.T_freeze)) {
-      for (int j = 1; j < nz; j++) {
-        const float Ta = Tj(j - 1), Tb = Tj(j);
-        if (Tb > C.T_freeze) {
-          const float q = (Tb - Ta) * (Tb - Ta);
-          gT[(long long)(j - 1) * nr] += (double)(glo * dw * (C.T_freeze - Tb) / q);
-          gT[(long long)j * nr] += (double)(-glo * dw * (C.T_freeze - Ta) / q);
+      for (int c = 0; c < nch; c++) {
+        const int j = 32 * c + lane;
+        const unsigned hit = __ballot_sync(0xffffffffu, j >= 1 && j < nz && Tj(j) > C.T_freeze);
+        if (hit) {
+          const int jl = 32 * c + __ffs(hit) - 1;
+          __syncwarp();
+          if (lane == 0) {
+            const float Ta = Tj(jl - 1), Tb = Tj(jl), q = (Tb - Ta) * (Tb - Ta);
+            g_T[at(jl - 1)] += (double)(glo * dw * (C.T_freeze - Tb) / q);
+            g_T[at(jl)] += (double)(-glo * dw * (C.T_freeze - Ta) / q);
+          }
           break;
         }
       }
     }
+    __syncwarp();
   }
 }
 
@@ -511,8 +557,8 @@ int launch_field_chain_adjoint(const rt_grid &g, const rt_geom &geo, const rt_li
   cudaError_t e = stream_alloc((void **)&scr, 2 * col * sizeof(float), stream);
   if (e != cudaSuccess)
     return set_error(RT_ENOMEM, "chain adjoint scratch: %s", cudaGetErrorString(e));
-  const int threads = 32;  // one warp per block: the columns spread over the SMs
-  const long long blocks = (g.nr + threads - 1) / threads;
+  const int threads = 128;  // four columns (warps) per block
+  const long long blocks = ((long long)g.nr * 32 + threads - 1) / threads;
   field_chain_adjoint_kernel<<<(unsigned)blocks, threads, 0, stream>>>(C, T, g_n, g_lo, g_hi, g_T,
                                                                        scr, scr + col);
   e = cudaGetLastError();
