@@ -41,3 +41,17 @@ def test_plain_rejects_rotation_field(rt):
     p = p.replace(vphi=np.ones_like(p.T))
     with pytest.raises(rt.RTError):
         rt.rt_render_plain(p)
+
+
+@pytest.mark.parametrize("mode", ["mach_linear", "hard_edge", "jy_background"])
+def test_plain_modes(rt, orc, mode):
+    """The plain march follows every mode of the physics: Mach turbulence on a linear radial
+    grid, hard-edged CO layers, Jy units with a background."""
+    p = synth.config_small(21)
+    if mode == "mach_linear":
+        p = p.replace(vturb_mach=1, vturb=np.full_like(p.vturb, 0.3), r_log=0)
+    elif mode == "hard_edge":
+        p = p.replace(edge_w=0.0)
+    else:
+        p = p.replace(units=1, I0=3e-3)
+    assert_cube_close(plain_cube(rt, p), orc.render(p), label=f"plain {mode}")
