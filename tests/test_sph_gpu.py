@@ -73,3 +73,13 @@ def test_sph_rejects_bad_grid(rt, bad):
             kw[k] = np.ascontiguousarray(kw[k][:, :, :bad["nr"]])
     with pytest.raises(rt.RTError):
         rt.rt_render_sph(p.replace(gs=synth.GridSph(**kw)))
+
+
+def test_sph_mach_turbulence(rt, orc):
+    """Turbulence given as a Mach number (the paper's form) on the spherical grid."""
+    p = synth.sphere3d(5, nsph=(30, 14, 20), nx=24, ny=24, nch=16, n_samples=96, incl=55.0)
+    g = p.gs
+    gs = synth.GridSph(g.nr, g.nth, g.nph, g.r_log, g.r_in, g.r_out, g.th0, g.th1, g.T, g.n_h2,
+                       np.full_like(g.T, 0.3), g.x_co, g.vr, g.vth, g.vph)
+    q = p.replace(gs=gs, vturb_mach=1)
+    assert_cube_close(gpu_cube_sph(rt, q), orc.render(q), label="sph Mach")
