@@ -235,7 +235,10 @@ int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geo
  * holds until the process exits.
  * Arguments, seeds, outputs and results are those of rt_render_adjoint. In addition:
  *   - The first call on a device looks up the array's device address (with that device
- *     current) and caches it; make that first call before any stream capture.
+ *     current) and caches it with the ID of the current CUDA context; make that first call
+ *     before any stream capture. A call in another context of that device (after
+ *     cudaDeviceReset, for example, which unloads the library's device code) looks the
+ *     address up again.
  *   - Every call on a device shares the same array. Each call clears what it needs (the
  *     checkpoints are written before they are read, the gradient copies are zeroed on
  *     `stream`), but calls whose kernels overlap on the GPU (different streams, or different
@@ -612,6 +615,34 @@ int rt_server_stats(rt_server *s, int *queued, int *running, size_t *bytes_in_us
 /* rt_server_destroy -- cancel queued requests, wait for running ones (their device work is
    finite), release streams and the scheduler thread. */
 int rt_server_destroy(rt_server *s);
+
+/*
+ * rt_pipe_peak -- measured issue rate of one arithmetic operation the march is built from,
+ * for the roofline denominators of the march kernels (measurement support; the paper has no
+ * counterpart). One wave of blocks (the occupancy limit x the device's SMs) runs 8
+ * independent chains per thread of `op` for `iters` steps; every block times its loop with
+ * the SM cycle counter.
+ *   op          RT_PEAK_* below
+ *   iters       16 .. 2^24 steps per chain (about 2^13 gives a few milliseconds)
+ *   per_clk_sm  (host) results per SM clock cycle per SM: lanes of the operation's results
+ *               completed by one SM's blocks / the median of the blocks' cycle counts
+ *               (packed two-lane forms count two results per lane)
+ *   ms          (host) CUDA-event time of the measured launch
+ *   sm_mhz      (host) the SM clock implied by that launch (cycles / wall time)
+ * Allocates two small buffers (one entry per block) on `stream` and synchronises it.
+ * Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
+ */
+#define RT_PEAK_FFMA 0   /* fma.rn.f32 */
+#define RT_PEAK_FFMA2 1  /* packed two-lane fma.rn.f32x2 (2 results per lane) */
+#define RT_PEAK_EX2 2    /* ex2.approx.ftz.f32 */
+#define RT_PEAK_RSQ 3    /* rsqrt.approx.ftz.f32 */
+#define RT_PEAK_LG2 4    /* lg2.approx.ftz.f32 */
+#define RT_PEAK_RCP 5    /* rcp.approx.ftz.f32 */
+#define RT_PEAK_SQRT 6   /* sqrt.approx.ftz.f32 */
+#define RT_PEAK_TANH 7   /* tanh.approx.f32 */
+#define RT_PEAK_TANH2 8  /* tanh.approx.f16x2 (2 results per lane) */
+int rt_pipe_peak(int op, int iters, double *per_clk_sm, double *ms, double *sm_mhz,
+                 void *stream);
 
 /* Message for the last error on this thread ("" if none). */
 const char *rt_last_error(void);

@@ -175,6 +175,9 @@ def lib():
             L.rt_render_plain.restype = C.c_int
             L.rt_render_launch_count.argtypes = base + [P(C.c_int)]
             L.rt_render_launch_count.restype = C.c_int
+            L.rt_pipe_peak.argtypes = [C.c_int, C.c_int, P(C.c_double), P(C.c_double),
+                                       P(C.c_double), C.c_void_p]
+            L.rt_pipe_peak.restype = C.c_int
             L.rt_mlp_status.argtypes = [P(C.c_int)]
             L.rt_mlp_status.restype = C.c_int
             L.rt_last_error.restype = C.c_char_p
@@ -726,6 +729,19 @@ def rt_render_modulated(problem, fields, mod, h_scale, out=None, stream=None):
     check(lib().rt_render_modulated(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
                                     _ptr(mod), float(h_scale), _ptr(out), stream_handle(stream)))
     return out
+
+
+PIPE_OPS = {"ffma": 0, "ffma2": 1, "ex2": 2, "rsqrt": 3, "lg2": 4, "rcp": 5, "sqrt": 6,
+            "tanh": 7, "tanh_f16x2": 8}
+
+
+def rt_pipe_peak(op: str, iters: int = 8192, stream=None) -> dict:
+    """Measured rate of one operation (rt_pipe_peak): results per SM clock per SM, the
+    launch's CUDA-event time [ms] and the SM clock it implies [MHz]."""
+    r, ms, mhz = C.c_double(), C.c_double(), C.c_double()
+    check(lib().rt_pipe_peak(PIPE_OPS[op], int(iters), C.byref(r), C.byref(ms), C.byref(mhz),
+                             stream_handle(stream)))
+    return {"per_clk_sm": r.value, "ms": ms.value, "sm_mhz": mhz.value}
 
 
 def rt_mlp_status() -> int:

@@ -817,21 +817,15 @@ static int run_adj(const MarchParams &P, const float *dLdc, const float *target,
   if (rc != RT_OK) return rc;
   const GradCopies c = copies_of(P, a, scratch);
   const int nseg = (P.n_samples + kSeg - 1) / kSeg;
-  const MarchParams *Q = &P;
-  MarchParams *packed = nullptr;
+  // the kernel takes the parameters by value, so the copy pointing at the corner quads only
+  // has to live until the launch (on the stack: no host allocation)
+  MarchParams Q = P;
   if (a.cell_bytes) {
-    packed = new (std::nothrow) MarchParams(P);
-    if (!packed) return set_error(RT_ENOMEM, "host allocation failed");
-    rc = pack_cells(*packed, scratch + a.cell_off, stream);
-    if (rc != RT_OK) {
-      delete packed;
-      return rc;
-    }
-    Q = packed;
+    rc = pack_cells(Q, scratch + a.cell_off, stream);
+    if (rc != RT_OK) return rc;
   }
   march_adj_kernel<LPR, CPL, VAR><<<(unsigned)blocks, adj_wpb<LPR>() * 32, 0, stream>>>(
-      *Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, dmax, c);
-  delete packed;
+      Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, dmax, c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "adjoint launch: %s", cudaGetErrorString(e));
   return sum_copies(P, G, c, a, stream);
@@ -931,25 +925,60 @@ namespace rtb {
 constexpr size_t kFixedScratchBytes = (size_t)32 << 20;  // 32 MiB per device
 static __device__ __align__(256) float g_fixed_scratch[kFixedScratchBytes / sizeof(float)];
 
-// Device address of g_fixed_scratch on the current device. The host-side name is only a
-// stand-in for the symbol, so the address is looked up once per device (with that device
-// current) and cached.
+// Unique ID of the CUDA context current on this thread (0 where none is current or the query
+// is unavailable), through the driver entry points the runtime hands out (no link-time
+// dependency on the driver library).
+static unsigned long long current_context_id() {
+  typedef int (*GetCurrent)(void **);
+  typedef int (*GetId)(void *, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr, *g = nullptr;
+    cudaDriverEntryPointQueryResult st;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &st) ==
+            cudaSuccess &&
+        st == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &st) ==
+            cudaSuccess &&
+        st == cudaDriverEntryPointSuccess) {
+      get_current = (GetCurrent)f;
+      get_id = (GetId)g;
+    }
+  });
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of g_fixed_scratch in the current device's context. The host-side name is
+// only a stand-in for the symbol, so the address is looked up with that device current and
+// cached per device together with the ID of the context it belongs to; a different context
+// (after cudaDeviceReset, say, the library's module is loaded anew) triggers a new lookup.
 static int fixed_scratch_address(float **out) {
+  struct Entry {
+    unsigned long long ctx;
+    float *addr;
+  };
   static std::mutex mu;
-  static float *addr[64] = {nullptr};
+  static Entry cache[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_error(RT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= 64) return set_error(RT_EINVAL, "device index %d out of range", dev);
   std::lock_guard<std::mutex> lk(mu);
-  if (!addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!cache[dev].addr || ctx == 0 || cache[dev].ctx != ctx) {
     void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_fixed_scratch);
+    e = cudaGetSymbolAddress(&p, g_fixed_scratch);  // also initialises the context if needed
     if (e != cudaSuccess || !p)
       return set_error(RT_ECUDA, "cudaGetSymbolAddress(fixed scratch): %s", cudaGetErrorString(e));
-    addr[dev] = (float *)p;
+    cache[dev].addr = (float *)p;
+    cache[dev].ctx = ctx ? ctx : current_context_id();
   }
-  *out = addr[dev];
+  *out = cache[dev].addr;
   return RT_OK;
 }
 

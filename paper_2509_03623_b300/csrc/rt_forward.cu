@@ -309,10 +309,9 @@ int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream) {
   cudaError_t e = stream_alloc((void **)&buf, cb, stream);
   if (e != cudaSuccess)
     return set_error(RT_ENOMEM, "corner quads (%zu bytes): %s", cb, cudaGetErrorString(e));
-  MarchParams *Q = new (std::nothrow) MarchParams(P);
-  int rc = Q ? pack_cells(*Q, buf, stream) : set_error(RT_ENOMEM, "host allocation failed");
-  if (rc == RT_OK) rc = launch_march(*Q, cube, stream);
-  delete Q;
+  MarchParams Q = P;  // passed by value to the kernel: the copy only lives until the launch
+  int rc = pack_cells(Q, buf, stream);
+  if (rc == RT_OK) rc = launch_march(Q, cube, stream);
   cudaFreeAsync(buf, stream);
   return rc;
 }

@@ -126,3 +126,11 @@ def test_plain_march_rejects_rotation_field(L):
     assert L.rt_render_plain(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
                              C.c_void_p(16), None) == -1
     assert b"Keplerian" in L.rt_last_error()
+
+
+def test_pipe_probe_rejects_bad_arguments(L):
+    import ctypes as C
+    d = C.c_double()
+    assert L.rt_pipe_peak(99, 1024, C.byref(d), C.byref(d), C.byref(d), None) == -1
+    assert L.rt_pipe_peak(0, 1, C.byref(d), C.byref(d), C.byref(d), None) == -1
+    assert L.rt_pipe_peak(0, 1024, None, C.byref(d), C.byref(d), None) == -1

@@ -135,6 +135,32 @@ def test_p7_profile_normalisation_centre_width(orc):
                                rel=1e-9)
 
 
+@pytest.mark.parametrize("T", [25.0, 80.0])
+def test_p7_mach_mode_line_width_from_the_spectrum(orc, T):
+    """Mach-mode line width (Methods, the alpha(x) and c_s equations): the turbulent speed is
+    a Mach number times c_s with c_s^2 = 2kT/m_mol as printed, so
+    alpha^2 = 2kT/m_CO + M^2 2kT/m_mol with m_CO = 28.0101 amu and m_mol = 2.37 m_H
+    (m_H = 1.007825 amu). Measured from the rendered spectrum of an optically thin, static,
+    isothermal slab: its line is the Gaussian exp(-v^2/alpha^2), whose second moment over a
+    fine channel grid is alpha^2/2. Two temperatures and three Mach numbers fix both terms:
+    a dropped factor 2 in c_s^2, the two masses swapped, or M entering linearly all fail."""
+    m_co = 28.0101 * ph.AMU
+    m_mol = 2.37 * 1.007825 * ph.AMU
+    for M in (0.0, 0.5, 2.0):
+        expect = (2 * ph.K * T / m_co + M * M * 2 * ph.K * T / m_mol) / 1e10   # km^2 s^-2
+        a = math.sqrt(expect)
+        v = np.linspace(-7 * a, 7 * a, 701)
+        p = uniform_problem(T=T, n=1e-3, vt=M, v=v, ns=8)
+        p = p.replace(vturb_mach=1)
+        spec = orc.render(p)[:, 0, 0]
+        assert spec.max() > 0
+        m2 = float((v * v * spec).sum() / spec.sum())
+        assert 2.0 * m2 == pytest.approx(expect, rel=1e-6), (T, M)
+        # the same width at the sample itself
+        assert orc.point(p, 300.0, 0.0, 0.0, 0.0)["alpha_kms"] ** 2 == pytest.approx(expect,
+                                                                                    rel=1e-12)
+
+
 def test_kepler_height_dependence(orc):
     p = uniform_problem(incl=90.0, mstar=1.0)
     v0 = orc.point(p, 200.0, 0.0, 0.0, 0.0)["v_los_kms"]

@@ -84,3 +84,27 @@ def test_noalloc_rejects_oversized_problem(rt):
     with pytest.raises(rt.RTError, match="fixed"):
         rt.rt_render_adjoint_noalloc(p, dd, cube, grads,
                                      dL_dcube=torch.zeros_like(cube))
+
+
+def test_noalloc_with_corner_quads(rt, orc):
+    """128x128 pixels x 256 samples = 2^22 samples on the 64x32 grid: enough samples for the
+    corner quads of the fields to be packed, so the fixed array holds them next to the
+    checkpoints and the surface and grid copies. Two calls in a row, against the allocating
+    adjoint (which is checked against the oracle elsewhere)."""
+    import torch
+    p = synth.config_small(34).replace(nx=128, ny=128, n_samples=256)
+    assert rt.rt_render_launch_count(p) == 2, "expected the corner-quad packing pass"
+    dd = rt.DeviceDisk(p)
+    w = np.random.default_rng(3).standard_normal((p.nch, p.ny, p.nx))
+    dl = torch.tensor(w, dtype=torch.float32, device="cuda")
+    ref_cube, ref = rt.rt_render_adjoint(p, dd, dL_dcube=dl)
+    ref_np = to_np(ref)
+    for call in range(2):
+        grads, cube = _alloc_outputs(torch, p)
+        for t in list(grads.values()) + [cube]:
+            t.fill_(float("nan"))
+        rt.rt_render_adjoint_noalloc(p, dd, cube, grads, dL_dcube=dl)
+        torch.cuda.synchronize()
+        assert_grads_close(to_np(grads), ref_np, label=f"no-alloc corner quads, call {call}")
+        c, rc = cube.cpu().numpy(), ref_cube.cpu().numpy()
+        np.testing.assert_allclose(c, rc, rtol=1e-6, atol=1e-7 * np.abs(rc).max())
