@@ -173,6 +173,19 @@ int rt_render_plain(const rt_grid *grid, const rt_fields *fields, const rt_geom 
                     const rt_view *view, const rt_line *line, float *cube, void *stream);
 
 /*
+ * rt_render_dense -- the dense FP32 march the forward is also compared against: rt_render's
+ * kernel (one warp per group of rays, the channel-independent physics of each sample computed
+ * once and shared by its channels, packed two-channel FP32 arithmetic) with its two work
+ * skips removed -- every sample of every ray's chord is visited (no gas sample range) and
+ * every channel of every sample is evaluated (no channel window) -- and the fields read from
+ * the node arrays (no corner quads). Same transfer (Methods, Eq. rt-int, Eq. optical_depth)
+ * and arguments as rt_render; its cube agrees with rt_render's to FP32 rounding. A
+ * measurement baseline, not a production path. Returns RT_OK, RT_EINVAL or RT_ECUDA.
+ */
+int rt_render_dense(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                    const rt_view *view, const rt_line *line, float *cube, void *stream);
+
+/*
  * rt_render_launch_count -- number of kernel launches rt_render makes for this problem
  * (written to *count, HOST): 0 for an empty image or channel list, 2 when it packs the corner
  * quads first (from 4M samples, see rt_render), else 1. Nothing is launched. Returns RT_OK or
@@ -620,15 +633,16 @@ int rt_server_destroy(rt_server *s);
  * rt_pipe_peak -- measured issue rate of one arithmetic operation the march is built from,
  * for the roofline denominators of the march kernels (measurement support; the paper has no
  * counterpart). One wave of blocks (the occupancy limit x the device's SMs) runs 8
- * independent chains per thread of `op` for `iters` steps; every block times its loop with
- * the SM cycle counter.
- *   op          RT_PEAK_* below
- *   iters       16 .. 2^24 steps per chain (about 2^13 gives a few milliseconds)
- *   per_clk_sm  (host) results per SM clock cycle per SM: lanes of the operation's results
- *               completed by one SM's blocks / the median of the blocks' cycle counts
- *               (packed two-lane forms count two results per lane)
- *   ms          (host) CUDA-event time of the measured launch
- *   sm_mhz      (host) the SM clock implied by that launch (cycles / wall time)
+ * independent chains per thread of `op` for `iters` steps.
+ *   op           RT_PEAK_* below
+ *   iters        16 .. 2^24 steps per chain (2^13 takes 1-10 ms)
+ *   per_s_sm     (host) results per second per SM: lanes of results completed by one SM's
+ *                blocks / the CUDA-event time of the launch (packed two-lane forms count two
+ *                results per lane). Divide by the SM clock sampled meanwhile for a rate per
+ *                clock.
+ *   ms           (host) CUDA-event time of the measured launch
+ *   counter_mhz  (host) ticks of the per-SM cycle counter (clock64) per microsecond of that
+ *                launch; on B300 it is not the SM clock
  * Allocates two small buffers (one entry per block) on `stream` and synchronises it.
  * Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
  */
@@ -641,7 +655,7 @@ int rt_server_destroy(rt_server *s);
 #define RT_PEAK_SQRT 6   /* sqrt.approx.ftz.f32 */
 #define RT_PEAK_TANH 7   /* tanh.approx.f32 */
 #define RT_PEAK_TANH2 8  /* tanh.approx.f16x2 (2 results per lane) */
-int rt_pipe_peak(int op, int iters, double *per_clk_sm, double *ms, double *sm_mhz,
+int rt_pipe_peak(int op, int iters, double *per_s_sm, double *ms, double *counter_mhz,
                  void *stream);
 
 /* Message for the last error on this thread ("" if none). */

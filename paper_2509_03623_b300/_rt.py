@@ -173,6 +173,8 @@ def lib():
             L.rt_render_sph.restype = C.c_int
             L.rt_render_plain.argtypes = base + [C.c_void_p, C.c_void_p]
             L.rt_render_plain.restype = C.c_int
+            L.rt_render_dense.argtypes = base + [C.c_void_p, C.c_void_p]
+            L.rt_render_dense.restype = C.c_int
             L.rt_render_launch_count.argtypes = base + [P(C.c_int)]
             L.rt_render_launch_count.restype = C.c_int
             L.rt_pipe_peak.argtypes = [C.c_int, C.c_int, P(C.c_double), P(C.c_double),
@@ -269,6 +271,20 @@ def rt_render_plain(problem, fields=None, out=None, stream=None):
     if out is None:
         out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=T.device)
     check(lib().rt_render_plain(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
+                                C.c_void_p(out.data_ptr()), stream_handle(stream)))
+    return out
+
+
+def rt_render_dense(problem, fields=None, out=None, stream=None):
+    """The dense FP32 comparison march (rt_render_dense); returns the cube tensor."""
+    import torch
+    dd = fields if fields is not None else DeviceDisk(problem)
+    T, n, vt, hlo, hhi = dd.tensors()
+    g, f, o, vw, ln, keep = structs(problem, T, n, vt, hlo, hhi,
+                                       getattr(dd, "vphi", None))
+    if out is None:
+        out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=T.device)
+    check(lib().rt_render_dense(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
                                 C.c_void_p(out.data_ptr()), stream_handle(stream)))
     return out
 
@@ -736,12 +752,12 @@ PIPE_OPS = {"ffma": 0, "ffma2": 1, "ex2": 2, "rsqrt": 3, "lg2": 4, "rcp": 5, "sq
 
 
 def rt_pipe_peak(op: str, iters: int = 8192, stream=None) -> dict:
-    """Measured rate of one operation (rt_pipe_peak): results per SM clock per SM, the
-    launch's CUDA-event time [ms] and the SM clock it implies [MHz]."""
+    """Measured rate of one operation (rt_pipe_peak): results per second per SM, the
+    launch's CUDA-event time [ms] and the rate of the per-SM cycle counter [MHz]."""
     r, ms, mhz = C.c_double(), C.c_double(), C.c_double()
     check(lib().rt_pipe_peak(PIPE_OPS[op], int(iters), C.byref(r), C.byref(ms), C.byref(mhz),
                              stream_handle(stream)))
-    return {"per_clk_sm": r.value, "ms": ms.value, "sm_mhz": mhz.value}
+    return {"per_s_sm": r.value, "ms": ms.value, "counter_mhz": mhz.value}
 
 
 def rt_mlp_status() -> int:

@@ -89,7 +89,7 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   const float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
   const float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
   const float r2 = fmaf(R.x, R.x, y * y);
-  if (!(in_gas(P, z, r2) && R.hit && k < P.n_samples)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (!(in_gas(P, z, r2) && k <= R.khi)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const Cell c = locate(P, z, r2);
   const NodeVals f = fields_at<ROT>(P, c);
   float T = f.T, n = f.n, hlo = f.hlo, hhi = f.hhi;

@@ -503,6 +503,24 @@ extern "C" int rt_render_plain(const rt_grid *grid, const rt_fields *fields,
   return rc;
 }
 
+extern "C" int rt_render_dense(const rt_grid *grid, const rt_fields *fields,
+                               const rt_geom *geom, const rt_view *view, const rt_line *line,
+                               float *cube, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params(grid, fields, geom, view, line, P);
+  if (rc == RT_OK) {
+    const long long n = (long long)P->nx * P->ny * P->nch;
+    if (n > 0 && !cube)
+      rc = set_error(RT_EINVAL, "null cube pointer");
+    else
+      rc = launch_forward_dense(*P, cube, (cudaStream_t)stream);
+  }
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
 extern "C" int rt_render_launch_count(const rt_grid *grid, const rt_fields *fields,
                                       const rt_geom *geom, const rt_view *view,
                                       const rt_line *line, int *count) {

@@ -25,8 +25,14 @@
 // Per sample-channel evaluation: 6 FP32 operations, issued as 3 packed two-channel
 // instructions (FFMA2/FMUL2/FADD2), and 2 MUFU.EX2. The optical depth is kept negated (so no
 // negation is needed before the exponential) and summed per batch, then folded into a
-// per-channel base at the end of every batch (blocked summation: about 2 N_s / LPR roundings
-// instead of N_s).
+// per-channel base at the end of every batch with Kahan compensation: the fold's rounding
+// error is carried into the next batch's sum, so the base is exact to about one rounding of
+// the total optical depth however many batches the ray has.
+//
+// Gas range. Each ray's setup gives the range of samples that can lie inside the gas wedge
+// (gas_range); a ray is marched from the first sample of its range, the warp's batches
+// running until the longest range of its rays ends. Samples outside the range are exact
+// no-ops of the march (no gas), so they are not visited.
 #include <mutex>
 #include <new>
 
@@ -71,7 +77,7 @@ __global__ void __launch_bounds__(kWarps * 32, MODE >= 2 ? 4 : (CPL == 8 ? 5 : 6
   }
   // the window test needs equally spaced channels; otherwise every block is marched
   // the window is tested in channel-index space; without equal spacing every block is marched
-  const bool windowed = P.v_uniform && P.dv != 0.0f;
+  const bool windowed = P.v_uniform && P.dv != 0.0f && !P.no_window;
   const float idv = windowed ? 1.0f / P.dv : 0.0f;
   const float2 mone = make_float2(-1.0f, -1.0f);
   // work counters (lane 0; only with P.work): samples whose physics found gas, channel
@@ -103,10 +109,11 @@ __global__ void __launch_bounds__(kWarps * 32, MODE >= 2 ? 4 : (CPL == 8 ? 5 : 6
         Tr[m] = make_float2(1.0f, 1.0f);
         I[m] = make_float2(0.0f, 0.0f);
       }
-      const int nsamp = __any_sync(0xffffffffu, ray.hit) ? P.n_samples : 0;
+      // the rays' gas sample ranges, marched from their first samples (klo) on
+      const int nsamp = __reduce_max_sync(0xffffffffu, max(ray.khi - ray.klo + 1, 0));
       for (int kb = 0; kb < nsamp; kb += 2 * LPR) {
-        const float4 mine = march_physics<MODE>(P, s_tab, ray, kb + q);
-        const float4 mine2 = march_physics<MODE>(P, s_tab, ray, kb + LPR + q);
+        const float4 mine = march_physics<MODE>(P, s_tab, ray, ray.klo + kb + q);
+        const float4 mine2 = march_physics<MODE>(P, s_tab, ray, ray.klo + kb + LPR + q);
         // channel window of a sample (empty without gas): fractional channel indices where
         // kd 2^{-d^2} >= 2^-40; the lane votes with the union of its two samples' windows
         auto window = [&](const float4 &m4, float &lo, float &hi) {
@@ -171,8 +178,11 @@ __global__ void __launch_bounds__(kWarps * 32, MODE >= 2 ? 4 : (CPL == 8 ? 5 : 6
             I[m] = __ffma2_rn(S, df, I[m]);
             Tr[m] = Tn;
           }
-          nb[m] = __fadd2_rn(nb[m], nl[m]);
-          nl[m] = make_float2(0.0f, 0.0f);
+          // compensated fold of the batch into the base (Kahan): nl carries the batch sum
+          // minus the base's rounding error left by the previous fold
+          const float2 t = __fadd2_rn(nb[m], nl[m]);
+          nl[m] = __ffma2_rn(__ffma2_rn(nb[m], mone, t), mone, nl[m]);
+          nb[m] = t;
         }
         __syncwarp();
       }
@@ -314,6 +324,18 @@ int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream) {
   if (rc == RT_OK) rc = launch_march(Q, cube, stream);
   cudaFreeAsync(buf, stream);
   return rc;
+}
+
+// The dense comparison march: the same kernel visiting every sample of every ray and every
+// channel block, reading the node arrays (no gas range, no channel window, no corner quads).
+int launch_forward_dense(const MarchParams &P, float *cube, cudaStream_t stream) {
+  if ((long long)P.nx * P.ny == 0 || P.nch == 0) return RT_OK;
+  MarchParams Q = P;
+  Q.full_range = 1;
+  Q.no_window = 1;
+  Q.cell = nullptr;
+  Q.hcell = nullptr;
+  return launch_march(Q, cube, stream);
 }
 
 static int launch_march(const MarchParams &P, float *cube, cudaStream_t stream) {

@@ -30,6 +30,9 @@ struct MarchParams {
   // 3-D Cartesian grid (rt_render3d; box != 0): chord box in double (ray setup), node
   // placement in float, packed node records {T, n, vt, x_co} and {vx, vy, vz, 0}
   int box;
+  // the dense comparison march: every sample of a ray is visited (no gas range) and every
+  // channel block is marched (no channel window)
+  int full_range, no_window;
   double bx0, bx1, by0, by1, bz0, bz1;
   int n3x, n3y, n3z;
   // per axis: a node near the centre of the box (index k and position c [au]) and the nodes
@@ -124,6 +127,7 @@ struct Ray {
   float vfac;              // sqrt(GM) sin i x  [km s^-1 au^{1/2}]
   int hit;                 // ray crosses the bounding cylinder
   int pix;                 // pixel index iy * nx + ix
+  int klo, khi;            // samples that can hold gas: klo..khi (khi < klo: none)
 };
 
 // Round v to `bits` significant bits.
@@ -138,6 +142,63 @@ __host__ __device__ __forceinline__ double round_bits(double v, int bits) {
 __device__ __forceinline__ float sample_coord(float kf, float base, float base2, float step,
                                               float step2) {
   return fmaf(kf, step, base) + fmaf(kf, step2, base2);
+}
+
+// Samples of a ray that can lie inside the gas wedge |z| <= zr_max r: the hull of
+// {s in [lo, hi] : zr_max^2 (x^2 + y(s)^2) - z(s)^2 >= 0} (a quadratic in s), widened by two
+// segments plus 2e-3 of the ray's coordinate magnitude (far above the FP32 rounding of the
+// roots, which is largest for rays grazing the wedge) and turned into sample indices. Every
+// sample outside the range fails the per-sample gas test, so marching only the range gives
+// the same cube. FP32 arithmetic, once per ray.
+__device__ __forceinline__ void gas_range(const MarchParams &P, float xs, float y0, float z0,
+                                          float wy, float wz, float lo, float hi, int *klo,
+                                          int *khi) {
+  const float m2 = P.zr_max2;
+  const float A = m2 * wy * wy - wz * wz;
+  const float B = 2.0f * (m2 * y0 * wy - z0 * wz);
+  const float C = m2 * fmaf(xs, xs, y0 * y0) - z0 * z0;
+  float s1 = lo, s2 = hi;
+  if (A == 0.0f) {  // linear: B s + C >= 0 (B = 0 as well: the whole chord)
+    if (B > 0.0f) s1 = fmaxf(lo, -C / B);
+    else if (B < 0.0f) s2 = fminf(hi, -C / B);
+  } else {
+    const float disc = B * B - 4.0f * A * C;
+    if (disc <= 0.0f) {
+      // A > 0: gas along the whole chord; A < 0: at most near the tangent point (the pad
+      // below covers a discriminant that rounded to zero or below)
+      if (A < 0.0f) s1 = s2 = -B / (2.0f * A);
+    } else {
+      const float q = -0.5f * (B + copysignf(sqrtf(disc), B));
+      float r1 = q / A, r2 = q != 0.0f ? C / q : r1;
+      if (r1 > r2) {
+        const float t = r1;
+        r1 = r2;
+        r2 = t;
+      }
+      if (A < 0.0f) {  // gas between the roots
+        s1 = fmaxf(lo, r1);
+        s2 = fminf(hi, r2);
+      } else {  // gas outside (r1, r2): hull of the two pieces inside the chord
+        s1 = lo <= r1 ? lo : fmaxf(lo, r2);
+        s2 = hi >= r2 ? hi : fminf(hi, r1);
+      }
+    }
+  }
+  const int n = P.n_samples;
+  const float ds = (hi - lo) / (float)n;
+  const float pad = 2.0f * ds + 2e-3f * (fabsf(lo) + fabsf(hi) + fabsf(xs) + fabsf(y0) + fabsf(z0));
+  s1 = fmaxf(s1 - pad, lo);
+  s2 = fminf(s2 + pad, hi);
+  // (fmaxf / fminf take lo / hi for a NaN bound: the whole ray)
+  if (!(s1 <= s2 && ds > 0.0f)) {  // the widened hull misses the chord: no gas
+    *klo = 0;
+    *khi = -1;
+    return;
+  }
+  // sample k sits at s = lo + (k + 1/2) ds
+  const float f1 = fmaxf((s1 - lo) / ds - 0.5f, 0.0f), f2 = fminf((s2 - lo) / ds - 0.5f, (float)n);
+  *klo = (int)floorf(f1);
+  *khi = min((int)ceilf(f2), n - 1);
 }
 
 __device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, bool active) {
@@ -224,6 +285,11 @@ __device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, b
   R.vfac = (float)((double)P.vk * P.sin_i * xs);
   R.hit = ok ? 1 : 0;
   R.pix = iy * P.nx + ix;
+  R.klo = 0;
+  R.khi = ok ? P.n_samples - 1 : -1;
+  if (ok && !P.box && !P.sph && !P.full_range)
+    gas_range(P, (float)xs, (float)P0y, (float)P0z, (float)wy, (float)wz, (float)lo, (float)hi,
+              &R.klo, &R.khi);
   return R;
 }
 
@@ -356,7 +422,7 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
   float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
   float r2 = fmaf(R.x, R.x, y * y);
   // samples without gas leave before the grid location (two multiplies and compares)
-  if (!(in_gas(P, z, r2) && R.hit && k < P.n_samples)) return make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+  if (!(in_gas(P, z, r2) && k <= R.khi)) return make_float4(0.0f, 0.0f, 1.0f, 0.0f);
   Cell c = locate(P, z, r2);
   const NodeVals f = fields_at<ROT>(P, c);
   float T = f.T, n = f.n, vt = f.vt, hlo = f.hlo, hhi = f.hhi;
@@ -391,7 +457,7 @@ __device__ __forceinline__ float4 sample_physics_box(const MarchParams &P, const
   const float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
   const float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
   float4 out = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
-  if (!(R.hit && k < P.n_samples)) return out;
+  if (!(k <= R.khi)) return out;
   // cell index and weight per axis, from the offset to the axis' central node
   auto axis = [](float pos, float c, float s, int k, int n, int &i, float &w) {
     const float f = (pos - c) * s;
@@ -452,7 +518,7 @@ __device__ __forceinline__ float4 sample_physics_sph(const MarchParams &P, const
   const float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
   const float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
   float4 out = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
-  if (!(R.hit && k < P.n_samples)) return out;
+  if (!(k <= R.khi)) return out;
   const float Rc2 = fmaf(R.x, R.x, y * y);
   const float r2 = fmaf(z, z, Rc2);
   if (!(r2 >= P.r_in2 && r2 <= P.r_out2)) return out;
@@ -523,6 +589,7 @@ int build_params(const rt_grid *grid, const rt_fields *fields, const rt_geom *ge
 int set_error(int code, const char *fmt, ...);
 void clear_error();
 int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream);
+int launch_forward_dense(const MarchParams &P, float *cube, cudaStream_t stream);
 int launch_plain(const MarchParams &P, float *cube, cudaStream_t stream);  // rt_plain.cu
 // Stream-ordered allocation from a library-owned pool of the current device, which keeps up
 // to kPoolKeepBytes cached between calls (so repeated renders do not map and unmap their

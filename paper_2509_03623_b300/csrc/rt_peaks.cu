@@ -1,19 +1,21 @@
 // Pipe-rate probe: sustained issue rates of the FP32 and MUFU operations the march is built
-// from, per SM clock and per SM, measured on the device the library runs on. These are the
+// from, per SM and second, measured on the device the library runs on. These are the
 // denominators of the march's ALU rooflines.
 //
 // One launch runs exactly one wave: blocks_per_sm x SMs blocks of 256 threads, every thread
 // advancing 8 independent chains of one operation `iters` times (so the pipe, not the
-// dependency latency, binds). Each block records the SM clock cycles between two
-// __syncthreads() around its loop (clock64); since every block of the wave runs for the same
-// span on its SM, the rate per SM clock is (operations of the blocks on one SM) / (median of
-// the blocks' cycle counts). Operation of a step (chain value x):
+// dependency latency, binds). The rate is the results of one SM's blocks over the CUDA-event
+// time of the launch (a few milliseconds, so the launch overhead is below 1e-3 of it). Each
+// block also reads the cycle counter (clock64) around its loop; on B300 that counter does not
+// run at the SM clock (about 1.27 GHz against a 2.03 GHz SM clock), so it is reported only as
+// the counter's rate, and rates per SM clock are formed by the caller from a sampled SM clock.
+// Operation of a step (chain value x):
 //   FFMA   x = x * 0.9999 + 1e-4               (one FFMA)
 //   FFMA2  (x, y) = (x, y) * 0.9999 + 1e-4     (one packed two-lane FFMA2: 2 FMAs)
 //   EX2    x = ex2.approx(-x)                  (converges to 0.64)
 //   RSQ    x = rsqrt.approx(x)                 (converges to 1)
 //   LG2    x = lg2.approx(x) + 2               (converges to 4; one FADD beside each MUFU)
-//   RCP    x = rcp.approx(x)                   (alternates between two values)
+//   RCP    x = rcp.approx(x) + 0.5             (converges to 1.28; one FADD beside each MUFU)
 //   SQRT   x = sqrt.approx(x)                  (converges to 1)
 //   TANH   x = tanh.approx.f32(x)
 //   TANH2  (x, y) = tanh.approx.f16x2(x, y)    (2 half-precision results per instruction)
@@ -43,6 +45,7 @@ __device__ __forceinline__ float peak_step(float x) {
     y += 2.0f;
   } else if (OP == RT_PEAK_RCP) {
     asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    y += 0.5f;
   } else if (OP == RT_PEAK_SQRT) {
     asm volatile("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   } else {  // RT_PEAK_TANH
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(kPeakThreads)
 static int lanes_per_op(int op) { return (op == RT_PEAK_FFMA2 || op == RT_PEAK_TANH2) ? 2 : 1; }
 
 template <int OP>
-static int run_peak(int iters, int nsm, double *per_clk_sm, double *ms, double *sm_mhz,
+static int run_peak(int iters, int nsm, double *per_s_sm, double *ms, double *counter_mhz,
                     cudaStream_t stream) {
   int bps = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, peak_kernel<OP>,
@@ -153,18 +156,18 @@ static int run_peak(int iters, int nsm, double *per_clk_sm, double *ms, double *
   std::nth_element(h.begin(), h.begin() + blocks / 2, h.end());
   const double cycles = (double)h[blocks / 2];
   const double ops_per_sm = (double)bps * kPeakThreads * kChains * iters * lanes_per_op(OP);
-  *per_clk_sm = ops_per_sm / cycles;
+  *per_s_sm = ops_per_sm / (t * 1e-3);
   *ms = t;
-  *sm_mhz = cycles / (t * 1e3);  // cycles of the wave / its wall time
+  *counter_mhz = cycles / (t * 1e3);  // cycle-counter ticks of the wave / its wall time
   return RT_OK;
 }
 
 }  // namespace rtb
 
-extern "C" int rt_pipe_peak(int op, int iters, double *per_clk_sm, double *ms, double *sm_mhz,
+extern "C" int rt_pipe_peak(int op, int iters, double *per_s_sm, double *ms, double *counter_mhz,
                             void *stream) {
   using namespace rtb;
-  if (!per_clk_sm || !ms || !sm_mhz) return set_error(RT_EINVAL, "null output pointer");
+  if (!per_s_sm || !ms || !counter_mhz) return set_error(RT_EINVAL, "null output pointer");
   if (iters < 16 || iters > (1 << 24)) return set_error(RT_EINVAL, "iters %d out of range", iters);
   if (op < RT_PEAK_FFMA || op > RT_PEAK_TANH2) return set_error(RT_EINVAL, "unknown operation %d", op);
   int dev = 0, nsm = 0;
@@ -174,15 +177,15 @@ extern "C" int rt_pipe_peak(int op, int iters, double *per_clk_sm, double *ms, d
   const cudaStream_t s = (cudaStream_t)stream;
   int rc;
   switch (op) {
-    case RT_PEAK_FFMA: rc = run_peak<RT_PEAK_FFMA>(iters, nsm, per_clk_sm, ms, sm_mhz, s); break;
-    case RT_PEAK_FFMA2: rc = run_peak<RT_PEAK_FFMA2>(iters, nsm, per_clk_sm, ms, sm_mhz, s); break;
-    case RT_PEAK_EX2: rc = run_peak<RT_PEAK_EX2>(iters, nsm, per_clk_sm, ms, sm_mhz, s); break;
-    case RT_PEAK_RSQ: rc = run_peak<RT_PEAK_RSQ>(iters, nsm, per_clk_sm, ms, sm_mhz, s); break;
-    case RT_PEAK_LG2: rc = run_peak<RT_PEAK_LG2>(iters, nsm, per_clk_sm, ms, sm_mhz, s); break;
-    case RT_PEAK_RCP: rc = run_peak<RT_PEAK_RCP>(iters, nsm, per_clk_sm, ms, sm_mhz, s); break;
-    case RT_PEAK_SQRT: rc = run_peak<RT_PEAK_SQRT>(iters, nsm, per_clk_sm, ms, sm_mhz, s); break;
-    case RT_PEAK_TANH: rc = run_peak<RT_PEAK_TANH>(iters, nsm, per_clk_sm, ms, sm_mhz, s); break;
-    case RT_PEAK_TANH2: rc = run_peak<RT_PEAK_TANH2>(iters, nsm, per_clk_sm, ms, sm_mhz, s); break;
+    case RT_PEAK_FFMA: rc = run_peak<RT_PEAK_FFMA>(iters, nsm, per_s_sm, ms, counter_mhz, s); break;
+    case RT_PEAK_FFMA2: rc = run_peak<RT_PEAK_FFMA2>(iters, nsm, per_s_sm, ms, counter_mhz, s); break;
+    case RT_PEAK_EX2: rc = run_peak<RT_PEAK_EX2>(iters, nsm, per_s_sm, ms, counter_mhz, s); break;
+    case RT_PEAK_RSQ: rc = run_peak<RT_PEAK_RSQ>(iters, nsm, per_s_sm, ms, counter_mhz, s); break;
+    case RT_PEAK_LG2: rc = run_peak<RT_PEAK_LG2>(iters, nsm, per_s_sm, ms, counter_mhz, s); break;
+    case RT_PEAK_RCP: rc = run_peak<RT_PEAK_RCP>(iters, nsm, per_s_sm, ms, counter_mhz, s); break;
+    case RT_PEAK_SQRT: rc = run_peak<RT_PEAK_SQRT>(iters, nsm, per_s_sm, ms, counter_mhz, s); break;
+    case RT_PEAK_TANH: rc = run_peak<RT_PEAK_TANH>(iters, nsm, per_s_sm, ms, counter_mhz, s); break;
+    case RT_PEAK_TANH2: rc = run_peak<RT_PEAK_TANH2>(iters, nsm, per_s_sm, ms, counter_mhz, s); break;
     default: return set_error(RT_EINVAL, "unknown operation %d", op);
   }
   if (rc == RT_OK) clear_error();

@@ -51,6 +51,32 @@ def test_small_disk_variants(rt, orc, case):
     print(f"variant {list(case)}: {e}")
 
 
+@pytest.mark.parametrize("case", [
+    dict(incl_deg=63.43494882292201),     # tan i = 1/zr_max: the wedge test is linear along rays
+    dict(incl_deg=90.0),                  # edge-on: gas on both sides of a gap around the axis
+    dict(incl_deg=75.0, pa_deg=30.0),     # rays entering and leaving through the wedge's faces
+    dict(incl_deg=30.0, half_fov_au=700.0, nx=61, ny=59),  # grazing rays at the disk's rim
+    dict(incl_deg=50.0, n_samples=4096, nx=24, ny=24),     # fine sampling of the range ends
+])
+def test_gas_range_geometries(rt, orc, case):
+    """Each ray is marched over the range of samples that can lie inside the gas wedge
+    |z| <= zr_max r (from the ray's quadratic); geometries where that range is degenerate,
+    splits in two, or grazes the wedge give the oracle's cube."""
+    p = synth.config_small(17).replace(**case)
+    e = assert_cube_close(gpu_cube(rt, p), orc.render(p), label=str(case))
+    print(f"gas range {case}: {e}")
+
+
+def test_thick_disk_1024_samples(rt, orc):
+    """Long optically thick rays (1024 samples, the serving mix's longest, H2 density x10 on
+    the observation-scale disk, 64^2 px): optical depths reach hundreds and the compensated
+    fold of the batch sums keeps the transmittance exact to FP32 rounding."""
+    p = synth.config_observation(6)
+    p = p.replace(nx=64, ny=64, n_samples=1024, n_h2=p.n_h2 * 10.0)
+    e = assert_cube_close(gpu_cube(rt, p), orc.render(p), label="thick 1024")
+    print(f"thick disk 1024 samples: {e}")
+
+
 def test_mach_mode_and_linear_grid(rt, orc):
     p = synth.config_small(12)
     p = p.replace(vturb_mach=1, vturb=np.full_like(p.vturb, 0.3), r_log=0)
