@@ -533,11 +533,319 @@ static int launch_mlp_t(const rt_mlp *m, const In &in, float *out, long long n,
   return RT_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// BF16 network forward with split operands ("three-pass" BF16): the product of every layer is
+// formed as W_hi a_hi + W_hi a_lo + W_lo a_hi, where x_hi = bf16(x) and x_lo = bf16(x - x_hi)
+// for the weights W and the activations a (the inputs of each layer, Fourier features
+// included), so the rounding of both operands to BF16 (2^-9 relative) drops out to second
+// order; SiLU is evaluated in FP32 (hardware tanh) and the output layer (128 -> 4) runs on the
+// CUDA cores in FP32. The accumulation is FP32 in tensor memory throughout.
+//
+// The product is taken transposed, D[out feature][sample] = W[out][in] a[in][sample], so that
+// the weights are the A operand: the high parts of every layer stay in shared memory (K-major
+// core matrices, 112 KB) and the low parts in tensor memory (A from tensor memory: row o in
+// lane o, two BF16 per 32-bit column, 224 columns), which leaves shared memory for three tile
+// groups of 64 samples. A group's activations are the B operand (MN-major core matrices of 8
+// features x 8 samples, high and low parts, 16 KB each); one thread per (output feature,
+// half of the samples) reads its accumulator row back, adds the bias, applies SiLU and writes
+// the next layer's high and low parts in place. After the fourth layer the FP32 activations
+// go to shared memory (XOR-swizzled, 32 KB) and one thread per (sample, output) forms the
+// output by a 128-term FP32 dot product.
+// ---------------------------------------------------------------------------------------
+constexpr int kSN = 64;                     // samples per tile (MMA N)
+constexpr int kSG = 3;                      // tile groups
+constexpr int kSGT = 256;                   // threads per group (two per TMEM lane row)
+constexpr unsigned kColWlo1 = 0;            // W1_lo: 128 x 64 -> 32 columns
+constexpr unsigned kColWloH = 32;           // W2..W4 lo: 64 columns each
+constexpr unsigned kColSplitD = 224;        // accumulators: 64 columns per group
+
+struct __align__(1024) SplitSmem {
+  h16 W1[kMlpW * kMlpF];                 // high parts, K-major core matrices (16 KB)
+  h16 Wh[3][kMlpW * kMlpW];              // (96 KB)
+  h16 B[kSG][2][kMlpW * kSN];            // activations per group: high, low parts (16 KB each)
+  float W5[kMlpOut][kMlpW];
+  float bias[4][kMlpW];
+  float bias5[kMlpOut];
+  float Bf[32][2];
+  float rh[kSG][kSN], zh[kSG][kSN];
+  long long idx[kSG][kSN];
+  int need[kSG][kSN];
+  unsigned long long mbar[kSG];
+  unsigned tmem_base;
+  int abort[kSG];
+};
+static_assert(sizeof(SplitSmem) <= 227 * 1024, "shared memory");
+static_assert(kColSplitD + 64 * kSG <= 512, "tensor memory");
+// the FP32 activations of the last hidden layer fill a group's two activation buffers
+static_assert(sizeof(float) * kMlpW * kSN == 2 * sizeof(h16) * kMlpW * kSN, "h4 staging");
+
+// Element offset of (feature k, sample s) in an MN-major B tile: core matrix (k/8, s/8) at
+// ((k/8) (kSN/8) + s/8) x 64 elements, row k % 8, element s % 8.
+__device__ __forceinline__ int bmn_off(int k, int s) {
+  return (((k >> 3) * (kSN >> 3) + (s >> 3)) << 6) + ((k & 7) << 3) + (s & 7);
+}
+
+// bf16 pair (low half = first) to two floats
+__device__ __forceinline__ float2 bf2f(unsigned u) {
+  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+
+// 8 values of feature k at samples s0..s0+7 (s0 multiple of 8): high and low BF16 parts
+__device__ __forceinline__ void split_store8(h16 *Bh, h16 *Bl, int k, int s0, const float *v) {
+  unsigned hi[4], lo[4];
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    hi[j] = pack16<false>(v[2 * j], v[2 * j + 1]);
+    const float2 h = bf2f(hi[j]);
+    lo[j] = pack16<false>(v[2 * j] - h.x, v[2 * j + 1] - h.y);
+  }
+  const int o = bmn_off(k, s0);
+  *reinterpret_cast<uint4 *>(Bh + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  *reinterpret_cast<uint4 *>(Bl + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+}
+
+// 32 consecutive 32-bit columns of this warp's TMEM lanes from registers
+__device__ __forceinline__ void tmem_st32(unsigned taddr, const unsigned *r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+      "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+// D (tmem) += A (tmem) x B (smem descriptor)
+__device__ __forceinline__ void mma_tmem_a(unsigned tmem_d, unsigned tmem_a,
+                                           unsigned long long b, unsigned idesc, int accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+template <class In>
+__global__ void __launch_bounds__(kSGT * kSG, 1)
+    mlp_split_kernel(const MlpParamsDev Wp, const __grid_constant__ In in,
+                     float *__restrict__ out, long long n) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  SplitSmem &S = *reinterpret_cast<SplitSmem *>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tg = tid / kSGT;            // tile group
+  const int gt = tid % kSGT;            // thread within the group
+  const int q = warp & 3;               // TMEM lane quadrant
+  const int hs = (warp >> 2) & 1;       // half of the tile's samples
+  const int f = q * 32 + lane;          // output feature (TMEM lane) of this thread
+
+  // ---- one-time setup: high parts to shared memory, low parts to tensor memory ----
+  for (int i = tid; i < kMlpW * kMlpF; i += blockDim.x)
+    S.W1[cm_off(i / kMlpF, i % kMlpF, kMlpF)] = to16<false>(Wp.W[0][i]);
+  for (int l = 0; l < 3; l++)
+    for (int i = tid; i < kMlpW * kMlpW; i += blockDim.x)
+      S.Wh[l][cm_off(i / kMlpW, i % kMlpW, kMlpW)] = to16<false>(Wp.W[l + 1][i]);
+  for (int i = tid; i < kMlpOut * kMlpW; i += blockDim.x) S.W5[i / kMlpW][i % kMlpW] = Wp.W[4][i];
+  for (int i = tid; i < 4 * kMlpW; i += blockDim.x) S.bias[i / kMlpW][i % kMlpW] = Wp.b[i / kMlpW][i % kMlpW];
+  if (tid < kMlpOut) S.bias5[tid] = Wp.b[4][tid];
+  if (tid < 64) S.Bf[tid >> 1][tid & 1] = Wp.B[tid];
+  if (tid == 0) {
+    for (int g = 0; g < kSG; g++) S.abort[g] = 0;
+    for (int g = 0; g < kSG; g++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar[g])), "r"(1));
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&S.tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tbase = S.tmem_base;
+  if (warp < 4) {
+    // warp w writes the low parts of rows 32w..32w+31 (row o = lane o): 32 columns of W1
+    // (64 inputs) and 64 of each hidden layer, two BF16 per column (the lower input first)
+    const unsigned trow = tbase + ((unsigned)(warp * 32) << 16);
+    const int o = warp * 32 + lane;
+    unsigned r[32];
+    auto lo2 = [](float a, float b) {
+      const float ha = __bfloat162float(__float2bfloat16_rn(a));
+      const float hb = __bfloat162float(__float2bfloat16_rn(b));
+      return pack16<false>(a - ha, b - hb);
+    };
+#pragma unroll
+    for (int c = 0; c < 32; c++) r[c] = lo2(Wp.W[0][o * kMlpF + 2 * c], Wp.W[0][o * kMlpF + 2 * c + 1]);
+    tmem_st32(trow + kColWlo1, r);
+    for (int l = 0; l < 3; l++)
+      for (int hh = 0; hh < 2; hh++) {
+#pragma unroll
+        for (int c = 0; c < 32; c++) {
+          const int k = 64 * hh + 2 * c;
+          r[c] = lo2(Wp.W[l + 1][o * kMlpW + k], Wp.W[l + 1][o * kMlpW + k + 1]);
+        }
+        tmem_st32(trow + kColWloH + 64 * l + 32 * hh, r);
+      }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  const unsigned tD = tbase + kColSplitD + 64 * tg;                   // this group's accumulator
+  const unsigned tDl = tD + ((unsigned)(q * 32) << 16) + 32 * hs;     // this thread's 32 columns
+  const unsigned mbar = smem_u32(&S.mbar[tg]);
+  h16 *Bh = S.B[tg][0], *Bl = S.B[tg][1];
+  const unsigned aBh = smem_u32(Bh), aBl = smem_u32(Bl);
+  // after layer 4 the group's two buffers (contiguous) hold the FP32 activations
+  // [feature][sample ^ (feature & 31)]
+  float *h4 = reinterpret_cast<float *>(Bh);
+  unsigned phase = 0;
+  auto gsync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(1 + tg), "r"(kSGT) : "memory"); };
+  // MN-major B (8 features x 8 samples core matrices): 128 B between sample groups, 1 KB
+  // between feature groups; one 16-feature K step = 2 KB
+  const unsigned idn = idesc_16(kSN, false, false, true);
+
+  const long long ntiles = (in_count(in, n) + kSN - 1) / kSN;
+  for (long long tile = (long long)blockIdx.x * kSG + tg; tile < ntiles;
+       tile += (long long)gridDim.x * kSG) {
+    bool need = false;
+    if (gt < kSN) {
+      long long s;
+      float rh = 0.0f, zh = 0.0f;
+      need = tile_input(in, tile * kSN, gt, &rh, &zh, &s);
+      S.rh[tg][gt] = rh;
+      S.zh[tg][gt] = zh;
+      S.idx[tg][gt] = s;
+      S.need[tg][gt] = need ? 1 : 0;
+    }
+    int any;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+        " bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(any)
+        : "r"((unsigned)need), "r"(1 + tg), "r"(kSGT)
+        : "memory");
+    if (!any) continue;
+    {
+      // Fourier features: direction j = gt % 32 for samples 8 (gt / 32) .. + 7 (range-reduced
+      // phases, hardware sin / cos), sin into feature j and cos into feature 32 + j
+      const int j = gt & 31, s0 = 8 * (gt >> 5);
+      float sv[8], cv[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        float ph = fmaf(S.Bf[j][0], S.rh[tg][s0 + i], S.Bf[j][1] * S.zh[tg][s0 + i]);
+        ph -= rintf(ph);
+        const float a = 6.283185307179586f * ph;
+        sv[i] = __sinf(a);
+        cv[i] = __cosf(a);
+      }
+      split_store8(Bh, Bl, j, s0, sv);
+      split_store8(Bh, Bl, 32 + j, s0, cv);
+    }
+    proxy_fence();
+    tc_fence_before();
+    gsync();
+    bool ok = true;
+    for (int l = 0; l < 4 && ok; l++) {
+      const int K = l == 0 ? kMlpF : kMlpW;
+      if (gt == 0) {
+        tc_fence_after();
+        const unsigned aW = l == 0 ? smem_u32(S.W1) : smem_u32(S.Wh[l - 1]);
+        const unsigned tWlo = tbase + (l == 0 ? kColWlo1 : kColWloH + 64 * (l - 1));
+        const unsigned long long dW = mma_desc(aW, K);
+        const unsigned long long dBh = mma_desc_mn(aBh, 128, 1024);
+        const unsigned long long dBl = mma_desc_mn(aBl, 128, 1024);
+        for (int ks = 0; ks < K / 16; ks++) {
+          mma_bf16(tD, dW + 16u * ks, dBh + 128u * ks, idn, ks > 0);       // W_hi a_hi
+          mma_bf16(tD, dW + 16u * ks, dBl + 128u * ks, idn, 1);            // W_hi a_lo
+          mma_tmem_a(tD, tWlo + 8u * ks, dBh + 128u * ks, idn, 1);         // W_lo a_hi
+        }
+        mma_commit(mbar);
+      }
+      ok = mbar_wait(mbar, phase);
+      phase ^= 1;
+      tc_fence_after();
+      if (!ok) {
+        S.abort[tg] = 1;
+        atomicExch(&g_mlp_error, 1);
+      }
+      if (ok) {
+        float v[32];
+        tmem_ld32(tDl, v);
+        const float b = S.bias[l][f];
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+          // SiLU(z) = h (1 + tanh h), h = z / 2
+          const float h = 0.5f * (v[i] + b);
+          float t;
+          asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
+          v[i] = fmaf(h, t, h);
+        }
+        if (l < 3) {
+#pragma unroll
+          for (int c = 0; c < 4; c++) split_store8(Bh, Bl, f, 32 * hs + 8 * c, v + 8 * c);
+        } else {
+          // the MMA of this layer has read the buffers: they now hold the FP32 activations
+#pragma unroll
+          for (int i = 0; i < 32; i++) h4[f * kSN + ((32 * hs + i) ^ lane)] = v[i];
+        }
+      }
+      proxy_fence();
+      tc_fence_before();
+      gsync();
+      ok = !S.abort[tg];
+    }
+    if (S.abort[tg]) break;
+    {
+      // output layer in FP32: thread gt -> sample gt / 4, output gt % 4
+      const int s = gt >> 2, o = gt & 3;
+      float acc = S.bias5[o];
+#pragma unroll 8
+      for (int k = 0; k < kMlpW; k++) acc = fmaf(S.W5[o][k], h4[k * kSN + (s ^ (k & 31))], acc);
+      if (S.need[tg][s]) out[S.idx[tg][s] * kMlpOut + o] = acc;
+    }
+    gsync();  // h4 and the tile inputs are read before the next tile overwrites them
+  }
+  // after a wait that ran out, let the MMA in flight finish (bounded) before the tensor
+  // memory is released
+  if (S.abort[tg] && gt == 0) mbar_wait(mbar, phase ^ 1);
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
+  }
+}
+
+template <class In>
+static int launch_mlp_split(const rt_mlp *m, const In &in, float *out, long long n,
+                            cudaStream_t stream) {
+  auto kern = mlp_split_kernel<In>;
+  const size_t smem = sizeof(SplitSmem);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess)
+    return set_error(RT_ECUDA, "mlp (split) smem attribute: %s", cudaGetErrorString(e));
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles = (n + kSN - 1) / kSN;
+  const long long groups = (tiles + kSG - 1) / kSG;
+  const long long blocks = groups < nsm ? groups : nsm;
+  kern<<<(unsigned)blocks, kSGT * kSG, smem, stream>>>(mlp_dev(m), in, out, n);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "mlp (split) launch: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
+// FP16 operands: one pass; BF16 operands: the split three-pass product above.
 template <class In>
 static int launch_mlp(const rt_mlp *m, const In &in, float *out, long long n,
                       cudaStream_t stream) {
   if (n <= 0) return RT_OK;
-  return m->precision == RT_MLP_BF16 ? launch_mlp_t<In, false>(m, in, out, n, stream)
+  return m->precision == RT_MLP_BF16 ? launch_mlp_split<In>(m, in, out, n, stream)
                                      : launch_mlp_t<In, true>(m, in, out, n, stream);
 }
 

@@ -1,5 +1,6 @@
-"""Tensor-core neural-field network (tcgen05, BF16 operands, FP32 accumulation) against the
-FP64 oracle network and a torch emulation of the same BF16 roundings."""
+"""Tensor-core neural-field network (tcgen05, FP32 accumulation) against the FP64 oracle
+network: FP16 operands (one pass, checked against a torch emulation of the same roundings as
+well) and BF16 operands (three-pass split product, FP32 SiLU, FP32 output layer)."""
 
 import numpy as np
 import pytest
@@ -39,15 +40,21 @@ def test_mlp_tensor_cores_vs_oracle_and_emulation(rt, orc, prec, n):
     torch.cuda.synchronize()
     assert rt.rt_mlp_status() == 0
     ref = orc.mlp_eval(w, x.astype(np.float64))
-    emu = emulation(torch, w, x, torch.float16 if prec == "f16" else torch.bfloat16)
     scale = np.abs(ref).max()
-    err_emu = np.abs(out - emu).max() / scale
     err_ref = np.abs(out - ref).max() / scale
-    print(f"{prec} n={n}: output scale {scale:.3e}, max err vs emulation {err_emu:.2e}, "
-          f"vs FP64 {err_ref:.2e}")
-    # 16-bit roundings of weights, features and activations; hardware tanh in SiLU
-    bound = 2e-3 if prec == "f16" else 1e-2
-    assert err_emu < bound and err_ref < bound
+    if prec == "f16":
+        # 16-bit roundings of weights, features and activations; hardware tanh in SiLU
+        emu = emulation(torch, w, x, torch.float16)
+        err_emu = np.abs(out - emu).max() / scale
+        print(f"f16 n={n}: output scale {scale:.3e}, max err vs emulation {err_emu:.2e}, "
+              f"vs FP64 {err_ref:.2e}")
+        assert err_emu < 2e-3 and err_ref < 2e-3
+    else:
+        # split BF16 operands: the operand roundings enter at second order (2^-18); what
+        # remains is the hardware tanh of SiLU (about 5e-4 relative per activation, largely
+        # averaging out over the 128-term products) and FP32 accumulation
+        print(f"bf16 n={n}: output scale {scale:.3e}, max err vs FP64 {err_ref:.2e}")
+        assert err_ref < 1e-3
 
 
 def neural_case(seed=0, **kw):
@@ -60,12 +67,12 @@ def neural_case(seed=0, **kw):
     dict(nx=33, ny=29, v_kms=np.linspace(-5, 5, 40), n_samples=100, incl_deg=70.0),
 ])
 def test_render_mlp_vs_oracle(rt, orc, kw):
-    """Tensor-core neural-field render vs the FP64 oracle: FP16 operands within 3e-3 per voxel
-    above 1e-3 of the peak; BF16 operands within 1e-2 (p99 3e-3); the FP32 network through the
-    same march within 1e-4."""
+    """Tensor-core neural-field render vs the FP64 oracle: FP16 and BF16 operands within 3e-3
+    per voxel above 1e-3 of the peak (the tolerance of the 16-bit network path); the FP32
+    network through the same march within 1e-4."""
     import torch
     from paper_2509_03623_b300 import neural
-    from tests.cubecheck import assert_cube_close, cube_errors
+    from tests.cubecheck import assert_cube_close
     p, w = neural_case(1, **kw)
     dd = rt.DeviceDisk(p)
     ref = orc.render_mlp(p, w)
@@ -75,8 +82,7 @@ def test_render_mlp_vs_oracle(rt, orc, kw):
     torch.cuda.synchronize()
     assert rt.rt_mlp_status() == 0
     e16 = assert_cube_close(f16, ref, rtol=3e-3, small_abs=3e-6, label="f16 mlp")
-    eb = cube_errors(bf16, ref)
-    assert eb["max_rel"] <= 1e-2 and eb["p99_rel"] <= 3e-3, eb
+    eb = assert_cube_close(bf16, ref, rtol=3e-3, small_abs=3e-6, label="bf16 mlp")
     e32 = assert_cube_close(fp32, ref, rtol=1e-4, label="fp32 mlp")
     print(f"mlp render {list(kw)}: f16 {e16}, bf16 {eb}, fp32 {e32}")
     # the network matters: a zero network gives a different cube
@@ -84,13 +90,15 @@ def test_render_mlp_vs_oracle(rt, orc, kw):
     assert np.abs(plain - ref).max() > 1e-2 * np.abs(ref).max()
 
 
-def test_render_mlp_neural_workload_sampled(rt, orc):
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_render_mlp_neural_workload_sampled(rt, orc, prec):
     """512x512 px, 128 channels, 256 samples (the neural-field workload) in the launch
-    configuration of the benchmark; the oracle computes 48 sampled spectra."""
+    configuration of the benchmark; the oracle computes 48 sampled spectra; 3e-3 per voxel
+    above 1e-3 of the peak for either operand format."""
     import torch
     p, w = neural_case(2)
     dd = rt.DeviceDisk(p)
-    net = rt.DeviceMLP(w, precision="f16")
+    net = rt.DeviceMLP(w, precision=prec)
     cube = rt.rt_render_mlp(p, dd, net).cpu().numpy()
     torch.cuda.synchronize()
     flux = cube.sum(axis=0).ravel()
@@ -102,5 +110,5 @@ def test_render_mlp_neural_workload_sampled(rt, orc):
     peak = np.abs(ref).max()
     big = np.abs(ref) > 1e-3 * peak
     rel = np.abs(got - ref)[big] / np.abs(ref)[big]
-    print(f"neural workload: {big.sum()} voxels, max rel {rel.max():.3e}")
+    print(f"neural workload {prec}: {big.sum()} voxels, max rel {rel.max():.3e}")
     assert big.sum() > 500 and rel.max() <= 3e-3
