@@ -34,28 +34,32 @@ sys.path.insert(0, ROOT)
 METRIC = "G sample*channel evals/s (forward render)"
 UNIT = "Gevals/s"
 L2_BYTES = 126 * 2 ** 20
-# B300 pipe model (measured: 128 FFMA lanes/clk/SM, 32 MUFU.EX2/clk/SM). Per forward
-# evaluation 6 FP32 operations (issued packed, two channels per instruction) + 2 EX2.
-EVALS_PER_CLK_SM = 16.0      # dense march: 2 MUFU.EX2 per eval at 32/clk/SM (FP32 ops packed x2)
-# MUFU issue slots (EX2 = 1, other MUFU functions run at half rate = 2) of the per-sample
-# physics with gas: EX2 x4, RSQ x3, LG2 x2, RCP x3, SQRT x1, plus the channel window (LG2,
-# SQRT, RCP): 4 + 2 x 12 = 28
-PHYS_MUFU_SLOTS = 28
-MUFU_SLOTS_PER_CLK_SM = 32.0
-ADJ_EVALS_PER_CLK_SM = 128.0 / 24.0  # adjoint: 24 FP32 ops per eval at 128/clk/SM (5 EX2: below)
+# Algorithmic MUFU operations of the per-sample physics of the forward march with gas
+# (sample_physics and its channel window): EX2 x4 (two CO edges, LTE factor, Boltzmann factor
+# of the source), RSQRT x3 (radius, Keplerian factor, line width), LG2 x3 (radius, LTE table,
+# window), RCP x4 (CO edges, 1/T, source quotient, window), SQRT x2 (Keplerian factor, window).
+PHYS_MUFU_OPS = {"ex2": 4, "rsqrt": 3, "lg2": 3, "rcp": 4, "sqrt": 2}
+# The adjoint's recompute of a sample's physics with its local derivatives (physics_jac) and
+# window: EX2 x4, RSQRT x3, LG2 x3, RCP x4, SQRT x2 as well
+JAC_MUFU_OPS = {"ex2": 4, "rsqrt": 3, "lg2": 3, "rcp": 4, "sqrt": 2}
+# Per sample-channel evaluation: forward march 2 EX2 + 6 FP32 (three packed two-channel
+# instructions); in the adjoint the forward pass the same, the segment recompute 1 EX2 + 3 FP32,
+# the reverse pass 2 EX2 + 15 FP32
+EVAL_EX2 = {"fwd": 2, "rec": 1, "rev": 2}
+EVAL_FP32 = {"fwd": 6, "rec": 3, "rev": 15}
 try:
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as _f:
         PEAKS = json.load(_f)
 except (OSError, ValueError):
     PEAKS = {}
-# FLOPs of one network evaluation on the tensor cores (64 -> 4 x 128 -> 16 padded outputs)
-MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 16)
+# FLOPs of one network evaluation as the method defines it: 2 x (64x128 + 3x128x128 + 128x4)
+MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 4)
 # DRAM bytes of one forward launch on the observation-scale workload (ncu, dram__bytes_read +
-# dram__bytes_write; the cube stays in L2 at the end of the launch)
-FWD_DRAM_BYTES = 3_334_912 + 25_600
+# dram__bytes_write of march_fwd_kernel<8,8,0>; the cube stays in L2 at the end of the launch)
+FWD_DRAM_BYTES = 3_343_616 + 31_232
 # DRAM bytes (read + write) of one fused-adjoint launch on the same workload (ncu capture of
-# march_adj_kernel<8, 8, 1>; most of it is the per-segment sample records reaching DRAM)
-ADJ_DRAM_BYTES = 52_092_416 + 501_120_768
+# march_adj_kernel<8, 8, 1>)
+ADJ_DRAM_BYTES = 52_613_120 + 500_046_080
 N_SM = 148
 SM_MAX_MHZ = 2032.0
 
@@ -138,17 +142,48 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def pipe_peaks(index: int):
+    """Measured rates of the arithmetic the march is built from (rt_pipe_peak), with the SM
+    clock sampled while the probes run: results per second per SM (the roofline
+    denominators, at the clock the probes ran at) and per SM clock."""
+    from paper_2509_03623_b300 import _rt
+    clk = ClockSampler(index)
+    clk.start()
+    time.sleep(0.15)
+    out = {}
+    for op in ("ffma", "ffma2", "ex2", "rsqrt", "lg2", "rcp", "sqrt", "tanh", "tanh_f16x2"):
+        best = max((_rt.rt_pipe_peak(op, 4096) for _ in range(3)), key=lambda r: r["per_s_sm"])
+        out[op] = {"per_s_sm": best["per_s_sm"], "ms": best["ms"]}
+    c = clk.stop()
+    mhz = c["sm_mhz"] or SM_MAX_MHZ
+    for v in out.values():
+        v["per_clk_sm"] = v["per_s_sm"] / (mhz * 1e6)
+    return {"ops": out, "sm_mhz_during_probe": mhz, "clock_reasons": c["reasons"],
+            "note": "rt_pipe_peak: one wave of blocks, 8 independent chains per thread; "
+                    "results per second per SM from CUDA events, per clock from the SM clock "
+                    "sampled by nvidia-smi during the probes (the cycle counter clock64 does not "
+                    "run at the SM clock on this part)"}
+
+
+def mufu_slots(ops: dict, peaks: dict) -> float:
+    """EX2-equivalent MUFU issue slots of a set of operations: each operation weighted by
+    (measured EX2 rate) / (its measured rate)."""
+    r_ex2 = peaks["ops"]["ex2"]["per_s_sm"]
+    return sum(n * r_ex2 / peaks["ops"][op]["per_s_sm"] for op, n in ops.items())
+
+
 def workload(seed: int = 0):
     from paper_2509_03623_b300 import synth
     return synth.config_observation(seed)
 
 
-def cpu_oracle_sample(p, budget_s: float, seed: int = 0):
-    """Time the FP64 oracle on a bounded random pixel sample of workload p."""
+def cpu_oracle_sample(p, budget_s: float, seed: int = 0, cores: int = 0):
+    """Time the FP64 oracle on a bounded random pixel sample of workload p, on `cores` host
+    threads (0: all)."""
     import oracle
     oracle.build()
     rng = np.random.default_rng(seed)
-    cores = os.cpu_count() or 1
+    cores = cores or os.cpu_count() or 1
     pix = rng.choice(p.nx * p.ny, size=64, replace=False)
     t0 = time.perf_counter()
     oracle.render_pixels(p, pix, nthreads=cores)
@@ -174,7 +209,12 @@ def config_of(p, extra=None):
 
 def serving_leg(dev, n=256, rate_hz=200.0, budget=40 << 30, max_inflight=8):
     """Poisson-arriving mix of renders and gradients (sizes drawn per request) through the
-    continuous-batching server; the same requests run back to back is the serial baseline."""
+    continuous-batching server (max_inflight streams), and the same requests through the same
+    server with one request at a time (FIFO, one stream) under the same arrival trace; then
+    both with every request submitted at once (saturated); then the same requests called
+    back to back without the server, and the render requests as serial plain FP32 renders.
+    Overlap on the device: the intervals between the events recorded on each request's
+    stream before and after its kernels."""
     import torch
     from paper_2509_03623_b300 import _rt, serve, synth
     mix = synth.request_mix(n, seed=0, rate_hz=rate_hz)
@@ -193,7 +233,38 @@ def serving_leg(dev, n=256, rate_hz=200.0, budget=40 << 30, max_inflight=8):
             prep.append((rq, dd, None, None, torch.empty(shape, dtype=torch.float32, device=dev)))
     evals = sum(rq.problem.evals for rq in mix)
     torch.cuda.synchronize()
-    # serial baseline: one request after another on one stream
+
+    def served(inflight, paced):
+        with serve.Server(mem_budget_bytes=budget, max_inflight=inflight) as srv:
+            tickets = []
+            t0 = time.perf_counter()
+            for rq, dd, tgt, g, cube in prep:
+                if paced:
+                    delay = t0 + rq.t_arrival_s - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                if rq.adjoint:
+                    tickets.append(srv.submit_adjoint(rq.problem, dd, g, target=tgt))
+                else:
+                    tickets.append(srv.submit_render(rq.problem, dd, cube))
+            lat = []
+            for t in tickets:
+                state, ms = srv.wait(t, 600000)
+                if state != "done":
+                    raise RuntimeError(f"request failed: {srv.error(t)}")
+                lat.append(ms)
+            wall = time.perf_counter() - t0
+            iv = [srv.device_times(t) for t in tickets]
+        lat = np.array(lat)
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "throughput": evals / wall / 1e9, "wall_s": wall,
+                "max_concurrent": serve.max_overlap(iv)}
+
+    mixed = served(max_inflight, True)
+    fifo = served(1, True)
+    sat = served(max_inflight, False)
+    sat1 = served(1, False)
+    # back to back on one stream without the server; render requests as plain FP32 renders
     t0 = time.perf_counter()
     for rq, dd, tgt, g, cube in prep:
         if rq.adjoint:
@@ -201,34 +272,42 @@ def serving_leg(dev, n=256, rate_hz=200.0, budget=40 << 30, max_inflight=8):
         else:
             _rt.rt_render(rq.problem, dd, cube)
     torch.cuda.synchronize()
-    serial_s = time.perf_counter() - t0
-    # served: submit at the arrival times
-    with serve.Server(mem_budget_bytes=budget, max_inflight=max_inflight) as srv:
-        tickets = []
-        t0 = time.perf_counter()
-        for rq, dd, tgt, g, cube in prep:
-            delay = t0 + rq.t_arrival_s - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            if rq.adjoint:
-                tickets.append(srv.submit_adjoint(rq.problem, dd, g, target=tgt))
-            else:
-                tickets.append(srv.submit_render(rq.problem, dd, cube))
-        lat = []
-        for t in tickets:
-            state, ms = srv.wait(t, 600000)
-            if state != "done":
-                raise RuntimeError(f"request failed: {srv.error(t)}")
-            lat.append(ms)
-        wall = time.perf_counter() - t0
-    lat = np.array(lat)
-    return {"requests": n, "arrival_rate_hz": rate_hz, "adjoint_requests": int(sum(r.adjoint for r in mix)),
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "throughput": evals / wall / 1e9, "unit": UNIT,
-            "wall_s": wall, "serial_throughput": evals / serial_s / 1e9, "serial_s": serial_s,
+    direct_s = time.perf_counter() - t0
+    renders = [(rq, dd, cube) for rq, dd, tgt, g, cube in prep if not rq.adjoint]
+    t0 = time.perf_counter()
+    for rq, dd, cube in renders:
+        _rt.rt_render_plain(rq.problem, dd, cube)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    plain_evals = sum(rq.problem.evals for rq, _, _ in renders)
+    t0 = time.perf_counter()
+    for rq, dd, cube in renders:
+        _rt.rt_render(rq.problem, dd, cube)
+    torch.cuda.synchronize()
+    fused_s = time.perf_counter() - t0
+    return {"requests": n, "arrival_rate_hz": rate_hz,
+            "adjoint_requests": int(sum(r.adjoint for r in mix)),
+            "p50_ms": mixed["p50_ms"], "p99_ms": mixed["p99_ms"], "mean_ms": mixed["mean_ms"],
+            "throughput": mixed["throughput"], "unit": UNIT, "wall_s": mixed["wall_s"],
+            "max_concurrent": mixed["max_concurrent"],
+            "serial_p50_ms": fifo["p50_ms"], "serial_p99_ms": fifo["p99_ms"],
+            "serial_throughput": fifo["throughput"], "serial_max_concurrent": fifo["max_concurrent"],
+            "saturated": {"throughput": sat["throughput"], "p50_ms": sat["p50_ms"],
+                          "p99_ms": sat["p99_ms"], "max_concurrent": sat["max_concurrent"],
+                          "serial_throughput": sat1["throughput"],
+                          "serial_p50_ms": sat1["p50_ms"], "serial_p99_ms": sat1["p99_ms"],
+                          "note": "all requests submitted at once"},
+            "direct_back_to_back_throughput": evals / direct_s / 1e9,
+            "render_requests_plain_fp32_serial": plain_evals / plain_s / 1e9,
+            "render_requests_fused_serial": plain_evals / fused_s / 1e9,
             "nominal_evals": evals, "max_inflight": max_inflight, "budget_bytes": budget,
             "workload": "256 requests, Poisson 200/s, pixels {128,256,512}^2, channels "
-                        "{32,64,128}, samples {128,256,1024}, 30% gradients, 40 GB budget"}
+                        "{32,64,128}, samples {128,256,1024}, 30% gradients, 40 GB budget",
+            "note": "serial_* = the same server with one request at a time (one stream, FIFO) "
+                    "under the same arrival trace; max_concurrent = most requests whose device "
+                    "intervals (events before / after their kernels on their streams) "
+                    "intersect; render_requests_* = the 70% render requests called back to "
+                    "back: plain FP32 march vs the fused march"}
 
 
 def chain_leg(dev, reps=50):
@@ -336,6 +415,35 @@ def plain_leg(dev, flush, p, dd, fwd_value, reps=5):
                     "forward_speedup = this line's value / plain value"}
 
 
+def dense_leg(dev, flush, p, dd, fwd_value, reps=10):
+    """The dense FP32 march (rt_render_dense: the fused kernel visiting every sample and
+    every channel, node-array reads) on the benchmark's workload; CUDA-event time per render,
+    L2 flushed before each."""
+    import torch
+    from paper_2509_03623_b300 import _rt
+    cube = torch.empty((p.nch, p.ny, p.nx), dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        _rt.rt_render_dense(p, dd, cube, stream=st)
+    ms = []
+    for i in range(reps):
+        flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _rt.rt_render_dense(p, dd, cube, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    v = p.evals / (t * 1e-3) / 1e9
+    return {"workload": p.name, "ms": t, "value": v, "unit": "Gevals/s",
+            "forward_speedup": fwd_value / v,
+            "note": "dense FP32 march on the same GPU: the forward kernel without the gas sample "
+                    "range, the channel window and the corner quads (same accuracy); "
+                    "forward_speedup = this line's value / dense value"}
+
+
 def _grid3d_time(dev, flush, p, render, dg, reps):
     """Median CUDA-event time [ms] of render(p, dg, cube, stream) with L2 flushed before
     each timed call."""
@@ -394,51 +502,57 @@ def sph_leg(dev, flush, reps=10):
 
 
 def neural_leg(dev, flush, reps=5):
-    """Neural-field workload (512x512 px, 128 channels, 256 samples): tensor-core network
-    with FP16 and BF16 operands, the FP32 network (cuBLAS, no TF32) driving the same march, and
-    the grid-field march alone; then forward plus adjoint through the march and the network
-    (loss sum (I - I*)^2 against a fixed target) with FP16 and BF16 operands."""
+    """Neural-field workload (512x512 px, 128 channels, 256 samples): the tensor-core network
+    with BF16 operands (three-pass split product, the workload's precision) and FP16 operands
+    (one pass), the FP32 network (cuBLAS, no TF32) driving the same march, and the grid-field
+    march alone; then forward plus adjoint through the march and the network (loss
+    sum (I - I*)^2 against a fixed target) with either operand format."""
     import torch
     from paper_2509_03623_b300 import _rt, neural, synth
     p = synth.config_neural(0)
     w = synth.mlp_weights(7)
-    dd = _rt.DeviceDisk(p, dev)
+    dd = _rt.DeviceDisk(p)
     cube = torch.empty((p.nch, p.ny, p.nx), dtype=torch.float32, device=dev)
-    nets = {k: _rt.DeviceMLP(w, dev, precision=k) for k in ("f16", "bf16")}
-    tgt = (_rt.rt_render_mlp(p, dd, nets["f16"]) * 1.05).contiguous()
+    nets = {k: _rt.DeviceMLP(w, dev, precision=k) for k in ("bf16", "f16")}
+    tgt = (_rt.rt_render_mlp(p, dd, nets["bf16"]) * 1.05).contiguous()
     runs = {
         "grid_only": lambda: _rt.rt_render(p, dd, cube),
-        "mlp_f16": lambda: _rt.rt_render_mlp(p, dd, nets["f16"], cube),
         "mlp_bf16": lambda: _rt.rt_render_mlp(p, dd, nets["bf16"], cube),
+        "mlp_f16": lambda: _rt.rt_render_mlp(p, dd, nets["f16"], cube),
         "mlp_fp32": lambda: neural.render_mlp_fp32(p, dd, nets["f16"], cube),
-        "fwd_adjoint_f16": lambda: _rt.rt_render_mlp_adjoint(p, dd, nets["f16"], target=tgt,
-                                                             cube_out=cube),
         "fwd_adjoint_bf16": lambda: _rt.rt_render_mlp_adjoint(p, dd, nets["bf16"], target=tgt,
                                                               cube_out=cube),
+        "fwd_adjoint_f16": lambda: _rt.rt_render_mlp_adjoint(p, dd, nets["f16"], target=tgt,
+                                                             cube_out=cube),
     }
     out = {"workload": p.name, "nominal_evals": p.evals,
            "mlp_samples": p.nx * p.ny * p.n_samples, "unit": UNIT}
-    # the network kernel alone on as many points as the render has samples (tensor roofline)
+    # the network kernels alone on as many points as the render has samples (tensor roofline)
     nmlp = p.nx * p.ny * p.n_samples
     xy = torch.rand((nmlp, 2), device=dev)
     yo = torch.empty((nmlp, 4), device=dev)
-    _rt.rt_mlp_eval(nets["f16"], xy, yo)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        _rt.rt_mlp_eval(nets["f16"], xy, yo)
-    e1.record()
-    torch.cuda.synchronize()
-    mlp_ms = e0.elapsed_time(e1) / reps
-    tf = nmlp * MLP_FLOP / (mlp_ms * 1e-3) / 1e12
-    out["mlp_kernel_roofline"] = {
-        "bound": "tensor", "achieved": tf, "peak": PEAKS.get("bf16_tflops", 1800.0),
-        "unit": "TFLOP/s", "frac": tf / PEAKS.get("bf16_tflops", 1800.0), "traffic": None,
-        "ms": mlp_ms, "points": nmlp,
-        "note": "rt_mlp_eval (FP16 operands, FP32 accumulate) on random inputs; FLOPs "
-                "2 x (64x128 + 3x128x128 + 128x16) per point; peak = measured bf16 burst "
-                "(FP16 has the same dense rate)"}
+    peak = PEAKS.get("bf16_tflops", 1800.0)
+    for prec, passes in (("bf16", 3), ("f16", 1)):
+        _rt.rt_mlp_eval(nets[prec], xy, yo)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            _rt.rt_mlp_eval(nets[prec], xy, yo)
+        e1.record()
+        torch.cuda.synchronize()
+        mlp_ms = e0.elapsed_time(e1) / reps
+        tf = nmlp * MLP_FLOP / (mlp_ms * 1e-3) / 1e12
+        out[f"mlp_kernel_roofline_{prec}"] = {
+            "bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+            "frac": tf / peak, "traffic": None, "ms": mlp_ms, "points": nmlp,
+            "tensor_passes": passes,
+            "note": f"rt_mlp_eval ({prec.upper()} operands, FP32 accumulate) on random inputs; "
+                    "achieved = the method's 115,712 FLOP per point / time; peak = measured "
+                    "bf16 burst (FP16 has the same dense rate); "
+                    + ("the split product issues three MMAs per K step (hi x hi, hi x lo, "
+                       "lo x hi), so the tensor pipe does 3x the algorithmic FLOPs"
+                       if passes == 3 else "one MMA per K step")}
     del xy, yo
     for name, fn in runs.items():
         fn()
@@ -500,6 +614,7 @@ def run_ours(args):
     executed = _rt.rt_count_gas_samples(p, dd) * p.nch
     _, phys_samples, computed = _rt.rt_render_work(p, dd, cube)  # untimed: work of one launch
     launches_per_step = _rt.rt_render_launch_count(p, dd)  # corner-quad packing + march
+    peaks = pipe_peaks(local) if rank == 0 else None
 
     def barrier():
         if world > 1:
@@ -533,6 +648,9 @@ def run_ours(args):
 
     # forward + fused adjoint (sum-of-squares loss against a fixed target cube)
     target = (cube * 1.05).contiguous()
+    adj_work = torch.zeros(4, dtype=torch.int64, device=dev)
+    _rt.rt_render_adjoint(p, dd, target=target, cube_out=None, work=adj_work)  # untimed count
+    adj_work = [int(x) for x in adj_work.cpu()]
     adj_steps = max(3, args.steps // 4)
     for _ in range(2):
         _rt.rt_render_adjoint(p, dd, target=target, cube_out=None)
@@ -591,11 +709,22 @@ def run_ours(args):
     evals = p.evals * world
     value = job_rate(p.evals, world, t_max)
     if rank == 0:
-        f_mhz = clocks["sm_mhz"] or SM_MAX_MHZ
-        peak = EVALS_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e9
-        achieved = executed / (ms * 1e-3) / 1e9
-        mufu_peak = MUFU_SLOTS_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e9
-        mufu_achieved = (2 * computed + PHYS_MUFU_SLOTS * phys_samples) / (ms * 1e-3) / 1e9
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        ops = peaks["ops"]
+        # forward: MUFU issue slots (EX2-equivalent) of one launch
+        slots_sample = mufu_slots(PHYS_MUFU_OPS, peaks)
+        fwd_slots = EVAL_EX2["fwd"] * computed + slots_sample * phys_samples
+        mufu_peak = ops["ex2"]["per_s_sm"] * n_sm / 1e9
+        mufu_achieved = fwd_slots / (ms * 1e-3) / 1e9
+        fma_peak = ops["ffma"]["per_s_sm"] * n_sm / 1e9
+        # adjoint: its own counts (gas samples, evaluations of its three passes)
+        a_gas, a_fwd, a_rec, a_rev = adj_work
+        adj_slots = (EVAL_EX2["fwd"] * a_fwd + EVAL_EX2["rec"] * a_rec + EVAL_EX2["rev"] * a_rev
+                     + (slots_sample + mufu_slots(JAC_MUFU_OPS, peaks)) * a_gas)
+        adj_fp32 = EVAL_FP32["fwd"] * a_fwd + EVAL_FP32["rec"] * a_rec + EVAL_FP32["rev"] * a_rev
+        adj_mufu_frac = adj_slots / (adj_ms * 1e-3) / 1e9 / mufu_peak
+        adj_fma_frac = adj_fp32 / (adj_ms * 1e-3) / 1e9 / fma_peak
+        adj_bind = "mufu" if adj_mufu_frac >= adj_fma_frac else "fma"
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max,
@@ -609,21 +738,18 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": mufu_achieved, "peak": mufu_peak,
                          "unit": "G MUFU slots/s", "frac": mufu_achieved / mufu_peak,
                          "traffic": FWD_DRAM_BYTES,
-                         "note": "binding pipe MUFU (32 EX2/clk/SM measured; other MUFU "
-                                 "functions take 2 slots). achieved = algorithmic MUFU slots of "
-                                 "one launch / its CUDA-event time: 2 EX2 per sample-channel "
+                         "note": "binding pipe MUFU. achieved = algorithmic MUFU issue slots of "
+                                 "one step / its CUDA-event time: 2 EX2 per sample-channel "
                                  "evaluation computed (after the channel window, counted by "
-                                 "rt_render_work) + 28 per sample with gas (physics and "
-                                 "window); peak = 32 x 148 SMs x 2032 MHz; traffic = DRAM "
-                                 "bytes of one launch (ncu)",
+                                 "rt_render_work) + the per-sample physics with gas (its MUFU "
+                                 "operations, each weighted by the measured EX2 rate / its own "
+                                 "rate: slots_per_sample); peak = measured EX2 rate per SM "
+                                 "(pipe_peaks) x SMs, at the clock the probe ran at; traffic = "
+                                 "DRAM bytes of one launch (ncu)",
                          "computed_evals": computed, "physics_samples": phys_samples,
-                         "dense_equivalent": {
-                             "achieved": achieved, "peak": peak, "unit": UNIT,
-                             "frac": achieved / peak,
-                             "note": "executed evaluations of the dense march (samples inside "
-                                     "the gas grid x channels) that the windowed kernel "
-                                     "replaces / time, vs 16 evals/clk/SM"},
-                         "frac_at_measured_clock": mufu_achieved / (mufu_peak * f_mhz / SM_MAX_MHZ)},
+                         "slots_per_sample": slots_sample,
+                         "peak_source": "measured (rt_pipe_peak, this run)"},
+            "pipe_peaks": peaks,
             "e2e": {"value": evals / (e2e_max * 1e-3) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_max,
@@ -633,25 +759,31 @@ def run_ours(args):
             "gpu_launches": args.steps * launches_per_step,
             "fwd_adjoint": {"value": evals / (adj_max * 1e-3) / 1e9, "unit": UNIT,
                             "ms_per_step": adj_max, "steps": adj_steps,
-                            "note": "fused forward + reverse march, node gradients summed in per-block "
-                                    "FP32 copies and reduced in FP64, "
-                                    "loss sum (I - I*)^2 formed in the kernel; nominal evals",
+                            "work": {"gas_samples": a_gas, "forward_evals": a_fwd,
+                                     "recompute_evals": a_rec, "reverse_evals": a_rev},
+                            "note": "fused forward + reverse march, node gradients summed in "
+                                    "per-block FP32 copies and reduced in FP64, loss "
+                                    "sum (I - I*)^2 formed in the kernel; nominal evals",
                             "roofline": {
-                                "bound": "alu",
-                                "achieved": executed / (adj_ms * 1e-3) / 1e9,
-                                "peak": ADJ_EVALS_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e9,
-                                "unit": UNIT,
-                                "frac": (executed / (adj_ms * 1e-3) / 1e9)
-                                        / (ADJ_EVALS_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e9),
+                                "bound": "alu", "pipe": adj_bind,
+                                "frac": max(adj_mufu_frac, adj_fma_frac),
+                                "achieved": (adj_slots if adj_bind == "mufu" else adj_fp32)
+                                            / (adj_ms * 1e-3) / 1e9,
+                                "peak": mufu_peak if adj_bind == "mufu" else fma_peak,
+                                "unit": "G MUFU slots/s" if adj_bind == "mufu" else "G FP32 op/s",
+                                "mufu_frac": adj_mufu_frac, "fma_frac": adj_fma_frac,
                                 "traffic": ADJ_DRAM_BYTES,
-                                "note": "executed evals / step time (memsets, march kernel, "
-                                        "gradient-copy sums); peak: 24 FP32 ops per eval "
-                                        "(forward 6, batch-start recompute 3, reverse 15) at 128 "
-                                        "lanes/clk/SM, the binding pipe (5 MUFU.EX2 per eval need "
-                                        "0.156 of 0.1875 clk)"}},
+                                "note": "computed work of one step (rt_render_adjoint_work) / "
+                                        "its time: MUFU slots = 2 EX2 per forward-pass and "
+                                        "reverse-pass evaluation + 1 per segment-recompute "
+                                        "evaluation + the physics of each gas sample twice "
+                                        "(forward pass; recompute with local derivatives); "
+                                        "FP32 ops = 6 + 3 + 15 per evaluation of the three "
+                                        "passes; peaks measured (pipe_peaks)"}},
             "clocks": clocks,
         }
         out["plain_fp32"] = plain_leg(dev, flush, p, dd, value / world)
+        out["dense_fp32"] = dense_leg(dev, flush, p, dd, value / world)
         if world == 1 and not args.no_serving:
             out["field_chain"] = chain_leg(dev)
             out["box3d"] = box_leg(dev, flush)
@@ -661,6 +793,9 @@ def run_ours(args):
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_oracle_sample(p, args.cpu_budget)
             out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            c1 = cpu_oracle_sample(p, min(args.cpu_budget, 8.0), seed=1, cores=1)
+            out["cpu_baseline"]["one_core"] = {k: c1[k] for k in ("value", "unit", "cores",
+                                                                 "sample")}
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -692,7 +827,7 @@ def run_profile(args):
         p = synth.config_neural(0).replace(nx=px, ny=px)
     dd = _rt.DeviceDisk(p, dev)
     if name in ("neural", "neural_adjoint", "mlp_eval"):
-        net = _rt.DeviceMLP(synth.mlp_weights(7), dev, precision="f16")
+        net = _rt.DeviceMLP(synth.mlp_weights(7), dev, precision=args.profile_prec)
     cube = _rt.rt_render(p, dd) if name not in ("neural", "neural_adjoint", "mlp_eval") else \
         _rt.rt_render_mlp(p, dd, net)
     tgt = (cube * 1.05).contiguous()
@@ -728,6 +863,8 @@ def main():
     ap.add_argument("--profile-reps", type=int, default=3)
     ap.add_argument("--profile-px", type=int, default=128,
                     help="image size of the neural-field workload in --profile mode")
+    ap.add_argument("--profile-prec", default="bf16", choices=["bf16", "f16"],
+                    help="network operand format in --profile mode")
     args = ap.parse_args()
     if args.profile:
         return run_profile(args)

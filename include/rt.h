@@ -237,6 +237,20 @@ int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geo
                       const float *target, float *cube_out, const rt_grads *grads, void *stream);
 
 /*
+ * rt_render_adjoint_work -- rt_render_adjoint (same arguments, results and errors) that also
+ * counts the work its kernel does (measurement support; no counterpart in the paper).
+ * `work` is a DEVICE pointer to four unsigned 64-bit counters, overwritten (stream-ordered):
+ *   [0] samples whose physics found gas (opacity > 0) in the forward pass,
+ *   [1] sample-channel evaluations computed in the forward pass (after the channel window),
+ *   [2] evaluations computed where each 64-sample segment's optical depths are recomputed,
+ *   [3] evaluations computed in the reverse pass.
+ */
+int rt_render_adjoint_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
+                           const rt_view *view, const rt_line *line, const float *dL_dcube,
+                           const float *target, float *cube_out, const rt_grads *grads,
+                           unsigned long long *work, void *stream);
+
+/*
  * rt_render_adjoint_noalloc -- rt_render_adjoint for callers that cannot allocate device
  * memory. The paper has no counterpart: this is a deployment variant of the same fused
  * adjoint. Some callers cannot call cudaMalloc or cudaMallocAsync, or have it called for
@@ -624,6 +638,17 @@ int rt_request_error(rt_server *s, uint64_t ticket, char *buf, size_t n);
 /* Counters: requests queued and running, bytes of budget in use, requests completed. */
 int rt_server_stats(rt_server *s, int *queued, int *running, size_t *bytes_in_use,
                     uint64_t *completed);
+
+/*
+ * rt_request_device_times -- when a finished request's work ran on the device (measurement
+ * support; no counterpart in the paper): the times [ms] at which its stream reached the
+ * points just before and just after its kernels, relative to an event the server recorded at
+ * creation (CUDA events on the request's stream). Intervals of different requests that
+ * intersect mean their work was in flight on the device at the same time.
+ * Returns RT_OK, RT_EINVAL (null argument, fake device), RT_ENOTFOUND, RT_EBUSY (not finished)
+ * or RT_ECUDA.
+ */
+int rt_request_device_times(rt_server *srv, uint64_t ticket, double *start_ms, double *end_ms);
 
 /* rt_server_destroy -- cancel queued requests, wait for running ones (their device work is
    finite), release streams and the scheduler thread. */

@@ -128,6 +128,9 @@ def lib():
             L.rt_render_adjoint.argtypes = base + [C.c_void_p, C.c_void_p, C.c_void_p,
                                                    P(rt_grads), C.c_void_p]
             L.rt_render_adjoint.restype = C.c_int
+            L.rt_render_adjoint_work.argtypes = base + [C.c_void_p, C.c_void_p, C.c_void_p,
+                                                        P(rt_grads), C.c_void_p, C.c_void_p]
+            L.rt_render_adjoint_work.restype = C.c_int
             L.rt_render_adjoint_noalloc.argtypes = L.rt_render_adjoint.argtypes
             L.rt_render_adjoint_noalloc.restype = C.c_int
             L.rt_surface_powerlaw_grad.argtypes = [P(rt_grid), C.c_void_p, C.c_void_p,
@@ -344,12 +347,14 @@ def rt_render_work(problem, fields=None, out=None, stream=None):
 
 
 def rt_render_adjoint(problem, fields=None, dL_dcube=None, target=None, cube_out=True,
-                      stream=None):
+                      stream=None, work=None):
     """Fused forward + reverse march through the C ABI.
 
     Give exactly one of dL_dcube (gradient of a loss w.r.t. the cube) or target (loss =
     sum (cube - target)^2). Returns (cube or None, grads) with grads a dict of float64 CUDA
-    tensors T, n_h2, vturb [nz][nr], h_lo, h_hi [nr] and loss (1 element)."""
+    tensors T, n_h2, vturb [nz][nr], h_lo, h_hi [nr] and loss (1 element). With `work` (a
+    CUDA int64 tensor of 4 elements) the call is rt_render_adjoint_work, which also counts the
+    kernel's work into it."""
     import torch
     dd = fields if fields is not None else DeviceDisk(problem)
     T, n, vt, hlo, hhi = dd.tensors()
@@ -373,9 +378,16 @@ def rt_render_adjoint(problem, fields=None, dL_dcube=None, target=None, cube_out
     gr = rt_grads(out["T"].data_ptr(), out["n_h2"].data_ptr(), out["vturb"].data_ptr(),
                   out["h_lo"].data_ptr(), out["h_hi"].data_ptr(), out["loss"].data_ptr(),
                   out["vphi"].data_ptr() if vp is not None else None)
-    check(lib().rt_render_adjoint(C.byref(g), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
-                                  _ptr(dL_dcube), _ptr(target), _ptr(cube), C.byref(gr),
-                                  stream_handle(stream)))
+    if work is not None:
+        assert work.is_cuda and work.dtype == torch.int64 and work.numel() >= 4
+        check(lib().rt_render_adjoint_work(C.byref(g), C.byref(f), C.byref(o), C.byref(vw),
+                                           C.byref(ln), _ptr(dL_dcube), _ptr(target),
+                                           _ptr(cube), C.byref(gr), _ptr(work),
+                                           stream_handle(stream)))
+    else:
+        check(lib().rt_render_adjoint(C.byref(g), C.byref(f), C.byref(o), C.byref(vw),
+                                      C.byref(ln), _ptr(dL_dcube), _ptr(target), _ptr(cube),
+                                      C.byref(gr), stream_handle(stream)))
     return cube, out
 
 

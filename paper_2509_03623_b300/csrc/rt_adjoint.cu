@@ -384,6 +384,8 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
   double loss = 0.0;
   float dmx = 0.0f;  // largest |dL/d(network output)| this lane wrote
   const GradSink Gb = block_sink(G, GC);
+  // work counters (only with P.work): samples with gas, evaluations of the three passes
+  unsigned long long wc_gas = 0, wc_fwd = 0, wc_rec = 0, wc_rev = 0;
 
   for (long long u0 = gw; u0 < nunits; u0 += W * NG) {
     {
@@ -423,11 +425,15 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
         }
         const float4 mine = sample_physics<ROT>(P, s_tab, ray, kb + q);
         const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
-        if (!act) continue;
         unsigned act2 = 0;
 #pragma unroll
         for (int m = 0; m < CPL / 2; m++)
           if ((act >> (2 * m)) & 3u) act2 |= 1u << m;
+        if (P.work) {
+          wc_gas += __popc(__ballot_sync(0xffffffffu, mine.x > 0.0f));
+          wc_fwd += (unsigned long long)__popc(act2) * 2 * LPR * 32;
+        }
+        if (!act) continue;
         ph[lane] = mine;
         __syncwarp();
 #pragma unroll 1
@@ -509,6 +515,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
           rb[0] = mine;
           const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
           if (lane == 0) s_act[wib][b] = act;
+          if (P.work) wc_rec += (unsigned long long)__popc(act) * LPR * 32;
           if (!act) continue;
           ph[lane] = mine;
           __syncwarp();
@@ -544,6 +551,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
 #pragma unroll
           for (int m = 0; m < CPL / 2; m++)
             if ((act >> (2 * m)) & 3u) act2 |= 1u << m;
+          if (P.work) wc_rev += (unsigned long long)__popc(act2) * 2 * LPR * 32;
           float2 cur[CPL / 2], Tn[CPL / 2];
 #pragma unroll
           for (int m = 0; m < CPL / 2; m++) {
@@ -630,6 +638,12 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
         }
       }
     }
+  }
+  if (P.work && lane == 0) {
+    atomicAdd(P.work, wc_gas);
+    atomicAdd(P.work + 1, wc_fwd);
+    atomicAdd(P.work + 2, wc_rec);
+    atomicAdd(P.work + 3, wc_rev);
   }
   if (G.loss && target) {
     for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);

@@ -592,6 +592,30 @@ int rtb::check_adjoint_args(const MarchParams &P, const float *dL_dcube, const f
   return RT_OK;
 }
 
+extern "C" int rt_render_adjoint_work(const rt_grid *grid, const rt_fields *fields,
+                                      const rt_geom *geom, const rt_view *view,
+                                      const rt_line *line, const float *dL_dcube,
+                                      const float *target, float *cube_out,
+                                      const rt_grads *grads, unsigned long long *work,
+                                      void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params(grid, fields, geom, view, line, P);
+  if (rc == RT_OK) rc = check_adjoint_args(*P, dL_dcube, target, grads);
+  if (rc == RT_OK && !work) rc = set_error(RT_EINVAL, "null work counters");
+  if (rc == RT_OK) {
+    cudaError_t e = cudaMemsetAsync(work, 0, 4 * sizeof(unsigned long long), (cudaStream_t)stream);
+    if (e != cudaSuccess) rc = set_error(RT_ECUDA, "memset: %s", cudaGetErrorString(e));
+  }
+  if (rc == RT_OK) {
+    P->work = work;
+    rc = launch_adjoint(*P, dL_dcube, target, cube_out, *grads, (cudaStream_t)stream);
+  }
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
 extern "C" int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields,
                                  const rt_geom *geom, const rt_view *view, const rt_line *line,
                                  const float *dL_dcube, const float *target, float *cube_out,

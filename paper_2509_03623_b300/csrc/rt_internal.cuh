@@ -70,8 +70,9 @@ struct MarchParams {
   // h_lo + h_scale o2, h_hi + h_scale o3; nullptr for grid fields alone
   const float4 *mod;
   float h_scale;
-  // optional work counters of the forward kernel (device, 2 x u64): samples with gas whose
-  // physics was evaluated, channel evaluations computed; nullptr for none
+  // optional work counters (device; nullptr for none). Forward kernel, 2 x u64: samples with
+  // gas whose physics was evaluated, channel evaluations computed. Adjoint kernel, 4 x u64:
+  // samples with gas, evaluations of the forward, segment-recompute and reverse passes.
   unsigned long long *work;
   // optional corner quads (pack_cells): per grid cell (i, j) the four nodes its bilinear
   // interpolation reads, {f(i,j), f(i+1,j), f(i,j+1), f(i+1,j+1)}, for T, n_H2, v_turb and

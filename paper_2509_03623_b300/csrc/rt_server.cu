@@ -51,6 +51,8 @@ struct Req {
   Clock::time_point t_submit, t_start, t_done, t_fake_end;
   std::string err;
   Done cb{};
+  // device timestamps: recorded on the request's stream before and after its kernels
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 }  // namespace
@@ -73,6 +75,7 @@ struct rt_server {
   std::vector<Req *> fake_running;
   std::thread sched;
   bool stop = false;
+  cudaEvent_t epoch = nullptr;  // reference of the requests' device timestamps
 };
 
 namespace {
@@ -112,10 +115,20 @@ int launch(rt_server *s, Req *q) {
   if (!P) return rtb::set_error(RT_ENOMEM, "host allocation failed");
   int rc = rtb::build_params(&q->r.grid, &q->r.fields, &q->r.geom, &q->r.view, &q->r.line, P);
   if (rc == RT_OK) {
+    cudaError_t e = cudaEventCreate(&q->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&q->ev1);
+    if (e == cudaSuccess) e = cudaEventRecord(q->ev0, st);
+    if (e != cudaSuccess) rc = rtb::set_error(RT_ECUDA, "request events: %s", cudaGetErrorString(e));
+  }
+  if (rc == RT_OK) {
     if (q->r.kind == RT_REQ_RENDER)
       rc = rtb::launch_forward(*P, q->r.cube, st);
     else
       rc = rtb::launch_adjoint(*P, q->r.dL_dcube, q->r.target, q->r.cube, q->r.grads, st);
+  }
+  if (rc == RT_OK) {
+    cudaError_t e = cudaEventRecord(q->ev1, st);
+    if (e != cudaSuccess) rc = rtb::set_error(RT_ECUDA, "request event: %s", cudaGetErrorString(e));
   }
   delete P;
   if (rc == RT_OK) {
@@ -240,8 +253,11 @@ extern "C" int rt_server_create(size_t mem_budget_bytes, int max_inflight, int m
       e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
       if (e == cudaSuccess) s->streams.push_back(st);
     }
+    if (e == cudaSuccess) e = cudaEventCreate(&s->epoch);
+    if (e == cudaSuccess) e = cudaEventRecord(s->epoch, s->streams[0]);
     if (e != cudaSuccess) {
       for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+      if (s->epoch) cudaEventDestroy(s->epoch);
       delete s;
       return rtb::set_error(RT_ECUDA, "server streams: %s", cudaGetErrorString(e));
     }
@@ -375,7 +391,37 @@ extern "C" int rt_server_destroy(rt_server *s) {
   s->cv_sched.notify_one();
   if (s->sched.joinable()) s->sched.join();  // returns once nothing is running
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
-  for (auto &kv : s->reqs) delete kv.second;
+  for (auto &kv : s->reqs) {
+    if (kv.second->ev0) cudaEventDestroy(kv.second->ev0);
+    if (kv.second->ev1) cudaEventDestroy(kv.second->ev1);
+    delete kv.second;
+  }
+  if (s->epoch) cudaEventDestroy(s->epoch);
   delete s;
+  return RT_OK;
+}
+
+extern "C" int rt_request_device_times(rt_server *s, uint64_t ticket, double *start_ms,
+                                       double *end_ms) {
+  if (!s || !start_ms || !end_ms) return rtb::set_error(RT_EINVAL, "null argument");
+  cudaEvent_t e0, e1;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    Req *q = find_locked(s, ticket);
+    if (!q) return rtb::set_error(RT_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    if (s->fake) return rtb::set_error(RT_EINVAL, "no device timestamps on the fake device");
+    if (q->state != RT_STATE_DONE || !q->ev0 || !q->ev1)
+      return rtb::set_error(RT_EBUSY, "request %llu has not finished on the device",
+                            (unsigned long long)ticket);
+    e0 = q->ev0;
+    e1 = q->ev1;
+  }
+  float a = 0.0f, b = 0.0f;
+  cudaError_t e = cudaEventElapsedTime(&a, s->epoch, e0);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&b, s->epoch, e1);
+  if (e != cudaSuccess) return rtb::set_error(RT_ECUDA, "request times: %s", cudaGetErrorString(e));
+  *start_ms = a;
+  *end_ms = b;
+  rtb::clear_error();
   return RT_OK;
 }

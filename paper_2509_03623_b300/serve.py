@@ -38,11 +38,24 @@ def _declare(L):
     L.rt_server_stats.argtypes = [C.c_void_p, P(C.c_int), P(C.c_int), P(C.c_size_t),
                                   P(C.c_uint64)]
     L.rt_server_destroy.argtypes = [C.c_void_p]
+    L.rt_request_device_times.argtypes = [C.c_void_p, C.c_uint64, P(C.c_double), P(C.c_double)]
     for f in ("rt_server_create", "rt_submit", "rt_poll", "rt_wait", "rt_cancel",
-              "rt_request_error", "rt_server_stats", "rt_server_destroy"):
+              "rt_request_error", "rt_server_stats", "rt_server_destroy",
+              "rt_request_device_times"):
         getattr(L, f).restype = C.c_int
     L._serve_declared = True
     return L
+
+
+def max_overlap(intervals):
+    """Largest number of (start, end) intervals that contain a common instant."""
+    ev = sorted([(a, 1) for a, _ in intervals] + [(b, -1) for _, b in intervals],
+                key=lambda e: (e[0], e[1]))
+    cur = best = 0
+    for _, d in ev:
+        cur += d
+        best = max(best, cur)
+    return best
 
 
 class Server:
@@ -119,6 +132,14 @@ class Server:
         buf = C.create_string_buffer(512)
         _rt.check(self.L.rt_request_error(self.h, C.c_uint64(ticket), buf, 512))
         return buf.value.decode()
+
+    def device_times(self, ticket):
+        """(start, end) [ms] of a finished request's work on the device, relative to the
+        server's creation."""
+        a, b = C.c_double(), C.c_double()
+        _rt.check(self.L.rt_request_device_times(self.h, C.c_uint64(ticket), C.byref(a),
+                                                 C.byref(b)))
+        return a.value, b.value
 
     def stats(self):
         q, r, b, c = C.c_int(), C.c_int(), C.c_size_t(), C.c_uint64()

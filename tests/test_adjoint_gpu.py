@@ -208,3 +208,25 @@ def test_adjoint_corner_quads_vs_oracle(rt, orc):
     e = assert_grads_close(to_np(g), g_ref, label="corner quads")
     print(f"adjoint corner quads: {e}")
     assert_cube_close(cube.cpu().numpy(), ref_cube, label="adjoint cube (corner quads)")
+
+
+def test_adjoint_work_counters(rt, orc):
+    """rt_render_adjoint_work returns the results of rt_render_adjoint and counts its work:
+    the samples with gas equal the forward march's count, the forward and reverse passes
+    evaluate the same channel blocks, and the segment recompute (finer blocks) no more."""
+    import torch
+    p = synth.config_small(8).replace(v_kms=np.linspace(-4, 4, 48))
+    dd = rt.DeviceDisk(p)
+    tgt = torch.tensor(loss_target(orc, p, 8), dtype=torch.float32, device="cuda")
+    cube0, g0 = rt.rt_render_adjoint(p, dd, target=tgt)
+    work = torch.zeros(4, dtype=torch.int64, device="cuda")
+    cube1, g1 = rt.rt_render_adjoint(p, dd, target=tgt, work=work)
+    _, phys, computed = rt.rt_render_work(p, dd)
+    torch.cuda.synchronize()
+    w = [int(x) for x in work.cpu()]
+    assert np.array_equal(cube0.cpu().numpy(), cube1.cpu().numpy())
+    assert_grads_close(to_np(g1), to_np(g0), atol=1e-6, rtol=1e-5, label="with counters")
+    assert w[0] == phys > 0
+    assert w[1] == w[3] > 0 and 0 < w[2] <= w[1]
+    assert w[1] <= p.nx * p.ny * p.n_samples * 64   # at most the dense count (64 = padded lanes)
+    print(f"adjoint work {w}; forward march: {phys} samples, {computed} evaluations")

@@ -155,3 +155,41 @@ def test_results_identical_alone_and_in_mix(serve, orc):
                 a, b = g[k].cpu().numpy(), ref_g[k]
                 assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max(), k
             assert float(g["loss"].item()) == pytest.approx(float(ref_g["loss"][0]), rel=1e-12)
+
+
+@pytest.mark.gpu
+def test_requests_overlap_on_device(serve):
+    """Eight renders that each occupy a few dozen SMs (32x32 px, 64 channels, 2048 samples),
+    submitted together, are in flight on the device at the same time: the intervals between
+    the events the server records on each request's stream before and after its kernels
+    intersect (at least two at one instant), and every cube equals the same render run alone."""
+    import torch
+    from paper_2509_03623_b300 import _rt
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    reqs = [synth.config_small(60 + i).replace(nx=32, ny=32, v_kms=np.linspace(-6, 6, 64),
+                                               n_samples=2048) for i in range(8)]
+    disks = [_rt.DeviceDisk(p) for p in reqs]
+    alone = [_rt.rt_render(p, dd).cpu().numpy() for p, dd in zip(reqs, disks)]
+    torch.cuda.synchronize()
+    with serve.Server(mem_budget_bytes=1 << 30, max_inflight=8) as s:
+        cubes = [torch.empty((p.nch, p.ny, p.nx), device="cuda") for p in reqs]
+        tickets = [s.submit_render(p, dd, c) for p, dd, c in zip(reqs, disks, cubes)]
+        for t in tickets:
+            assert s.wait(t, 60000)[0] == "done", s.error(t)
+        iv = [s.device_times(t) for t in tickets]
+    assert all(b > a for a, b in iv)
+    peak = serve.max_overlap(iv)
+    print(f"device intervals (ms): {[(round(a, 3), round(b, 3)) for a, b in iv]}; "
+          f"max in flight {peak}")
+    assert peak >= 2
+    for c, ref in zip(cubes, alone):
+        assert np.array_equal(c.cpu().numpy(), ref)
+
+
+def test_max_overlap_counts_intersections():
+    from paper_2509_03623_b300.serve import max_overlap
+    assert max_overlap([]) == 0
+    assert max_overlap([(0, 1), (1, 2)]) == 1          # touching ends do not overlap
+    assert max_overlap([(0, 3), (1, 2), (1.5, 4)]) == 3
+    assert max_overlap([(0, 1), (2, 3), (2.5, 5), (4, 6)]) == 2
