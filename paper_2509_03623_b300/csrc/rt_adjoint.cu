@@ -82,7 +82,7 @@ static_assert(J_MN == 4 * (kRec - 2) && J_T > J_MN && J_N > J_MN && J_VPX > J_MN
 // has gas to the record slots rec[32 (i + 1)], i < kRec - 1 (entries 4i .. 4i + 3 of the enum).
 // Returns {kd, a, b, S} as sample_physics does for a sample with gas, and zeros (b = 0 marks
 // "no gas") otherwise. The arithmetic of kd, a, b and S is the same as sample_physics'.
-template <bool ROT>
+template <bool ROT, bool SPEC = false>
 __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float *tab,
                                               const Ray &R, int k, float4 *rec) {
   const float kf = (float)k;
@@ -90,12 +90,12 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   const float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
   const float r2 = fmaf(R.x, R.x, y * y);
   if (!(in_gas(P, z, r2) && k <= R.khi)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  const Cell c = locate(P, z, r2);
-  const NodeVals f = fields_at<ROT>(P, c);
+  const Cell c = locate<SPEC>(P, z, r2);
+  const NodeVals f = fields_at<ROT, SPEC>(P, c);
   float T = f.T, n = f.n, hlo = f.hlo, hhi = f.hhi;
   const float vt = f.vt;
   float mT = 1.0f, mn = 1.0f;
-  if (P.mod) {
+  if (!SPEC && P.mod) {
     const float4 o = __ldg(P.mod + (long long)R.pix * P.n_samples + k);
     mT = ex2(o.x * 1.4426950408889634f);
     mn = ex2(o.y * 1.4426950408889634f);
@@ -105,7 +105,7 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
     hhi = fmaf(P.h_scale, o.w, hhi);
   }
   float X, sa = 0.0f, sb = 0.0f;
-  if (P.hard_edge) {
+  if (!SPEC && P.hard_edge) {
     X = (c.zr >= hlo && c.zr <= hhi) ? P.x_co : 0.0f;
   } else {
     // X = x_co / ((1 + ea)(1 + eb)), ea = 2^{(h_lo - z/r) k}, eb = 2^{(z/r - h_hi) k}
@@ -125,7 +125,7 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   const bool clampT = T < 1e-3f;
   const float Tg = fmaxf(T, 1e-3f);
   float a2, da2T, da2v;
-  if (P.vturb_mach) {
+  if (!SPEC && P.vturb_mach) {
     const float m = fmaf(P.c_mach, vt * vt, P.c_th);
     a2 = Tg * m;
     da2T = m;
@@ -164,7 +164,7 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   for (int e = kJ; e < 4 * (kRec - 1); e++) J[e] = 0.0f;
 #pragma unroll
   for (int i = 0; i < kRec - 1; i++)
-    if (i < kRec - 2 || P.mod || ROT)
+    if (i < kRec - 2 || (!SPEC && P.mod) || ROT)
       rec[(i + 1) * 32] = make_float4(J[4 * i], J[4 * i + 1], J[4 * i + 2], J[4 * i + 3]);
   float4 out;
   out.x = P.kappa_k * (X * n) * F * ia * R.ds;
@@ -346,7 +346,8 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
                      const rt_grads G, float *__restrict__ scratch, int nseg,
                      float4 *__restrict__ dmod, unsigned *__restrict__ dmax,
                      const GradCopies GC) {
-  constexpr bool UNIF = (VAR & 1) != 0;  // equally spaced channels
+  constexpr bool SPEC = (VAR & 4) != 0;  // the common configuration (spec_ok)
+  constexpr bool UNIF = SPEC || (VAR & 1) != 0;  // equally spaced channels
   constexpr bool ROT = (VAR & 2) != 0;   // a rotation field (gradient with respect to it too)
   constexpr int WPB = adj_wpb<LPR>();
   constexpr int R = 32 / LPR;          // rays per warp
@@ -402,7 +403,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
       const long long pix = u * R + rr;
       const bool active = pix < npix;
       const Ray ray = s_ray[wib][gi * R + rr];
-      const int nsamp = __any_sync(0xffffffffu, ray.hit) ? P.n_samples : 0;
+      // the rays' gas sample ranges (samples outside are exact no-ops), counted from klo;
+      // segments and checkpoints are relative to it
+      const int nsamp = __reduce_max_sync(0xffffffffu, max(ray.khi - ray.klo + 1, 0));
 
       // ---------------- forward march with checkpoints every kSeg samples ----------------
       // channel slots in pairs (2m, 2m+1), packed two-lane FP32 instructions
@@ -417,13 +420,14 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
       const float2 mone = make_float2(-1.0f, -1.0f);
       for (int kb = 0; kb < nsamp; kb += LPR) {
         if (kb % kSeg == 0) {
+          // checkpoint: the base plus the compensation the last fold left in tl
 #pragma unroll
           for (int m = 0; m < CPL / 2; m++) {
-            ck[((kb / kSeg) * CPL + 2 * m) * 32 + lane] = tb[m].x;
-            ck[((kb / kSeg) * CPL + 2 * m + 1) * 32 + lane] = tb[m].y;
+            ck[((kb / kSeg) * CPL + 2 * m) * 32 + lane] = tb[m].x + tl[m].x;
+            ck[((kb / kSeg) * CPL + 2 * m + 1) * 32 + lane] = tb[m].y + tl[m].y;
           }
         }
-        const float4 mine = sample_physics<ROT>(P, s_tab, ray, kb + q);
+        const float4 mine = sample_physics<ROT, SPEC>(P, s_tab, ray, ray.klo + kb + q);
         const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
         unsigned act2 = 0;
 #pragma unroll
@@ -457,10 +461,13 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             Tr[m] = Tn;
           }
         }
+        // compensated fold of the batch into the base (Kahan, as in the forward march): tl
+        // carries the batch sum minus the rounding error of the previous fold
 #pragma unroll
         for (int m = 0; m < CPL / 2; m++) {
-          tb[m] = __fadd2_rn(tb[m], tl[m]);
-          tl[m] = make_float2(0.0f, 0.0f);
+          const float2 t = __fadd2_rn(tb[m], tl[m]);
+          tl[m] = __ffma2_rn(__ffma2_rn(tb[m], mone, t), mone, tl[m]);
+          tb[m] = t;
         }
         __syncwarp();
       }
@@ -493,14 +500,14 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
       if (nsamp == 0) continue;
 
       // ---------------- reverse march over segments ----------------
-      const int nseg_ray = (P.n_samples + kSeg - 1) / kSeg;
+      const int nseg_ray = (nsamp + kSeg - 1) / kSeg;
       float2 A[CPL / 2];  // suffix sums of channel slots (2m, 2m+1)
 #pragma unroll
       for (int m = 0; m < CPL / 2; m++) A[m] = make_float2(0.0f, 0.0f);
       float Snext = S_bg;
       for (int seg = nseg_ray - 1; seg >= 0; seg--) {
         const int k0 = seg * kSeg;
-        const int nb = min(NB, (P.n_samples - k0 + LPR - 1) / LPR);
+        const int nb = min(NB, (nsamp - k0 + LPR - 1) / LPR);
         // batch starts of the segment, summed forward from its checkpoint
         float tbs[CPL];
 #pragma unroll
@@ -511,7 +518,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
           for (int j = 0; j < CPL; j++) bs[(b * CPL + j) * 32 + lane] = tbs[j];
           // physics and local derivatives, kept for the reverse pass over this batch
           float4 *rb = rec + (long long)b * kRec * 32;
-          const float4 mine = physics_jac<ROT>(P, s_tab, ray, k0 + b * LPR + q, rb);
+          const float4 mine = physics_jac<ROT, SPEC>(P, s_tab, ray, ray.klo + k0 + b * LPR + q, rb);
           rb[0] = mine;
           const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
           if (lane == 0) s_act[wib][b] = act;
@@ -623,7 +630,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
             float Jv[4 * (kRec - 1)];
 #pragma unroll
             for (int i = 0; i < kRec - 1; i++) {
-              const float4 v = (i < kRec - 2 || P.mod || ROT) ? rb[(i + 1) * 32]
+              const float4 v = (i < kRec - 2 || (!SPEC && P.mod) || ROT) ? rb[(i + 1) * 32]
                                                               : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
               Jv[4 * i] = v.x;
               Jv[4 * i + 1] = v.y;
@@ -631,7 +638,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
               Jv[4 * i + 3] = v.w;
             }
             dmx = fmaxf(dmx, scatter_grad<ROT>(P, Jv, mine.x, mine.z, s.x, s.y, s.z, s.w, Gb,
-                                          dmod ? dmod + (long long)pix * P.n_samples + kb + q
+                                          dmod ? dmod + (long long)pix * P.n_samples + ray.klo + kb + q
                                                : nullptr));
           }
           __syncwarp();
@@ -655,7 +662,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
   }
 }
 
-// Kernel variant of a problem: bit 0 equally spaced channels, bit 1 a rotation field.
+// Kernel variant of a problem: bit 0 equally spaced channels, bit 1 a rotation field; the
+// common configuration without a rotation field (spec_ok, checked after the corner quads are
+// planned) takes variant 5, specialised for it.
 static int adj_variant(const MarchParams &P) {
   return (P.v_uniform ? 1 : 0) | (P.vphi ? 2 : 0);
 }
@@ -838,8 +847,17 @@ static int run_adj(const MarchParams &P, const float *dLdc, const float *target,
     rc = pack_cells(Q, scratch + a.cell_off, stream);
     if (rc != RT_OK) return rc;
   }
-  march_adj_kernel<LPR, CPL, VAR><<<(unsigned)blocks, adj_wpb<LPR>() * 32, 0, stream>>>(
-      Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, dmax, c);
+  bool launched = false;
+  if constexpr (VAR == 1) {
+    if (spec_ok(Q)) {  // the specialised variant (same scratch layout and block count)
+      march_adj_kernel<LPR, CPL, 5><<<(unsigned)blocks, adj_wpb<LPR>() * 32, 0, stream>>>(
+          Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, dmax, c);
+      launched = true;
+    }
+  }
+  if (!launched)
+    march_adj_kernel<LPR, CPL, VAR><<<(unsigned)blocks, adj_wpb<LPR>() * 32, 0, stream>>>(
+        Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, dmax, c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "adjoint launch: %s", cudaGetErrorString(e));
   return sum_copies(P, G, c, a, stream);

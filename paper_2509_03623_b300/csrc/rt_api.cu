@@ -175,6 +175,12 @@ static void fill_common(const rt_geom &o, const rt_view &v, const rt_line &l, do
   P->cos_i = cos(inc);
   P->sin_pa = sin(pa);
   P->cos_pa = cos(pa);
+  // reciprocals for the per-ray setup (the device then multiplies instead of dividing: FP64
+  // division is a long instruction sequence on this part's narrow FP64 pipe)
+  P->inv_wy = P->sin_i != 0.0 ? 1.0 / P->sin_i : 0.0;
+  P->inv_wz = P->cos_i != 0.0 ? -1.0 / P->cos_i : 0.0;
+  P->inv_2a = P->sin_i != 0.0 ? 0.5 / (P->sin_i * P->sin_i) : 0.0;
+  P->inv_ns = v.n_samples > 0 ? 1.0 / v.n_samples : 0.0;
   double hf = v.half_fov_au > 0 ? v.half_fov_au : 1.1 * r_fov;
   P->px = v.nx > 0 ? 2.0 * hf / v.nx : 0.0;
   P->py = v.ny > 0 ? 2.0 * hf / v.ny : 0.0;

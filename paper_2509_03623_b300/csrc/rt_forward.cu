@@ -47,7 +47,7 @@ constexpr float kWinLog2 = 40.0f;  // skipped optical depths are below 2^-40 per
 // per lane, 6 with 4; 4 (128 registers) for the 3-D grids, whose sample physics holds 16
 // node records in flight.
 template <int LPR, int CPL, int MODE>
-__global__ void __launch_bounds__(kWarps * 32, MODE >= 2 ? 4 : (CPL == 8 ? 5 : 6))
+__global__ void __launch_bounds__(kWarps * 32, (MODE == 2 || MODE == 3) ? 4 : (CPL == 8 ? 5 : 6))
     march_fwd_kernel(const __grid_constant__ MarchParams P, float *__restrict__ cube) {
   constexpr int R = 32 / LPR;  // rays marched together by one warp (one work unit)
   constexpr int G = 32 / R;    // work units whose ray setups are computed together
@@ -72,12 +72,13 @@ __global__ void __launch_bounds__(kWarps * 32, MODE >= 2 ? 4 : (CPL == 8 ? 5 : 6
 #pragma unroll
   for (int m = 0; m < H; m++) {
     const int c0 = q + LPR * (2 * m), c1 = c0 + LPR;
-    vp[m] = P.v_uniform ? make_float2(fmaf((float)c0, P.dv, P.v0), fmaf((float)c1, P.dv, P.v0))
+    vp[m] = (MODE >= 4 || P.v_uniform) ? make_float2(fmaf((float)c0, P.dv, P.v0),
+                                                     fmaf((float)c1, P.dv, P.v0))
                         : make_float2(P.v[min(c0, RT_MAX_CH - 1)], P.v[min(c1, RT_MAX_CH - 1)]);
   }
   // the window test needs equally spaced channels; otherwise every block is marched
   // the window is tested in channel-index space; without equal spacing every block is marched
-  const bool windowed = P.v_uniform && P.dv != 0.0f && !P.no_window;
+  const bool windowed = MODE >= 4 || (P.v_uniform && P.dv != 0.0f && !P.no_window);
   const float idv = windowed ? 1.0f / P.dv : 0.0f;
   const float2 mone = make_float2(-1.0f, -1.0f);
   // work counters (lane 0; only with P.work): samples whose physics found gas, channel
@@ -233,9 +234,11 @@ int resident_blocks(const void *kernel, int threads) {
 
 template <int LPR, int CPL>
 static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
+  const bool spec = spec_ok(P);
   auto kern = P.sph ? march_fwd_kernel<LPR, CPL, 3>
-               : P.box ? march_fwd_kernel<LPR, CPL, 2>
-                       : (P.vphi ? march_fwd_kernel<LPR, CPL, 1> : march_fwd_kernel<LPR, CPL, 0>);
+              : P.box ? march_fwd_kernel<LPR, CPL, 2>
+              : P.vphi ? (spec ? march_fwd_kernel<LPR, CPL, 5> : march_fwd_kernel<LPR, CPL, 1>)
+                       : (spec ? march_fwd_kernel<LPR, CPL, 4> : march_fwd_kernel<LPR, CPL, 0>);
   long long npix = (long long)P.nx * P.ny;
   long long units = (npix + (32 / LPR) - 1) / (32 / LPR);
   long long need = (units + kWarps - 1) / kWarps;

@@ -53,8 +53,10 @@ struct MarchParams {
   float x_co, edge_k;       // edge_k = log2(e) / edge_w
   int vturb_mach;
   float c_th, c_mach;       // alpha^2 [km^2 s^-2] = c_th T + vt^2  |  T (c_th + c_mach vt^2)
-  // geometry (double: per-ray setup only)
+  // geometry (double: per-ray setup only); reciprocals of the ray direction's components
+  // (omega = (0, sin i, -cos i); 0 where the component is 0), of 2 sin^2 i and of n_samples
   double sin_i, cos_i, cos_pa, sin_pa, R_cyl, H_cyl, px, py;
+  double inv_wy, inv_wz, inv_2a, inv_ns;
   float vk;                 // sqrt(G M) [km s^-1 au^1/2]
   float vsys;
   // view
@@ -131,13 +133,12 @@ struct Ray {
   int klo, khi;            // samples that can hold gas: klo..khi (khi < klo: none)
 };
 
-// Round v to `bits` significant bits.
+// Round v to `bits` significant bits (scalings by powers of two are exact, so no division).
 __host__ __device__ __forceinline__ double round_bits(double v, int bits) {
   if (v == 0.0) return 0.0;
   int e;
   frexp(v, &e);
-  double q = ldexp(1.0, e - bits);
-  return nearbyint(v / q) * q;
+  return ldexp(nearbyint(ldexp(v, bits - e)), e - bits);
 }
 
 __device__ __forceinline__ float sample_coord(float kf, float base, float base2, float step,
@@ -228,21 +229,21 @@ __device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, b
     // chord through the box, slab by slab (omega = (0, wy, wz), so x is constant)
     if (xs < P.bx0 || xs > P.bx1) ok = false;
     if (wy != 0.0) {
-      double t1 = (P.by0 - P0y) / wy, t2 = (P.by1 - P0y) / wy;
+      double t1 = (P.by0 - P0y) * P.inv_wy, t2 = (P.by1 - P0y) * P.inv_wy;
       lo = fmax(lo, fmin(t1, t2));
       hi = fmin(hi, fmax(t1, t2));
     } else if (P0y < P.by0 || P0y > P.by1) {
       ok = false;
     }
     if (wz != 0.0) {
-      double t1 = (P.bz0 - P0z) / wz, t2 = (P.bz1 - P0z) / wz;
+      double t1 = (P.bz0 - P0z) * P.inv_wz, t2 = (P.bz1 - P0z) * P.inv_wz;
       lo = fmax(lo, fmin(t1, t2));
       hi = fmin(hi, fmax(t1, t2));
     } else if (P0z < P.bz0 || P0z > P.bz1) {
       ok = false;
     }
   } else if (wz != 0.0) {
-    double t1 = (-P.H_cyl - P0z) / wz, t2 = (P.H_cyl - P0z) / wz;
+    double t1 = (-P.H_cyl - P0z) * P.inv_wz, t2 = (P.H_cyl - P0z) * P.inv_wz;
     lo = fmax(lo, fmin(t1, t2));
     hi = fmin(hi, fmax(t1, t2));
   } else if (fabs(P0z) > P.H_cyl) {
@@ -252,14 +253,15 @@ __device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, b
   if (P.box || P.sph) {
     // (the box or sphere chord is complete)
   } else if (wy != 0.0) {
-    double a = wy * wy, b = 2.0 * P0y * wy;
-    double disc = b * b - 4.0 * a * c;
+    // roots of a s^2 + b s + c with a = wy^2, b = 2 P0y wy: (-b -+ sqrt(b^2 - 4 a c)) / (2 a)
+    double b = 2.0 * P0y * wy;
+    double disc = b * b - 4.0 * (wy * wy) * c;
     if (disc < 0.0) {
       ok = false;
     } else {
       double sq = sqrt(disc);
-      lo = fmax(lo, (-b - sq) / (2.0 * a));
-      hi = fmin(hi, (-b + sq) / (2.0 * a));
+      lo = fmax(lo, (-b - sq) * P.inv_2a);
+      hi = fmin(hi, (-b + sq) * P.inv_2a);
     }
   } else if (c > 0.0) {
     ok = false;
@@ -269,7 +271,7 @@ __device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, b
     lo = 0.0;
     hi = 0.0;
   }
-  double ds = (hi - lo) / P.n_samples;
+  double ds = (hi - lo) * P.inv_ns;
   double s0 = lo + 0.5 * ds;
   double yb = P0y + s0 * wy, zb = P0z + s0 * wz, dy = ds * wy, dz = ds * wz;
   R.x = (float)xs;
@@ -310,12 +312,15 @@ __device__ __forceinline__ bool in_gas(const MarchParams &P, float z, float r2) 
   return (r2 >= P.r_in2) && (z * z <= P.zr_max2 * r2);
 }
 
+// LOG: the radial grid is known to be log-spaced (specialised kernels).
+template <bool LOG = false>
 __device__ __forceinline__ Cell locate(const MarchParams &P, float z, float r2) {
   Cell c;
   float ir = rsq(r2);
   float zr = fabsf(z) * ir;
   c.gas = in_gas(P, z, r2);
-  float u = P.r_log ? lg2(r2 * P.inv_rin2) * P.lr_scale : fmaf(r2 * ir, P.lr_scale, P.lr_off);
+  float u = (LOG || P.r_log) ? lg2(r2 * P.inv_rin2) * P.lr_scale
+                             : fmaf(r2 * ir, P.lr_scale, P.lr_off);
   u = fminf(fmaxf(u, 0.0f), (float)(P.nr - 1));
   int i0 = min((int)u, P.nr - 2);
   float w = fminf(fmaxf(zr * P.w_scale, 0.0f), (float)(P.nz - 1));
@@ -346,11 +351,11 @@ struct NodeVals {
 };
 
 // ROT: the problem has a rotation field (then the corner quads hold four fields per cell,
-// otherwise three).
-template <bool ROT>
+// otherwise three). QUADS: the corner quads are known to be packed (specialised kernels).
+template <bool ROT, bool QUADS = false>
 __device__ __forceinline__ NodeVals fields_at(const MarchParams &P, const Cell &c) {
   NodeVals v;
-  if (P.cell) {
+  if (QUADS || P.cell) {
     const float4 *q = P.cell + (ROT ? 4 : 3) * ((long long)c.j0 * (P.nr - 1) + c.i0);
     const float4 qT = __ldg(q), qn = __ldg(q + 1), qv = __ldg(q + 2);
     v.vphi = ROT ? quad_lerp(__ldg(q + 3), c) : 0.0f;
@@ -393,13 +398,16 @@ __device__ __forceinline__ float lte_phi(const float *__restrict__ tab, float t,
 }
 
 // Line physics of a sample from its primitives: thermal + turbulent width, LTE source and
-// tabulated opacity factor; returns {kd, a, b, S} (see sample_physics).
+// tabulated opacity factor; returns {kd, a, b, S} (see sample_physics). ABS: the turbulence is
+// known to be absolute (km/s, not a Mach number; specialised kernels).
+template <bool ABS = false>
 __device__ __forceinline__ float4 line_tail(const MarchParams &P, const float *tab, float T,
                                             float n, float X, float vt, float vlos, float ds) {
   float4 out;
   // line width
   float Tg = fmaxf(T, 1e-3f);
-  float a2 = P.vturb_mach ? Tg * fmaf(P.c_mach, vt * vt, P.c_th) : fmaf(P.c_th, Tg, vt * vt);
+  float a2 = (!ABS && P.vturb_mach) ? Tg * fmaf(P.c_mach, vt * vt, P.c_th)
+                                    : fmaf(P.c_th, Tg, vt * vt);
   float ia = rsq(a2);
   // LTE: source function and tabulated lower-level opacity factor
   float phi = lte_phi(tab, lg2(Tg), nullptr);
@@ -415,7 +423,10 @@ __device__ __forceinline__ float4 line_tail(const MarchParams &P, const float *t
 //   kd  optical depth per unit profile (log2 units): dtau_c = kd 2^{-d_c^2}, 0 without gas
 //   a,b profile argument d_c = v_c b - a (b = sqrt(log2 e)/alpha, a = v_los b)
 //   S   LTE source function in units of 2 h nu0^3 / c^2
-template <bool ROT = false>
+// SPEC: the common configuration is known at compile time (spec_ok: packed corner quads, log
+// radial grid, logistic CO edges, absolute turbulence, no network modulation), so its
+// branches on the parameters are removed.
+template <bool ROT = false, bool SPEC = false>
 __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const float *tab,
                                                  const Ray &R, int k) {
   float kf = (float)k;
@@ -424,10 +435,10 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
   float r2 = fmaf(R.x, R.x, y * y);
   // samples without gas leave before the grid location (two multiplies and compares)
   if (!(in_gas(P, z, r2) && k <= R.khi)) return make_float4(0.0f, 0.0f, 1.0f, 0.0f);
-  Cell c = locate(P, z, r2);
-  const NodeVals f = fields_at<ROT>(P, c);
+  Cell c = locate<SPEC>(P, z, r2);
+  const NodeVals f = fields_at<ROT, SPEC>(P, c);
   float T = f.T, n = f.n, vt = f.vt, hlo = f.hlo, hhi = f.hhi;
-  if (P.mod) {
+  if (!SPEC && P.mod) {
     const float4 o = __ldg(P.mod + (long long)R.pix * P.n_samples + k);
     T *= ex2(o.x * 1.4426950408889634f);
     n *= ex2(o.y * 1.4426950408889634f);
@@ -435,7 +446,7 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
     hhi = fmaf(P.h_scale, o.w, hhi);
   }
   float X;
-  if (P.hard_edge) {
+  if (!SPEC && P.hard_edge) {
     X = (c.zr >= hlo && c.zr <= hhi) ? P.x_co : 0.0f;
   } else {
     float ea = ex2((hlo - c.zr) * P.edge_k);
@@ -445,7 +456,13 @@ __device__ __forceinline__ float4 sample_physics(const MarchParams &P, const flo
   // Keplerian rotation: v_los = sqrt(GM) sin i x (r^2 + z^2)^{-3/4} + v_sys
   float vlos = ROT ? fmaf(f.vphi * (P.sin_if * R.x), c.ir, P.vsys)
                   : fmaf(R.vfac, kepler_q(fmaf(z, z, r2)), P.vsys);
-  return line_tail(P, tab, T, n, X, vt, vlos, R.ds);
+  return line_tail<SPEC>(P, tab, T, n, X, vt, vlos, R.ds);
+}
+
+// The configuration the specialised kernels assume (see sample_physics).
+__host__ __device__ inline bool spec_ok(const MarchParams &P) {
+  return P.cell != nullptr && P.r_log && !P.hard_edge && !P.vturb_mach && P.mod == nullptr &&
+         P.v_uniform && P.dv != 0.0f && !P.no_window && !P.box && !P.sph;
 }
 
 // Sample physics on a 3-D Cartesian grid (rt_render3d): trilinear interpolation of the
@@ -575,12 +592,14 @@ __device__ __forceinline__ float4 sample_physics_sph(const MarchParams &P, const
 }
 
 // Sample physics of the forward march by mode: 0 axisymmetric grid, Keplerian rotation; 1
-// axisymmetric grid with a rotation field; 2 3-D Cartesian grid; 3 3-D spherical grid.
+// axisymmetric grid with a rotation field; 2 3-D Cartesian grid; 3 3-D spherical grid; 4 and 5
+// modes 0 and 1 specialised for the common configuration (spec_ok).
 template <int MODE>
 __device__ __forceinline__ float4 march_physics(const MarchParams &P, const float *tab,
                                                 const Ray &R, int k) {
   if (MODE == 3) return sample_physics_sph(P, tab, R, k);
   if (MODE == 2) return sample_physics_box(P, tab, R, k);
+  if (MODE >= 4) return sample_physics<MODE == 5, true>(P, tab, R, k);
   return sample_physics<MODE == 1>(P, tab, R, k);
 }
 
