@@ -549,8 +549,8 @@ static int launch_mlp_t(const rt_mlp *m, const In &in, float *out, long long n,
 // features x 8 samples, high and low parts, 16 KB each); one thread per (output feature,
 // half of the samples) reads its accumulator row back, adds the bias, applies SiLU and writes
 // the next layer's high and low parts in place. After the fourth layer the FP32 activations
-// go to shared memory (XOR-swizzled, 32 KB) and one thread per (sample, output) forms the
-// output by a 128-term FP32 dot product.
+// go to shared memory (XOR-swizzled, 32 KB); four threads per sample each form the four
+// outputs over a quarter of the 128 inputs in FP32, and one adds the quarters.
 // ---------------------------------------------------------------------------------------
 constexpr int kSN = 64;                     // samples per tile (MMA N)
 constexpr int kSG = 3;                      // tile groups
@@ -563,7 +563,7 @@ struct __align__(1024) SplitSmem {
   h16 W1[kMlpW * kMlpF];                 // high parts, K-major core matrices (16 KB)
   h16 Wh[3][kMlpW * kMlpW];              // (96 KB)
   h16 B[kSG][2][kMlpW * kSN];            // activations per group: high, low parts (16 KB each)
-  float W5[kMlpOut][kMlpW];
+  float4 W5T[kMlpW];                     // output layer, transposed: W5T[k] = W5[0..3][k]
   float bias[4][kMlpW];
   float bias5[kMlpOut];
   float Bf[32][2];
@@ -645,7 +645,9 @@ __global__ void __launch_bounds__(kSGT * kSG, 1)
   for (int l = 0; l < 3; l++)
     for (int i = tid; i < kMlpW * kMlpW; i += blockDim.x)
       S.Wh[l][cm_off(i / kMlpW, i % kMlpW, kMlpW)] = to16<false>(Wp.W[l + 1][i]);
-  for (int i = tid; i < kMlpOut * kMlpW; i += blockDim.x) S.W5[i / kMlpW][i % kMlpW] = Wp.W[4][i];
+  for (int k = tid; k < kMlpW; k += blockDim.x)
+    S.W5T[k] = make_float4(Wp.W[4][k], Wp.W[4][kMlpW + k], Wp.W[4][2 * kMlpW + k],
+                           Wp.W[4][3 * kMlpW + k]);
   for (int i = tid; i < 4 * kMlpW; i += blockDim.x) S.bias[i / kMlpW][i % kMlpW] = Wp.b[i / kMlpW][i % kMlpW];
   if (tid < kMlpOut) S.bias5[tid] = Wp.b[4][tid];
   if (tid < 64) S.Bf[tid >> 1][tid & 1] = Wp.B[tid];
@@ -709,16 +711,21 @@ __global__ void __launch_bounds__(kSGT * kSG, 1)
   const unsigned idn = idesc_16(kSN, false, false, true);
 
   const long long ntiles = (in_count(in, n) + kSN - 1) / kSN;
-  for (long long tile = (long long)blockIdx.x * kSG + tg; tile < ntiles;
-       tile += (long long)gridDim.x * kSG) {
+  const long long tstride = (long long)gridDim.x * kSG;
+  // the inputs of a group's next tile are read (threads gt < 64) while its current tile's
+  // first layer runs on the tensor cores, off the tile's critical path
+  long long nidx = 0;
+  float nrh = 0.0f, nzh = 0.0f;
+  bool nneed = false;
+  const long long tile0 = (long long)blockIdx.x * kSG + tg;
+  if (gt < kSN && tile0 < ntiles) nneed = tile_input(in, tile0 * kSN, gt, &nrh, &nzh, &nidx);
+  for (long long tile = tile0; tile < ntiles; tile += tstride) {
     bool need = false;
     if (gt < kSN) {
-      long long s;
-      float rh = 0.0f, zh = 0.0f;
-      need = tile_input(in, tile * kSN, gt, &rh, &zh, &s);
-      S.rh[tg][gt] = rh;
-      S.zh[tg][gt] = zh;
-      S.idx[tg][gt] = s;
+      need = nneed;
+      S.rh[tg][gt] = nrh;
+      S.zh[tg][gt] = nzh;
+      S.idx[tg][gt] = nidx;
       S.need[tg][gt] = need ? 1 : 0;
     }
     int any;
@@ -728,7 +735,14 @@ __global__ void __launch_bounds__(kSGT * kSG, 1)
         : "=r"(any)
         : "r"((unsigned)need), "r"(1 + tg), "r"(kSGT)
         : "memory");
-    if (!any) continue;
+    if (!any) {  // nothing to evaluate in this tile: read the next tile's inputs and go on
+      if (gt < kSN) {
+        nneed = false;
+        if (tile + tstride < ntiles)
+          nneed = tile_input(in, (tile + tstride) * kSN, gt, &nrh, &nzh, &nidx);
+      }
+      continue;
+    }
     {
       // Fourier features: direction j = gt % 32 for samples 8 (gt / 32) .. + 7 (range-reduced
       // phases, hardware sin / cos), sin into feature j and cos into feature 32 + j
@@ -765,6 +779,11 @@ __global__ void __launch_bounds__(kSGT * kSG, 1)
         }
         mma_commit(mbar);
       }
+      if (l == 0 && gt < kSN) {
+        nneed = false;
+        if (tile + tstride < ntiles)
+          nneed = tile_input(in, (tile + tstride) * kSN, gt, &nrh, &nzh, &nidx);
+      }
       ok = mbar_wait(mbar, phase);
       phase ^= 1;
       tc_fence_after();
@@ -800,14 +819,36 @@ __global__ void __launch_bounds__(kSGT * kSG, 1)
     }
     if (S.abort[tg]) break;
     {
-      // output layer in FP32: thread gt -> sample gt / 4, output gt % 4
-      const int s = gt >> 2, o = gt & 3;
-      float acc = S.bias5[o];
+      // output layer in FP32: thread gt -> sample gt % 64, inputs 32 (gt / 64) .. + 31, all
+      // four outputs (W5T rows are broadcast; h4 reads are conflict-free by the swizzle);
+      // then one thread per sample adds the four partial sums
+      const int s = gt & (kSN - 1), kq = gt >> 6;
+      float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll 8
-      for (int k = 0; k < kMlpW; k++) acc = fmaf(S.W5[o][k], h4[k * kSN + (s ^ (k & 31))], acc);
-      if (S.need[tg][s]) out[S.idx[tg][s] * kMlpOut + o] = acc;
+      for (int k = 32 * kq; k < 32 * kq + 32; k++) {
+        const float h = h4[k * kSN + (s ^ (k & 31))];
+        const float4 w = S.W5T[k];
+        acc.x = fmaf(w.x, h, acc.x);
+        acc.y = fmaf(w.y, h, acc.y);
+        acc.z = fmaf(w.z, h, acc.z);
+        acc.w = fmaf(w.w, h, acc.w);
+      }
+      // the partial sums replace h4 once every thread has read it
+      float4 *red = reinterpret_cast<float4 *>(h4);  // [quarter][sample]
+      gsync();
+      red[kq * kSN + s] = acc;
+      gsync();
+      if (gt < kSN && S.need[tg][gt]) {
+        const float4 a = red[gt], b = red[kSN + gt], c = red[2 * kSN + gt],
+                     d = red[3 * kSN + gt];
+        const float4 o = make_float4(S.bias5[0] + ((a.x + b.x) + (c.x + d.x)),
+                                     S.bias5[1] + ((a.y + b.y) + (c.y + d.y)),
+                                     S.bias5[2] + ((a.z + b.z) + (c.z + d.z)),
+                                     S.bias5[3] + ((a.w + b.w) + (c.w + d.w)));
+        reinterpret_cast<float4 *>(out)[S.idx[tg][gt]] = o;
+      }
     }
-    gsync();  // h4 and the tile inputs are read before the next tile overwrites them
+    gsync();  // h4, the partial sums and the tile inputs are read before the next tile
   }
   // after a wait that ran out, let the MMA in flight finish (bounded) before the tensor
   // memory is released
