@@ -56,10 +56,10 @@ except (OSError, ValueError):
 MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 4)
 # DRAM bytes of one forward launch on the observation-scale workload (ncu, dram__bytes_read +
 # dram__bytes_write of march_fwd_kernel<8,8,0>; the cube stays in L2 at the end of the launch)
-FWD_DRAM_BYTES = 3_343_616 + 31_232
+FWD_DRAM_BYTES = 3_331_840 + 30_464
 # DRAM bytes (read + write) of one fused-adjoint launch on the same workload (ncu capture of
 # march_adj_kernel<8, 8, 1>)
-ADJ_DRAM_BYTES = 52_613_120 + 500_046_080
+ADJ_DRAM_BYTES = 44_500_736 + 444_428_544
 N_SM = 148
 SM_MAX_MHZ = 2032.0
 
