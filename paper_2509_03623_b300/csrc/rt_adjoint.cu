@@ -340,7 +340,7 @@ __device__ __forceinline__ unsigned adj_window(const MarchParams &P, const float
 }
 
 template <int LPR, int CPL, int VAR>
-__global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
+__global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
     march_adj_kernel(const __grid_constant__ MarchParams P, const float *__restrict__ dLdc,
                      const float *__restrict__ target, float *__restrict__ cube_out,
                      const rt_grads G, float *__restrict__ scratch, int nseg,
@@ -440,14 +440,16 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
         if (!act) continue;
         ph[lane] = mine;
         __syncwarp();
-#pragma unroll 1
-        for (int t = 0; t < LPR; t++) {
-          const float4 p = ph[rr * LPR + t];
-          const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
-          const float2 kd2 = make_float2(p.x, p.x), S2 = make_float2(p.w, p.w);
+        // channel pairs outside, the batch's samples inside: one warp-uniform window test per
+        // pair and batch
 #pragma unroll
-          for (int m = 0; m < CPL / 2; m++) {
-            if (!(act2 & (1u << m))) continue;  // warp-uniform
+        for (int m = 0; m < CPL / 2; m++) {
+          if (!(act2 & (1u << m))) continue;  // warp-uniform
+#pragma unroll
+          for (int t = 0; t < LPR; t++) {
+            const float4 p = ph[rr * LPR + t];
+            const float dc = fmaf(vq, p.z, -p.y), db = __fmul_rn(dvs, p.z);
+            const float2 kd2 = make_float2(p.x, p.x), S2 = make_float2(p.w, p.w);
             const float2 d =
                 UNIF ? __ffma2_rn(make_float2((float)(2 * m), (float)(2 * m + 1)),
                                   make_float2(db, db), make_float2(dc, dc))
@@ -526,14 +528,18 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
           if (!act) continue;
           ph[lane] = mine;
           __syncwarp();
-#pragma unroll 1
-          for (int t = 0; t < LPR; t++) {
-            const float4 p = ph[rr * LPR + t];
-            const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
 #pragma unroll
-            for (int j = 0; j < CPL; j++) {
-              if (!(act & (1u << j))) continue;  // warp-uniform
-              const float d = UNIF ? fmaf((float)j, db, dc) : fmaf(vc[j], p.z, -p.y);
+          for (int j = 0; j < CPL; j++) {
+            if (!(act & (1u << j))) continue;  // warp-uniform, once per block and batch
+#pragma unroll
+            for (int t = 0; t < LPR; t++) {
+              const float4 p = ph[rr * LPR + t];
+              // the same roundings as the reverse pass's packed d (db rounded on its own, then
+              // one fma): the reverse subtracts its own increments from these sums, and any
+              // difference in the last bit (a contracted dvs * p.z, say) leaves optical depth
+              // behind that the CO-edge Jacobian amplifies tenfold
+              const float d = UNIF ? fmaf((float)j, __fmul_rn(dvs, p.z), fmaf(vq, p.z, -p.y))
+                                   : fmaf(vc[j], p.z, -p.y);
               tbs[j] = fmaf(p.x, ex2(d * -d), tbs[j]);
             }
           }
@@ -568,47 +574,57 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32)
           }
           __syncwarp();
           const float2 mone = make_float2(-1.0f, -1.0f);
-#pragma unroll 1
-          for (int t = LPR - 1; t >= 0; t--) {
-            const float4 p = ph[rr * LPR + t];
-            const bool gas = p.z > 0.0f;
-            const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
-            Snext = gas ? p.w : Snext;
-            const float dc = fmaf(vq, p.z, -p.y), db = dvs * p.z;
+          // reverse step of one channel pair m at sample t of the batch: advances the suffix
+          // sums A, the optical depth cur and the transmittance Tn of the pair, and returns its
+          // contributions to the per-sample channel sums (ax, ay, az, aw)
+          auto rev_step = [&](int m, const float4 &p, float cs) {
+            const float dc = fmaf(vq, p.z, -p.y), db = __fmul_rn(dvs, p.z);
             const float2 cs2 = make_float2(cs, cs), kd2 = make_float2(p.x, p.x);
-            float2 ax = make_float2(0.0f, 0.0f), ay = ax, aw = ax, az = ax;
+            const float2 d =
+                UNIF ? __ffma2_rn(make_float2((float)(2 * m), (float)(2 * m + 1)),
+                                  make_float2(db, db), make_float2(dc, dc))
+                     : __ffma2_rn(make_float2(vc[2 * m], vc[2 * m + 1]),
+                                  make_float2(p.z, p.z), make_float2(-p.y, -p.y));
+            const float2 d2 = __fmul2_rn(d, d);
+            const float2 gg = make_float2(ex2(-d2.x), ex2(-d2.y));
+            A[m] = __ffma2_rn(cs2, Tn[m], A[m]);
+            const float2 ug = __fmul2_rn(__fmul2_rn(gI[m], A[m]), gg);
+            const float2 dt = __fmul2_rn(kd2, gg);
+            cur[m] = __ffma2_rn(dt, mone, cur[m]);
+            const float2 T0 = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
+            // T_k - T_{k+1} = T_{k+1} (2^dt - 1): series below dt = 0.07 (the difference of
+            // two rounded transmittances would lose the small optical depths)
+            const float2 poly = __ffma2_rn(
+                __ffma2_rn(dt, make_float2(0.0555041087f, 0.0555041087f),
+                           make_float2(0.240226507f, 0.240226507f)),
+                dt, make_float2(0.693147181f, 0.693147181f));
+            const float2 ser = __fmul2_rn(__fmul2_rn(Tn[m], dt), poly);
+            const float2 dif = __ffma2_rn(Tn[m], mone, T0);
+            const float2 dTk = make_float2(dt.x < 0.07f ? ser.x : dif.x,
+                                           dt.y < 0.07f ? ser.y : dif.y);
+            Tn[m] = T0;
+            const float2 wy = __fmul2_rn(ug, d2), wz = __fmul2_rn(ug, d), ww = __fmul2_rn(gI[m], dTk);
+            return make_float4(ug.x + ug.y, wy.x + wy.y, ROT ? wz.x + wz.y : 0.0f, ww.x + ww.y);
+          };
+          {
+#pragma unroll 1
+            for (int t = LPR - 1; t >= 0; t--) {
+              const float4 p = ph[rr * LPR + t];
+              const bool gas = p.z > 0.0f;
+              const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
+              Snext = gas ? p.w : Snext;
+              float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
-            for (int m = 0; m < CPL / 2; m++) {
-              if (!(act2 & (1u << m))) continue;  // warp-uniform
-              const float2 d =
-                  UNIF ? __ffma2_rn(make_float2((float)(2 * m), (float)(2 * m + 1)),
-                                    make_float2(db, db), make_float2(dc, dc))
-                       : __ffma2_rn(make_float2(vc[2 * m], vc[2 * m + 1]),
-                                    make_float2(p.z, p.z), make_float2(-p.y, -p.y));
-              const float2 d2 = __fmul2_rn(d, d);
-              const float2 gg = make_float2(ex2(-d2.x), ex2(-d2.y));
-              A[m] = __ffma2_rn(cs2, Tn[m], A[m]);
-              const float2 ug = __fmul2_rn(__fmul2_rn(gI[m], A[m]), gg);
-              ax = __fadd2_rn(ax, ug);
-              ay = __ffma2_rn(ug, d2, ay);
-              if (ROT) az = __ffma2_rn(ug, d, az);
-              const float2 dt = __fmul2_rn(kd2, gg);
-              cur[m] = __ffma2_rn(dt, mone, cur[m]);
-              const float2 T0 = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
-              // T_k - T_{k+1} = T_{k+1} (2^dt - 1): series below dt = 0.07 (the difference of
-              // two rounded transmittances would lose the small optical depths)
-              const float2 poly = __ffma2_rn(
-                  __ffma2_rn(dt, make_float2(0.0555041087f, 0.0555041087f),
-                             make_float2(0.240226507f, 0.240226507f)),
-                  dt, make_float2(0.693147181f, 0.693147181f));
-              const float2 ser = __fmul2_rn(__fmul2_rn(Tn[m], dt), poly);
-              const float2 dif = __ffma2_rn(Tn[m], mone, T0);
-              const float2 dTk = make_float2(dt.x < 0.07f ? ser.x : dif.x,
-                                             dt.y < 0.07f ? ser.y : dif.y);
-              aw = __ffma2_rn(gI[m], dTk, aw);
-              Tn[m] = T0;
+              for (int m = 0; m < CPL / 2; m++) {
+                if (!(act2 & (1u << m))) continue;  // warp-uniform
+                const float4 c = rev_step(m, p, cs);
+                a.x += c.x;
+                a.y += c.y;
+                a.z += c.z;
+                a.w += c.w;
+              }
+              part[t][lane ^ (t & 7)] = a;
             }
-            part[t][lane ^ (t & 7)] = make_float4(ax.x + ax.y, ay.x + ay.y, az.x + az.y, aw.x + aw.y);
           }
           // blocks outside every window: T is constant over the batch, so the suffix sums
           // advance by T (S before the batch - S of its first sample with gas)
