@@ -184,3 +184,21 @@ def test_render_launch_count(rt):
     assert rt.rt_render_launch_count(synth.config_small(0)) == 1
     assert rt.rt_render_launch_count(synth.config_observation(0)) == 2
     assert rt.rt_render_launch_count(synth.config_small(0).replace(nx=0)) == 0
+
+
+def test_specialised_march_sampled_and_repeatable(rt, orc):
+    """The common configuration (packed corner quads from 4 M samples, log grid, logistic
+    edges, absolute turbulence, equally spaced channels) runs the specialised kernel: its
+    cube meets the parity criterion on a sample of pixels and repeats bit for bit."""
+    p = synth.config_observation(2).replace(nx=128, ny=128, n_samples=256)
+    assert p.nx * p.ny * p.n_samples >= 1 << 22
+    assert rt.rt_render_launch_count(p) == 2      # corner-quad packing + march
+    a = gpu_cube(rt, p)
+    b = gpu_cube(rt, p)
+    assert np.array_equal(a, b)
+    rng = np.random.default_rng(9)
+    flux = a.sum(axis=0).ravel()
+    pix = np.unique(np.concatenate([np.argsort(flux)[::-1][:16],
+                                    rng.choice(p.nx * p.ny, 16, replace=False)]))
+    ref = orc.render_pixels(p, pix)
+    assert_cube_close(a.reshape(p.nch, -1)[:, pix].T, ref, label="specialised")
