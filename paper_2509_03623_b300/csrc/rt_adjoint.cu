@@ -27,6 +27,7 @@
 // gradients with FP64 atomics into replicated accumulators.
 #include <mutex>
 #include <new>
+#include <type_traits>
 
 #include "rt_internal.cuh"
 
@@ -371,6 +372,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
   float *ck = scratch + gw * adj_warp_floats<LPR, CPL>(nseg);  // this warp's checkpoints
   float *bs = ck + (long long)nseg * CPL * 32;                  // and batch starts
   float4 *rec = reinterpret_cast<float4 *>(bs + (NB + 1) * CPL * 32) + lane;  // sample records
+  // float4 per lane and batch of the records actually used: the fifth (network and rotation
+  // entries) only with a network or a rotation field (a smaller working set in L2)
+  const int rstride = (ROT || (!SPEC && P.mod)) ? kRec : kRec - 1;
   float4 *ph = s_ph[wib];
   float4(*part)[32] = s_part[wib];
   float vc[CPL];
@@ -519,7 +523,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
 #pragma unroll
           for (int j = 0; j < CPL; j++) bs[(b * CPL + j) * 32 + lane] = tbs[j];
           // physics and local derivatives, kept for the reverse pass over this batch
-          float4 *rb = rec + (long long)b * kRec * 32;
+          float4 *rb = rec + (long long)b * rstride * 32;
           const float4 mine = physics_jac<ROT, SPEC>(P, s_tab, ray, ray.klo + k0 + b * LPR + q, rb);
           rb[0] = mine;
           const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
@@ -552,7 +556,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
         // backward over the batches of the segment
         for (int b = nb - 1; b >= 0; b--) {
           const int kb = k0 + b * LPR;
-          const float4 *rb = rec + (long long)b * kRec * 32;
+          const float4 *rb = rec + (long long)b * rstride * 32;
           const float4 mine = rb[0];
           if (!__any_sync(0xffffffffu, mine.z > 0.0f)) continue;  // no gas in the batch
           const unsigned act = s_act[wib][b];
@@ -606,7 +610,29 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
             const float2 wy = __fmul2_rn(ug, d2), wz = __fmul2_rn(ug, d), ww = __fmul2_rn(gI[m], dTk);
             return make_float4(ug.x + ug.y, wy.x + wy.y, ROT ? wz.x + wz.y : 0.0f, ww.x + ww.y);
           };
-          {
+          // one channel pair in the window (the common case): its loop without per-sample
+          // window tests, the pair index a compile-time constant
+          auto one_pair = [&](auto M) {
+            constexpr int m = decltype(M)::value;
+#pragma unroll 1
+            for (int t = LPR - 1; t >= 0; t--) {
+              const float4 p = ph[rr * LPR + t];
+              const bool gas = p.z > 0.0f;
+              const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
+              Snext = gas ? p.w : Snext;
+              part[t][lane ^ (t & 7)] = rev_step(m, p, cs);
+            }
+          };
+          const int npair = __popc(act2);
+          if (npair == 1 && act2 == 1u) {
+            one_pair(std::integral_constant<int, 0>());
+          } else if (npair == 1 && act2 == 2u) {
+            one_pair(std::integral_constant<int, 1>());
+          } else if (CPL / 2 > 2 && npair == 1 && act2 == 4u) {
+            one_pair(std::integral_constant<int, (CPL / 2 > 2 ? 2 : 0)>());
+          } else if (CPL / 2 > 3 && npair == 1 && act2 == 8u) {
+            one_pair(std::integral_constant<int, (CPL / 2 > 3 ? 3 : 0)>());
+          } else {
 #pragma unroll 1
             for (int t = LPR - 1; t >= 0; t--) {
               const float4 p = ph[rr * LPR + t];
