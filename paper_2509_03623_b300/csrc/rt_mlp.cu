@@ -596,8 +596,9 @@ __device__ __forceinline__ void split_store8(h16 *Bh, h16 *Bl, int k, int s0, co
 #pragma unroll
   for (int j = 0; j < 4; j++) {
     hi[j] = pack16<false>(v[2 * j], v[2 * j + 1]);
-    const float2 h = bf2f(hi[j]);
-    lo[j] = pack16<false>(v[2 * j] - h.x, v[2 * j + 1] - h.y);
+    const float2 r = __ffma2_rn(bf2f(hi[j]), make_float2(-1.0f, -1.0f),
+                                make_float2(v[2 * j], v[2 * j + 1]));  // exact residual
+    lo[j] = pack16<false>(r.x, r.y);
   }
   const int o = bmn_off(k, s0);
   *reinterpret_cast<uint4 *>(Bh + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -794,14 +795,19 @@ __global__ void __launch_bounds__(kSGT * kSG, 1)
       if (ok) {
         float v[32];
         tmem_ld32(tDl, v);
-        const float b = S.bias[l][f];
+        const float hb = 0.5f * S.bias[l][f];
 #pragma unroll
-        for (int i = 0; i < 32; i++) {
-          // SiLU(z) = h (1 + tanh h), h = z / 2
-          const float h = 0.5f * (v[i] + b);
-          float t;
-          asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
-          v[i] = fmaf(h, t, h);
+        for (int i = 0; i < 32; i += 2) {
+          // SiLU(z) = h (1 + tanh h), h = z / 2 = v/2 + b/2 (halving is exact), two columns
+          // per packed instruction
+          const float2 h = __ffma2_rn(make_float2(v[i], v[i + 1]), make_float2(0.5f, 0.5f),
+                                      make_float2(hb, hb));
+          float t0, t1;
+          asm("tanh.approx.f32 %0, %1;" : "=f"(t0) : "f"(h.x));
+          asm("tanh.approx.f32 %0, %1;" : "=f"(t1) : "f"(h.y));
+          const float2 a = __ffma2_rn(h, make_float2(t0, t1), h);
+          v[i] = a.x;
+          v[i + 1] = a.y;
         }
         if (l < 3) {
 #pragma unroll
