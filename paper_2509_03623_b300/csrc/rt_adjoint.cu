@@ -489,11 +489,13 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
           const float Ij = (j & 1) ? I[j >> 1].y : I[j >> 1].x;
           const float Trj = (j & 1) ? Tr[j >> 1].y : Tr[j >> 1].x;
           const float out = fmaf(Ij, P.out_scale, P.I0 * Trj);
-          if (cube_out) cube_out[o] = out;
+          if (cube_out) __stcs(cube_out + o, out);
+          // read once: streamed past L2 (evict first), which keeps the per-warp scratch and
+          // the gradient copies resident
           if (dLdc) {
-            go = dLdc[o];
+            go = __ldcs(dLdc + o);
           } else {
-            const float r = out - target[o];
+            const float r = out - __ldcs(target + o);
             go = 2.0f * r;
             loss += (double)r * (double)r;
           }
