@@ -548,7 +548,7 @@ int rt_mlp_backward(const rt_mlp *mlp, const float *xy, const float *dout, long 
  * to the grid fields before the network's modulation. In addition mlp_grads receives dL/dW
  * and dL/db of the network. Steps: the network forward at every sample (as rt_render_mlp),
  * the fused march adjoint with the modulation, which also writes dL/d(outputs) per sample,
- * then rt_mlp_backward over those samples. Device buffers of 32 n_pix n_samples bytes plus
+ * then rt_mlp_backward over those samples. Device buffers of 40 n_pix n_samples bytes plus
  * the scratch of both steps are allocated and freed on `stream`. Returns RT_OK, RT_EINVAL,
  * RT_ENOMEM or RT_ECUDA.
  */

@@ -826,12 +826,16 @@ extern "C" int rt_render_mlp_adjoint(const rt_grid *grid, const rt_fields *field
   const long long ns = npix * (rc == RT_OK ? P->n_samples : 0);
   if (rc == RT_OK) {
     cudaStream_t st = (cudaStream_t)stream;
-    // one buffer: network outputs, dL/d(outputs), ray setups, backward scratch, gradient scale
-    const size_t mod_bytes = (size_t)ns * sizeof(float4);
+    // one buffer: network outputs (after the march adjoint: the gathered output gradients of
+    // the backward), dL/d(outputs), ray setups, sample list, gathered network inputs, backward
+    // scratch, gradient scale
+    const size_t ng = mlp_bwd_gather_entries(ns);
+    const size_t mod_bytes = ((ng > (size_t)ns ? ng : (size_t)ns) * sizeof(float4) + 255) & ~(size_t)255;
     const size_t ray_bytes = (ray_buffer_bytes(npix) + 255) & ~(size_t)255;
     const size_t list_bytes = (sample_list_bytes(npix, P->n_samples) + 255) & ~(size_t)255;
+    const size_t xy_bytes = (ng * sizeof(float2) + 255) & ~(size_t)255;
     const size_t spill_bytes = mlp_bwd_scratch_bytes(ns);
-    const size_t bytes = 2 * mod_bytes + ray_bytes + list_bytes + spill_bytes + 256;
+    const size_t bytes = 2 * mod_bytes + ray_bytes + list_bytes + xy_bytes + spill_bytes + 256;
     char *buf = nullptr;
     cudaError_t e = stream_alloc((void **)&buf, bytes, st);
     if (e != cudaSuccess) {
@@ -842,7 +846,8 @@ extern "C" int rt_render_mlp_adjoint(const rt_grid *grid, const rt_fields *field
       float4 *dmod = reinterpret_cast<float4 *>(buf + mod_bytes);
       char *rays = buf + 2 * mod_bytes;
       char *list = list_bytes ? rays + ray_bytes : nullptr;
-      char *spill = rays + ray_bytes + list_bytes;
+      float2 *xy = reinterpret_cast<float2 *>(rays + ray_bytes + list_bytes);
+      char *spill = rays + ray_bytes + list_bytes + xy_bytes;
       unsigned *dmax = reinterpret_cast<unsigned *>(spill + spill_bytes);
       e = cudaMemsetAsync(dmod, 0, mod_bytes, st);
       if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, sizeof(unsigned), st);
@@ -854,8 +859,8 @@ extern "C" int rt_render_mlp_adjoint(const rt_grid *grid, const rt_fields *field
         rc = launch_adjoint(*P, dL_dcube, target, cube_out, *grads, st, dmod, dmax);
       }
       if (rc == RT_OK)
-        rc = launch_mlp_bwd_rays(mlp, *P, rays, ns > 0 ? list : nullptr, dmod, dmax, spill,
-                                 mlp_grads, st);
+        rc = launch_mlp_bwd_rays(mlp, *P, rays, ns > 0 ? list : nullptr, dmod, dmax, spill, xy,
+                                 mod, mlp_grads, st);
       cudaFreeAsync(buf, st);
     }
   }

@@ -646,9 +646,12 @@ size_t sample_list_bytes(long long npix, int n_samples);
 int mlp_validate(const rt_mlp *m);
 int mlp_grads_validate(const rt_mlp_grads *g);
 size_t mlp_bwd_scratch_bytes(long long n);
+// entries of the gathered backward inputs (xy and g buffers) for n samples
+size_t mlp_bwd_gather_entries(long long n);
 int launch_mlp_bwd_rays(const rt_mlp *m, const MarchParams &P, const void *ray_buf,
                         const void *list_buf, const float4 *dmod, const unsigned *dmax,
-                        void *spill, const rt_mlp_grads *g, cudaStream_t stream);
+                        void *spill, float2 *xy_buf, float4 *g_buf, const rt_mlp_grads *g,
+                        cudaStream_t stream);
 int launch_coords(const MarchParams &P, float2 *xy, cudaStream_t stream);
 int launch_surface_grad(const rt_grid &g, const double *dh, const float *h, double c,
                         double *out, cudaStream_t stream);

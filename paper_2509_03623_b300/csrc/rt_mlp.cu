@@ -336,6 +336,26 @@ __device__ __forceinline__ bool tile_input(const ListInput &in, long long s0, in
   return gas;
 }
 
+// The listed samples with their inputs and output gradients already gathered in list order
+// (gather_list_kernel): xy[i] and g[i], padded with zeros to whole 64-sample tiles, so a row
+// needs one load and no bound check.
+struct PackedInput {
+  const float2 *xy;
+  const unsigned *count;
+};
+
+__device__ __forceinline__ long long in_count(const PackedInput &in, long long) { return *in.count; }
+
+__device__ __forceinline__ bool tile_input(const PackedInput &in, long long s0, int tid, float *rh,
+                                           float *zh, long long *idx) {
+  const long long s = s0 + tid;
+  *idx = s;
+  const float2 v = in.xy[s];
+  *rh = v.x;
+  *zh = v.y;
+  return true;
+}
+
 // Ray setups of every pixel (one thread per ray).
 __global__ void rays_kernel(const __grid_constant__ MarchParams P, Ray *__restrict__ rays) {
   const long long npix = (long long)P.nx * P.ny;
@@ -1101,93 +1121,105 @@ int launch_coords(const MarchParams &P, float2 *xy, cudaStream_t stream) {
 // Backward pass of the network: dL/dW and dL/db of every layer from per-sample dL/d(outputs)
 // (reverse mode of the network written out by hand, on the tensor cores).
 //
-// One persistent CTA per SM, 16 warps (four per TMEM lane quadrant, each reading 16 of every
-// 64 accumulator columns: the epilogues are latency-bound, so more threads share them). Tensor memory (512
-// columns) holds the weight-gradient accumulators for the whole run of the CTA -- dW2..dW4
-// (128 columns each) and dW5^T (16) -- and an 80-column working accumulator; dW1 (128 x 64)
-// is staged through the working columns once per tile and summed in registers. Per tile of
-// 128 samples:
-//   forward: features -> 4 SiLU layers, each as two 64-column MMA chunks (M = samples); the
-//     16-bit pre-activations go to a per-CTA scratch in global memory (L2-resident);
-//   backward: delta_5 = dL/d(outputs) (scaled by a power of two so that the largest is below
-//     one: FP16 has no room for raw gradients), then per layer l = 5..1
-//       dW_l += delta_l^T a_{l-1}            (M = out features, K = samples, MN-major operands)
-//       db_l += delta_l^T 1                  (an MMA against a block of ones)
-//       delta_{l-1} = (delta_l W_l) SiLU'(z_{l-1})   (M = samples, K = out features; W_l read
-//                                                      MN-major from the same shared copy)
-//     with a_{l-1} recomputed from the stored pre-activations where it was overwritten.
-// A single thread issues the MMAs; the working accumulator is read with tcgen05.ld and freed
-// (barrier) before the epilogue arithmetic, so the next chunk's MMA overlaps it. At the end
-// each CTA adds its accumulators, unscaled, to the FP64 outputs with atomics. Waits on the
-// mbarrier are bounded: on expiry the CTA records an error, stops and releases its tensor
-// memory.
+// The products are taken transposed, as in the split forward: features are the MMA's M (the
+// TMEM lanes), samples its N. One persistent CTA per SM runs two tile groups of 64 samples
+// (256 threads each: two per TMEM lane row, each owning 32 of the group's 64 accumulator
+// columns), so that one group's epilogue arithmetic runs while the tensor core works on the
+// other group's products. Tensor memory holds the weight-gradient accumulators dW2..dW4 (128
+// columns each; zeroed at the start and shared by both groups) and a 64-column working
+// accumulator per group. Shared memory holds the 16-bit weights (K-major core matrices, 112
+// KB: the A operand of the forward products and, read MN-major, of the transposed ones) and per
+// group three 16 KB operand buffers X, Y, D of core matrices of 8 features x 8 samples, which
+// serve as MN-major B operands (features along K) and as K-major operands (samples along K)
+// alike. With W_l mapping layer l-1 to layer l, a_0 = gamma the Fourier features, z_l the
+// pre-activations and a_l = SiLU(z_l), per tile:
+//   forward   z_l = W_l a_{l-1} + b_l for l = 1..4 (gamma in D, a_1 -> X, a_2 -> Y, a_3 -> X);
+//             z_1..z_3 (16-bit) go to a per-CTA scratch in global memory (L2-resident);
+//   output    on the CUDA cores in FP32, element by element in the layer-4 epilogue:
+//             dW5 += delta_5 a_4^T and delta_4 = (W5^T delta_5) SiLU'(z_4) -> D, with
+//             delta_5 = dL/d(outputs) scaled by a power of two that brings the largest below
+//             one (FP16 has no room for raw gradients);
+//   backward  l = 4, 3, 2: dW_l += delta_l a_{l-1}^T (M = out features, N = in features,
+//             K = samples) and delta_{l-1} = (W_l^T delta_l) SiLU'(z_{l-1}) under one commit;
+//             a_1 returns to X by a TMA bulk copy of the buffer's image, stored to the scratch
+//             after layer 1 (a_3 overwrote it), and gamma is recomputed into Y;
+//             dW1 = delta_1 gamma^T goes through the working columns and is summed in
+//             registers.
+// The inputs of a group's next tile are read during its first forward product. For a render,
+// gather_list_kernel has packed the listed samples' inputs and output gradients in list
+// order, so a tile's rows are two plain loads.
+// The bias gradients are per-thread sums (a thread owns one feature row of the tile). Each
+// group's first thread issues that group's MMAs; both groups accumulate into the same dW
+// columns, so the order of the FP32 sums (not their terms) depends on the timing of the two.
+// At the end each CTA adds its sums, unscaled, to the FP64 outputs with atomics. Waits on the
+// mbarriers are bounded: on expiry the group records an error and stops, and the CTA releases
+// its tensor memory after the MMAs in flight have finished.
 // ---------------------------------------------------------------------------------------
-constexpr int kBwdThreads = 512;
-constexpr unsigned kColW2 = 0, kColW3 = 128, kColW4 = 256, kColW5 = 384, kColWork = 400;
-constexpr unsigned kColDb = kColWork + 64;  // bias sums (16 columns) inside the working range
-constexpr int kChunk = 64;                  // columns per layer-output MMA chunk
+constexpr int kBN = kSN;                  // samples per tile (MMA N): the layout of bmn_off
+constexpr int kBG = 2;                    // tile groups per CTA
+constexpr int kBGT = 256;                 // threads per group
+constexpr int kBwdThreads = kBG * kBGT;
+constexpr unsigned kColDW = 0;            // dW2, dW3, dW4: 128 columns each
+constexpr unsigned kColBwdWork = 384;     // working accumulators: 64 columns per group
 
 struct __align__(1024) BwdSmem {
-  h16 P[kMlpTile * kMlpW];          // activations / deltas, rows = samples (32 KB)
-  h16 Q[kMlpTile * kMlpW];          // (32 KB)
-  h16 F[kMlpTile * kMlpF];          // Fourier features (16 KB)
-  h16 D5[kMlpTile * kMlpOutPad];    // output-layer deltas, 4 of 16 columns used (4 KB)
-  h16 ONES[kMlpOutPad * kMlpTile];  // all ones [16][samples]: bias sums as an MMA (4 KB)
-  h16 W5[kMlpOutPad * kMlpW];       // (4 KB)
-  h16 W1[kMlpW * kMlpF];            // (16 KB)
-  h16 Wh[3][kMlpW * kMlpW];         // W2..W4 (96 KB)
+  h16 W1[kMlpW * kMlpF];           // K-major core matrices (16 KB)
+  h16 Wh[3][kMlpW * kMlpW];        // W2..W4 (96 KB)
+  h16 buf[kBG][3][kMlpW * kBN];    // per group X, Y, D (16 KB each)
+  float d5[kBG][4][kBN];           // scaled dL/d(outputs) of the group's samples
   float bias[4][kMlpW];
+  float4 W5T[kMlpW];               // output layer, transposed: W5T[k] = W5[0..3][k]
+  float rh[kBG][kBN], zh[kBG][kBN];
   float Bf[32][2];
-  unsigned long long mbar;
+  unsigned long long mbar[kBG];
+  unsigned long long mbar_a1[kBG];  // bulk reload of a_1 into X
   unsigned tmem_base;
-  int abort;
+  int abort[kBG];
 };
-
-// One past the highest byte an MN-major operand touches: base offset, largest per-instruction
-// offset, extents in core matrices along MN and K, and the strides along MN and K.
-constexpr size_t mn_reach(size_t off, size_t step, size_t nmn, size_t nk, size_t smn,
-                          size_t sk) {
-  return off + step + (nmn - 1) * smn + (nk - 1) * sk + 128;
-}
-constexpr size_t kActBytes = sizeof(h16) * kMlpTile * kMlpW;
-// every MN-major read stays inside the array it addresses
-static_assert(mn_reach(0, 1024 + 7 * 4096, 8, 2, 128, 2048) <= kActBytes, "W_l (MN-major) reach");
-static_assert(mn_reach(0, 1024, 8, 2, 128, 2048) <= sizeof(h16) * kMlpOutPad * kMlpW,
-              "W5 (MN-major) reach");
-static_assert(mn_reach(0, 7 * 4096, 16, 2, 128, 2048) <= kActBytes, "activations (MN-major) reach");
-static_assert(mn_reach(0, 7 * 2048, 8, 2, 128, 1024) <= sizeof(h16) * kMlpTile * kMlpF,
-              "features (MN-major) reach");
-static_assert(mn_reach(0, 7 * 512, 2, 2, 128, 256) <= sizeof(h16) * kMlpTile * kMlpOutPad,
-              "output deltas (MN-major) reach");
 static_assert(sizeof(BwdSmem) <= 227 * 1024, "shared memory");
-static_assert(kColDb + 16 <= 512, "tensor memory");
+// per group in the scratch: z_1..z_3 (48 KB) and the image of the operand buffer holding a_1
+constexpr size_t kBwdScratchU4 = 3 * 2 * 4 * kMlpW + kMlpW * kBN * sizeof(h16) / sizeof(uint4);
+static_assert(kColBwdWork + 64 * kBG <= 512, "tensor memory");
+// 96 columns of dW per warp (16 warps, four per lane quadrant) at zeroing and read-back
+static_assert(kBwdThreads == 512 && 4 * 96 == kColBwdWork, "dW column split");
 
 struct MlpGradsDev {
   double *dW[5];
   double *db[5];
 };
 
-// 16 accumulator columns of a layer-output chunk -> the 8 pairs this thread stores.
-__device__ __forceinline__ void store16(h16 *A, int t, int f0, const unsigned *p) {
-#pragma unroll
-  for (int k = 0; k < 2; k++)
-    *reinterpret_cast<uint4 *>(A + cm_off(t, f0 + 8 * k, kMlpW)) =
-        make_uint4(p[4 * k], p[4 * k + 1], p[4 * k + 2], p[4 * k + 3]);
+// 8 values of feature k at samples s0..s0+7 (s0 multiple of 8), rounded to the 16-bit format,
+// into an operand buffer of 8 features x 8 samples core matrices
+template <bool F16>
+__device__ __forceinline__ void store8s(h16 *B, int k, int s0, const float *v) {
+  *reinterpret_cast<uint4 *>(B + bmn_off(k, s0)) =
+      make_uint4(pack16<F16>(v[0], v[1]), pack16<F16>(v[2], v[3]), pack16<F16>(v[4], v[5]),
+                 pack16<F16>(v[6], v[7]));
 }
 
-// Fourier features for directions [8 qt, 8 qt + 8): sin into f[0..7], cos into f[8..15]
-// (the arithmetic of features()).
-__device__ __forceinline__ void features8(const float (*Bf)[2], float rh, float zh, int qt,
-                                          float *f) {
-#pragma unroll
-  for (int j = 0; j < 8; j++) {
-    const int i = 8 * qt + j;
-    float ph = fmaf(Bf[i][0], rh, Bf[i][1] * zh);
-    ph -= rintf(ph);
-    float a = 6.283185307179586f * ph;
-    f[j] = __sinf(a);
-    f[8 + j] = __cosf(a);
-  }
+// SiLU'(z) of a pair, the arithmetic of dsilu() in packed two-lane instructions
+__device__ __forceinline__ float2 dsilu2(float2 z) {
+  const float2 h = __fmul2_rn(z, make_float2(0.5f, 0.5f));
+  float t0, t1;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t0) : "f"(h.x));
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t1) : "f"(h.y));
+  const float2 one = make_float2(1.0f, 1.0f);
+  const float2 s = __ffma2_rn(make_float2(0.5f, 0.5f), make_float2(t0, t1), make_float2(0.5f, 0.5f));
+  const float2 oms = __ffma2_rn(s, make_float2(-1.0f, -1.0f), one);  // 1 - s, one rounding
+  return __fmul2_rn(s, __ffma2_rn(z, oms, one));
+}
+
+// 32-bit word i of four uint4 (i a compile-time constant after unrolling: no address taken,
+// so the array stays in registers)
+__device__ __forceinline__ unsigned word_of(const uint4 (&a)[4], int i) {
+  const uint4 &u = a[i >> 2];
+  return (i & 3) == 0 ? u.x : (i & 3) == 1 ? u.y : (i & 3) == 2 ? u.z : u.w;
+}
+
+// 8 packed pairs (16 values of feature k at samples s0..s0+15) into an operand buffer
+__device__ __forceinline__ void store16p(h16 *B, int k, int s0, const unsigned *p) {
+  *reinterpret_cast<uint4 *>(B + bmn_off(k, s0)) = make_uint4(p[0], p[1], p[2], p[3]);
+  *reinterpret_cast<uint4 *>(B + bmn_off(k, s0 + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
 }
 
 template <class In, bool F16>
@@ -1199,9 +1231,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   BwdSmem &S = *reinterpret_cast<BwdSmem *>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int q = warp & 3, qt = warp >> 2;  // TMEM lane quadrant; quarter of every chunk
-  const int t = q * 32 + lane;  // tile row: sample (or output feature of a weight gradient)
-  h16 *Z = spill + (size_t)blockIdx.x * (4 * kMlpTile * kMlpW);  // this CTA's pre-activations
+  const int g = tid / kBGT;           // tile group
+  const int gt = tid % kBGT;          // thread within the group
+  const int q = warp & 3;             // TMEM lane quadrant
+  const int hs = (warp >> 2) & 1;     // half of the tile's samples (accumulator columns)
+  const int f = q * 32 + lane;        // feature row (TMEM lane) of this thread
 
   // ---- one-time setup ----
   for (int i = tid; i < kMlpW * kMlpF; i += kBwdThreads)
@@ -1209,20 +1243,18 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
   for (int l = 0; l < 3; l++)
     for (int i = tid; i < kMlpW * kMlpW; i += kBwdThreads)
       S.Wh[l][cm_off(i / kMlpW, i % kMlpW, kMlpW)] = to16<F16>(Wp.W[l + 1][i]);
-  for (int i = tid; i < kMlpOutPad * kMlpW; i += kBwdThreads) {
-    int o = i / kMlpW, k = i % kMlpW;
-    S.W5[cm_off(o, k, kMlpW)] = to16<F16>(o < kMlpOut ? Wp.W[4][o * kMlpW + k] : 0.0f);
-  }
-  for (int i = tid; i < kMlpOutPad * kMlpTile; i += kBwdThreads) {
-    S.ONES[i] = to16<F16>(1.0f);
-    S.D5[i] = 0;  // columns 4..15 stay zero
-  }
   for (int i = tid; i < 4 * kMlpW; i += kBwdThreads) S.bias[i / kMlpW][i % kMlpW] = Wp.b[i / kMlpW][i % kMlpW];
   if (tid < 64) S.Bf[tid >> 1][tid & 1] = Wp.B[tid];
   if (tid == 0) {
-    S.abort = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar)), "r"(1));
+    for (int i = 0; i < kBG; i++) {
+      S.abort[i] = 0;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar_a1[i])), "r"(1));
+    }
   }
+  for (int k = tid; k < kMlpW; k += kBwdThreads)
+    S.W5T[k] = make_float4(Wp.W[4][k], Wp.W[4][kMlpW + k], Wp.W[4][2 * kMlpW + k],
+                           Wp.W[4][3 * kMlpW + k]);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&S.tmem_base)),
@@ -1233,9 +1265,26 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const unsigned tm = S.tmem_base;
-  const unsigned tl = tm + ((unsigned)(q * 32) << 16);  // this warp's lanes
-  const unsigned mbar = smem_u32(&S.mbar);
+  const unsigned tbase = S.tmem_base;
+  // zero the dW accumulators: warp w clears 96 columns of its lane quadrant
+  const unsigned tq = tbase + ((unsigned)(q * 32) << 16);
+  {
+    unsigned zr[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) zr[j] = 0u;
+#pragma unroll
+    for (int c = 0; c < 3; c++) tmem_st32(tq + kColDW + 96 * (warp >> 2) + 32 * c, zr);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  const unsigned tD = tbase + kColBwdWork + 64 * g;              // this group's accumulator
+  const unsigned tDl = tD + ((unsigned)(q * 32) << 16) + 32 * hs;  // this thread's 32 columns
+  const unsigned mbar = smem_u32(&S.mbar[g]);
+  h16 *X = S.buf[g][0], *Y = S.buf[g][1], *Dd = S.buf[g][2];
+  const unsigned aX = smem_u32(X), aY = smem_u32(Y), aD = smem_u32(Dd);
   unsigned phase = 0;
   // power-of-two scale that brings the largest |dL/d(output)| below one
   int ex = 0;
@@ -1245,311 +1294,341 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
     ex = max(-120, min(120, ex));
   }
   const float scale = ldexpf(1.0f, -ex);
-  float dw1[16];                               // dW1[t][16 qt + j]
+  float dw1[32];  // dW1[f][32 hs + j] of this group's tiles
 #pragma unroll
-  for (int j = 0; j < 16; j++) dw1[j] = 0.0f;
-  float dbacc[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // db_l of output feature t (quarter 0)
-  float db5acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // db_5 over this warp's rows (lane 0, quarter 0)
-  bool first = true;
-  const unsigned aP = smem_u32(S.P), aQ = smem_u32(S.Q), aF = smem_u32(S.F);
-  const unsigned aD5 = smem_u32(S.D5), aONE = smem_u32(S.ONES), aW5 = smem_u32(S.W5);
+  for (int j = 0; j < 32; j++) dw1[j] = 0.0f;
+  float db[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // db_1..db_4 of feature f over this thread's columns
+  float dw5[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // dW5[o][f] over this thread's columns
+  float db5[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // db_5 over a warp's samples (lane 0, gt < 64)
+  // this group's pre-activations z_1..z_3: per (layer, column half, 8-sample quarter) a row
+  // of 128 uint4 (one per feature), so a warp's stores are contiguous
+  uint4 *Z = reinterpret_cast<uint4 *>(spill) + ((size_t)blockIdx.x * kBG + g) * kBwdScratchU4;
+  uint4 *A1img = Z + 3 * 2 * 4 * kMlpW;  // 16 KB, 16-byte aligned
+  const unsigned mbar_a1 = smem_u32(&S.mbar_a1[g]);
+  unsigned a1_phase = 0;
+  bool a1_pending = false;  // a reload of a_1 is in flight (issuing thread)
+  auto zrow = [&](int l, int k) __attribute__((always_inline)) -> uint4 * { return Z + ((((l - 1) * 2 + hs) * 4 + k) * kMlpW + f); };
 
-  // bounded wait for the last commit; records a failure in S.abort
-  auto wait_mma = [&]() {
-    const bool ok = mbar_wait(mbar, phase);
-    phase ^= 1;
+  auto gsync = [&]() __attribute__((always_inline)) { asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kBGT) : "memory"); };
+  // group barrier that also returns whether any thread of the group passed p = true
+  auto gsync_or = [&](bool p) __attribute__((always_inline)) -> bool {
+    unsigned r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+        " bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((unsigned)p), "r"(1 + g), "r"(kBGT)
+        : "memory");
+    return r != 0;
+  };
+  bool last_ok = true;  // this thread's most recent wait ended in time
+  auto wait_mma = [&]() __attribute__((always_inline)) -> bool {
+    last_ok = mbar_wait(mbar, phase);
+    if (last_ok) phase ^= 1;
     tc_fence_after();
-    if (!ok) {
-      S.abort = 1;
-      atomicExch(&g_mlp_error, 1);
-    }
+    return last_ok;
   };
-  // z (16-bit, packed pairs) of layer index L, chunk c, this thread's quarter and row: 2 x uint4
-  auto zrow = [&](int L, int c) {
-    return reinterpret_cast<uint4 *>(Z + ((size_t)((L * 2 + c) * 4 + qt) * kMlpTile + t) * 16);
+  // Fourier features of the tile's samples into features 0..63 of an operand buffer:
+  // direction j = gt % 32 at samples 8 (gt / 32) .. + 7 (the arithmetic of features())
+  auto write_features = [&](h16 *B) __attribute__((always_inline)) {
+    const int j = gt & 31, s0 = 8 * (gt >> 5);
+    float sv[8], cv[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      float ph = fmaf(S.Bf[j][0], S.rh[g][s0 + i], S.Bf[j][1] * S.zh[g][s0 + i]);
+      ph -= rintf(ph);
+      const float a = 6.283185307179586f * ph;
+      sv[i] = __sinf(a);
+      cv[i] = __cosf(a);
+    }
+    store8s<F16>(B, j, s0, sv);
+    store8s<F16>(B, 32 + j, s0, cv);
   };
 
-  const long long ntiles = (in_count(in, n) + kMlpTile - 1) / kMlpTile;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    long long s;
-    float rh = 0.0f, zh = 0.0f;
-    const bool need = tile_input(in, tile * kMlpTile, t, &rh, &zh, &s);
-    if (!__syncthreads_or(need)) continue;
-    float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (need) {
-      g = gout[s];
-      g.x *= scale;
-      g.y *= scale;
-      g.z *= scale;
-      g.w *= scale;
+  // ---- MMA issue (the group's first thread) ----
+  // forward z_l: A = W_l (K-major), B = a_{l-1} (MN-major: 128 B between sample groups, 1 KB
+  // between feature groups, 2 KB per 16-feature K step)
+  auto issue_forward = [&](int l, unsigned ain) __attribute__((always_inline)) {
+    const int K = l == 1 ? kMlpF : kMlpW;
+    const unsigned aW = l == 1 ? smem_u32(S.W1) : smem_u32(S.Wh[l - 2]);
+    const unsigned long long dA = mma_desc(aW, K), dB = mma_desc_mn(ain, 128, 1024);
+    const unsigned id = idesc_16(kBN, F16, false, true);
+    for (int ks = 0; ks < K / 16; ks++) mma_bf16(tD, dA + 16u * ks, dB + 128u * ks, id, ks > 0);
+    mma_commit(mbar);
+  };
+  // backward step l: dW_l += delta_l a_{l-1}^T (A = delta_l from D and B = a_{l-1}, both with
+  // the samples along K: K-major, 1 KB between feature groups), then W_l^T delta_l into the
+  // working columns (A = W_l read MN-major: 128 B between input-feature groups, 2 KB between
+  // output-feature groups; B = delta_l MN-major)
+  auto issue_backward = [&](int l, unsigned ax) __attribute__((always_inline)) {
+    const unsigned long long dA = mma_desc(aD, kBN), dX = mma_desc(ax, kBN);
+    const unsigned idw = idesc_16(kMlpW, F16, false, false);
+    const unsigned tW = tbase + kColDW + 128u * (unsigned)(l - 2);
+    for (int ks = 0; ks < kBN / 16; ks++) mma_bf16(tW, dA + 16u * ks, dX + 16u * ks, idw, 1);
+    const unsigned long long dWt = mma_desc_mn(smem_u32(S.Wh[l - 2]), 128, 2048);
+    const unsigned long long dDl = mma_desc_mn(aD, 128, 1024);
+    const unsigned idt = idesc_16(kBN, F16, true, true);
+    for (int ks = 0; ks < kMlpW / 16; ks++)
+      mma_bf16(tD, dWt + 256u * ks, dDl + 128u * ks, idt, ks > 0);
+    mma_commit(mbar);
+  };
+  // dW1 of the tile: delta_1 gamma^T into the working columns (gamma in Y, N = 64)
+  auto issue_dw1 = [&]() __attribute__((always_inline)) {
+    const unsigned long long dA = mma_desc(aD, kBN), dG = mma_desc(aY, kBN);
+    const unsigned id = idesc_16(kMlpF, F16, false, false);
+    for (int ks = 0; ks < kBN / 16; ks++) mma_bf16(tD, dA + 16u * ks, dG + 16u * ks, id, ks > 0);
+    mma_commit(mbar);
+  };
+
+  bool bad = false;  // group-uniform: a wait ran out
+  const long long ntiles = (in_count(in, n) + kBN - 1) / kBN;
+  const long long tstride = (long long)gridDim.x * kBG;
+  const long long tile0 = (long long)blockIdx.x * kBG + g;
+  // inputs of the group's next tile (threads gt < 64), read a tile ahead so that the list and
+  // ray lookups stay off the tile's chain of dependent phases
+  float nrh = 0.0f, nzh = 0.0f;
+  float4 nd = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  bool nneed = false;
+  auto fetch = [&](long long t) __attribute__((always_inline)) {
+    nneed = false;
+    nrh = nzh = 0.0f;
+    nd = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (gt < kBN && t < ntiles) {
+      long long s = 0;
+      nneed = tile_input(in, t * kBN, gt, &nrh, &nzh, &s);
+      if (nneed) nd = gout[s];  // scaled when stored: nothing here waits for the load
     }
-    {
-      float f[16];
-      features8(S.Bf, rh, zh, qt, f);
-      store8<F16>(S.F, t, 8 * qt, kMlpF, f);
-      store8<F16>(S.F, t, 32 + 8 * qt, kMlpF, f + 8);
-    }
-    if (qt == 0) {
-      const float d[8] = {g.x, g.y, g.z, g.w, 0.0f, 0.0f, 0.0f, 0.0f};
-      store8<F16>(S.D5, t, 0, kMlpOutPad, d);
-      float r[4] = {g.x, g.y, g.z, g.w};
+  };
+  fetch(tile0);
+  for (long long tile = tile0; tile < ntiles; tile += tstride) {
+    // ---- inputs: sample coordinates and scaled output gradients ----
+    const bool need = nneed;
+    if (gt < kBN) {
+      const float4 d = make_float4(nd.x * scale, nd.y * scale, nd.z * scale, nd.w * scale);
+      S.rh[g][gt] = nrh;
+      S.zh[g][gt] = nzh;
+      S.d5[g][0][gt] = d.x;
+      S.d5[g][1][gt] = d.y;
+      S.d5[g][2][gt] = d.z;
+      S.d5[g][3][gt] = d.w;
+      float r[4] = {d.x, d.y, d.z, d.w};
 #pragma unroll
       for (int o = 0; o < 4; o++)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) r[o] += __shfl_xor_sync(0xffffffffu, r[o], off);
       if (lane == 0)
 #pragma unroll
-        for (int o = 0; o < 4; o++) db5acc[o] += r[o];
+        for (int o = 0; o < 4; o++) db5[o] += r[o];
     }
+    if (!gsync_or(need)) {  // no sample of this tile needs the network
+      fetch(tile + tstride);
+      continue;
+    }
+    write_features(Dd);
     proxy_fence();
     tc_fence_before();
-    __syncthreads();
+    gsync();
 
-    uint4 zn[4];  // this thread's pre-activations of the next backward layer (2 chunks x 2)
-    // ---------------- forward: a1..a4 (P, Q, P, Q), pre-activations to the scratch ----------------
-    for (int l = 0; l < 4; l++) {
-      const int K = l == 0 ? kMlpF : kMlpW;
-      const unsigned ain = l == 0 ? aF : ((l & 1) ? aP : aQ);
-      h16 *Aout = (l & 1) ? S.Q : S.P;
-      const unsigned wl = l == 0 ? smem_u32(S.W1) : smem_u32(S.Wh[l - 1]);
-      auto issue = [&](int c) {
-        tc_fence_after();
-        const unsigned b0 = wl + (unsigned)(c * 8 * (K / 8) * 128);  // rows 64c.. of W_l
-        const unsigned long long dA = mma_desc(ain, K), dB = mma_desc(b0, K);
-        for (int ks = 0; ks < K / 16; ks++)
-          mma_bf16(tm + kColWork, dA + 16u * ks, dB + 16u * ks, idesc_16(kChunk, F16), ks > 0);
-        mma_commit(mbar);
-      };
-      if (tid == 0) issue(0);
-      for (int c = 0; c < 2; c++) {
-        wait_mma();
-        float v[16];
-        tmem_ld16(tl + kColWork + 16 * qt, v);
-        tc_fence_before();
-        __syncthreads();  // working columns free
-        if (S.abort) goto done;
-        if (tid == 0 && c == 0) issue(1);
-        const int f0 = kChunk * c + 16 * qt;
-        unsigned zp[8], ap[8];
+    // ---- forward: a_1 -> X, a_2 -> Y, a_3 -> X; layer 4 ends in the output layer ----
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-          zp[j] = pack16<F16>(v[2 * j] + S.bias[l][f0 + 2 * j], v[2 * j + 1] + S.bias[l][f0 + 2 * j + 1]);
-          ap[j] = silu2p<F16>(zp[j]);
+    for (int l = 1; l <= 4; l++) {
+      if (gt == 0) {
+        tc_fence_after();
+        issue_forward(l, l == 1 ? aD : (l == 3 ? aY : aX));
+        if (l == 2) {  // keep an image of a_1 (X): a_3 overwrites it, dW2 needs it again
+          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(A1img),
+                       "r"(aX), "r"(kMlpW * kBN * (int)sizeof(h16))
+                       : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
-        uint4 *zr = zrow(l, c);
-#pragma unroll
-        for (int k = 0; k < 2; k++) zr[k] = make_uint4(zp[4 * k], zp[4 * k + 1], zp[4 * k + 2], zp[4 * k + 3]);
-        store16(Aout, t, f0, ap);
       }
-      proxy_fence();
-      tc_fence_before();
-      __syncthreads();
-    }
-
-    // ---------------- output layer: dW5^T += a4^T delta5, delta4 = (delta5 W5) SiLU'(z4) ----------------
-    {
-      auto issue = [&](int c) {
-        tc_fence_after();
-        mma_bf16(tm + kColWork, mma_desc(aD5, kMlpOutPad), mma_desc_mn(aW5 + c * 1024, 128, 2048),
-                 idesc_16(kChunk, F16, false, true), 0);
-        mma_commit(mbar);
-      };
-      if (tid == 0) {
-        tc_fence_after();
-        const unsigned long long dA = mma_desc_mn(aQ, 128, 2048), dB = mma_desc_mn(aD5, 128, 256);
+      if (l == 1) fetch(tile + tstride);
+      const bool ok = wait_mma();
+      if (ok) {
+        const float b = S.bias[l - 1][f];
+        const float2 b2 = make_float2(b, b);
+        if (l < 4) {
+          h16 *Aout = l == 2 ? Y : X;
+          float v[32];
+          tmem_ld32(tDl, v);
 #pragma unroll
-        for (int ks = 0; ks < kMlpTile / 16; ks++)
-          mma_bf16(tm + kColW5, dA + 256u * ks, dB + 32u * ks, idesc_16(16, F16, true, true),
-                   !first || ks > 0);
-        issue(0);
-      }
-      for (int c = 0; c < 2; c++) {
-        const uint4 *zr = zrow(3, c);
-        uint4 zq[2];
+          for (int h = 0; h < 2; h++) {
+            unsigned zp[8], ap[8];
 #pragma unroll
-        for (int k = 0; k < 2; k++) zq[k] = zr[k];
-        wait_mma();
-        float v[16];
-        tmem_ld16(tl + kColWork + 16 * qt, v);
-        tc_fence_before();
-        __syncthreads();
-        if (S.abort) goto done;
-        if (tid == 0 && c == 0) issue(1);
-        const int f0 = kChunk * c + 16 * qt;
-        const unsigned *zz = reinterpret_cast<const unsigned *>(zq);
-        unsigned dp[8];
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-          const float2 z = unpack16<F16>(zz[j]);
-          dp[j] = pack16<F16>(v[2 * j] * dsilu(z.x), v[2 * j + 1] * dsilu(z.y));
-        }
-        store16(S.Q, t, f0, dp);
-      }
-      // pre-activations z_2 for layer 4's delta epilogue, loaded ahead of the barrier
-#pragma unroll
-      for (int c = 0; c < 2; c++) {
-        const uint4 *zr = zrow(2, c);
-        zn[2 * c] = zr[0];
-        zn[2 * c + 1] = zr[1];
-      }
-      proxy_fence();
-      tc_fence_before();
-      __syncthreads();
-    }
-
-    // ---------------- hidden layers l = 4..1 ----------------
-    for (int l = 4; l >= 1; l--) {
-      const unsigned ay = (l & 1) ? aP : aQ;                            // delta_l
-      h16 *X = (l & 1) ? S.Q : S.P;                                     // a_{l-1} (l >= 2)
-      const unsigned ax = l == 1 ? aF : smem_u32(X);
-      const int Kin = l == 1 ? kMlpF : kMlpW;
-      if (l == 3 || l == 2) {  // a_{l-1} was overwritten: recompute it from z_{l-1} (in zn)
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-          unsigned ap[8];
-#pragma unroll
-          for (int k = 0; k < 2; k++) {
-            const uint4 z = zn[2 * c + k];
-            ap[4 * k] = silu2p<F16>(z.x);
-            ap[4 * k + 1] = silu2p<F16>(z.y);
-            ap[4 * k + 2] = silu2p<F16>(z.z);
-            ap[4 * k + 3] = silu2p<F16>(z.w);
+            for (int j = 0; j < 8; j++) {
+              const float2 z = __fadd2_rn(make_float2(v[16 * h + 2 * j], v[16 * h + 2 * j + 1]), b2);
+              zp[j] = pack16<F16>(z.x, z.y);
+              ap[j] = silu2p<F16>(zp[j]);
+            }
+            *zrow(l, 2 * h) = make_uint4(zp[0], zp[1], zp[2], zp[3]);
+            *zrow(l, 2 * h + 1) = make_uint4(zp[4], zp[5], zp[6], zp[7]);
+            store16p(Aout, f, 32 * hs + 16 * h, ap);
           }
-          store16(X, t, kChunk * c + 16 * qt, ap);
-        }
-        proxy_fence();
-        tc_fence_before();
-        __syncthreads();
-      }
-      // dW_l (persistent columns; dW1 goes through the working columns once per tile) and
-      // db_l; for l >= 2 the first delta_{l-1} chunk is issued behind them under the same
-      // commit (the tensor pipe runs them in order, so its completion also means dW_l has
-      // finished reading a_{l-1}, which the delta epilogue overwrites)
-      const unsigned wl = l >= 2 ? smem_u32(S.Wh[l - 2]) : 0u;  // W_l
-      auto issue_delta = [&](int c) {
-        const unsigned long long dA = mma_desc(ay, kMlpW);
-        const unsigned long long dB = mma_desc_mn(wl + c * 1024, 128, 2048);
+        } else {
+          // output layer (FP32, pairs of samples): dW5 += delta_5 a_4^T and
+          // delta_4 = (W5^T delta_5) SiLU'(z_4)
+          float2 dsum = make_float2(0.0f, 0.0f);
+          float2 acc5[4] = {dsum, dsum, dsum, dsum};
+          const float4 w5 = S.W5T[f];  // W5 column of this thread's feature (FP32)
+          const float2 w5x = make_float2(w5.x, w5.x), w5y = make_float2(w5.y, w5.y);
+          const float2 w5z = make_float2(w5.z, w5.z), w5w = make_float2(w5.w, w5.w);
+          float v[32];
+          tmem_ld32(tDl, v);
 #pragma unroll
-        for (int ks = 0; ks < kMlpW / 16; ks++)
-          mma_bf16(tm + kColWork, dA + 16u * ks, dB + 256u * ks,
-                   idesc_16(kChunk, F16, false, true), ks > 0);
-      };
-      if (tid == 0) {
+          for (int h = 0; h < 2; h++) {
+            unsigned dp[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+              const int sc = 32 * hs + 16 * h + 2 * j;
+              const float2 zf = __fadd2_rn(make_float2(v[16 * h + 2 * j], v[16 * h + 2 * j + 1]), b2);
+              const unsigned zp = pack16<F16>(zf.x, zf.y);
+              const float2 a = unpack16<F16>(silu2p<F16>(zp));
+              const float2 z = unpack16<F16>(zp);
+              const float2 dx = *reinterpret_cast<const float2 *>(&S.d5[g][0][sc]);
+              const float2 dy = *reinterpret_cast<const float2 *>(&S.d5[g][1][sc]);
+              const float2 dz = *reinterpret_cast<const float2 *>(&S.d5[g][2][sc]);
+              const float2 dw = *reinterpret_cast<const float2 *>(&S.d5[g][3][sc]);
+              acc5[0] = __ffma2_rn(dx, a, acc5[0]);
+              acc5[1] = __ffma2_rn(dy, a, acc5[1]);
+              acc5[2] = __ffma2_rn(dz, a, acc5[2]);
+              acc5[3] = __ffma2_rn(dw, a, acc5[3]);
+              const float2 t =
+                  __ffma2_rn(w5x, dx, __ffma2_rn(w5y, dy, __ffma2_rn(w5z, dz, __fmul2_rn(w5w, dw))));
+              const float2 dl = __fmul2_rn(t, dsilu2(z));
+              dsum = __fadd2_rn(dsum, dl);
+              dp[j] = pack16<F16>(dl.x, dl.y);
+            }
+            store16p(Dd, f, 32 * hs + 16 * h, dp);
+          }
+#pragma unroll
+          for (int o = 0; o < 4; o++) dw5[o] += acc5[o].x + acc5[o].y;
+          db[3] += dsum.x + dsum.y;
+        }
+      }
+      if (l == 2 && gt == 0)  // the image is read out before layer 3 writes a_3 into X
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      proxy_fence();
+      tc_fence_before();
+      bad = gsync_or(!ok);
+      if (bad) break;
+    }
+    if (bad) break;
+
+    // ---- backward steps l = 4, 3, 2: a_{l-1} is a_3 (X), a_2 (Y), a_1 (X, recomputed) ----
+#pragma unroll
+    for (int l = 4; l >= 2; l--) {
+      uint4 zq[4];  // z_{l-1} of this thread
+#pragma unroll
+      for (int k = 0; k < 4; k++) zq[k] = *zrow(l - 1, k);
+      bool a1_ok = true;
+      if (gt == 0) {
+        if (l == 2) {  // a_1 back in X
+          a1_ok = mbar_wait(mbar_a1, a1_phase);
+          if (a1_ok) {
+            a1_phase ^= 1;
+            a1_pending = false;
+          }
+        }
         tc_fence_after();
-        const unsigned colw = l == 1 ? kColWork : (l == 2 ? kColW2 : (l == 3 ? kColW3 : kColW4));
-        const unsigned kst = (unsigned)(Kin / 8) * 128;  // distance between 8-sample groups of X
-        const unsigned long long dY = mma_desc_mn(ay, 128, 2048), dX = mma_desc_mn(ax, 128, kst);
-        const unsigned long long dO = mma_desc(aONE, kMlpTile);
-        const unsigned idw = l == 1 ? idesc_16(kMlpF, F16, true, true) : idesc_16(kMlpW, F16, true, true);
-        const bool acc = l > 1 && !first;
-#pragma unroll
-        for (int ks = 0; ks < kMlpTile / 16; ks++)
-          mma_bf16(tm + colw, dY + 256u * ks, dX + (unsigned long long)(ks * 2 * kst >> 4), idw,
-                   acc || ks > 0);
-#pragma unroll
-        for (int ks = 0; ks < kMlpTile / 16; ks++)
-          mma_bf16(tm + kColDb, dY + 256u * ks, dO + 16u * ks, idesc_16(16, F16, true, false),
-                   ks > 0);
-        if (l >= 2) issue_delta(0);
-        mma_commit(mbar);
+        if (a1_ok) issue_backward(l, l == 3 ? aY : aX);  // else the group's wait runs out
       }
-      if (l == 1) {
-        wait_mma();
-        if (qt == 0) {
-          float v[16];
-          tmem_ld16(tl + kColDb, v);
-          dbacc[0] += v[0];
-        }
-        float v[16];
-        tmem_ld16(tl + kColWork + 16 * qt, v);
-#pragma unroll
-        for (int j = 0; j < 16; j++) dw1[j] += v[j];
-        tc_fence_before();
-        __syncthreads();
-        if (S.abort) goto done;
-        break;
+      const bool ok = wait_mma();
+      if (ok && l == 4 && gt == 0) {  // dW4 has read a_3: reload a_1 into X
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_a1),
+                     "r"(kMlpW * kBN * (int)sizeof(h16))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"(aX),
+            "l"(A1img), "r"(kMlpW * kBN * (int)sizeof(h16)), "r"(mbar_a1)
+            : "memory");
+        a1_pending = true;
       }
+      if (ok) {
+        float2 dsum = make_float2(0.0f, 0.0f);
+        float v[32];
+        tmem_ld32(tDl, v);
 #pragma unroll
-      for (int c = 0; c < 2; c++) {
-        const uint4 zq[2] = {zn[2 * c], zn[2 * c + 1]};  // z_{l-1}, loaded a layer ahead
-        wait_mma();
-        if (c == 0 && qt == 0) {
-          float v[16];
-          tmem_ld16(tl + kColDb, v);
-          dbacc[l - 1] += v[0];
-        }
-        float v[16];
-        tmem_ld16(tl + kColWork + 16 * qt, v);
-        tc_fence_before();
-        __syncthreads();
-        if (S.abort) goto done;
-        if (tid == 0 && c == 0) {
-          tc_fence_after();
-          issue_delta(1);
-          mma_commit(mbar);
-        }
-        const int f0 = kChunk * c + 16 * qt;
-        const unsigned *zz = reinterpret_cast<const unsigned *>(zq);
-        unsigned dp[8];
+        for (int h = 0; h < 2; h++) {
+          unsigned dp[8];
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-          const float2 z = unpack16<F16>(zz[j]);
-          dp[j] = pack16<F16>(v[2 * j] * dsilu(z.x), v[2 * j + 1] * dsilu(z.y));
+          for (int j = 0; j < 8; j++) {
+            const float2 z = unpack16<F16>(word_of(zq, 8 * h + j));
+            const float2 d = __fmul2_rn(make_float2(v[16 * h + 2 * j], v[16 * h + 2 * j + 1]), dsilu2(z));
+            dsum = __fadd2_rn(dsum, d);
+            dp[j] = pack16<F16>(d.x, d.y);
+          }
+          store16p(Dd, f, 32 * hs + 16 * h, dp);  // delta_l has been read
         }
-        store16(X, t, f0, dp);
-      }
-      if (l >= 3) {  // z_{l-2} for the next layer, loaded ahead of the barrier
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-          const uint4 *zr = zrow(l - 3, c);
-          zn[2 * c] = zr[0];
-          zn[2 * c + 1] = zr[1];
-        }
+        db[l - 2] += dsum.x + dsum.y;
+        if (l == 2) write_features(Y);  // gamma for dW1 (a_2 has been read)
       }
       proxy_fence();
       tc_fence_before();
-      __syncthreads();
+      bad = gsync_or(!ok);
+      if (bad) break;
     }
-    first = false;
+    if (bad) break;
+
+    // ---- dW1 += delta_1 gamma^T, through the working columns ----
+    if (gt == 0) {
+      tc_fence_after();
+      issue_dw1();
+    }
+    const bool ok = wait_mma();
+    if (ok) {
+      float v[32];
+      tmem_ld32(tDl, v);
+#pragma unroll
+      for (int j = 0; j < 32; j++) dw1[j] += v[j];
+    }
+    tc_fence_before();
+    bad = gsync_or(!ok);  // the tile's buffers and inputs are free after this barrier
+    if (bad) break;
   }
 
-done:
+  if (bad) {
+    if (!last_ok) atomicExch(&g_mlp_error, 1);
+    if (gt == 0) {
+      S.abort[g] = 1;
+      // let an MMA and a bulk copy still in flight finish (bounded) before the tensor memory
+      // and the shared memory are released
+      if (!last_ok) mbar_wait(mbar, phase);
+      if (a1_pending) mbar_wait(mbar_a1, a1_phase);
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+  }
+  tc_fence_before();
   __syncthreads();
-  if (S.abort) {
-    // let an MMA still in flight finish (bounded) before the tensor memory is released
-    if (tid == 0) mbar_wait(mbar, phase);
-  } else if (!first) {
-    tc_fence_after();
+  tc_fence_after();
+  if (!S.abort[0] && !S.abort[1]) {
     const double un = ldexp(1.0, ex);
 #pragma unroll
-    for (int j = 0; j < 16; j++) atomicAdd(G.dW[0] + t * kMlpF + 16 * qt + j, (double)dw1[j] * un);
-    for (int L = 1; L < 4; L++) {
-      const unsigned col = kColW2 + (unsigned)(L - 1) * 128;
-      for (int cc = 0; cc < 2; cc++) {
-        float v[16];
-        tmem_ld16(tl + col + 32 * qt + 16 * cc, v);
+    for (int j = 0; j < 32; j++)
+      atomicAdd(G.dW[0] + f * kMlpF + 32 * hs + j, (double)dw1[j] * un);
 #pragma unroll
-        for (int j = 0; j < 16; j++)
-          atomicAdd(G.dW[L] + t * kMlpW + 32 * qt + 16 * cc + j, (double)v[j] * un);
-      }
-    }
-    if (qt == 0) {
+    for (int l = 0; l < 4; l++) atomicAdd(G.db[l] + f, (double)db[l] * un);
+#pragma unroll
+    for (int o = 0; o < kMlpOut; o++) atomicAdd(G.dW[4] + o * kMlpW + f, (double)dw5[o] * un);
+    if (gt < kBN && lane == 0)
+#pragma unroll
+      for (int o = 0; o < kMlpOut; o++) atomicAdd(G.db[4] + o, (double)db5[o] * un);
+    // dW2..dW4: warp w reads 96 columns of its lane quadrant (16-column chunks never straddle
+    // a layer boundary)
+    for (int c = 0; c < 6; c++) {
+      const int col = 96 * (warp >> 2) + 16 * c;
       float v[16];
-      tmem_ld16(tl + kColW5, v);  // row = input feature t, columns = outputs
+      tmem_ld16(tq + kColDW + col, v);
+      double *dst = G.dW[1 + col / kMlpW] + f * kMlpW + col % kMlpW;
 #pragma unroll
-      for (int o = 0; o < kMlpOut; o++) atomicAdd(G.dW[4] + o * kMlpW + t, (double)v[o] * un);
-#pragma unroll
-      for (int l = 0; l < 4; l++) atomicAdd(G.db[l] + t, (double)dbacc[l] * un);
-      if (lane == 0)
-#pragma unroll
-        for (int o = 0; o < kMlpOut; o++) atomicAdd(G.db[4] + o, (double)db5acc[o] * un);
+      for (int j = 0; j < 16; j++) atomicAdd(dst + j, (double)v[j] * un);
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(512));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
   }
 }
 
@@ -1565,8 +1644,9 @@ __global__ void absmax_kernel(const float4 *__restrict__ x, long long n, unsigne
   if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(out, __float_as_uint(m));
 }
 
+// pre-activation scratch of the backward kernel: z_1..z_3 of one tile per group and CTA
 static size_t mlp_spill_bytes(long long blocks) {
-  return (size_t)blocks * 4 * kMlpTile * kMlpW * sizeof(h16);
+  return (size_t)blocks * kBG * kBwdScratchU4 * sizeof(uint4);
 }
 
 // Zeroes the gradient outputs and runs the backward kernel over n samples; spill must hold
@@ -1575,8 +1655,8 @@ static long long mlp_bwd_blocks(long long n) {
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  long long tiles = (n + kMlpTile - 1) / kMlpTile;
-  return tiles < nsm ? (tiles > 0 ? tiles : 1) : nsm;
+  const long long pairs = ((n + kBN - 1) / kBN + kBG - 1) / kBG;
+  return pairs < nsm ? (pairs > 0 ? pairs : 1) : nsm;
 }
 
 template <class In, bool F16>
@@ -1628,18 +1708,52 @@ size_t mlp_bwd_scratch_bytes(long long n) { return mlp_spill_bytes(mlp_bwd_block
 
 // Backward pass over the samples of a render (rays from the forward's pre-pass in ray_buf,
 // per-sample dL/d(outputs) in dmod, their largest magnitude in *dmax).
+// Inputs and output gradients of the listed samples in list order, padded with zeros to whole
+// backward tiles: xy[i] = (rhat, zhat) of sample list[i], g[i] = dmod[list[i]] (zero without
+// gas); i < *count rounded up to a multiple of 64.
+__global__ void gather_list_kernel(const __grid_constant__ MarchParams P,
+                                   const Ray *__restrict__ rays, const unsigned *__restrict__ list,
+                                   const unsigned *__restrict__ count,
+                                   const float4 *__restrict__ dmod, float2 *__restrict__ xy,
+                                   float4 *__restrict__ g) {
+  const long long c = *count;
+  const long long cp = (c + kBN - 1) / kBN * kBN;
+  const unsigned ns = (unsigned)P.n_samples;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cp;
+       i += (long long)gridDim.x * blockDim.x) {
+    float rh = 0.0f, zh = 0.0f;
+    float4 d = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (i < c) {
+      const unsigned v = list[i];
+      bool gas;
+      sample_coords(P, rays[v / ns], (int)(v % ns), &gas, &rh, &zh);
+      if (gas) d = dmod[v];
+    }
+    xy[i] = make_float2(rh, zh);
+    g[i] = d;
+  }
+}
+
+size_t mlp_bwd_gather_entries(long long n) { return (size_t)((n + kBN - 1) / kBN * kBN); }
+
 int launch_mlp_bwd_rays(const rt_mlp *m, const MarchParams &P, const void *ray_buf,
                         const void *list_buf, const float4 *dmod, const unsigned *dmax,
-                        void *spill, const rt_mlp_grads *g, cudaStream_t stream) {
+                        void *spill, float2 *xy_buf, float4 *g_buf, const rt_mlp_grads *g,
+                        cudaStream_t stream) {
   long long n = (long long)P.nx * P.ny * P.n_samples;
   if (list_buf) {
     const SampleList sl = sample_list_view(P, list_buf);
-    ListInput in;
-    in.P = P;
-    in.rays = reinterpret_cast<const Ray *>(ray_buf);
-    in.list = sl.list;
+    if (n > 0) {
+      const long long nb = (n + 255) / 256;
+      gather_list_kernel<<<(unsigned)(nb < 148 * 16 ? nb : 148 * 16), 256, 0, stream>>>(
+          P, reinterpret_cast<const Ray *>(ray_buf), sl.list, sl.count, dmod, xy_buf, g_buf);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return set_error(RT_ECUDA, "gather launch: %s", cudaGetErrorString(e));
+    }
+    PackedInput in;
+    in.xy = xy_buf;
     in.count = sl.count;
-    return launch_mlp_bwd(m, in, dmod, n, dmax, reinterpret_cast<h16 *>(spill), g, stream);
+    return launch_mlp_bwd(m, in, g_buf, n, dmax, reinterpret_cast<h16 *>(spill), g, stream);
   }
   RayInput in;
   in.P = P;
