@@ -625,8 +625,28 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
               part[t][lane ^ (t & 7)] = rev_step(m, p, cs);
             }
           };
+          // two adjacent pairs in the window (the next most common case), likewise
+          auto two_pairs = [&](auto M) {
+            constexpr int m = decltype(M)::value;
+#pragma unroll 1
+            for (int t = LPR - 1; t >= 0; t--) {
+              const float4 p = ph[rr * LPR + t];
+              const bool gas = p.z > 0.0f;
+              const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
+              Snext = gas ? p.w : Snext;
+              const float4 c0 = rev_step(m, p, cs), c1 = rev_step(m + 1, p, cs);
+              part[t][lane ^ (t & 7)] =
+                  make_float4(c0.x + c1.x, c0.y + c1.y, c0.z + c1.z, c0.w + c1.w);
+            }
+          };
           const int npair = __popc(act2);
-          if (npair == 1 && act2 == 1u) {
+          if (npair == 2 && act2 == 3u) {
+            two_pairs(std::integral_constant<int, 0>());
+          } else if (CPL / 2 > 2 && npair == 2 && act2 == 6u) {
+            two_pairs(std::integral_constant<int, (CPL / 2 > 2 ? 1 : 0)>());
+          } else if (CPL / 2 > 3 && npair == 2 && act2 == 12u) {
+            two_pairs(std::integral_constant<int, (CPL / 2 > 3 ? 2 : 0)>());
+          } else if (npair == 1 && act2 == 1u) {
             one_pair(std::integral_constant<int, 0>());
           } else if (npair == 1 && act2 == 2u) {
             one_pair(std::integral_constant<int, 1>());
