@@ -554,29 +554,35 @@ static int launch_mlp_t(const rt_mlp *m, const In &in, float *out, long long n,
 }
 
 // ---------------------------------------------------------------------------------------
-// BF16 network forward with split operands ("three-pass" BF16): the product of every layer is
-// formed as W_hi a_hi + W_hi a_lo + W_lo a_hi, where x_hi = bf16(x) and x_lo = bf16(x - x_hi)
-// for the weights W and the activations a (the inputs of each layer, Fourier features
-// included), so the rounding of both operands to BF16 (2^-9 relative) drops out to second
-// order; SiLU is evaluated in FP32 (hardware tanh) and the output layer (128 -> 4) runs on the
-// CUDA cores in FP32. The accumulation is FP32 in tensor memory throughout.
+// BF16 network forward with split operands: the product of every layer is formed as
+// W_hi a_hi + W_hi a_lo + W_lo a_hi, where x_hi = bf16(x) and x_lo = x - x_hi for the weights
+// W and the activations a (the inputs of each layer, Fourier features included), so the
+// rounding of both operands to BF16 (2^-9 relative) drops out to second order. The two
+// correction products are about 2^-8 of the main one, so 3 significant bits suffice for
+// their factors: they run as FP8 (E5M2, whose 5-bit exponent holds the small low parts
+// without scaling) MMAs of K = 32, at twice the BF16 rate, so a K step of 32 costs two BF16
+// MMAs and two FP8 MMAs instead of six BF16 MMAs. SiLU is evaluated in FP32 (hardware tanh)
+// and the output layer (128 -> 4) runs on the CUDA cores in FP32. The accumulation is FP32 in
+// tensor memory throughout.
 //
 // The product is taken transposed, D[out feature][sample] = W[out][in] a[in][sample], so that
-// the weights are the A operand: the high parts of every layer stay in shared memory (K-major
-// core matrices, 112 KB) and the low parts in tensor memory (A from tensor memory: row o in
-// lane o, two BF16 per 32-bit column, 224 columns), which leaves shared memory for three tile
-// groups of 64 samples. A group's activations are the B operand (MN-major core matrices of 8
-// features x 8 samples, high and low parts, 16 KB each); one thread per (output feature,
-// half of the samples) reads its accumulator row back, adds the bias, applies SiLU and writes
-// the next layer's high and low parts in place. After the fourth layer the FP32 activations
+// the weights are the A operand: W_hi of every layer stays in shared memory (BF16, K-major
+// core matrices, 112 KB) and E5M2 copies of W and of W_lo in tensor memory (A from tensor
+// memory: row o in lane o, four E5M2 per 32-bit column, the lower input in the low byte;
+// 224 columns), which leaves shared memory for three tile groups of 64 samples. A group's
+// activations are the B operand: a_hi in BF16 (MN-major core matrices of 8 features x 8
+// samples, 16 KB) and E5M2 copies of a and of a_lo (MN-major core matrices of 8 features x
+// 16 samples, 8 KB each); one thread per (output feature, half of the samples) reads its
+// accumulator row back, adds the bias, applies SiLU and writes the next layer's three
+// operands in place. After the fourth layer the FP32 activations
 // go to shared memory (XOR-swizzled, 32 KB); four threads per sample each form the four
 // outputs over a quarter of the 128 inputs in FP32, and one adds the quarters.
 // ---------------------------------------------------------------------------------------
 constexpr int kSN = 64;                     // samples per tile (MMA N)
 constexpr int kSG = 3;                      // tile groups
 constexpr int kSGT = 256;                   // threads per group (two per TMEM lane row)
-constexpr unsigned kColWlo1 = 0;            // W1_lo: 128 x 64 -> 32 columns
-constexpr unsigned kColWloH = 32;           // W2..W4 lo: 64 columns each
+constexpr unsigned kColW8 = 0;              // E5M2 of W: W1 16 columns, W2..W4 32 each
+constexpr unsigned kColWlo8 = 112;          // E5M2 of W_lo, the same layout
 constexpr unsigned kColSplitD = 224;        // accumulators: 64 columns per group
 
 struct __align__(1024) SplitSmem {
@@ -596,6 +602,11 @@ struct __align__(1024) SplitSmem {
 };
 static_assert(sizeof(SplitSmem) <= 227 * 1024, "shared memory");
 static_assert(kColSplitD + 64 * kSG <= 512, "tensor memory");
+static_assert(kColWlo8 + 112 <= kColSplitD, "FP8 weight columns");
+// TMEM column of layer l's E5M2 weights (l = 0: W1, 64 inputs; l >= 1: 128 inputs)
+__device__ __forceinline__ unsigned col8(unsigned base, int l) {
+  return base + (l == 0 ? 0u : 16u + 32u * (unsigned)(l - 1));
+}
 // the FP32 activations of the last hidden layer fill a group's two activation buffers
 static_assert(sizeof(float) * kMlpW * kSN == 2 * sizeof(h16) * kMlpW * kSN, "h4 staging");
 
@@ -605,24 +616,45 @@ __device__ __forceinline__ int bmn_off(int k, int s) {
   return (((k >> 3) * (kSN >> 3) + (s >> 3)) << 6) + ((k & 7) << 3) + (s & 7);
 }
 
+// Byte offset of (feature k, sample s) in an 8-bit MN-major B tile: core matrix (k/8, s/16) of
+// 8 features x 16 samples at ((k/8) (kSN/16) + s/16) x 128 bytes, row k % 8, byte s % 16.
+__device__ __forceinline__ int b8_off(int k, int s) {
+  return (((k >> 3) * (kSN >> 4) + (s >> 4)) << 7) + ((k & 7) << 4) + (s & 15);
+}
+
+// four floats to E5M2 (round to nearest, saturating), x0 in the low byte
+__device__ __forceinline__ unsigned e5m2x4(float x0, float x1, float x2, float x3) {
+  unsigned short lo, hi;
+  asm("cvt.rn.satfinite.e5m2x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(x1), "f"(x0));
+  asm("cvt.rn.satfinite.e5m2x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(x3), "f"(x2));
+  return (unsigned)lo | ((unsigned)hi << 16);
+}
+
 // bf16 pair (low half = first) to two floats
 __device__ __forceinline__ float2 bf2f(unsigned u) {
   return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
 }
 
-// 8 values of feature k at samples s0..s0+7 (s0 multiple of 8): high and low BF16 parts
-__device__ __forceinline__ void split_store8(h16 *Bh, h16 *Bl, int k, int s0, const float *v) {
-  unsigned hi[4], lo[4];
+// 8 values of feature k at samples s0..s0+7 (s0 multiple of 8): the BF16 high part into Bh and
+// E5M2 copies of the value and of its low part into B8 and B8l (8 bytes each)
+__device__ __forceinline__ void split_store8(h16 *Bh, unsigned char *B8, unsigned char *B8l,
+                                             int k, int s0, const float *v) {
+  unsigned hi[4];
+  float lo[8];
 #pragma unroll
   for (int j = 0; j < 4; j++) {
     hi[j] = pack16<false>(v[2 * j], v[2 * j + 1]);
     const float2 r = __ffma2_rn(bf2f(hi[j]), make_float2(-1.0f, -1.0f),
                                 make_float2(v[2 * j], v[2 * j + 1]));  // exact residual
-    lo[j] = pack16<false>(r.x, r.y);
+    lo[2 * j] = r.x;
+    lo[2 * j + 1] = r.y;
   }
-  const int o = bmn_off(k, s0);
-  *reinterpret_cast<uint4 *>(Bh + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-  *reinterpret_cast<uint4 *>(Bl + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  *reinterpret_cast<uint4 *>(Bh + bmn_off(k, s0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  const int o8 = b8_off(k, s0);
+  *reinterpret_cast<uint2 *>(B8 + o8) =
+      make_uint2(e5m2x4(v[0], v[1], v[2], v[3]), e5m2x4(v[4], v[5], v[6], v[7]));
+  *reinterpret_cast<uint2 *>(B8l + o8) =
+      make_uint2(e5m2x4(lo[0], lo[1], lo[2], lo[3]), e5m2x4(lo[4], lo[5], lo[6], lo[7]));
 }
 
 // 32 consecutive 32-bit columns of this warp's TMEM lanes from registers
@@ -638,12 +670,24 @@ __device__ __forceinline__ void tmem_st32(unsigned taddr, const unsigned *r) {
       : "memory");
 }
 
-// D (tmem) += A (tmem) x B (smem descriptor)
-__device__ __forceinline__ void mma_tmem_a(unsigned tmem_d, unsigned tmem_a,
-                                           unsigned long long b, unsigned idesc, int accum) {
+// 16 consecutive 32-bit columns of this warp's TMEM lanes from registers
+__device__ __forceinline__ void tmem_st16(unsigned taddr, const unsigned *r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+}
+
+// D (tmem) += A (tmem) x B (smem descriptor), 8-bit operands (K = 32); the format fields of the
+// instruction descriptor read as E5M2 for this kind
+__device__ __forceinline__ void mma_f8_tmem_a(unsigned tmem_d, unsigned tmem_a,
+                                              unsigned long long b, unsigned idesc, int accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
       "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum));
 }
 
@@ -689,28 +733,32 @@ __global__ void __launch_bounds__(kSGT * kSG, 1)
   tc_fence_after();
   const unsigned tbase = S.tmem_base;
   if (warp < 4) {
-    // warp w writes the low parts of rows 32w..32w+31 (row o = lane o): 32 columns of W1
-    // (64 inputs) and 64 of each hidden layer, two BF16 per column (the lower input first)
+    // warp w writes rows 32w..32w+31 (row o = lane o) of the E5M2 copies of W and of W_lo:
+    // 16 columns for W1 (64 inputs), 32 for each hidden layer, four inputs per column
     const unsigned trow = tbase + ((unsigned)(warp * 32) << 16);
     const int o = warp * 32 + lane;
-    unsigned r[32];
-    auto lo2 = [](float a, float b) {
-      const float ha = __bfloat162float(__float2bfloat16_rn(a));
-      const float hb = __bfloat162float(__float2bfloat16_rn(b));
-      return pack16<false>(a - ha, b - hb);
-    };
+    auto lo = [](float a) { return a - __bfloat162float(__float2bfloat16_rn(a)); };
+    for (int l = 0; l < 4; l++) {
+      const int K = l == 0 ? kMlpF : kMlpW;
+      const float *w = Wp.W[l] + (size_t)o * K;
+      unsigned rh[32], rl[32];
 #pragma unroll
-    for (int c = 0; c < 32; c++) r[c] = lo2(Wp.W[0][o * kMlpF + 2 * c], Wp.W[0][o * kMlpF + 2 * c + 1]);
-    tmem_st32(trow + kColWlo1, r);
-    for (int l = 0; l < 3; l++)
-      for (int hh = 0; hh < 2; hh++) {
-#pragma unroll
-        for (int c = 0; c < 32; c++) {
-          const int k = 64 * hh + 2 * c;
-          r[c] = lo2(Wp.W[l + 1][o * kMlpW + k], Wp.W[l + 1][o * kMlpW + k + 1]);
+      for (int c = 0; c < 32; c++) {
+        if (4 * c < K) {
+          rh[c] = e5m2x4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+          rl[c] = e5m2x4(lo(w[4 * c]), lo(w[4 * c + 1]), lo(w[4 * c + 2]), lo(w[4 * c + 3]));
+        } else {
+          rh[c] = rl[c] = 0u;
         }
-        tmem_st32(trow + kColWloH + 64 * l + 32 * hh, r);
       }
+      if (l == 0) {
+        tmem_st16(trow + col8(kColW8, 0), rh);
+        tmem_st16(trow + col8(kColWlo8, 0), rl);
+      } else {
+        tmem_st32(trow + col8(kColW8, l), rh);
+        tmem_st32(trow + col8(kColWlo8, l), rl);
+      }
+    }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
@@ -720,8 +768,11 @@ __global__ void __launch_bounds__(kSGT * kSG, 1)
   const unsigned tD = tbase + kColSplitD + 64 * tg;                   // this group's accumulator
   const unsigned tDl = tD + ((unsigned)(q * 32) << 16) + 32 * hs;     // this thread's 32 columns
   const unsigned mbar = smem_u32(&S.mbar[tg]);
-  h16 *Bh = S.B[tg][0], *Bl = S.B[tg][1];
-  const unsigned aBh = smem_u32(Bh), aBl = smem_u32(Bl);
+  // the group's operands: a_hi (BF16) and, in the second 16 KB, E5M2 copies of a and a_lo
+  h16 *Bh = S.B[tg][0];
+  unsigned char *B8 = reinterpret_cast<unsigned char *>(S.B[tg][1]);
+  unsigned char *B8l = B8 + kMlpW * kSN;
+  const unsigned aBh = smem_u32(Bh), aB8 = smem_u32(B8), aB8l = smem_u32(B8l);
   // after layer 4 the group's two buffers (contiguous) hold the FP32 activations
   // [feature][sample ^ (feature & 31)]
   float *h4 = reinterpret_cast<float *>(Bh);
@@ -777,8 +828,8 @@ __global__ void __launch_bounds__(kSGT * kSG, 1)
         sv[i] = __sinf(a);
         cv[i] = __cosf(a);
       }
-      split_store8(Bh, Bl, j, s0, sv);
-      split_store8(Bh, Bl, 32 + j, s0, cv);
+      split_store8(Bh, B8, B8l, j, s0, sv);
+      split_store8(Bh, B8, B8l, 32 + j, s0, cv);
     }
     proxy_fence();
     tc_fence_before();
@@ -789,14 +840,18 @@ __global__ void __launch_bounds__(kSGT * kSG, 1)
       if (gt == 0) {
         tc_fence_after();
         const unsigned aW = l == 0 ? smem_u32(S.W1) : smem_u32(S.Wh[l - 1]);
-        const unsigned tWlo = tbase + (l == 0 ? kColWlo1 : kColWloH + 64 * (l - 1));
+        const unsigned tW8 = tbase + col8(kColW8, l), tWl8 = tbase + col8(kColWlo8, l);
         const unsigned long long dW = mma_desc(aW, K);
         const unsigned long long dBh = mma_desc_mn(aBh, 128, 1024);
-        const unsigned long long dBl = mma_desc_mn(aBl, 128, 1024);
-        for (int ks = 0; ks < K / 16; ks++) {
-          mma_bf16(tD, dW + 16u * ks, dBh + 128u * ks, idn, ks > 0);       // W_hi a_hi
-          mma_bf16(tD, dW + 16u * ks, dBl + 128u * ks, idn, 1);            // W_hi a_lo
-          mma_tmem_a(tD, tWlo + 8u * ks, dBh + 128u * ks, idn, 1);         // W_lo a_hi
+        // 8-bit MN-major B: 128 B between 16-sample groups, 512 B between feature groups;
+        // one 32-feature K step = 2 KB
+        const unsigned long long dB8 = mma_desc_mn(aB8, 128, 512);
+        const unsigned long long dB8l = mma_desc_mn(aB8l, 128, 512);
+        for (int k2 = 0; k2 < K / 32; k2++) {
+          mma_bf16(tD, dW + 32u * k2, dBh + 256u * k2, idn, k2 > 0);       // W_hi a_hi
+          mma_bf16(tD, dW + 32u * k2 + 16u, dBh + 256u * k2 + 128u, idn, 1);
+          mma_f8_tmem_a(tD, tW8 + 8u * k2, dB8l + 128u * k2, idn, 1);      // W a_lo (E5M2)
+          mma_f8_tmem_a(tD, tWl8 + 8u * k2, dB8 + 128u * k2, idn, 1);      // W_lo a (E5M2)
         }
         mma_commit(mbar);
       }
@@ -831,7 +886,7 @@ __global__ void __launch_bounds__(kSGT * kSG, 1)
         }
         if (l < 3) {
 #pragma unroll
-          for (int c = 0; c < 4; c++) split_store8(Bh, Bl, f, 32 * hs + 8 * c, v + 8 * c);
+          for (int c = 0; c < 4; c++) split_store8(Bh, B8, B8l, f, 32 * hs + 8 * c, v + 8 * c);
         } else {
           // the MMA of this layer has read the buffers: they now hold the FP32 activations
 #pragma unroll
