@@ -631,7 +631,7 @@ int launch_field_chain_adjoint(const rt_grid &g, const rt_geom &geo, const rt_li
                                cudaStream_t stream);
 int pack_cells(MarchParams &P, void *buf, cudaStream_t stream);
 int launch_count(const MarchParams &P, unsigned long long *count, cudaStream_t stream);
-void lane_layout(int nch, int *lpr, int *cpl);
+void lane_layout(int nch, bool dense, int *lpr, int *cpl);
 int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target, float *cube_out,
                    const rt_grads &G, cudaStream_t stream, float4 *dmod = nullptr,
                    unsigned *dmax = nullptr);
