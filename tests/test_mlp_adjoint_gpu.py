@@ -32,7 +32,9 @@ def net_weights(seed=7):
 
 
 @pytest.mark.parametrize("prec", ["f16", "bf16"])
-@pytest.mark.parametrize("n", [1, 300, 5000, 40001])
+# sizes around the backward's 64-sample tiles and a CTA's pair of tile groups, and one with
+# several tiles per group (both groups accumulating into the same weight gradients)
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 128, 129, 300, 5000, 40001])
 def test_mlp_backward_vs_oracle(rt, orc, prec, n):
     """Random inputs (ragged last tile, a single input, several tiles per CTA) and random
     output gradients spanning a wide dynamic range (the kernel scales them to FP16 range)."""
