@@ -58,8 +58,8 @@ MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 4)
 # dram__bytes_write of march_fwd_kernel<8,8,0>; the cube stays in L2 at the end of the launch)
 FWD_DRAM_BYTES = 3_331_840 + 30_464
 # DRAM bytes (read + write) of one fused-adjoint launch on the same workload (ncu capture of
-# march_adj_kernel<8, 8, 1>)
-ADJ_DRAM_BYTES = 44_500_736 + 444_428_544
+# march_adj_kernel<8, 8, 5> with 32-sample segments and a 16 MiB grid-copy budget)
+ADJ_DRAM_BYTES = 32_708_096 + 104_248_576
 N_SM = 148
 SM_MAX_MHZ = 2032.0
 

@@ -217,11 +217,11 @@ int rt_render_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *
  * FP32 rounding). Gradients w.r.t. every node of T, n_H2, v_turb and both surfaces
  * overwrite the FP64 arrays; with a rotation field (fields->vphi_kms) so does its gradient
  * (grads->dvphi, required then), through v_los = v_phi sin i x / r + v_sys. The call allocates and frees one device scratch buffer on
- * `stream` (stream-ordered) holding the optical-depth checkpoints (every 64
- * samples), the reverse march's per-warp record of the 64-sample segment it is reversing
+ * `stream` (stream-ordered) holding the optical-depth checkpoints (every 32
+ * samples), the reverse march's per-warp record of the 32-sample segment it is reversing
  * (recomputed from the segment's checkpoint: batch optical depths, and the physics and local
  * derivatives of each sample, 64 bytes per sample, 80 with a network) and up to 32 replicated FP32
- * copies of the node gradients (at most 32 MiB, {dT, dn, dvt, dvphi} interleaved per node) plus up
+ * copies of the node gradients (at most 16 MiB, {dT, dn, dvt, dvphi} interleaved per node) plus up
  * to 128 of the surface gradients: each block of the kernel reduces into one copy, and the
  * copies are summed in FP64, in a fixed order, into the outputs at the end. Atomics on one
  * address are applied one after another, and without the copies the surface entries, which
@@ -242,7 +242,7 @@ int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geo
  * `work` is a DEVICE pointer to four unsigned 64-bit counters, overwritten (stream-ordered):
  *   [0] samples whose physics found gas (opacity > 0) in the forward pass,
  *   [1] sample-channel evaluations computed in the forward pass (after the channel window),
- *   [2] evaluations computed where each 64-sample segment's optical depths are recomputed,
+ *   [2] evaluations computed where each 32-sample segment's optical depths are recomputed,
  *   [3] evaluations computed in the reverse pass.
  */
 int rt_render_adjoint_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
