@@ -359,7 +359,10 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
   constexpr int NG = 32 / R;           // work units whose setups are computed together
   constexpr int NB = kSeg / LPR;       // batches per segment
   __shared__ __align__(16) float s_tab[kTabSeg * 4];
-  __shared__ float4 s_ph[WPB][32];
+  // per ray LPR records plus one float4 of padding, so that the rays of a warp (reading one
+  // record each, broadcast to their lanes) fall on different banks
+  constexpr int kPhStride = LPR + 1;
+  __shared__ float4 s_ph[WPB][(32 / LPR) * kPhStride];
   __shared__ Ray s_ray[WPB][32];
   // per-sample channel sums of each lane, [sample t][lane ^ (t & 7)] (conflict-free both ways)
   __shared__ float4 s_part[WPB][LPR][32];
@@ -446,7 +449,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
           wc_fwd += (unsigned long long)__popc(act2) * 2 * LPR * 32;
         }
         if (!act) continue;
-        ph[lane] = mine;
+        ph[rr * kPhStride + q] = mine;
         __syncwarp();
         // channel pairs outside, the batch's samples inside: one warp-uniform window test per
         // pair and batch
@@ -455,7 +458,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
           if (!(act2 & (1u << m))) continue;  // warp-uniform
 #pragma unroll
           for (int t = 0; t < LPR; t++) {
-            const float4 p = ph[rr * LPR + t];
+            const float4 p = ph[rr * kPhStride + t];
             const float dc = fmaf(vq, p.z, -p.y), db = __fmul_rn(dvs, p.z);
             const float2 kd2 = make_float2(p.x, p.x), S2 = make_float2(p.w, p.w);
             const float2 d =
@@ -536,14 +539,14 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
           if (lane == 0) s_act[wib][b] = act;
           if (P.work) wc_rec += (unsigned long long)__popc(act) * LPR * 32;
           if (!act) continue;
-          ph[lane] = mine;
+          ph[rr * kPhStride + q] = mine;
           __syncwarp();
 #pragma unroll
           for (int j = 0; j < CPL; j++) {
             if (!(act & (1u << j))) continue;  // warp-uniform, once per block and batch
 #pragma unroll
             for (int t = 0; t < LPR; t++) {
-              const float4 p = ph[rr * LPR + t];
+              const float4 p = ph[rr * kPhStride + t];
               // the same roundings as the reverse pass's packed d (db rounded on its own, then
               // one fma): the reverse subtracts its own increments from these sums, and any
               // difference in the last bit (a contracted dvs * p.z, say) leaves optical depth
@@ -567,7 +570,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
           if (!__any_sync(0xffffffffu, mine.z > 0.0f)) continue;  // no gas in the batch
           const unsigned act = s_act[wib][b];
           const float Sbefore = Snext;
-          ph[lane] = mine;
+          ph[rr * kPhStride + q] = mine;
           // channel slots in pairs (2m, 2m+1) for the packed two-lane FP32 instructions; a
           // pair is marched when either slot's block is in the window
           unsigned act2 = 0;
@@ -622,7 +625,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
             constexpr int m = decltype(M)::value;
 #pragma unroll 1
             for (int t = LPR - 1; t >= 0; t--) {
-              const float4 p = ph[rr * LPR + t];
+              const float4 p = ph[rr * kPhStride + t];
               const bool gas = p.z > 0.0f;
               const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
               Snext = gas ? p.w : Snext;
@@ -634,7 +637,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
             constexpr int m = decltype(M)::value;
 #pragma unroll 1
             for (int t = LPR - 1; t >= 0; t--) {
-              const float4 p = ph[rr * LPR + t];
+              const float4 p = ph[rr * kPhStride + t];
               const bool gas = p.z > 0.0f;
               const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
               Snext = gas ? p.w : Snext;
@@ -661,7 +664,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
           } else {
 #pragma unroll 1
             for (int t = LPR - 1; t >= 0; t--) {
-              const float4 p = ph[rr * LPR + t];
+              const float4 p = ph[rr * kPhStride + t];
               const bool gas = p.z > 0.0f;
               const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
               Snext = gas ? p.w : Snext;

@@ -54,7 +54,10 @@ __global__ void __launch_bounds__(kWarps * 32, (MODE == 2 || MODE == 3) ? 4 : (C
   constexpr int H = CPL / 2;   // channel pairs per lane = channel blocks
   __shared__ __align__(16) float s_tab[kTabSeg * 4];
   // per sample: {-kd, -kd, S, S} and {b, b, -a, -a} (pairs ready for the packed arithmetic)
-  __shared__ float4 s_ph[kWarps][2][64];
+  // per ray 2 LPR records plus one float4 of padding, so that the rays of a warp (reading one
+  // record each, broadcast to their lanes) fall on different banks
+  constexpr int kPhStride = 2 * LPR + 1;
+  __shared__ float4 s_ph[kWarps][2][(32 / LPR) * kPhStride];
   __shared__ Ray s_ray[kWarps][32];
   for (int i = threadIdx.x; i < kTabSeg * 4; i += blockDim.x) s_tab[i] = P.tab[i];
   __syncthreads();
@@ -154,10 +157,10 @@ __global__ void __launch_bounds__(kWarps * 32, (MODE == 2 || MODE == 3) ? 4 : (C
           wc_eval += (unsigned long long)__popc(act) * 128 * LPR;
         }
         if (!act) continue;  // no channel of any ray reached in this batch
-        ph0[rr * 2 * LPR + q] = make_float4(-mine.x, -mine.x, mine.w, mine.w);
-        ph1[rr * 2 * LPR + q] = make_float4(mine.z, mine.z, -mine.y, -mine.y);
-        ph0[rr * 2 * LPR + LPR + q] = make_float4(-mine2.x, -mine2.x, mine2.w, mine2.w);
-        ph1[rr * 2 * LPR + LPR + q] = make_float4(mine2.z, mine2.z, -mine2.y, -mine2.y);
+        ph0[rr * kPhStride + q] = make_float4(-mine.x, -mine.x, mine.w, mine.w);
+        ph1[rr * kPhStride + q] = make_float4(mine.z, mine.z, -mine.y, -mine.y);
+        ph0[rr * kPhStride + LPR + q] = make_float4(-mine2.x, -mine2.x, mine2.w, mine2.w);
+        ph1[rr * kPhStride + LPR + q] = make_float4(mine2.z, mine2.z, -mine2.y, -mine2.y);
         __syncwarp();
 #pragma unroll
         for (int m = 0; m < H; m++) {
@@ -165,8 +168,8 @@ __global__ void __launch_bounds__(kWarps * 32, (MODE == 2 || MODE == 3) ? 4 : (C
           // every sample of the batch in order; samples without gas are exact no-ops
 #pragma unroll
           for (int t = 0; t < 2 * LPR; t++) {
-            const float4 p0 = ph0[rr * 2 * LPR + t];
-            const float4 p1 = ph1[rr * 2 * LPR + t];
+            const float4 p0 = ph0[rr * kPhStride + t];
+            const float4 p1 = ph1[rr * kPhStride + t];
             const float2 nkd = make_float2(p0.x, p0.y), S = make_float2(p0.z, p0.w);
             const float2 b = make_float2(p1.x, p1.y), na = make_float2(p1.z, p1.w);
             const float2 d = __ffma2_rn(vp[m], b, na);  // (v_c - v_los) / alpha (scaled)
