@@ -55,11 +55,11 @@ except (OSError, ValueError):
 # FLOPs of one network evaluation as the method defines it: 2 x (64x128 + 3x128x128 + 128x4)
 MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 4)
 # DRAM bytes of one forward launch on the observation-scale workload (ncu, dram__bytes_read +
-# dram__bytes_write of march_fwd_kernel<8,8,0>; the cube stays in L2 at the end of the launch)
-FWD_DRAM_BYTES = 3_331_840 + 30_464
+# dram__bytes_write of march_fwd_kernel<8,8,4>; the cube stays in L2 at the end of the launch)
+FWD_DRAM_BYTES = 3_329_280 + 29_184
 # DRAM bytes (read + write) of one fused-adjoint launch on the same workload (ncu capture of
 # march_adj_kernel<8, 8, 5> with 32-sample segments and a 16 MiB grid-copy budget)
-ADJ_DRAM_BYTES = 32_708_096 + 104_248_576
+ADJ_DRAM_BYTES = 32_533_504 + 104_930_560
 N_SM = 148
 SM_MAX_MHZ = 2032.0
 
