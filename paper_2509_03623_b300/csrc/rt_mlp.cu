@@ -681,6 +681,32 @@ __device__ __forceinline__ void tmem_st16(unsigned taddr, const unsigned *r) {
       : "memory");
 }
 
+// 16 values of feature k at samples s0..s0+15 (s0 multiple of 16): the BF16 high part into Bh
+// (two rows of 8 samples) and E5M2 copies of the value and of its low part into B8 and B8l
+// (one full 16-byte core-matrix row each, so the lanes of a warp store whole rows)
+__device__ __forceinline__ void split_store16(h16 *Bh, unsigned char *B8, unsigned char *B8l,
+                                              int k, int s0, const float *v) {
+  unsigned hi[8];
+  float lo[16];
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    hi[j] = pack16<false>(v[2 * j], v[2 * j + 1]);
+    const float2 r = __ffma2_rn(bf2f(hi[j]), make_float2(-1.0f, -1.0f),
+                                make_float2(v[2 * j], v[2 * j + 1]));  // exact residual
+    lo[2 * j] = r.x;
+    lo[2 * j + 1] = r.y;
+  }
+  *reinterpret_cast<uint4 *>(Bh + bmn_off(k, s0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  *reinterpret_cast<uint4 *>(Bh + bmn_off(k, s0 + 8)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+  const int o8 = b8_off(k, s0);
+  *reinterpret_cast<uint4 *>(B8 + o8) =
+      make_uint4(e5m2x4(v[0], v[1], v[2], v[3]), e5m2x4(v[4], v[5], v[6], v[7]),
+                 e5m2x4(v[8], v[9], v[10], v[11]), e5m2x4(v[12], v[13], v[14], v[15]));
+  *reinterpret_cast<uint4 *>(B8l + o8) =
+      make_uint4(e5m2x4(lo[0], lo[1], lo[2], lo[3]), e5m2x4(lo[4], lo[5], lo[6], lo[7]),
+                 e5m2x4(lo[8], lo[9], lo[10], lo[11]), e5m2x4(lo[12], lo[13], lo[14], lo[15]));
+}
+
 // D (tmem) += A (tmem) x B (smem descriptor), 8-bit operands (K = 32); the format fields of the
 // instruction descriptor read as E5M2 for this kind
 __device__ __forceinline__ void mma_f8_tmem_a(unsigned tmem_d, unsigned tmem_a,
@@ -886,7 +912,7 @@ __global__ void __launch_bounds__(kSGT * kSG, 1)
         }
         if (l < 3) {
 #pragma unroll
-          for (int c = 0; c < 4; c++) split_store8(Bh, B8, B8l, f, 32 * hs + 8 * c, v + 8 * c);
+          for (int c = 0; c < 2; c++) split_store16(Bh, B8, B8l, f, 32 * hs + 16 * c, v + 16 * c);
         } else {
           // the MMA of this layer has read the buffers: they now hold the FP32 activations
 #pragma unroll
