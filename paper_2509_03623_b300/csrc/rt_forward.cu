@@ -88,22 +88,9 @@ __global__ void __launch_bounds__(kWarps * 32, (MODE == 2 || MODE == 3) ? 4 : (C
   // evaluations computed (every lane of an active block, LPR samples x 2 channels each)
   unsigned long long wc_phys = 0, wc_eval = 0;
 
-  // Work units u = gw, gw + W, gw + 2W, ... (interleaved over the grid for balance); the
-  // setups of G units (32 rays) are computed at once, one ray per lane.
-  for (long long u0 = (long long)blockIdx.x * kWarps + wib; u0 < nunits; u0 += W * G) {
-    {
-      long long pix = (u0 + (long long)(lane / R) * W) * R + lane % R;
-      bool act = pix < npix;
-      Ray s = setup_ray(P, act ? (int)(pix % P.nx) : 0, act ? (int)(pix / P.nx) : 0, act);
-      __syncwarp();
-      s_ray[wib][lane] = s;
-      __syncwarp();
-    }
-    for (int g = 0; g < G; g++) {
-      const long long u = u0 + (long long)g * W;
-      if (u >= nunits) break;
+  // One work unit: the R rays of a warp (pixels u R .. u R + R - 1), marched to the cube.
+  auto march_unit = [&](long long u, Ray ray) __attribute__((always_inline)) {
       const long long pix = u * R + rr;
-      const Ray ray = s_ray[wib][g * R + rr];
       // negated optical depth: batch part and base; transmittance; intensity
       float2 nl[H], nb[H], Tr[H], I[H];
 #pragma unroll
@@ -197,6 +184,37 @@ __global__ void __launch_bounds__(kWarps * 32, (MODE == 2 || MODE == 3) ? 4 : (C
           if (c0 < P.nch) cube[(long long)c0 * npix + pix] = fmaf(I[m].x, P.out_scale, P.I0 * Tr[m].x);
           if (c1 < P.nch) cube[(long long)c1 * npix + pix] = fmaf(I[m].y, P.out_scale, P.I0 * Tr[m].y);
         }
+      }
+  };
+  if (P.unit_ctr) {
+    // Dynamic: a warp takes one unit at a time from the launch-wide counter, in pixel order,
+    // so warps that drew short rays take more units, and the last units handed out are the
+    // bottom rows of the image, which cross little gas (a short tail); the ray setups come
+    // from the pre-pass.
+    for (;;) {
+      unsigned uc = 0;
+      if (lane == 0) uc = atomicAdd(P.unit_ctr, 1u);
+      const long long u = (long long)__shfl_sync(0xffffffffu, uc, 0);
+      if (u >= nunits) break;
+      const long long pix = u * R + rr;
+      march_unit(u, P.rays[pix < npix ? pix : npix - 1]);  // a ray past the end stores nothing
+    }
+  } else {
+    // Static: units u = gw, gw + W, gw + 2W, ... (interleaved over the grid); the setups of G
+    // units (32 rays) are computed at once, one ray per lane.
+    for (long long u0 = (long long)blockIdx.x * kWarps + wib; u0 < nunits; u0 += W * G) {
+      {
+        long long pix = (u0 + (long long)(lane / R) * W) * R + lane % R;
+        bool act = pix < npix;
+        Ray s = setup_ray(P, act ? (int)(pix % P.nx) : 0, act ? (int)(pix / P.nx) : 0, act);
+        __syncwarp();
+        s_ray[wib][lane] = s;
+        __syncwarp();
+      }
+      for (int g = 0; g < G; g++) {
+        const long long u = u0 + (long long)g * W;
+        if (u >= nunits) break;
+        march_unit(u, s_ray[wib][g * R + rr]);
       }
     }
   }
@@ -317,20 +335,32 @@ int pack_cells(MarchParams &P, void *buf, cudaStream_t stream) {
 
 static int launch_march(const MarchParams &P, float *cube, cudaStream_t stream);
 
-// Forward march; packs the corner quads first (into a stream-ordered allocation freed after
-// the launch) where they pay.
+// Forward march. One stream-ordered allocation, freed after the launch, holds the corner
+// quads where they pay (packed first), the ray setups of every pixel (a pre-pass) and the
+// counter of the march's dynamic work distribution (zeroed first).
 int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream) {
   long long npix = (long long)P.nx * P.ny;
   if (npix == 0 || P.nch == 0) return RT_OK;
-  const size_t cb = P.cell ? 0 : cell_bytes(P);
-  if (!cb) return launch_march(P, cube, stream);
-  void *buf = nullptr;
-  cudaError_t e = stream_alloc((void **)&buf, cb, stream);
+  const size_t cb = (P.cell ? 0 : cell_bytes(P) + 255) & ~(size_t)255;
+  const size_t rb = (ray_buffer_bytes(npix) + 255) & ~(size_t)255;
+  char *buf = nullptr;
+  cudaError_t e = stream_alloc((void **)&buf, cb + rb + 256, stream);
   if (e != cudaSuccess)
-    return set_error(RT_ENOMEM, "corner quads (%zu bytes): %s", cb, cudaGetErrorString(e));
+    return set_error(RT_ENOMEM, "forward scratch (%zu bytes): %s", cb + rb + 256,
+                     cudaGetErrorString(e));
   MarchParams Q = P;  // passed by value to the kernel: the copy only lives until the launch
-  int rc = pack_cells(Q, buf, stream);
-  if (rc == RT_OK) rc = launch_march(Q, cube, stream);
+  Ray *rays = reinterpret_cast<Ray *>(buf + cb);
+  unsigned *ctr = reinterpret_cast<unsigned *>(buf + cb + rb);
+  int rc = RT_OK;
+  e = cudaMemsetAsync(ctr, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) rc = set_error(RT_ECUDA, "memset: %s", cudaGetErrorString(e));
+  if (rc == RT_OK && cb) rc = pack_cells(Q, buf, stream);
+  if (rc == RT_OK) rc = launch_rays(Q, rays, stream);
+  if (rc == RT_OK) {
+    Q.rays = rays;
+    Q.unit_ctr = ctr;
+    rc = launch_march(Q, cube, stream);
+  }
   cudaFreeAsync(buf, stream);
   return rc;
 }
@@ -344,6 +374,8 @@ int launch_forward_dense(const MarchParams &P, float *cube, cudaStream_t stream)
   Q.no_window = 1;
   Q.cell = nullptr;
   Q.hcell = nullptr;
+  Q.rays = nullptr;  // static work distribution, ray setups in the kernel
+  Q.unit_ctr = nullptr;
   return launch_march(Q, cube, stream);
 }
 

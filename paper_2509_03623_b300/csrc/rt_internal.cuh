@@ -18,6 +18,8 @@ constexpr float kTabT0 = 0.0f;
 constexpr float kTabInvH = 16.0f;
 constexpr int kTabSeg = kTabN - 1;
 
+struct Ray;
+
 struct MarchParams {
   // grid
   int nr, nz, r_log, hard_edge;
@@ -83,6 +85,12 @@ struct MarchParams {
   // {h_lo(i), h_lo(i+1), h_hi(i), h_hi(i+1)}: four 16-byte loads per sample instead of 16
   // scalar ones. nullptr: the kernels read the node arrays (same values, same rounding).
   const float4 *cell, *hcell;
+  // optional dynamic work distribution of the forward march (nullptr: each warp takes a fixed
+  // interleaved share of the work units and sets up its rays itself): the ray setups of
+  // every pixel from a pre-pass, and a launch-wide counter (zeroed before the launch) from
+  // which warps take work units one at a time
+  const Ray *rays;
+  unsigned *unit_ctr;
   float v[RT_MAX_CH];
   float tab[kTabSeg * 4];
 };
@@ -642,6 +650,8 @@ int check_adjoint_args(const MarchParams &P, const float *dL_dcube, const float 
 int launch_mlp_rays(const rt_mlp *m, const MarchParams &P, float4 *mod, void *ray_buf,
                     void *list_buf, cudaStream_t stream);
 size_t ray_buffer_bytes(long long npix);
+// ray setups of every pixel of P into rays (ray_buffer_bytes(nx ny) bytes)
+int launch_rays(const MarchParams &P, Ray *rays, cudaStream_t stream);
 size_t sample_list_bytes(long long npix, int n_samples);
 int mlp_validate(const rt_mlp *m);
 int mlp_grads_validate(const rt_mlp_grads *g);

@@ -1173,6 +1173,15 @@ int launch_mlp_rays(const rt_mlp *m, const MarchParams &P, float4 *mod, void *ra
 
 size_t ray_buffer_bytes(long long npix) { return (size_t)npix * sizeof(Ray); }
 
+int launch_rays(const MarchParams &P, Ray *rays, cudaStream_t stream) {
+  const long long npix = (long long)P.nx * P.ny;
+  if (npix == 0) return RT_OK;
+  rays_kernel<<<(unsigned)((npix + 127) / 128), 128, 0, stream>>>(P, rays);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "ray setup launch: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
 // Network inputs (rhat, zhat) of every (pixel, sample): [npix][n_samples] float2, (-1, -1)
 // where the sample has no gas.
 __global__ void coords_kernel(const __grid_constant__ MarchParams P, float2 *__restrict__ xy) {
