@@ -103,7 +103,7 @@ typedef struct {
 
 /* Image and spectral sampling. */
 typedef struct {
-  int nx, ny;           /* pixels (0 allowed: nothing to do) */
+  int nx, ny;           /* pixels (0 allowed: nothing to do; nx*ny <= 2^31) */
   double half_fov_au;   /* <= 0: 1.1 r_out */
   int nch;              /* 0..RT_MAX_CH */
   const float *v_kms;   /* HOST [nch] channel velocities */

@@ -356,14 +356,12 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
   constexpr bool ROT = (VAR & 2) != 0;   // a rotation field (gradient with respect to it too)
   constexpr int WPB = adj_wpb<LPR>();
   constexpr int R = 32 / LPR;          // rays per warp
-  constexpr int NG = 32 / R;           // work units whose setups are computed together
   constexpr int NB = kSeg / LPR;       // batches per segment
   __shared__ __align__(16) float s_tab[kTabSeg * 4];
   // per ray LPR records plus one float4 of padding, so that the rays of a warp (reading one
   // record each, broadcast to their lanes) fall on different banks
   constexpr int kPhStride = LPR + 1;
   __shared__ float4 s_ph[WPB][(32 / LPR) * kPhStride];
-  __shared__ Ray s_ray[WPB][32];
   // per-sample channel sums of each lane, [sample t][lane ^ (t & 7)] (conflict-free both ways)
   __shared__ float4 s_part[WPB][LPR][32];
   __shared__ unsigned s_act[WPB][NB];  // window of each batch of the segment being reversed
@@ -374,7 +372,6 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
   const int q = lane % LPR, rr = lane / LPR;
   const long long npix = (long long)P.nx * P.ny;
   const long long nunits = (npix + R - 1) / R;
-  const long long W = (long long)gridDim.x * WPB;
   const long long gw = (long long)blockIdx.x * WPB + wib;
   float *ck = scratch + gw * adj_warp_floats<LPR, CPL>(nseg);  // this warp's checkpoints
   float *bs = ck + (long long)nseg * CPL * 32;                  // and batch starts
@@ -399,21 +396,20 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
   // work counters (only with P.work): samples with gas, evaluations of the three passes
   unsigned long long wc_gas = 0, wc_fwd = 0, wc_rec = 0, wc_rev = 0;
 
-  for (long long u0 = gw; u0 < nunits; u0 += W * NG) {
+  // Dynamic work distribution: each warp takes the next unit (R neighbouring rays) from a
+  // launch-wide counter, in pixel order, until none is left; the lanes set up their own ray
+  // (about 1 % of a unit's work), so a warp that drew short rays simply takes more units and
+  // the launch ends when the work does, not when the unluckiest warp's static share does.
+  for (;;) {
     {
-      long long pix = (u0 + (long long)(lane / R) * W) * R + lane % R;
-      bool act = pix < npix;
-      Ray s = setup_ray(P, act ? (int)(pix % P.nx) : 0, act ? (int)(pix / P.nx) : 0, act);
-      __syncwarp();
-      s_ray[wib][lane] = s;
-      __syncwarp();
-    }
-    for (int gi = 0; gi < NG; gi++) {
-      const long long u = u0 + (long long)gi * W;
+      unsigned uc = 0;
+      if (lane == 0) uc = atomicAdd(P.unit_ctr, 1u);
+      const long long u = (long long)__shfl_sync(0xffffffffu, uc, 0);
       if (u >= nunits) break;
       const long long pix = u * R + rr;
       const bool active = pix < npix;
-      const Ray ray = s_ray[wib][gi * R + rr];
+      const Ray ray =
+          setup_ray(P, active ? (int)(pix % P.nx) : 0, active ? (int)(pix / P.nx) : 0, active);
       // the rays' gas sample ranges (samples outside are exact no-ops), counted from klo;
       // segments and checkpoints are relative to it
       const int nsamp = __reduce_max_sync(0xffffffffu, max(ray.khi - ray.klo + 1, 0));
@@ -808,7 +804,7 @@ static size_t adj_block_bytes(const MarchParams &P) {
 // Scratch of one adjoint launch: the warps' checkpoints, the gradient copies, then the
 // corner quads of the fields (cell_bytes; 0 when the kernel reads the node arrays).
 struct AdjScratch {
-  size_t ck_bytes, g_off, h_off, cell_off, cell_bytes, total;
+  size_t ck_bytes, g_off, h_off, cell_off, cell_bytes, ctr_off, total;
   int kg, kh;
 };
 
@@ -834,7 +830,7 @@ static AdjScratch plan_scratch(const MarchParams &P, long long blocks, size_t ck
   if (avail) {
     // surface copies first (small, and without them every radius serializes), then the
     // corner quads, then grid copies in what is left
-    size_t left = avail > a.ck_bytes ? avail - a.ck_bytes : 0;
+    size_t left = avail > a.ck_bytes + 256 ? avail - a.ck_bytes - 256 : 0;  // (the counter)
     while (kh > 0 && (size_t)kh * hcopy > left / 4) kh /= 2;
     left -= align256((size_t)kh * hcopy);
     if (a.cell_bytes + 256 > left) a.cell_bytes = 0;
@@ -846,7 +842,8 @@ static AdjScratch plan_scratch(const MarchParams &P, long long blocks, size_t ck
   a.g_off = a.ck_bytes;
   a.h_off = a.g_off + align256((size_t)a.kg * gcopy);
   a.cell_off = a.h_off + align256((size_t)a.kh * hcopy);
-  a.total = a.cell_off + a.cell_bytes;
+  a.ctr_off = a.cell_off + a.cell_bytes;  // the work counter of the dynamic distribution
+  a.total = a.ctr_off + 256;
   return a;
 }
 
@@ -869,6 +866,7 @@ static int zero_grads(const MarchParams &P, const rt_grads &G, const AdjScratch 
     if (e == cudaSuccess) e = cudaMemsetAsync(G.dh_hi, 0, nh, stream);
   }
   if (e == cudaSuccess && G.loss) e = cudaMemsetAsync(G.loss, 0, sizeof(double), stream);
+  if (e == cudaSuccess && scratch) e = cudaMemsetAsync(scratch + a.ctr_off, 0, 256, stream);
   if (e != cudaSuccess) return set_error(RT_ECUDA, "gradient memset: %s", cudaGetErrorString(e));
   return RT_OK;
 }
@@ -914,6 +912,8 @@ static int run_adj(const MarchParams &P, const float *dLdc, const float *target,
   // the kernel takes the parameters by value, so the copy pointing at the corner quads only
   // has to live until the launch (on the stack: no host allocation)
   MarchParams Q = P;
+  Q.rays = nullptr;
+  Q.unit_ctr = reinterpret_cast<unsigned *>(scratch + a.ctr_off);
   if (a.cell_bytes) {
     rc = pack_cells(Q, scratch + a.cell_off, stream);
     if (rc != RT_OK) return rc;

@@ -143,6 +143,8 @@ static int check_common(const rt_geom &o, const rt_view &v, const rt_line &l) {
       !is_finite(o.vsys_kms))
     return set_error(RT_EINVAL, "geometry must be finite with mstar >= 0");
   if (v.nx < 0 || v.ny < 0) return set_error(RT_EINVAL, "negative image size");
+  // (the kernels' 32-bit work counters count at most this many rays, plus one per warp)
+  if ((long long)v.nx * v.ny > (1LL << 31)) return set_error(RT_EINVAL, "more than 2^31 pixels");
   if (v.nch < 0 || v.nch > RT_MAX_CH)
     return set_error(RT_EINVAL, "nch must be in [0, %d] (got %d)", RT_MAX_CH, v.nch);
   if (v.nch > 0 && !v.v_kms) return set_error(RT_EINVAL, "null channel velocities");
