@@ -60,6 +60,9 @@ __global__ void __launch_bounds__(kWarps * 32, (MODE == 2 || MODE == 3) ? 4 : (C
   __shared__ float4 s_ph[kWarps][2][(32 / LPR) * kPhStride];
   __shared__ Ray s_ray[kWarps][32];
   for (int i = threadIdx.x; i < kTabSeg * 4; i += blockDim.x) s_tab[i] = P.tab[i];
+  // launched as the prep kernel's programmatic dependent: the ray setups, the counter and the
+  // corner quads are complete and visible after this (a no-op in an ordinary launch)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
 
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -265,7 +268,18 @@ static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
   long long need = (units + kWarps - 1) / kWarps;
   long long cap = resident_blocks((const void *)kern, kWarps * 32);
   long long blocks = need < cap ? need : cap;
-  kern<<<(unsigned)blocks, kWarps * 32, 0, stream>>>(P, cube);
+  // the dynamic march follows its prep kernel as a programmatic dependent launch
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(kWarps * 32);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = P.unit_ctr ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, P, cube);
 }
 
 // Channels per lane (4, or 8 from 32 channels up) and lanes per ray (power of two). Without
@@ -283,14 +297,18 @@ void lane_layout(int nch, bool dense, int *lpr, int *cpl) {
 // Corner quads of the node fields (MarchParams::cell, hcell), rebuilt from the caller's
 // arrays before every launch that uses them: one thread per cell gathers the four nodes of
 // each field that the cell's bilinear interpolation reads.
-__global__ void pack_cells_kernel(const float *__restrict__ T, const float *__restrict__ n,
-                                  const float *__restrict__ vt, const float *__restrict__ hlo,
-                                  const float *__restrict__ hhi,
-                                  const float *__restrict__ vphi, int nr, int nz,
-                                  float4 *__restrict__ cell, float4 *__restrict__ hcell) {
+// Cells first, first + stride, ... of the grid.
+__device__ __forceinline__ void pack_cells_from(const float *__restrict__ T,
+                                                const float *__restrict__ n,
+                                                const float *__restrict__ vt,
+                                                const float *__restrict__ hlo,
+                                                const float *__restrict__ hhi,
+                                                const float *__restrict__ vphi, int nr, int nz,
+                                                float4 *__restrict__ cell,
+                                                float4 *__restrict__ hcell, long long first,
+                                                long long stride) {
   const long long m = (long long)(nr - 1) * (nz - 1);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = first; i < m; i += stride) {
     const int j = (int)(i / (nr - 1)), r = (int)(i - (long long)j * (nr - 1));
     const long long b = (long long)j * nr + r;  // node (r, j); the cell's nodes end at b+nr+1
     const int nq = vphi ? 4 : 3;
@@ -300,6 +318,37 @@ __global__ void pack_cells_kernel(const float *__restrict__ T, const float *__re
     cq[2] = make_float4(vt[b], vt[b + 1], vt[b + nr], vt[b + nr + 1]);
     if (vphi) cq[3] = make_float4(vphi[b], vphi[b + 1], vphi[b + nr], vphi[b + nr + 1]);
     if (j == 0) hcell[r] = make_float4(hlo[r], hlo[r + 1], hhi[r], hhi[r + 1]);
+  }
+}
+
+__global__ void pack_cells_kernel(const float *__restrict__ T, const float *__restrict__ n,
+                                  const float *__restrict__ vt, const float *__restrict__ hlo,
+                                  const float *__restrict__ hhi,
+                                  const float *__restrict__ vphi, int nr, int nz,
+                                  float4 *__restrict__ cell, float4 *__restrict__ hcell) {
+  pack_cells_from(T, n, vt, hlo, hhi, vphi, nr, nz, cell, hcell,
+                  (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                  (long long)gridDim.x * blockDim.x);
+}
+
+// Everything the dynamic forward march reads besides the caller's arrays, in one launch: the
+// ray setups of every pixel (blocks below ray_blocks, one thread per ray), the zeroed work
+// counter and, with cell != nullptr, the corner quads (the other blocks). The march is
+// launched as its programmatic dependent: its blocks start as this grid's last blocks are
+// scheduled, stage their tables, and wait for this grid to finish before they read any of it.
+__global__ void march_prep_kernel(const __grid_constant__ MarchParams P, Ray *__restrict__ rays,
+                                  unsigned *__restrict__ ctr, unsigned ray_blocks,
+                                  float4 *__restrict__ cell, float4 *__restrict__ hcell) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (blockIdx.x < ray_blocks) {
+    const long long npix = (long long)P.nx * P.ny;
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix == 0) *ctr = 0u;
+    if (pix < npix) rays[pix] = setup_ray(P, (int)(pix % P.nx), (int)(pix / P.nx), true);
+  } else if (cell) {
+    pack_cells_from(P.T, P.n, P.vt, P.hlo, P.hhi, P.vphi, P.nr, P.nz, cell, hcell,
+                    (long long)(blockIdx.x - ray_blocks) * blockDim.x + threadIdx.x,
+                    (long long)(gridDim.x - ray_blocks) * blockDim.x);
   }
 }
 
@@ -351,12 +400,25 @@ int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream) {
   MarchParams Q = P;  // passed by value to the kernel: the copy only lives until the launch
   Ray *rays = reinterpret_cast<Ray *>(buf + cb);
   unsigned *ctr = reinterpret_cast<unsigned *>(buf + cb + rb);
+  float4 *cell = nullptr, *hcell = nullptr;
+  const long long cells = (long long)(P.nr - 1) * (P.nz - 1);
+  if (cb) {
+    cell = reinterpret_cast<float4 *>(buf);
+    hcell = cell + (P.vphi ? 4 : 3) * cells;
+  }
+  const long long ray_blocks = (npix + 255) / 256;
+  long long cell_blocks = cb ? (cells + 255) / 256 : 0;
+  if (cell_blocks > 4096) cell_blocks = 4096;
+  march_prep_kernel<<<(unsigned)(ray_blocks + cell_blocks), 256, 0, stream>>>(
+      P, rays, ctr, (unsigned)ray_blocks, cell, hcell);
   int rc = RT_OK;
-  e = cudaMemsetAsync(ctr, 0, sizeof(unsigned), stream);
-  if (e != cudaSuccess) rc = set_error(RT_ECUDA, "memset: %s", cudaGetErrorString(e));
-  if (rc == RT_OK && cb) rc = pack_cells(Q, buf, stream);
-  if (rc == RT_OK) rc = launch_rays(Q, rays, stream);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) rc = set_error(RT_ECUDA, "forward prep launch: %s", cudaGetErrorString(e));
   if (rc == RT_OK) {
+    if (cb) {
+      Q.cell = cell;
+      Q.hcell = hcell;
+    }
     Q.rays = rays;
     Q.unit_ctr = ctr;
     rc = launch_march(Q, cube, stream);
