@@ -683,6 +683,21 @@ int rt_server_destroy(rt_server *s);
 int rt_pipe_peak(int op, int iters, double *per_s_sm, double *ms, double *counter_mhz,
                  void *stream);
 
+/*
+ * rt_kernel_timing / rt_kernel_time -- device time of the forward march kernel alone
+ * (measurement support; no counterpart in the paper). With rt_kernel_timing(1), every forward
+ * render (rt_render and the neural-field and served forwards) records a pair of CUDA events
+ * on its stream around the launch of the march kernel; the march then starts after its prep
+ * kernel (ray setups, corner quads) instead of overlapping its launch with it, so timed calls
+ * can be a few microseconds slower. rt_kernel_time synchronises on the recorded events and
+ * returns the summed milliseconds and the number of timed launches since the last read (or
+ * since timing was switched on), then forgets them. rt_kernel_timing(0) stops recording and
+ * drops unread pairs. Process-wide; at most 4096 pairs are kept (later launches are not
+ * timed). Returns RT_OK, RT_EINVAL (null argument) or RT_ECUDA.
+ */
+int rt_kernel_timing(int on);
+int rt_kernel_time(double *total_ms, int *launches);
+
 /* Message for the last error on this thread ("" if none). */
 const char *rt_last_error(void);
 

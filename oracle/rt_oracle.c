@@ -159,7 +159,10 @@ static int chord(const orc_problem *p, const double P0[3], const double om[3], d
   double b = 2.0 * (P0[0] * om[0] + P0[1] * om[1]);
   double c = P0[0] * P0[0] + P0[1] * P0[1] - R * R;
   if (a > 0.0) {
-    double disc = b * b - 4.0 * a * c;
+    /* b^2 - 4ac; for a ray of constant x (om[0] = 0, every view of the disk) it equals
+       4a (R - x)(R + x), evaluated so: the difference of squares loses the chords of rays
+       that graze the wall */
+    double disc = om[0] == 0.0 ? 4.0 * a * ((R - P0[0]) * (R + P0[0])) : b * b - 4.0 * a * c;
     if (disc < 0.0) return 0;
     double sq = sqrt(disc);
     lo = fmax(lo, (-b - sq) / (2.0 * a));

@@ -183,6 +183,10 @@ def lib():
             L.rt_pipe_peak.argtypes = [C.c_int, C.c_int, P(C.c_double), P(C.c_double),
                                        P(C.c_double), C.c_void_p]
             L.rt_pipe_peak.restype = C.c_int
+            L.rt_kernel_timing.argtypes = [C.c_int]
+            L.rt_kernel_timing.restype = C.c_int
+            L.rt_kernel_time.argtypes = [P(C.c_double), P(C.c_int)]
+            L.rt_kernel_time.restype = C.c_int
             L.rt_mlp_status.argtypes = [P(C.c_int)]
             L.rt_mlp_status.restype = C.c_int
             L.rt_last_error.restype = C.c_char_p
@@ -770,6 +774,19 @@ def rt_pipe_peak(op: str, iters: int = 8192, stream=None) -> dict:
     check(lib().rt_pipe_peak(PIPE_OPS[op], int(iters), C.byref(r), C.byref(ms), C.byref(mhz),
                              stream_handle(stream)))
     return {"per_s_sm": r.value, "ms": ms.value, "counter_mhz": mhz.value}
+
+
+def rt_kernel_timing(on: bool) -> None:
+    """Switch the CUDA-event timing of forward march launches on or off (rt_kernel_timing)."""
+    check(lib().rt_kernel_timing(1 if on else 0))
+
+
+def rt_kernel_time() -> tuple:
+    """Summed milliseconds and count of the march launches timed since the last read
+    (rt_kernel_time)."""
+    ms, n = C.c_double(), C.c_int()
+    check(lib().rt_kernel_time(C.byref(ms), C.byref(n)))
+    return ms.value, n.value
 
 
 def rt_mlp_status() -> int:

@@ -196,6 +196,29 @@ static void fill_common(const rt_geom &o, const rt_view &v, const rt_line &l, do
   int kb = 0;
   while ((1LL << kb) < (long long)v.n_samples) kb++;  // bits of the largest sample index
   P->step_bits = 24 - kb;
+  // double-float copies for the FP32 ray setup of the disk (pixel centres (i + 1/2 - n/2)
+  // are exact in FP32 below 2^22 pixels a side)
+  auto f2 = [](double d) {
+    F2 r;
+    r.hi = (float)d;
+    r.lo = (float)(d - (double)r.hi);
+    return r;
+  };
+  P->f_px = f2(P->px);
+  P->f_py = f2(P->py);
+  P->f_cos_pa = f2(P->cos_pa);
+  P->f_sin_pa = f2(P->sin_pa);
+  P->f_cos_i = f2(P->cos_i);
+  P->f_sin_i = f2(P->sin_i);
+  P->f_H = f2(P->H_cyl);
+  P->f_R = f2(P->R_cyl);
+  P->f_R2 = f2(P->R_cyl * P->R_cyl);
+  P->f_4a = f2(4.0 * P->sin_i * P->sin_i);
+  P->f_inv_wz = f2(P->inv_wz);
+  P->f_inv_2a = f2(P->inv_2a);
+  P->f_inv_ns = f2(P->inv_ns);
+  P->f_vks = f2((double)P->vk * P->sin_i);
+  P->f2_setup = (!P->box && !P->sph && v.nx <= (1 << 22) && v.ny <= (1 << 22)) ? 1 : 0;
   double B_nu = 2.0 * kH * pow(l.nu0_hz, 3) / (kC * kC);  // 2 h nu0^3 / c^2
   double conv = 1.0;
   if (v.units == 1) {

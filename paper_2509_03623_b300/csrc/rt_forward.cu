@@ -257,7 +257,7 @@ int resident_blocks(const void *kernel, int threads) {
 }
 
 template <int LPR, int CPL>
-static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
+static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream, bool pdl) {
   const bool spec = spec_ok(P);
   auto kern = P.sph ? march_fwd_kernel<LPR, CPL, 3>
               : P.box ? march_fwd_kernel<LPR, CPL, 2>
@@ -268,7 +268,7 @@ static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
   long long need = (units + kWarps - 1) / kWarps;
   long long cap = resident_blocks((const void *)kern, kWarps * 32);
   long long blocks = need < cap ? need : cap;
-  // the dynamic march follows its prep kernel as a programmatic dependent launch
+  // the dynamic march follows its prep kernel as a programmatic dependent launch (pdl)
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(kWarps * 32);
@@ -278,7 +278,7 @@ static void launch_t(const MarchParams &P, float *cube, cudaStream_t stream) {
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = P.unit_ctr ? 1 : 0;
+  cfg.numAttrs = pdl ? 1 : 0;
   cudaLaunchKernelEx(&cfg, kern, P, cube);
 }
 
@@ -382,7 +382,44 @@ int pack_cells(MarchParams &P, void *buf, cudaStream_t stream) {
   return RT_OK;
 }
 
-static int launch_march(const MarchParams &P, float *cube, cudaStream_t stream);
+static int launch_march(const MarchParams &P, float *cube, cudaStream_t stream, bool pdl);
+
+// Kernel timing (rt_kernel_timing): CUDA event pairs recorded around march launches.
+namespace {
+constexpr int kMaxTimed = 4096;
+struct KernelTimer {
+  std::mutex mu;
+  bool on = false;
+  int n = 0;
+  cudaEvent_t ev[kMaxTimed][2];
+};
+KernelTimer &ktimer() {
+  static KernelTimer t;
+  return t;
+}
+// A fresh event pair for one launch, or false (timing off, no room, no events).
+bool timer_pair(cudaEvent_t *a, cudaEvent_t *b) {
+  KernelTimer &t = ktimer();
+  std::lock_guard<std::mutex> lk(t.mu);
+  if (!t.on || t.n >= kMaxTimed) return false;
+  if (cudaEventCreate(a) != cudaSuccess) return false;
+  if (cudaEventCreate(b) != cudaSuccess) {
+    cudaEventDestroy(*a);
+    return false;
+  }
+  t.ev[t.n][0] = *a;
+  t.ev[t.n][1] = *b;
+  t.n++;
+  return true;
+}
+void timer_drop_locked(KernelTimer &t) {
+  for (int i = 0; i < t.n; i++) {
+    cudaEventDestroy(t.ev[i][0]);
+    cudaEventDestroy(t.ev[i][1]);
+  }
+  t.n = 0;
+}
+}  // namespace
 
 // Forward march. One stream-ordered allocation, freed after the launch, holds the corner
 // quads where they pay (packed first), the ray setups of every pixel (a pre-pass) and the
@@ -421,7 +458,11 @@ int launch_forward(const MarchParams &P, float *cube, cudaStream_t stream) {
     }
     Q.rays = rays;
     Q.unit_ctr = ctr;
-    rc = launch_march(Q, cube, stream);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    const bool timed = timer_pair(&t0, &t1);  // (then an ordinary launch after the prep)
+    if (timed) cudaEventRecord(t0, stream);
+    rc = launch_march(Q, cube, stream, !timed);
+    if (timed) cudaEventRecord(t1, stream);
   }
   cudaFreeAsync(buf, stream);
   return rc;
@@ -438,23 +479,24 @@ int launch_forward_dense(const MarchParams &P, float *cube, cudaStream_t stream)
   Q.hcell = nullptr;
   Q.rays = nullptr;  // static work distribution, ray setups in the kernel
   Q.unit_ctr = nullptr;
-  return launch_march(Q, cube, stream);
+  return launch_march(Q, cube, stream, false);
 }
 
-static int launch_march(const MarchParams &P, float *cube, cudaStream_t stream) {
+// pdl: launch as the programmatic dependent of the kernel just before it on the stream.
+static int launch_march(const MarchParams &P, float *cube, cudaStream_t stream, bool pdl) {
   int LPR, CPL;
   lane_layout(P.nch, P.no_window, &LPR, &CPL);
   if (CPL == 8) {
-    if (LPR == 32) launch_t<32, 8>(P, cube, stream);
-    else if (LPR == 16) launch_t<16, 8>(P, cube, stream);
-    else if (LPR == 8) launch_t<8, 8>(P, cube, stream);
-    else launch_t<4, 8>(P, cube, stream);
+    if (LPR == 32) launch_t<32, 8>(P, cube, stream, pdl);
+    else if (LPR == 16) launch_t<16, 8>(P, cube, stream, pdl);
+    else if (LPR == 8) launch_t<8, 8>(P, cube, stream, pdl);
+    else launch_t<4, 8>(P, cube, stream, pdl);
   } else {
-    if (LPR == 16) launch_t<16, 4>(P, cube, stream);
-    else if (LPR == 8) launch_t<8, 4>(P, cube, stream);
-    else if (LPR == 4) launch_t<4, 4>(P, cube, stream);
-    else if (LPR == 2) launch_t<2, 4>(P, cube, stream);
-    else launch_t<1, 4>(P, cube, stream);
+    if (LPR == 16) launch_t<16, 4>(P, cube, stream, pdl);
+    else if (LPR == 8) launch_t<8, 4>(P, cube, stream, pdl);
+    else if (LPR == 4) launch_t<4, 4>(P, cube, stream, pdl);
+    else if (LPR == 2) launch_t<2, 4>(P, cube, stream, pdl);
+    else launch_t<1, 4>(P, cube, stream, pdl);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "forward launch: %s", cudaGetErrorString(e));
@@ -497,3 +539,31 @@ int launch_count(const MarchParams &P, unsigned long long *count, cudaStream_t s
 }
 
 }  // namespace rtb
+
+extern "C" int rt_kernel_timing(int on) {
+  rtb::KernelTimer &t = rtb::ktimer();
+  std::lock_guard<std::mutex> lk(t.mu);
+  if (!on) rtb::timer_drop_locked(t);
+  t.on = on != 0;
+  return RT_OK;
+}
+
+extern "C" int rt_kernel_time(double *total_ms, int *launches) {
+  if (!total_ms || !launches) return rtb::set_error(RT_EINVAL, "null argument");
+  rtb::KernelTimer &t = rtb::ktimer();
+  std::lock_guard<std::mutex> lk(t.mu);
+  double sum = 0.0;
+  int rc = RT_OK;
+  for (int i = 0; i < t.n && rc == RT_OK; i++) {
+    float ms = 0.0f;
+    cudaError_t e = cudaEventSynchronize(t.ev[i][1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.ev[i][0], t.ev[i][1]);
+    if (e != cudaSuccess)
+      rc = rtb::set_error(RT_ECUDA, "kernel timing: %s", cudaGetErrorString(e));
+    sum += ms;
+  }
+  *total_ms = rc == RT_OK ? sum : 0.0;
+  *launches = rc == RT_OK ? t.n : 0;
+  rtb::timer_drop_locked(t);
+  return rc;
+}

@@ -20,6 +20,13 @@ constexpr int kTabSeg = kTabN - 1;
 
 struct Ray;
 
+// A double-float number: the unevaluated sum hi + lo of two FP32 numbers, |lo| <= ulp(hi) / 2
+// (about 44 significant bits). The disk's ray setup runs in this arithmetic on the FP32 pipes
+// (the FP64 pipe of this part retires about two lanes per clock per SM).
+struct F2 {
+  float hi, lo;
+};
+
 struct MarchParams {
   // grid
   int nr, nz, r_log, hard_edge;
@@ -59,6 +66,12 @@ struct MarchParams {
   // (omega = (0, sin i, -cos i); 0 where the component is 0), of 2 sin^2 i and of n_samples
   double sin_i, cos_i, cos_pa, sin_pa, R_cyl, H_cyl, px, py;
   double inv_wy, inv_wz, inv_2a, inv_ns;
+  // the same constants as double-float numbers for the FP32 ray setup of the disk (f2_setup:
+  // a disk view whose pixel indices are below 2^22), with H_cyl, R_cyl, R_cyl^2, 4 sin^2 i and
+  // vk sin i
+  F2 f_px, f_py, f_cos_pa, f_sin_pa, f_cos_i, f_sin_i, f_H, f_R, f_R2, f_4a, f_inv_wz,
+      f_inv_2a, f_inv_ns, f_vks;
+  int f2_setup;
   float vk;                 // sqrt(G M) [km s^-1 au^1/2]
   float vsys;
   // view
@@ -211,7 +224,135 @@ __device__ __forceinline__ void gas_range(const MarchParams &P, float xs, float 
   *khi = min((int)ceilf(f2), n - 1);
 }
 
+// Double-float arithmetic: error-free transformations of a sum (Knuth's TwoSum; Dekker's
+// Fast2Sum, for |a| >= |b|) and of a product (one FMA), and the double-word sum, product and
+// square root built from them (Dekker 1971; Joldes, Muller and Popescu 2017: relative errors
+// of a few 2^-48 for the sum and product).
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  return F2{s, __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp))};
+}
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return F2{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const F2 s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+  const F2 v = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
+}
+__device__ __forceinline__ F2 f2_neg(F2 a) { return F2{-a.hi, -a.lo}; }
+__device__ __forceinline__ F2 f2_sub(F2 a, F2 b) { return f2_add(a, f2_neg(b)); }
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = __fmaf_rn(a.hi, b.hi, -p);  // a.hi b.hi - p exactly
+  return fast_two_sum(p, __fadd_rn(e, __fmaf_rn(a.lo, b.hi, __fmul_rn(a.hi, b.lo))));
+}
+__device__ __forceinline__ F2 f2_mul1(F2 a, float b) {  // by an FP32 number
+  const float p = __fmul_rn(a.hi, b);
+  return fast_two_sum(p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p)));
+}
+__device__ __forceinline__ F2 f2_scale(F2 a, float pow2) {  // by a power of two (exact)
+  return F2{a.hi * pow2, a.lo * pow2};
+}
+// square root of a >= 0: the FP32 root of the high part plus one correction from the exact
+// residual a - s^2 (s^2 by the product transformation; a.hi - s^2 rounded is exact)
+__device__ __forceinline__ F2 f2_sqrt(F2 a) {
+  if (!(a.hi > 0.0f)) return F2{0.0f, 0.0f};
+  const float s = __fsqrt_rn(a.hi);
+  const float p = __fmul_rn(s, s), e = __fmaf_rn(s, s, -p);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), e), a.lo);
+  return fast_two_sum(s, __fmul_rn(r, 0.5f * rcp(s)));
+}
+__device__ __forceinline__ bool f2_lt(F2 a, F2 b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+
+// Round v to `bits` significant bits (FP32).
+__device__ __forceinline__ float round_bits_f(float v, int bits) {
+  if (v == 0.0f) return 0.0f;
+  int e;
+  frexpf(v, &e);
+  return ldexpf(rintf(ldexpf(v, bits - e)), e - bits);
+}
+
+// The disk's ray setup (setup_ray below) in double-float arithmetic: the same steps and the
+// same Ray, with the start point and step carried to about 2^-44 relative instead of FP64's
+// 2^-53 (the FP32 sample positions built from them round once to their own magnitude either
+// way).
+__device__ __forceinline__ Ray setup_ray_f2(const MarchParams &P, int ix, int iy, bool active) {
+  Ray R;
+  // pixel centre offsets (i + 1/2 - n/2), exact in FP32 below 2^22 pixels a side
+  const float cx = ((float)ix + 0.5f) - 0.5f * (float)P.nx;
+  const float cy = ((float)iy + 0.5f) - 0.5f * (float)P.ny;
+  const F2 X = f2_mul1(P.f_px, cx), Y = f2_mul1(P.f_py, cy);
+  const F2 xs = f2_add(f2_mul(X, P.f_cos_pa), f2_mul(Y, P.f_sin_pa));
+  const F2 ys = f2_sub(f2_mul(Y, P.f_cos_pa), f2_mul(X, P.f_sin_pa));
+  const F2 P0y = f2_mul(ys, P.f_cos_i), P0z = f2_mul(ys, P.f_sin_i);
+  const F2 wy = P.f_sin_i, wz = f2_neg(P.f_cos_i);
+  F2 lo = F2{-INFINITY, 0.0f}, hi = F2{INFINITY, 0.0f};
+  bool ok = active;
+  if (wz.hi != 0.0f) {  // the slab |z| <= H_cyl
+    const F2 t1 = f2_mul(f2_sub(f2_neg(P.f_H), P0z), P.f_inv_wz);
+    const F2 t2 = f2_mul(f2_sub(P.f_H, P0z), P.f_inv_wz);
+    const bool o = f2_lt(t1, t2);
+    lo = o ? t1 : t2;
+    hi = o ? t2 : t1;
+  } else if (f2_lt(P.f_H, F2{fabsf(P0z.hi), P0z.hi < 0.0f ? -P0z.lo : P0z.lo})) {
+    ok = false;
+  }
+  const F2 c = f2_sub(f2_add(f2_mul(xs, xs), f2_mul(P0y, P0y)), P.f_R2);
+  if (wy.hi != 0.0f) {
+    // the cylinder r <= R_cyl: roots of a s^2 + b s + c, a = wy^2, b = 2 P0y wy, with the
+    // discriminant 4 a (R - x)(R + x)
+    const F2 b = f2_scale(f2_mul(P0y, wy), 2.0f);
+    const F2 disc = f2_mul(P.f_4a, f2_mul(f2_sub(P.f_R, xs), f2_add(P.f_R, xs)));
+    if (disc.hi < 0.0f) {
+      ok = false;
+    } else {
+      const F2 sq = f2_sqrt(disc);
+      const F2 r1 = f2_mul(f2_sub(f2_neg(b), sq), P.f_inv_2a);
+      const F2 r2 = f2_mul(f2_sub(sq, b), P.f_inv_2a);
+      if (f2_lt(lo, r1)) lo = r1;
+      if (f2_lt(r2, hi)) hi = r2;
+    }
+  } else if (c.hi > 0.0f || (c.hi == 0.0f && c.lo > 0.0f)) {
+    ok = false;
+  }
+  ok = ok && f2_lt(lo, hi);
+  if (!ok) {
+    lo = F2{0.0f, 0.0f};
+    hi = F2{0.0f, 0.0f};
+  }
+  const F2 ds = f2_mul(f2_sub(hi, lo), P.f_inv_ns);
+  const F2 s0 = f2_add(lo, f2_scale(ds, 0.5f));
+  const F2 yb = f2_add(P0y, f2_mul(s0, wy)), zb = f2_add(P0z, f2_mul(s0, wz));
+  const F2 dy = f2_mul(ds, wy), dz = f2_mul(ds, wz);
+  R.x = xs.hi;
+  R.yb = yb.hi;
+  R.yb2 = yb.lo;
+  R.zb = zb.hi;
+  R.zb2 = zb.lo;
+  const float dyh = round_bits_f(dy.hi, P.step_bits), dzh = round_bits_f(dz.hi, P.step_bits);
+  R.dy = dyh;
+  R.dy2 = __fadd_rn(__fsub_rn(dy.hi, dyh), dy.lo);
+  R.dz = dzh;
+  R.dz2 = __fadd_rn(__fsub_rn(dz.hi, dzh), dz.lo);
+  R.ds = ds.hi;
+  R.vfac = f2_mul(P.f_vks, xs).hi;
+  R.hit = ok ? 1 : 0;
+  R.pix = iy * P.nx + ix;
+  R.klo = 0;
+  R.khi = ok ? P.n_samples - 1 : -1;
+  if (ok && !P.full_range)
+    gas_range(P, xs.hi, P0y.hi, P0z.hi, wy.hi, wz.hi, lo.hi, hi.hi, &R.klo, &R.khi);
+  return R;
+}
+
 __device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, bool active) {
+  if (P.f2_setup) return setup_ray_f2(P, ix, iy, active);
   Ray R;
   double X = ((double)ix + 0.5 - 0.5 * P.nx) * P.px;
   double Y = ((double)iy + 0.5 - 0.5 * P.ny) * P.py;
@@ -261,9 +402,11 @@ __device__ __forceinline__ Ray setup_ray(const MarchParams &P, int ix, int iy, b
   if (P.box || P.sph) {
     // (the box or sphere chord is complete)
   } else if (wy != 0.0) {
-    // roots of a s^2 + b s + c with a = wy^2, b = 2 P0y wy: (-b -+ sqrt(b^2 - 4 a c)) / (2 a)
+    // roots of a s^2 + b s + c with a = wy^2, b = 2 P0y wy: (-b -+ sqrt(b^2 - 4 a c)) / (2 a),
+    // the discriminant as 4 a (R - x)(R + x) (equal: x is constant along the ray; the
+    // difference of squares would lose the chords of grazing rays)
     double b = 2.0 * P0y * wy;
-    double disc = b * b - 4.0 * (wy * wy) * c;
+    double disc = 4.0 * (wy * wy) * ((P.R_cyl - xs) * (P.R_cyl + xs));
     if (disc < 0.0) {
       ok = false;
     } else {
