@@ -1,5 +1,5 @@
 // Fused adjoint of the march: a forward march that renders the cube, forms the loss seed and
-// stores optical-depth checkpoints every kSeg (32) samples, then a reverse march that propagates
+// keeps the optical depth at every batch boundary, then a reverse march that propagates
 // dL/dcube back to every node of the (r, z/r) fields and the CO surfaces (and, for
 // neural-field renders, to the per-sample network outputs).
 //
@@ -13,10 +13,11 @@
 // Samples without gas (dt = 0 in every channel) drop out exactly, so they are skipped and
 // S_{k+1} means the source of the next sample with gas.
 //
-// The transmittance of the reverse march comes from optical depths summed front to back: per
-// segment (last to first) the batch starts are recomputed forward from the
-// segment's checkpoint into the warp's scratch, and within a batch of LPR samples the
-// optical depth is rebuilt by subtracting the recomputed increments from the batch end.
+// The transmittance of the reverse march comes from optical depths summed front to back: the
+// forward pass keeps the (compensated) optical depth of every channel slot at every boundary
+// between batches of LPR samples in the warp's scratch, and within a batch the reverse
+// rebuilds it by subtracting its own increments from the batch end (recomputed with the
+// forward pass's roundings), so no rounding carries from one batch into the next.
 //
 // Per sample, lane q of a ray computes the channel-independent physics of its sample with
 // the local partial derivatives (kept in shared memory); the per-channel sums
@@ -38,11 +39,6 @@ template <int LPR>
 constexpr int adj_wpb() {
   return LPR >= 16 ? 2 : 4;
 }
-// Samples per checkpoint segment. 32 keeps the warps' scratch (per segment: batch starts and
-// sample records; per ray: checkpoints) and the gradient copies inside L2 on the observation
-// workload: 137 MB of DRAM traffic per launch against 498 MB with 64-sample segments and twice
-// the copies, at the same time.
-constexpr int kSeg = 32;
 
 // Per-sample record of the segment being reversed: the physics {kd, a, b, S} and the local
 // derivatives (below), five float4 per lane and batch; without a network or a rotation field
@@ -50,12 +46,17 @@ constexpr int kSeg = 32;
 // d v_los / d v_phi) is neither written nor read.
 constexpr int kRec = 5;
 
-// Per-warp scratch in floats: checkpoints of each segment, then the batch starts of the
-// segment being reversed, each CPL x 32 (lane-contiguous), then the segment's sample records
-// ([batch][kRec][lane] float4).
+// Per-warp scratch in floats: the optical depths of the lanes' channel slots at every batch
+// boundary of the forward pass (nbat batches of LPR samples: nbat + 1 boundaries), laid out
+// [boundary][lane][CPL] so that a lane stores and loads its CPL values as float4.
 template <int LPR, int CPL>
-__host__ __device__ constexpr long long adj_warp_floats(int nseg) {
-  return (long long)(nseg + kSeg / LPR + 1) * CPL * 32 + (long long)(kSeg / LPR) * kRec * 4 * 32;
+__host__ __device__ constexpr long long adj_warp_floats(int nbat) {
+  return (long long)(nbat + 1) * CPL * 32;
+}
+// Batches of LPR samples of the longest ray.
+template <int LPR>
+__host__ __device__ constexpr int adj_batches(int n_samples) {
+  return (n_samples + LPR - 1) / LPR;
 }
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -348,7 +349,7 @@ template <int LPR, int CPL, int VAR>
 __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
     march_adj_kernel(const __grid_constant__ MarchParams P, const float *__restrict__ dLdc,
                      const float *__restrict__ target, float *__restrict__ cube_out,
-                     const rt_grads G, float *__restrict__ scratch, int nseg,
+                     const rt_grads G, float *__restrict__ scratch, int nbat,
                      float4 *__restrict__ dmod, unsigned *__restrict__ dmax,
                      const GradCopies GC) {
   constexpr bool SPEC = (VAR & 4) != 0;  // the common configuration (spec_ok)
@@ -356,7 +357,6 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
   constexpr bool ROT = (VAR & 2) != 0;   // a rotation field (gradient with respect to it too)
   constexpr int WPB = adj_wpb<LPR>();
   constexpr int R = 32 / LPR;          // rays per warp
-  constexpr int NB = kSeg / LPR;       // batches per segment
   __shared__ __align__(16) float s_tab[kTabSeg * 4];
   // per ray LPR records plus one float4 of padding, so that the rays of a warp (reading one
   // record each, broadcast to their lanes) fall on different banks
@@ -364,7 +364,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
   __shared__ float4 s_ph[WPB][(32 / LPR) * kPhStride];
   // per-sample channel sums of each lane, [sample t][lane ^ (t & 7)] (conflict-free both ways)
   __shared__ float4 s_part[WPB][LPR][32];
-  __shared__ unsigned s_act[WPB][NB];  // window of each batch of the segment being reversed
+  // local derivatives of each lane's sample of the batch being reversed (physics_jac's
+  // records, [slot][lane])
+  __shared__ float4 s_rec[WPB][kRec][32];
   for (int i = threadIdx.x; i < kTabSeg * 4; i += blockDim.x) s_tab[i] = P.tab[i];
   __syncthreads();
 
@@ -373,12 +375,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
   const long long npix = (long long)P.nx * P.ny;
   const long long nunits = (npix + R - 1) / R;
   const long long gw = (long long)blockIdx.x * WPB + wib;
-  float *ck = scratch + gw * adj_warp_floats<LPR, CPL>(nseg);  // this warp's checkpoints
-  float *bs = ck + (long long)nseg * CPL * 32;                  // and batch starts
-  float4 *rec = reinterpret_cast<float4 *>(bs + (NB + 1) * CPL * 32) + lane;  // sample records
-  // float4 per lane and batch of the records actually used: the fifth (network and rotation
-  // entries) only with a network or a rotation field (a smaller working set in L2)
-  const int rstride = (ROT || (!SPEC && P.mod)) ? kRec : kRec - 1;
+  // this warp's optical depths at the batch boundaries, lane-major (adj_warp_floats)
+  float *ck = scratch + gw * adj_warp_floats<LPR, CPL>(nbat);
+  float4 *rb = &s_rec[wib][0][lane];  // this lane's sample records
   float4 *ph = s_ph[wib];
   float4(*part)[32] = s_part[wib];
   float vc[CPL];
@@ -393,8 +392,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
   double loss = 0.0;
   float dmx = 0.0f;  // largest |dL/d(network output)| this lane wrote
   const GradSink Gb = block_sink(G, GC);
-  // work counters (only with P.work): samples with gas, evaluations of the three passes
-  unsigned long long wc_gas = 0, wc_fwd = 0, wc_rec = 0, wc_rev = 0;
+  // work counters (only with P.work): samples with gas, evaluations of the forward and reverse
+  // passes
+  unsigned long long wc_gas = 0, wc_fwd = 0, wc_rev = 0;
 
   // Dynamic work distribution: each warp takes the next unit (R neighbouring rays) from a
   // launch-wide counter, in pixel order, until none is left; the lanes set up their own ray
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
       // segments and checkpoints are relative to it
       const int nsamp = __reduce_max_sync(0xffffffffu, max(ray.khi - ray.klo + 1, 0));
 
-      // ---------------- forward march with checkpoints every kSeg samples ----------------
+      // ---------- forward march, keeping the optical depth at every batch boundary ----------
       // channel slots in pairs (2m, 2m+1), packed two-lane FP32 instructions
       float2 tl[CPL / 2], tb[CPL / 2], Tr[CPL / 2], I[CPL / 2];
 #pragma unroll
@@ -425,15 +425,17 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
         I[m] = make_float2(0.0f, 0.0f);
       }
       const float2 mone = make_float2(-1.0f, -1.0f);
-      for (int kb = 0; kb < nsamp; kb += LPR) {
-        if (kb % kSeg == 0) {
-          // checkpoint: the base plus the compensation the last fold left in tl
+      // the optical depth at a batch boundary: the base plus the compensation the last fold
+      // left in tl (CPL values of the lane, as float4)
+      auto keep_depths = [&](int bnd) __attribute__((always_inline)) {
+        float4 *o = reinterpret_cast<float4 *>(ck + ((long long)bnd * 32 + lane) * CPL);
 #pragma unroll
-          for (int m = 0; m < CPL / 2; m++) {
-            ck[((kb / kSeg) * CPL + 2 * m) * 32 + lane] = tb[m].x + tl[m].x;
-            ck[((kb / kSeg) * CPL + 2 * m + 1) * 32 + lane] = tb[m].y + tl[m].y;
-          }
-        }
+        for (int m = 0; m < CPL / 2; m += 2)
+          o[m / 2] = make_float4(tb[m].x + tl[m].x, tb[m].y + tl[m].y, tb[m + 1].x + tl[m + 1].x,
+                                 tb[m + 1].y + tl[m + 1].y);
+      };
+      for (int kb = 0; kb < nsamp; kb += LPR) {
+        keep_depths(kb / LPR);
         const float4 mine = sample_physics<ROT, SPEC>(P, s_tab, ray, ray.klo + kb + q);
         const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
         unsigned act2 = 0;
@@ -480,6 +482,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
         }
         __syncwarp();
       }
+      keep_depths((nsamp + LPR - 1) / LPR);  // the end of the ray
 
       // ---------------- loss seed ----------------
       float2 gI[CPL / 2];  // dL/d(internal intensity) of slots (2m, 2m+1)
@@ -510,213 +513,173 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
       }
       if (nsamp == 0) continue;
 
-      // ---------------- reverse march over segments ----------------
-      const int nseg_ray = (nsamp + kSeg - 1) / kSeg;
+      // ---------------- reverse march, batch by batch (last to first) ----------------
       float2 A[CPL / 2];  // suffix sums of channel slots (2m, 2m+1)
 #pragma unroll
       for (int m = 0; m < CPL / 2; m++) A[m] = make_float2(0.0f, 0.0f);
       float Snext = S_bg;
-      for (int seg = nseg_ray - 1; seg >= 0; seg--) {
-        const int k0 = seg * kSeg;
-        const int nb = min(NB, (nsamp - k0 + LPR - 1) / LPR);
-        // batch starts of the segment, summed forward from its checkpoint
-        float tbs[CPL];
+      for (int b = (nsamp + LPR - 1) / LPR - 1; b >= 0; b--) {
+        const int kb = b * LPR;
+        // physics and local derivatives of this lane's sample (records in shared memory, read
+        // back by the same lane for its chain rule)
+        const float4 mine = physics_jac<ROT, SPEC>(P, s_tab, ray, ray.klo + kb + q, rb);
+        if (!__any_sync(0xffffffffu, mine.z > 0.0f)) continue;  // no gas in the batch
+        const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
+        const float Sbefore = Snext;
+        ph[rr * kPhStride + q] = mine;
+        // channel slots in pairs (2m, 2m+1) for the packed two-lane FP32 instructions; a
+        // pair is marched when either slot's block is in the window
+        unsigned act2 = 0;
 #pragma unroll
-        for (int j = 0; j < CPL; j++) tbs[j] = ck[(seg * CPL + j) * 32 + lane];
-        __syncwarp();  // the previous segment's reverse pass has read s_act
-        for (int b = 0; b < nb; b++) {
+        for (int m = 0; m < CPL / 2; m++)
+          if ((act >> (2 * m)) & 3u) act2 |= 1u << m;
+        if (P.work) wc_rev += (unsigned long long)__popc(act2) * 2 * LPR * 32;
+        // optical depths at the batch end, kept by the forward pass; within the batch the
+        // reverse subtracts its own increments from them
+        float2 cur[CPL / 2], Tn[CPL / 2];
+        const float4 *ce = reinterpret_cast<const float4 *>(ck + ((long long)(b + 1) * 32 + lane) * CPL);
 #pragma unroll
-          for (int j = 0; j < CPL; j++) bs[(b * CPL + j) * 32 + lane] = tbs[j];
-          // physics and local derivatives, kept for the reverse pass over this batch
-          float4 *rb = rec + (long long)b * rstride * 32;
-          const float4 mine = physics_jac<ROT, SPEC>(P, s_tab, ray, ray.klo + k0 + b * LPR + q, rb);
-          rb[0] = mine;
-          const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
-          if (lane == 0) s_act[wib][b] = act;
-          if (P.work) wc_rec += (unsigned long long)__popc(act) * LPR * 32;
-          if (!act) continue;
-          ph[rr * kPhStride + q] = mine;
-          __syncwarp();
-#pragma unroll
-          for (int j = 0; j < CPL; j++) {
-            if (!(act & (1u << j))) continue;  // warp-uniform, once per block and batch
-#pragma unroll
-            for (int t = 0; t < LPR; t++) {
-              const float4 p = ph[rr * kPhStride + t];
-              // the same roundings as the reverse pass's packed d (db rounded on its own, then
-              // one fma): the reverse subtracts its own increments from these sums, and any
-              // difference in the last bit (a contracted dvs * p.z, say) leaves optical depth
-              // behind that the CO-edge Jacobian amplifies tenfold
-              const float d = UNIF ? fmaf((float)j, __fmul_rn(dvs, p.z), fmaf(vq, p.z, -p.y))
-                                   : fmaf(vc[j], p.z, -p.y);
-              tbs[j] = fmaf(p.x, ex2(d * -d), tbs[j]);
-            }
-          }
-          __syncwarp();
+        for (int m = 0; m < CPL / 2; m += 2) {
+          const float4 v = ce[m / 2];
+          cur[m] = make_float2(v.x, v.y);
+          cur[m + 1] = make_float2(v.z, v.w);
         }
 #pragma unroll
-        for (int j = 0; j < CPL; j++) bs[(nb * CPL + j) * 32 + lane] = tbs[j];
-        __syncwarp();  // s_act of the segment
-
-        // backward over the batches of the segment
-        for (int b = nb - 1; b >= 0; b--) {
-          const int kb = k0 + b * LPR;
-          const float4 *rb = rec + (long long)b * rstride * 32;
-          const float4 mine = rb[0];
-          if (!__any_sync(0xffffffffu, mine.z > 0.0f)) continue;  // no gas in the batch
-          const unsigned act = s_act[wib][b];
-          const float Sbefore = Snext;
-          ph[rr * kPhStride + q] = mine;
-          // channel slots in pairs (2m, 2m+1) for the packed two-lane FP32 instructions; a
-          // pair is marched when either slot's block is in the window
-          unsigned act2 = 0;
-#pragma unroll
-          for (int m = 0; m < CPL / 2; m++)
-            if ((act >> (2 * m)) & 3u) act2 |= 1u << m;
-          if (P.work) wc_rev += (unsigned long long)__popc(act2) * 2 * LPR * 32;
-          float2 cur[CPL / 2], Tn[CPL / 2];
-#pragma unroll
-          for (int m = 0; m < CPL / 2; m++) {
-            cur[m] = make_float2(bs[((b + 1) * CPL + 2 * m) * 32 + lane],
-                                 bs[((b + 1) * CPL + 2 * m + 1) * 32 + lane]);
-            Tn[m] = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
+        for (int m = 0; m < CPL / 2; m++) Tn[m] = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
+        __syncwarp();
+        const float2 mone = make_float2(-1.0f, -1.0f);
+        // reverse step of one channel pair m at sample t of the batch: advances the suffix
+        // sums A, the optical depth cur and the transmittance Tn of the pair, and returns its
+        // contributions to the per-sample channel sums (ax, ay, az, aw)
+        auto rev_step = [&](int m, const float4 &p, float cs) {
+          const float dc = fmaf(vq, p.z, -p.y), db = __fmul_rn(dvs, p.z);
+          const float2 cs2 = make_float2(cs, cs), kd2 = make_float2(p.x, p.x);
+          const float2 d =
+              UNIF ? __ffma2_rn(make_float2((float)(2 * m), (float)(2 * m + 1)),
+                                make_float2(db, db), make_float2(dc, dc))
+                   : __ffma2_rn(make_float2(vc[2 * m], vc[2 * m + 1]),
+                                make_float2(p.z, p.z), make_float2(-p.y, -p.y));
+          const float2 d2 = __fmul2_rn(d, d);
+          const float2 gg = make_float2(ex2(-d2.x), ex2(-d2.y));
+          A[m] = __ffma2_rn(cs2, Tn[m], A[m]);
+          const float2 ug = __fmul2_rn(__fmul2_rn(gI[m], A[m]), gg);
+          const float2 dt = __fmul2_rn(kd2, gg);
+          cur[m] = __ffma2_rn(dt, mone, cur[m]);
+          const float2 T0 = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
+          // T_k - T_{k+1} = T_{k+1} (2^dt - 1): series below dt = 0.07 (the difference of
+          // two rounded transmittances would lose the small optical depths)
+          const float2 poly = __ffma2_rn(
+              __ffma2_rn(dt, make_float2(0.0555041087f, 0.0555041087f),
+                         make_float2(0.240226507f, 0.240226507f)),
+              dt, make_float2(0.693147181f, 0.693147181f));
+          const float2 ser = __fmul2_rn(__fmul2_rn(Tn[m], dt), poly);
+          const float2 dif = __ffma2_rn(Tn[m], mone, T0);
+          const float2 dTk = make_float2(dt.x < 0.07f ? ser.x : dif.x,
+                                         dt.y < 0.07f ? ser.y : dif.y);
+          Tn[m] = T0;
+          const float2 wy = __fmul2_rn(ug, d2), wz = __fmul2_rn(ug, d), ww = __fmul2_rn(gI[m], dTk);
+          return make_float4(ug.x + ug.y, wy.x + wy.y, ROT ? wz.x + wz.y : 0.0f, ww.x + ww.y);
+        };
+        // one channel pair in the window (the common case): its loop without per-sample
+        // window tests, the pair index a compile-time constant
+        auto one_pair = [&](auto M) {
+          constexpr int m = decltype(M)::value;
+#pragma unroll 1
+          for (int t = LPR - 1; t >= 0; t--) {
+            const float4 p = ph[rr * kPhStride + t];
+            const bool gas = p.z > 0.0f;
+            const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
+            Snext = gas ? p.w : Snext;
+            part[t][lane ^ (t & 7)] = rev_step(m, p, cs);
           }
-          __syncwarp();
-          const float2 mone = make_float2(-1.0f, -1.0f);
-          // reverse step of one channel pair m at sample t of the batch: advances the suffix
-          // sums A, the optical depth cur and the transmittance Tn of the pair, and returns its
-          // contributions to the per-sample channel sums (ax, ay, az, aw)
-          auto rev_step = [&](int m, const float4 &p, float cs) {
-            const float dc = fmaf(vq, p.z, -p.y), db = __fmul_rn(dvs, p.z);
-            const float2 cs2 = make_float2(cs, cs), kd2 = make_float2(p.x, p.x);
-            const float2 d =
-                UNIF ? __ffma2_rn(make_float2((float)(2 * m), (float)(2 * m + 1)),
-                                  make_float2(db, db), make_float2(dc, dc))
-                     : __ffma2_rn(make_float2(vc[2 * m], vc[2 * m + 1]),
-                                  make_float2(p.z, p.z), make_float2(-p.y, -p.y));
-            const float2 d2 = __fmul2_rn(d, d);
-            const float2 gg = make_float2(ex2(-d2.x), ex2(-d2.y));
-            A[m] = __ffma2_rn(cs2, Tn[m], A[m]);
-            const float2 ug = __fmul2_rn(__fmul2_rn(gI[m], A[m]), gg);
-            const float2 dt = __fmul2_rn(kd2, gg);
-            cur[m] = __ffma2_rn(dt, mone, cur[m]);
-            const float2 T0 = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
-            // T_k - T_{k+1} = T_{k+1} (2^dt - 1): series below dt = 0.07 (the difference of
-            // two rounded transmittances would lose the small optical depths)
-            const float2 poly = __ffma2_rn(
-                __ffma2_rn(dt, make_float2(0.0555041087f, 0.0555041087f),
-                           make_float2(0.240226507f, 0.240226507f)),
-                dt, make_float2(0.693147181f, 0.693147181f));
-            const float2 ser = __fmul2_rn(__fmul2_rn(Tn[m], dt), poly);
-            const float2 dif = __ffma2_rn(Tn[m], mone, T0);
-            const float2 dTk = make_float2(dt.x < 0.07f ? ser.x : dif.x,
-                                           dt.y < 0.07f ? ser.y : dif.y);
-            Tn[m] = T0;
-            const float2 wy = __fmul2_rn(ug, d2), wz = __fmul2_rn(ug, d), ww = __fmul2_rn(gI[m], dTk);
-            return make_float4(ug.x + ug.y, wy.x + wy.y, ROT ? wz.x + wz.y : 0.0f, ww.x + ww.y);
-          };
-          // one channel pair in the window (the common case): its loop without per-sample
-          // window tests, the pair index a compile-time constant
-          auto one_pair = [&](auto M) {
-            constexpr int m = decltype(M)::value;
+        };
+        // two adjacent pairs in the window (the next most common case), likewise
+        auto two_pairs = [&](auto M) {
+          constexpr int m = decltype(M)::value;
 #pragma unroll 1
-            for (int t = LPR - 1; t >= 0; t--) {
-              const float4 p = ph[rr * kPhStride + t];
-              const bool gas = p.z > 0.0f;
-              const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
-              Snext = gas ? p.w : Snext;
-              part[t][lane ^ (t & 7)] = rev_step(m, p, cs);
-            }
-          };
-          // two adjacent pairs in the window (the next most common case), likewise
-          auto two_pairs = [&](auto M) {
-            constexpr int m = decltype(M)::value;
-#pragma unroll 1
-            for (int t = LPR - 1; t >= 0; t--) {
-              const float4 p = ph[rr * kPhStride + t];
-              const bool gas = p.z > 0.0f;
-              const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
-              Snext = gas ? p.w : Snext;
-              const float4 c0 = rev_step(m, p, cs), c1 = rev_step(m + 1, p, cs);
-              part[t][lane ^ (t & 7)] =
-                  make_float4(c0.x + c1.x, c0.y + c1.y, c0.z + c1.z, c0.w + c1.w);
-            }
-          };
-          const int npair = __popc(act2);
-          if (npair == 2 && act2 == 3u) {
-            two_pairs(std::integral_constant<int, 0>());
-          } else if (CPL / 2 > 2 && npair == 2 && act2 == 6u) {
-            two_pairs(std::integral_constant<int, (CPL / 2 > 2 ? 1 : 0)>());
-          } else if (CPL / 2 > 3 && npair == 2 && act2 == 12u) {
-            two_pairs(std::integral_constant<int, (CPL / 2 > 3 ? 2 : 0)>());
-          } else if (npair == 1 && act2 == 1u) {
-            one_pair(std::integral_constant<int, 0>());
-          } else if (npair == 1 && act2 == 2u) {
-            one_pair(std::integral_constant<int, 1>());
-          } else if (CPL / 2 > 2 && npair == 1 && act2 == 4u) {
-            one_pair(std::integral_constant<int, (CPL / 2 > 2 ? 2 : 0)>());
-          } else if (CPL / 2 > 3 && npair == 1 && act2 == 8u) {
-            one_pair(std::integral_constant<int, (CPL / 2 > 3 ? 3 : 0)>());
-          } else {
-#pragma unroll 1
-            for (int t = LPR - 1; t >= 0; t--) {
-              const float4 p = ph[rr * kPhStride + t];
-              const bool gas = p.z > 0.0f;
-              const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
-              Snext = gas ? p.w : Snext;
-              float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-#pragma unroll
-              for (int m = 0; m < CPL / 2; m++) {
-                if (!(act2 & (1u << m))) continue;  // warp-uniform
-                const float4 c = rev_step(m, p, cs);
-                a.x += c.x;
-                a.y += c.y;
-                a.z += c.z;
-                a.w += c.w;
-              }
-              part[t][lane ^ (t & 7)] = a;
-            }
+          for (int t = LPR - 1; t >= 0; t--) {
+            const float4 p = ph[rr * kPhStride + t];
+            const bool gas = p.z > 0.0f;
+            const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
+            Snext = gas ? p.w : Snext;
+            const float4 c0 = rev_step(m, p, cs), c1 = rev_step(m + 1, p, cs);
+            part[t][lane ^ (t & 7)] =
+                make_float4(c0.x + c1.x, c0.y + c1.y, c0.z + c1.z, c0.w + c1.w);
           }
-          // blocks outside every window: T is constant over the batch, so the suffix sums
-          // advance by T (S before the batch - S of its first sample with gas)
-          const float dS = Sbefore - Snext;
+        };
+        const int npair = __popc(act2);
+        if (npair == 2 && act2 == 3u) {
+          two_pairs(std::integral_constant<int, 0>());
+        } else if (CPL / 2 > 2 && npair == 2 && act2 == 6u) {
+          two_pairs(std::integral_constant<int, (CPL / 2 > 2 ? 1 : 0)>());
+        } else if (CPL / 2 > 3 && npair == 2 && act2 == 12u) {
+          two_pairs(std::integral_constant<int, (CPL / 2 > 3 ? 2 : 0)>());
+        } else if (npair == 1 && act2 == 1u) {
+          one_pair(std::integral_constant<int, 0>());
+        } else if (npair == 1 && act2 == 2u) {
+          one_pair(std::integral_constant<int, 1>());
+        } else if (CPL / 2 > 2 && npair == 1 && act2 == 4u) {
+          one_pair(std::integral_constant<int, (CPL / 2 > 2 ? 2 : 0)>());
+        } else if (CPL / 2 > 3 && npair == 1 && act2 == 8u) {
+          one_pair(std::integral_constant<int, (CPL / 2 > 3 ? 3 : 0)>());
+        } else {
+#pragma unroll 1
+          for (int t = LPR - 1; t >= 0; t--) {
+            const float4 p = ph[rr * kPhStride + t];
+            const bool gas = p.z > 0.0f;
+            const float cs = gas ? Snext - p.w : 0.0f;  // S_{k+1} - S_k
+            Snext = gas ? p.w : Snext;
+            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
-          for (int m = 0; m < CPL / 2; m++)
-            if (!(act2 & (1u << m))) A[m] = __ffma2_rn(make_float2(dS, dS), Tn[m], A[m]);
-          __syncwarp();
-          float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (int m = 0; m < CPL / 2; m++) {
+              if (!(act2 & (1u << m))) continue;  // warp-uniform
+              const float4 c = rev_step(m, p, cs);
+              a.x += c.x;
+              a.y += c.y;
+              a.z += c.z;
+              a.w += c.w;
+            }
+            part[t][lane ^ (t & 7)] = a;
+          }
+        }
+        // blocks outside every window: T is constant over the batch, so the suffix sums
+        // advance by T (S before the batch - S of its first sample with gas)
+        const float dS = Sbefore - Snext;
+#pragma unroll
+        for (int m = 0; m < CPL / 2; m++)
+          if (!(act2 & (1u << m))) A[m] = __ffma2_rn(make_float2(dS, dS), Tn[m], A[m]);
+        __syncwarp();
+        float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll 8
-          for (int i = 0; i < LPR; i++) {
-            const float4 v = part[q][(rr * LPR + i) ^ (q & 7)];
-            s.x += v.x;
-            s.y += v.y;
-            if (ROT) s.z += v.z;
-            s.w += v.w;
-          }
-          if (active && mine.z > 0.0f) {
-            float Jv[4 * (kRec - 1)];
-#pragma unroll
-            for (int i = 0; i < kRec - 1; i++) {
-              const float4 v = (i < kRec - 2 || (!SPEC && P.mod) || ROT) ? rb[(i + 1) * 32]
-                                                              : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-              Jv[4 * i] = v.x;
-              Jv[4 * i + 1] = v.y;
-              Jv[4 * i + 2] = v.z;
-              Jv[4 * i + 3] = v.w;
-            }
-            dmx = fmaxf(dmx, scatter_grad<ROT>(P, Jv, mine.x, mine.z, s.x, s.y, s.z, s.w, Gb,
-                                          dmod ? dmod + (long long)pix * P.n_samples + ray.klo + kb + q
-                                               : nullptr));
-          }
-          __syncwarp();
+        for (int i = 0; i < LPR; i++) {
+          const float4 v = part[q][(rr * LPR + i) ^ (q & 7)];
+          s.x += v.x;
+          s.y += v.y;
+          if (ROT) s.z += v.z;
+          s.w += v.w;
         }
+        if (active && mine.z > 0.0f) {
+          float Jv[4 * (kRec - 1)];
+#pragma unroll
+          for (int i = 0; i < kRec - 1; i++) {
+            const float4 v = (i < kRec - 2 || (!SPEC && P.mod) || ROT) ? rb[(i + 1) * 32]
+                                                            : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+            Jv[4 * i] = v.x;
+            Jv[4 * i + 1] = v.y;
+            Jv[4 * i + 2] = v.z;
+            Jv[4 * i + 3] = v.w;
+          }
+          dmx = fmaxf(dmx, scatter_grad<ROT>(P, Jv, mine.x, mine.z, s.x, s.y, s.z, s.w, Gb,
+                                        dmod ? dmod + (long long)pix * P.n_samples + ray.klo + kb + q
+                                             : nullptr));
+        }
+        __syncwarp();
       }
     }
   }
   if (P.work && lane == 0) {
     atomicAdd(P.work, wc_gas);
     atomicAdd(P.work + 1, wc_fwd);
-    atomicAdd(P.work + 2, wc_rec);
     atomicAdd(P.work + 3, wc_rev);
   }
   if (G.loss && target) {
@@ -797,8 +760,8 @@ static long long adj_blocks(const MarchParams &P, long long cap_blocks) {
 // Bytes of per-warp scratch (checkpoints and batch starts) one block needs.
 template <int LPR, int CPL>
 static size_t adj_block_bytes(const MarchParams &P) {
-  int nseg = (P.n_samples + kSeg - 1) / kSeg;
-  return (size_t)adj_wpb<LPR>() * adj_warp_floats<LPR, CPL>(nseg) * sizeof(float);
+  return (size_t)adj_wpb<LPR>() * adj_warp_floats<LPR, CPL>(adj_batches<LPR>(P.n_samples)) *
+         sizeof(float);
 }
 
 // Scratch of one adjoint launch: the warps' checkpoints, the gradient copies, then the
@@ -908,7 +871,7 @@ static int run_adj(const MarchParams &P, const float *dLdc, const float *target,
   int rc = zero_grads(P, G, a, scratch, stream);
   if (rc != RT_OK) return rc;
   const GradCopies c = copies_of(P, a, scratch);
-  const int nseg = (P.n_samples + kSeg - 1) / kSeg;
+  const int nbat = adj_batches<LPR>(P.n_samples);
   // the kernel takes the parameters by value, so the copy pointing at the corner quads only
   // has to live until the launch (on the stack: no host allocation)
   MarchParams Q = P;
@@ -922,13 +885,13 @@ static int run_adj(const MarchParams &P, const float *dLdc, const float *target,
   if constexpr (VAR == 1) {
     if (spec_ok(Q)) {  // the specialised variant (same scratch layout and block count)
       march_adj_kernel<LPR, CPL, 5><<<(unsigned)blocks, adj_wpb<LPR>() * 32, 0, stream>>>(
-          Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, dmax, c);
+          Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nbat, dmod, dmax, c);
       launched = true;
     }
   }
   if (!launched)
     march_adj_kernel<LPR, CPL, VAR><<<(unsigned)blocks, adj_wpb<LPR>() * 32, 0, stream>>>(
-        Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nseg, dmod, dmax, c);
+        Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch), nbat, dmod, dmax, c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(RT_ECUDA, "adjoint launch: %s", cudaGetErrorString(e));
   return sum_copies(P, G, c, a, stream);
