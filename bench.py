@@ -58,8 +58,9 @@ MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 4)
 # dram__bytes_write of march_fwd_kernel<8,8,4>; the cube stays in L2 at the end of the launch)
 FWD_DRAM_BYTES = 3_329_280 + 29_184
 # DRAM bytes (read + write) of one fused-adjoint launch on the same workload (ncu capture of
-# march_adj_kernel<8, 8, 5> with 32-sample segments and a 16 MiB grid-copy budget)
-ADJ_DRAM_BYTES = 32_533_504 + 104_930_560
+# march_adj_kernel<8, 8, 5>: per-batch depth entries of the advanced channel pairs, 16 MiB
+# grid-copy budget)
+ADJ_DRAM_BYTES = 30_705_152 + 43_197_696
 N_SM = 148
 E2E_STREAMS = 4  # streams of the end-to-end leg
 SM_MAX_MHZ = 2032.0

@@ -13,10 +13,11 @@
 // Samples without gas (dt = 0 in every channel) drop out exactly, so they are skipped and
 // S_{k+1} means the source of the next sample with gas.
 //
-// The transmittance of the reverse march comes from optical depths summed front to back: the
-// forward pass keeps the (compensated) optical depth of every channel slot at every boundary
-// between batches of LPR samples in the warp's scratch, and within a batch the reverse
-// rebuilds it by subtracting its own increments from the batch end (recomputed with the
+// The transmittance of the reverse march comes from optical depths summed front to back: for
+// every batch of LPR samples the forward pass keeps, in the warp's scratch, the (compensated)
+// optical depths at the batch's end of the channel pairs the batch advanced (the others did
+// not change), and the batch's pair mask; the reverse reloads those at each batch and
+// rebuilds the depths inside it by subtracting its own increments (recomputed with the
 // forward pass's roundings), so no rounding carries from one batch into the next.
 //
 // Per sample, lane q of a ray computes the channel-independent physics of its sample with
@@ -46,12 +47,15 @@ constexpr int adj_wpb() {
 // d v_los / d v_phi) is neither written nor read.
 constexpr int kRec = 5;
 
-// Per-warp scratch in floats: the optical depths of the lanes' channel slots at every batch
-// boundary of the forward pass (nbat batches of LPR samples: nbat + 1 boundaries), laid out
-// [boundary][lane][CPL] so that a lane stores and loads its CPL values as float4.
+// Per-warp scratch in floats, for rays of nbat batches of LPR samples at most: the optical
+// depths of the lanes' CPL channel slots at the end of the rays ([lane][CPL], float4 per
+// lane), then one entry per (batch, channel pair the batch advances): the pair's depths at the
+// end of the batch ([entry][lane] float2; nbat CPL / 2 entries at most, about a third of that
+// with the channel window), then the forward pass's pair mask of every batch (one byte each).
+// Only what the rays use is touched, which keeps the warps' scratch in L2.
 template <int LPR, int CPL>
 __host__ __device__ constexpr long long adj_warp_floats(int nbat) {
-  return (long long)(nbat + 1) * CPL * 32;
+  return (long long)CPL * 32 + (long long)nbat * (CPL / 2) * 64 + (long long)(nbat + 15) / 16 * 4;
 }
 // Batches of LPR samples of the longest ray.
 template <int LPR>
@@ -375,8 +379,11 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
   const long long npix = (long long)P.nx * P.ny;
   const long long nunits = (npix + R - 1) / R;
   const long long gw = (long long)blockIdx.x * WPB + wib;
-  // this warp's optical depths at the batch boundaries, lane-major (adj_warp_floats)
+  // this warp's scratch (adj_warp_floats): the depths at the end of the rays, the per-batch
+  // entries and the batches' pair masks
   float *ck = scratch + gw * adj_warp_floats<LPR, CPL>(nbat);
+  float2 *ent = reinterpret_cast<float2 *>(ck + CPL * 32) + lane;
+  unsigned char *acts = reinterpret_cast<unsigned char *>(ck + CPL * 32 + (long long)nbat * (CPL / 2) * 64);
   float4 *rb = &s_rec[wib][0][lane];  // this lane's sample records
   float4 *ph = s_ph[wib];
   float4(*part)[32] = s_part[wib];
@@ -425,23 +432,15 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
         I[m] = make_float2(0.0f, 0.0f);
       }
       const float2 mone = make_float2(-1.0f, -1.0f);
-      // the optical depth at a batch boundary: the base plus the compensation the last fold
-      // left in tl (CPL values of the lane, as float4)
-      auto keep_depths = [&](int bnd) __attribute__((always_inline)) {
-        float4 *o = reinterpret_cast<float4 *>(ck + ((long long)bnd * 32 + lane) * CPL);
-#pragma unroll
-        for (int m = 0; m < CPL / 2; m += 2)
-          o[m / 2] = make_float4(tb[m].x + tl[m].x, tb[m].y + tl[m].y, tb[m + 1].x + tl[m + 1].x,
-                                 tb[m + 1].y + tl[m + 1].y);
-      };
+      int nent = 0;  // entries kept (warp-uniform)
       for (int kb = 0; kb < nsamp; kb += LPR) {
-        keep_depths(kb / LPR);
         const float4 mine = sample_physics<ROT, SPEC>(P, s_tab, ray, ray.klo + kb + q);
         const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
         unsigned act2 = 0;
 #pragma unroll
         for (int m = 0; m < CPL / 2; m++)
           if ((act >> (2 * m)) & 3u) act2 |= 1u << m;
+        if (lane == 0) acts[kb / LPR] = (unsigned char)act2;  // (the reverse marches these)
         if (P.work) {
           wc_gas += __popc(__ballot_sync(0xffffffffu, mine.x > 0.0f));
           wc_fwd += (unsigned long long)__popc(act2) * 2 * LPR * 32;
@@ -480,9 +479,24 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
           tl[m] = __ffma2_rn(__ffma2_rn(tb[m], mone, t), mone, tl[m]);
           tb[m] = t;
         }
+        // the depths of the pairs this batch advanced, at its end: the base plus the
+        // compensation the fold left in tl (one entry per pair, in pair order)
+#pragma unroll
+        for (int m = 0; m < CPL / 2; m++)
+          if (act2 & (1u << m)) {  // warp-uniform
+            ent[(long long)nent * 32] = make_float2(tb[m].x + tl[m].x, tb[m].y + tl[m].y);
+            nent++;
+          }
         __syncwarp();
       }
-      keep_depths((nsamp + LPR - 1) / LPR);  // the end of the ray
+      {  // the depths at the end of the rays
+        float4 *o = reinterpret_cast<float4 *>(ck + lane * CPL);
+#pragma unroll
+        for (int m = 0; m < CPL / 2; m += 2)
+          o[m / 2] = make_float4(tb[m].x + tl[m].x, tb[m].y + tl[m].y, tb[m + 1].x + tl[m + 1].x,
+                                 tb[m + 1].y + tl[m + 1].y);
+      }
+      __syncwarp();  // (lane 0's pair masks, for every lane's reverse pass)
 
       // ---------------- loss seed ----------------
       float2 gI[CPL / 2];  // dL/d(internal intensity) of slots (2m, 2m+1)
@@ -518,26 +532,12 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
 #pragma unroll
       for (int m = 0; m < CPL / 2; m++) A[m] = make_float2(0.0f, 0.0f);
       float Snext = S_bg;
-      for (int b = (nsamp + LPR - 1) / LPR - 1; b >= 0; b--) {
-        const int kb = b * LPR;
-        // physics and local derivatives of this lane's sample (records in shared memory, read
-        // back by the same lane for its chain rule)
-        const float4 mine = physics_jac<ROT, SPEC>(P, s_tab, ray, ray.klo + kb + q, rb);
-        if (!__any_sync(0xffffffffu, mine.z > 0.0f)) continue;  // no gas in the batch
-        const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
-        const float Sbefore = Snext;
-        ph[rr * kPhStride + q] = mine;
-        // channel slots in pairs (2m, 2m+1) for the packed two-lane FP32 instructions; a
-        // pair is marched when either slot's block is in the window
-        unsigned act2 = 0;
-#pragma unroll
-        for (int m = 0; m < CPL / 2; m++)
-          if ((act >> (2 * m)) & 3u) act2 |= 1u << m;
-        if (P.work) wc_rev += (unsigned long long)__popc(act2) * 2 * LPR * 32;
-        // optical depths at the batch end, kept by the forward pass; within the batch the
-        // reverse subtracts its own increments from them
-        float2 cur[CPL / 2], Tn[CPL / 2];
-        const float4 *ce = reinterpret_cast<const float4 *>(ck + ((long long)(b + 1) * 32 + lane) * CPL);
+      // optical depths and transmittances of the channel pairs at the end of the batch being
+      // reversed: the forward pass's values for the pairs the batch advances; the other pairs
+      // carry theirs from the later batches (unchanged in between)
+      float2 cur[CPL / 2], Tn[CPL / 2];
+      {
+        const float4 *ce = reinterpret_cast<const float4 *>(ck + lane * CPL);
 #pragma unroll
         for (int m = 0; m < CPL / 2; m += 2) {
           const float4 v = ce[m / 2];
@@ -546,6 +546,31 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
         }
 #pragma unroll
         for (int m = 0; m < CPL / 2; m++) Tn[m] = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
+      }
+      int ient = nent;
+      for (int b = (nsamp + LPR - 1) / LPR - 1; b >= 0; b--) {
+        const int kb = b * LPR;
+        // the channel pairs the forward pass advanced in this batch (the same window), whose
+        // entries precede the later batches'
+        const unsigned act2 = acts[b];
+        ient -= __popc(act2);
+        // physics and local derivatives of this lane's sample (records in shared memory, read
+        // back by the same lane for its chain rule)
+        const float4 mine = physics_jac<ROT, SPEC>(P, s_tab, ray, ray.klo + kb + q, rb);
+        if (!__any_sync(0xffffffffu, mine.z > 0.0f)) continue;  // no gas in the batch
+        const float Sbefore = Snext;
+        ph[rr * kPhStride + q] = mine;
+        if (P.work) wc_rev += (unsigned long long)__popc(act2) * 2 * LPR * 32;
+        {
+          int e = ient;
+#pragma unroll
+          for (int m = 0; m < CPL / 2; m++)
+            if (act2 & (1u << m)) {  // warp-uniform
+              cur[m] = ent[(long long)e * 32];
+              Tn[m] = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
+              e++;
+            }
+        }
         __syncwarp();
         const float2 mone = make_float2(-1.0f, -1.0f);
         // reverse step of one channel pair m at sample t of the batch: advances the suffix
