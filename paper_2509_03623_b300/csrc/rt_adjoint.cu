@@ -471,19 +471,17 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
             Tr[m] = Tn;
           }
         }
-        // compensated fold of the batch into the base (Kahan, as in the forward march): tl
-        // carries the batch sum minus the rounding error of the previous fold
-#pragma unroll
-        for (int m = 0; m < CPL / 2; m++) {
-          const float2 t = __fadd2_rn(tb[m], tl[m]);
-          tl[m] = __ffma2_rn(__ffma2_rn(tb[m], mone, t), mone, tl[m]);
-          tb[m] = t;
-        }
-        // the depths of the pairs this batch advanced, at its end: the base plus the
-        // compensation the fold left in tl (one entry per pair, in pair order)
+        // compensated fold of the batch into the base of the pairs it advanced (Kahan, as in
+        // the forward march; the other pairs' sums did not change): tl carries the batch sum
+        // minus the rounding error of the previous fold. Their depths at the batch end (the
+        // base plus the compensation the fold left in tl) are kept: one entry per pair, in
+        // pair order.
 #pragma unroll
         for (int m = 0; m < CPL / 2; m++)
           if (act2 & (1u << m)) {  // warp-uniform
+            const float2 t = __fadd2_rn(tb[m], tl[m]);
+            tl[m] = __ffma2_rn(__ffma2_rn(tb[m], mone, t), mone, tl[m]);
+            tb[m] = t;
             ent[(long long)nent * 32] = make_float2(tb[m].x + tl[m].x, tb[m].y + tl[m].y);
             nent++;
           }
