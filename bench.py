@@ -39,12 +39,12 @@ L2_BYTES = 126 * 2 ** 20
 # of the source), RSQRT x3 (radius, Keplerian factor, line width), LG2 x3 (radius, LTE table,
 # window), RCP x4 (CO edges, 1/T, source quotient, window), SQRT x2 (Keplerian factor, window).
 PHYS_MUFU_OPS = {"ex2": 4, "rsqrt": 3, "lg2": 3, "rcp": 4, "sqrt": 2}
-# The adjoint's recompute of a sample's physics with its local derivatives (physics_jac) and
-# window: EX2 x4, RSQRT x3, LG2 x3, RCP x4, SQRT x2 as well
+# The adjoint reverse pass's evaluation of a sample's physics with its local derivatives
+# (physics_jac) and window: EX2 x4, RSQRT x3, LG2 x3, RCP x4, SQRT x2 as well
 JAC_MUFU_OPS = {"ex2": 4, "rsqrt": 3, "lg2": 3, "rcp": 4, "sqrt": 2}
 # Per sample-channel evaluation: forward march 2 EX2 + 6 FP32 (three packed two-channel
-# instructions); in the adjoint the forward pass the same, the segment recompute 1 EX2 + 3 FP32,
-# the reverse pass 2 EX2 + 15 FP32
+# instructions); in the adjoint the forward pass the same, the reverse pass 2 EX2 + 15 FP32 (the
+# "rec" entries count a segment recompute, which the adjoint no longer runs: its counter is 0)
 EVAL_EX2 = {"fwd": 2, "rec": 1, "rev": 2}
 EVAL_FP32 = {"fwd": 6, "rec": 3, "rev": 15}
 try:
@@ -55,12 +55,13 @@ except (OSError, ValueError):
 # FLOPs of one network evaluation as the method defines it: 2 x (64x128 + 3x128x128 + 128x4)
 MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 4)
 # DRAM bytes of one forward launch on the observation-scale workload (ncu, dram__bytes_read +
-# dram__bytes_write of march_fwd_kernel<8,8,4>; the cube stays in L2 at the end of the launch)
-FWD_DRAM_BYTES = 3_329_280 + 29_184
+# dram__bytes_write of march_fwd_kernel<8,8,4> with the two-sample physics; the reads include
+# the ray setups the prep launch wrote; the cube stays in L2 at the end of the launch)
+FWD_DRAM_BYTES = 7_281_408 + 23_296
 # DRAM bytes (read + write) of one fused-adjoint launch on the same workload (ncu capture of
 # march_adj_kernel<8, 8, 5>: per-batch depth entries of the advanced channel pairs, 16 MiB
 # grid-copy budget)
-ADJ_DRAM_BYTES = 30_705_152 + 43_197_696
+ADJ_DRAM_BYTES = 30_820_608 + 44_011_520
 N_SM = 148
 E2E_STREAMS = 4  # streams of the end-to-end leg
 SM_MAX_MHZ = 2032.0
@@ -804,11 +805,10 @@ def run_ours(args):
                                 "traffic": ADJ_DRAM_BYTES,
                                 "note": "computed work of one step (rt_render_adjoint_work) / "
                                         "its time: MUFU slots = 2 EX2 per forward-pass and "
-                                        "reverse-pass evaluation + 1 per segment-recompute "
-                                        "evaluation + the physics of each gas sample twice "
-                                        "(forward pass; recompute with local derivatives); "
-                                        "FP32 ops = 6 + 3 + 15 per evaluation of the three "
-                                        "passes; peaks measured (pipe_peaks)"}},
+                                        "reverse-pass evaluation + the physics of each gas "
+                                        "sample twice (forward pass; reverse pass with local "
+                                        "derivatives); FP32 ops = 6 + 15 per evaluation of the "
+                                        "two passes; peaks measured (pipe_peaks)"}},
             "clocks": clocks,
         }
         out["plain_fp32"] = plain_leg(dev, flush, p, dd, value / world)

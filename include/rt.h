@@ -270,13 +270,15 @@ int rt_render_adjoint_work(const rt_grid *grid, const rt_fields *fields, const r
  *     checkpoints are written before they are read, the gradient copies are zeroed on
  *     `stream`), but calls whose kernels overlap on the GPU (different streams, or different
  *     host threads) race on the array: serialize them.
- *   - Checkpoints get at most 24 MiB of the array. When that cannot hold checkpoints for a
- *     full grid, fewer blocks are launched; where fewer gradient copies fit (or none: then
- *     the kernel adds straight into the FP64 output arrays), the sums run in another order.
- *     Same results up to that rounding (about 1e-7 of the largest gradient), lower
- *     throughput. A problem whose single block needs more than 24 MiB
- *     of checkpoints (above about 389,000 samples per ray at the earliest) is rejected with
- *     RT_EINVAL and a message naming the limit.
+ *   - Checkpoints (the optical depths the forward pass keeps at every batch boundary) get
+ *     at most 24 MiB of the array. When that cannot hold checkpoints for a full grid, fewer
+ *     blocks are launched; where fewer gradient copies fit (or none: then the kernel adds
+ *     straight into the FP64 output arrays), the sums run in another order. Same results up
+ *     to that rounding (about 1e-7 of the largest gradient), lower throughput. A problem
+ *     whose single block needs more than 24 MiB of checkpoints is rejected with RT_EINVAL and
+ *     a message naming the limit: above 24,526 samples per ray with up to 8 channels, 24,548
+ *     with 32, 49,052 with 9 to 16, 49,096 with 33 to 64, 98,104 with 17 to 31, 196,400 with
+ *     65 to 128 and 392,800 with 129 to 256.
  * Returns RT_OK, RT_EINVAL or RT_ECUDA.
  */
 int rt_render_adjoint_noalloc(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,

@@ -9,7 +9,8 @@
 // Samples advance in batches of 2 LPR: in the physics phase lane q evaluates the channel-
 // independent physics of samples kb+q and kb+LPR+q of its ray (fields, CO layer, Keplerian
 // velocity, line width, LTE source and opacity; two independent evaluations per lane for
-// instruction-level parallelism) once and publishes them in shared memory; in the channel
+// instruction-level parallelism, which the specialised modes issue as two-lane FP32
+// instructions, FFMA2 / FMUL2 / FADD2) once and publishes them in shared memory; in the channel
 // phase every lane walks the batch's samples in order, evaluating the Doppler-shifted Gaussian
 // profile and advancing optical depth, transmittance and intensity front to back (Eq. rt-int
 // with Eq. optical_depth; the source is constant over each segment).
@@ -45,9 +46,12 @@ constexpr float kWinLog2 = 40.0f;  // skipped optical depths are below 2^-40 per
 
 // Blocks per SM the register budget is sized for: 5 (at most 102 registers) with 8 channels
 // per lane, 6 with 4; 4 (128 registers) for the 3-D grids, whose sample physics holds 16
-// node records in flight.
+// node records in flight, and for the specialised modes, whose two-sample physics holds both
+// samples' corner quads and intermediates at once (spilled at 96 registers: 0.276 ms against
+// 0.255 ms at 128 on the observation-scale disk).
 template <int LPR, int CPL, int MODE>
-__global__ void __launch_bounds__(kWarps * 32, (MODE == 2 || MODE == 3) ? 4 : (CPL == 8 ? 5 : 6))
+__global__ void __launch_bounds__(kWarps * 32,
+                                  (MODE == 2 || MODE == 3 || MODE >= 4) ? 4 : (CPL == 8 ? 5 : 6))
     march_fwd_kernel(const __grid_constant__ MarchParams P, float *__restrict__ cube) {
   constexpr int R = 32 / LPR;  // rays marched together by one warp (one work unit)
   constexpr int G = 32 / R;    // work units whose ray setups are computed together
@@ -106,30 +110,36 @@ __global__ void __launch_bounds__(kWarps * 32, (MODE == 2 || MODE == 3) ? 4 : (C
       // the rays' gas sample ranges, marched from their first samples (klo) on
       const int nsamp = __reduce_max_sync(0xffffffffu, max(ray.khi - ray.klo + 1, 0));
       for (int kb = 0; kb < nsamp; kb += 2 * LPR) {
-        const float4 mine = march_physics<MODE>(P, s_tab, ray, ray.klo + kb + q);
-        const float4 mine2 = march_physics<MODE>(P, s_tab, ray, ray.klo + kb + LPR + q);
-        // channel window of a sample (empty without gas): fractional channel indices where
-        // kd 2^{-d^2} >= 2^-40; the lane votes with the union of its two samples' windows
-        auto window = [&](const float4 &m4, float &lo, float &hi) {
-          lo = 1e30f;
-          hi = -1e30f;
-          if (m4.x > 0.0f) {
-            const float w2 = kWinLog2 + lg2(m4.x);
-            if (w2 > 0.0f) {
-              const float ib = rcp(m4.z);
-              const float hw = sqa(w2) * ib;
-              const float vl = m4.y * ib;
-              const float e0 = (vl - hw - P.v0) * idv, e1 = (vl + hw - P.v0) * idv;
-              lo = fminf(e0, e1) - 0.01f;
-              hi = fmaxf(e0, e1) + 0.01f;
-            }
+        float4 mine, mine2;
+        if (MODE >= 4) {
+          // the specialised physics of both samples in two-lane arithmetic (same results)
+          sample_physics_x2<MODE == 5>(P, s_tab, ray, ray.klo + kb + q, ray.klo + kb + LPR + q,
+                                       mine, mine2);
+        } else {
+          mine = march_physics<MODE>(P, s_tab, ray, ray.klo + kb + q);
+          mine2 = march_physics<MODE>(P, s_tab, ray, ray.klo + kb + LPR + q);
+        }
+        // channel window of each sample (empty without gas): fractional channel indices where
+        // kd 2^{-d^2} >= 2^-40; the lane votes with the union of its two samples' windows.
+        // Both samples' bounds in two-lane arithmetic; a sample without gas (kd = 0) or whose
+        // window is empty (w2 <= 0) gives the empty range.
+        float clo = 1e30f, chi = -1e30f;
+        if (mine.x > 0.0f || mine2.x > 0.0f) {
+          const float2 w2 = __fadd2_rn(bc2(kWinLog2), make_float2(lg2(mine.x), lg2(mine2.x)));
+          const float2 ib = make_float2(rcp(mine.z), rcp(mine2.z));
+          const float2 hw = __fmul2_rn(make_float2(sqa(w2.x), sqa(w2.y)), ib);
+          const float2 vl = __fmul2_rn(make_float2(mine.y, mine2.y), ib);
+          const float2 e0 = __fmul2_rn(sub2(sub2(vl, hw), bc2(P.v0)), bc2(idv));
+          const float2 e1 = __fmul2_rn(sub2(__fadd2_rn(vl, hw), bc2(P.v0)), bc2(idv));
+          if (mine.x > 0.0f && w2.x > 0.0f) {
+            clo = fminf(e0.x, e1.x) - 0.01f;
+            chi = fmaxf(e0.x, e1.x) + 0.01f;
           }
-        };
-        float clo, chi, clo2, chi2;
-        window(mine, clo, chi);
-        window(mine2, clo2, chi2);
-        clo = fminf(clo, clo2);
-        chi = fmaxf(chi, chi2);
+          if (mine2.x > 0.0f && w2.y > 0.0f) {
+            clo = fminf(clo, fminf(e0.y, e1.y) - 0.01f);
+            chi = fmaxf(chi, fmaxf(e0.y, e1.y) + 0.01f);
+          }
+        }
         unsigned act = 0;
         if (windowed) {
 #pragma unroll

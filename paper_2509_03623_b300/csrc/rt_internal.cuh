@@ -616,6 +616,110 @@ __host__ __device__ inline bool spec_ok(const MarchParams &P) {
          P.v_uniform && P.dv != 0.0f && !P.no_window && !P.box && !P.sph;
 }
 
+// Two-lane FP32 arithmetic (FFMA2 / FMUL2 / FADD2: one instruction for two independent
+// operations, each rounded as its scalar form).
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float2 t) {
+  return __ffma2_rn(t, sub2(b, a), a);
+}
+
+// sample_physics<ROT, true> for two samples k0, k1 of one ray at once: the same operations in
+// the same order, the FP32 ones issued as two-lane instructions (the MUFU operations, the
+// clamps and the loads stay per sample), so each result is bit-identical to the scalar
+// form's. Both samples are evaluated when either has gas (the grid location clamps the cell
+// indices, so a sample without gas reads valid cells); a sample without gas returns
+// {0, 0, 1, 0}.
+template <bool ROT>
+__device__ __forceinline__ void sample_physics_x2(const MarchParams &P, const float *tab,
+                                                  const Ray &R, int k0, int k1, float4 &o0,
+                                                  float4 &o1) {
+  const float2 kf = make_float2((float)k0, (float)k1);
+  const float2 y = __fadd2_rn(__ffma2_rn(kf, bc2(R.dy), bc2(R.yb)),
+                              __ffma2_rn(kf, bc2(R.dy2), bc2(R.yb2)));
+  const float2 z = __fadd2_rn(__ffma2_rn(kf, bc2(R.dz), bc2(R.zb)),
+                              __ffma2_rn(kf, bc2(R.dz2), bc2(R.zb2)));
+  const float2 r2 = __ffma2_rn(bc2(R.x), bc2(R.x), __fmul2_rn(y, y));
+  const float2 zz = __fmul2_rn(z, z), lim = __fmul2_rn(bc2(P.zr_max2), r2);
+  const bool g0 = (r2.x >= P.r_in2) && (zz.x <= lim.x) && k0 <= R.khi;
+  const bool g1 = (r2.y >= P.r_in2) && (zz.y <= lim.y) && k1 <= R.khi;
+  o0 = o1 = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+  if (!(g0 || g1)) return;
+  // grid location (locate<true>)
+  const float2 ir = make_float2(rsq(r2.x), rsq(r2.y));
+  const float2 zr = __fmul2_rn(make_float2(fabsf(z.x), fabsf(z.y)), ir);
+  const float2 lr = __fmul2_rn(r2, bc2(P.inv_rin2));
+  float2 u = __fmul2_rn(make_float2(lg2(lr.x), lg2(lr.y)), bc2(P.lr_scale));
+  float2 w = __fmul2_rn(zr, bc2(P.w_scale));
+  const float umax = (float)(P.nr - 1), wmax = (float)(P.nz - 1);
+  u = make_float2(fminf(fmaxf(u.x, 0.0f), umax), fminf(fmaxf(u.y, 0.0f), umax));
+  w = make_float2(fminf(fmaxf(w.x, 0.0f), wmax), fminf(fmaxf(w.y, 0.0f), wmax));
+  const int ia0 = min((int)u.x, P.nr - 2), ia1 = min((int)u.y, P.nr - 2);
+  const int ja0 = min((int)w.x, P.nz - 2), ja1 = min((int)w.y, P.nz - 2);
+  const float2 fr = __fadd2_rn(u, make_float2(-(float)ia0, -(float)ia1));
+  const float2 fz = __fadd2_rn(w, make_float2(-(float)ja0, -(float)ja1));
+  // corner quads (fields_at<ROT, true>)
+  constexpr int NQ = ROT ? 4 : 3;
+  const float4 *qa = P.cell + NQ * ((long long)ja0 * (P.nr - 1) + ia0);
+  const float4 *qb = P.cell + NQ * ((long long)ja1 * (P.nr - 1) + ia1);
+  const float4 aT = __ldg(qa), an = __ldg(qa + 1), av = __ldg(qa + 2);
+  const float4 bT = __ldg(qb), bn = __ldg(qb + 1), bv = __ldg(qb + 2);
+  const float4 ah = __ldg(P.hcell + ia0), bh = __ldg(P.hcell + ia1);
+  auto qlerp = [&](const float4 &a, const float4 &b) {
+    const float2 lo = lerp2(make_float2(a.x, b.x), make_float2(a.y, b.y), fr);
+    const float2 hi = lerp2(make_float2(a.z, b.z), make_float2(a.w, b.w), fr);
+    return lerp2(lo, hi, fz);
+  };
+  const float2 T = qlerp(aT, bT), n = qlerp(an, bn), vt = qlerp(av, bv);
+  const float2 hlo = lerp2(make_float2(ah.x, bh.x), make_float2(ah.y, bh.y), fr);
+  const float2 hhi = lerp2(make_float2(ah.z, bh.z), make_float2(ah.w, bh.w), fr);
+  // logistic CO edges
+  const float2 xa = __fmul2_rn(sub2(hlo, zr), bc2(P.edge_k));
+  const float2 xb = __fmul2_rn(sub2(zr, hhi), bc2(P.edge_k));
+  const float2 ea = make_float2(ex2(xa.x), ex2(xa.y)), eb = make_float2(ex2(xb.x), ex2(xb.y));
+  const float2 den = __fmul2_rn(__fadd2_rn(bc2(1.0f), ea), __fadd2_rn(bc2(1.0f), eb));
+  const float2 X = __fmul2_rn(bc2(P.x_co), make_float2(rcp(den.x), rcp(den.y)));
+  // line-of-sight velocity
+  float2 vlos;
+  if (ROT) {
+    const float2 vp = qlerp(__ldg(qa + 3), __ldg(qb + 3));
+    vlos = __ffma2_rn(__fmul2_rn(vp, bc2(P.sin_if * R.x)), ir, bc2(P.vsys));
+  } else {
+    const float2 d2 = __ffma2_rn(z, z, r2);
+    float2 kq = make_float2(rsq(d2.x), rsq(d2.y));
+    const float2 h = __fmul2_rn(__fmul2_rn(bc2(-0.5f), d2), kq);
+    kq = __fmul2_rn(kq, __ffma2_rn(h, kq, bc2(1.5f)));
+    kq = __fmul2_rn(kq, make_float2(sqa(kq.x), sqa(kq.y)));
+    vlos = __ffma2_rn(bc2(R.vfac), kq, bc2(P.vsys));
+  }
+  // line physics (line_tail<true>)
+  const float2 Tg = make_float2(fmaxf(T.x, 1e-3f), fmaxf(T.y, 1e-3f));
+  const float2 a2 = __ffma2_rn(bc2(P.c_th), Tg, __fmul2_rn(vt, vt));
+  const float2 ia = make_float2(rsq(a2.x), rsq(a2.y));
+  float2 xt = __fmul2_rn(make_float2(lg2(Tg.x), lg2(Tg.y)), bc2(kTabInvH));
+  xt = make_float2(fminf(fmaxf(xt.x, 0.0f), (float)kTabSeg),
+                   fminf(fmaxf(xt.y, 0.0f), (float)kTabSeg));
+  const int ta = min((int)xt.x, kTabSeg - 1), tb = min((int)xt.y, kTabSeg - 1);
+  const float2 f = __fadd2_rn(xt, make_float2(-(float)ta, -(float)tb));
+  const float4 ca = reinterpret_cast<const float4 *>(tab)[ta];
+  const float4 cb = reinterpret_cast<const float4 *>(tab)[tb];
+  float2 phi = __ffma2_rn(f, make_float2(ca.w, cb.w), make_float2(ca.z, cb.z));
+  phi = __ffma2_rn(f, phi, make_float2(ca.y, cb.y));
+  phi = __ffma2_rn(f, phi, make_float2(ca.x, cb.x));
+  const float2 es = __fmul2_rn(bc2(-P.theta_s), make_float2(rcp(Tg.x), rcp(Tg.y)));
+  const float2 eS = make_float2(ex2(es.x), ex2(es.y));
+  const float2 om = __fadd2_rn(bc2(1.0f), neg2(eS));
+  const float2 S = __fmul2_rn(eS, make_float2(rcp(om.x), rcp(om.y)));
+  float2 kd = __fmul2_rn(bc2(P.kappa_k), __fmul2_rn(X, n));
+  kd = __fmul2_rn(__fmul2_rn(__fmul2_rn(kd, make_float2(ex2(phi.x), ex2(phi.y))), ia),
+                  bc2(R.ds));
+  const float2 b = __fmul2_rn(ia, bc2(1.2011224087864498f));
+  const float2 a = __fmul2_rn(vlos, b);
+  if (g0) o0 = make_float4(kd.x, a.x, b.x, S.x);
+  if (g1) o1 = make_float4(kd.y, a.y, b.y, S.y);
+}
+
 // Sample physics on a 3-D Cartesian grid (rt_render3d): trilinear interpolation of the
 // packed node records {T, n, vt, x_co} and {vx, vy, vz, 0} (16 loads of 16 bytes), the
 // line-of-sight velocity omega . v + v_sys with omega = (0, sin i, -cos i), then the line
