@@ -162,31 +162,52 @@ __global__ void __launch_bounds__(kWarps * 32,
         ph0[rr * kPhStride + LPR + q] = make_float4(-mine2.x, -mine2.x, mine2.w, mine2.w);
         ph1[rr * kPhStride + LPR + q] = make_float4(mine2.z, mine2.z, -mine2.y, -mine2.y);
         __syncwarp();
-#pragma unroll
-        for (int m = 0; m < H; m++) {
-          if (!(act & (1u << m))) continue;  // warp-uniform: block m outside every window
-          // every sample of the batch in order; samples without gas are exact no-ops
-#pragma unroll
-          for (int t = 0; t < 2 * LPR; t++) {
-            const float4 p0 = ph0[rr * kPhStride + t];
-            const float4 p1 = ph1[rr * kPhStride + t];
-            const float2 nkd = make_float2(p0.x, p0.y), S = make_float2(p0.z, p0.w);
-            const float2 b = make_float2(p1.x, p1.y), na = make_float2(p1.z, p1.w);
-            const float2 d = __ffma2_rn(vp[m], b, na);  // (v_c - v_los) / alpha (scaled)
-            const float2 d2 = __fmul2_rn(d, d);
-            const float2 gp = make_float2(ex2(-d2.x), ex2(-d2.y));
-            nl[m] = __ffma2_rn(nkd, gp, nl[m]);
-            const float2 nt = __fadd2_rn(nb[m], nl[m]);
-            const float2 Tn = make_float2(ex2(nt.x), ex2(nt.y));
-            const float2 df = __ffma2_rn(Tn, mone, Tr[m]);  // T_k - T_{k+1}
-            I[m] = __ffma2_rn(S, df, I[m]);
-            Tr[m] = Tn;
-          }
-          // compensated fold of the batch into the base (Kahan): nl carries the batch sum
-          // minus the base's rounding error left by the previous fold
+        // one sample of the batch in channel block m: profile, optical depth, transmittance
+        // and intensity (samples without gas are exact no-ops)
+        auto step = [&](int m, const float4 &p0, const float4 &p1) __attribute__((always_inline)) {
+          const float2 nkd = make_float2(p0.x, p0.y), S = make_float2(p0.z, p0.w);
+          const float2 b = make_float2(p1.x, p1.y), na = make_float2(p1.z, p1.w);
+          const float2 d = __ffma2_rn(vp[m], b, na);  // (v_c - v_los) / alpha (scaled)
+          const float2 d2 = __fmul2_rn(d, d);
+          const float2 gp = make_float2(ex2(-d2.x), ex2(-d2.y));
+          nl[m] = __ffma2_rn(nkd, gp, nl[m]);
+          const float2 nt = __fadd2_rn(nb[m], nl[m]);
+          const float2 Tn = make_float2(ex2(nt.x), ex2(nt.y));
+          const float2 df = __ffma2_rn(Tn, mone, Tr[m]);  // T_k - T_{k+1}
+          I[m] = __ffma2_rn(S, df, I[m]);
+          Tr[m] = Tn;
+        };
+        // compensated fold of the batch into the base (Kahan): nl carries the batch sum minus
+        // the base's rounding error left by the previous fold
+        auto fold = [&](int m) __attribute__((always_inline)) {
           const float2 t = __fadd2_rn(nb[m], nl[m]);
           nl[m] = __ffma2_rn(__ffma2_rn(nb[m], mone, t), mone, nl[m]);
           nb[m] = t;
+        };
+        // the active blocks (warp-uniform), two adjacent ones in one pass over the batch's
+        // samples: each sample's records are read once for both, and the two blocks' chains
+        // interleave; every channel sees the same operations in the same order either way
+        unsigned rem = act;
+#pragma unroll
+        for (int m = 0; m < H; m++) {
+          if (!(rem & (1u << m))) continue;  // block m outside every window
+          if (m + 1 < H && (rem & (2u << m))) {
+            rem &= ~(2u << m);
+#pragma unroll
+            for (int t = 0; t < 2 * LPR; t++) {
+              const float4 p0 = ph0[rr * kPhStride + t];
+              const float4 p1 = ph1[rr * kPhStride + t];
+              step(m, p0, p1);
+              step(m + 1 < H ? m + 1 : m, p0, p1);
+            }
+            fold(m);
+            fold(m + 1 < H ? m + 1 : m);
+          } else {
+#pragma unroll
+            for (int t = 0; t < 2 * LPR; t++)
+              step(m, ph0[rr * kPhStride + t], ph1[rr * kPhStride + t]);
+            fold(m);
+          }
         }
         __syncwarp();
       }
