@@ -55,9 +55,10 @@ except (OSError, ValueError):
 # FLOPs of one network evaluation as the method defines it: 2 x (64x128 + 3x128x128 + 128x4)
 MLP_FLOP = 2 * (64 * 128 + 3 * 128 * 128 + 128 * 4)
 # DRAM bytes of one forward launch on the observation-scale workload (ncu, dram__bytes_read +
-# dram__bytes_write of march_fwd_kernel<8,8,4> with the two-sample physics; the reads include
+# dram__bytes_write of march_fwd_kernel<8,8,4> with the two-sample physics and the two-block
+# channel pass; the reads include
 # the ray setups the prep launch wrote; the cube stays in L2 at the end of the launch)
-FWD_DRAM_BYTES = 7_281_408 + 23_296
+FWD_DRAM_BYTES = 7_280_896 + 24_064
 # DRAM bytes (read + write) of one fused-adjoint launch on the same workload (ncu capture of
 # march_adj_kernel<8, 8, 5>: per-batch depth entries of the advanced channel pairs, 16 MiB
 # grid-copy budget)
