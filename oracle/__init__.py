@@ -110,6 +110,7 @@ def _load():
             lib.orc_partition.restype = C.c_double
             lib.orc_render_adjoint.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
             lib.orc_render_adjoint_vphi.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
+            lib.orc_render_adjoint3.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
             lib.orc_mlp_eval.argtypes = [C.POINTER(_MLP), dp, C.c_int, dp]
             lib.orc_mlp_grad.argtypes = [C.POINTER(_MLP), dp, dp, C.c_int, dp, dp]
             lib.orc_render_mlp.argtypes = [pp, C.POINTER(_MLP), C.POINTER(C.c_longlong),
@@ -294,6 +295,24 @@ def render_adjoint_vphi(p, dL_dcube: np.ndarray, nthreads: int = 0):
     if rc:
         raise ValueError("oracle: invalid problem (a rotation field is required)")
     return cube, dict(T=dT, n_h2=dn, vturb=dvt, h_lo=dlo, h_hi=dhi, vphi=dvp)
+
+
+def render_adjoint3(p, dL_dcube: np.ndarray, nthreads: int = 0):
+    """Reverse mode of the 3-D Cartesian grid march (p.g3): (cube, grads) with grads a dict of
+    T, n_h2, vturb, x_co, vx, vy, vz, each [nz][ny][nx] like the grid's fields."""
+    lib = _load()
+    pk = _Packed(p)
+    g3 = p.g3
+    g = np.ascontiguousarray(np.asarray(dL_dcube, dtype=np.float64))
+    cube = np.zeros((pk.nch, int(p.ny), int(p.nx)), dtype=np.float64)
+    shp = (int(g3.nz), int(g3.ny), int(g3.nx))
+    keys = ("T", "n_h2", "vturb", "x_co", "vx", "vy", "vz")
+    out = {k: np.zeros(shp) for k in keys}
+    rc = lib.orc_render_adjoint3(C.byref(pk.s), _dptr(g), _dptr(cube),
+                                 *[_dptr(out[k]) for k in keys], _threads(nthreads))
+    if rc:
+        raise ValueError("oracle: invalid problem (a 3-D Cartesian grid is required)")
+    return cube, out
 
 
 def mlp_eval(w, x: np.ndarray) -> np.ndarray:

@@ -210,6 +210,10 @@ typedef struct {
   double xin[2], o[4], mT, mn;
   /* d v_los / d(rotation-field value) [cm/s per km/s] with a rotation field, 0 otherwise */
   double dvlos_dvphi;
+  /* 3-D Cartesian grid: the cell (lowest node index per axis) and the fractional position in
+     it, as the trilinear interpolation used them */
+  int i3[3];
+  double f3[3];
 } pt;
 
 static double bilerp(const double *F, int nr, int i0, int j0, double fr, double fz) {
@@ -305,6 +309,10 @@ static void eval_point(const orc_problem *p, const orc_mlp *m, const double P[3]
         acc += w * F[q][((long long)(i3[2] + dz) * g->ny + (i3[1] + dy)) * g->nx + (i3[0] + dx)];
       }
       val[q] = acc;
+    }
+    for (int a = 0; a < 3; a++) {
+      st->i3[a] = i3[a];
+      st->f3[a] = f[a];
     }
     st->T = val[0];
     st->n = val[1];
@@ -577,6 +585,9 @@ typedef struct {
   double *gT, *gn, *gvt, *ghlo, *ghhi;
   double *gW, *gb; /* network parameters, flat in layer order (NULL without a network) */
   double *gvphi;   /* rotation field (NULL without one) */
+  /* 3-D Cartesian grid: abundance and velocity fields (gT, gn, gvt then hold the grid's
+     nodes as well; ghlo, ghhi are unused) */
+  double *gxco, *gvx, *gvy, *gvz;
 } grads;
 
 static void mlp_backward(const orc_mlp *m, const double xin[2], const double *gout,
@@ -685,6 +696,27 @@ static void adjoint_pixel(const orc_problem *p, const orc_mlp *m, int ix, int iy
     double gvt = galpha * dadvt;
     /* n_CO = X n */
     double gX = gnco * q->n, gn = gnco * q->X;
+    if (p->g3) {
+      /* 3-D grid: every field is interpolated trilinearly, X is a field of its own and
+         v_los = 1e5 (omega . v) + v_sys (v in km/s); the weight of corner (dx, dy, dz) is the
+         product of f or 1 - f along each axis */
+      const orc_grid3 *g3 = p->g3;
+      for (int c8 = 0; c8 < 8; c8++) {
+        int dx = c8 & 1, dy = (c8 >> 1) & 1, dz = c8 >> 2;
+        double w = (dx ? q->f3[0] : 1.0 - q->f3[0]) * (dy ? q->f3[1] : 1.0 - q->f3[1]) *
+                   (dz ? q->f3[2] : 1.0 - q->f3[2]);
+        long long id = ((long long)(q->i3[2] + dz) * g3->ny + (q->i3[1] + dy)) * g3->nx +
+                       (q->i3[0] + dx);
+        g->gT[id] += gT * w;
+        g->gn[id] += gn * w;
+        g->gvt[id] += gvt * w;
+        g->gxco[id] += gX * w;
+        g->gvx[id] += gvlos * 1e5 * om[0] * w;
+        g->gvy[id] += gvlos * 1e5 * om[1] * w;
+        g->gvz[id] += gvlos * 1e5 * om[2] * w;
+      }
+      continue;
+    }
     double ghlo = 0.0, ghhi = 0.0;
     if (p->edge_w > 0) {
       ghlo = gX * p->x_co * q->sb * q->sa * (1.0 - q->sa) * (-1.0 / p->edge_w);
@@ -836,6 +868,60 @@ int orc_render_adjoint_vphi(const orc_problem *p, const double *dL_dcube, double
   if (!p || !p->vphi || !dvphi) return -1;
   return render_adjoint_impl(p, NULL, dL_dcube, cube, dT, dn, dvt, dh_lo, dh_hi, NULL, NULL,
                              dvphi, nthreads);
+}
+
+int orc_render_adjoint3(const orc_problem *p, const double *dL_dcube, double *cube, double *dT,
+                        double *dn, double *dvt, double *dxco, double *dvx, double *dvy,
+                        double *dvz, int nthreads) {
+  if (!p || !p->g3 || p->gs || check(p) || !dL_dcube) return -1;
+  const orc_grid3 *g3 = p->g3;
+  long long G = (long long)g3->nx * g3->ny * g3->nz;
+  long long npix = (long long)p->nx * p->ny;
+  double *out[7] = {dT, dn, dvt, dxco, dvx, dvy, dvz};
+  for (int a = 0; a < 7; a++) memset(out[a], 0, sizeof(double) * G);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+  {
+    grads g;
+    memset(&g, 0, sizeof(g));
+    double *acc[7];
+    for (int a = 0; a < 7; a++) acc[a] = (double *)calloc(G, sizeof(double));
+    g.gT = acc[0];
+    g.gn = acc[1];
+    g.gvt = acc[2];
+    g.gxco = acc[3];
+    g.gvx = acc[4];
+    g.gvy = acc[5];
+    g.gvz = acc[6];
+    double *gout = (double *)malloc(sizeof(double) * (p->nch > 0 ? p->nch : 1));
+    double *I = (double *)malloc(sizeof(double) * (p->nch > 0 ? p->nch : 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+    for (int iy = 0; iy < p->ny; iy++) {
+      for (int ix = 0; ix < p->nx; ix++) {
+        long long pix = (long long)iy * p->nx + ix;
+        for (int c = 0; c < p->nch; c++) gout[c] = dL_dcube[c * npix + pix];
+        adjoint_pixel(p, NULL, ix, iy, gout, I, &g);
+        if (cube)
+          for (int c = 0; c < p->nch; c++) cube[c * npix + pix] = I[c];
+      }
+    }
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+    {
+      for (int a = 0; a < 7; a++)
+        for (long long i = 0; i < G; i++) out[a][i] += acc[a][i];
+    }
+    for (int a = 0; a < 7; a++) free(acc[a]);
+    free(gout);
+    free(I);
+  }
+  (void)nthreads;
+  return 0;
 }
 
 int orc_render_mlp_adjoint(const orc_problem *p, const orc_mlp *m, const double *dL_dcube,
