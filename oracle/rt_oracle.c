@@ -671,18 +671,18 @@ static void adjoint_pixel(const orc_problem *p, const orc_mlp *m, int ix, int iy
       gvlos += g_phi * phi[k * C + c] * (-2.0 * xx) / q->alpha;
     }
     if (!q->gas) continue;
-    /* S = A_ul n_u / D (both populations scale with n_CO, which cancels) */
-    double gnu = gS * p->A_ul / q->D - gD * Bul;
-    double gnl = gD * Blu;
-    double gD_from_S = -gS * p->A_ul * q->nu_ / (q->D * q->D);
-    gnu += -gD_from_S * Bul;
-    gnl += gD_from_S * Blu;
-    /* n_u = n_CO f_u(T), n_l = n_CO f_l(T), f_J = g_J exp(-E_J/kT)/Z */
+    /* D = n_CO Du with Du = f_l B_lu - f_u B_ul, and S = A_ul n_u / D = A_ul f_u / Du: the
+       source does not depend on n_CO (it cancels), so dL/dn_CO = gD Du, and through
+       f_J = g_J exp(-E_J/kT)/Z(T)
+         dS/dT = A_ul B_lu (f_l f_u' - f_u f_l') / Du^2,  dD/dT = n_CO (B_lu f_l' - B_ul f_u')
+       (written without dividing by D, which underflows where n_CO does) */
     double kT2 = K_BOLTZ * q->T * q->T;
     double Em = mean_energy(q->T, B);
     double dfu = q->fu * (Eu - Em) / kT2, dfl = q->fl * (El - Em) / kT2;
-    double gnco = gnu * q->fu + gnl * q->fl;
-    double gT = q->nco * (gnu * dfu + gnl * dfl);
+    double Du = q->fl * Blu - q->fu * Bul;
+    double gnco = gD * Du;
+    double dSdT = p->A_ul * Blu * (q->fl * dfu - q->fu * dfl) / (Du * Du);
+    double gT = gS * dSdT + gD * q->nco * (Blu * dfl - Bul * dfu);
     /* alpha */
     double dadT, dadvt;
     if (p->vturb_mach) {
