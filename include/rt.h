@@ -375,6 +375,41 @@ typedef struct {
 int rt_render3d(const rt_grid3 *grid3, const rt_fields3 *fields3, const rt_geom *geom,
                 const rt_view *view, const rt_line *line, float *cube, void *stream);
 
+/* Gradient outputs of rt_render3d_adjoint: DEVICE float64 arrays [nz][ny][nx] (x fastest,
+   like the fields of rt_fields3), overwritten by the call. */
+typedef struct {
+  double *dT;      /* dL/dT_K */
+  double *dn_h2;   /* dL/dn_h2_cm3 */
+  double *dvturb;  /* dL/dvturb (per the vturb input's unit) */
+  double *dx_co;   /* dL/dx_co */
+  double *dvx;     /* dL/dvx_kms: zero (v_los = omega . v has no x component) */
+  double *dvy;     /* dL/dvy_kms (per km/s) */
+  double *dvz;     /* dL/dvz_kms (per km/s) */
+  double *loss;    /* 1 value: sum over voxels of (cube - target)^2 when a target is given;
+                      may be NULL */
+} rt_grads3;
+
+/*
+ * rt_render3d_adjoint -- fused reverse mode of rt_render3d: the gradient of a scalar loss L
+ * with respect to every node of the seven fields of a 3-D Cartesian grid (the reverse march
+ * of Eq. rt-int / Eq. optical_depth, as rt_render_adjoint, differentiated through the
+ * trilinear interpolation; RadJAX obtains these gradients by automatic differentiation:
+ * Methods, "Line Radiative Transfer with RadJAX"). Inputs as rt_render3d. Give exactly one of
+ *   dL_dcube  DEVICE [nch][ny][nx] float32: dL/dcube of the caller's loss, or
+ *   target    DEVICE [nch][ny][nx] float32: L = sum (cube - target)^2, formed in the kernel.
+ * cube_out: DEVICE [nch][ny][nx] float32 receiving the rendered cube (may be NULL).
+ * grads: outputs (rt_grads3), all seven arrays required; loss optional.
+ * The call allocates (stream-ordered, freed after the launch) the node records (32 bytes per
+ * node), one FP32 gradient copy (24 bytes per node) and the per-warp optical depths the
+ * forward pass keeps at every batch boundary; node gradients are FP32 sums per node, written
+ * out in FP64.
+ * Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
+ */
+int rt_render3d_adjoint(const rt_grid3 *grid3, const rt_fields3 *fields3, const rt_geom *geom,
+                        const rt_view *view, const rt_line *line, const float *dL_dcube,
+                        const float *target, float *cube_out, const rt_grads3 *grads,
+                        void *stream);
+
 /*
  * rt_render_sph -- forward march through a 3-D spherical grid centred on the star. RadJAX
  * runs on regularly or log-spaced Cartesian or spherical grids (Methods, "Line Radiative

@@ -89,6 +89,12 @@ class rt_fields3(C.Structure):
                 ("vz_kms", C.c_void_p), ("vturb_mach", C.c_int)]
 
 
+class rt_grads3(C.Structure):
+    _fields_ = [("dT", C.c_void_p), ("dn_h2", C.c_void_p), ("dvturb", C.c_void_p),
+                ("dx_co", C.c_void_p), ("dvx", C.c_void_p), ("dvy", C.c_void_p),
+                ("dvz", C.c_void_p), ("loss", C.c_void_p)]
+
+
 class rt_grid_sph(C.Structure):
     _fields_ = [("nr", C.c_int), ("nth", C.c_int), ("nph", C.c_int), ("r_log", C.c_int),
                 ("r_in_au", C.c_double), ("r_out_au", C.c_double), ("th0_rad", C.c_double),
@@ -171,6 +177,10 @@ def lib():
             L.rt_render3d.argtypes = [P(rt_grid3), P(rt_fields3), P(rt_geom), P(rt_view),
                                       P(rt_line), C.c_void_p, C.c_void_p]
             L.rt_render3d.restype = C.c_int
+            L.rt_render3d_adjoint.argtypes = [P(rt_grid3), P(rt_fields3), P(rt_geom),
+                                              P(rt_view), P(rt_line), C.c_void_p, C.c_void_p,
+                                              C.c_void_p, P(rt_grads3), C.c_void_p]
+            L.rt_render3d_adjoint.restype = C.c_int
             L.rt_render_sph.argtypes = [P(rt_grid_sph), P(rt_fields_sph), P(rt_geom),
                                         P(rt_view), P(rt_line), C.c_void_p, C.c_void_p]
             L.rt_render_sph.restype = C.c_int
@@ -624,6 +634,42 @@ def rt_render3d(problem, grid=None, out=None, stream=None):
     check(lib().rt_render3d(C.byref(gg), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
                             _ptr(out), stream_handle(stream)))
     return out
+
+
+def rt_render3d_adjoint(problem, grid=None, dL_dcube=None, target=None, cube_out=True,
+                        stream=None):
+    """Fused forward + reverse march through a 3-D Cartesian grid (problem.g3), through the C
+    ABI. Give exactly one of dL_dcube or target (loss = sum (cube - target)^2). Returns
+    (cube or None, grads) with grads a dict of float64 CUDA tensors T, n_h2, vturb, x_co, vx,
+    vy, vz [nz][ny][nx] and loss (1 element)."""
+    import torch
+    g3 = problem.g3
+    dg = grid if grid is not None else DeviceGrid3(problem)
+    shp = (int(g3.nz), int(g3.ny), int(g3.nx))
+    for k in DeviceGrid3.FIELDS:
+        t = getattr(dg, k)
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shp:
+            raise ValueError(f"3-D field {k} must be a contiguous CUDA float32 tensor of shape {shp}")
+    gg = rt_grid3(*shp[::-1], *(float(v) for v in g3.extent))
+    f = rt_fields3(*(getattr(dg, k).data_ptr() for k in DeviceGrid3.FIELDS),
+                   int(problem.vturb_mach))
+    o, v, vw, ln = _view_line_geom(problem)
+    cshape = (vw.nch, vw.ny, vw.nx)
+    dL_dcube = _cube_arg(dL_dcube, cshape, "dL_dcube")
+    target = _cube_arg(target, cshape, "target")
+    dev = dg.T.device
+    cube = None
+    if cube_out is True:
+        cube = torch.empty(cshape, dtype=torch.float32, device=dev)
+    elif cube_out is not None and cube_out is not False:
+        cube = _cube_arg(cube_out, cshape, "cube_out")
+    out = {k: torch.empty(shp, dtype=torch.float64, device=dev) for k in DeviceGrid3.FIELDS}
+    out["loss"] = torch.empty(1, dtype=torch.float64, device=dev)
+    gr = rt_grads3(*(out[k].data_ptr() for k in DeviceGrid3.FIELDS), out["loss"].data_ptr())
+    check(lib().rt_render3d_adjoint(C.byref(gg), C.byref(f), C.byref(o), C.byref(vw),
+                                    C.byref(ln), _ptr(dL_dcube), _ptr(target), _ptr(cube),
+                                    C.byref(gr), stream_handle(stream)))
+    return cube, out
 
 
 class DeviceMLP:

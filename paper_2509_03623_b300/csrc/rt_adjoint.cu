@@ -63,6 +63,15 @@ __host__ __device__ constexpr int adj_batches(int n_samples) {
   return (n_samples + LPR - 1) / LPR;
 }
 constexpr float kLn2 = 0.6931471805599453f;
+// Cap on one sample's optical-depth increment in one channel (log2 units). Behind an increment
+// of 128 the transmittance is below 2^-128, which ex2.approx.ftz returns as 0, so capping
+// changes no transmittance, no intensity and no gradient term (every term behind the sample
+// carries that zero). It bounds a batch's depth range by LPR x 128, so the depths the reverse
+// pass rebuilds by subtracting increments from a batch end keep an absolute error of a few
+// 1e-5: without it one optically very thick sample (increments of 1e5 in a dense midplane)
+// left ulp(1e5) ~ 1e-2 of error in the depths in front of it. Both passes form each increment
+// as the rounded product kd g, capped, so the reverse subtracts exactly what the forward added.
+constexpr float kDtCap = 128.0f;
 
 // Per-sample local derivatives kept in shared memory between the physics and the chain rule.
 enum {
@@ -180,6 +189,105 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   out.x = P.kappa_k * (X * n) * F * ia * R.ds;
   out.z = ia * 1.2011224087864498f;  // b = sqrt(log2 e) / alpha
   out.y = vlos * out.z;              // a = v_los b
+  out.w = eS * om;
+  return out;
+}
+
+// physics_jac on the 3-D Cartesian grid (rt_render3d): sample_physics_box's arithmetic for
+// {kd, a, b, S} (bit-identical, which the reverse pass's rebuilt depths rely on) and the local
+// derivatives, in physics_jac's slots where they mean the same (J_KDN, J_DPHI, J_QT, J_QV,
+// J_DS); J_SA holds dkd/dX (the CO abundance is a field of its own), J_FR, J_FZ, J_I0 the
+// trilinear weights along x, y, z and J_CELL the cell's lowest node index. Zeros without gas.
+__device__ __forceinline__ float4 physics_jac_box(const MarchParams &P, const float *tab,
+                                                  const Ray &R, int k, float4 *rec) {
+  const float kf = (float)k;
+  const float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
+  const float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
+  if (!(k <= R.khi)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  auto axis = [](float pos, float c, float s, int k, int n, int &i, float &w) {
+    const float f = (pos - c) * s;
+    const float fl = floorf(f);
+    i = k + (int)fl;
+    w = f - fl;
+    if (i < 0) {
+      i = 0;
+      w = 0.0f;
+    } else if (i > n - 2) {
+      i = n - 2;
+      w = 1.0f;
+    }
+  };
+  int ix, iy, iz;
+  float wx, wy, wz;
+  axis(R.x, P.g3cx, P.g3sx, P.g3kx, P.n3x, ix, wx);
+  axis(y, P.g3cy, P.g3sy, P.g3ky, P.n3y, iy, wy);
+  axis(z, P.g3cz, P.g3sz, P.g3kz, P.n3z, iz, wz);
+  const long long sy = P.n3x, sz = (long long)P.n3x * P.n3y;
+  const long long b = iz * sz + iy * sy + ix;
+  const long long o[8] = {b, b + 1, b + sy, b + sy + 1, b + sz, b + sz + 1, b + sz + sy,
+                          b + sz + sy + 1};
+  float4 a[8], v[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    a[c] = __ldg(P.node_a + o[c]);
+    v[c] = __ldg(P.node_b + o[c]);
+  }
+  auto tri = [&](float f0, float f1, float f2, float f3, float f4, float f5, float f6, float f7) {
+    const float x0 = lerpf(f0, f1, wx), x1 = lerpf(f2, f3, wx);
+    const float x2 = lerpf(f4, f5, wx), x3 = lerpf(f6, f7, wx);
+    return lerpf(lerpf(x0, x1, wy), lerpf(x2, x3, wy), wz);
+  };
+  const float T = tri(a[0].x, a[1].x, a[2].x, a[3].x, a[4].x, a[5].x, a[6].x, a[7].x);
+  const float n = tri(a[0].y, a[1].y, a[2].y, a[3].y, a[4].y, a[5].y, a[6].y, a[7].y);
+  const float vt = tri(a[0].z, a[1].z, a[2].z, a[3].z, a[4].z, a[5].z, a[6].z, a[7].z);
+  const float X = tri(a[0].w, a[1].w, a[2].w, a[3].w, a[4].w, a[5].w, a[6].w, a[7].w);
+  const float vy = tri(v[0].y, v[1].y, v[2].y, v[3].y, v[4].y, v[5].y, v[6].y, v[7].y);
+  const float vz = tri(v[0].z, v[1].z, v[2].z, v[3].z, v[4].z, v[5].z, v[6].z, v[7].z);
+  if (!(X * n > 0.0f)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float vlos = fmaf(P.sin_if, vy, fmaf(-P.cos_if, vz, P.vsys));
+  // line physics (line_tail's arithmetic) with its derivatives (as physics_jac)
+  const bool clampT = T < 1e-3f;
+  const float Tg = fmaxf(T, 1e-3f);
+  float a2, da2T, da2v;
+  if (P.vturb_mach) {
+    const float m = fmaf(P.c_mach, vt * vt, P.c_th);
+    a2 = Tg * m;
+    da2T = m;
+    da2v = Tg * P.c_mach * 2.0f * vt;
+  } else {
+    a2 = fmaf(P.c_th, Tg, vt * vt);
+    da2T = P.c_th;
+    da2v = 2.0f * vt;
+  }
+  const float ia = rsq(a2);
+  float dphi;
+  const float phi = lte_phi(tab, lg2(Tg), &dphi);
+  const float iT = rcp(Tg);
+  const float eS = ex2(-P.theta_s * iT);
+  const float om = rcp(1.0f - eS);
+  const float F = ex2(phi);
+  const float q = -0.5f * ia * ia;
+  float J[12];
+  J[J_KDN] = P.kappa_k * X * F * ia * R.ds;
+  J[J_DPHI] = clampT ? 0.0f : dphi * iT;
+  J[J_QT] = clampT ? 0.0f : q * da2T;
+  J[J_QV] = q * da2v;
+  J[J_DS] = clampT ? 0.0f : eS * om * om * kLn2 * P.theta_s * iT * iT;
+  J[J_SA] = P.kappa_k * n * F * ia * R.ds;  // dkd/dX
+  J[J_SB] = 0.0f;
+  J[J_FR] = wx;
+  J[J_FZ] = wy;
+  J[J_CELL] = __int_as_float((int)b);
+  J[J_I0] = wz;
+  J[J_MT] = 1.0f;
+  static_assert(J_MT == 11 && J_I0 == 10 && J_CELL == 9, "box entries in the first 12 slots");
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+    rec[(i + 1) * 32] = make_float4(J[4 * i], J[4 * i + 1], J[4 * i + 2], J[4 * i + 3]);
+  float4 out;
+  out.x = P.kappa_k * (X * n) * F * ia * R.ds;
+  out.z = ia * 1.2011224087864498f;
+  out.y = vlos * out.z;
   out.w = eS * om;
   return out;
 }
@@ -320,18 +428,73 @@ __device__ __forceinline__ float scatter_grad(const MarchParams &P, const float 
   return dm;
 }
 
+// Chain rule of one sample on the 3-D Cartesian grid (physics_jac_box's entries): dL/d of T,
+// n_H2, v_turb and the CO abundance as a float4 per node and dL/dv_los as the first entry of
+// a float2 per node (the velocity components' gradients are sin i and -cos i times it,
+// formed when the copy is summed), each spread over the cell's 8 corners with the trilinear
+// weights: 8 16-byte and 8 8-byte FP32 reductions into the block's copy.
+__device__ __forceinline__ void scatter_box(const MarchParams &P, const float *J, float kd,
+                                            float b, float ax, float ay, float az, float aS,
+                                            const GradSink &G) {
+  const float gx = -kLn2 * ax;                    // dL/dkd
+  const float GB = 2.0f * kLn2 * kLn2 * kd * ay;  // b dL/db
+  const float gk = fmaf(gx, kd, GB);
+  const float gT = fmaf(gx * kd, J[J_DPHI], fmaf(gk, J[J_QT], aS * J[J_DS]));
+  const float gv = gk * J[J_QV];
+  const float gn = gx * J[J_KDN];
+  const float gX = gx * J[J_SA];
+  const float gl = -2.0f * kLn2 * kLn2 * kd * b * az;  // dL/dv_los
+  const float wx = J[J_FR], wy = J[J_FZ], wz = J[J_I0];
+  const long long b0 = __float_as_int(J[J_CELL]);
+  const long long sy = P.n3x, sz = (long long)P.n3x * P.n3y;
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) *
+                    ((c & 4) ? wz : 1.0f - wz);
+    const long long id = b0 + (c & 1) + ((c >> 1) & 1) * sy + (c >> 2) * sz;
+    atomicAdd(G.g + id, make_float4(gT * w, gn * w, gv * w, gX * w));
+    atomicAdd(G.h + id, make_float2(gl * w, 0.0f));
+  }
+}
+
+// Sums of the 3-D grid's gradient copy (one copy) in FP64: {dT, dn, dvt, dX} per node and
+// dL/dv_los, whose share of the velocity components is omega = (0, sin i, -cos i).
+__global__ void box_grads_kernel(const float4 *__restrict__ g4, const float2 *__restrict__ g2,
+                                 long long n, double sin_i, double cos_i, rt_grads3 G) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float4 v = g4[i];
+    const double l = g2[i].x;
+    G.dT[i] = v.x;
+    G.dn_h2[i] = v.y;
+    G.dvturb[i] = v.z;
+    G.dx_co[i] = v.w;
+    G.dvx[i] = 0.0;
+    G.dvy[i] = l * sin_i;
+    G.dvz[i] = -l * cos_i;
+  }
+}
+
 // Channel window (as in the forward march): slot j of every lane is the channel block
 // [LPR j, LPR j + LPR); bit j is set when some sample of the warp's batch has
 // kd 2^{-d^2} >= 2^-40 in a channel of the block. Without equally spaced channels every block
 // of a batch with gas is set. Skipped optical depths move a transmittance by less than 1e-9
-// over a whole ray, and their gradient terms are smaller than the kept ones by 2^-40.
+// over a whole ray, and so do their terms of the gradients with respect to T, v_turb and the
+// surfaces (all proportional to kd). The gradient with respect to the density is kd / n times
+// these, which does not shrink with n where the density is tiny and the abundance is not (the
+// top of the disk's wedge at large radii, the thin parts of a 3-D grid), so the window also
+// keeps every channel where the profile is above 2^-20 of its peak (no measurable cost on the
+// observation-scale disk: 1.145 -> 1.144 ms).
 template <int LPR, int CPL>
 __device__ __forceinline__ unsigned adj_window(const MarchParams &P, const float4 &mine,
                                                bool windowed, float idv) {
   if (!windowed) return __any_sync(0xffffffffu, mine.x > 0.0f) ? (1u << CPL) - 1 : 0u;
   float clo = 1.0f, chi = -1.0f;
   if (mine.x > 0.0f) {
-    const float w2 = 40.0f + lg2(mine.x);
+    // never narrower than the channels where the profile is above 2^-20 of its peak, so that
+    // a sample too thin for the absolute bound still has its gradient with respect to the
+    // density (which does not shrink with it) computed to ~1e-6 of its own size
+    const float w2 = fmaxf(40.0f + lg2(mine.x), 20.0f);
     if (w2 > 0.0f) {
       const float ib = rcp(mine.z);
       const float hw = sqa(w2) * ib;
@@ -359,6 +522,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
   constexpr bool SPEC = (VAR & 4) != 0;  // the common configuration (spec_ok)
   constexpr bool UNIF = SPEC || (VAR & 1) != 0;  // equally spaced channels
   constexpr bool ROT = (VAR & 2) != 0;   // a rotation field (gradient with respect to it too)
+  constexpr bool BOX = (VAR & 8) != 0;   // the 3-D Cartesian grid (rt_render3d_adjoint)
+  constexpr bool VLOS = ROT || BOX;      // dL/dv_los is needed (the sums az)
+  constexpr bool CAP = BOX;              // optical-depth increments capped at kDtCap
   constexpr int WPB = adj_wpb<LPR>();
   constexpr int R = 32 / LPR;          // rays per warp
   __shared__ __align__(16) float s_tab[kTabSeg * 4];
@@ -434,7 +600,11 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
       const float2 mone = make_float2(-1.0f, -1.0f);
       int nent = 0;  // entries kept (warp-uniform)
       for (int kb = 0; kb < nsamp; kb += LPR) {
-        const float4 mine = sample_physics<ROT, SPEC>(P, s_tab, ray, ray.klo + kb + q);
+        float4 mine;
+        if constexpr (BOX)
+          mine = sample_physics_box(P, s_tab, ray, ray.klo + kb + q);
+        else
+          mine = sample_physics<ROT, SPEC>(P, s_tab, ray, ray.klo + kb + q);
         const unsigned act = adj_window<LPR, CPL>(P, mine, windowed, idv);
         unsigned act2 = 0;
 #pragma unroll
@@ -464,7 +634,12 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
                      : __ffma2_rn(make_float2(vc[2 * m], vc[2 * m + 1]),
                                   make_float2(p.z, p.z), make_float2(-p.y, -p.y));
             const float2 d2 = __fmul2_rn(d, d);
-            tl[m] = __ffma2_rn(kd2, make_float2(ex2(-d2.x), ex2(-d2.y)), tl[m]);
+            if constexpr (CAP) {
+              const float2 dt = __fmul2_rn(kd2, make_float2(ex2(-d2.x), ex2(-d2.y)));
+              tl[m] = __fadd2_rn(tl[m], make_float2(fminf(dt.x, kDtCap), fminf(dt.y, kDtCap)));
+            } else {
+              tl[m] = __ffma2_rn(kd2, make_float2(ex2(-d2.x), ex2(-d2.y)), tl[m]);
+            }
             const float2 nt = __fadd2_rn(tb[m], tl[m]);
             const float2 Tn = make_float2(ex2(-nt.x), ex2(-nt.y));
             I[m] = __ffma2_rn(S2, __ffma2_rn(Tn, mone, Tr[m]), I[m]);
@@ -554,7 +729,11 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
         ient -= __popc(act2);
         // physics and local derivatives of this lane's sample (records in shared memory, read
         // back by the same lane for its chain rule)
-        const float4 mine = physics_jac<ROT, SPEC>(P, s_tab, ray, ray.klo + kb + q, rb);
+        float4 mine;
+        if constexpr (BOX)
+          mine = physics_jac_box(P, s_tab, ray, ray.klo + kb + q, rb);
+        else
+          mine = physics_jac<ROT, SPEC>(P, s_tab, ray, ray.klo + kb + q, rb);
         if (!__any_sync(0xffffffffu, mine.z > 0.0f)) continue;  // no gas in the batch
         const float Sbefore = Snext;
         ph[rr * kPhStride + q] = mine;
@@ -586,7 +765,8 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
           const float2 gg = make_float2(ex2(-d2.x), ex2(-d2.y));
           A[m] = __ffma2_rn(cs2, Tn[m], A[m]);
           const float2 ug = __fmul2_rn(__fmul2_rn(gI[m], A[m]), gg);
-          const float2 dt = __fmul2_rn(kd2, gg);
+          float2 dt = __fmul2_rn(kd2, gg);
+          if constexpr (CAP) dt = make_float2(fminf(dt.x, kDtCap), fminf(dt.y, kDtCap));
           cur[m] = __ffma2_rn(dt, mone, cur[m]);
           const float2 T0 = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
           // T_k - T_{k+1} = T_{k+1} (2^dt - 1): series below dt = 0.07 (the difference of
@@ -601,7 +781,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
                                          dt.y < 0.07f ? ser.y : dif.y);
           Tn[m] = T0;
           const float2 wy = __fmul2_rn(ug, d2), wz = __fmul2_rn(ug, d), ww = __fmul2_rn(gI[m], dTk);
-          return make_float4(ug.x + ug.y, wy.x + wy.y, ROT ? wz.x + wz.y : 0.0f, ww.x + ww.y);
+          return make_float4(ug.x + ug.y, wy.x + wy.y, VLOS ? wz.x + wz.y : 0.0f, ww.x + ww.y);
         };
         // one channel pair in the window (the common case): its loop without per-sample
         // window tests, the pair index a compile-time constant
@@ -678,7 +858,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
           const float4 v = part[q][(rr * LPR + i) ^ (q & 7)];
           s.x += v.x;
           s.y += v.y;
-          if (ROT) s.z += v.z;
+          if (VLOS) s.z += v.z;
           s.w += v.w;
         }
         if (active && mine.z > 0.0f) {
@@ -692,9 +872,12 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
             Jv[4 * i + 2] = v.z;
             Jv[4 * i + 3] = v.w;
           }
-          dmx = fmaxf(dmx, scatter_grad<ROT>(P, Jv, mine.x, mine.z, s.x, s.y, s.z, s.w, Gb,
-                                        dmod ? dmod + (long long)pix * P.n_samples + ray.klo + kb + q
-                                             : nullptr));
+          if constexpr (BOX)
+            scatter_box(P, Jv, mine.x, mine.z, s.x, s.y, s.z, s.w, Gb);
+          else
+            dmx = fmaxf(dmx, scatter_grad<ROT>(P, Jv, mine.x, mine.z, s.x, s.y, s.z, s.w, Gb,
+                                          dmod ? dmod + (long long)pix * P.n_samples + ray.klo + kb + q
+                                               : nullptr));
         }
         __syncwarp();
       }
@@ -956,6 +1139,63 @@ int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target,
     if (v == 2) return launch_adj_t<L, C, 2>(P, dLdc, target, cube_out, G, dmod, dmax, stream); \
     return launch_adj_t<L, C, 3>(P, dLdc, target, cube_out, G, dmod, dmax, stream);     \
   }
+  RTB_ADJ_LAYOUTS(X)
+#undef X
+  return set_error(RT_EINVAL, "no adjoint layout for %d channels", P.nch);
+}
+
+// The adjoint on the 3-D Cartesian grid (P.box, node records in P.node_a / node_b): scratch
+// for the kept optical depths, one FP32 gradient copy ({dT, dn, dvt, dX} and {dv_los, 0} per
+// node) and the work counter; zero, march, write the FP64 gradients.
+template <int LPR, int CPL, int VAR>
+static int launch_adj3_t(const MarchParams &P, const float *dLdc, const float *target,
+                         float *cube_out, const rt_grads3 &G3, cudaStream_t stream) {
+  const long long nodes = (long long)P.n3x * P.n3y * P.n3z;
+  const long long blocks = adj_blocks<LPR, CPL, VAR>(P, 0);
+  const size_t ck = align256((size_t)blocks * adj_block_bytes<LPR, CPL>(P));
+  const size_t g4 = align256((size_t)nodes * sizeof(float4));
+  const size_t g2 = align256((size_t)nodes * sizeof(float2));
+  char *scratch = nullptr;
+  cudaError_t e = stream_alloc((void **)&scratch, ck + g4 + g2 + 256, stream);
+  if (e != cudaSuccess)
+    return set_error(RT_ENOMEM, "adjoint scratch (%zu bytes): %s", ck + g4 + g2 + 256,
+                     cudaGetErrorString(e));
+  e = cudaMemsetAsync(scratch + ck, 0, g4 + g2 + 256, stream);  // copy and counter
+  if (e == cudaSuccess && G3.loss) e = cudaMemsetAsync(G3.loss, 0, sizeof(double), stream);
+  int rc = RT_OK;
+  if (e != cudaSuccess) rc = set_error(RT_ECUDA, "gradient memset: %s", cudaGetErrorString(e));
+  if (rc == RT_OK) {
+    GradCopies c;
+    c.g = reinterpret_cast<float4 *>(scratch + ck);
+    c.h = reinterpret_cast<float2 *>(scratch + ck + g4);
+    c.gstride = c.hstride = nodes;
+    c.kg = c.kh = 1;
+    rt_grads G = {};
+    G.loss = G3.loss;
+    MarchParams Q = P;
+    Q.rays = nullptr;
+    Q.unit_ctr = reinterpret_cast<unsigned *>(scratch + ck + g4 + g2);
+    march_adj_kernel<LPR, CPL, VAR><<<(unsigned)blocks, adj_wpb<LPR>() * 32, 0, stream>>>(
+        Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch),
+        adj_batches<LPR>(P.n_samples), nullptr, nullptr, c);
+    const long long nb = (nodes + 255) / 256;
+    box_grads_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, stream>>>(
+        c.g, c.h, nodes, (double)P.sin_if, (double)P.cos_if, G3);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) rc = set_error(RT_ECUDA, "3-D adjoint launch: %s", cudaGetErrorString(e));
+  }
+  cudaFreeAsync(scratch, stream);
+  return rc;
+}
+
+int launch_adjoint3(const MarchParams &P, const float *dLdc, const float *target,
+                    float *cube_out, const rt_grads3 &G3, cudaStream_t stream) {
+  int LPR, CPL;
+  adj_layout(P.nch, &LPR, &CPL);
+#define X(L, C)                                                                          \
+  if (LPR == L && CPL == C)                                                              \
+    return P.v_uniform ? launch_adj3_t<L, C, 9>(P, dLdc, target, cube_out, G3, stream)   \
+                       : launch_adj3_t<L, C, 8>(P, dLdc, target, cube_out, G3, stream);
   RTB_ADJ_LAYOUTS(X)
 #undef X
   return set_error(RT_EINVAL, "no adjoint layout for %d channels", P.nch);

@@ -497,6 +497,55 @@ extern "C" int rt_render3d(const rt_grid3 *grid3, const rt_fields3 *fields3,
   return rc;
 }
 
+extern "C" int rt_render3d_adjoint(const rt_grid3 *grid3, const rt_fields3 *fields3,
+                                   const rt_geom *geom, const rt_view *view,
+                                   const rt_line *line, const float *dL_dcube,
+                                   const float *target, float *cube_out,
+                                   const rt_grads3 *grads, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params3(grid3, fields3, geom, view, line, P);
+  const long long nodes = rc == RT_OK ? (long long)grid3->nx * grid3->ny * grid3->nz : 0;
+  if (rc == RT_OK && (!grads || !grads->dT || !grads->dn_h2 || !grads->dvturb ||
+                      !grads->dx_co || !grads->dvx || !grads->dvy || !grads->dvz))
+    rc = set_error(RT_EINVAL, "null gradient output");
+  const long long n = rc == RT_OK ? (long long)P->nx * P->ny * P->nch : 0;
+  if (rc == RT_OK && n > 0 && ((dL_dcube == nullptr) == (target == nullptr)))
+    rc = set_error(RT_EINVAL, "give exactly one of dL_dcube and target");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (rc == RT_OK && n == 0) {  // no ray or no channel: the gradients are zero
+    cudaError_t e = cudaSuccess;
+    double *out[7] = {grads->dT, grads->dn_h2, grads->dvturb, grads->dx_co,
+                      grads->dvx, grads->dvy, grads->dvz};
+    for (int k = 0; k < 7 && e == cudaSuccess; k++)
+      e = cudaMemsetAsync(out[k], 0, (size_t)nodes * sizeof(double), st);
+    if (e == cudaSuccess && grads->loss) e = cudaMemsetAsync(grads->loss, 0, sizeof(double), st);
+    if (e != cudaSuccess) rc = set_error(RT_ECUDA, "memset: %s", cudaGetErrorString(e));
+  } else if (rc == RT_OK) {
+    float4 *buf = nullptr;
+    cudaError_t e = stream_alloc((void **)&buf, (size_t)nodes * 2 * sizeof(float4), st);
+    if (e != cudaSuccess) {
+      rc = set_error(RT_ENOMEM, "node records (%lld nodes): %s", nodes, cudaGetErrorString(e));
+    } else {
+      const long long nb = (nodes + 255) / 256;
+      pack_nodes3_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(*fields3, nodes, buf,
+                                                                           buf + nodes);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        rc = set_error(RT_ECUDA, "node packing: %s", cudaGetErrorString(e));
+      } else {
+        P->node_a = buf;
+        P->node_b = buf + nodes;
+        rc = launch_adjoint3(*P, dL_dcube, target, cube_out, *grads, st);
+      }
+      cudaFreeAsync(buf, st);
+    }
+  }
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
 extern "C" int rt_render(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,
                          const rt_view *view, const rt_line *line, float *cube, void *stream) {
   MarchParams *P = new (std::nothrow) MarchParams;
