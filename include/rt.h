@@ -358,7 +358,8 @@ int rt_field_chain_adjoint(const rt_grid *grid, const rt_geom *geom, const rt_li
  *   Mach number with vturb_mach), x_co (CO abundance per H2), vx, vy, vz (km/s).
  * cube: DEVICE [nch][ny][nx] float32, caller-allocated, overwritten.
  * The call packs the node fields into two float4 records per node (a stream-ordered
- * allocation of 32 bytes per node, freed after the launch). Forward only.
+ * allocation of 32 bytes per node, freed after the launch). Its reverse mode is
+ * rt_render3d_adjoint (below).
  * Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
  */
 typedef struct {
