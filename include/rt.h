@@ -89,8 +89,9 @@ typedef struct {
                              gas_velocity_pressure with the pressure term, e.g. from
                              rt_pressure_vphi), interpolated like the other fields and
                              projected as v_los = v_phi (x / r) sin i + v_sys; NULL: the
-                             Keplerian term alone, evaluated at each sample. The adjoint
-                             entry points reject a non-NULL vphi_kms (forward only). */
+                             Keplerian term alone, evaluated at each sample. With it the
+                             adjoint entry points also return dL/dvphi_kms (rt_grads.dvphi,
+                             required then). */
 } rt_fields;
 
 /* Viewing geometry and kinematics. */
