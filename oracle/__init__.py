@@ -298,20 +298,26 @@ def render_adjoint_vphi(p, dL_dcube: np.ndarray, nthreads: int = 0):
 
 
 def render_adjoint3(p, dL_dcube: np.ndarray, nthreads: int = 0):
-    """Reverse mode of the 3-D Cartesian grid march (p.g3): (cube, grads) with grads a dict of
-    T, n_h2, vturb, x_co, vx, vy, vz, each [nz][ny][nx] like the grid's fields."""
+    """Reverse mode of the 3-D grid marches: (cube, grads) with grads a dict of T, n_h2,
+    vturb, x_co and the velocity fields (vx, vy, vz on a Cartesian grid p.g3, [nz][ny][nx];
+    vr, vth, vph on a spherical grid p.gs, [nph][nth][nr]), like the grid's fields."""
     lib = _load()
     pk = _Packed(p)
-    g3 = p.g3
     g = np.ascontiguousarray(np.asarray(dL_dcube, dtype=np.float64))
     cube = np.zeros((pk.nch, int(p.ny), int(p.nx)), dtype=np.float64)
-    shp = (int(g3.nz), int(g3.ny), int(g3.nx))
-    keys = ("T", "n_h2", "vturb", "x_co", "vx", "vy", "vz")
+    if getattr(p, "gs", None) is not None:
+        gs = p.gs
+        shp = (int(gs.nph), int(gs.nth), int(gs.nr))
+        keys = ("T", "n_h2", "vturb", "x_co", "vr", "vth", "vph")
+    else:
+        g3 = p.g3
+        shp = (int(g3.nz), int(g3.ny), int(g3.nx))
+        keys = ("T", "n_h2", "vturb", "x_co", "vx", "vy", "vz")
     out = {k: np.zeros(shp) for k in keys}
     rc = lib.orc_render_adjoint3(C.byref(pk.s), _dptr(g), _dptr(cube),
                                  *[_dptr(out[k]) for k in keys], _threads(nthreads))
     if rc:
-        raise ValueError("oracle: invalid problem (a 3-D Cartesian grid is required)")
+        raise ValueError("oracle: invalid problem (one 3-D grid is required)")
     return cube, out
 
 

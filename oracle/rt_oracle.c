@@ -210,10 +210,11 @@ typedef struct {
   double xin[2], o[4], mT, mn;
   /* d v_los / d(rotation-field value) [cm/s per km/s] with a rotation field, 0 otherwise */
   double dvlos_dvphi;
-  /* 3-D Cartesian grid: the cell (lowest node index per axis) and the fractional position in
-     it, as the trilinear interpolation used them */
-  int i3[3];
-  double f3[3];
+  /* 3-D grids: the cell (lowest node index per axis; on the spherical grid k1 is the azimuth
+     node after i3[2], periodic) and the fractional position in it, as the trilinear
+     interpolation used them, and d v_los / d(the three velocity fields) [cm/s per km/s] */
+  int i3[3], k1;
+  double f3[3], dv3[3];
 } pt;
 
 static double bilerp(const double *F, int nr, int i0, int j0, double fr, double fz) {
@@ -280,6 +281,15 @@ static void eval_point(const orc_problem *p, const orc_mlp *m, const double P[3]
     const double vel[3] = {val[4] * st_ * cp + val[5] * ct * cp - val[6] * sp,
                            val[4] * st_ * sp + val[5] * ct * sp + val[6] * cp,
                            val[4] * ct - val[5] * st_};
+    st->i3[0] = i0;
+    st->i3[1] = j0;
+    st->i3[2] = k0;
+    st->k1 = k1;
+    for (int a = 0; a < 3; a++) st->f3[a] = f[a];
+    /* v_los = 1e5 omega . (v_r r^ + v_theta theta^ + v_phi phi^) + v_sys */
+    st->dv3[0] = 1e5 * (om[0] * st_ * cp + om[1] * st_ * sp + om[2] * ct);
+    st->dv3[1] = 1e5 * (om[0] * ct * cp + om[1] * ct * sp - om[2] * st_);
+    st->dv3[2] = 1e5 * (-om[0] * sp + om[1] * cp);
     st->vlos = 1e5 * (om[0] * vel[0] + om[1] * vel[1] + om[2] * vel[2]) + p->vsys_kms * 1e5;
     goto line_physics;
   }
@@ -313,6 +323,7 @@ static void eval_point(const orc_problem *p, const orc_mlp *m, const double P[3]
     for (int a = 0; a < 3; a++) {
       st->i3[a] = i3[a];
       st->f3[a] = f[a];
+      st->dv3[a] = 1e5 * om[a];
     }
     st->T = val[0];
     st->n = val[1];
@@ -696,24 +707,29 @@ static void adjoint_pixel(const orc_problem *p, const orc_mlp *m, int ix, int iy
     double gvt = galpha * dadvt;
     /* n_CO = X n */
     double gX = gnco * q->n, gn = gnco * q->X;
-    if (p->g3) {
-      /* 3-D grid: every field is interpolated trilinearly, X is a field of its own and
-         v_los = 1e5 (omega . v) + v_sys (v in km/s); the weight of corner (dx, dy, dz) is the
-         product of f or 1 - f along each axis */
-      const orc_grid3 *g3 = p->g3;
+    if (p->g3 || p->gs) {
+      /* 3-D grids: every field is interpolated trilinearly, X is a field of its own and
+         v_los is linear in the three velocity fields (d v_los / d field = dv3); the weight of
+         corner (dx, dy, dz) is the product of f or 1 - f along each axis. Cartesian nodes are
+         [z][y][x]; spherical ones [phi][theta][r], the azimuth periodic */
       for (int c8 = 0; c8 < 8; c8++) {
         int dx = c8 & 1, dy = (c8 >> 1) & 1, dz = c8 >> 2;
         double w = (dx ? q->f3[0] : 1.0 - q->f3[0]) * (dy ? q->f3[1] : 1.0 - q->f3[1]) *
                    (dz ? q->f3[2] : 1.0 - q->f3[2]);
-        long long id = ((long long)(q->i3[2] + dz) * g3->ny + (q->i3[1] + dy)) * g3->nx +
-                       (q->i3[0] + dx);
+        long long id;
+        if (p->g3)
+          id = ((long long)(q->i3[2] + dz) * p->g3->ny + (q->i3[1] + dy)) * p->g3->nx +
+               (q->i3[0] + dx);
+        else
+          id = ((long long)(dz ? q->k1 : q->i3[2]) * p->gs->nth + (q->i3[1] + dy)) * p->gs->nr +
+               (q->i3[0] + dx);
         g->gT[id] += gT * w;
         g->gn[id] += gn * w;
         g->gvt[id] += gvt * w;
         g->gxco[id] += gX * w;
-        g->gvx[id] += gvlos * 1e5 * om[0] * w;
-        g->gvy[id] += gvlos * 1e5 * om[1] * w;
-        g->gvz[id] += gvlos * 1e5 * om[2] * w;
+        g->gvx[id] += gvlos * q->dv3[0] * w;
+        g->gvy[id] += gvlos * q->dv3[1] * w;
+        g->gvz[id] += gvlos * q->dv3[2] * w;
       }
       continue;
     }
@@ -873,9 +889,9 @@ int orc_render_adjoint_vphi(const orc_problem *p, const double *dL_dcube, double
 int orc_render_adjoint3(const orc_problem *p, const double *dL_dcube, double *cube, double *dT,
                         double *dn, double *dvt, double *dxco, double *dvx, double *dvy,
                         double *dvz, int nthreads) {
-  if (!p || !p->g3 || p->gs || check(p) || !dL_dcube) return -1;
-  const orc_grid3 *g3 = p->g3;
-  long long G = (long long)g3->nx * g3->ny * g3->nz;
+  if (!p || !p->g3 == !p->gs || check(p) || !dL_dcube) return -1;
+  long long G = p->g3 ? (long long)p->g3->nx * p->g3->ny * p->g3->nz
+                      : (long long)p->gs->nr * p->gs->nth * p->gs->nph;
   long long npix = (long long)p->nx * p->ny;
   double *out[7] = {dT, dn, dvt, dxco, dvx, dvy, dvz};
   for (int a = 0; a < 7; a++) memset(out[a], 0, sizeof(double) * G);

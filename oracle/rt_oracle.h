@@ -117,11 +117,12 @@ int orc_render_adjoint_vphi(const orc_problem *p, const double *dL_dcube, double
                             double *dT, double *dn, double *dvt, double *dh_lo, double *dh_hi,
                             double *dvphi, int nthreads);
 
-/* Reverse mode of the 3-D Cartesian grid march (p->g3 set, no spherical grid): given
-   dL/dcube [nch][ny][nx], writes the cube and dL/d(node fields) [nz][ny][nx] for T, n_H2,
-   v_turb, the CO abundance and the three velocity components (per km/s); every gradient array
-   is overwritten. The hand-derived reverse of the same per-sample loop as orc_render_adjoint,
-   with the trilinear weights in place of the bilinear ones. */
+/* Reverse mode of the 3-D grid marches (exactly one of p->g3, p->gs set): given dL/dcube
+   [nch][ny][nx], writes the cube and dL/d(node fields) in the grid's node order ([nz][ny][nx]
+   Cartesian, [nph][nth][nr] spherical) for T, n_H2, v_turb, the CO abundance and the three
+   velocity fields (dvx, dvy, dvz receive v_x, v_y, v_z or v_r, v_theta, v_phi; per km/s); every
+   gradient array is overwritten. The hand-derived reverse of the same per-sample loop as
+   orc_render_adjoint, with the trilinear weights in place of the bilinear ones. */
 int orc_render_adjoint3(const orc_problem *p, const double *dL_dcube, double *cube, double *dT,
                         double *dn, double *dvt, double *dxco, double *dvx, double *dvy,
                         double *dvz, int nthreads);
