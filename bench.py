@@ -469,31 +469,40 @@ def _grid3d_time(dev, flush, p, render, dg, reps):
     return statistics.median(ms)
 
 
+def _adjoint3_time(dev, flush, p, adjoint, dg, reps):
+    """Median CUDA-event time [ms] of the fused forward + adjoint on a 3-D grid with the
+    sum-of-squares loss against a fixed target cube (1.05 x the render), L2 flushed before
+    each timed call."""
+    import torch
+    from paper_2509_03623_b300 import _rt
+    render = _rt.rt_render3d if getattr(p, "g3", None) is not None else _rt.rt_render_sph
+    target = (render(p, dg) * 1.05).contiguous()
+    st = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        adjoint(p, dg, target=target, cube_out=None, stream=st)
+    ms = []
+    for i in range(max(3, reps)):
+        flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        adjoint(p, dg, target=target, cube_out=None, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
 def box_leg(dev, flush, reps=10):
     """3-D Cartesian grid march (rt_render3d): 128^3-node box, 256^2 px, 64 channels, 256
     samples; CUDA-event time per render (node packing included), L2 flushed before each."""
     from paper_2509_03623_b300 import _rt, synth
-    import torch
     p = synth.config_box(0)
     dg = _rt.DeviceGrid3(p, dev)
     t = _grid3d_time(dev, flush, p, _rt.rt_render3d, dg, reps)
     # forward + fused adjoint through the box (rt_render3d_adjoint), sum-of-squares loss
     # against a fixed target cube
-    target = (_rt.rt_render3d(p, dg) * 1.05).contiguous()
-    st = torch.cuda.current_stream(dev)
-    for _ in range(2):
-        _rt.rt_render3d_adjoint(p, dg, target=target, cube_out=None, stream=st)
-    ms = []
-    for i in range(max(3, reps // 2)):
-        flush.fill_(float(i))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        _rt.rt_render3d_adjoint(p, dg, target=target, cube_out=None, stream=st)
-        e1.record(st)
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    ta = statistics.median(ms)
+    ta = _adjoint3_time(dev, flush, p, _rt.rt_render3d_adjoint, dg, reps // 2)
     return {"workload": p.name, "ms": t, "value": p.evals / (t * 1e-3) / 1e9,
             "unit": "Gevals/s", "nodes": p.g3.nx * p.g3.ny * p.g3.nz,
             "fwd_adjoint_ms": ta, "fwd_adjoint_value": p.evals / (ta * 1e-3) / 1e9,
@@ -521,10 +530,14 @@ def sph_leg(dev, flush, reps=10):
         tq = _grid3d_time(dev, flush, q, _rt.rt_render_sph, dg, 5)
         sweep.append({"px": nx, "channels": nch, "ms": tq,
                       "value": q.evals / (tq * 1e-3) / 1e9})
+    ta = _adjoint3_time(dev, flush, p, _rt.rt_render_sph_adjoint, dg, reps // 2)
     return {"workload": p.name, "ms": t, "value": p.evals / (t * 1e-3) / 1e9,
             "unit": "Gevals/s", "nodes": g.nr * g.nth * g.nph, "sweep": sweep,
+            "fwd_adjoint_ms": ta, "fwd_adjoint_value": p.evals / (ta * 1e-3) / 1e9,
             "note": "nominal sample-channel evaluations / time; includes packing the 7 node "
-                    "fields into two float4 records (403 MB); sweep: 512 samples per ray"}
+                    "fields into two float4 records (403 MB); sweep: 512 samples per ray; "
+                    "fwd_adjoint: rt_render_sph_adjoint (gradients of all 7 node fields, "
+                    "FP32 copy of 32 B per node written out in FP64), L2 flushed before each"}
 
 
 def neural_leg(dev, flush, reps=5):

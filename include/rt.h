@@ -453,6 +453,25 @@ int rt_render_sph(const rt_grid_sph *grid, const rt_fields_sph *fields, const rt
                   const rt_view *view, const rt_line *line, float *cube, void *stream);
 
 /*
+ * rt_render_sph_adjoint -- fused reverse mode of rt_render_sph: the gradient of a scalar loss
+ * with respect to every node of the seven fields of the spherical grid, as
+ * rt_render3d_adjoint does for the Cartesian grid (the reverse march of Eq. rt-int /
+ * Eq. optical_depth through the trilinear interpolation in (radial index, theta, phi),
+ * periodic in phi, and through v_los = omega . (v_r r^ + v_theta theta^ + v_phi phi^)).
+ * Inputs as rt_render_sph; dL_dcube / target / cube_out as rt_render3d_adjoint.
+ * grads (rt_grads3): all seven arrays required, each [nph][nth][nr] like the fields; dvx, dvy
+ * and dvz receive dL/dvr_kms, dL/dvth_kms and dL/dvph_kms (per km/s); loss optional.
+ * The call allocates (stream-ordered, freed after the launch) the node records (32 bytes per
+ * node), one FP32 gradient copy (32 bytes per node) and the per-warp optical depths kept at
+ * every batch boundary.
+ * Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
+ */
+int rt_render_sph_adjoint(const rt_grid_sph *grid, const rt_fields_sph *fields,
+                          const rt_geom *geom, const rt_view *view, const rt_line *line,
+                          const float *dL_dcube, const float *target, float *cube_out,
+                          const rt_grads3 *grads, void *stream);
+
+/*
  * rt_pressure_vphi -- pressure-corrected rotation on the nodes (Methods, "Parametric Disk
  * Modeling", Eq. gas_velocity_pressure; "Neural Temperature Recovery" derives v_phi from
  * the density and temperature this way):

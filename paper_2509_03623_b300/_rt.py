@@ -184,6 +184,10 @@ def lib():
             L.rt_render_sph.argtypes = [P(rt_grid_sph), P(rt_fields_sph), P(rt_geom),
                                         P(rt_view), P(rt_line), C.c_void_p, C.c_void_p]
             L.rt_render_sph.restype = C.c_int
+            L.rt_render_sph_adjoint.argtypes = [P(rt_grid_sph), P(rt_fields_sph), P(rt_geom),
+                                                P(rt_view), P(rt_line), C.c_void_p, C.c_void_p,
+                                                C.c_void_p, P(rt_grads3), C.c_void_p]
+            L.rt_render_sph_adjoint.restype = C.c_int
             L.rt_render_plain.argtypes = base + [C.c_void_p, C.c_void_p]
             L.rt_render_plain.restype = C.c_int
             L.rt_render_dense.argtypes = base + [C.c_void_p, C.c_void_p]
@@ -605,6 +609,44 @@ def rt_render_sph(problem, grid=None, out=None, stream=None):
     check(lib().rt_render_sph(C.byref(gg), C.byref(f), C.byref(o), C.byref(vw), C.byref(ln),
                               _ptr(out), stream_handle(stream)))
     return out
+
+
+def rt_render_sph_adjoint(problem, grid=None, dL_dcube=None, target=None, cube_out=True,
+                          stream=None):
+    """Fused forward + reverse march through a 3-D spherical grid (problem.gs), through the C
+    ABI. Give exactly one of dL_dcube or target (loss = sum (cube - target)^2). Returns
+    (cube or None, grads) with grads a dict of float64 CUDA tensors T, n_h2, vturb, x_co, vr,
+    vth, vph [nph][nth][nr] and loss (1 element)."""
+    import torch
+    gs = problem.gs
+    dg = grid if grid is not None else DeviceGridSph(problem)
+    shp = (int(gs.nph), int(gs.nth), int(gs.nr))
+    for k in DeviceGridSph.FIELDS:
+        t = getattr(dg, k)
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shp:
+            raise ValueError(f"spherical field {k} must be a contiguous CUDA float32 tensor of "
+                             f"shape {shp}")
+    gg = rt_grid_sph(int(gs.nr), int(gs.nth), int(gs.nph), int(gs.r_log), float(gs.r_in),
+                     float(gs.r_out), float(gs.th0), float(gs.th1))
+    f = rt_fields_sph(*(getattr(dg, k).data_ptr() for k in DeviceGridSph.FIELDS),
+                      int(problem.vturb_mach))
+    o, v, vw, ln = _view_line_geom(problem)
+    cshape = (vw.nch, vw.ny, vw.nx)
+    dL_dcube = _cube_arg(dL_dcube, cshape, "dL_dcube")
+    target = _cube_arg(target, cshape, "target")
+    dev = dg.T.device
+    cube = None
+    if cube_out is True:
+        cube = torch.empty(cshape, dtype=torch.float32, device=dev)
+    elif cube_out is not None and cube_out is not False:
+        cube = _cube_arg(cube_out, cshape, "cube_out")
+    out = {k: torch.empty(shp, dtype=torch.float64, device=dev) for k in DeviceGridSph.FIELDS}
+    out["loss"] = torch.empty(1, dtype=torch.float64, device=dev)
+    gr = rt_grads3(*(out[k].data_ptr() for k in DeviceGridSph.FIELDS), out["loss"].data_ptr())
+    check(lib().rt_render_sph_adjoint(C.byref(gg), C.byref(f), C.byref(o), C.byref(vw),
+                                      C.byref(ln), _ptr(dL_dcube), _ptr(target), _ptr(cube),
+                                      C.byref(gr), stream_handle(stream)))
+    return cube, out
 
 
 def rt_render3d(problem, grid=None, out=None, stream=None):

@@ -193,11 +193,57 @@ __device__ __forceinline__ float4 physics_jac(const MarchParams &P, const float 
   return out;
 }
 
-// physics_jac on the 3-D Cartesian grid (rt_render3d): sample_physics_box's arithmetic for
-// {kd, a, b, S} (bit-identical, which the reverse pass's rebuilt depths rely on) and the local
-// derivatives, in physics_jac's slots where they mean the same (J_KDN, J_DPHI, J_QT, J_QV,
-// J_DS); J_SA holds dkd/dX (the CO abundance is a field of its own), J_FR, J_FZ, J_I0 the
-// trilinear weights along x, y, z and J_CELL the cell's lowest node index. Zeros without gas.
+// Line physics of a sample on a 3-D grid (line_tail's arithmetic, so {kd, a, b, S} are
+// bit-identical to the forward march's, which the reverse pass's rebuilt depths rely on) with
+// the local derivatives in physics_jac's slots where they mean the same (J_KDN, J_DPHI, J_QT,
+// J_QV, J_DS) and dkd/dX in J_SA (the CO abundance is a field of its own on these grids).
+__device__ __forceinline__ float4 line_jac3(const MarchParams &P, const float *tab, const Ray &R,
+                                            float T, float n, float X, float vt, float vlos,
+                                            float *J) {
+  const bool clampT = T < 1e-3f;
+  const float Tg = fmaxf(T, 1e-3f);
+  float a2, da2T, da2v;
+  if (P.vturb_mach) {
+    const float m = fmaf(P.c_mach, vt * vt, P.c_th);
+    a2 = Tg * m;
+    da2T = m;
+    da2v = Tg * P.c_mach * 2.0f * vt;
+  } else {
+    a2 = fmaf(P.c_th, Tg, vt * vt);
+    da2T = P.c_th;
+    da2v = 2.0f * vt;
+  }
+  const float ia = rsq(a2);
+  float dphi;
+  const float phi = lte_phi(tab, lg2(Tg), &dphi);
+  const float iT = rcp(Tg);
+  const float eS = ex2(-P.theta_s * iT);
+  const float om = rcp(1.0f - eS);
+  const float F = ex2(phi);
+  const float q = -0.5f * ia * ia;
+  J[J_KDN] = P.kappa_k * X * F * ia * R.ds;
+  J[J_DPHI] = clampT ? 0.0f : dphi * iT;
+  J[J_QT] = clampT ? 0.0f : q * da2T;
+  J[J_QV] = q * da2v;
+  J[J_DS] = clampT ? 0.0f : eS * om * om * kLn2 * P.theta_s * iT * iT;
+  J[J_SA] = P.kappa_k * n * F * ia * R.ds;  // dkd/dX
+  float4 out;
+  out.x = P.kappa_k * (X * n) * F * ia * R.ds;
+  out.z = ia * 1.2011224087864498f;
+  out.y = vlos * out.z;
+  out.w = eS * om;
+  return out;
+}
+
+// Slots of the 3-D grids' records beyond line_jac3's: the cell's trilinear weights along its
+// three axes, its lowest node (on the spherical grid: in the azimuth plane k0, and the node of
+// the same (r, theta) in the plane k1 after it, periodic), and on the spherical grid
+// d v_los / d(v_r, v_theta, v_phi) at the sample.
+enum { J3_B1 = J_SB, J3_W0 = J_FR, J3_W1 = J_FZ, J3_B0 = J_CELL, J3_W2 = J_I0, J3_ER = J_MT,
+       J3_ETH = 12, J3_EPH = 13 };
+
+// physics_jac on the 3-D Cartesian grid (rt_render3d): sample_physics_box's arithmetic and
+// line_jac3; zeros without gas.
 __device__ __forceinline__ float4 physics_jac_box(const MarchParams &P, const float *tab,
                                                   const Ray &R, int k, float4 *rec) {
   const float kf = (float)k;
@@ -245,50 +291,95 @@ __device__ __forceinline__ float4 physics_jac_box(const MarchParams &P, const fl
   const float vz = tri(v[0].z, v[1].z, v[2].z, v[3].z, v[4].z, v[5].z, v[6].z, v[7].z);
   if (!(X * n > 0.0f)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const float vlos = fmaf(P.sin_if, vy, fmaf(-P.cos_if, vz, P.vsys));
-  // line physics (line_tail's arithmetic) with its derivatives (as physics_jac)
-  const bool clampT = T < 1e-3f;
-  const float Tg = fmaxf(T, 1e-3f);
-  float a2, da2T, da2v;
-  if (P.vturb_mach) {
-    const float m = fmaf(P.c_mach, vt * vt, P.c_th);
-    a2 = Tg * m;
-    da2T = m;
-    da2v = Tg * P.c_mach * 2.0f * vt;
-  } else {
-    a2 = fmaf(P.c_th, Tg, vt * vt);
-    da2T = P.c_th;
-    da2v = 2.0f * vt;
-  }
-  const float ia = rsq(a2);
-  float dphi;
-  const float phi = lte_phi(tab, lg2(Tg), &dphi);
-  const float iT = rcp(Tg);
-  const float eS = ex2(-P.theta_s * iT);
-  const float om = rcp(1.0f - eS);
-  const float F = ex2(phi);
-  const float q = -0.5f * ia * ia;
   float J[12];
-  J[J_KDN] = P.kappa_k * X * F * ia * R.ds;
-  J[J_DPHI] = clampT ? 0.0f : dphi * iT;
-  J[J_QT] = clampT ? 0.0f : q * da2T;
-  J[J_QV] = q * da2v;
-  J[J_DS] = clampT ? 0.0f : eS * om * om * kLn2 * P.theta_s * iT * iT;
-  J[J_SA] = P.kappa_k * n * F * ia * R.ds;  // dkd/dX
-  J[J_SB] = 0.0f;
-  J[J_FR] = wx;
-  J[J_FZ] = wy;
-  J[J_CELL] = __int_as_float((int)b);
-  J[J_I0] = wz;
-  J[J_MT] = 1.0f;
-  static_assert(J_MT == 11 && J_I0 == 10 && J_CELL == 9, "box entries in the first 12 slots");
+  const float4 out = line_jac3(P, tab, R, T, n, X, vt, vlos, J);
+  J[J3_B1] = 0.0f;
+  J[J3_W0] = wx;
+  J[J3_W1] = wy;
+  J[J3_B0] = __int_as_float((int)b);
+  J[J3_W2] = wz;
+  J[J3_ER] = 0.0f;
 #pragma unroll
   for (int i = 0; i < 3; i++)
     rec[(i + 1) * 32] = make_float4(J[4 * i], J[4 * i + 1], J[4 * i + 2], J[4 * i + 3]);
-  float4 out;
-  out.x = P.kappa_k * (X * n) * F * ia * R.ds;
-  out.z = ia * 1.2011224087864498f;
-  out.y = vlos * out.z;
-  out.w = eS * om;
+  return out;
+}
+
+// physics_jac on the 3-D spherical grid (rt_render_sph): sample_physics_sph's arithmetic and
+// line_jac3, the velocity factors d v_los / d(v_r, v_theta, v_phi) =
+// (sin i sin th sin ph - cos i cos th, sin i cos th sin ph + cos i sin th, sin i cos ph);
+// zeros without gas.
+__device__ __forceinline__ float4 physics_jac_sph(const MarchParams &P, const float *tab,
+                                                  const Ray &R, int k, float4 *rec) {
+  const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float kf = (float)k;
+  const float y = sample_coord(kf, R.yb, R.yb2, R.dy, R.dy2);
+  const float z = sample_coord(kf, R.zb, R.zb2, R.dz, R.dz2);
+  if (!(k <= R.khi)) return zero;
+  const float Rc2 = fmaf(R.x, R.x, y * y);
+  const float r2 = fmaf(z, z, Rc2);
+  if (!(r2 >= P.r_in2 && r2 <= P.r_out2)) return zero;
+  const float iRc = Rc2 > 0.0f ? rsq(Rc2) : 0.0f;
+  const float Rc = Rc2 * iRc;
+  const float th = atan2f(Rc, z);
+  if (!(th >= P.th0 && th <= P.th1)) return zero;
+  float ph = atan2f(y, R.x);
+  if (ph < 0.0f) ph += 6.283185307179586f;
+  const float ir = r2 > 0.0f ? rsq(r2) : 0.0f;
+  float u = P.r_log ? lg2(r2 * P.inv_rin2) * P.lr_scale : fmaf(r2 * ir, P.lr_scale, P.lr_off);
+  u = fminf(fmaxf(u, 0.0f), (float)(P.snr - 1));
+  const int i0 = min((int)u, P.snr - 2);
+  const float fr = u - (float)i0;
+  const float v = fminf(fmaxf((th - P.th0) * P.th_scale, 0.0f), (float)(P.snth - 1));
+  const int j0 = min((int)v, P.snth - 2);
+  const float ft = v - (float)j0;
+  const float w = ph * P.ph_scale;
+  int k0 = (int)w;
+  const float fp = w - (float)k0;
+  if (k0 >= P.snph) k0 -= P.snph;
+  const int k1 = k0 + 1 == P.snph ? 0 : k0 + 1;
+  const long long sj = P.snr, sk0 = (long long)k0 * P.snth * P.snr,
+                  sk1 = (long long)k1 * P.snth * P.snr;
+  const long long b0 = sk0 + j0 * sj + i0, b1 = sk1 + j0 * sj + i0;
+  const long long o[8] = {b0, b0 + 1, b0 + sj, b0 + sj + 1, b1, b1 + 1, b1 + sj, b1 + sj + 1};
+  float4 a[8], vv[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    a[c] = __ldg(P.node_a + o[c]);
+    vv[c] = __ldg(P.node_b + o[c]);
+  }
+  auto tri = [&](float f0, float f1, float f2, float f3, float f4, float f5, float f6, float f7) {
+    const float x0 = lerpf(f0, f1, fr), x1 = lerpf(f2, f3, fr);
+    const float x2 = lerpf(f4, f5, fr), x3 = lerpf(f6, f7, fr);
+    return lerpf(lerpf(x0, x1, ft), lerpf(x2, x3, ft), fp);
+  };
+  const float T = tri(a[0].x, a[1].x, a[2].x, a[3].x, a[4].x, a[5].x, a[6].x, a[7].x);
+  const float n = tri(a[0].y, a[1].y, a[2].y, a[3].y, a[4].y, a[5].y, a[6].y, a[7].y);
+  const float vt = tri(a[0].z, a[1].z, a[2].z, a[3].z, a[4].z, a[5].z, a[6].z, a[7].z);
+  const float X = tri(a[0].w, a[1].w, a[2].w, a[3].w, a[4].w, a[5].w, a[6].w, a[7].w);
+  if (!(X * n > 0.0f)) return zero;
+  const float vr = tri(vv[0].x, vv[1].x, vv[2].x, vv[3].x, vv[4].x, vv[5].x, vv[6].x, vv[7].x);
+  const float vth = tri(vv[0].y, vv[1].y, vv[2].y, vv[3].y, vv[4].y, vv[5].y, vv[6].y, vv[7].y);
+  const float vph = tri(vv[0].z, vv[1].z, vv[2].z, vv[3].z, vv[4].z, vv[5].z, vv[6].z, vv[7].z);
+  const float sth = Rc * ir, cth = z * ir;
+  const float sph_ = y * iRc, cph = R.x * iRc;
+  const float vy = fmaf(fmaf(vr, sth, vth * cth), sph_, vph * cph);
+  const float vz = fmaf(vr, cth, -vth * sth);
+  const float vlos = fmaf(P.sin_if, vy, fmaf(-P.cos_if, vz, P.vsys));
+  float J[16];
+  const float4 out = line_jac3(P, tab, R, T, n, X, vt, vlos, J);
+  J[J3_B1] = __int_as_float((int)b1);
+  J[J3_W0] = fr;
+  J[J3_W1] = ft;
+  J[J3_B0] = __int_as_float((int)b0);
+  J[J3_W2] = fp;
+  J[J3_ER] = fmaf(P.sin_if, sth * sph_, -P.cos_if * cth);
+  J[J3_ETH] = fmaf(P.sin_if, cth * sph_, P.cos_if * sth);
+  J[J3_EPH] = P.sin_if * cph;
+  J[14] = J[15] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+    rec[(i + 1) * 32] = make_float4(J[4 * i], J[4 * i + 1], J[4 * i + 2], J[4 * i + 3]);
   return out;
 }
 
@@ -306,6 +397,10 @@ struct GradCopies {
   float2 *h;  // kh copies of [nr] {dh_lo, dh_hi}, hstride float2 apart
   long long gstride, hstride;
   int kg, kh;
+  // 3-D grids (one copy each, the node count apart from nothing): g holds {dT, dn, dvt, dX}
+  // per node, h {dL/dv_los, 0} per node on the Cartesian grid, v {dv_r, dv_theta, dv_phi, 0}
+  // per node on the spherical grid
+  float4 *v;
 };
 
 // Where one block's gradient contributions go.
@@ -313,6 +408,7 @@ struct GradSink {
   rt_grads G;  // caller's FP64 arrays (used where the copies below are absent)
   float4 *g;   // this block's grid copy, or nullptr
   float2 *h;   // this block's surface copy, or nullptr
+  float4 *v;   // the spherical grid's velocity copy, or nullptr
 };
 
 __device__ __forceinline__ GradSink block_sink(const rt_grads &G, const GradCopies &C) {
@@ -320,6 +416,7 @@ __device__ __forceinline__ GradSink block_sink(const rt_grads &G, const GradCopi
   S.G = G;
   S.g = C.g ? C.g + (long long)(blockIdx.x % C.kg) * C.gstride : nullptr;
   S.h = C.h ? C.h + (long long)(blockIdx.x % C.kh) * C.hstride : nullptr;
+  S.v = C.v;
   return S;
 }
 
@@ -428,14 +525,18 @@ __device__ __forceinline__ float scatter_grad(const MarchParams &P, const float 
   return dm;
 }
 
-// Chain rule of one sample on the 3-D Cartesian grid (physics_jac_box's entries): dL/d of T,
-// n_H2, v_turb and the CO abundance as a float4 per node and dL/dv_los as the first entry of
-// a float2 per node (the velocity components' gradients are sin i and -cos i times it,
-// formed when the copy is summed), each spread over the cell's 8 corners with the trilinear
-// weights: 8 16-byte and 8 8-byte FP32 reductions into the block's copy.
-__device__ __forceinline__ void scatter_box(const MarchParams &P, const float *J, float kd,
-                                            float b, float ax, float ay, float az, float aS,
-                                            const GradSink &G) {
+// Chain rule of one sample on a 3-D grid (line_jac3's entries and the cell of physics_jac_box
+// or physics_jac_sph): dL/d of T, n_H2, v_turb and the CO abundance as a float4 per node, and
+// the velocity fields' share of dL/dv_los -- on the Cartesian grid dL/dv_los itself as the
+// first entry of a float2 per node (the components' gradients are sin i and -cos i times it,
+// formed when the copy is written out), on the spherical grid dL/dv_los times the sample's
+// factors for v_r, v_theta, v_phi as a float4 per node -- each spread over the cell's 8 corners
+// with the trilinear weights (corner bit 0 the first axis, bit 1 the second, bit 2 the third:
+// z on the Cartesian grid, the next azimuth plane on the spherical one).
+template <bool SPH>
+__device__ __forceinline__ void scatter_3d(const MarchParams &P, const float *J, float kd,
+                                           float b, float ax, float ay, float az, float aS,
+                                           const GradSink &G) {
   const float gx = -kLn2 * ax;                    // dL/dkd
   const float GB = 2.0f * kLn2 * kLn2 * kd * ay;  // b dL/db
   const float gk = fmaf(gx, kd, GB);
@@ -444,34 +545,51 @@ __device__ __forceinline__ void scatter_box(const MarchParams &P, const float *J
   const float gn = gx * J[J_KDN];
   const float gX = gx * J[J_SA];
   const float gl = -2.0f * kLn2 * kLn2 * kd * b * az;  // dL/dv_los
-  const float wx = J[J_FR], wy = J[J_FZ], wz = J[J_I0];
-  const long long b0 = __float_as_int(J[J_CELL]);
-  const long long sy = P.n3x, sz = (long long)P.n3x * P.n3y;
+  const float w0 = J[J3_W0], w1 = J[J3_W1], w2 = J[J3_W2];
+  const long long b0 = __float_as_int(J[J3_B0]);
+  const long long b1 = SPH ? (long long)__float_as_int(J[J3_B1]) : 0;
+  const long long s1 = SPH ? (long long)P.snr : (long long)P.n3x;
+  const long long s2 = (long long)P.n3x * P.n3y;
 #pragma unroll
   for (int c = 0; c < 8; c++) {
-    const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) *
-                    ((c & 4) ? wz : 1.0f - wz);
-    const long long id = b0 + (c & 1) + ((c >> 1) & 1) * sy + (c >> 2) * sz;
+    const float w = ((c & 1) ? w0 : 1.0f - w0) * ((c & 2) ? w1 : 1.0f - w1) *
+                    ((c & 4) ? w2 : 1.0f - w2);
+    const long long id = SPH ? ((c & 4) ? b1 : b0) + (c & 1) + ((c >> 1) & 1) * s1
+                             : b0 + (c & 1) + ((c >> 1) & 1) * s1 + (c >> 2) * s2;
     atomicAdd(G.g + id, make_float4(gT * w, gn * w, gv * w, gX * w));
-    atomicAdd(G.h + id, make_float2(gl * w, 0.0f));
+    if (SPH) {
+      const float lw = gl * w;
+      atomicAdd(G.v + id, make_float4(lw * J[J3_ER], lw * J[J3_ETH], lw * J[J3_EPH], 0.0f));
+    } else {
+      atomicAdd(G.h + id, make_float2(gl * w, 0.0f));
+    }
   }
 }
 
-// Sums of the 3-D grid's gradient copy (one copy) in FP64: {dT, dn, dvt, dX} per node and
-// dL/dv_los, whose share of the velocity components is omega = (0, sin i, -cos i).
-__global__ void box_grads_kernel(const float4 *__restrict__ g4, const float2 *__restrict__ g2,
-                                 long long n, double sin_i, double cos_i, rt_grads3 G) {
+// The 3-D grids' gradient copy (one copy) written out in FP64: {dT, dn, dvt, dX} per node and
+// the velocity fields' gradients -- on the Cartesian grid from dL/dv_los (g2, the components'
+// share of it is omega = (0, sin i, -cos i)), on the spherical grid as summed (v).
+__global__ void grads3_kernel(const float4 *__restrict__ g4, const float2 *__restrict__ g2,
+                              const float4 *__restrict__ v, long long n, double sin_i,
+                              double cos_i, rt_grads3 G) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const float4 v = g4[i];
-    const double l = g2[i].x;
-    G.dT[i] = v.x;
-    G.dn_h2[i] = v.y;
-    G.dvturb[i] = v.z;
-    G.dx_co[i] = v.w;
-    G.dvx[i] = 0.0;
-    G.dvy[i] = l * sin_i;
-    G.dvz[i] = -l * cos_i;
+    const float4 a = g4[i];
+    G.dT[i] = a.x;
+    G.dn_h2[i] = a.y;
+    G.dvturb[i] = a.z;
+    G.dx_co[i] = a.w;
+    if (v) {
+      const float4 u = v[i];
+      G.dvx[i] = u.x;
+      G.dvy[i] = u.y;
+      G.dvz[i] = u.z;
+    } else {
+      const double l = g2[i].x;
+      G.dvx[i] = 0.0;
+      G.dvy[i] = l * sin_i;
+      G.dvz[i] = -l * cos_i;
+    }
   }
 }
 
@@ -523,8 +641,10 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
   constexpr bool UNIF = SPEC || (VAR & 1) != 0;  // equally spaced channels
   constexpr bool ROT = (VAR & 2) != 0;   // a rotation field (gradient with respect to it too)
   constexpr bool BOX = (VAR & 8) != 0;   // the 3-D Cartesian grid (rt_render3d_adjoint)
-  constexpr bool VLOS = ROT || BOX;      // dL/dv_los is needed (the sums az)
-  constexpr bool CAP = BOX;              // optical-depth increments capped at kDtCap
+  constexpr bool SPH = (VAR & 16) != 0;  // the 3-D spherical grid (rt_render_sph_adjoint)
+  constexpr bool GRID3 = BOX || SPH;
+  constexpr bool VLOS = ROT || GRID3;    // dL/dv_los is needed (the sums az)
+  constexpr bool CAP = GRID3;            // optical-depth increments capped at kDtCap
   constexpr int WPB = adj_wpb<LPR>();
   constexpr int R = 32 / LPR;          // rays per warp
   __shared__ __align__(16) float s_tab[kTabSeg * 4];
@@ -601,7 +721,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
       int nent = 0;  // entries kept (warp-uniform)
       for (int kb = 0; kb < nsamp; kb += LPR) {
         float4 mine;
-        if constexpr (BOX)
+        if constexpr (SPH)
+          mine = sample_physics_sph(P, s_tab, ray, ray.klo + kb + q);
+        else if constexpr (BOX)
           mine = sample_physics_box(P, s_tab, ray, ray.klo + kb + q);
         else
           mine = sample_physics<ROT, SPEC>(P, s_tab, ray, ray.klo + kb + q);
@@ -730,7 +852,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
         // physics and local derivatives of this lane's sample (records in shared memory, read
         // back by the same lane for its chain rule)
         float4 mine;
-        if constexpr (BOX)
+        if constexpr (SPH)
+          mine = physics_jac_sph(P, s_tab, ray, ray.klo + kb + q, rb);
+        else if constexpr (BOX)
           mine = physics_jac_box(P, s_tab, ray, ray.klo + kb + q, rb);
         else
           mine = physics_jac<ROT, SPEC>(P, s_tab, ray, ray.klo + kb + q, rb);
@@ -865,15 +989,15 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
           float Jv[4 * (kRec - 1)];
 #pragma unroll
           for (int i = 0; i < kRec - 1; i++) {
-            const float4 v = (i < kRec - 2 || (!SPEC && P.mod) || ROT) ? rb[(i + 1) * 32]
+            const float4 v = (i < kRec - 2 || (!SPEC && P.mod) || ROT || SPH) ? rb[(i + 1) * 32]
                                                             : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
             Jv[4 * i] = v.x;
             Jv[4 * i + 1] = v.y;
             Jv[4 * i + 2] = v.z;
             Jv[4 * i + 3] = v.w;
           }
-          if constexpr (BOX)
-            scatter_box(P, Jv, mine.x, mine.z, s.x, s.y, s.z, s.w, Gb);
+          if constexpr (GRID3)
+            scatter_3d<SPH>(P, Jv, mine.x, mine.z, s.x, s.y, s.z, s.w, Gb);
           else
             dmx = fmaxf(dmx, scatter_grad<ROT>(P, Jv, mine.x, mine.z, s.x, s.y, s.z, s.w, Gb,
                                           dmod ? dmod + (long long)pix * P.n_samples + ray.klo + kb + q
@@ -1048,6 +1172,7 @@ static GradCopies copies_of(const MarchParams &P, const AdjScratch &a, char *scr
   c.hstride = P.nr;
   c.kg = a.kg > 0 ? a.kg : 1;
   c.kh = a.kh > 0 ? a.kh : 1;
+  c.v = nullptr;
   return c;
 }
 
@@ -1144,17 +1269,20 @@ int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target,
   return set_error(RT_EINVAL, "no adjoint layout for %d channels", P.nch);
 }
 
-// The adjoint on the 3-D Cartesian grid (P.box, node records in P.node_a / node_b): scratch
-// for the kept optical depths, one FP32 gradient copy ({dT, dn, dvt, dX} and {dv_los, 0} per
-// node) and the work counter; zero, march, write the FP64 gradients.
+// The adjoint on a 3-D grid (P.box or P.sph, node records in P.node_a / node_b): scratch for
+// the kept optical depths, one FP32 gradient copy ({dT, dn, dvt, dX} per node, and {dv_los, 0}
+// per node on the Cartesian grid or {dv_r, dv_theta, dv_phi, 0} on the spherical one) and the
+// work counter; zero, march, write the FP64 gradients.
 template <int LPR, int CPL, int VAR>
 static int launch_adj3_t(const MarchParams &P, const float *dLdc, const float *target,
                          float *cube_out, const rt_grads3 &G3, cudaStream_t stream) {
-  const long long nodes = (long long)P.n3x * P.n3y * P.n3z;
+  constexpr bool SPH = (VAR & 16) != 0;
+  const long long nodes = SPH ? (long long)P.snr * P.snth * P.snph
+                              : (long long)P.n3x * P.n3y * P.n3z;
   const long long blocks = adj_blocks<LPR, CPL, VAR>(P, 0);
   const size_t ck = align256((size_t)blocks * adj_block_bytes<LPR, CPL>(P));
   const size_t g4 = align256((size_t)nodes * sizeof(float4));
-  const size_t g2 = align256((size_t)nodes * sizeof(float2));
+  const size_t g2 = align256((size_t)nodes * (SPH ? sizeof(float4) : sizeof(float2)));
   char *scratch = nullptr;
   cudaError_t e = stream_alloc((void **)&scratch, ck + g4 + g2 + 256, stream);
   if (e != cudaSuccess)
@@ -1167,7 +1295,8 @@ static int launch_adj3_t(const MarchParams &P, const float *dLdc, const float *t
   if (rc == RT_OK) {
     GradCopies c;
     c.g = reinterpret_cast<float4 *>(scratch + ck);
-    c.h = reinterpret_cast<float2 *>(scratch + ck + g4);
+    c.h = SPH ? nullptr : reinterpret_cast<float2 *>(scratch + ck + g4);
+    c.v = SPH ? reinterpret_cast<float4 *>(scratch + ck + g4) : nullptr;
     c.gstride = c.hstride = nodes;
     c.kg = c.kh = 1;
     rt_grads G = {};
@@ -1179,8 +1308,8 @@ static int launch_adj3_t(const MarchParams &P, const float *dLdc, const float *t
         Q, dLdc, target, cube_out, G, reinterpret_cast<float *>(scratch),
         adj_batches<LPR>(P.n_samples), nullptr, nullptr, c);
     const long long nb = (nodes + 255) / 256;
-    box_grads_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, stream>>>(
-        c.g, c.h, nodes, (double)P.sin_if, (double)P.cos_if, G3);
+    grads3_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, stream>>>(
+        c.g, c.h, c.v, nodes, (double)P.sin_if, (double)P.cos_if, G3);
     e = cudaGetLastError();
     if (e != cudaSuccess) rc = set_error(RT_ECUDA, "3-D adjoint launch: %s", cudaGetErrorString(e));
   }
@@ -1192,10 +1321,14 @@ int launch_adjoint3(const MarchParams &P, const float *dLdc, const float *target
                     float *cube_out, const rt_grads3 &G3, cudaStream_t stream) {
   int LPR, CPL;
   adj_layout(P.nch, &LPR, &CPL);
-#define X(L, C)                                                                          \
-  if (LPR == L && CPL == C)                                                              \
-    return P.v_uniform ? launch_adj3_t<L, C, 9>(P, dLdc, target, cube_out, G3, stream)   \
-                       : launch_adj3_t<L, C, 8>(P, dLdc, target, cube_out, G3, stream);
+#define X(L, C)                                                                            \
+  if (LPR == L && CPL == C) {                                                              \
+    if (P.sph)                                                                             \
+      return P.v_uniform ? launch_adj3_t<L, C, 17>(P, dLdc, target, cube_out, G3, stream)  \
+                         : launch_adj3_t<L, C, 16>(P, dLdc, target, cube_out, G3, stream); \
+    return P.v_uniform ? launch_adj3_t<L, C, 9>(P, dLdc, target, cube_out, G3, stream)     \
+                       : launch_adj3_t<L, C, 8>(P, dLdc, target, cube_out, G3, stream);    \
+  }
   RTB_ADJ_LAYOUTS(X)
 #undef X
   return set_error(RT_EINVAL, "no adjoint layout for %d channels", P.nch);

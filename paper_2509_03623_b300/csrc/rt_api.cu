@@ -497,6 +497,51 @@ extern "C" int rt_render3d(const rt_grid3 *grid3, const rt_fields3 *fields3,
   return rc;
 }
 
+namespace rtb {
+
+// Argument checks, node packing and the fused adjoint on a 3-D grid (P built by
+// build_params3 or build_params_sph; f3 its fields in the packing order).
+static int adjoint3_call(MarchParams &P, const rt_fields3 &f3, long long nodes,
+                         const float *dL_dcube, const float *target, float *cube_out,
+                         const rt_grads3 *grads, cudaStream_t st) {
+  if (!grads || !grads->dT || !grads->dn_h2 || !grads->dvturb || !grads->dx_co || !grads->dvx ||
+      !grads->dvy || !grads->dvz)
+    return set_error(RT_EINVAL, "null gradient output");
+  const long long n = (long long)P.nx * P.ny * P.nch;
+  if (n > 0 && ((dL_dcube == nullptr) == (target == nullptr)))
+    return set_error(RT_EINVAL, "give exactly one of dL_dcube and target");
+  if (n == 0) {  // no ray or no channel: the gradients are zero
+    cudaError_t e = cudaSuccess;
+    double *out[7] = {grads->dT, grads->dn_h2, grads->dvturb, grads->dx_co,
+                      grads->dvx, grads->dvy, grads->dvz};
+    for (int k = 0; k < 7 && e == cudaSuccess; k++)
+      e = cudaMemsetAsync(out[k], 0, (size_t)nodes * sizeof(double), st);
+    if (e == cudaSuccess && grads->loss) e = cudaMemsetAsync(grads->loss, 0, sizeof(double), st);
+    if (e != cudaSuccess) return set_error(RT_ECUDA, "memset: %s", cudaGetErrorString(e));
+    return RT_OK;
+  }
+  float4 *buf = nullptr;
+  cudaError_t e = stream_alloc((void **)&buf, (size_t)nodes * 2 * sizeof(float4), st);
+  if (e != cudaSuccess)
+    return set_error(RT_ENOMEM, "node records (%lld nodes): %s", nodes, cudaGetErrorString(e));
+  int rc = RT_OK;
+  const long long nb = (nodes + 255) / 256;
+  pack_nodes3_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(f3, nodes, buf,
+                                                                       buf + nodes);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    rc = set_error(RT_ECUDA, "node packing: %s", cudaGetErrorString(e));
+  } else {
+    P.node_a = buf;
+    P.node_b = buf + nodes;
+    rc = launch_adjoint3(P, dL_dcube, target, cube_out, *grads, st);
+  }
+  cudaFreeAsync(buf, st);
+  return rc;
+}
+
+}  // namespace rtb
+
 extern "C" int rt_render3d_adjoint(const rt_grid3 *grid3, const rt_fields3 *fields3,
                                    const rt_geom *geom, const rt_view *view,
                                    const rt_line *line, const float *dL_dcube,
@@ -505,41 +550,34 @@ extern "C" int rt_render3d_adjoint(const rt_grid3 *grid3, const rt_fields3 *fiel
   MarchParams *P = new (std::nothrow) MarchParams;
   if (!P) return set_error(RT_ENOMEM, "host allocation failed");
   int rc = build_params3(grid3, fields3, geom, view, line, P);
-  const long long nodes = rc == RT_OK ? (long long)grid3->nx * grid3->ny * grid3->nz : 0;
-  if (rc == RT_OK && (!grads || !grads->dT || !grads->dn_h2 || !grads->dvturb ||
-                      !grads->dx_co || !grads->dvx || !grads->dvy || !grads->dvz))
-    rc = set_error(RT_EINVAL, "null gradient output");
-  const long long n = rc == RT_OK ? (long long)P->nx * P->ny * P->nch : 0;
-  if (rc == RT_OK && n > 0 && ((dL_dcube == nullptr) == (target == nullptr)))
-    rc = set_error(RT_EINVAL, "give exactly one of dL_dcube and target");
-  cudaStream_t st = (cudaStream_t)stream;
-  if (rc == RT_OK && n == 0) {  // no ray or no channel: the gradients are zero
-    cudaError_t e = cudaSuccess;
-    double *out[7] = {grads->dT, grads->dn_h2, grads->dvturb, grads->dx_co,
-                      grads->dvx, grads->dvy, grads->dvz};
-    for (int k = 0; k < 7 && e == cudaSuccess; k++)
-      e = cudaMemsetAsync(out[k], 0, (size_t)nodes * sizeof(double), st);
-    if (e == cudaSuccess && grads->loss) e = cudaMemsetAsync(grads->loss, 0, sizeof(double), st);
-    if (e != cudaSuccess) rc = set_error(RT_ECUDA, "memset: %s", cudaGetErrorString(e));
-  } else if (rc == RT_OK) {
-    float4 *buf = nullptr;
-    cudaError_t e = stream_alloc((void **)&buf, (size_t)nodes * 2 * sizeof(float4), st);
-    if (e != cudaSuccess) {
-      rc = set_error(RT_ENOMEM, "node records (%lld nodes): %s", nodes, cudaGetErrorString(e));
-    } else {
-      const long long nb = (nodes + 255) / 256;
-      pack_nodes3_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(*fields3, nodes, buf,
-                                                                           buf + nodes);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) {
-        rc = set_error(RT_ECUDA, "node packing: %s", cudaGetErrorString(e));
-      } else {
-        P->node_a = buf;
-        P->node_b = buf + nodes;
-        rc = launch_adjoint3(*P, dL_dcube, target, cube_out, *grads, st);
-      }
-      cudaFreeAsync(buf, st);
-    }
+  if (rc == RT_OK)
+    rc = adjoint3_call(*P, *fields3, (long long)grid3->nx * grid3->ny * grid3->nz, dL_dcube,
+                       target, cube_out, grads, (cudaStream_t)stream);
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+extern "C" int rt_render_sph_adjoint(const rt_grid_sph *grid, const rt_fields_sph *fields,
+                                     const rt_geom *geom, const rt_view *view,
+                                     const rt_line *line, const float *dL_dcube,
+                                     const float *target, float *cube_out,
+                                     const rt_grads3 *grads, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params_sph(grid, fields, geom, view, line, P);
+  if (rc == RT_OK) {
+    rt_fields3 f3;
+    f3.T_K = fields->T_K;
+    f3.n_h2_cm3 = fields->n_h2_cm3;
+    f3.vturb = fields->vturb;
+    f3.x_co = fields->x_co;
+    f3.vx_kms = fields->vr_kms;
+    f3.vy_kms = fields->vth_kms;
+    f3.vz_kms = fields->vph_kms;
+    f3.vturb_mach = fields->vturb_mach;
+    rc = adjoint3_call(*P, f3, (long long)grid->nr * grid->nth * grid->nph, dL_dcube, target,
+                       cube_out, grads, (cudaStream_t)stream);
   }
   delete P;
   if (rc == RT_OK) clear_error();

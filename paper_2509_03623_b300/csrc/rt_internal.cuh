@@ -891,7 +891,7 @@ int launch_adjoint(const MarchParams &P, const float *dLdc, const float *target,
                    const rt_grads &G, cudaStream_t stream, float4 *dmod = nullptr,
                    unsigned *dmax = nullptr);
 void adj_layout(int nch, int *lpr, int *cpl);
-// the fused adjoint on the 3-D Cartesian grid (P.box with its node records packed)
+// the fused adjoint on a 3-D grid (P.box or P.sph, with its node records packed)
 int launch_adjoint3(const MarchParams &P, const float *dLdc, const float *target,
                     float *cube_out, const rt_grads3 &G3, cudaStream_t stream);
 size_t adjoint_scratch_bytes(const MarchParams &P, long long cap_blocks);
