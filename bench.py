@@ -875,6 +875,22 @@ def run_profile(args):
     build.build()
     dev = torch.device("cuda", 0)
     name = args.profile
+    if name in ("box_adjoint", "sph_adjoint"):
+        if name == "box_adjoint":
+            p = synth.config_box(0)
+            dg = _rt.DeviceGrid3(p, dev)
+            cube = _rt.rt_render3d(p, dg)
+            adjoint = _rt.rt_render3d_adjoint
+        else:
+            p = synth.config_sph(0)
+            dg = _rt.DeviceGridSph(p, dev)
+            cube = _rt.rt_render_sph(p, dg)
+            adjoint = _rt.rt_render_sph_adjoint
+        tgt = (cube * 1.05).contiguous()
+        for _ in range(args.profile_reps):
+            adjoint(p, dg, target=tgt, cube_out=None)
+        torch.cuda.synchronize()
+        return 0
     if name == "sph":
         p = synth.config_sph(0)
         dg = _rt.DeviceGridSph(p, dev)
@@ -923,7 +939,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--profile", default=None,
                     choices=["forward", "adjoint", "small_adjoint", "neural", "neural_adjoint",
-                             "mlp_eval", "sph"],
+                             "mlp_eval", "sph", "box_adjoint", "sph_adjoint"],
                     help="run one workload --profile-reps times for an ncu capture and exit")
     ap.add_argument("--profile-reps", type=int, default=3)
     ap.add_argument("--profile-px", type=int, default=128,
