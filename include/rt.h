@@ -435,7 +435,8 @@ int rt_render3d_adjoint(const rt_grid3 *grid3, const rt_fields3 *fields3, const 
  *   vr_kms, vth_kms, vph_kms (km/s).
  * cube: DEVICE [nch][ny][nx] float32, caller-allocated, overwritten.
  * The call packs the node fields into two float4 records per node (a stream-ordered
- * allocation of 32 bytes per node, freed after the launch). Forward only.
+ * allocation of 32 bytes per node, freed after the launch). Its reverse mode is
+ * rt_render_sph_adjoint (below).
  * Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
  */
 typedef struct {
