@@ -7,6 +7,8 @@ FieldChainFn: forward  -> rt_field_chain (T -> n_H2, h_lo, h_hi)
               backward -> rt_field_chain_adjoint
 PressureVphiFn: forward  -> rt_pressure_vphi (n_H2, T -> v_phi)
                 backward -> rt_pressure_vphi_adjoint
+Render3Fn: forward  -> rt_render3d / rt_render_sph (3-D Cartesian or spherical grid)
+           backward -> rt_render3d_adjoint / rt_render_sph_adjoint
 so that with n, h_lo, h_hi = field_chain(problem, chain, T), vphi = pressure_vphi(problem, n, T)
 and cube = render(problem, T, n, vt, h_lo, h_hi, vphi) a loss differentiates with respect to T
 through the march, the rotation and the chain.
@@ -103,3 +105,43 @@ class PressureVphiFn(torch.autograd.Function):
 def pressure_vphi(problem, n, T):
     """Differentiable pressure-corrected rotation [nz][nr] km/s from n_H2 and T (CUDA)."""
     return PressureVphiFn.apply(n, T, problem)
+
+
+class _Grid3Fields:
+    def __init__(self, keys, ts):
+        for k, t in zip(keys, ts):
+            setattr(self, k, t)
+
+
+class Render3Fn(torch.autograd.Function):
+    """cube = render through a 3-D grid of the problem (problem.g3: Cartesian, fields T, n_H2,
+    v_turb, X_CO, v_x, v_y, v_z; problem.gs: spherical, fields T, n_H2, v_turb, X_CO, v_r,
+    v_theta, v_phi), for a fixed geometry, view and line: forward rt_render3d / rt_render_sph,
+    backward rt_render3d_adjoint / rt_render_sph_adjoint seeded with the incoming cube
+    gradient."""
+
+    @staticmethod
+    def forward(ctx, problem, *fields):
+        ts = [x.detach().contiguous().float() for x in fields]
+        ctx.save_for_backward(*ts)
+        ctx.problem = problem
+        if getattr(problem, "gs", None) is not None:
+            return _rt.rt_render_sph(problem, _Grid3Fields(_rt.DeviceGridSph.FIELDS, ts))
+        return _rt.rt_render3d(problem, _Grid3Fields(_rt.DeviceGrid3.FIELDS, ts))
+
+    @staticmethod
+    def backward(ctx, grad_cube):
+        ts = ctx.saved_tensors
+        sph = getattr(ctx.problem, "gs", None) is not None
+        keys = _rt.DeviceGridSph.FIELDS if sph else _rt.DeviceGrid3.FIELDS
+        adjoint = _rt.rt_render_sph_adjoint if sph else _rt.rt_render3d_adjoint
+        _, g = adjoint(ctx.problem, _Grid3Fields(keys, ts),
+                       dL_dcube=grad_cube.contiguous().float(), cube_out=None)
+        return (None, *[g[k].to(t.dtype) for k, t in zip(keys, ts)])
+
+
+def render3(problem, *fields):
+    """Differentiable forward render through the problem's 3-D grid: the seven node fields in
+    the order of DeviceGrid3.FIELDS (Cartesian) or DeviceGridSph.FIELDS (spherical), CUDA
+    float32 tensors in the grid's node order."""
+    return Render3Fn.apply(problem, *fields)
