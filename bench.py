@@ -503,8 +503,12 @@ def box_leg(dev, flush, reps=10):
     # forward + fused adjoint through the box (rt_render3d_adjoint), sum-of-squares loss
     # against a fixed target cube
     ta = _adjoint3_time(dev, flush, p, _rt.rt_render3d_adjoint, dg, reps // 2)
+    rec = _rt.rt_pack_nodes3(p, dg)
+    tp = _grid3d_time(dev, flush, p, lambda q, r, cube, stream=None:
+                      _rt.rt_render_packed(q, r, cube, stream), rec, reps)
     return {"workload": p.name, "ms": t, "value": p.evals / (t * 1e-3) / 1e9,
             "unit": "Gevals/s", "nodes": p.g3.nx * p.g3.ny * p.g3.nz,
+            "ms_packed": tp, "value_packed": p.evals / (tp * 1e-3) / 1e9,
             "fwd_adjoint_ms": ta, "fwd_adjoint_value": p.evals / (ta * 1e-3) / 1e9,
             "note": "nominal sample-channel evaluations / time; includes packing the 7 node "
                     "fields into two float4 records (64 MB); fwd_adjoint: rt_render3d_adjoint "
@@ -531,11 +535,17 @@ def sph_leg(dev, flush, reps=10):
         sweep.append({"px": nx, "channels": nch, "ms": tq,
                       "value": q.evals / (tq * 1e-3) / 1e9})
     ta = _adjoint3_time(dev, flush, p, _rt.rt_render_sph_adjoint, dg, reps // 2)
+    # the same render from node records packed once (rt_pack_nodes3 + rt_render_sph_packed)
+    rec = _rt.rt_pack_nodes3(p, dg)
+    tp = _grid3d_time(dev, flush, p, lambda q, r, cube, stream=None:
+                      _rt.rt_render_packed(q, r, cube, stream), rec, reps)
     return {"workload": p.name, "ms": t, "value": p.evals / (t * 1e-3) / 1e9,
             "unit": "Gevals/s", "nodes": g.nr * g.nth * g.nph, "sweep": sweep,
+            "ms_packed": tp, "value_packed": p.evals / (tp * 1e-3) / 1e9,
             "fwd_adjoint_ms": ta, "fwd_adjoint_value": p.evals / (ta * 1e-3) / 1e9,
             "note": "nominal sample-channel evaluations / time; includes packing the 7 node "
-                    "fields into two float4 records (403 MB); sweep: 512 samples per ray; "
+                    "fields into two float4 records (403 MB); ms_packed: from records packed "
+                    "once (rt_pack_nodes3), no packing in the call; sweep: 512 samples per ray; "
                     "fwd_adjoint: rt_render_sph_adjoint (gradients of all 7 node fields, "
                     "FP32 copy of 32 B per node written out in FP64), L2 flushed before each"}
 

@@ -377,6 +377,33 @@ typedef struct {
 int rt_render3d(const rt_grid3 *grid3, const rt_fields3 *fields3, const rt_geom *geom,
                 const rt_view *view, const rt_line *line, float *cube, void *stream);
 
+/*
+ * rt_pack_nodes3 -- the node records the 3-D renders read, packed once so that several
+ * renders of the same fields (other views, channel sets, image sizes: the sweeps of the paper's
+ * runtime benchmark) skip the packing each rt_render3d / rt_render_sph call does. No
+ * counterpart in the paper (a re-layout of its fields; the renders are those of Eq. rt-int).
+ * fields3: DEVICE float32 node fields as rt_render3d takes them; for a spherical grid pass
+ *   v_r, v_theta, v_phi as vx_kms, vy_kms, vz_kms (vturb_mach is not read here).
+ * nodes: number of nodes (nx ny nz, or nr nth nph), 1 .. 2^28.
+ * records: DEVICE, 16-byte aligned, 32 bytes x nodes, caller-allocated and owned, overwritten:
+ *   nodes float4 {T_K, n_h2_cm3, vturb, x_co} followed by nodes float4 {v0, v1, v2, 0}, in the
+ *   fields' node order. Stream-ordered on `stream`; the records depend on nothing else.
+ * Returns RT_OK, RT_EINVAL or RT_ECUDA.
+ */
+int rt_pack_nodes3(const rt_fields3 *fields3, long long nodes, void *records, void *stream);
+
+/*
+ * rt_render3d_packed (and rt_render_sph_packed, declared after the spherical grid's types) --
+ * rt_render3d / rt_render_sph from node records
+ * packed by rt_pack_nodes3 for the same grid (same results bit for bit; no packing and no
+ * node-record allocation in the call). vturb_mach as rt_fields3.vturb_mach /
+ * rt_fields_sph.vturb_mach; the other arguments as the unpacked renders.
+ * Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
+ */
+int rt_render3d_packed(const rt_grid3 *grid3, const void *records, int vturb_mach,
+                       const rt_geom *geom, const rt_view *view, const rt_line *line,
+                       float *cube, void *stream);
+
 /* Gradient outputs of rt_render3d_adjoint: DEVICE float64 arrays [nz][ny][nx] (x fastest,
    like the fields of rt_fields3), overwritten by the call. */
 typedef struct {
@@ -471,6 +498,11 @@ int rt_render_sph_adjoint(const rt_grid_sph *grid, const rt_fields_sph *fields,
                           const rt_geom *geom, const rt_view *view, const rt_line *line,
                           const float *dL_dcube, const float *target, float *cube_out,
                           const rt_grads3 *grads, void *stream);
+
+/* rt_render_sph from node records packed by rt_pack_nodes3 (see rt_render3d_packed). */
+int rt_render_sph_packed(const rt_grid_sph *grid, const void *records, int vturb_mach,
+                         const rt_geom *geom, const rt_view *view, const rt_line *line,
+                         float *cube, void *stream);
 
 /*
  * rt_pressure_vphi -- pressure-corrected rotation on the nodes (Methods, "Parametric Disk

@@ -188,6 +188,14 @@ def lib():
                                                 P(rt_view), P(rt_line), C.c_void_p, C.c_void_p,
                                                 C.c_void_p, P(rt_grads3), C.c_void_p]
             L.rt_render_sph_adjoint.restype = C.c_int
+            L.rt_pack_nodes3.argtypes = [P(rt_fields3), C.c_longlong, C.c_void_p, C.c_void_p]
+            L.rt_pack_nodes3.restype = C.c_int
+            L.rt_render3d_packed.argtypes = [P(rt_grid3), C.c_void_p, C.c_int, P(rt_geom),
+                                             P(rt_view), P(rt_line), C.c_void_p, C.c_void_p]
+            L.rt_render3d_packed.restype = C.c_int
+            L.rt_render_sph_packed.argtypes = [P(rt_grid_sph), C.c_void_p, C.c_int, P(rt_geom),
+                                               P(rt_view), P(rt_line), C.c_void_p, C.c_void_p]
+            L.rt_render_sph_packed.restype = C.c_int
             L.rt_render_plain.argtypes = base + [C.c_void_p, C.c_void_p]
             L.rt_render_plain.restype = C.c_int
             L.rt_render_dense.argtypes = base + [C.c_void_p, C.c_void_p]
@@ -647,6 +655,60 @@ def rt_render_sph_adjoint(problem, grid=None, dL_dcube=None, target=None, cube_o
                                       C.byref(ln), _ptr(dL_dcube), _ptr(target), _ptr(cube),
                                       C.byref(gr), stream_handle(stream)))
     return cube, out
+
+
+def rt_pack_nodes3(problem, grid=None, out=None, stream=None):
+    """Node records of the problem's 3-D grid (Cartesian problem.g3 or spherical problem.gs)
+    packed once through rt_pack_nodes3: a CUDA float32 tensor [2][nodes][4] for
+    rt_render3d_packed / rt_render_sph_packed."""
+    import torch
+    sph = getattr(problem, "gs", None) is not None
+    if sph:
+        dg = grid if grid is not None else DeviceGridSph(problem)
+        keys, g = DeviceGridSph.FIELDS, problem.gs
+        nodes = int(g.nr) * int(g.nth) * int(g.nph)
+    else:
+        dg = grid if grid is not None else DeviceGrid3(problem)
+        keys, g = DeviceGrid3.FIELDS, problem.g3
+        nodes = int(g.nx) * int(g.ny) * int(g.nz)
+    for k in keys:
+        t = getattr(dg, k)
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != nodes:
+            raise ValueError(f"3-D field {k} must be a contiguous CUDA float32 tensor of {nodes} nodes")
+    f = rt_fields3(*(getattr(dg, k).data_ptr() for k in keys), int(problem.vturb_mach))
+    if out is None:
+        out = torch.empty((2, nodes, 4), dtype=torch.float32, device=dg.T.device)
+    check(lib().rt_pack_nodes3(C.byref(f), nodes, _ptr(out), stream_handle(stream)))
+    return out
+
+
+def rt_render_packed(problem, records, out=None, stream=None):
+    """Forward render through the problem's 3-D grid from records of rt_pack_nodes3
+    (rt_render3d_packed or rt_render_sph_packed); returns the cube [nch][ny][nx] float32."""
+    import torch
+    if not records.is_cuda or not records.is_contiguous() or records.dtype != torch.float32:
+        raise ValueError("records must be a contiguous CUDA float32 tensor from rt_pack_nodes3")
+    o, v, vw, ln = _view_line_geom(problem)
+    if out is None:
+        out = torch.empty((vw.nch, vw.ny, vw.nx), dtype=torch.float32, device=records.device)
+    if getattr(problem, "gs", None) is not None:
+        gs = problem.gs
+        if records.numel() != 8 * int(gs.nr) * int(gs.nth) * int(gs.nph):
+            raise ValueError("records do not match the spherical grid")
+        gg = rt_grid_sph(int(gs.nr), int(gs.nth), int(gs.nph), int(gs.r_log), float(gs.r_in),
+                         float(gs.r_out), float(gs.th0), float(gs.th1))
+        check(lib().rt_render_sph_packed(C.byref(gg), _ptr(records), int(problem.vturb_mach),
+                                         C.byref(o), C.byref(vw), C.byref(ln), _ptr(out),
+                                         stream_handle(stream)))
+    else:
+        g3 = problem.g3
+        if records.numel() != 8 * int(g3.nx) * int(g3.ny) * int(g3.nz):
+            raise ValueError("records do not match the 3-D grid")
+        gg = rt_grid3(int(g3.nx), int(g3.ny), int(g3.nz), *(float(v) for v in g3.extent))
+        check(lib().rt_render3d_packed(C.byref(gg), _ptr(records), int(problem.vturb_mach),
+                                       C.byref(o), C.byref(vw), C.byref(ln), _ptr(out),
+                                       stream_handle(stream)))
+    return out
 
 
 def rt_render3d(problem, grid=None, out=None, stream=None):

@@ -323,12 +323,25 @@ __global__ void pack_nodes3_kernel(const rt_fields3 f, long long n, float4 *__re
   }
 }
 
+// The parameters of a 3-D Cartesian render from the grid and the turbulence mode (the field
+// pointers are checked by the callers that read them).
+static int build_params3_core(const rt_grid3 *grid, int vturb_mach, const rt_geom *geom,
+                              const rt_view *view, const rt_line *line, MarchParams *P);
+
 static int build_params3(const rt_grid3 *grid, const rt_fields3 *fields, const rt_geom *geom,
                          const rt_view *view, const rt_line *line, MarchParams *P) {
-  if (!grid || !fields || !geom || !view || !line || !P)
+  if (!fields) return set_error(RT_EINVAL, "null argument struct");
+  const rt_fields3 &f = *fields;
+  if (!f.T_K || !f.n_h2_cm3 || !f.vturb || !f.x_co || !f.vx_kms || !f.vy_kms || !f.vz_kms)
+    return set_error(RT_EINVAL, "null field pointer");
+  return build_params3_core(grid, f.vturb_mach, geom, view, line, P);
+}
+
+static int build_params3_core(const rt_grid3 *grid, int vturb_mach, const rt_geom *geom,
+                              const rt_view *view, const rt_line *line, MarchParams *P) {
+  if (!grid || !geom || !view || !line || !P)
     return set_error(RT_EINVAL, "null argument struct");
   const rt_grid3 &g = *grid;
-  const rt_fields3 &f = *fields;
   if (g.nx < 2 || g.ny < 2 || g.nz < 2 || (long long)g.nx * g.ny * g.nz > (1LL << 28))
     return set_error(RT_EINVAL, "3-D grid needs >= 2 nodes per axis and <= 2^28 nodes "
                      "(got %d x %d x %d)", g.nx, g.ny, g.nz);
@@ -337,8 +350,6 @@ static int build_params3(const rt_grid3 *grid, const rt_fields3 *fields, const r
     if (!is_finite(ext[k])) return set_error(RT_EINVAL, "non-finite box extent");
   if (!(g.x1_au > g.x0_au) || !(g.y1_au > g.y0_au) || !(g.z1_au > g.z0_au))
     return set_error(RT_EINVAL, "box extents need x0 < x1, y0 < y1, z0 < z1");
-  if (!f.T_K || !f.n_h2_cm3 || !f.vturb || !f.x_co || !f.vx_kms || !f.vy_kms || !f.vz_kms)
-    return set_error(RT_EINVAL, "null field pointer");
   int rc = check_common(*geom, *view, *line);
   if (rc != RT_OK) return rc;
   memset(P, 0, sizeof(*P));
@@ -364,7 +375,7 @@ static int build_params3(const rt_grid3 *grid, const rt_fields3 *fields, const r
   axis(g.x0_au, g.x1_au, g.nx, &P->g3kx, &P->g3cx, &P->g3sx);
   axis(g.y0_au, g.y1_au, g.ny, &P->g3ky, &P->g3cy, &P->g3sy);
   axis(g.z0_au, g.z1_au, g.nz, &P->g3kz, &P->g3cz, &P->g3sz);
-  P->vturb_mach = f.vturb_mach ? 1 : 0;
+  P->vturb_mach = vturb_mach ? 1 : 0;
   double reach = 0.0;
   for (int k = 0; k < 6; k++) reach = fmax(reach, fabs(ext[k]));
   fill_common(*geom, *view, *line, reach, P);
@@ -372,13 +383,26 @@ static int build_params3(const rt_grid3 *grid, const rt_fields3 *fields, const r
   return RT_OK;
 }
 
+// The parameters of a spherical render from the grid and the turbulence mode (the field
+// pointers are checked by the callers that read them).
+static int build_params_sph_core(const rt_grid_sph *grid, int vturb_mach, const rt_geom *geom,
+                                 const rt_view *view, const rt_line *line, MarchParams *P);
+
 static int build_params_sph(const rt_grid_sph *grid, const rt_fields_sph *fields,
                             const rt_geom *geom, const rt_view *view, const rt_line *line,
                             MarchParams *P) {
-  if (!grid || !fields || !geom || !view || !line || !P)
+  if (!fields) return set_error(RT_EINVAL, "null argument struct");
+  const rt_fields_sph &f = *fields;
+  if (!f.T_K || !f.n_h2_cm3 || !f.vturb || !f.x_co || !f.vr_kms || !f.vth_kms || !f.vph_kms)
+    return set_error(RT_EINVAL, "null field pointer");
+  return build_params_sph_core(grid, f.vturb_mach, geom, view, line, P);
+}
+
+static int build_params_sph_core(const rt_grid_sph *grid, int vturb_mach, const rt_geom *geom,
+                                 const rt_view *view, const rt_line *line, MarchParams *P) {
+  if (!grid || !geom || !view || !line || !P)
     return set_error(RT_EINVAL, "null argument struct");
   const rt_grid_sph &g = *grid;
-  const rt_fields_sph &f = *fields;
   if (g.nr < 2 || g.nth < 2 || g.nph < 1 || (long long)g.nr * g.nth * g.nph > (1LL << 28))
     return set_error(RT_EINVAL, "spherical grid needs nr, nth >= 2, nph >= 1 and <= 2^28 "
                      "nodes (got %d x %d x %d)", g.nr, g.nth, g.nph);
@@ -389,8 +413,6 @@ static int build_params_sph(const rt_grid_sph *grid, const rt_fields_sph *fields
   if (!is_finite(g.th0_rad) || !is_finite(g.th1_rad) || !(g.th0_rad >= 0) ||
       !(g.th1_rad > g.th0_rad) || !(g.th1_rad <= 3.14159265358979323846))
     return set_error(RT_EINVAL, "colatitudes need 0 <= th0 < th1 <= pi");
-  if (!f.T_K || !f.n_h2_cm3 || !f.vturb || !f.x_co || !f.vr_kms || !f.vth_kms || !f.vph_kms)
-    return set_error(RT_EINVAL, "null field pointer");
   int rc = check_common(*geom, *view, *line);
   if (rc != RT_OK) return rc;
   memset(P, 0, sizeof(*P));
@@ -415,7 +437,7 @@ static int build_params_sph(const rt_grid_sph *grid, const rt_fields_sph *fields
   P->th_scale = (float)((g.nth - 1) / (g.th1_rad - g.th0_rad));
   P->ph_scale = (float)(g.nph / (2.0 * 3.14159265358979323846));
   P->R_cyl = g.r_out_au;
-  P->vturb_mach = f.vturb_mach ? 1 : 0;
+  P->vturb_mach = vturb_mach ? 1 : 0;
   fill_common(*geom, *view, *line, g.r_out_au, P);
   P->cos_if = (float)P->cos_i;
   return RT_OK;
@@ -579,6 +601,72 @@ extern "C" int rt_render_sph_adjoint(const rt_grid_sph *grid, const rt_fields_sp
     rc = adjoint3_call(*P, f3, (long long)grid->nr * grid->nth * grid->nph, dL_dcube, target,
                        cube_out, grads, (cudaStream_t)stream);
   }
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+extern "C" int rt_pack_nodes3(const rt_fields3 *fields3, long long nodes, void *records,
+                              void *stream) {
+  if (!fields3) return set_error(RT_EINVAL, "null argument struct");
+  const rt_fields3 &f = *fields3;
+  if (!f.T_K || !f.n_h2_cm3 || !f.vturb || !f.x_co || !f.vx_kms || !f.vy_kms || !f.vz_kms)
+    return set_error(RT_EINVAL, "null field pointer");
+  if (nodes < 1 || nodes > (1LL << 28))
+    return set_error(RT_EINVAL, "node count %lld outside 1 .. 2^28", nodes);
+  if (!records || (reinterpret_cast<uintptr_t>(records) & 15))
+    return set_error(RT_EINVAL, "records must be a 16-byte aligned device pointer");
+  float4 *a = static_cast<float4 *>(records);
+  const long long nb = (nodes + 255) / 256;
+  pack_nodes3_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, (cudaStream_t)stream>>>(
+      f, nodes, a, a + nodes);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(RT_ECUDA, "node packing: %s", cudaGetErrorString(e));
+  clear_error();
+  return RT_OK;
+}
+
+namespace rtb {
+
+// A 3-D render (P from build_params3_core or build_params_sph_core) from node records packed
+// by rt_pack_nodes3.
+static int render_packed(MarchParams &P, const void *records, long long nodes, float *cube,
+                         cudaStream_t st) {
+  const long long n = (long long)P.nx * P.ny * P.nch;
+  if (n > 0 && !cube) return set_error(RT_EINVAL, "null cube pointer");
+  if (!records || (reinterpret_cast<uintptr_t>(records) & 15))
+    return set_error(RT_EINVAL, "records must be a 16-byte aligned device pointer");
+  if (n == 0) return RT_OK;
+  P.node_a = static_cast<const float4 *>(records);
+  P.node_b = P.node_a + nodes;
+  return launch_forward(P, cube, st);
+}
+
+}  // namespace rtb
+
+extern "C" int rt_render3d_packed(const rt_grid3 *grid3, const void *records, int vturb_mach,
+                                  const rt_geom *geom, const rt_view *view, const rt_line *line,
+                                  float *cube, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params3_core(grid3, vturb_mach, geom, view, line, P);
+  if (rc == RT_OK)
+    rc = render_packed(*P, records, (long long)grid3->nx * grid3->ny * grid3->nz, cube,
+                       (cudaStream_t)stream);
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+extern "C" int rt_render_sph_packed(const rt_grid_sph *grid, const void *records, int vturb_mach,
+                                    const rt_geom *geom, const rt_view *view,
+                                    const rt_line *line, float *cube, void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params_sph_core(grid, vturb_mach, geom, view, line, P);
+  if (rc == RT_OK)
+    rc = render_packed(*P, records, (long long)grid->nr * grid->nth * grid->nph, cube,
+                       (cudaStream_t)stream);
   delete P;
   if (rc == RT_OK) clear_error();
   return rc;
