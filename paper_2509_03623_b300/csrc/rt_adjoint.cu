@@ -843,12 +843,26 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
         for (int m = 0; m < CPL / 2; m++) Tn[m] = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
       }
       int ient = nent;
-      for (int b = (nsamp + LPR - 1) / LPR - 1; b >= 0; b--) {
+      const int blast = (nsamp + LPR - 1) / LPR - 1;
+      unsigned act_next = blast >= 0 ? acts[blast] : 0u;  // read a batch ahead
+      for (int b = blast; b >= 0; b--) {
         const int kb = b * LPR;
         // the channel pairs the forward pass advanced in this batch (the same window), whose
         // entries precede the later batches'
-        const unsigned act2 = acts[b];
+        const unsigned act2 = act_next;
+        if (b > 0) act_next = acts[b - 1];
         ient -= __popc(act2);
+        // the kept depths of those pairs, loaded before the sample's physics so that their L2
+        // latency overlaps it (a batch without gas advanced no pair and loads nothing)
+        {
+          int e = ient;
+#pragma unroll
+          for (int m = 0; m < CPL / 2; m++)
+            if (act2 & (1u << m)) {  // warp-uniform
+              cur[m] = ent[(long long)e * 32];
+              e++;
+            }
+        }
         // physics and local derivatives of this lane's sample (records in shared memory, read
         // back by the same lane for its chain rule)
         float4 mine;
@@ -862,16 +876,9 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
         const float Sbefore = Snext;
         ph[rr * kPhStride + q] = mine;
         if (P.work) wc_rev += (unsigned long long)__popc(act2) * 2 * LPR * 32;
-        {
-          int e = ient;
 #pragma unroll
-          for (int m = 0; m < CPL / 2; m++)
-            if (act2 & (1u << m)) {  // warp-uniform
-              cur[m] = ent[(long long)e * 32];
-              Tn[m] = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
-              e++;
-            }
-        }
+        for (int m = 0; m < CPL / 2; m++)
+          if (act2 & (1u << m)) Tn[m] = make_float2(ex2(-cur[m].x), ex2(-cur[m].y));
         __syncwarp();
         const float2 mone = make_float2(-1.0f, -1.0f);
         // reverse step of one channel pair m at sample t of the batch: advances the suffix
