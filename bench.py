@@ -62,7 +62,7 @@ FWD_DRAM_BYTES = 7_280_896 + 24_064
 # DRAM bytes (read + write) of one fused-adjoint launch on the same workload (ncu capture of
 # march_adj_kernel<8, 8, 5>: per-batch depth entries of the advanced channel pairs, 16 MiB
 # grid-copy budget)
-ADJ_DRAM_BYTES = 30_794_496 + 44_016_128
+ADJ_DRAM_BYTES = 30_717_440 + 44_095_744
 N_SM = 148
 E2E_STREAMS = 4  # streams of the end-to-end leg
 SM_MAX_MHZ = 2032.0
