@@ -217,11 +217,12 @@ int rt_render_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *
  * cube_out (DEVICE, may be NULL) receives the rendered cube (same values as rt_render up to
  * FP32 rounding). Gradients w.r.t. every node of T, n_H2, v_turb and both surfaces
  * overwrite the FP64 arrays; with a rotation field (fields->vphi_kms) so does its gradient
- * (grads->dvphi, required then), through v_los = v_phi sin i x / r + v_sys. The call allocates and frees one device scratch buffer on
- * `stream` (stream-ordered) holding the optical-depth checkpoints (every 32
- * samples), the reverse march's per-warp record of the 32-sample segment it is reversing
- * (recomputed from the segment's checkpoint: batch optical depths, and the physics and local
- * derivatives of each sample, 64 bytes per sample, 80 with a network) and up to 32 replicated FP32
+ * (grads->dvphi, required then), through v_los = v_phi sin i x / r + v_sys. The call
+ * allocates and frees one device scratch buffer on `stream` (stream-ordered) holding, per warp
+ * of the persistent grid, the optical depths the forward pass keeps at every batch boundary
+ * (8 bytes per lane for each channel pair a batch advanced, and a one-byte pair mask per
+ * batch; the reverse pass walks the batches back to front from them, with each sample's
+ * physics and local derivatives in shared memory), and up to 32 replicated FP32
  * copies of the node gradients (at most 16 MiB, {dT, dn, dvt, dvphi} interleaved per node) plus up
  * to 128 of the surface gradients: each block of the kernel reduces into one copy, and the
  * copies are summed in FP64, in a fixed order, into the outputs at the end. Atomics on one
@@ -243,7 +244,7 @@ int rt_render_adjoint(const rt_grid *grid, const rt_fields *fields, const rt_geo
  * `work` is a DEVICE pointer to four unsigned 64-bit counters, overwritten (stream-ordered):
  *   [0] samples whose physics found gas (opacity > 0) in the forward pass,
  *   [1] sample-channel evaluations computed in the forward pass (after the channel window),
- *   [2] evaluations computed where each 32-sample segment's optical depths are recomputed,
+ *   [2] 0 (a recompute pass of an earlier design; the counter is kept for the layout),
  *   [3] evaluations computed in the reverse pass.
  */
 int rt_render_adjoint_work(const rt_grid *grid, const rt_fields *fields, const rt_geom *geom,

@@ -41,8 +41,8 @@ constexpr int adj_wpb() {
   return LPR >= 16 ? 2 : 4;
 }
 
-// Per-sample record of the segment being reversed: the physics {kd, a, b, S} and the local
-// derivatives (below), five float4 per lane and batch; without a network or a rotation field
+// Per-sample record of the batch being reversed (shared memory, one per lane): the physics
+// {kd, a, b, S} and the local derivatives (below), five float4 per lane; without a network or a rotation field
 // the fifth (J_MN, J_T, J_N, J_VPX: the network factor on n, the modulated primitives and
 // d v_los / d v_phi) is neither written nor read.
 constexpr int kRec = 5;
@@ -704,7 +704,7 @@ __global__ void __launch_bounds__(adj_wpb<LPR>() * 32, LPR >= 16 ? 7 : 4)
       const Ray ray =
           setup_ray(P, active ? (int)(pix % P.nx) : 0, active ? (int)(pix / P.nx) : 0, active);
       // the rays' gas sample ranges (samples outside are exact no-ops), counted from klo;
-      // segments and checkpoints are relative to it
+      // batches and their kept depths are relative to it
       const int nsamp = __reduce_max_sync(0xffffffffu, max(ray.khi - ray.klo + 1, 0));
 
       // ---------- forward march, keeping the optical depth at every batch boundary ----------
@@ -1094,7 +1094,8 @@ static long long adj_blocks(const MarchParams &P, long long cap_blocks) {
   return need < cap ? need : cap;
 }
 
-// Bytes of per-warp scratch (checkpoints and batch starts) one block needs.
+// Bytes of per-warp scratch (the depths kept at the batch boundaries and the batches' pair
+// masks; "checkpoints" below) one block needs.
 template <int LPR, int CPL>
 static size_t adj_block_bytes(const MarchParams &P) {
   return (size_t)adj_wpb<LPR>() * adj_warp_floats<LPR, CPL>(adj_batches<LPR>(P.n_samples)) *

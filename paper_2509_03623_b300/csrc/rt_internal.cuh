@@ -89,7 +89,8 @@ struct MarchParams {
   float h_scale;
   // optional work counters (device; nullptr for none). Forward kernel, 2 x u64: samples with
   // gas whose physics was evaluated, channel evaluations computed. Adjoint kernel, 4 x u64:
-  // samples with gas, evaluations of the forward, segment-recompute and reverse passes.
+  // samples with gas, evaluations of the forward pass, 0 (a recompute pass of an earlier
+  // design), evaluations of the reverse pass.
   unsigned long long *work;
   // optional corner quads (pack_cells): per grid cell (i, j) the four nodes its bilinear
   // interpolation reads, {f(i,j), f(i+1,j), f(i,j+1), f(i+1,j+1)}, for T, n_H2, v_turb and
