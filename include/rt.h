@@ -506,6 +506,22 @@ int rt_render_sph_packed(const rt_grid_sph *grid, const void *records, int vturb
                          float *cube, void *stream);
 
 /*
+ * rt_render3d_adjoint_packed / rt_render_sph_adjoint_packed -- rt_render3d_adjoint /
+ * rt_render_sph_adjoint from node records packed by rt_pack_nodes3 for the same grid (no
+ * packing and no node-record allocation in the call; the same gradients up to the order of
+ * the FP32 reductions). vturb_mach as the fields' flag; the other arguments as the unpacked
+ * adjoints. Returns RT_OK, RT_EINVAL, RT_ENOMEM or RT_ECUDA.
+ */
+int rt_render3d_adjoint_packed(const rt_grid3 *grid3, const void *records, int vturb_mach,
+                               const rt_geom *geom, const rt_view *view, const rt_line *line,
+                               const float *dL_dcube, const float *target, float *cube_out,
+                               const rt_grads3 *grads, void *stream);
+int rt_render_sph_adjoint_packed(const rt_grid_sph *grid, const void *records, int vturb_mach,
+                                 const rt_geom *geom, const rt_view *view, const rt_line *line,
+                                 const float *dL_dcube, const float *target, float *cube_out,
+                                 const rt_grads3 *grads, void *stream);
+
+/*
  * rt_pressure_vphi -- pressure-corrected rotation on the nodes (Methods, "Parametric Disk
  * Modeling", Eq. gas_velocity_pressure; "Neural Temperature Recovery" derives v_phi from
  * the density and temperature this way):

@@ -196,6 +196,12 @@ def lib():
             L.rt_render_sph_packed.argtypes = [P(rt_grid_sph), C.c_void_p, C.c_int, P(rt_geom),
                                                P(rt_view), P(rt_line), C.c_void_p, C.c_void_p]
             L.rt_render_sph_packed.restype = C.c_int
+            for nm, G in (("rt_render3d_adjoint_packed", rt_grid3),
+                          ("rt_render_sph_adjoint_packed", rt_grid_sph)):
+                fn = getattr(L, nm)
+                fn.argtypes = [P(G), C.c_void_p, C.c_int, P(rt_geom), P(rt_view), P(rt_line),
+                               C.c_void_p, C.c_void_p, C.c_void_p, P(rt_grads3), C.c_void_p]
+                fn.restype = C.c_int
             L.rt_render_plain.argtypes = base + [C.c_void_p, C.c_void_p]
             L.rt_render_plain.restype = C.c_int
             L.rt_render_dense.argtypes = base + [C.c_void_p, C.c_void_p]
@@ -709,6 +715,48 @@ def rt_render_packed(problem, records, out=None, stream=None):
                                        C.byref(o), C.byref(vw), C.byref(ln), _ptr(out),
                                        stream_handle(stream)))
     return out
+
+
+def rt_render_adjoint_packed(problem, records, dL_dcube=None, target=None, cube_out=True,
+                             stream=None):
+    """Fused forward + reverse march through the problem's 3-D grid from records of
+    rt_pack_nodes3 (rt_render3d_adjoint_packed / rt_render_sph_adjoint_packed). Returns
+    (cube or None, grads) as rt_render3d_adjoint / rt_render_sph_adjoint."""
+    import torch
+    if not records.is_cuda or not records.is_contiguous() or records.dtype != torch.float32:
+        raise ValueError("records must be a contiguous CUDA float32 tensor from rt_pack_nodes3")
+    sph = getattr(problem, "gs", None) is not None
+    if sph:
+        gs = problem.gs
+        shp = (int(gs.nph), int(gs.nth), int(gs.nr))
+        keys = DeviceGridSph.FIELDS
+        gg = rt_grid_sph(int(gs.nr), int(gs.nth), int(gs.nph), int(gs.r_log), float(gs.r_in),
+                         float(gs.r_out), float(gs.th0), float(gs.th1))
+    else:
+        g3 = problem.g3
+        shp = (int(g3.nz), int(g3.ny), int(g3.nx))
+        keys = DeviceGrid3.FIELDS
+        gg = rt_grid3(int(g3.nx), int(g3.ny), int(g3.nz), *(float(v) for v in g3.extent))
+    if records.numel() != 8 * shp[0] * shp[1] * shp[2]:
+        raise ValueError("records do not match the grid")
+    o, v, vw, ln = _view_line_geom(problem)
+    cshape = (vw.nch, vw.ny, vw.nx)
+    dL_dcube = _cube_arg(dL_dcube, cshape, "dL_dcube")
+    target = _cube_arg(target, cshape, "target")
+    dev = records.device
+    cube = None
+    if cube_out is True:
+        cube = torch.empty(cshape, dtype=torch.float32, device=dev)
+    elif cube_out is not None and cube_out is not False:
+        cube = _cube_arg(cube_out, cshape, "cube_out")
+    out = {k: torch.empty(shp, dtype=torch.float64, device=dev) for k in keys}
+    out["loss"] = torch.empty(1, dtype=torch.float64, device=dev)
+    gr = rt_grads3(*(out[k].data_ptr() for k in keys), out["loss"].data_ptr())
+    fn = lib().rt_render_sph_adjoint_packed if sph else lib().rt_render3d_adjoint_packed
+    check(fn(C.byref(gg), _ptr(records), int(problem.vturb_mach), C.byref(o), C.byref(vw),
+             C.byref(ln), _ptr(dL_dcube), _ptr(target), _ptr(cube), C.byref(gr),
+             stream_handle(stream)))
+    return cube, out
 
 
 def rt_render3d(problem, grid=None, out=None, stream=None):

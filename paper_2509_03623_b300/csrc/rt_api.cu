@@ -522,10 +522,11 @@ extern "C" int rt_render3d(const rt_grid3 *grid3, const rt_fields3 *fields3,
 namespace rtb {
 
 // Argument checks, node packing and the fused adjoint on a 3-D grid (P built by
-// build_params3 or build_params_sph; f3 its fields in the packing order).
-static int adjoint3_call(MarchParams &P, const rt_fields3 &f3, long long nodes,
-                         const float *dL_dcube, const float *target, float *cube_out,
-                         const rt_grads3 *grads, cudaStream_t st) {
+// build_params3(_core) or build_params_sph(_core)): from the fields f3 (in the packing order),
+// packed here, or from records already packed by rt_pack_nodes3 (f3 then unused).
+static int adjoint3_call(MarchParams &P, const rt_fields3 *f3, const void *packed,
+                         long long nodes, const float *dL_dcube, const float *target,
+                         float *cube_out, const rt_grads3 *grads, cudaStream_t st) {
   if (!grads || !grads->dT || !grads->dn_h2 || !grads->dvturb || !grads->dx_co || !grads->dvx ||
       !grads->dvy || !grads->dvz)
     return set_error(RT_EINVAL, "null gradient output");
@@ -542,14 +543,21 @@ static int adjoint3_call(MarchParams &P, const rt_fields3 &f3, long long nodes,
     if (e != cudaSuccess) return set_error(RT_ECUDA, "memset: %s", cudaGetErrorString(e));
     return RT_OK;
   }
+  if (packed) {  // node records packed by rt_pack_nodes3
+    if (reinterpret_cast<uintptr_t>(packed) & 15)
+      return set_error(RT_EINVAL, "records must be a 16-byte aligned device pointer");
+    P.node_a = static_cast<const float4 *>(packed);
+    P.node_b = P.node_a + nodes;
+    return launch_adjoint3(P, dL_dcube, target, cube_out, *grads, st);
+  }
   float4 *buf = nullptr;
   cudaError_t e = stream_alloc((void **)&buf, (size_t)nodes * 2 * sizeof(float4), st);
   if (e != cudaSuccess)
     return set_error(RT_ENOMEM, "node records (%lld nodes): %s", nodes, cudaGetErrorString(e));
   int rc = RT_OK;
   const long long nb = (nodes + 255) / 256;
-  pack_nodes3_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(f3, nodes, buf,
-                                                                       buf + nodes);
+  pack_nodes3_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(*f3, nodes, buf,
+                                                                        buf + nodes);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     rc = set_error(RT_ECUDA, "node packing: %s", cudaGetErrorString(e));
@@ -573,8 +581,8 @@ extern "C" int rt_render3d_adjoint(const rt_grid3 *grid3, const rt_fields3 *fiel
   if (!P) return set_error(RT_ENOMEM, "host allocation failed");
   int rc = build_params3(grid3, fields3, geom, view, line, P);
   if (rc == RT_OK)
-    rc = adjoint3_call(*P, *fields3, (long long)grid3->nx * grid3->ny * grid3->nz, dL_dcube,
-                       target, cube_out, grads, (cudaStream_t)stream);
+    rc = adjoint3_call(*P, fields3, nullptr, (long long)grid3->nx * grid3->ny * grid3->nz,
+                       dL_dcube, target, cube_out, grads, (cudaStream_t)stream);
   delete P;
   if (rc == RT_OK) clear_error();
   return rc;
@@ -598,8 +606,8 @@ extern "C" int rt_render_sph_adjoint(const rt_grid_sph *grid, const rt_fields_sp
     f3.vy_kms = fields->vth_kms;
     f3.vz_kms = fields->vph_kms;
     f3.vturb_mach = fields->vturb_mach;
-    rc = adjoint3_call(*P, f3, (long long)grid->nr * grid->nth * grid->nph, dL_dcube, target,
-                       cube_out, grads, (cudaStream_t)stream);
+    rc = adjoint3_call(*P, &f3, nullptr, (long long)grid->nr * grid->nth * grid->nph, dL_dcube,
+                       target, cube_out, grads, (cudaStream_t)stream);
   }
   delete P;
   if (rc == RT_OK) clear_error();
@@ -667,6 +675,42 @@ extern "C" int rt_render_sph_packed(const rt_grid_sph *grid, const void *records
   if (rc == RT_OK)
     rc = render_packed(*P, records, (long long)grid->nr * grid->nth * grid->nph, cube,
                        (cudaStream_t)stream);
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+extern "C" int rt_render3d_adjoint_packed(const rt_grid3 *grid3, const void *records,
+                                          int vturb_mach, const rt_geom *geom,
+                                          const rt_view *view, const rt_line *line,
+                                          const float *dL_dcube, const float *target,
+                                          float *cube_out, const rt_grads3 *grads,
+                                          void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params3_core(grid3, vturb_mach, geom, view, line, P);
+  if (rc == RT_OK && !records) rc = set_error(RT_EINVAL, "null records pointer");
+  if (rc == RT_OK)
+    rc = adjoint3_call(*P, nullptr, records, (long long)grid3->nx * grid3->ny * grid3->nz,
+                       dL_dcube, target, cube_out, grads, (cudaStream_t)stream);
+  delete P;
+  if (rc == RT_OK) clear_error();
+  return rc;
+}
+
+extern "C" int rt_render_sph_adjoint_packed(const rt_grid_sph *grid, const void *records,
+                                            int vturb_mach, const rt_geom *geom,
+                                            const rt_view *view, const rt_line *line,
+                                            const float *dL_dcube, const float *target,
+                                            float *cube_out, const rt_grads3 *grads,
+                                            void *stream) {
+  MarchParams *P = new (std::nothrow) MarchParams;
+  if (!P) return set_error(RT_ENOMEM, "host allocation failed");
+  int rc = build_params_sph_core(grid, vturb_mach, geom, view, line, P);
+  if (rc == RT_OK && !records) rc = set_error(RT_EINVAL, "null records pointer");
+  if (rc == RT_OK)
+    rc = adjoint3_call(*P, nullptr, records, (long long)grid->nr * grid->nth * grid->nph,
+                       dL_dcube, target, cube_out, grads, (cudaStream_t)stream);
   delete P;
   if (rc == RT_OK) clear_error();
   return rc;
